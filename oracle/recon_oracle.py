@@ -1,0 +1,337 @@
+"""FP64 CPU oracle for iterative Fourier-space reconstruction (Burden, Percival & Howlett 2015).
+
+TEST INFRASTRUCTURE ONLY.  This module is the slow, obviously-correct reference that the CUDA path
+is checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it.  The product path (``paper_1504_02591_gb300``) never imports, calls or
+links it, and it shares no code with the CUDA kernels.
+
+Everything is float64 numpy.  The 3-D FFT is ``numpy.fft.rfftn`` / ``irfftn`` used as a library
+primitive (forward e^{-ik.x} unnormalised, inverse with 1/N^3); the test suite pins it against a
+brute-force DFT.  There is no blocking, fusion or reordering beyond what the paper's equations state.
+
+Conventions (readings of the paper where it is silent or inconsistent; each is listed in the design doc):
+
+* Grid: nodes at x_i = i*H, i = 0..N-1 per axis, H = L/N, periodic.  Arrays are indexed [ix, iy, iz].
+* k_j = 2 pi m_j / L with m_j in {0..N/2-1, -N/2..-1}.  The derivative wavenumber kd_j equals k_j
+  except at the Nyquist index m_j = N/2 where it is 0 (keeps real fields real); k^2 uses the full k.
+* Zel'dovich operator (Eq. Zeldovich): Z[s](k) = i kd s(k) / k^2, with Z[s](k=0) = 0, so that
+  div Z[s] = -s (Eq. delta) for every mode whose kd = k.
+* The solved equation is Eq. Nusser with the redshift-space coefficient read as beta = f/b:
+  div Psi + beta div((Psi.r)r) = -delta/b.  With S = delta/b + beta div((Psi.r)r) this is Psi = Z[S].
+  The sign is fixed by the plane-parallel Kaiser limit S = (delta/b)/(1 + beta mu^2).
+* Smoothing kernel exp(-k^2 R^2 / 2) (the printed "-ik^2R^2/2" of Sec. 3.1 read as a real Gaussian).
+* CIC (cloud-in-cell) mass assignment on the nodes, periodic wrap; the paper bins with NGP (Sec. 3).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+LOS_RADIAL = 0
+LOS_FIXED = 1
+
+START_PLAIN = 0      # Psi_red,FFT: no RSD correction (Sec. 5.2, first starting point)
+START_APPROX1 = 1    # Eq. approx1: irrotational approximation, coefficient beta/(1+beta)
+START_FFTA = 2       # Eq. approx2: 0.75-ratio approximation, coefficient 3 beta/(7+3 beta)
+
+LOG_FLOOR = 1e-6     # floor on 1+delta before the logarithm of Eq. logdelta
+
+
+# --------------------------------------------------------------------------------------------
+# Fourier grid
+# --------------------------------------------------------------------------------------------
+def axis_wavenumbers(n: int, L: float, half: bool = False):
+    """Wavenumbers of one axis: (k, kd).  ``half`` gives the r2c axis (m = 0..n/2)."""
+    if half:
+        m = np.arange(n // 2 + 1, dtype=np.float64)
+    else:
+        m = np.fft.fftfreq(n, d=1.0 / n)
+    k = 2.0 * np.pi * m / L
+    kd = k.copy()
+    if n % 2 == 0:
+        kd[np.abs(m) == n // 2] = 0.0
+    return k, kd
+
+
+def kgrid(n: int, L: float):
+    """Broadcastable (kx, ky, kz), (kdx, kdy, kdz) and k^2 on the rfftn grid (n, n, n/2+1)."""
+    kx, kdx = axis_wavenumbers(n, L)
+    ky, kdy = axis_wavenumbers(n, L)
+    kz, kdz = axis_wavenumbers(n, L, half=True)
+    kx, ky, kz = kx[:, None, None], ky[None, :, None], kz[None, None, :]
+    kdx, kdy, kdz = kdx[:, None, None], kdy[None, :, None], kdz[None, None, :]
+    k2 = kx * kx + ky * ky + kz * kz
+    return (kx, ky, kz), (kdx, kdy, kdz), k2
+
+
+def fft3(a):
+    return np.fft.rfftn(a, axes=(0, 1, 2))
+
+
+def ifft3(A, n):
+    return np.fft.irfftn(A, s=(n, n, n), axes=(0, 1, 2))
+
+
+# --------------------------------------------------------------------------------------------
+# Mass assignment (Sec. 3: binning of tracers on the mesh; CIC instead of the paper's NGP)
+# --------------------------------------------------------------------------------------------
+def _cic_corners(pos, n, L):
+    """Yield (flat node index, weight) for the 8 CIC corners of every particle."""
+    u = np.asarray(pos, dtype=np.float64) * (n / L)
+    i0 = np.floor(u)
+    t = u - i0
+    i0 = i0.astype(np.int64)
+    for dx in (0, 1):
+        wx = t[:, 0] if dx else 1.0 - t[:, 0]
+        ix = (i0[:, 0] + dx) % n
+        for dy in (0, 1):
+            wy = t[:, 1] if dy else 1.0 - t[:, 1]
+            iy = (i0[:, 1] + dy) % n
+            for dz in (0, 1):
+                wz = t[:, 2] if dz else 1.0 - t[:, 2]
+                iz = (i0[:, 2] + dz) % n
+                yield (ix * n + iy) * n + iz, wx * wy * wz
+
+
+def cic_deposit(pos, w, n: int, L: float):
+    """rho on the n^3 nodes: sum over particles of w * prod_axis (1 - |u - i|)."""
+    pos = np.asarray(pos, dtype=np.float64)
+    w = np.ones(len(pos)) if w is None else np.asarray(w, dtype=np.float64)
+    rho = np.zeros(n * n * n)
+    for idx, cw in _cic_corners(pos, n, L):
+        rho += np.bincount(idx, weights=w * cw, minlength=n ** 3)
+    return rho.reshape(n, n, n)
+
+
+def cic_gather(field, pos, L: float):
+    """Interpolate a real field (n,n,n) or (3,n,n,n) to particles with the CIC (trilinear) kernel."""
+    field = np.asarray(field, dtype=np.float64)
+    vec = field.ndim == 4
+    n = field.shape[-1]
+    flat = field.reshape(3, -1) if vec else field.reshape(1, -1)
+    out = np.zeros((flat.shape[0], len(pos)))
+    for idx, cw in _cic_corners(pos, n, L):
+        out += flat[:, idx] * cw
+    return out.T if vec else out[0]
+
+
+# --------------------------------------------------------------------------------------------
+# Overdensity, smoothing, mask, lognormal (Sec. 3.1, 3.2, 6)
+# --------------------------------------------------------------------------------------------
+def smooth(field, R: float, L: float):
+    """Gaussian smoothing S(k) = exp(-k^2 R^2 / 2) applied in Fourier space (Sec. 3.1)."""
+    n = field.shape[0]
+    _, _, k2 = kgrid(n, L)
+    return ifft3(fft3(field) * np.exp(-0.5 * k2 * R * R), n)
+
+
+def overdensity_randoms(rho_g_s, rho_r_s, sum_wg: float, sum_wr: float, mask_frac: float):
+    """delta = rho_g,s / (alpha rho_r,s) - 1 inside the survey mask, 0 outside (Sec. 3.2).
+
+    alpha = sum w_g / sum w_r.  The binary mask keeps nodes where the smoothed random density exceeds
+    mask_frac times its mean over nodes with positive smoothed random density.
+    Returns (delta, mask, alpha, threshold).
+    """
+    alpha = sum_wg / sum_wr
+    pos = rho_r_s > 0
+    thr = mask_frac * rho_r_s[pos].mean()
+    mask = rho_r_s > thr
+    delta = np.zeros_like(rho_g_s)
+    delta[mask] = rho_g_s[mask] / (alpha * rho_r_s[mask]) - 1.0
+    return delta, mask, alpha, thr
+
+
+def overdensity_uniform(rho_g_s, sum_wg: float):
+    """delta = rho / rho_bar - 1 with rho_bar = sum w / N^3 (Sec. 2 definition, periodic box)."""
+    rho_bar = sum_wg / rho_g_s.size
+    return rho_g_s / rho_bar - 1.0
+
+
+def lognormal(delta):
+    """Eq. logdelta: delta -> ln(1 + delta) + C with C = -<ln(1 + delta)> (Sec. 6), 1+delta floored."""
+    ld = np.log(np.maximum(1.0 + delta, LOG_FLOOR))
+    return ld - ld.mean(), -ld.mean()
+
+
+# --------------------------------------------------------------------------------------------
+# Displacement operators (Eq. Zeldovich, Eq. Nusser)
+# --------------------------------------------------------------------------------------------
+def zeldovich_k(s_k, n: int, L: float):
+    """Z[s] in Fourier space: the three components i kd_j s(k) / k^2, zero at k = 0."""
+    _, kd, k2 = kgrid(n, L)
+    inv = np.zeros_like(k2)
+    np.divide(1.0, k2, out=inv, where=k2 > 0)
+    return [1j * kd[j] * s_k * inv for j in range(3)]
+
+
+def zeldovich(s, L: float):
+    """Z[s] in configuration space: Psi with div Psi = -s (Eq. Zeldovich with s the source)."""
+    n = s.shape[0]
+    return np.stack([ifft3(c, n) for c in zeldovich_k(fft3(s), n, L)])
+
+
+def divergence(v, L: float):
+    """Spectral divergence of a real vector field v (3, n, n, n), returned in Fourier space."""
+    n = v.shape[-1]
+    _, kd, _ = kgrid(n, L)
+    return sum(1j * kd[j] * fft3(v[j]) for j in range(3))
+
+
+def rhat_field(n: int, L: float, observer, los_mode: int):
+    """Unit line-of-sight vector at every node (Sec. 3.1: pointing away from the observer).
+
+    Radial mode: (x_i - observer)/|x_i - observer|, zero at a node that coincides with the observer.
+    Fixed mode: ``observer`` is read as the LOS direction and normalised (plane-parallel limit, Sec. 4.1).
+    """
+    o = np.asarray(observer, dtype=np.float64)
+    if los_mode == LOS_FIXED:
+        u = o / np.linalg.norm(o)
+        return np.broadcast_to(u[:, None, None, None], (3, n, n, n)).copy()
+    x = np.arange(n) * (L / n)
+    d = np.stack(np.meshgrid(x - o[0], x - o[1], x - o[2], indexing="ij"))
+    r = np.sqrt((d * d).sum(0))
+    out = np.zeros_like(d)
+    np.divide(d, r, out=out, where=r > 0)
+    return out
+
+
+def radial_projection(psi, rhat):
+    """(Psi . r) r at every node."""
+    u = (psi * rhat).sum(0)
+    return u * rhat
+
+
+def start_coefficient(start: int, beta: float) -> float:
+    """Coefficient c of the starting estimate Psi_0 = Z[delta/b] - c (Z[delta/b].r) r.
+
+    plain: 0; Eq. approx1: beta/(1+beta); Eq. approx2 (FFTA): 3 beta/(7 + 3 beta).  The paper writes
+    f where this build uses beta = f/b.
+    """
+    if start == START_PLAIN:
+        return 0.0
+    if start == START_APPROX1:
+        return beta / (1.0 + beta)
+    if start == START_FFTA:
+        return 3.0 * beta / (7.0 + 3.0 * beta)
+    raise ValueError("unknown start")
+
+
+def iterate(delta, b: float, f: float, L: float, rhat, start: int = START_PLAIN,
+            tol: float = 0.0, max_iter: int = 6, return_all: bool = False):
+    """Iterative solution of Eq. Nusser (Sec. 5.1, Eq. iterative), Psi in configuration space.
+
+    Psi_0 is the starting estimate (plain or Eq. approx1/approx2).  For n = 0, 1, ...:
+        S_n      = delta/b + beta div((Psi_n . r) r)        (estimate of the real-space delta / b)
+        Psi_n+1  = Z[S_n]                                   (Psi_FFT,n+1 = -grad grad^-2 S_n)
+    always restarting from the original delta.  rel[n] = |Psi_n+1 - Psi_n| / |Psi_n+1| (L2 over all
+    nodes and components), except rel[0], which is measured against the uncorrected estimate
+    Z[delta/b] for every start.  Stops when rel[n] < tol with n >= 1, or after max_iter updates.
+    Returns (Psi_final (3,n,n,n), rel list, n_updates[, list of all Psi_n]).
+    """
+    n = delta.shape[0]
+    beta = f / b
+    src0 = delta / b
+    psi_s = zeldovich(src0, L)
+    c = start_coefficient(start, beta)
+    psi = psi_s - c * radial_projection(psi_s, rhat)
+    prev_for_rel = psi_s
+    rels, history = [], [psi]
+    it = 0
+    while it < max_iter:
+        S_k = fft3(src0) + beta * divergence(radial_projection(psi, rhat), L)
+        psi_new = np.stack([ifft3(c_k, n) for c_k in zeldovich_k(S_k, n, L)])
+        num = np.sqrt(((psi_new - prev_for_rel) ** 2).sum())
+        den = np.sqrt((psi_new ** 2).sum())
+        rels.append(num / den if den > 0 else 0.0)
+        psi = psi_new
+        prev_for_rel = psi_new
+        history.append(psi)
+        it += 1
+        if it >= 2 and rels[-1] < tol:
+            break
+    if return_all:
+        return psi, rels, it, history
+    return psi, rels, it
+
+
+# --------------------------------------------------------------------------------------------
+# Reconstruction shift (Sec. 1: move galaxies and randoms back along the displacement)
+# --------------------------------------------------------------------------------------------
+def particle_rhat(pos, observer, los_mode: int):
+    o = np.asarray(observer, dtype=np.float64)
+    if los_mode == LOS_FIXED:
+        u = o / np.linalg.norm(o)
+        return np.broadcast_to(u, np.shape(pos)).copy()
+    d = np.asarray(pos, dtype=np.float64) - o
+    r = np.sqrt((d * d).sum(1))[:, None]
+    out = np.zeros_like(d)
+    np.divide(d, r, out=out, where=r > 0)
+    return out
+
+
+def shift_vectors(psi, pos, L: float, f: float, observer, los_mode: int, is_galaxy: bool):
+    """Shift d = -[Psi + f (Psi.r) r] for galaxies and d = -Psi for randoms, Psi CIC-interpolated."""
+    p = cic_gather(psi, pos, L)
+    if not is_galaxy:
+        return -p
+    rh = particle_rhat(pos, observer, los_mode)
+    u = (p * rh).sum(1)[:, None]
+    return -(p + f * u * rh)
+
+
+def shifted_positions(pos, d, L: float, periodic: bool):
+    x = np.asarray(pos, dtype=np.float64) + d
+    return np.mod(x, L) if periodic else x
+
+
+# --------------------------------------------------------------------------------------------
+# Whole pipeline (what recon_deposit -> smooth -> iterate -> shift computes)
+# --------------------------------------------------------------------------------------------
+def reconstruct(params: dict, gal_pos, gal_w=None, ran_pos=None, ran_w=None,
+                start: int = START_PLAIN, tol: float = 0.0, max_iter: int = 6,
+                shift: bool = True):
+    """Run the whole method on a catalogue; returns a dict of every intermediate.
+
+    params: n, L, b, f, R, los_mode, observer, periodic, mask_frac, lognormal, uniform (bool).
+    """
+    n, L = int(params["n"]), float(params["L"])
+    gal_pos = np.asarray(gal_pos, dtype=np.float64)
+    wg = np.ones(len(gal_pos)) if gal_w is None else np.asarray(gal_w, dtype=np.float64)
+    out = {}
+    rho_g = cic_deposit(gal_pos, wg, n, L)
+    out["rho_g"] = rho_g
+    out["sum_wg"] = wg.sum()
+    rho_g_s = smooth(rho_g, params["R"], L)
+    if params.get("uniform", False):
+        delta = overdensity_uniform(rho_g_s, wg.sum())
+        out["mask"] = np.ones(delta.shape, dtype=bool)
+    else:
+        ran_pos = np.asarray(ran_pos, dtype=np.float64)
+        wr = np.ones(len(ran_pos)) if ran_w is None else np.asarray(ran_w, dtype=np.float64)
+        rho_r = cic_deposit(ran_pos, wr, n, L)
+        out["rho_r"] = rho_r
+        out["sum_wr"] = wr.sum()
+        rho_r_s = smooth(rho_r, params["R"], L)
+        out["rho_r_s"] = rho_r_s
+        delta, mask, alpha, thr = overdensity_randoms(rho_g_s, rho_r_s, wg.sum(), wr.sum(),
+                                                      params.get("mask_frac", 0.01))
+        out.update(mask=mask, alpha=alpha, threshold=thr)
+    out["rho_g_s"] = rho_g_s
+    if params.get("lognormal", False):
+        delta, C = lognormal(delta)
+        out["lognormal_C"] = C
+    out["delta"] = delta
+    rhat = rhat_field(n, L, params["observer"], params.get("los_mode", LOS_RADIAL))
+    psi, rels, it = iterate(delta, params["b"], params["f"], L, rhat, start, tol, max_iter)
+    out.update(psi=psi, rel=rels, n_iter=it)
+    if shift:
+        periodic = bool(params.get("periodic", False))
+        dg = shift_vectors(psi, gal_pos, L, params["f"], params["observer"],
+                           params.get("los_mode", LOS_RADIAL), True)
+        out["shift_g"] = dg
+        out["pos_g"] = shifted_positions(gal_pos, dg, L, periodic)
+        if ran_pos is not None:
+            dr = shift_vectors(psi, ran_pos, L, params["f"], params["observer"],
+                               params.get("los_mode", LOS_RADIAL), False)
+            out["shift_r"] = dr
+            out["pos_r"] = shifted_positions(ran_pos, dr, L, periodic)
+    return out

@@ -1,0 +1,268 @@
+"""Seeded synthetic catalogues shaped like the workloads of Burden, Percival & Howlett (2015).
+
+The paper's own inputs (a GADGET-2 N-body run, Sec. 3.1; PTHalo BOSS DR11 CMASS mocks, Sec. 3.2) are
+not available, so these generators stand in for them with the same shapes: box, mesh, tracer counts,
+random-to-galaxy ratio, survey-like shell windows and a radial line of sight.
+
+Recipe: a Gaussian random field with P(k) = A k^-1.5 exp(-(k/0.3)^2) (A chosen so that the field
+smoothed with a Gaussian of R = 15 Mpc/h has unit variance) is drawn on a coarse generator grid from
+seeded normal noise.  Its first-order displacement moves Lagrangian points q (a jittered lattice or
+uniform points) to x = q + D(q); galaxies are kept with probability proportional to
+max(0, 1 + (b - 1) delta_L(q)) (Lagrangian bias) and moved to redshift space by s = x + f (D.r) r.
+Randoms are uniform in the same window.
+
+This module is input plumbing only.  It is shared by the tests, the benchmark and the oracle runs, and
+it contains no code of either the CUDA path or the oracle; its small Fourier-space displacement and
+trilinear interpolation are its own.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+try:  # threaded FFTs when scipy is present; numpy otherwise (same results up to rounding)
+    import scipy.fft as _sfft
+
+    def _rfftn(a):
+        return _sfft.rfftn(a, workers=-1)
+
+    def _irfftn(a, s):
+        return _sfft.irfftn(a, s=s, workers=-1)
+except Exception:  # pragma: no cover
+    def _rfftn(a):
+        return np.fft.rfftn(a)
+
+    def _irfftn(a, s):
+        return np.fft.irfftn(a, s=s)
+
+PK_AMPLITUDE = 1940.5   # (Mpc/h)^1.5: sigma(R = 15 Mpc/h) = 1 for the spectrum below
+PK_SLOPE = -1.5
+PK_CUTOFF = 0.3         # h/Mpc
+
+
+def power_spectrum(k):
+    k = np.asarray(k, dtype=np.float64)
+    out = np.zeros_like(k)
+    pos = k > 0
+    out[pos] = PK_AMPLITUDE * k[pos] ** PK_SLOPE * np.exp(-(k[pos] / PK_CUTOFF) ** 2)
+    return out
+
+
+@dataclass
+class GeneratorField:
+    """Linear density and displacement on a periodic generator grid."""
+    ng: int
+    L: float
+    delta: np.ndarray            # (ng, ng, ng) float32
+    disp: np.ndarray             # (3, ng, ng, ng) float32
+
+    def sample(self, pts):
+        """Trilinear interpolation of (delta, disp) at points (n, 3); periodic."""
+        u = np.asarray(pts, dtype=np.float64) * (self.ng / self.L)
+        f0 = np.floor(u)
+        t = (u - f0).astype(np.float32)
+        i0 = f0.astype(np.int64) % self.ng
+        i1 = (i0 + 1) % self.ng
+        d = np.zeros(len(u), dtype=np.float32)
+        v = np.zeros((len(u), 3), dtype=np.float32)
+        for cx in (0, 1):
+            ix = i1[:, 0] if cx else i0[:, 0]
+            wx = t[:, 0] if cx else 1 - t[:, 0]
+            for cy in (0, 1):
+                iy = i1[:, 1] if cy else i0[:, 1]
+                wy = t[:, 1] if cy else 1 - t[:, 1]
+                for cz in (0, 1):
+                    iz = i1[:, 2] if cz else i0[:, 2]
+                    wz = t[:, 2] if cz else 1 - t[:, 2]
+                    w = wx * wy * wz
+                    d += w * self.delta[ix, iy, iz]
+                    for a in range(3):
+                        v[:, a] += w * self.disp[a, ix, iy, iz]
+        return d, v
+
+
+def gaussian_field(ng: int, L: float, seed: int) -> GeneratorField:
+    rng = np.random.default_rng(seed)
+    white = rng.standard_normal((ng, ng, ng), dtype=np.float32)
+    W = _rfftn(white)
+    m = np.fft.fftfreq(ng, d=1.0 / ng)
+    mz = np.arange(ng // 2 + 1)
+    kf = 2 * np.pi / L
+    kx = (kf * m)[:, None, None]
+    ky = (kf * m)[None, :, None]
+    kz = (kf * mz)[None, None, :]
+    kk = np.sqrt(kx ** 2 + ky ** 2 + kz ** 2)
+    vcell = (L / ng) ** 3
+    D = W * np.sqrt(power_spectrum(kk) / vcell)
+    D[0, 0, 0] = 0
+    delta = _irfftn(D, (ng, ng, ng)).astype(np.float32)
+    inv_k2 = np.zeros_like(kk)
+    np.divide(1.0, kk ** 2, out=inv_k2, where=kk > 0)
+    disp = np.empty((3, ng, ng, ng), dtype=np.float32)
+    for a, ka in enumerate((kx, ky, kz)):
+        disp[a] = _irfftn(1j * ka * D * inv_k2, (ng, ng, ng))
+    return GeneratorField(ng, L, delta, disp)
+
+
+def _unit(v):
+    v = np.asarray(v, dtype=np.float64)
+    r = np.sqrt((v * v).sum(-1, keepdims=True))
+    return np.divide(v, r, out=np.zeros_like(v), where=r > 0)
+
+
+@dataclass
+class Catalog:
+    pos: np.ndarray                      # (n, 3) float64, Mpc/h
+    w: np.ndarray | None = None          # (n,) float32 or None (unit weights)
+
+
+@dataclass
+class Mock:
+    name: str
+    L: float
+    n_mesh: int
+    b: float
+    f: float
+    R: float
+    observer: tuple
+    los_mode: int = 0                    # 0 radial, 1 fixed (observer read as a direction)
+    periodic: bool = True
+    uniform: bool = False                # mean density from N^3 instead of randoms
+    galaxies: Catalog | None = None
+    randoms: Catalog | None = None
+    window: dict = field(default_factory=dict)
+
+    def params(self, **over):
+        p = dict(n=self.n_mesh, L=self.L, b=self.b, f=self.f, R=self.R, observer=self.observer,
+                 los_mode=self.los_mode, periodic=self.periodic, uniform=self.uniform,
+                 mask_frac=0.01, lognormal=False)
+        p.update(over)
+        return p
+
+
+def _rsd(x, v, f, observer, los_mode):
+    if los_mode == 1:
+        rh = np.broadcast_to(_unit(np.asarray(observer, dtype=np.float64)), x.shape)
+    else:
+        rh = _unit(x - np.asarray(observer, dtype=np.float64))
+    return x + f * (v * rh).sum(1, keepdims=True) * rh
+
+
+def periodic_box(L: float, n_mesh: int, n_gal: int, n_ran: int, b: float, f: float, R: float,
+                 observer, seed_field: int, seed_gal: int, seed_ran: int, ng: int | None = None,
+                 los_mode: int = 0, uniform: bool = False, name: str = "periodic") -> Mock:
+    """Periodic box: galaxies from a jittered lattice, Zel'dovich-displaced, biased, RSD-shifted."""
+    ng = ng or min(n_mesh, 256)
+    gf = gaussian_field(ng, L, seed_field)
+    rng = np.random.default_rng(seed_gal)
+    # lattice with enough sites that the biased selection can keep n_gal of them
+    side = int(np.ceil((2.0 * n_gal) ** (1.0 / 3.0)))
+    g = (np.arange(side) + 0.5) * (L / side)
+    q = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    q = q + rng.uniform(-0.5, 0.5, q.shape) * (L / side)          # jitter inside the lattice cell
+    dl, v = gf.sample(q)
+    p_keep = np.maximum(0.0, 1.0 + (b - 1.0) * dl.astype(np.float64))
+    p_keep /= p_keep.max()
+    # keep the n_gal sites with the smallest u/p (a weighted draw without replacement)
+    key = rng.uniform(size=len(q)) / np.maximum(p_keep, 1e-12)
+    sel = np.argsort(key)[:n_gal]
+    x = q[sel] + v[sel].astype(np.float64)
+    s = np.mod(_rsd(x, v[sel].astype(np.float64), f, observer, los_mode), L)
+    mock = Mock(name, L, n_mesh, b, f, R, tuple(observer), los_mode, True, uniform,
+                galaxies=Catalog(s))
+    if n_ran > 0:
+        rr = np.random.default_rng(seed_ran)
+        mock.randoms = Catalog(rr.uniform(0.0, L, (n_ran, 3)))
+    return mock
+
+
+def _in_window(p, observer, axis, r_min, r_max, cos_min):
+    d = p - np.asarray(observer)
+    r = np.sqrt((d * d).sum(1))
+    c = (d @ np.asarray(axis)) / np.maximum(r, 1e-30)
+    return (r >= r_min) & (r <= r_max) & (c >= cos_min)
+
+
+def shell_survey(L: float, n_mesh: int, n_gal: int, n_ran: int, b: float, f: float, R: float,
+                 observer, axis, r_min: float, r_max: float, sky_frac: float,
+                 seed_field: int, seed_gal: int, seed_ran: int, ng: int | None = None,
+                 name: str = "shell") -> Mock:
+    """Spherical-shell cap window (r_min..r_max around the observer, sky fraction sky_frac)."""
+    ng = ng or min(n_mesh, 256)
+    gf = gaussian_field(ng, L, seed_field)
+    obs = np.asarray(observer, dtype=np.float64)
+    ax = _unit(np.asarray(axis, dtype=np.float64))
+    cos_min = 1.0 - 2.0 * sky_frac
+    # bounding box of the window, widened by a displacement margin
+    margin = 80.0
+    lo = np.clip(obs - r_max - margin, 0, L)
+    hi = np.clip(obs + r_max + margin, 0, L)
+    sin_max = np.sqrt(max(0.0, 1 - cos_min ** 2))
+    for a in range(3):  # tighten along the cap axis when it is a coordinate axis
+        if abs(ax[a]) > 0.999:
+            if ax[a] > 0:
+                lo[a] = max(lo[a], obs[a] + r_min * cos_min - margin)
+            else:
+                hi[a] = min(hi[a], obs[a] - r_min * cos_min + margin)
+    del sin_max
+    rng = np.random.default_rng(seed_gal)
+    got, chunks = 0, []
+    vol_box = np.prod(hi - lo)
+    vol_win = sky_frac * 4.0 / 3.0 * np.pi * (r_max ** 3 - r_min ** 3)
+    per = int(n_gal * 2.0 * vol_box / vol_win) + 1000
+    while got < n_gal:
+        q = lo + rng.uniform(size=(per, 3)) * (hi - lo)
+        dl, v = gf.sample(q)
+        p_keep = np.maximum(0.0, 1.0 + (b - 1.0) * dl.astype(np.float64))
+        keep = rng.uniform(size=per) * 4.0 < p_keep          # thinning; 4 bounds 1+(b-1)delta
+        q, v = q[keep], v[keep].astype(np.float64)
+        s = _rsd(q + v, v, f, obs, 0)
+        s = s[_in_window(s, obs, ax, r_min, r_max, cos_min)]
+        chunks.append(s)
+        got += len(s)
+    gal = np.concatenate(chunks)[:n_gal]
+    rr = np.random.default_rng(seed_ran)
+    u = rr.uniform(size=(n_ran, 3))
+    r = np.cbrt(u[:, 0] * (r_max ** 3 - r_min ** 3) + r_min ** 3)
+    ct = cos_min + u[:, 1] * (1.0 - cos_min)
+    st = np.sqrt(np.maximum(0.0, 1 - ct * ct))
+    ph = 2 * np.pi * u[:, 2]
+    # orthonormal frame around the cap axis
+    t1 = _unit(np.cross(ax, [0.0, 0.0, 1.0]) if abs(ax[2]) < 0.9 else np.cross(ax, [1.0, 0.0, 0.0]))
+    t2 = np.cross(ax, t1)
+    dirs = ct[:, None] * ax + (st * np.cos(ph))[:, None] * t1 + (st * np.sin(ph))[:, None] * t2
+    ran = obs + r[:, None] * dirs
+    mock = Mock(name, L, n_mesh, b, f, R, tuple(obs), 0, False, False,
+                galaxies=Catalog(gal), randoms=Catalog(ran),
+                window=dict(axis=tuple(ax), r_min=r_min, r_max=r_max, sky_frac=sky_frac))
+    return mock
+
+
+# ---------------------------------------------------------------------------------------------
+# The workloads (sizes and parameters as the paper's data sets and the build's configurations)
+# ---------------------------------------------------------------------------------------------
+def small_periodic(n_gal: int = 200_000, n_ran: int = 2_000_000, n_mesh: int = 64) -> Mock:
+    """64^3 periodic box, L = 1000 Mpc/h, 2e5 galaxies, 2e6 randoms, b = 2, f = 0.74, R = 15,
+    observer at the box centre offset by 1500 Mpc/h along x."""
+    return periodic_box(1000.0, n_mesh, n_gal, n_ran, 2.0, 0.74, 15.0, (2000.0, 500.0, 500.0),
+                        1, 2, 3, ng=128, name="periodic-64")
+
+
+def survey_shell_512(n_gal: int = 600_000, ran_ratio: int = 50, n_mesh: int = 512,
+                     L: float = 3500.0) -> Mock:
+    """512^3 mesh in a 3500 Mpc/h box, shell 1100-1800 Mpc/h, 25% sky cap, 6e5 galaxies, 50x
+    randoms, b = 1.85, f = 0.74, R = 15.  Observer at the centre of the x = 0 face, cap axis +x
+    (a box-corner observer sees at most 1/8 of the sky, so a 25% cap cannot sit at the corner)."""
+    return shell_survey(L, n_mesh, n_gal, n_gal * ran_ratio, 1.85, 0.74, 15.0,
+                        (0.0, L / 2, L / 2), (1.0, 0.0, 0.0), 1100.0, 1800.0, 0.25,
+                        10, 11, 12, ng=256, name=f"shell-{n_mesh}")
+
+
+def scaled_shell(n_mesh: int, L: float, n_gal: int, ran_ratio: int, b: float, f: float,
+                 seed: int) -> Mock:
+    """Shell survey scaled to box L (distances scaled from the 3500 Mpc/h shape)."""
+    s = L / 3500.0
+    return shell_survey(L, n_mesh, n_gal, n_gal * ran_ratio, b, f, 15.0, (0.0, L / 2, L / 2),
+                        (1.0, 0.0, 0.0), 1100.0 * s, 1800.0 * s, 0.25, seed, seed + 1, seed + 2,
+                        ng=min(256, n_mesh), name=f"shell-{n_mesh}-{seed}")

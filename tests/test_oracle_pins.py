@@ -1,0 +1,256 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics (no GPU).
+
+Each test checks the oracle against something other than itself: a brute-force DFT, a closed form,
+an explicit matrix solve, a finite-difference derivative, or an invariant.  Chosen so that a dropped
+term, a wrong sign or index, or a transposed operand in the oracle fails at least one of them.
+"""
+import numpy as np
+import pytest
+
+from oracle import recon_oracle as O
+
+
+def brute_rdft(a):
+    """Definition of the 3-D forward DFT, sum_x a(x) exp(-2 pi i m.x / N), on the r2c half grid."""
+    n = a.shape[0]
+    idx = np.arange(n)
+    E = np.exp(-2j * np.pi * np.outer(idx, idx) / n)          # E[m, x]
+    full = np.einsum("ax,by,cz,xyz->abc", E, E, E, a)
+    return full[:, :, : n // 2 + 1]
+
+
+@pytest.mark.parametrize("n", [6, 8])
+def test_fft_matches_brute_dft(n):
+    rng = np.random.default_rng(n)
+    a = rng.standard_normal((n, n, n))
+    F = O.fft3(a)
+    assert np.abs(F - brute_rdft(a)).max() <= 1e-12 * np.abs(F).max()
+    assert np.abs(O.ifft3(F, n) - a).max() <= 1e-13 * np.abs(a).max()
+
+
+def _mode(n, L, m, A=1.3, phase=0.0):
+    x = np.arange(n) * (L / n)
+    X = np.stack(np.meshgrid(x, x, x, indexing="ij"))
+    k = 2 * np.pi * np.asarray(m, dtype=float) / L
+    arg = (k[:, None, None, None] * X).sum(0) + phase
+    return k, arg
+
+
+@pytest.mark.parametrize("m", [(1, 0, 0), (0, 2, 0), (1, 1, 0), (2, -1, 3), (3, 3, -2)])
+def test_plane_wave_zeldovich(m):
+    """delta = A cos(k.x)  =>  Psi = -(A/b) (k/k^2) sin(k.x) (Eq. Zeldovich, sign fixed by Eq. delta)."""
+    n, L, A, b = 16, 500.0, 1.3, 1.9
+    k, arg = _mode(n, L, m)
+    delta = A * np.cos(arg)
+    psi = O.zeldovich(delta / b, L)
+    want = -(A / b) * (k[:, None, None, None] / (k @ k)) * np.sin(arg)[None]
+    assert np.abs(psi - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_divergence_sign_against_finite_differences():
+    """div Z[s] = -s, checked with a second-order central difference on a smooth field."""
+    n, L = 64, 1000.0
+    rng = np.random.default_rng(3)
+    s = np.zeros((n, n, n))
+    for _ in range(4):  # a few long-wavelength modes: FD error (kH)^2/6 <= 7e-3
+        k, arg = _mode(n, L, rng.integers(-1, 2, 3) + np.array([1, 0, 0]))
+        s += rng.standard_normal() * np.cos(arg + rng.uniform(0, 6))
+    psi = O.zeldovich(s, L)
+    H = L / n
+    div = sum((np.roll(psi[j], -1, axis=j) - np.roll(psi[j], 1, axis=j)) / (2 * H) for j in range(3))
+    assert np.abs(div + s).max() <= 1e-2 * np.abs(s).max()   # a sign error gives 2
+
+
+def test_f_zero_converges_in_one_step():
+    """f = 0: the source never changes, Psi_1 = Psi_0 = Z[delta/b] and rel = 0."""
+    n, L = 16, 800.0
+    delta = np.random.default_rng(0).standard_normal((n, n, n))
+    rh = O.rhat_field(n, L, (1200.0, 400.0, 400.0), O.LOS_RADIAL)
+    psi, rel, it = O.iterate(delta, 2.0, 0.0, L, rh, O.START_PLAIN, tol=1e-12, max_iter=5)
+    assert it == 2 and max(rel) < 1e-15
+    assert np.abs(psi - O.zeldovich(delta / 2.0, L)).max() < 1e-14 * np.abs(psi).max()
+
+
+def _kaiser_parts(delta, b, L):
+    n = delta.shape[0]
+    _, kd, k2 = O.kgrid(n, L)
+    inv = np.where(k2 > 0, 1.0 / np.where(k2 > 0, k2, 1), 0.0)
+    mu2 = kd[0] ** 2 * inv                   # (kd_x / k)^2, LOS along x
+    return O.fft3(delta / b), mu2
+
+
+@pytest.mark.parametrize("start", [O.START_PLAIN, O.START_APPROX1, O.START_FFTA])
+def test_plane_parallel_iterates_closed_form(start):
+    """Fixed LOS x: S_n = delta/b - beta mu^2 S_n-1, so every iterate has a closed form, and the
+    limit is Kaiser Z[delta/b]/(1 + beta mu^2) (Eq. itpsi with the sign that matches Tables 2-3)."""
+    n, L, b, f = 16, 600.0, 1.8, 0.7
+    beta = f / b
+    delta = np.random.default_rng(1).standard_normal((n, n, n))
+    rh = O.rhat_field(n, L, (1.0, 0.0, 0.0), O.LOS_FIXED)
+    _, rel, it, hist = O.iterate(delta, b, f, L, rh, start, tol=0.0, max_iter=8, return_all=True)
+    D, mu2 = _kaiser_parts(delta, b, L)
+    a = -beta * mu2
+    c = O.start_coefficient(start, beta)
+    # Psi_0 = Z[D] - c (Z[D].x) x  gives the radial source term (1-c) a D; S_0 = D + (1-c) a D
+    S = D + (1 - c) * a * D
+    for m in range(1, it + 1):
+        want = np.stack([O.ifft3(ck, n) for ck in O.zeldovich_k(S, n, L)])
+        got = hist[m]
+        assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max(), m
+        S = D + a * S
+    kaiser = np.stack([O.ifft3(ck, n) for ck in O.zeldovich_k(D / (1 - a), n, L)])
+    if start == O.START_PLAIN:
+        # Psi_n = Psi_K [1 - (-beta mu^2)^(n+1)]
+        for m in range(0, it + 1):
+            want = np.stack([O.ifft3(ck, n) for ck in
+                             O.zeldovich_k(D / (1 - a) * (1 - a ** (m + 1)), n, L)])
+            assert np.abs(hist[m] - want).max() <= 1e-11 * np.abs(want).max()
+    err = np.abs(hist[-1] - kaiser).max() / np.abs(kaiser).max()
+    assert err < (beta ** (it + 1)) * 3
+
+
+def test_approx1_exact_for_radial_mode():
+    """A mode with k parallel to the LOS (mu = 1): Eq. approx1 is the exact Kaiser solution."""
+    n, L, b, f = 16, 600.0, 2.0, 0.74
+    k, arg = _mode(n, L, (2, 0, 0))
+    delta = 0.8 * np.cos(arg)
+    rh = O.rhat_field(n, L, (1.0, 0.0, 0.0), O.LOS_FIXED)
+    beta = f / b
+    psi_s = O.zeldovich(delta / b, L)
+    psi0 = psi_s - O.start_coefficient(O.START_APPROX1, beta) * O.radial_projection(psi_s, rh)
+    assert np.abs(psi0 - psi_s / (1 + beta)).max() < 1e-14
+    psi, rel, it = O.iterate(delta, b, f, L, rh, O.START_APPROX1, tol=1e-13, max_iter=4)
+    assert np.abs(psi - psi_s / (1 + beta)).max() < 1e-13 and it == 2
+
+
+def test_ffta_coefficient_from_the_075_ratio():
+    """Sec. 4.1: grad A = 0.75 curl B and grad A + curl B = (Psi.r)r give grad A = (3/7)(Psi.r)r,
+    so Eq. approx2's coefficient is (3/7)beta / (1 + (3/7)beta) = 3 beta/(7 + 3 beta)."""
+    for beta in (0.2, 0.37, 0.4, 0.74):
+        g = 0.75 / 1.75
+        assert O.start_coefficient(O.START_FFTA, beta) == pytest.approx(g * beta / (1 + g * beta), rel=1e-15)
+        assert O.start_coefficient(O.START_APPROX1, beta) == pytest.approx(beta / (1 + beta), rel=1e-15)
+
+
+def _dft_matrix(n):
+    idx = np.arange(n)
+    return np.exp(-2j * np.pi * np.outer(idx, idx) / n)
+
+
+def test_radial_fixed_point_matches_dense_solve():
+    """Radial LOS on 8^3: the converged iterate equals the solution of the linear system
+    S - beta div_spec((Z[S].r)r) = delta/b assembled from explicit DFT matrices (no FFT library)."""
+    n, L, b, f = 8, 400.0, 2.0, 0.6
+    beta = f / b
+    rng = np.random.default_rng(7)
+    delta = rng.standard_normal((n, n, n))
+    obs = (-150.0, 210.0, 130.0)
+    rh = O.rhat_field(n, L, obs, O.LOS_RADIAL)
+    E = _dft_matrix(n)
+    F = np.kron(np.kron(E, E), E)                  # full 3-D DFT on flattened [x, y, z]
+    Fi = np.conj(F) / n ** 3
+    m = np.fft.fftfreq(n, 1.0 / n)
+    kk = 2 * np.pi * m / L
+    kdd = np.where(np.abs(m) == n // 2, 0.0, kk)
+    KX, KY, KZ = np.meshgrid(kk, kk, kk, indexing="ij")
+    DX, DY, DZ = np.meshgrid(kdd, kdd, kdd, indexing="ij")
+    k2 = (KX ** 2 + KY ** 2 + KZ ** 2).ravel()
+    inv = np.where(k2 > 0, 1 / np.where(k2 > 0, k2, 1), 0.0)
+    kd = [DX.ravel(), DY.ravel(), DZ.ravel()]
+    Z = [np.real(Fi @ np.diag(1j * kd[j] * inv) @ F) for j in range(3)]        # S -> Psi_j
+    Dv = [np.real(Fi @ np.diag(1j * kd[j]) @ F) for j in range(3)]             # P_j -> div part
+    R = [rh[j].ravel() for j in range(3)]
+    proj = sum(np.diag(R[j]) @ Z[j] for j in range(3))                          # S -> Psi.r
+    DP = sum(Dv[j] @ np.diag(R[j]) @ proj for j in range(3))                    # S -> div((Psi.r)r)
+    A = np.eye(n ** 3) - beta * DP
+    S = np.linalg.solve(A, (delta / b).ravel())
+    want = np.stack([(Z[j] @ S).reshape(n, n, n) for j in range(3)])
+    psi, rel, it = O.iterate(delta, b, f, L, rh, O.START_FFTA, tol=1e-14, max_iter=200)
+    assert np.abs(psi - want).max() <= 1e-10 * np.abs(want).max()
+
+
+def test_distant_observer_tends_to_kaiser():
+    """A radial LOS from an observer far along -x approaches the plane-parallel Kaiser solution."""
+    n, L, b, f = 16, 500.0, 2.0, 0.74
+    delta = np.random.default_rng(5).standard_normal((n, n, n))
+    rh = O.rhat_field(n, L, (-1e7, 250.0, 250.0), O.LOS_RADIAL)
+    psi, _, _ = O.iterate(delta, b, f, L, rh, O.START_PLAIN, tol=1e-12, max_iter=100)
+    D, mu2 = _kaiser_parts(delta, b, L)
+    kaiser = np.stack([O.ifft3(ck, n) for ck in O.zeldovich_k(D / (1 + f / b * mu2), n, L)])
+    assert np.abs(psi - kaiser).max() <= 1e-4 * np.abs(kaiser).max()
+
+
+def test_cic_mass_and_node_and_adjoint():
+    n, L = 12, 300.0
+    rng = np.random.default_rng(11)
+    pos = rng.uniform(0, L, (5000, 3))
+    w = rng.uniform(0.5, 2.0, 5000)
+    rho = O.cic_deposit(pos, w, n, L)
+    assert abs(rho.sum() - w.sum()) <= 1e-12 * w.sum()
+    # a particle exactly on a node deposits its whole weight on that node
+    node = np.array([[3, 7, 11]]) * (L / n)
+    r1 = O.cic_deposit(node, np.array([2.5]), n, L)
+    assert r1[3, 7, 11] == 2.5 and np.count_nonzero(r1) == 1
+    # wrap: a particle at u = n - 0.25 shares with node 0
+    r2 = O.cic_deposit(np.array([[L - 0.25 * L / n, 0.0, 0.0]]), None, n, L)
+    assert r2[n - 1, 0, 0] == pytest.approx(0.25) and r2[0, 0, 0] == pytest.approx(0.75)
+    # adjointness <deposit(w), F> = sum_p w_p gather(F)(x_p)
+    F = rng.standard_normal((n, n, n))
+    assert (rho * F).sum() == pytest.approx((w * O.cic_gather(F, pos, L)).sum(), rel=1e-12)
+
+
+def test_cic_gathers_linear_field_exactly():
+    n, L = 16, 160.0
+    x = np.arange(n) * (L / n)
+    X = np.stack(np.meshgrid(x, x, x, indexing="ij"))
+    a, g = 0.3, np.array([0.7, -1.1, 0.4])
+    F = a + (g[:, None, None, None] * X).sum(0)
+    pos = np.random.default_rng(2).uniform(0, L - L / n, (2000, 3))   # away from the wrap
+    assert np.abs(O.cic_gather(F, pos, L) - (a + pos @ g)).max() < 1e-12
+
+
+def test_smoothing_single_mode():
+    n, L, R = 32, 640.0, 15.0
+    k, arg = _mode(n, L, (2, 1, 0))
+    out = O.smooth(np.cos(arg), R, L)
+    assert np.abs(out - np.exp(-0.5 * (k @ k) * R * R) * np.cos(arg)).max() < 1e-13
+
+
+def test_lognormal_small_delta_and_mean():
+    rng = np.random.default_rng(4)
+    d = 1e-3 * rng.standard_normal((8, 8, 8))
+    ld, C = O.lognormal(d)
+    want = d - d * d / 2 + d ** 3 / 3 - d ** 4 / 4     # Taylor series; next term ~ 2e-13
+    want = want - want.mean()
+    assert np.abs(ld - want).max() < 1e-12
+    assert abs(ld.mean()) < 1e-17 and C == pytest.approx(-np.log(1 + d).mean(), rel=1e-12)
+
+
+def test_overdensity_zero_when_galaxies_trace_randoms():
+    rng = np.random.default_rng(8)
+    rr = rng.uniform(0.1, 2.0, (8, 8, 8))
+    rr[0, 0, :4] = 0.0
+    d, mask, alpha, thr = O.overdensity_randoms(3.0 * rr, rr, 30.0, 10.0, 0.01)
+    assert alpha == 3.0 and not mask[0, 0, 0] and mask[4, 4, 4]
+    assert np.abs(d).max() < 1e-15
+    assert thr == pytest.approx(0.01 * rr[rr > 0].mean())
+
+
+def test_shift_decomposition():
+    """Galaxy shift: along the LOS -(1+f)(Psi.r); across it -Psi_perp.  Randoms: -Psi."""
+    n, L, f = 8, 200.0, 0.74
+    rng = np.random.default_rng(9)
+    psi = rng.standard_normal((3, n, n, n))
+    pos = rng.uniform(0, L, (300, 3))
+    obs = (-100.0, 50.0, 20.0)
+    p = O.cic_gather(psi, pos, L)
+    rh = O.particle_rhat(pos, obs, O.LOS_RADIAL)
+    dg = O.shift_vectors(psi, pos, L, f, obs, O.LOS_RADIAL, True)
+    dr = O.shift_vectors(psi, pos, L, f, obs, O.LOS_RADIAL, False)
+    par = (p * rh).sum(1)
+    assert np.abs((dg * rh).sum(1) + (1 + f) * par).max() < 1e-12
+    perp_g = dg - (dg * rh).sum(1)[:, None] * rh
+    perp_p = p - par[:, None] * rh
+    assert np.abs(perp_g + perp_p).max() < 1e-12
+    assert np.abs(dr + p).max() == 0.0
+    assert np.allclose(np.linalg.norm(rh, axis=1), 1.0)
