@@ -1,0 +1,206 @@
+/* recon.h: C ABI of the GB300 (sm_103a) iterative Fourier-space reconstruction library.
+ *
+ * The method is that of Burden, Percival & Howlett, "Reconstruction in Fourier space" (2015):
+ * tracers are binned on a mesh, the overdensity is smoothed (Sec. 3), and the redshift-space
+ * displacement equation (Eq. Nusser)
+ *
+ *     div Psi + beta div((Psi . r) r) = -delta / b,          beta = f / b,
+ *
+ * is solved for a radial line of sight by the fixed-point FFT iteration of Sec. 5.1
+ * (Eq. iterative): S_n = delta/b + beta div((Psi_n . r) r), Psi_n+1 = Z[S_n], Z[s](k) = i k s / k^2
+ * (Eq. Zeldovich).  Galaxies and randoms are then moved back along Psi (Sec. 1; Eq. Lagrange).
+ *
+ * Conventions shared by every entry point
+ *   - Mesh: cubic, N = nmesh[0] = nmesh[1] = nmesh[2] in {32, 48, 64, 96, 128, 256, 384, 512, 1024};
+ *     box side L = box[0] = box[1] = box[2] (Mpc/h); nodes at x_i = i L / N; periodic indexing.
+ *   - Real fields are float32 [ix][iy][iz] (iz fastest), N^3 values.
+ *   - Complex fields on the r2c half grid are float32 pairs [kx][ky][kz], kz = 0..N/2 (N/2+1
+ *     values, kz fastest), forward transform e^{-ik.x} unnormalised.
+ *   - Positions are (n, 3) row-major (x, y, z per particle), float64 or float32, in [0, L) up to
+ *     periodic wrap.  Weights are float32 or NULL (unit weights).
+ *   - Every call is ordered on the CUDA stream given to recon_create.  Calls that return values to
+ *     the host (recon_iterate, recon_get_scalars) synchronise that stream.
+ *   - Ownership: the handle owns its device fields (inside the caller's workspace when one is
+ *     given).  Input pointers are borrowed for the duration of the call.  Output buffers are the
+ *     caller's.  A host pointer must be ordinary or pinned host memory; a device pointer must be
+ *     memory of the device that was current at recon_create.
+ *   - Errors: every entry point returns a recon_status; no exception crosses the ABI.  After
+ *     RECON_ERR_CUDA, recon_last_error gives the CUDA message.  A handle whose call failed with
+ *     RECON_ERR_CUDA should be destroyed.
+ */
+#ifndef RECON_GB300_H
+#define RECON_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum recon_status {
+  RECON_OK = 0,
+  RECON_ERR_INVALID_ARG = 1,   /* a null pointer, a size out of range, an unsupported mesh      */
+  RECON_ERR_OOM = 2,           /* device allocation failed or the workspace is too small        */
+  RECON_ERR_CUDA = 3,          /* a CUDA runtime error; see recon_last_error                    */
+  RECON_ERR_NOT_CONVERGED = 4, /* max_iter reached before tol; all outputs are still valid      */
+  RECON_ERR_NONFINITE = 5,     /* a NaN or Inf appeared in the convergence norms                */
+  RECON_ERR_STATE = 6,         /* calls out of order (create -> deposit -> smooth -> iterate)   */
+  RECON_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up                            */
+  RECON_ERR_UNSUPPORTED = 8    /* a valid request this build does not implement                 */
+} recon_status;
+
+enum { RECON_LOS_RADIAL = 0, RECON_LOS_FIXED = 1 };
+enum { RECON_MEAN_RANDOMS = 0, RECON_MEAN_UNIFORM = 1 };
+enum { RECON_F64 = 0, RECON_F32 = 1 };
+
+/* Starting estimates of the iteration (Sec. 5.2).  The estimate is
+ * Psi_0 = Z[delta/b] - c (Z[delta/b] . r) r with
+ *   PLAIN   c = 0                  (Psi_red,FFT: no RSD correction)
+ *   APPROX1 c = beta / (1 + beta)  (Eq. approx1, irrotational approximation)
+ *   FFTA    c = 3 beta / (7+3 beta)(Eq. approx2, the "RSD-corrected" first estimate)
+ * (the paper writes f where this library uses beta = f / b). */
+enum { RECON_START_PLAIN = 0, RECON_START_APPROX1 = 1, RECON_START_FFTA = 2 };
+
+/* Fields recon_get_field can export. */
+enum {
+  RECON_FIELD_RHO_G = 0,     /* CIC density of galaxies (real), valid between deposit and smooth */
+  RECON_FIELD_RHO_R = 1,     /* CIC density of randoms (real), same validity                     */
+  RECON_FIELD_DELTA = 2,     /* smoothed, masked (optionally lognormal) overdensity (real)       */
+  RECON_FIELD_DELTA_K = 3,   /* its forward transform on the half grid, valid after iterate      */
+  RECON_FIELD_PSI = 4        /* the final displacement, 3 real fields [comp][ix][iy][iz]         */
+};
+
+typedef struct recon_params {
+  int nmesh[3];            /* N per axis; must be equal                                        */
+  double box[3];           /* L per axis (Mpc/h); must be equal; box origin at 0               */
+  double b;                /* linear galaxy bias (Sec. 3.2: b = 1.87 for the CMASS mocks)      */
+  double f;                /* growth rate; the solve uses beta = f/b, the galaxy shift uses f   */
+  double smooth_R;         /* Gaussian smoothing length R (Mpc/h), S(k) = exp(-k^2 R^2 / 2)    */
+  int los_mode;            /* RECON_LOS_RADIAL (observer position) or RECON_LOS_FIXED          */
+  double observer[3];      /* radial: observer position (Mpc/h); fixed: LOS direction vector   */
+  int periodic;            /* 1: shifted positions wrap modulo L; 0: survey (no wrap)          */
+  double mask_frac;        /* survey mask: keep nodes whose smoothed random density exceeds
+                              mask_frac x its mean over nodes where it is positive (0.01)      */
+  int lognormal;           /* 1: delta -> ln(max(1+delta, 1e-6)) - <ln(...)> (Eq. logdelta)    */
+  int mean_density_mode;   /* RECON_MEAN_RANDOMS (delta from randoms) or RECON_MEAN_UNIFORM    */
+} recon_params;
+
+typedef struct recon_catalog {
+  const void* pos;         /* (n, 3) positions, dtype below                                    */
+  const float* w;          /* (n) weights or NULL for unit weights                              */
+  int64_t n;               /* number of particles, 0 allowed                                    */
+  int dtype;               /* RECON_F64 or RECON_F32 (positions)                                */
+  int on_device;           /* 1: pos and w are device pointers; 0: host pointers                */
+} recon_catalog;
+
+typedef struct recon_handle recon_handle;
+
+/* Bytes of device workspace recon_create needs for these parameters (fields, reductions, host
+ * staging).  Fails with INVALID_ARG for an unsupported mesh. */
+recon_status recon_workspace_bytes(const recon_params* p, size_t* bytes);
+
+/* Create a reconstruction context on the current device.
+ *   stream     cudaStream_t to order all work on (NULL = legacy default stream)
+ *   workspace  device memory of at least recon_workspace_bytes bytes, 256-byte aligned, owned by
+ *              the caller and kept alive until recon_destroy; NULL makes the handle allocate it
+ *              itself with cudaMalloc (and free it in recon_destroy). */
+recon_status recon_create(const recon_params* p, void* stream, void* workspace,
+                          size_t workspace_bytes, recon_handle** out);
+
+/* CIC mass assignment of galaxies and randoms (Sec. 3: binning; CIC instead of NGP) and the
+ * weight sums sum w_g, sum w_r (float64) that give alpha = sum w_g / sum w_r.
+ * ran may be NULL (or n = 0) only with RECON_MEAN_UNIFORM. */
+recon_status recon_deposit(recon_handle* h, const recon_catalog* gal, const recon_catalog* ran);
+
+/* Gaussian smoothing of both densities (Sec. 3.1, 3.2: smoothed before delta is formed),
+ * delta = rho_g,s / (alpha rho_r,s) - 1 inside the binary survey mask and 0 outside (Sec. 3.2), or
+ * rho_g,s / rho_bar - 1 in RECON_MEAN_UNIFORM mode, then the optional lognormal transform
+ * (Sec. 6, Eq. logdelta). */
+recon_status recon_smooth(recon_handle* h);
+
+/* The iteration of Sec. 5.1 from the chosen start.  Runs until rel < tol after at least two
+ * updates, or max_iter updates, where rel = |Psi_n+1 - Psi_n| / |Psi_n+1| (L2 over all nodes and
+ * components, from the Parseval sum of the sources; the first entry is measured against the
+ * uncorrected estimate Z[delta/b]).  On return *n_iter is the number of updates and *rel_change
+ * the last rel.  Returns NOT_CONVERGED when max_iter was reached with rel >= tol and tol > 0.
+ * Blocks the calling thread once per iteration to read the norm. */
+recon_status recon_iterate(recon_handle* h, int start, double tol, int max_iter, int* n_iter,
+                           double* rel_change);
+
+/* The rel values of the last recon_iterate: up to cap entries into rel (host), count into *n. */
+recon_status recon_get_trace(recon_handle* h, double* rel, int cap, int* n);
+
+/* Reconstruction shift (Sec. 1; Eq. Lagrange x = q + Psi reversed): Psi is CIC-interpolated to each
+ * particle; galaxies move by -[Psi + f (Psi . r) r] with r from the particle position, randoms by
+ * -Psi.  shift_out: (n, 3) float32, required.  pos_out: (n, 3) float64 shifted positions
+ * (wrapped modulo L when periodic) or NULL.  Both are host or device memory as out_on_device
+ * says; particle order is the catalogue's. */
+recon_status recon_shift(recon_handle* h, const recon_catalog* cat, int is_galaxy,
+                         float* shift_out, double* pos_out, int out_on_device);
+
+/* Copy the final displacement, 3 N^3 float32 [comp][ix][iy][iz], to out (host or device). */
+recon_status recon_get_psi(recon_handle* h, float* out, int out_on_device);
+
+/* Copy an internal field (RECON_FIELD_*) to out: N^3 float32 for real fields, N*N*(N/2+1) float32
+ * pairs for RECON_FIELD_DELTA_K, 3 N^3 float32 for RECON_FIELD_PSI. */
+recon_status recon_get_field(recon_handle* h, int which, float* out, int out_on_device);
+
+/* Scalars of the last calls, float64, into out[8]: sum w_g, sum w_r, alpha, mask threshold,
+ * lognormal constant C, number of masked-in nodes, last |dPsi|^2, last |Psi|^2. */
+recon_status recon_get_scalars(recon_handle* h, double out[8]);
+
+/* Forward 3-D r2c transform of a real N^3 float32 field (device pointer) into the half grid
+ * (device pointer), with the library's own FFT passes; uses the handle's field buffers, so it
+ * invalidates the reconstruction state. */
+recon_status recon_fft_r2c(recon_handle* h, const float* in_real, float* out_half);
+
+/* Unnormalised inverse c2r transform: half grid (device) -> N^3 real (device), equal to N^3 times
+ * the inverse DFT. Invalidates the reconstruction state like recon_fft_r2c. */
+recon_status recon_fft_c2r(recon_handle* h, const float* in_half, float* out_real);
+
+/* Kernel kinds counted and (optionally) timed by the handle. */
+enum {
+  RECON_K_DEPOSIT = 0,   /* CIC deposit                                  */
+  RECON_K_ZFWD = 1,      /* Z pass, r2c (densities, FFT export)          */
+  RECON_K_ZINV = 2,      /* Z pass, c2r of the smoothed densities        */
+  RECON_K_ZDELTA = 3,    /* Z pass forming delta + r2c                   */
+  RECON_K_ZPROJ = 4,     /* Z pass: c2r, radial projection, r2c          */
+  RECON_K_ZFINAL = 5,    /* Z pass: c2r of the final Psi                 */
+  RECON_K_YFWD = 6,      /* Y pass forward                               */
+  RECON_K_YINV = 7,      /* Y pass inverse                               */
+  RECON_K_XSMOOTH = 8,   /* X pass with the Gaussian smoothing           */
+  RECON_K_XDELTA = 9,    /* X pass: delta(k), S_-1 and Z[delta/b]        */
+  RECON_K_XITER = 10,    /* X pass: source update, norms and Z[S]        */
+  RECON_K_SHIFT = 11,    /* CIC interpolation and shift                  */
+  RECON_K_OTHER = 12,    /* reductions, FFT export passes                */
+  RECON_K_COUNT = 13
+};
+
+/* Enable (1) or disable (0) CUDA-event timing of every kernel launch on the handle's stream.
+ * Launch counts are always kept. */
+recon_status recon_set_timing(recon_handle* h, int enable);
+
+/* Launch count, summed algorithmic bytes (the bytes each launch must read and write at least:
+ * its input and output fields and particle arrays) and, if timing was enabled, summed device
+ * milliseconds of one kernel kind since the last recon_reset_timing.  Synchronises the stream
+ * when timing is on.  Any output pointer may be NULL. */
+recon_status recon_get_timing(recon_handle* h, int kind, double* total_ms, int64_t* launches,
+                              double* alg_bytes);
+
+/* Zero the launch counts and timings. */
+recon_status recon_reset_timing(recon_handle* h);
+
+/* Release the handle and, if it allocated them, its device buffers. NULL is accepted. */
+recon_status recon_destroy(recon_handle* h);
+
+/* Static description of a status code. */
+const char* recon_status_str(recon_status s);
+
+/* Last CUDA error text recorded on the handle (empty string if none). */
+const char* recon_last_error(recon_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RECON_GB300_H */

@@ -1,0 +1,326 @@
+"""Thin ctypes binding of the C ABI in include/recon.h (argument marshalling only).
+
+Every step of the reconstruction runs in the CUDA kernels of librecon_gb300.so.  There is no CPU
+path: if the library is missing, or no CUDA device is present, the calls raise.  PyTorch supplies
+device memory (the workspace and output tensors) and the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "librecon_gb300.so")
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_NONFINITE, ERR_STATE, ERR_TIMEOUT, \
+    ERR_UNSUPPORTED = range(9)
+LOS_RADIAL, LOS_FIXED = 0, 1
+MEAN_RANDOMS, MEAN_UNIFORM = 0, 1
+F64, F32 = 0, 1
+START_PLAIN, START_APPROX1, START_FFTA = 0, 1, 2
+FIELD_RHO_G, FIELD_RHO_R, FIELD_DELTA, FIELD_DELTA_K, FIELD_PSI = range(5)
+
+# every symbol include/recon.h declares
+ABI_SYMBOLS = (
+    "recon_workspace_bytes", "recon_create", "recon_deposit", "recon_smooth", "recon_iterate",
+    "recon_get_trace", "recon_shift", "recon_get_psi", "recon_get_field", "recon_get_scalars",
+    "recon_fft_r2c", "recon_fft_c2r", "recon_destroy", "recon_status_str", "recon_last_error",
+    "recon_set_timing", "recon_get_timing", "recon_reset_timing",
+)
+KERNEL_KINDS = ("deposit", "z_fwd", "z_inv", "z_delta", "z_proj", "z_final", "y_fwd", "y_inv",
+                "x_smooth", "x_delta", "x_iter", "shift", "other")
+
+
+class ReconParams(C.Structure):
+    _fields_ = [("nmesh", C.c_int * 3), ("box", C.c_double * 3), ("b", C.c_double), ("f", C.c_double),
+                ("smooth_R", C.c_double), ("los_mode", C.c_int), ("observer", C.c_double * 3),
+                ("periodic", C.c_int), ("mask_frac", C.c_double), ("lognormal", C.c_int),
+                ("mean_density_mode", C.c_int)]
+
+
+class ReconCatalog(C.Structure):
+    _fields_ = [("pos", C.c_void_p), ("w", C.c_void_p), ("n", C.c_int64), ("dtype", C.c_int),
+                ("on_device", C.c_int)]
+
+
+class ReconError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(msg)
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load librecon_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "(there is no CPU fallback)")
+    lib = C.CDLL(path)
+    P, VP, I, D = C.POINTER, C.c_void_p, C.c_int, C.c_double
+    lib.recon_workspace_bytes.argtypes = [P(ReconParams), P(C.c_size_t)]
+    lib.recon_create.argtypes = [P(ReconParams), VP, VP, C.c_size_t, P(VP)]
+    lib.recon_deposit.argtypes = [VP, P(ReconCatalog), P(ReconCatalog)]
+    lib.recon_smooth.argtypes = [VP]
+    lib.recon_iterate.argtypes = [VP, I, D, I, P(I), P(D)]
+    lib.recon_get_trace.argtypes = [VP, P(D), I, P(I)]
+    lib.recon_shift.argtypes = [VP, P(ReconCatalog), I, VP, VP, I]
+    lib.recon_get_psi.argtypes = [VP, VP, I]
+    lib.recon_get_field.argtypes = [VP, I, VP, I]
+    lib.recon_get_scalars.argtypes = [VP, P(D)]
+    lib.recon_fft_r2c.argtypes = [VP, VP, VP]
+    lib.recon_fft_c2r.argtypes = [VP, VP, VP]
+    lib.recon_destroy.argtypes = [VP]
+    lib.recon_set_timing.argtypes = [VP, I]
+    lib.recon_get_timing.argtypes = [VP, I, P(D), P(C.c_int64), P(D)]
+    lib.recon_reset_timing.argtypes = [VP]
+    lib.recon_status_str.argtypes = [I]
+    lib.recon_status_str.restype = C.c_char_p
+    lib.recon_last_error.argtypes = [VP]
+    lib.recon_last_error.restype = C.c_char_p
+    for name in ABI_SYMBOLS:
+        if name not in ("recon_status_str", "recon_last_error"):
+            getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+def make_params(n, L, b, f, R, observer, los_mode=LOS_RADIAL, periodic=False, mask_frac=0.01,
+                lognormal=False, uniform=False) -> ReconParams:
+    p = ReconParams()
+    p.nmesh[:] = (int(n),) * 3
+    p.box[:] = (float(L),) * 3
+    p.b, p.f, p.smooth_R = float(b), float(f), float(R)
+    p.los_mode = int(los_mode)
+    p.observer[:] = tuple(float(v) for v in observer)
+    p.periodic = int(bool(periodic))
+    p.mask_frac = float(mask_frac)
+    p.lognormal = int(bool(lognormal))
+    p.mean_density_mode = MEAN_UNIFORM if uniform else MEAN_RANDOMS
+    return p
+
+
+def workspace_bytes(params: ReconParams) -> int:
+    lib = load()
+    out = C.c_size_t(0)
+    st = lib.recon_workspace_bytes(C.byref(params), C.byref(out))
+    if st != OK:
+        raise ReconError(st, "recon_workspace_bytes: " + lib.recon_status_str(st).decode())
+    return out.value
+
+
+def _catalog(pos, w, keep):
+    """Build a recon_catalog from a torch tensor (CUDA or CPU) or a numpy array."""
+    import torch
+    cat = ReconCatalog()
+    if pos is None:
+        return None
+    if isinstance(pos, np.ndarray):
+        pos = np.ascontiguousarray(pos)
+        if pos.dtype not in (np.float64, np.float32) or pos.ndim != 2 or pos.shape[1] != 3:
+            raise ValueError("positions must be (n, 3) float64 or float32")
+        keep.append(pos)
+        cat.pos = pos.ctypes.data if len(pos) else None
+        cat.n = len(pos)
+        cat.dtype = F64 if pos.dtype == np.float64 else F32
+        cat.on_device = 0
+        if w is not None:
+            w = np.ascontiguousarray(w, dtype=np.float32)
+            keep.append(w)
+            cat.w = w.ctypes.data
+        return cat
+    if not isinstance(pos, torch.Tensor):
+        raise TypeError("positions must be a torch.Tensor or numpy.ndarray")
+    pos = pos.contiguous()
+    if pos.dtype not in (torch.float64, torch.float32) or pos.dim() != 2 or pos.shape[1] != 3:
+        raise ValueError("positions must be (n, 3) float64 or float32")
+    keep.append(pos)
+    cat.pos = pos.data_ptr() if pos.numel() else None
+    cat.n = pos.shape[0]
+    cat.dtype = F64 if pos.dtype == torch.float64 else F32
+    cat.on_device = int(pos.is_cuda)
+    if w is not None:
+        w = w.to(device=pos.device, dtype=torch.float32).contiguous()
+        keep.append(w)
+        cat.w = w.data_ptr()
+    return cat
+
+
+def _host_ptr(x):
+    """Address of a host numpy array or CPU torch tensor (pinned or not)."""
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+class Recon:
+    """One reconstruction context (a recon_handle) on the current CUDA device and stream."""
+
+    def __init__(self, n, L, b, f, R, observer, los_mode=LOS_RADIAL, periodic=False, mask_frac=0.01,
+                 lognormal=False, uniform=False, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the reconstruction runs only on the GPU")
+        self.lib = load()
+        self.params = make_params(n, L, b, f, R, observer, los_mode, periodic, mask_frac, lognormal,
+                                  uniform)
+        self.n = int(n)
+        self.uniform = bool(uniform)
+        self.ws_bytes = workspace_bytes(self.params)
+        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        st = self.lib.recon_create(C.byref(self.params), C.c_void_p(self.stream.cuda_stream),
+                                   C.c_void_p(self.workspace.data_ptr()), self.ws_bytes, C.byref(h))
+        self._check(st, "recon_create", handle=False)
+        self.h = h
+
+    @classmethod
+    def from_mock(cls, mock, **over):
+        p = mock.params(**over)
+        return cls(p["n"], p["L"], p["b"], p["f"], p["R"], p["observer"], p["los_mode"],
+                   p["periodic"], p["mask_frac"], p["lognormal"], p["uniform"])
+
+    def _check(self, st, what, handle=True, allow=()):
+        if st == OK or st in allow:
+            return st
+        msg = f"{what}: {self.lib.recon_status_str(st).decode()}"
+        if handle and getattr(self, "h", None):
+            extra = self.lib.recon_last_error(self.h).decode()
+            if extra:
+                msg += f" ({extra})"
+        raise ReconError(st, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.recon_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- pipeline --------------------------------------------------------------------------------
+    def deposit(self, gal_pos, gal_w=None, ran_pos=None, ran_w=None):
+        keep = []
+        g = _catalog(gal_pos, gal_w, keep)
+        r = _catalog(ran_pos, ran_w, keep)
+        st = self.lib.recon_deposit(self.h, C.byref(g), C.byref(r) if r is not None else None)
+        self._check(st, "recon_deposit")
+
+    def smooth(self):
+        self._check(self.lib.recon_smooth(self.h), "recon_smooth")
+
+    def iterate(self, start=START_PLAIN, tol=0.0, max_iter=6):
+        """Returns (n_iter, rel, status); status is OK or ERR_NOT_CONVERGED."""
+        n = C.c_int(0)
+        rel = C.c_double(0)
+        st = self.lib.recon_iterate(self.h, int(start), float(tol), int(max_iter), C.byref(n), C.byref(rel))
+        self._check(st, "recon_iterate", allow=(ERR_NOT_CONVERGED,))
+        return n.value, rel.value, st
+
+    def trace(self):
+        buf = (C.c_double * 4096)()
+        n = C.c_int(0)
+        self._check(self.lib.recon_get_trace(self.h, buf, 4096, C.byref(n)), "recon_get_trace")
+        return [buf[i] for i in range(min(n.value, 4096))]
+
+    def shift(self, pos, is_galaxy, want_pos=False, out=None, pos_out=None):
+        """Shift vectors (n, 3) float32 (and shifted positions (n, 3) float64 if want_pos).
+        Outputs live where the positions live (CUDA tensors for CUDA input, numpy for host)."""
+        import torch
+        keep = []
+        cat = _catalog(pos, None, keep)
+        n = cat.n
+        on_dev = bool(cat.on_device)
+        if on_dev:
+            sh = out if out is not None else torch.empty((n, 3), dtype=torch.float32, device="cuda")
+            po = (pos_out if pos_out is not None else torch.empty((n, 3), dtype=torch.float64, device="cuda")) \
+                if want_pos else None
+            sp, pp = sh.data_ptr(), (po.data_ptr() if po is not None else None)
+        else:
+            sh = out if out is not None else np.empty((n, 3), dtype=np.float32)
+            po = (pos_out if pos_out is not None else np.empty((n, 3), dtype=np.float64)) if want_pos else None
+            sp, pp = _host_ptr(sh), (_host_ptr(po) if po is not None else None)
+        st = self.lib.recon_shift(self.h, C.byref(cat), int(bool(is_galaxy)), C.c_void_p(sp),
+                                  C.c_void_p(pp) if pp else None, int(on_dev))
+        self._check(st, "recon_shift")
+        return (sh, po) if want_pos else sh
+
+    # -- accessors -------------------------------------------------------------------------------
+    def get_psi(self):
+        import torch
+        out = torch.empty((3, self.n, self.n, self.n), dtype=torch.float32, device="cuda")
+        self._check(self.lib.recon_get_psi(self.h, C.c_void_p(out.data_ptr()), 1), "recon_get_psi")
+        return out
+
+    def get_field(self, which):
+        import torch
+        n = self.n
+        if which == FIELD_DELTA_K:
+            out = torch.empty((n, n, n // 2 + 1, 2), dtype=torch.float32, device="cuda")
+        elif which == FIELD_PSI:
+            out = torch.empty((3, n, n, n), dtype=torch.float32, device="cuda")
+        else:
+            out = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+        self._check(self.lib.recon_get_field(self.h, int(which), C.c_void_p(out.data_ptr()), 1),
+                    "recon_get_field")
+        if which == FIELD_DELTA_K:
+            return torch.view_as_complex(out)
+        return out
+
+    def scalars(self):
+        buf = (C.c_double * 8)()
+        self._check(self.lib.recon_get_scalars(self.h, buf), "recon_get_scalars")
+        keys = ("sum_wg", "sum_wr", "alpha", "threshold", "lognormal_C", "n_mask", "norm_d2", "norm_s2")
+        return dict(zip(keys, list(buf)))
+
+    def set_timing(self, enable: bool):
+        self._check(self.lib.recon_set_timing(self.h, int(bool(enable))), "recon_set_timing")
+
+    def reset_timing(self):
+        self._check(self.lib.recon_reset_timing(self.h), "recon_reset_timing")
+
+    def timing(self):
+        """{kind: (launches, total_ms, algorithmic_bytes)} for every kernel kind."""
+        out = {}
+        for k, name in enumerate(KERNEL_KINDS):
+            ms = C.c_double(0)
+            cnt = C.c_int64(0)
+            by = C.c_double(0)
+            self._check(self.lib.recon_get_timing(self.h, k, C.byref(ms), C.byref(cnt), C.byref(by)),
+                        "recon_get_timing")
+            out[name] = (cnt.value, ms.value, by.value)
+        return out
+
+    def fft_r2c(self, x):
+        import torch
+        x = x.to(device="cuda", dtype=torch.float32).contiguous()
+        n = self.n
+        out = torch.empty((n, n, n // 2 + 1, 2), dtype=torch.float32, device="cuda")
+        self._check(self.lib.recon_fft_r2c(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr())),
+                    "recon_fft_r2c")
+        return torch.view_as_complex(out)
+
+    def fft_c2r(self, X):
+        import torch
+        X = torch.view_as_real(X.to(device="cuda", dtype=torch.complex64).contiguous()).contiguous()
+        n = self.n
+        out = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+        self._check(self.lib.recon_fft_c2r(self.h, C.c_void_p(X.data_ptr()), C.c_void_p(out.data_ptr())),
+                    "recon_fft_c2r")
+        return out
+
+    def run(self, gal_pos, ran_pos=None, start=START_PLAIN, tol=0.0, max_iter=6, gal_w=None, ran_w=None):
+        """deposit -> smooth -> iterate; returns (n_iter, rel, status)."""
+        self.deposit(gal_pos, gal_w, ran_pos, ran_w)
+        self.smooth()
+        return self.iterate(start, tol, max_iter)

@@ -1,0 +1,184 @@
+// cic.cu: cloud-in-cell mass assignment and interpolation, the reconstruction shift, reductions.
+//
+// Mass assignment (Sec. 3 bins tracers on the mesh; this library uses CIC instead of NGP): a
+// particle at grid coordinate u = x N / L deposits w (1 - t) and w t on the nodes floor(u) and
+// floor(u) + 1 of each axis, t = u - floor(u), with periodic wrap.  The same kernel interpolates
+// Psi back to particles for the shift of Sec. 1 (reversing Eq. Lagrange x = q + Psi).
+#include "cic.h"
+
+namespace rg {
+
+__device__ __forceinline__ int wrapi(long long i, int n) {
+  long long r = i % n;
+  return (int)(r < 0 ? r + n : r);
+}
+
+template <typename PT>
+__device__ __forceinline__ void cic_setup(const PT* __restrict__ pos, long long p, int n, double scale,
+                                          int (&i0)[3], int (&i1)[3], float (&t)[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double u = (double)pos[3 * p + a] * scale;
+    const double fl = floor(u);
+    t[a] = (float)(u - fl);
+    const long long ii = (long long)fl;
+    i0[a] = wrapi(ii, n);
+    i1[a] = (i0[a] + 1 == n) ? 0 : i0[a] + 1;
+  }
+}
+
+__device__ __forceinline__ double block_sum_d(double v) {
+  __shared__ double sh[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+  return r;
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(256) deposit_kernel(const PT* __restrict__ pos, const float* __restrict__ w,
+                                                      long long np, int n, double scale,
+                                                      float* __restrict__ rho, double* __restrict__ partials) {
+  double wsum = 0.0;
+  const size_t nn = (size_t)n;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np;
+       p += (long long)gridDim.x * blockDim.x) {
+    int i0[3], i1[3];
+    float t[3];
+    cic_setup(pos, p, n, scale, i0, i1, t);
+    const float wp = w ? w[p] : 1.f;
+    wsum += wp;
+    const float wx0 = wp * (1.f - t[0]), wx1 = wp * t[0];
+    const float wy0 = 1.f - t[1], wy1 = t[1];
+    const float wz0 = 1.f - t[2], wz1 = t[2];
+    const size_t r00 = ((size_t)i0[0] * nn + i0[1]) * nn, r01 = ((size_t)i0[0] * nn + i1[1]) * nn;
+    const size_t r10 = ((size_t)i1[0] * nn + i0[1]) * nn, r11 = ((size_t)i1[0] * nn + i1[1]) * nn;
+    atomicAdd(rho + r00 + i0[2], wx0 * wy0 * wz0);
+    atomicAdd(rho + r00 + i1[2], wx0 * wy0 * wz1);
+    atomicAdd(rho + r01 + i0[2], wx0 * wy1 * wz0);
+    atomicAdd(rho + r01 + i1[2], wx0 * wy1 * wz1);
+    atomicAdd(rho + r10 + i0[2], wx1 * wy0 * wz0);
+    atomicAdd(rho + r10 + i1[2], wx1 * wy0 * wz1);
+    atomicAdd(rho + r11 + i0[2], wx1 * wy1 * wz0);
+    atomicAdd(rho + r11 + i1[2], wx1 * wy1 * wz1);
+  }
+  const double s = block_sum_d(wsum);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(256) shift_kernel(const PT* __restrict__ pos, long long np, ShiftArgs a) {
+  const size_t nn = (size_t)a.n;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np;
+       p += (long long)gridDim.x * blockDim.x) {
+    int i0[3], i1[3];
+    float t[3];
+    cic_setup(pos, p, a.n, a.scale, i0, i1, t);
+    const size_t r00 = ((size_t)i0[0] * nn + i0[1]) * nn, r01 = ((size_t)i0[0] * nn + i1[1]) * nn;
+    const size_t r10 = ((size_t)i1[0] * nn + i0[1]) * nn, r11 = ((size_t)i1[0] * nn + i1[1]) * nn;
+    const float wx0 = 1.f - t[0], wx1 = t[0], wy0 = 1.f - t[1], wy1 = t[1], wz0 = 1.f - t[2], wz1 = t[2];
+    const size_t idx[8] = {r00 + i0[2], r00 + i1[2], r01 + i0[2], r01 + i1[2],
+                           r10 + i0[2], r10 + i1[2], r11 + i0[2], r11 + i1[2]};
+    const float cw[8] = {wx0 * wy0 * wz0, wx0 * wy0 * wz1, wx0 * wy1 * wz0, wx0 * wy1 * wz1,
+                         wx1 * wy0 * wz0, wx1 * wy0 * wz1, wx1 * wy1 * wz0, wx1 * wy1 * wz1};
+    float ps[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc = fmaf(cw[k], __ldg(a.psi[c] + idx[k]), acc);
+      ps[c] = acc;
+    }
+    const double x0 = (double)pos[3 * p], x1 = (double)pos[3 * p + 1], x2 = (double)pos[3 * p + 2];
+    float d[3];
+    if (a.is_galaxy) {
+      float rx, ry, rz;
+      if (a.los_mode == 1) {
+        rx = a.los.x; ry = a.los.y; rz = a.los.z;
+      } else {
+        const float dx = (float)(x0 - a.obs[0]), dy = (float)(x1 - a.obs[1]), dz = (float)(x2 - a.obs[2]);
+        const float q = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float ir = q > 0.f ? rsqrtf(q) : 0.f;
+        rx = dx * ir; ry = dy * ir; rz = dz * ir;
+      }
+      const float u = a.f * fmaf(ps[0], rx, fmaf(ps[1], ry, ps[2] * rz));
+      d[0] = -fmaf(u, rx, ps[0]);
+      d[1] = -fmaf(u, ry, ps[1]);
+      d[2] = -fmaf(u, rz, ps[2]);
+    } else {
+      d[0] = -ps[0]; d[1] = -ps[1]; d[2] = -ps[2];
+    }
+    a.shift[3 * p + 0] = d[0];
+    a.shift[3 * p + 1] = d[1];
+    a.shift[3 * p + 2] = d[2];
+    if (a.pos_out) {
+      double y[3] = {x0 + d[0], x1 + d[1], x2 + d[2]};
+      if (a.periodic) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          y[c] = y[c] - floor(y[c] / a.L) * a.L;
+          if (y[c] >= a.L) y[c] -= a.L;
+        }
+      }
+      a.pos_out[3 * p + 0] = y[0];
+      a.pos_out[3 * p + 1] = y[1];
+      a.pos_out[3 * p + 2] = y[2];
+    }
+  }
+}
+
+// Sum nq interleaved partial columns: red[dst + q] (=|+=) sum_b partials[b * nq + q].
+__global__ void __launch_bounds__(256) finalize_kernel(const double* __restrict__ partials, int nblocks, int nq,
+                                                       double* __restrict__ red, int dst, int accumulate) {
+  for (int q = 0; q < nq; ++q) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partials[(size_t)b * nq + q];
+    s = block_sum_d(s);
+    if (threadIdx.x == 0) red[dst + q] = accumulate ? red[dst + q] + s : s;
+  }
+}
+
+__global__ void add_scalar_kernel(float* __restrict__ x, size_t n, float v) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    x[i] += v;
+}
+
+cudaError_t launch_deposit(const void* pos, int dtype, const float* w, long long np, int n, double L,
+                           float* rho, double* partials, int blocks, cudaStream_t st) {
+  if (np <= 0) return cudaSuccess;
+  const double scale = (double)n / L;
+  if (dtype == 0)
+    deposit_kernel<double><<<blocks, 256, 0, st>>>((const double*)pos, w, np, n, scale, rho, partials);
+  else
+    deposit_kernel<float><<<blocks, 256, 0, st>>>((const float*)pos, w, np, n, scale, rho, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shift(const void* pos, int dtype, long long np, const ShiftArgs& a, cudaStream_t st) {
+  if (np <= 0) return cudaSuccess;
+  long long want = (np + 255) / 256;
+  const int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
+  if (dtype == 0)
+    shift_kernel<double><<<blocks, 256, 0, st>>>((const double*)pos, np, a);
+  else
+    shift_kernel<float><<<blocks, 256, 0, st>>>((const float*)pos, np, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const double* partials, int nblocks, int nq, double* red, int dst, int accumulate,
+                            cudaStream_t st) {
+  finalize_kernel<<<1, 256, 0, st>>>(partials, nblocks, nq, red, dst, accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_scalar(float* x, size_t n, float v, cudaStream_t st) {
+  add_scalar_kernel<<<152 * 8, 256, 0, st>>>(x, n, v);
+  return cudaGetLastError();
+}
+
+}  // namespace rg

@@ -1,0 +1,32 @@
+// cic.h: launchers of the particle kernels and the reduction helpers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace rg {
+
+struct ShiftArgs {
+  const float* psi[3];   // real Psi components, N^3 each
+  int n;
+  double scale;          // N / L
+  double L;
+  int is_galaxy;
+  float f;               // growth rate of the galaxy RSD term
+  int los_mode;          // 0 radial, 1 fixed
+  float3 los;            // fixed LOS unit vector
+  double obs[3];         // observer position (radial)
+  int periodic;
+  float* shift;          // (n, 3) out
+  double* pos_out;       // (n, 3) out or null
+};
+
+constexpr int kDepositBlocks = 152 * 8;
+
+cudaError_t launch_deposit(const void* pos, int dtype, const float* w, long long np, int n, double L,
+                           float* rho, double* partials, int blocks, cudaStream_t st);
+cudaError_t launch_shift(const void* pos, int dtype, long long np, const ShiftArgs& a, cudaStream_t st);
+cudaError_t launch_finalize(const double* partials, int nblocks, int nq, double* red, int dst, int accumulate,
+                            cudaStream_t st);
+cudaError_t launch_add_scalar(float* x, size_t n, float v, cudaStream_t st);
+
+}  // namespace rg

@@ -1,0 +1,214 @@
+// fft_core.cuh: shared-memory Stockham FFT building blocks for the reconstruction passes.
+//
+// A batch of complex lines of length L sits in shared memory; every stage of radix R reads R values
+// at stride L/R, applies the inter-stage twiddles, does an R-point DFT in registers and writes the
+// results in the autosorted (Stockham) order, so the output comes out in natural order with no bit
+// reversal.  Mixed radices (2, 3, 4, 6, 8) give every mesh side 2^a 3^b used by the library.
+// Transforms are unnormalised in both directions; the 1/N^3 of the inverse is applied once in
+// the k-space kernels.  Twiddles come from a float32 table of exp(-2 pi i m / M) that the host
+// computes in float64, so no fast-math sin/cos enters the transform.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rg {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by -i (forward sign) or +i (inverse sign)
+template <bool INV>
+__device__ __forceinline__ float2 rot(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+// multiply by i
+__device__ __forceinline__ float2 mul_i(float2 a) { return make_float2(-a.y, a.x); }
+
+// ----------------------------------------------------------------------------------------------
+// Small DFTs in registers.  Forward: y_m = sum_r x_r exp(-2 pi i r m / R); INV flips the sign.
+// ----------------------------------------------------------------------------------------------
+template <int R, bool INV>
+struct Dft;
+
+template <bool INV>
+struct Dft<2, INV> {
+  __device__ __forceinline__ static void run(float2* v) {
+    float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  }
+};
+
+template <bool INV>
+struct Dft<4, INV> {
+  __device__ __forceinline__ static void run(float2* v) {
+    float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    float2 t2 = cadd(v[1], v[3]), t3 = rot<INV>(csub(v[1], v[3]));
+    v[0] = cadd(t0, t2);
+    v[2] = csub(t0, t2);
+    v[1] = cadd(t1, t3);
+    v[3] = csub(t1, t3);
+  }
+};
+
+template <bool INV>
+struct Dft<8, INV> {
+  __device__ __forceinline__ static void run(float2* v) {
+    const float h = 0.70710678118654752f;
+    float2 e[4] = {v[0], v[2], v[4], v[6]};
+    float2 o[4] = {v[1], v[3], v[5], v[7]};
+    Dft<4, INV>::run(e);
+    Dft<4, INV>::run(o);
+    // o[m] *= w8^m, w8 = exp(-+ 2 pi i / 8)
+    float2 o1 = INV ? make_float2(h * (o[1].x - o[1].y), h * (o[1].x + o[1].y))
+                    : make_float2(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));
+    float2 o2 = rot<INV>(o[2]);
+    float2 o3 = INV ? make_float2(-h * (o[3].x + o[3].y), h * (o[3].x - o[3].y))
+                    : make_float2(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], o1);
+    v[5] = csub(e[1], o1);
+    v[2] = cadd(e[2], o2);
+    v[6] = csub(e[2], o2);
+    v[3] = cadd(e[3], o3);
+    v[7] = csub(e[3], o3);
+  }
+};
+
+template <bool INV>
+struct Dft<3, INV> {
+  __device__ __forceinline__ static void run(float2* v) {
+    const float s3 = 0.86602540378443865f;
+    float2 a = v[0], b = v[1], c = v[2];
+    float2 sum = cadd(b, c);
+    float2 t = make_float2(a.x - 0.5f * sum.x, a.y - 0.5f * sum.y);
+    float2 d = csub(b, c);
+    // s = (b - c) * (-+ i sqrt(3)/2)
+    float2 s = INV ? make_float2(-s3 * d.y, s3 * d.x) : make_float2(s3 * d.y, -s3 * d.x);
+    v[0] = cadd(a, sum);
+    v[1] = cadd(t, s);
+    v[2] = csub(t, s);
+  }
+};
+
+template <bool INV>
+struct Dft<6, INV> {
+  __device__ __forceinline__ static void run(float2* v) {
+    const float s3 = 0.86602540378443865f;
+    float2 e[3] = {v[0], v[2], v[4]};
+    float2 o[3] = {v[1], v[3], v[5]};
+    Dft<3, INV>::run(e);
+    Dft<3, INV>::run(o);
+    // w6 = exp(-+ i pi / 3) = (1/2, -+ s3); w6^2 = (-1/2, -+ s3)
+    const float sg = INV ? s3 : -s3;
+    float2 o1 = cmul(o[1], make_float2(0.5f, sg));
+    float2 o2 = cmul(o[2], make_float2(-0.5f, sg));
+    v[0] = cadd(e[0], o[0]);
+    v[3] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], o1);
+    v[4] = csub(e[1], o1);
+    v[2] = cadd(e[2], o2);
+    v[5] = csub(e[2], o2);
+  }
+};
+
+// ----------------------------------------------------------------------------------------------
+// Shared-memory layouts.  Element i of line col lives at phys(i, col).
+//   ColLayout<C>: lines are columns of an [L][C] tile (strided passes), C lines side by side.
+//   RowLayout<L>: lines are rows, padded by one element every 8 to spread bank accesses.
+// ----------------------------------------------------------------------------------------------
+template <int C>
+struct ColLayout {
+  static constexpr bool kColFast = true;
+  __device__ __forceinline__ static int phys(int i, int col) { return i * C + col; }
+};
+
+template <int L>
+struct RowLayout {
+  static constexpr bool kColFast = false;
+  static constexpr int kStride = L + L / 8;
+  __device__ __forceinline__ static int phys(int i, int col) { return col * kStride + i + (i >> 3); }
+};
+
+// One Stockham stage over NCOL lines of length L with T threads.  The twiddle table holds
+// exp(-2 pi i m / (L * TWS)); index m * TWS gives exp(-2 pi i m / L).
+template <int L, int NCOL, int T, int R, int NS, bool INV, class Lay, int TWS>
+__device__ __forceinline__ void stockham_stage(float2* __restrict__ s, const float2* __restrict__ tw) {
+  constexpr int NBL = L / R;
+  constexpr int NB = NBL * NCOL;
+  constexpr int PER = (NB + T - 1) / T;
+  constexpr int TWSTEP = L / (NS * R);
+  float2 v[PER][R];
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int b = threadIdx.x + p * T;
+    if ((NB % T == 0) || b < NB) {
+      const int col = Lay::kColFast ? (b % NCOL) : (b / NBL);
+      const int j = Lay::kColFast ? (b / NCOL) : (b % NBL);
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[p][r] = s[Lay::phys(j + r * NBL, col)];
+      if (NS > 1) {
+        const int k = j % NS;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = tw[(r * k * TWSTEP) * TWS];
+          if (INV) w.y = -w.y;
+          v[p][r] = cmul(v[p][r], w);
+        }
+      }
+      Dft<R, INV>::run(v[p]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int b = threadIdx.x + p * T;
+    if ((NB % T == 0) || b < NB) {
+      const int col = Lay::kColFast ? (b % NCOL) : (b / NBL);
+      const int j = Lay::kColFast ? (b / NCOL) : (b % NBL);
+      const int k = j % NS;
+      const int base = (j / NS) * NS * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) s[Lay::phys(base + r * NS, col)] = v[p][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <int L, int NCOL, int T, bool INV, class Lay, int TWS, int NS, int R, int... Rest>
+__device__ __forceinline__ void stockham_run(float2* s, const float2* tw) {
+  stockham_stage<L, NCOL, T, R, NS, INV, Lay, TWS>(s, tw);
+  if constexpr (sizeof...(Rest) > 0) stockham_run<L, NCOL, T, INV, Lay, TWS, NS * R, Rest...>(s, tw);
+}
+
+// Radix plan per line length.
+template <int L>
+struct Plan;
+#define RG_PLAN(LEN, ...)                                                                   \
+  template <>                                                                               \
+  struct Plan<LEN> {                                                                        \
+    template <int NCOL, int T, bool INV, class Lay, int TWS>                                \
+    __device__ __forceinline__ static void run(float2* s, const float2* tw) {               \
+      stockham_run<LEN, NCOL, T, INV, Lay, TWS, 1, __VA_ARGS__>(s, tw);                    \
+    }                                                                                       \
+  };
+RG_PLAN(16, 4, 4)
+RG_PLAN(24, 8, 3)
+RG_PLAN(32, 8, 4)
+RG_PLAN(48, 8, 6)
+RG_PLAN(64, 8, 8)
+RG_PLAN(96, 8, 4, 3)
+RG_PLAN(128, 8, 4, 4)
+RG_PLAN(192, 8, 8, 3)
+RG_PLAN(256, 8, 8, 4)
+RG_PLAN(384, 8, 8, 6)
+RG_PLAN(512, 8, 8, 8)
+RG_PLAN(1024, 8, 8, 4, 4)
+#undef RG_PLAN
+
+}  // namespace rg

@@ -1,0 +1,508 @@
+// passes.cuh: the three kinds of FFT pass of the reconstruction, each with its pointwise work fused.
+//
+// A 3-D r2c transform is three passes over the field: Z (contiguous rows, real <-> half complex),
+// Y and X (strided lines, one [N x C] tile of C adjacent columns per CTA).  Work that is pointwise
+// in configuration space rides on the Z pass (delta formation, the radial projection (Psi.r)r of
+// Eq. Nusser); work that is pointwise in Fourier space rides on the X pass, between its forward
+// and inverse transforms (Gaussian smoothing of Sec. 3.1, Z[s] = i k s / k^2 of Eq. Zeldovich, the
+// source update of Eq. iterative with its convergence norms).
+#pragma once
+#include "fft_core.cuh"
+#include "types.h"
+
+namespace rg {
+
+constexpr int kZThreads = 256;
+constexpr int kSThreads = 256;
+
+template <int N>
+struct ZRows {  // rows of the real field handled by one CTA of a Z pass
+  static constexpr int v = (N >= 512) ? 4 : (N >= 256 ? 8 : (N >= 128 ? 16 : 32));
+};
+template <int N>
+struct SCols {  // adjacent columns in one strided tile
+  static constexpr int v = (N >= 1024) ? 4 : 8;
+};
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+  return r;  // valid in thread 0
+}
+
+// ------------------------------------------------------------------------------------------------
+// Z pass: real rows of N floats <-> N/2+1 complex values (kz = 0..N/2).
+// A real row is packed as N/2 complex z_m = x_2m + i x_2m+1 and transformed with an N/2-point FFT;
+// the split into even/odd spectra with the exp(-2 pi i k / N) twiddles completes the r2c (and the
+// reverse for c2r, which returns N times the inverse transform of the row).
+// ------------------------------------------------------------------------------------------------
+template <int N, int NCOL>
+__device__ __forceinline__ void r2c_split(float2* s, float2* qv, const float2* tw) {
+  constexpr int L = N / 2;
+  using Lay = RowLayout<L>;
+  // every line: pairs (k, L - k) for k = 1..L/2, and k = 0 (which also gives the Nyquist value)
+  for (int e = threadIdx.x; e < NCOL * (L / 2 + 1); e += kZThreads) {
+    const int col = e / (L / 2 + 1), k = e % (L / 2 + 1);
+    if (k == 0) {
+      float2 z0 = s[Lay::phys(0, col)];
+      s[Lay::phys(0, col)] = make_float2(z0.x + z0.y, 0.f);
+      qv[col] = make_float2(z0.x - z0.y, 0.f);
+    } else {
+      const float2 zk = s[Lay::phys(k, col)], zm = s[Lay::phys(L - k, col)];
+      const float2 wk = tw[k], wm = tw[L - k];
+      // X[k] = (Zk + conj Zm)/2 - i w^k (Zk - conj Zm)/2
+      float2 ev = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+      float2 o = make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y + zm.y));
+      float2 xk = cadd(ev, cmul(make_float2(o.y, -o.x), wk));
+      float2 ev2 = make_float2(0.5f * (zm.x + zk.x), 0.5f * (zm.y - zk.y));
+      float2 o2 = make_float2(0.5f * (zm.x - zk.x), 0.5f * (zm.y + zk.y));
+      float2 xm = cadd(ev2, cmul(make_float2(o2.y, -o2.x), wm));
+      s[Lay::phys(k, col)] = xk;
+      s[Lay::phys(L - k, col)] = xm;
+    }
+  }
+}
+
+template <int N, int NCOL>
+__device__ __forceinline__ void c2r_merge(float2* s, const float2* qv, const float2* tw) {
+  constexpr int L = N / 2;
+  using Lay = RowLayout<L>;
+  for (int e = threadIdx.x; e < NCOL * (L / 2 + 1); e += kZThreads) {
+    const int col = e / (L / 2 + 1), k = e % (L / 2 + 1);
+    if (k == 0) {
+      const float2 x0 = s[Lay::phys(0, col)], xl = qv[col];
+      // E = X0 + conj XL, O = X0 - conj XL, Z0 = E + i O
+      float2 ev = make_float2(x0.x + xl.x, x0.y - xl.y);
+      float2 o = make_float2(x0.x - xl.x, x0.y + xl.y);
+      s[Lay::phys(0, col)] = cadd(ev, mul_i(o));
+    } else {
+      const float2 xk = s[Lay::phys(k, col)], xm = s[Lay::phys(L - k, col)];
+      const float2 wk = cconj(tw[k]), wm = cconj(tw[L - k]);
+      float2 ev = make_float2(xk.x + xm.x, xk.y - xm.y);
+      float2 o = cmul(make_float2(xk.x - xm.x, xk.y + xm.y), wk);
+      float2 ev2 = make_float2(xm.x + xk.x, xm.y - xk.y);
+      float2 o2 = cmul(make_float2(xm.x - xk.x, xm.y + xk.y), wm);
+      s[Lay::phys(k, col)] = cadd(ev, mul_i(o));
+      s[Lay::phys(L - k, col)] = cadd(ev2, mul_i(o2));
+    }
+  }
+}
+
+template <int N, int MODE, int NC>
+__global__ void __launch_bounds__(kZThreads) zpass_kernel(const ZArgs a) {
+  constexpr int L = N / 2;
+  constexpr int ROWS = ZRows<N>::v;
+  constexpr int NF = (MODE == Z_DELTA) ? 1 : NC;   // lines transformed per row
+  constexpr int NCOL = ROWS * NF;
+  using Lay = RowLayout<L>;
+  extern __shared__ float4 zsm[];
+  float2* tw = reinterpret_cast<float2*>(zsm);
+  float2* qv = tw + N;                       // Nyquist values, one per line
+  float2* s = qv + NCOL + (NCOL & 1);        // lines
+  __shared__ double red_sh[kZThreads / 32];
+
+  for (int m = threadIdx.x; m < N; m += kZThreads) tw[m] = a.tw[m];
+  const size_t row0 = (size_t)blockIdx.x * ROWS;
+
+  float acc0 = 0.f, acc1 = 0.f;
+  constexpr bool kInverse = (MODE == Z_INV || MODE == Z_PROJ || MODE == Z_FINAL);
+
+  if (kInverse) {
+    // load M rows (L complex) and the Nyquist values
+    for (int e = threadIdx.x; e < NC * ROWS * (L / 2); e += kZThreads) {
+      const int q = e / (ROWS * (L / 2));
+      const int rem = e % (ROWS * (L / 2));
+      const int row = rem / (L / 2), m2 = rem % (L / 2);
+      const float4 v = reinterpret_cast<const float4*>(a.f[q].M + (row0 + row) * L)[m2];
+      const int col = q * ROWS + row;
+      s[Lay::phys(2 * m2, col)] = make_float2(v.x, v.y);
+      s[Lay::phys(2 * m2 + 1, col)] = make_float2(v.z, v.w);
+    }
+    for (int e = threadIdx.x; e < NC * ROWS; e += kZThreads) {
+      const int q = e / ROWS, row = e % ROWS;
+      qv[q * ROWS + row] = a.f[q].Q[row0 + row];
+    }
+    __syncthreads();
+    c2r_merge<N, NCOL>(s, qv, tw);
+    __syncthreads();
+    Plan<L>::template run<NCOL, kZThreads, true, Lay, 2>(s, tw);
+  } else {
+    // load real rows of N floats as L packed complex values
+    const int nin = (MODE == Z_DELTA) ? (a.uniform ? 1 : 2) : NC;
+    if (MODE == Z_DELTA) {
+      const double* red = a.red;
+      const float inv_alpha = a.uniform ? (float)((double)N * N * N / red[RED_SUM_WG])
+                                        : (float)(red[RED_SUM_WR] / red[RED_SUM_WG]);
+      const float thr = a.uniform ? 0.f : (float)(a.mask_frac * red[RED_SUM_RPOS] / red[RED_CNT_RPOS]);
+      for (int e = threadIdx.x; e < ROWS * (L / 2); e += kZThreads) {
+        const int row = e / (L / 2), m2 = e % (L / 2);
+        const float4 g = reinterpret_cast<const float4*>(a.f[0].M + (row0 + row) * L)[m2];
+        float d[4];
+        if (nin == 1) {
+          d[0] = g.x * inv_alpha - 1.f; d[1] = g.y * inv_alpha - 1.f;
+          d[2] = g.z * inv_alpha - 1.f; d[3] = g.w * inv_alpha - 1.f;
+        } else {
+          const float4 r = reinterpret_cast<const float4*>(a.f[1].M + (row0 + row) * L)[m2];
+          const float gg[4] = {g.x, g.y, g.z, g.w}, rr[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const bool in = rr[u] > thr;
+            d[u] = in ? gg[u] * inv_alpha / rr[u] - 1.f : 0.f;
+            acc1 += in ? 1.f : 0.f;
+          }
+        }
+        if (a.lognormal) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            d[u] = logf(fmaxf(1.f + d[u], 1e-6f));
+            acc0 += d[u];
+          }
+        }
+        if (a.delta_real)
+          reinterpret_cast<float4*>(a.delta_real + (row0 + row) * N)[m2] = make_float4(d[0], d[1], d[2], d[3]);
+        s[Lay::phys(2 * m2, row)] = make_float2(d[0], d[1]);
+        s[Lay::phys(2 * m2 + 1, row)] = make_float2(d[2], d[3]);
+      }
+    } else {
+      for (int e = threadIdx.x; e < NC * ROWS * (L / 2); e += kZThreads) {
+        const int q = e / (ROWS * (L / 2));
+        const int rem = e % (ROWS * (L / 2));
+        const int row = rem / (L / 2), m2 = rem % (L / 2);
+        const float4 v = reinterpret_cast<const float4*>(a.f[q].M + (row0 + row) * L)[m2];
+        const int col = q * ROWS + row;
+        s[Lay::phys(2 * m2, col)] = make_float2(v.x, v.y);
+        s[Lay::phys(2 * m2 + 1, col)] = make_float2(v.z, v.w);
+      }
+    }
+    __syncthreads();
+  }
+
+  if (MODE == Z_PROJ || MODE == Z_FINAL) {
+    // s holds Psi_j(x, y, z) for the rows, z = 2m (.x) and 2m + 1 (.y)
+    if (MODE == Z_PROJ) {
+      const Geometry& g = a.g;
+      for (int e = threadIdx.x; e < ROWS * L; e += kZThreads) {
+        const int row = e / L, m = e % L;
+        const size_t rr = row0 + row;
+        const int ix = (int)(rr / N), iy = (int)(rr % N);
+        float2 p0 = s[Lay::phys(m, 0 * ROWS + row)];
+        float2 p1 = s[Lay::phys(m, 1 * ROWS + row)];
+        float2 p2 = s[Lay::phys(m, 2 * ROWS + row)];
+        float rx0, ry0, rz0, rx1, ry1, rz1;
+        if (g.los_mode == 1) {
+          rx0 = rx1 = g.los.x; ry0 = ry1 = g.los.y; rz0 = rz1 = g.los.z;
+        } else {
+          const float dx = g.off[ix], dy = g.off[N + iy];
+          const float dz0 = g.off[2 * N + 2 * m], dz1 = g.off[2 * N + 2 * m + 1];
+          const float q0 = fmaf(dx, dx, fmaf(dy, dy, dz0 * dz0));
+          const float q1 = fmaf(dx, dx, fmaf(dy, dy, dz1 * dz1));
+          const float i0 = q0 > 0.f ? rsqrtf(q0) : 0.f;
+          const float i1 = q1 > 0.f ? rsqrtf(q1) : 0.f;
+          rx0 = dx * i0; ry0 = dy * i0; rz0 = dz0 * i0;
+          rx1 = dx * i1; ry1 = dy * i1; rz1 = dz1 * i1;
+        }
+        const float u0 = a.coef * fmaf(p0.x, rx0, fmaf(p1.x, ry0, p2.x * rz0));
+        const float u1 = a.coef * fmaf(p0.y, rx1, fmaf(p1.y, ry1, p2.y * rz1));
+        s[Lay::phys(m, 0 * ROWS + row)] = make_float2(u0 * rx0, u1 * rx1);
+        s[Lay::phys(m, 1 * ROWS + row)] = make_float2(u0 * ry0, u1 * ry1);
+        s[Lay::phys(m, 2 * ROWS + row)] = make_float2(u0 * rz0, u1 * rz1);
+      }
+      __syncthreads();
+    }
+  }
+
+  if (MODE == Z_INV || MODE == Z_FINAL) {
+    // store real rows
+    for (int e = threadIdx.x; e < NC * ROWS * (L / 2); e += kZThreads) {
+      const int q = e / (ROWS * (L / 2));
+      const int rem = e % (ROWS * (L / 2));
+      const int row = rem / (L / 2), m2 = rem % (L / 2);
+      const int col = q * ROWS + row;
+      const float2 v0 = s[Lay::phys(2 * m2, col)], v1 = s[Lay::phys(2 * m2 + 1, col)];
+      if (MODE == Z_INV && a.stats && q == 1) {
+        acc0 += (v0.x > 0.f ? v0.x : 0.f) + (v0.y > 0.f ? v0.y : 0.f) + (v1.x > 0.f ? v1.x : 0.f) +
+                (v1.y > 0.f ? v1.y : 0.f);
+        acc1 += (v0.x > 0.f) + (v0.y > 0.f) + (v1.x > 0.f) + (v1.y > 0.f);
+      }
+      reinterpret_cast<float4*>(a.f[q].M + (row0 + row) * L)[m2] = make_float4(v0.x, v0.y, v1.x, v1.y);
+    }
+  } else {
+    // forward: FFT, split, store half complex rows + Nyquist
+    Plan<L>::template run<NCOL, kZThreads, false, Lay, 2>(s, tw);
+    r2c_split<N, NCOL>(s, qv, tw);
+    __syncthreads();
+    for (int e = threadIdx.x; e < NCOL * (L / 2); e += kZThreads) {
+      const int col = e / (L / 2), m2 = e % (L / 2);
+      const int q = col / ROWS, row = col % ROWS;
+      const float2 v0 = s[Lay::phys(2 * m2, col)], v1 = s[Lay::phys(2 * m2 + 1, col)];
+      float2* dst = (MODE == Z_DELTA) ? a.dout.M : a.f[q].M;
+      reinterpret_cast<float4*>(dst + (row0 + row) * L)[m2] = make_float4(v0.x, v0.y, v1.x, v1.y);
+    }
+    for (int e = threadIdx.x; e < NCOL; e += kZThreads) {
+      const int q = e / ROWS, row = e % ROWS;
+      float2* dst = (MODE == Z_DELTA) ? a.dout.Q : a.f[q].Q;
+      dst[row0 + row] = qv[e];
+    }
+  }
+
+  const bool want_red = (MODE == Z_DELTA) || (MODE == Z_INV && a.stats);
+  if (want_red) {
+    double r0 = block_sum((double)acc0, red_sh);
+    double r1 = block_sum((double)acc1, red_sh);
+    if (threadIdx.x == 0) {
+      a.partials[2 * blockIdx.x + 0] = r0;
+      a.partials[2 * blockIdx.x + 1] = r1;
+    }
+  }
+}
+
+template <int N, int NC>
+constexpr size_t zpass_smem(int mode) {
+  return sizeof(float2) * (N + 2 * ZRows<N>::v * NC + 2 +
+                           (size_t)ZRows<N>::v * (mode == Z_DELTA ? 1 : NC) * RowLayout<N / 2>::kStride);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Strided passes (Y and X).  A tile is N lines x C adjacent columns.  Tiles over the main array M:
+//   Y: lines along y at fixed x, columns kz0..kz0+C-1      (offset (x N + y) N/2 + kz)
+//   X: lines along x at fixed ky, columns kz0..kz0+C-1     (offset (x N + ky) N/2 + kz)
+// and over the Nyquist plane Q [kx][ky]:
+//   Y: lines along y (contiguous), columns are C values of x
+//   X: lines along x (stride N), columns are C adjacent ky
+// ------------------------------------------------------------------------------------------------
+struct Tile {
+  size_t base;
+  int ls, cs;      // line stride, column stride (complex elements)
+  int isQ;
+  int a;           // x (Y pass) or ky (X pass) of an M tile
+  int c0;          // first kz (M) or first column (Q)
+};
+
+template <int N, int C, int AXIS>
+__device__ __forceinline__ Tile tile_of(int t) {
+  constexpr int H = N / 2;
+  constexpr int MT = N * (H / C);
+  Tile r;
+  if (t < MT) {
+    r.isQ = 0;
+    r.a = t / (H / C);
+    r.c0 = (t % (H / C)) * C;
+    r.base = (AXIS == AX_Y) ? (size_t)r.a * N * H + r.c0 : (size_t)r.a * H + r.c0;
+    r.ls = (AXIS == AX_Y) ? H : N * H;
+    r.cs = 1;
+  } else {
+    r.isQ = 1;
+    r.a = 0;
+    r.c0 = (t - MT) * C;
+    r.base = (AXIS == AX_Y) ? (size_t)r.c0 * N : (size_t)r.c0;
+    r.ls = (AXIS == AX_Y) ? 1 : N;
+    r.cs = (AXIS == AX_Y) ? N : 1;
+  }
+  return r;
+}
+
+template <int N, int C>
+__device__ __forceinline__ void tile_load(float2* s, const float2* __restrict__ P, const Tile& t) {
+  using Lay = ColLayout<C>;
+  if (t.cs == 1) {
+    for (int e = threadIdx.x; e < N * (C / 2); e += kSThreads) {
+      const int i = e / (C / 2), cp = e % (C / 2);
+      const float4 v = *reinterpret_cast<const float4*>(P + t.base + (size_t)i * t.ls + 2 * cp);
+      s[Lay::phys(i, 2 * cp)] = make_float2(v.x, v.y);
+      s[Lay::phys(i, 2 * cp + 1)] = make_float2(v.z, v.w);
+    }
+  } else {
+    for (int e = threadIdx.x; e < N * C; e += kSThreads) {
+      const int c = e / N, i = e % N;
+      s[Lay::phys(i, c)] = P[t.base + (size_t)c * t.cs + (size_t)i * t.ls];
+    }
+  }
+}
+
+template <int N, int C>
+__device__ __forceinline__ void tile_store(const float2* s, float2* __restrict__ P, const Tile& t) {
+  using Lay = ColLayout<C>;
+  if (t.cs == 1) {
+    for (int e = threadIdx.x; e < N * (C / 2); e += kSThreads) {
+      const int i = e / (C / 2), cp = e % (C / 2);
+      const float2 v0 = s[Lay::phys(i, 2 * cp)], v1 = s[Lay::phys(i, 2 * cp + 1)];
+      *reinterpret_cast<float4*>(P + t.base + (size_t)i * t.ls + 2 * cp) = make_float4(v0.x, v0.y, v1.x, v1.y);
+    }
+  } else {
+    for (int e = threadIdx.x; e < N * C; e += kSThreads) {
+      const int c = e / N, i = e % N;
+      P[t.base + (size_t)c * t.cs + (size_t)i * t.ls] = s[Lay::phys(i, c)];
+    }
+  }
+}
+
+template <int N, int MODE, int NC, int AXIS>
+__global__ void __launch_bounds__(kSThreads) spass_kernel(const SArgs a) {
+  constexpr int C = SCols<N>::v;
+  constexpr int H = N / 2;
+  constexpr int NS = (MODE == S_DELTA || MODE == S_ITER) ? 3 : NC;   // smem slots
+  using Lay = ColLayout<C>;
+  extern __shared__ float4 ssm[];
+  float2* tw = reinterpret_cast<float2*>(ssm);
+  float2* s = tw + N;
+  __shared__ double red_sh[kSThreads / 32];
+
+  for (int m = threadIdx.x; m < N; m += kSThreads) tw[m] = a.tw[m];
+  const Tile t = tile_of<N, C, AXIS>(blockIdx.x);
+
+  // ---- load
+  if (MODE == S_DELTA) {
+    tile_load<N, C>(s, t.isQ ? a.dk.Q : a.dk.M, t);
+  } else {
+#pragma unroll
+    for (int q = 0; q < NC; ++q) tile_load<N, C>(s + q * N * C, t.isQ ? a.f[q].Q : a.f[q].M, t);
+  }
+  __syncthreads();
+
+  // ---- forward transform along the line
+  if (MODE == S_FWD || MODE == S_SMOOTH || MODE == S_ITER) {
+#pragma unroll
+    for (int q = 0; q < NC; ++q) Plan<N>::template run<C, kSThreads, false, Lay, 1>(s + q * N * C, tw);
+  } else if (MODE == S_DELTA) {
+    if (!a.d_is_k) Plan<N>::template run<C, kSThreads, false, Lay, 1>(s, tw);
+  }
+
+  float d2 = 0.f, s2 = 0.f;
+  if (MODE == S_SMOOTH || MODE == S_DELTA || MODE == S_ITER) {
+    const Geometry& g = a.g;
+    for (int e = threadIdx.x; e < N * C; e += kSThreads) {
+      const int i = e / C, c = e % C;
+      const int mx = (i < H) ? i : i - N;
+      int ky, kz;
+      if (!t.isQ) { ky = t.a; kz = t.c0 + c; } else { ky = t.c0 + c; kz = H; }
+      const int my = (ky < H) ? ky : ky - N;
+      const float kx = g.kf * mx, kyf = g.kf * my, kzf = g.kf * kz;
+      const float k2 = kx * kx + kyf * kyf + kzf * kzf;
+      const int p = Lay::phys(i, c);
+      if (MODE == S_SMOOTH) {
+        const float w = expf(-a.half_R2 * k2) * g.inv_n3;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) s[q * N * C + p] = cscale(s[q * N * C + p], w);
+      } else {
+        const float kdx = (i == H) ? 0.f : kx;
+        const float kdy = (ky == H) ? 0.f : kyf;
+        const float kdz = (kz == H) ? 0.f : kzf;
+        const size_t gi = t.base + (size_t)i * t.ls + (size_t)c * t.cs;
+        float2* Sp = t.isQ ? a.sbuf.Q : a.sbuf.M;
+        float2 S;
+        if (MODE == S_DELTA) {
+          float2 dk = s[p];
+          if (!a.d_is_k) {
+            if (a.lognormal && i == 0 && ky == 0 && kz == 0)
+              dk.x -= (float)(a.red[RED_SUM_LOG]);   // subtract N^3 <ln(1+delta)> at k = 0
+            (t.isQ ? a.dk.Q : a.dk.M)[gi] = dk;
+          }
+          S = cscale(dk, a.inv_b);
+        } else {
+          const float2 dk = (t.isQ ? a.dk.Q : a.dk.M)[gi];
+          const float2 px = s[p], py = s[N * C + p], pz = s[2 * N * C + p];
+          // i k . P
+          const float dre = kdx * px.x + kdy * py.x + kdz * pz.x;
+          const float dim = kdx * px.y + kdy * py.y + kdz * pz.y;
+          S = make_float2(fmaf(a.beta, -dim, dk.x * a.inv_b), fmaf(a.beta, dre, dk.y * a.inv_b));
+        }
+        if (k2 == 0.f) S = make_float2(0.f, 0.f);
+        const float inv_k2 = (k2 > 0.f) ? 1.f / k2 : 0.f;
+        if (MODE == S_ITER) {
+          const float2 sp = Sp[gi];
+          const float wgt = (kz == 0 || kz == H) ? 1.f : 2.f;
+          const float fac = wgt * (kdx * kdx + kdy * kdy + kdz * kdz) * inv_k2 * inv_k2;
+          const float ddx = S.x - sp.x, ddy = S.y - sp.y;
+          d2 = fmaf(fac, ddx * ddx + ddy * ddy, d2);
+          s2 = fmaf(fac, S.x * S.x + S.y * S.y, s2);
+        }
+        Sp[gi] = S;
+        // Psi_j = i kd_j S / k^2, with the 1/N^3 of the inverse transform folded in
+        const float2 iS = cscale(mul_i(S), inv_k2 * g.inv_n3);
+        s[p] = cscale(iS, kdx);
+        s[N * C + p] = cscale(iS, kdy);
+        s[2 * N * C + p] = cscale(iS, kdz);
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- inverse transform along the line
+  if (MODE == S_INV || MODE == S_SMOOTH || MODE == S_DELTA || MODE == S_ITER) {
+#pragma unroll
+    for (int q = 0; q < NS; ++q) Plan<N>::template run<C, kSThreads, true, Lay, 1>(s + q * N * C, tw);
+  }
+
+  // ---- store
+#pragma unroll
+  for (int q = 0; q < NS; ++q) tile_store<N, C>(s + q * N * C, t.isQ ? a.f[q].Q : a.f[q].M, t);
+
+  if (MODE == S_ITER) {
+    double r0 = block_sum((double)d2, red_sh);
+    double r1 = block_sum((double)s2, red_sh);
+    if (threadIdx.x == 0) {
+      a.partials[2 * blockIdx.x + 0] = r0;
+      a.partials[2 * blockIdx.x + 1] = r1;
+    }
+  }
+}
+
+template <int N>
+constexpr size_t spass_smem(int nslots) {
+  return sizeof(float2) * ((size_t)N + (size_t)nslots * N * SCols<N>::v);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Launch tables
+// ------------------------------------------------------------------------------------------------
+template <class K>
+static cudaError_t launch_with_smem(K kern, int blocks, int threads, size_t smem, cudaStream_t st, const void* arg) {
+  static_assert(sizeof(K) > 0, "");
+  cudaError_t e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {const_cast<void*>(arg)};
+  return cudaLaunchKernel((const void*)kern, dim3(blocks), dim3(threads), args, smem, st);
+}
+
+template <int N>
+struct MeshImpl {
+  static constexpr int kZBlocks = N * N / ZRows<N>::v;
+  static constexpr int kSBlocks = N * ((N / 2) / SCols<N>::v) + N / SCols<N>::v;
+
+  static cudaError_t zpass(int mode, int nc, const ZArgs& a, cudaStream_t st) {
+#define RG_Z(M_, NC_)                                                                                   \
+  if (mode == M_ && nc == NC_)                                                                          \
+    return launch_with_smem(zpass_kernel<N, M_, NC_>, kZBlocks, kZThreads, zpass_smem<N, NC_>(M_), st, &a);
+    RG_Z(Z_FWD, 1) RG_Z(Z_FWD, 2) RG_Z(Z_INV, 1) RG_Z(Z_INV, 2) RG_Z(Z_DELTA, 2) RG_Z(Z_PROJ, 3)
+    RG_Z(Z_FINAL, 3)
+#undef RG_Z
+    return cudaErrorInvalidValue;
+  }
+
+  static cudaError_t spass(int mode, int nc, int axis, const SArgs& a, cudaStream_t st) {
+#define RG_S(M_, NC_, AX_)                                                                              \
+  if (mode == M_ && nc == NC_ && axis == AX_)                                                           \
+    return launch_with_smem(spass_kernel<N, M_, NC_, AX_>, kSBlocks, kSThreads,                         \
+                            spass_smem<N>((M_ == S_DELTA || M_ == S_ITER) ? 3 : NC_), st, &a);
+    RG_S(S_FWD, 1, AX_Y) RG_S(S_FWD, 2, AX_Y) RG_S(S_FWD, 3, AX_Y)
+    RG_S(S_INV, 1, AX_Y) RG_S(S_INV, 2, AX_Y) RG_S(S_INV, 3, AX_Y)
+    RG_S(S_FWD, 1, AX_X) RG_S(S_INV, 1, AX_X)
+    RG_S(S_SMOOTH, 1, AX_X) RG_S(S_SMOOTH, 2, AX_X)
+    RG_S(S_DELTA, 1, AX_X) RG_S(S_ITER, 3, AX_X)
+#undef RG_S
+    return cudaErrorInvalidValue;
+  }
+
+  static const MeshKernels* table() {
+    static const MeshKernels t = {N, kZBlocks, kSBlocks, &zpass, &spass};
+    return &t;
+  }
+};
+
+}  // namespace rg

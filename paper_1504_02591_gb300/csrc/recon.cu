@@ -1,0 +1,788 @@
+// recon.cu: the C ABI (include/recon.h) and the host-side orchestration of the passes.
+//
+// Pipeline per reconstruction (Burden, Percival & Howlett 2015):
+//   deposit  CIC of galaxies and randoms -> rho_g, rho_r; sums of weights (float64)
+//   smooth   Z r2c | Y | X (x exp(-k^2 R^2/2)) | Y | Z c2r + mask statistics      (Sec. 3.1, 3.2)
+//            Z: delta = rho_g,s/(alpha rho_r,s) - 1 in the mask (+ lognormal) and its r2c | Y
+//   iterate  X: delta(k), S_-1 = delta/b, Psi_s = Z[delta/b] | Y | Z: P_0 = (1-c)(Psi_s.r)r | Y
+//            repeat: X: S_n = delta/b + beta i k.P_n, norms, Psi = i k S/k^2 | Y |
+//                    Z: P = (Psi.r)r (or the final real Psi) | Y                  (Sec. 5.1)
+//   shift    CIC interpolation of Psi to the particles, d = -(Psi + f (Psi.r) r) or -Psi (Sec. 1)
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/recon.h"
+#include "cic.h"
+#include "types.h"
+
+namespace rg {
+const MeshKernels* mesh_kernels_32();
+const MeshKernels* mesh_kernels_48();
+const MeshKernels* mesh_kernels_64();
+const MeshKernels* mesh_kernels_96();
+const MeshKernels* mesh_kernels_128();
+const MeshKernels* mesh_kernels_256();
+const MeshKernels* mesh_kernels_384();
+const MeshKernels* mesh_kernels_512();
+const MeshKernels* mesh_kernels_1024();
+
+const MeshKernels* mesh_kernels(int n) {
+  switch (n) {
+    case 32: return mesh_kernels_32();
+    case 48: return mesh_kernels_48();
+    case 64: return mesh_kernels_64();
+    case 96: return mesh_kernels_96();
+    case 128: return mesh_kernels_128();
+    case 256: return mesh_kernels_256();
+    case 384: return mesh_kernels_384();
+    case 512: return mesh_kernels_512();
+    case 1024: return mesh_kernels_1024();
+    default: return nullptr;
+  }
+}
+}  // namespace rg
+
+using namespace rg;
+
+namespace {
+
+constexpr long long kStageParticles = 1LL << 21;   // particles per host<->device chunk
+constexpr size_t kStageBytesPer = 64;              // 24 pos + 4 w + 12 shift + 24 pos_out
+
+enum State { ST_CREATED = 0, ST_DEPOSITED = 1, ST_SMOOTHED = 2, ST_ITERATED = 3 };
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t field_M, field_Q, field, tw, off, red, partials, stage, total;
+};
+
+Layout layout_for(int n) {
+  const MeshKernels* mk = mesh_kernels(n);
+  Layout l{};
+  l.field_M = align256((size_t)n * n * n * sizeof(float));
+  l.field_Q = align256((size_t)n * n * sizeof(float2));
+  l.field = l.field_M + l.field_Q;
+  l.tw = align256((size_t)n * sizeof(float2));
+  l.off = align256((size_t)3 * n * sizeof(float));
+  l.red = align256(64 * sizeof(double));
+  size_t nb = (size_t)mk->z_blocks;
+  if ((size_t)mk->s_blocks > nb) nb = mk->s_blocks;
+  if ((size_t)kDepositBlocks > nb) nb = kDepositBlocks;
+  l.partials = align256(nb * 4 * sizeof(double));
+  l.stage = align256((size_t)kStageParticles * kStageBytesPer);
+  l.total = 5 * l.field + l.tw + l.off + l.red + l.partials + l.stage;
+  return l;
+}
+
+bool valid_params(const recon_params* p) {
+  if (!p) return false;
+  const int n = p->nmesh[0];
+  if (p->nmesh[1] != n || p->nmesh[2] != n) return false;
+  if (!mesh_kernels(n)) return false;
+  if (!(p->box[0] > 0) || p->box[1] != p->box[0] || p->box[2] != p->box[0]) return false;
+  if (!(p->b > 0) || !std::isfinite(p->f) || p->f < 0) return false;
+  if (!(p->smooth_R >= 0)) return false;
+  if (p->los_mode != RECON_LOS_RADIAL && p->los_mode != RECON_LOS_FIXED) return false;
+  if (p->los_mode == RECON_LOS_FIXED) {
+    const double q = p->observer[0] * p->observer[0] + p->observer[1] * p->observer[1] +
+                     p->observer[2] * p->observer[2];
+    if (!(q > 0)) return false;
+  }
+  if (p->mean_density_mode != RECON_MEAN_RANDOMS && p->mean_density_mode != RECON_MEAN_UNIFORM) return false;
+  if (!(p->mask_frac >= 0)) return false;
+  return true;
+}
+
+}  // namespace
+
+struct recon_handle {
+  recon_params p{};
+  int n = 0;
+  double L = 0;
+  cudaStream_t st = nullptr;
+  int device = 0;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool own_ws = false;
+  Layout lay{};
+  Field V[3]{}, D{}, S{};
+  float2* tw = nullptr;
+  float* off = nullptr;
+  double* red = nullptr;
+  double* partials = nullptr;
+  char* stage = nullptr;
+  const MeshKernels* mk = nullptr;
+  int state = ST_CREATED;
+  int d_is_k = 0;
+  int delta_real_valid = 0;
+  std::vector<double> trace;
+  std::string err;
+  Geometry geo{};
+  // launch accounting
+  int timing = 0;
+  int64_t launches[RECON_K_COUNT] = {};
+  double ms[RECON_K_COUNT] = {};
+  double bytes[RECON_K_COUNT] = {};
+  struct Pending { int kind; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+};
+
+#define RG_CUDA(call)                                            \
+  do {                                                           \
+    cudaError_t e_ = (call);                                     \
+    if (e_ != cudaSuccess) {                                     \
+      h->err = std::string(#call) + ": " + cudaGetErrorString(e_); \
+      return RECON_ERR_CUDA;                                     \
+    }                                                            \
+  } while (0)
+
+namespace {
+
+// Run one kernel launch, counting it and, when timing is on, bracketing it with events.
+template <class F>
+cudaError_t timed(recon_handle* h, int kind, double alg_bytes, F&& launch) {
+  h->launches[kind] += 1;
+  h->bytes[kind] += alg_bytes;
+  if (!h->timing) return launch();
+  recon_handle::Pending p{kind, nullptr, nullptr};
+  cudaError_t e;
+  if ((e = cudaEventCreate(&p.a)) != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&p.b)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(p.a, h->st)) != cudaSuccess) return e;
+  if ((e = launch()) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(p.b, h->st)) != cudaSuccess) return e;
+  h->pending.push_back(p);
+  return cudaSuccess;
+}
+
+cudaError_t drain_timing(recon_handle* h) {
+  cudaError_t first = cudaSuccess;
+  for (auto& p : h->pending) {
+    float t = 0.f;
+    cudaError_t e = cudaEventSynchronize(p.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, p.a, p.b);
+    if (e == cudaSuccess) h->ms[p.kind] += t;
+    else if (first == cudaSuccess) first = e;
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  h->pending.clear();
+  return first;
+}
+
+int zkind(int mode) {
+  switch (mode) {
+    case Z_FWD: return RECON_K_ZFWD;
+    case Z_INV: return RECON_K_ZINV;
+    case Z_DELTA: return RECON_K_ZDELTA;
+    case Z_PROJ: return RECON_K_ZPROJ;
+    default: return RECON_K_ZFINAL;
+  }
+}
+
+int skind(int mode, int axis) {
+  if (axis == AX_Y) return mode == S_FWD ? RECON_K_YFWD : RECON_K_YINV;
+  switch (mode) {
+    case S_SMOOTH: return RECON_K_XSMOOTH;
+    case S_DELTA: return RECON_K_XDELTA;
+    case S_ITER: return RECON_K_XITER;
+    default: return RECON_K_OTHER;
+  }
+}
+
+Field field_at(char* base, const Layout& l) {
+  Field f;
+  f.M = reinterpret_cast<float2*>(base);
+  f.Q = reinterpret_cast<float2*>(base + l.field_M);
+  return f;
+}
+
+ZArgs zargs(recon_handle* h) {
+  ZArgs a{};
+  a.g = h->geo;
+  a.tw = h->tw;
+  a.partials = h->partials;
+  a.red = h->red;
+  a.coef = 1.f;
+  a.mask_frac = (float)h->p.mask_frac;
+  a.uniform = h->p.mean_density_mode == RECON_MEAN_UNIFORM;
+  a.lognormal = h->p.lognormal;
+  return a;
+}
+
+SArgs sargs(recon_handle* h) {
+  SArgs a{};
+  a.g = h->geo;
+  a.tw = h->tw;
+  a.partials = h->partials;
+  a.red = h->red;
+  a.dk = h->D;
+  a.sbuf = h->S;
+  a.inv_b = (float)(1.0 / h->p.b);
+  a.beta = (float)(h->p.f / h->p.b);
+  a.half_R2 = (float)(0.5 * h->p.smooth_R * h->p.smooth_R);
+  a.lognormal = h->p.lognormal;
+  return a;
+}
+
+// Algorithmic bytes of one pass: every field it reads and writes, once.
+double cfield(const recon_handle* h) { return (double)h->n * h->n * h->n * 4.0 + (double)h->n * h->n * 8.0; }
+double rfield(const recon_handle* h) { return (double)h->n * h->n * h->n * 4.0; }
+
+double zbytes(const recon_handle* h, int mode, int nc, const ZArgs& a) {
+  if (mode == Z_DELTA) {
+    const int nin = a.uniform ? 1 : 2;
+    return nin * rfield(h) + cfield(h) + (a.delta_real ? rfield(h) : 0.0);
+  }
+  if (mode == Z_FINAL) return nc * (cfield(h) + rfield(h));
+  return 2.0 * nc * cfield(h);
+}
+
+double sbytes(const recon_handle* h, int mode, int nc) {
+  if (mode == S_DELTA) return (1.0 + 1.0 + 1.0 + 3.0) * cfield(h);   // delta in, delta(k), S, 3 Psi
+  if (mode == S_ITER) return 9.0 * cfield(h);                         // 3 P + delta(k) + S in; 3 Psi + S out
+  return 2.0 * nc * cfield(h);
+}
+
+recon_status run_z(recon_handle* h, int mode, int nc, const ZArgs& a) {
+  RG_CUDA(timed(h, zkind(mode), zbytes(h, mode, nc, a), [&] { return h->mk->zpass(mode, nc, a, h->st); }));
+  return RECON_OK;
+}
+
+recon_status run_s(recon_handle* h, int mode, int nc, int axis, const SArgs& a) {
+  RG_CUDA(timed(h, skind(mode, axis), sbytes(h, mode, nc), [&] { return h->mk->spass(mode, nc, axis, a, h->st); }));
+  return RECON_OK;
+}
+
+recon_status finalize(recon_handle* h, int nblocks, int nq, int dst, int accumulate) {
+  RG_CUDA(timed(h, RECON_K_OTHER, 8.0 * nblocks * nq, [&] {
+    return launch_finalize(h->partials, nblocks, nq, h->red, dst, accumulate, h->st); }));
+  return RECON_OK;
+}
+
+#define RG_TRY(x)                      \
+  do {                                 \
+    recon_status s_ = (x);             \
+    if (s_ != RECON_OK) return s_;     \
+  } while (0)
+
+// plain Y pass over nc of the vector fields
+recon_status ypass(recon_handle* h, int mode, int nc, const Field* f) {
+  SArgs a = sargs(h);
+  for (int q = 0; q < nc; ++q) a.f[q] = f[q];
+  return run_s(h, mode, nc, AX_Y, a);
+}
+
+size_t elem_size(int dtype) { return dtype == RECON_F64 ? 8 : 4; }
+
+recon_status check_catalog(const recon_catalog* c) {
+  if (!c) return RECON_ERR_INVALID_ARG;
+  if (c->n < 0) return RECON_ERR_INVALID_ARG;
+  if (c->n > 0 && !c->pos) return RECON_ERR_INVALID_ARG;
+  if (c->dtype != RECON_F64 && c->dtype != RECON_F32) return RECON_ERR_INVALID_ARG;
+  return RECON_OK;
+}
+
+// Deposit one catalogue into rho; the weight sum goes to red[slot].
+recon_status deposit_one(recon_handle* h, const recon_catalog* c, float* rho, int slot) {
+  const size_t es = elem_size(c->dtype);
+  if (c->on_device || c->n == 0) {
+    const int blocks = kDepositBlocks;
+    RG_CUDA(timed(h, RECON_K_DEPOSIT, (double)c->n * (3 * es + (c->w ? 4 : 0)) + rfield(h), [&] {
+      return launch_deposit(c->pos, c->dtype, c->w, c->n, h->n, h->L, rho, h->partials, blocks, h->st); }));
+    RG_TRY(finalize(h, blocks, 1, slot, 0));
+    return RECON_OK;
+  }
+  char* spos = h->stage;
+  float* sw = reinterpret_cast<float*>(h->stage + kStageParticles * 24);
+  for (long long p0 = 0; p0 < c->n; p0 += kStageParticles) {
+    const long long m = (c->n - p0 < kStageParticles) ? c->n - p0 : kStageParticles;
+    RG_CUDA(cudaMemcpyAsync(spos, (const char*)c->pos + (size_t)p0 * 3 * es, (size_t)m * 3 * es,
+                            cudaMemcpyHostToDevice, h->st));
+    if (c->w)
+      RG_CUDA(cudaMemcpyAsync(sw, c->w + p0, (size_t)m * sizeof(float), cudaMemcpyHostToDevice, h->st));
+    const int blocks = kDepositBlocks;
+    RG_CUDA(timed(h, RECON_K_DEPOSIT, (double)m * (3 * es + (c->w ? 4 : 0)) + (p0 == 0 ? rfield(h) : 0.0), [&] {
+      return launch_deposit(spos, c->dtype, c->w ? sw : nullptr, m, h->n, h->L, rho, h->partials, blocks, h->st); }));
+    RG_TRY(finalize(h, blocks, 1, slot, p0 > 0));
+  }
+  return RECON_OK;
+}
+
+// Copy a half-grid field (M, Q) into the standard [kx][ky][kz = 0..N/2] layout (or back).
+recon_status export_half(recon_handle* h, const Field& f, float* out) {
+  const int n = h->n;
+  const size_t H = n / 2;
+  RG_CUDA(cudaMemcpy2DAsync(out, (H + 1) * sizeof(float2), f.M, H * sizeof(float2), H * sizeof(float2),
+                            (size_t)n * n, cudaMemcpyDefault, h->st));
+  RG_CUDA(cudaMemcpy2DAsync(reinterpret_cast<float2*>(out) + H, (H + 1) * sizeof(float2), f.Q, sizeof(float2),
+                            sizeof(float2), (size_t)n * n, cudaMemcpyDefault, h->st));
+  return RECON_OK;
+}
+
+recon_status import_half(recon_handle* h, const float* in, const Field& f) {
+  const int n = h->n;
+  const size_t H = n / 2;
+  RG_CUDA(cudaMemcpy2DAsync(f.M, H * sizeof(float2), in, (H + 1) * sizeof(float2), H * sizeof(float2),
+                            (size_t)n * n, cudaMemcpyDefault, h->st));
+  RG_CUDA(cudaMemcpy2DAsync(f.Q, sizeof(float2), reinterpret_cast<const float2*>(in) + H, (H + 1) * sizeof(float2),
+                            sizeof(float2), (size_t)n * n, cudaMemcpyDefault, h->st));
+  return RECON_OK;
+}
+
+double start_coefficient(int start, double beta) {
+  if (start == RECON_START_APPROX1) return beta / (1.0 + beta);
+  if (start == RECON_START_FFTA) return 3.0 * beta / (7.0 + 3.0 * beta);
+  return 0.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* recon_status_str(recon_status s) {
+  switch (s) {
+    case RECON_OK: return "ok";
+    case RECON_ERR_INVALID_ARG: return "invalid argument";
+    case RECON_ERR_OOM: return "out of device memory or workspace too small";
+    case RECON_ERR_CUDA: return "CUDA error";
+    case RECON_ERR_NOT_CONVERGED: return "not converged within max_iter";
+    case RECON_ERR_NONFINITE: return "non-finite value in the convergence norms";
+    case RECON_ERR_STATE: return "call out of order";
+    case RECON_ERR_TIMEOUT: return "bounded device wait timed out";
+    case RECON_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* recon_last_error(recon_handle* h) { return h ? h->err.c_str() : ""; }
+
+recon_status recon_workspace_bytes(const recon_params* p, size_t* bytes) {
+  if (!valid_params(p) || !bytes) return RECON_ERR_INVALID_ARG;
+  *bytes = layout_for(p->nmesh[0]).total;
+  return RECON_OK;
+}
+
+recon_status recon_create(const recon_params* p, void* stream, void* workspace, size_t workspace_bytes,
+                          recon_handle** out) {
+  if (!out || !valid_params(p)) return RECON_ERR_INVALID_ARG;
+  *out = nullptr;
+  recon_handle* h = new recon_handle();
+  h->p = *p;
+  h->n = p->nmesh[0];
+  h->L = p->box[0];
+  h->st = (cudaStream_t)stream;
+  h->mk = mesh_kernels(h->n);
+  h->lay = layout_for(h->n);
+  cudaGetDevice(&h->device);
+  if (workspace) {
+    if (workspace_bytes < h->lay.total || ((uintptr_t)workspace & 255)) {
+      delete h;
+      return workspace_bytes < 0 ? RECON_ERR_INVALID_ARG : RECON_ERR_OOM;
+    }
+    h->ws = (char*)workspace;
+    h->ws_bytes = workspace_bytes;
+  } else {
+    if (cudaMalloc(&h->ws, h->lay.total) != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      return RECON_ERR_OOM;
+    }
+    h->own_ws = true;
+    h->ws_bytes = h->lay.total;
+  }
+  char* b = h->ws;
+  for (int q = 0; q < 3; ++q, b += h->lay.field) h->V[q] = field_at(b, h->lay);
+  h->D = field_at(b, h->lay);
+  b += h->lay.field;
+  h->S = field_at(b, h->lay);
+  b += h->lay.field;
+  h->tw = (float2*)b;
+  b += h->lay.tw;
+  h->off = (float*)b;
+  b += h->lay.off;
+  h->red = (double*)b;
+  b += h->lay.red;
+  h->partials = (double*)b;
+  b += h->lay.partials;
+  h->stage = b;
+
+  // twiddles exp(-2 pi i m / N) and node offsets from the observer, computed in float64
+  const int n = h->n;
+  std::vector<float2> tw(n);
+  for (int m = 0; m < n; ++m) {
+    const double ang = -2.0 * M_PI * (double)m / (double)n;
+    tw[m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+  }
+  std::vector<float> off(3 * n);
+  const double H = h->L / n;
+  for (int a = 0; a < 3; ++a)
+    for (int i = 0; i < n; ++i) off[a * n + i] = (float)((double)i * H - p->observer[a]);
+  recon_status rs = RECON_OK;
+  do {
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(h->tw, tw.data(), n * sizeof(float2), cudaMemcpyHostToDevice, h->st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(h->off, off.data(), 3 * n * sizeof(float), cudaMemcpyHostToDevice, h->st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(h->red, 0, h->lay.red, h->st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(h->st)) != cudaSuccess) {
+      h->err = cudaGetErrorString(e);
+      rs = RECON_ERR_CUDA;
+    }
+  } while (0);
+  if (rs != RECON_OK) {
+    if (h->own_ws) cudaFree(h->ws);
+    delete h;
+    return rs;
+  }
+  Geometry& g = h->geo;
+  g.n = n;
+  g.kf = (float)(2.0 * M_PI / h->L);
+  g.inv_n3 = (float)(1.0 / ((double)n * n * n));
+  g.los_mode = p->los_mode;
+  if (p->los_mode == RECON_LOS_FIXED) {
+    const double q = std::sqrt(p->observer[0] * p->observer[0] + p->observer[1] * p->observer[1] +
+                               p->observer[2] * p->observer[2]);
+    g.los = make_float3((float)(p->observer[0] / q), (float)(p->observer[1] / q), (float)(p->observer[2] / q));
+  } else {
+    g.los = make_float3(0.f, 0.f, 0.f);
+  }
+  g.off = h->off;
+  *out = h;
+  return RECON_OK;
+}
+
+recon_status recon_set_timing(recon_handle* h, int enable) {
+  if (!h) return RECON_ERR_INVALID_ARG;
+  h->timing = enable ? 1 : 0;
+  return RECON_OK;
+}
+
+recon_status recon_get_timing(recon_handle* h, int kind, double* total_ms, int64_t* launches,
+                              double* alg_bytes) {
+  if (!h || kind < 0 || kind >= RECON_K_COUNT) return RECON_ERR_INVALID_ARG;
+  RG_CUDA(drain_timing(h));
+  if (total_ms) *total_ms = h->ms[kind];
+  if (launches) *launches = h->launches[kind];
+  if (alg_bytes) *alg_bytes = h->bytes[kind];
+  return RECON_OK;
+}
+
+recon_status recon_reset_timing(recon_handle* h) {
+  if (!h) return RECON_ERR_INVALID_ARG;
+  RG_CUDA(drain_timing(h));
+  for (int k = 0; k < RECON_K_COUNT; ++k) {
+    h->ms[k] = 0.0;
+    h->bytes[k] = 0.0;
+    h->launches[k] = 0;
+  }
+  return RECON_OK;
+}
+
+recon_status recon_destroy(recon_handle* h) {
+  if (!h) return RECON_OK;
+  drain_timing(h);
+  if (h->own_ws && h->ws) {
+    cudaStreamSynchronize(h->st);
+    cudaFree(h->ws);
+  }
+  delete h;
+  return RECON_OK;
+}
+
+recon_status recon_deposit(recon_handle* h, const recon_catalog* gal, const recon_catalog* ran) {
+  if (!h) return RECON_ERR_INVALID_ARG;
+  RG_TRY(check_catalog(gal));
+  const bool uniform = h->p.mean_density_mode == RECON_MEAN_UNIFORM;
+  if (gal->n == 0) return RECON_ERR_INVALID_ARG;
+  if (!uniform) {
+    if (!ran) return RECON_ERR_INVALID_ARG;
+    RG_TRY(check_catalog(ran));
+    if (ran->n == 0) return RECON_ERR_INVALID_ARG;
+  }
+  const size_t bytes = (size_t)h->n * h->n * h->n * sizeof(float);
+  RG_CUDA(cudaMemsetAsync(h->red, 0, h->lay.red, h->st));
+  RG_CUDA(cudaMemsetAsync(h->V[0].M, 0, bytes, h->st));
+  RG_TRY(deposit_one(h, gal, reinterpret_cast<float*>(h->V[0].M), RED_SUM_WG));
+  if (!uniform) {
+    RG_CUDA(cudaMemsetAsync(h->V[1].M, 0, bytes, h->st));
+    RG_TRY(deposit_one(h, ran, reinterpret_cast<float*>(h->V[1].M), RED_SUM_WR));
+  }
+  h->state = ST_DEPOSITED;
+  h->delta_real_valid = 0;
+  h->d_is_k = 0;
+  return RECON_OK;
+}
+
+recon_status recon_smooth(recon_handle* h) {
+  if (!h) return RECON_ERR_INVALID_ARG;
+  if (h->state != ST_DEPOSITED) return RECON_ERR_STATE;
+  const bool uniform = h->p.mean_density_mode == RECON_MEAN_UNIFORM;
+  const int nc = uniform ? 1 : 2;
+  {
+    ZArgs a = zargs(h);
+    a.f[0] = h->V[0];
+    a.f[1] = h->V[1];
+    RG_TRY(run_z(h, Z_FWD, nc, a));
+  }
+  RG_TRY(ypass(h, S_FWD, nc, h->V));
+  {
+    SArgs a = sargs(h);
+    a.f[0] = h->V[0];
+    a.f[1] = h->V[1];
+    RG_TRY(run_s(h, S_SMOOTH, nc, AX_X, a));
+  }
+  RG_TRY(ypass(h, S_INV, nc, h->V));
+  {
+    ZArgs a = zargs(h);
+    a.f[0] = h->V[0];
+    a.f[1] = h->V[1];
+    a.stats = !uniform;
+    RG_TRY(run_z(h, Z_INV, nc, a));
+    if (!uniform) RG_TRY(finalize(h, h->mk->z_blocks, 2, RED_SUM_RPOS, 0));
+  }
+  {
+    ZArgs a = zargs(h);
+    a.f[0] = h->V[0];
+    a.f[1] = h->V[1];
+    a.dout = h->D;
+    a.delta_real = reinterpret_cast<float*>(h->V[2].M);
+    RG_TRY(run_z(h, Z_DELTA, 2, a));
+    RG_TRY(finalize(h, h->mk->z_blocks, 2, RED_SUM_LOG, 0));
+  }
+  RG_TRY(ypass(h, S_FWD, 1, &h->D));
+  h->state = ST_SMOOTHED;
+  h->d_is_k = 0;
+  h->delta_real_valid = 1;
+  return RECON_OK;
+}
+
+recon_status recon_iterate(recon_handle* h, int start, double tol, int max_iter, int* n_iter, double* rel_change) {
+  if (!h) return RECON_ERR_INVALID_ARG;
+  if (h->state < ST_SMOOTHED) return RECON_ERR_STATE;
+  if (max_iter < 1 || !(tol >= 0) || start < RECON_START_PLAIN || start > RECON_START_FFTA)
+    return RECON_ERR_INVALID_ARG;
+  const double beta = h->p.f / h->p.b;
+  const float coef0 = (float)(1.0 - start_coefficient(start, beta));
+  h->trace.clear();
+  h->delta_real_valid = 0;
+  // start: delta(k), S_-1 = delta/b, Psi_s = Z[delta/b], P_0 = (1 - c)(Psi_s.r) r
+  {
+    SArgs a = sargs(h);
+    for (int q = 0; q < 3; ++q) a.f[q] = h->V[q];
+    a.d_is_k = h->d_is_k;
+    RG_TRY(run_s(h, S_DELTA, 1, AX_X, a));
+    h->d_is_k = 1;
+  }
+  RG_TRY(ypass(h, S_INV, 3, h->V));
+  ZArgs za = zargs(h);
+  for (int q = 0; q < 3; ++q) za.f[q] = h->V[q];
+  za.coef = coef0;
+  RG_TRY(run_z(h, Z_PROJ, 3, za));
+  za.coef = 1.f;
+  RG_TRY(ypass(h, S_FWD, 3, h->V));
+
+  SArgs ia = sargs(h);
+  for (int q = 0; q < 3; ++q) ia.f[q] = h->V[q];
+  double host_norm[2] = {0, 0};
+  double rel = 0.0;
+  int it = 0;
+  recon_status result = RECON_OK;
+  while (true) {
+    RG_TRY(run_s(h, S_ITER, 3, AX_X, ia));
+    RG_TRY(finalize(h, h->mk->s_blocks, 2, RED_NORM_D2, 0));
+    RG_CUDA(cudaMemcpyAsync(host_norm, h->red + RED_NORM_D2, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    cudaEvent_t ev;
+    RG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    RG_CUDA(cudaEventRecord(ev, h->st));
+    RG_TRY(ypass(h, S_INV, 3, h->V));
+    cudaError_t es = cudaEventSynchronize(ev);
+    cudaEventDestroy(ev);
+    RG_CUDA(es);
+    ++it;
+    if (!std::isfinite(host_norm[0]) || !std::isfinite(host_norm[1])) {
+      h->state = ST_SMOOTHED;
+      result = RECON_ERR_NONFINITE;
+      break;
+    }
+    rel = host_norm[1] > 0 ? std::sqrt(host_norm[0] / host_norm[1]) : 0.0;
+    h->trace.push_back(rel);
+    const bool done = (it >= 2 && rel < tol) || it >= max_iter;
+    if (done) {
+      RG_TRY(run_z(h, Z_FINAL, 3, za));
+      break;
+    }
+    RG_TRY(run_z(h, Z_PROJ, 3, za));
+    RG_TRY(ypass(h, S_FWD, 3, h->V));
+  }
+  if (result == RECON_OK) {
+    h->state = ST_ITERATED;
+    if (tol > 0 && rel >= tol) result = RECON_ERR_NOT_CONVERGED;
+  }
+  if (n_iter) *n_iter = it;
+  if (rel_change) *rel_change = rel;
+  return result;
+}
+
+recon_status recon_get_trace(recon_handle* h, double* rel, int cap, int* n) {
+  if (!h || (cap > 0 && !rel)) return RECON_ERR_INVALID_ARG;
+  const int m = (int)h->trace.size();
+  for (int i = 0; i < m && i < cap; ++i) rel[i] = h->trace[i];
+  if (n) *n = m;
+  return RECON_OK;
+}
+
+recon_status recon_shift(recon_handle* h, const recon_catalog* cat, int is_galaxy, float* shift_out,
+                         double* pos_out, int out_on_device) {
+  if (!h) return RECON_ERR_INVALID_ARG;
+  RG_TRY(check_catalog(cat));
+  if (cat->n > 0 && !shift_out) return RECON_ERR_INVALID_ARG;
+  if (h->state != ST_ITERATED) return RECON_ERR_STATE;
+  ShiftArgs a{};
+  for (int q = 0; q < 3; ++q) a.psi[q] = reinterpret_cast<const float*>(h->V[q].M);
+  a.n = h->n;
+  a.scale = (double)h->n / h->L;
+  a.L = h->L;
+  a.is_galaxy = is_galaxy ? 1 : 0;
+  a.f = (float)h->p.f;
+  a.los_mode = h->p.los_mode;
+  a.los = h->geo.los;
+  for (int q = 0; q < 3; ++q) a.obs[q] = h->p.observer[q];
+  a.periodic = h->p.periodic;
+  const size_t es = elem_size(cat->dtype);
+  if (cat->on_device && out_on_device) {
+    a.shift = shift_out;
+    a.pos_out = pos_out;
+    RG_CUDA(timed(h, RECON_K_SHIFT, (double)cat->n * (3 * es + 12 + (pos_out ? 24 : 0)),
+                  [&] { return launch_shift(cat->pos, cat->dtype, cat->n, a, h->st); }));
+    return RECON_OK;
+  }
+  char* spos = h->stage;
+  float* sshift = reinterpret_cast<float*>(h->stage + kStageParticles * 28);
+  double* spout = reinterpret_cast<double*>(h->stage + kStageParticles * 40);
+  for (long long p0 = 0; p0 < cat->n; p0 += kStageParticles) {
+    const long long m = (cat->n - p0 < kStageParticles) ? cat->n - p0 : kStageParticles;
+    const void* pin = (const char*)cat->pos + (size_t)p0 * 3 * es;
+    if (!cat->on_device) {
+      RG_CUDA(cudaMemcpyAsync(spos, pin, (size_t)m * 3 * es, cudaMemcpyHostToDevice, h->st));
+      pin = spos;
+    }
+    a.shift = out_on_device ? shift_out + 3 * p0 : sshift;
+    a.pos_out = pos_out ? (out_on_device ? pos_out + 3 * p0 : spout) : nullptr;
+    RG_CUDA(timed(h, RECON_K_SHIFT, (double)m * (3 * es + 12 + (pos_out ? 24 : 0)),
+                  [&] { return launch_shift(pin, cat->dtype, m, a, h->st); }));
+    if (!out_on_device) {
+      RG_CUDA(cudaMemcpyAsync(shift_out + 3 * p0, sshift, (size_t)m * 3 * sizeof(float), cudaMemcpyDeviceToHost, h->st));
+      if (pos_out)
+        RG_CUDA(cudaMemcpyAsync(pos_out + 3 * p0, spout, (size_t)m * 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    }
+  }
+  if (!out_on_device) RG_CUDA(cudaStreamSynchronize(h->st));
+  return RECON_OK;
+}
+
+recon_status recon_get_psi(recon_handle* h, float* out, int out_on_device) {
+  return recon_get_field(h, RECON_FIELD_PSI, out, out_on_device);
+}
+
+recon_status recon_get_field(recon_handle* h, int which, float* out, int out_on_device) {
+  if (!h || !out) return RECON_ERR_INVALID_ARG;
+  const size_t nr = (size_t)h->n * h->n * h->n;
+  const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  switch (which) {
+    case RECON_FIELD_RHO_G:
+    case RECON_FIELD_RHO_R:
+      if (h->state != ST_DEPOSITED) return RECON_ERR_STATE;
+      if (which == RECON_FIELD_RHO_R && h->p.mean_density_mode == RECON_MEAN_UNIFORM) return RECON_ERR_INVALID_ARG;
+      RG_CUDA(cudaMemcpyAsync(out, h->V[which == RECON_FIELD_RHO_G ? 0 : 1].M, nr * sizeof(float), kind, h->st));
+      break;
+    case RECON_FIELD_DELTA: {
+      if (!h->delta_real_valid) return RECON_ERR_STATE;
+      RG_CUDA(cudaMemcpyAsync(out, h->V[2].M, nr * sizeof(float), kind, h->st));
+      if (h->p.lognormal) {
+        double s = 0;
+        RG_CUDA(cudaMemcpyAsync(&s, h->red + RED_SUM_LOG, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        RG_CUDA(cudaStreamSynchronize(h->st));
+        const float c = (float)(-s / (double)nr);
+        if (out_on_device) {
+          RG_CUDA(timed(h, RECON_K_OTHER, 8.0 * nr, [&] { return launch_add_scalar(out, nr, c, h->st); }));
+        } else {
+          for (size_t i = 0; i < nr; ++i) out[i] += c;
+        }
+      }
+      break;
+    }
+    case RECON_FIELD_DELTA_K:
+      if (!h->d_is_k || h->state < ST_SMOOTHED) return RECON_ERR_STATE;
+      RG_TRY(export_half(h, h->D, out));
+      break;
+    case RECON_FIELD_PSI:
+      if (h->state != ST_ITERATED) return RECON_ERR_STATE;
+      for (int q = 0; q < 3; ++q)
+        RG_CUDA(cudaMemcpyAsync(out + q * nr, h->V[q].M, nr * sizeof(float), kind, h->st));
+      break;
+    default:
+      return RECON_ERR_INVALID_ARG;
+  }
+  if (!out_on_device) RG_CUDA(cudaStreamSynchronize(h->st));
+  return RECON_OK;
+}
+
+recon_status recon_get_scalars(recon_handle* h, double out[8]) {
+  if (!h || !out) return RECON_ERR_INVALID_ARG;
+  double r[RED_COUNT];
+  RG_CUDA(cudaMemcpyAsync(r, h->red, sizeof(r), cudaMemcpyDeviceToHost, h->st));
+  RG_CUDA(cudaStreamSynchronize(h->st));
+  const double nr = (double)h->n * h->n * h->n;
+  const bool uniform = h->p.mean_density_mode == RECON_MEAN_UNIFORM;
+  out[0] = r[RED_SUM_WG];
+  out[1] = r[RED_SUM_WR];
+  out[2] = uniform ? r[RED_SUM_WG] / nr : r[RED_SUM_WG] / r[RED_SUM_WR];
+  out[3] = uniform ? 0.0 : h->p.mask_frac * r[RED_SUM_RPOS] / r[RED_CNT_RPOS];
+  out[4] = h->p.lognormal ? -r[RED_SUM_LOG] / nr : 0.0;
+  out[5] = uniform ? nr : r[RED_CNT_MASK];
+  out[6] = r[RED_NORM_D2];
+  out[7] = r[RED_NORM_S2];
+  return RECON_OK;
+}
+
+recon_status recon_fft_r2c(recon_handle* h, const float* in_real, float* out_half) {
+  if (!h || !in_real || !out_half) return RECON_ERR_INVALID_ARG;
+  const size_t nr = (size_t)h->n * h->n * h->n;
+  h->state = ST_CREATED;
+  h->d_is_k = 0;
+  h->delta_real_valid = 0;
+  RG_CUDA(cudaMemcpyAsync(h->V[0].M, in_real, nr * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
+  ZArgs a = zargs(h);
+  a.f[0] = h->V[0];
+  RG_TRY(run_z(h, Z_FWD, 1, a));
+  RG_TRY(ypass(h, S_FWD, 1, h->V));
+  SArgs s = sargs(h);
+  s.f[0] = h->V[0];
+  RG_TRY(run_s(h, S_FWD, 1, AX_X, s));
+  RG_TRY(export_half(h, h->V[0], out_half));
+  return RECON_OK;
+}
+
+recon_status recon_fft_c2r(recon_handle* h, const float* in_half, float* out_real) {
+  if (!h || !in_half || !out_real) return RECON_ERR_INVALID_ARG;
+  const size_t nr = (size_t)h->n * h->n * h->n;
+  h->state = ST_CREATED;
+  h->d_is_k = 0;
+  h->delta_real_valid = 0;
+  RG_TRY(import_half(h, in_half, h->V[0]));
+  SArgs s = sargs(h);
+  s.f[0] = h->V[0];
+  RG_TRY(run_s(h, S_INV, 1, AX_X, s));
+  RG_TRY(ypass(h, S_INV, 1, h->V));
+  ZArgs a = zargs(h);
+  a.f[0] = h->V[0];
+  RG_TRY(run_z(h, Z_INV, 1, a));
+  RG_CUDA(cudaMemcpyAsync(out_real, h->V[0].M, nr * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
+  return RECON_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+// types.h: argument blocks shared by the host orchestration and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace rg {
+
+// A field on the mesh.  In configuration space M holds N^3 float32 [ix][iy][iz].  On the r2c half
+// grid M holds the kz = 0..N/2-1 planes as N*N*(N/2) float2 [kx][ky][kz] (same bytes as the real
+// field, so every row stays 16-byte aligned) and Q holds the kz = N/2 (Nyquist) plane, N*N float2
+// [kx][ky].
+struct Field {
+  float2* M;
+  float2* Q;
+};
+
+// Slots of the float64 reduction block kept on the device.
+enum RedSlot {
+  RED_SUM_WG = 0,      // sum of galaxy weights
+  RED_SUM_WR = 1,      // sum of random weights
+  RED_SUM_RPOS = 2,    // sum of smoothed random density over nodes where it is > 0
+  RED_CNT_RPOS = 3,    // number of such nodes
+  RED_SUM_LOG = 4,     // sum over nodes of ln(max(1 + delta, floor)) (lognormal mode)
+  RED_CNT_MASK = 5,    // number of nodes inside the survey mask
+  RED_NORM_D2 = 6,     // Parseval sum for |dPsi|^2 of the last iteration
+  RED_NORM_S2 = 7,     // Parseval sum for |Psi|^2 of the last iteration
+  RED_COUNT = 8
+};
+
+struct Geometry {
+  int n;                  // mesh side
+  float kf;               // 2 pi / L
+  float inv_n3;           // 1 / N^3
+  int los_mode;           // 0 radial, 1 fixed
+  float3 los;             // fixed LOS unit vector
+  const float* off;       // 3 N node offsets from the observer: x_i - o_a, per axis a (radial)
+};
+
+enum ZMode { Z_FWD = 0, Z_INV = 1, Z_DELTA = 2, Z_PROJ = 3, Z_FINAL = 4 };
+enum SMode { S_FWD = 0, S_INV = 1, S_SMOOTH = 2, S_DELTA = 3, S_ITER = 4 };
+enum Axis { AX_X = 0, AX_Y = 1 };
+
+struct ZArgs {
+  Field f[3];             // fields transformed in place
+  Geometry g;
+  const float2* tw;       // exp(-2 pi i m / N), m < N
+  double* partials;       // per-block reduction partials (4 per block)
+  const double* red;      // reduction block (read by Z_DELTA)
+  int stats;              // Z_INV: accumulate positive-part statistics of f[1]
+  float coef;             // Z_PROJ: (1 - c) multiplier of the projection
+  // Z_DELTA
+  Field dout;             // delta on the (z-transformed) half grid
+  float* delta_real;      // optional real copy of delta
+  float mask_frac;
+  int uniform;            // delta from rho_bar = sum w_g / N^3
+  int lognormal;
+};
+
+struct SArgs {
+  Field f[3];             // fields transformed in place
+  Geometry g;
+  const float2* tw;       // exp(-2 pi i m / N), m < N
+  double* partials;       // per-block partials (2 per block, S_ITER)
+  const double* red;      // reduction block (S_DELTA reads the lognormal sum)
+  Field dk;               // delta: partially transformed (S_DELTA input) / k-space (S_ITER)
+  Field sbuf;             // stored source S of the previous iteration
+  float inv_b;            // 1 / b
+  float beta;             // f / b
+  float half_R2;          // R^2 / 2 (S_SMOOTH)
+  int d_is_k;             // S_DELTA: dk is already fully transformed
+  int lognormal;          // S_DELTA: subtract the lognormal constant at k = 0
+};
+
+// Kernels of one mesh size (one table per supported N).
+struct MeshKernels {
+  int n;
+  int z_blocks;           // CTAs of a Z pass
+  int s_blocks;           // CTAs of a strided pass
+  cudaError_t (*zpass)(int mode, int nc, const ZArgs& a, cudaStream_t st);
+  cudaError_t (*spass)(int mode, int nc, int axis, const SArgs& a, cudaStream_t st);
+};
+
+const MeshKernels* mesh_kernels(int n);
+
+}  // namespace rg

@@ -1,0 +1,199 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on seeded synthetic inputs.
+
+Tolerances (stated by the method's precision policy): relative L2 error of Psi <= 1e-5 and maximum
+particle-shift error <= 1e-4 Mpc/h against the FP64 oracle.  Intermediate fields are checked at the
+float32 rounding level they are computed at.
+"""
+import numpy as np
+import pytest
+
+from oracle import recon_oracle as O
+from paper_1504_02591_gb300 import mocks
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PSI_TOL = 1e-5
+SHIFT_TOL = 1e-4
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
+
+
+@pytest.fixture(scope="module")
+def B(lib):
+    from paper_1504_02591_gb300 import binding
+    return binding
+
+
+# ------------------------------------------------------------------------------------------------
+# Spectral engine alone
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [32, 48, 64, 96, 128])
+def test_fft_r2c_c2r_vs_oracle(B, n):
+    rng = np.random.default_rng(100 + n)
+    x = rng.standard_normal((n, n, n))
+    r = B.Recon(n, 1000.0, 2.0, 0.7, 10.0, (0, 0, 0), uniform=True)
+    X = r.fft_r2c(torch.from_numpy(x.astype(np.float32))).cpu().numpy().astype(np.complex128)
+    want = O.fft3(x.astype(np.float32).astype(np.float64))
+    assert np.abs(X - want).max() <= 2e-6 * np.abs(want).max()
+    assert rel_l2(X.view(np.float64), want.view(np.float64)) <= 1e-6
+    # c2r of the exact spectrum is N^3 times the inverse transform
+    y = r.fft_c2r(torch.from_numpy(want.astype(np.complex64))).cpu().numpy()
+    assert rel_l2(y / n ** 3, x.astype(np.float32)) <= 1e-6
+    r.close()
+
+
+# ------------------------------------------------------------------------------------------------
+# Whole pipeline, small periodic box (64^3, 2e5 galaxies, 2e6 randoms, radial LOS)
+# ------------------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def periodic_mock():
+    return mocks.small_periodic()
+
+
+@pytest.fixture(scope="module")
+def periodic_oracle(periodic_mock):
+    m = periodic_mock
+    out = {}
+    for start in (O.START_PLAIN, O.START_FFTA):
+        out[start] = O.reconstruct(m.params(), m.galaxies.pos, None, m.randoms.pos, None,
+                                   start=start, tol=0.0, max_iter=6)
+    return out
+
+
+@pytest.mark.parametrize("start", [0, 2])
+def test_periodic_pipeline_vs_oracle(B, periodic_mock, periodic_oracle, start):
+    m = periodic_mock
+    ref = periodic_oracle[start]
+    r = B.Recon.from_mock(m)
+    gal = torch.from_numpy(m.galaxies.pos).cuda()
+    ran = torch.from_numpy(m.randoms.pos).cuda()
+    r.deposit(gal, None, ran, None)
+    rho_g = r.get_field(B.FIELD_RHO_G).cpu().numpy()
+    assert rel_l2(rho_g, ref["rho_g"]) < 1e-6
+    assert abs(rho_g.astype(np.float64).sum() - len(m.galaxies.pos)) < 1e-5 * len(m.galaxies.pos)
+    r.smooth()
+    sc = r.scalars()
+    assert sc["sum_wg"] == len(m.galaxies.pos) and sc["sum_wr"] == len(m.randoms.pos)
+    assert sc["threshold"] == pytest.approx(ref["threshold"], rel=1e-5)
+    delta = r.get_field(B.FIELD_DELTA).cpu().numpy()
+    assert rel_l2(delta, ref["delta"]) < 2e-6
+    n_it, rel, st = r.iterate(start, 0.0, 6)
+    assert n_it == 6 and st == B.OK
+    tr = np.array(r.trace())
+    assert np.allclose(tr, ref["rel"], rtol=1e-3, atol=0)
+    psi = r.get_psi().cpu().numpy()
+    assert rel_l2(psi, ref["psi"]) <= PSI_TOL
+    sg = r.shift(gal, True).cpu().numpy()
+    sr = r.shift(ran, False).cpu().numpy()
+    assert np.abs(sg - ref["shift_g"]).max() <= SHIFT_TOL
+    assert np.abs(sr - ref["shift_r"]).max() <= SHIFT_TOL
+    # host-memory catalogue and outputs give the same shifts and wrapped positions
+    sh_h, po_h = r.shift(m.galaxies.pos, True, want_pos=True)
+    assert np.array_equal(sh_h, sg)
+    assert np.abs(po_h - ref["pos_g"]).max() <= SHIFT_TOL
+    r.close()
+
+
+def test_delta_k_export_matches_oracle(B, periodic_mock, periodic_oracle):
+    m = periodic_mock
+    r = B.Recon.from_mock(m)
+    r.run(m.galaxies.pos, m.randoms.pos, start=0, tol=0, max_iter=2)
+    dk = r.get_field(B.FIELD_DELTA_K).cpu().numpy()
+    want = O.fft3(periodic_oracle[0]["delta"])
+    assert rel_l2(dk.view(np.float32).astype(np.float64), want.view(np.float64)) < 3e-6
+    r.close()
+
+
+# ------------------------------------------------------------------------------------------------
+# Survey shell with mask (the 512^3 survey shape scaled to 128^3 and 6e4 galaxies)
+# ------------------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def shell_case():
+    m = mocks.survey_shell_512(n_gal=60_000, ran_ratio=50, n_mesh=128)
+    ref = O.reconstruct(m.params(), m.galaxies.pos, None, m.randoms.pos, None,
+                        start=O.START_FFTA, tol=1e-6, max_iter=40)
+    return m, ref
+
+
+def test_shell_survey_converged_vs_oracle(B, shell_case):
+    m, ref = shell_case
+    r = B.Recon.from_mock(m)
+    n_it, rel, st = r.run(torch.from_numpy(m.galaxies.pos).cuda(), torch.from_numpy(m.randoms.pos).cuda(),
+                          start=2, tol=1e-6, max_iter=40)
+    assert st == B.OK and rel < 1e-6
+    assert abs(n_it - ref["n_iter"]) <= 1
+    sc = r.scalars()
+    # the mask is a float32 decision on the smoothed randoms: nodes may differ only at the threshold
+    assert abs(sc["n_mask"] - ref["mask"].sum()) <= 1e-4 * ref["mask"].sum() + 5
+    psi = r.get_psi().cpu().numpy()
+    assert rel_l2(psi, ref["psi"]) <= PSI_TOL
+    sg = r.shift(torch.from_numpy(m.galaxies.pos).cuda(), True).cpu().numpy()
+    assert np.abs(sg - ref["shift_g"]).max() <= SHIFT_TOL
+    sr = r.shift(torch.from_numpy(m.randoms.pos).cuda(), False).cpu().numpy()
+    assert np.abs(sr - ref["shift_r"]).max() <= SHIFT_TOL
+    r.close()
+
+
+# ------------------------------------------------------------------------------------------------
+# Uniform mean density, fixed LOS and lognormal (the large periodic run's options, at 64^3)
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("los_mode,lognormal", [(1, False), (0, True), (1, True)])
+def test_uniform_options_vs_oracle(B, los_mode, lognormal):
+    obs = (1.0, 0.0, 0.0) if los_mode == 1 else (-1000.0, 1250.0, 1250.0)
+    m = mocks.periodic_box(2500.0, 64, 150_000, 0, 1.0, 0.74, 40.0, obs, 20, 21, 22, ng=64,
+                           los_mode=los_mode, uniform=True)
+    p = m.params(lognormal=lognormal)
+    ref = O.reconstruct(p, m.galaxies.pos, None, None, None, start=O.START_FFTA, tol=0.0, max_iter=6)
+    r = B.Recon.from_mock(m, lognormal=lognormal)
+    r.run(torch.from_numpy(m.galaxies.pos).cuda(), None, start=2, tol=0.0, max_iter=6)
+    psi = r.get_psi().cpu().numpy()
+    assert rel_l2(psi, ref["psi"]) <= PSI_TOL
+    sg = r.shift(torch.from_numpy(m.galaxies.pos).cuda(), True).cpu().numpy()
+    assert np.abs(sg - ref["shift_g"]).max() <= SHIFT_TOL
+    if lognormal:
+        assert r.scalars()["lognormal_C"] == pytest.approx(ref["lognormal_C"], rel=1e-4)
+    r.close()
+
+
+# ------------------------------------------------------------------------------------------------
+# Edge cases and errors
+# ------------------------------------------------------------------------------------------------
+def test_state_and_argument_errors(B):
+    r = B.Recon(32, 500.0, 2.0, 0.7, 10.0, (600.0, 250.0, 250.0))
+    with pytest.raises(B.ReconError) as e:
+        r.smooth()
+    assert e.value.status == B.ERR_STATE
+    with pytest.raises(B.ReconError) as e:
+        r.deposit(np.zeros((0, 3)), None, np.random.default_rng(0).uniform(0, 500, (100, 3)))
+    assert e.value.status == B.ERR_INVALID_ARG
+    with pytest.raises(B.ReconError) as e:
+        r.deposit(np.random.default_rng(0).uniform(0, 500, (100, 3)), None, None)
+    assert e.value.status == B.ERR_INVALID_ARG
+    r.close()
+
+
+def test_not_converged_reports_status(B):
+    m = mocks.small_periodic(n_gal=20_000, n_ran=200_000, n_mesh=32)
+    r = B.Recon.from_mock(m)
+    n_it, rel, st = r.run(m.galaxies.pos, m.randoms.pos, start=0, tol=1e-12, max_iter=3)
+    assert n_it == 3 and st == B.ERR_NOT_CONVERGED and rel > 1e-12
+    r.close()
+
+
+def test_ragged_particle_counts(B):
+    """Counts that are not multiples of the block size or the staging chunk."""
+    rng = np.random.default_rng(5)
+    gal = rng.uniform(0, 500.0, (1, 3))
+    ran = rng.uniform(0, 500.0, (2_097_152 + 37, 3))
+    r = B.Recon(32, 500.0, 2.0, 0.7, 20.0, (250.0, 250.0, 250.0), periodic=True)
+    r.deposit(gal, None, ran, None)
+    rho_r = r.get_field(B.FIELD_RHO_R).cpu().numpy()
+    assert abs(rho_r.astype(np.float64).sum() - len(ran)) <= 1e-5 * len(ran)
+    want = O.cic_deposit(ran, None, 32, 500.0)
+    assert rel_l2(rho_r, want) < 1e-6
+    r.close()
