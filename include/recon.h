@@ -81,7 +81,8 @@ typedef struct recon_params {
   double observer[3];      /* radial: observer position (Mpc/h); fixed: LOS direction vector   */
   int periodic;            /* 1: shifted positions wrap modulo L; 0: survey (no wrap)          */
   double mask_frac;        /* survey mask: keep nodes whose smoothed random density exceeds
-                              mask_frac x its mean over nodes where it is positive (0.01)      */
+                              mask_frac x sum w_r / (number of nodes that received random
+                              mass in the deposit), i.e. of the survey's mean density (0.01)   */
   int lognormal;           /* 1: delta -> ln(max(1+delta, 1e-6)) - <ln(...)> (Eq. logdelta)    */
   int mean_density_mode;   /* RECON_MEAN_RANDOMS (delta from randoms) or RECON_MEAN_UNIFORM    */
 } recon_params;

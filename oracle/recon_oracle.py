@@ -124,16 +124,17 @@ def smooth(field, R: float, L: float):
     return ifft3(fft3(field) * np.exp(-0.5 * k2 * R * R), n)
 
 
-def overdensity_randoms(rho_g_s, rho_r_s, sum_wg: float, sum_wr: float, mask_frac: float):
+def overdensity_randoms(rho_g_s, rho_r_s, sum_wg: float, sum_wr: float, mask_frac: float,
+                        n_touched: int):
     """delta = rho_g,s / (alpha rho_r,s) - 1 inside the survey mask, 0 outside (Sec. 3.2).
 
     alpha = sum w_g / sum w_r.  The binary mask keeps nodes where the smoothed random density exceeds
-    mask_frac times its mean over nodes with positive smoothed random density.
+    mask_frac times the mean random density of the survey, sum w_r / n_touched, where n_touched is
+    the number of nodes that received random mass in the (unsmoothed) deposit.
     Returns (delta, mask, alpha, threshold).
     """
     alpha = sum_wg / sum_wr
-    pos = rho_r_s > 0
-    thr = mask_frac * rho_r_s[pos].mean()
+    thr = mask_frac * sum_wr / n_touched
     mask = rho_r_s > thr
     delta = np.zeros_like(rho_g_s)
     delta[mask] = rho_g_s[mask] / (alpha * rho_r_s[mask]) - 1.0
@@ -313,7 +314,8 @@ def reconstruct(params: dict, gal_pos, gal_w=None, ran_pos=None, ran_w=None,
         rho_r_s = smooth(rho_r, params["R"], L)
         out["rho_r_s"] = rho_r_s
         delta, mask, alpha, thr = overdensity_randoms(rho_g_s, rho_r_s, wg.sum(), wr.sum(),
-                                                      params.get("mask_frac", 0.01))
+                                                      params.get("mask_frac", 0.01),
+                                                      int(np.count_nonzero(rho_r > 0)))
         out.update(mask=mask, alpha=alpha, threshold=thr)
     out["rho_g_s"] = rho_g_s
     if params.get("lognormal", False):

@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kZThreads) zpass_kernel(const ZArgs a) {
       const double* red = a.red;
       const float inv_alpha = a.uniform ? (float)((double)N * N * N / red[RED_SUM_WG])
                                         : (float)(red[RED_SUM_WR] / red[RED_SUM_WG]);
-      const float thr = a.uniform ? 0.f : (float)(a.mask_frac * red[RED_SUM_RPOS] / red[RED_CNT_RPOS]);
+      const float thr = a.uniform ? 0.f : (float)(a.mask_frac * red[RED_SUM_WR] / red[RED_CNT_RPOS]);
       for (int e = threadIdx.x; e < ROWS * (L / 2); e += kZThreads) {
         const int row = e / (L / 2), m2 = e % (L / 2);
         const float4 g = reinterpret_cast<const float4*>(a.f[0].M + (row0 + row) * L)[m2];
@@ -176,6 +176,8 @@ __global__ void __launch_bounds__(kZThreads) zpass_kernel(const ZArgs a) {
         const int row = rem / (L / 2), m2 = rem % (L / 2);
         const float4 v = reinterpret_cast<const float4*>(a.f[q].M + (row0 + row) * L)[m2];
         const int col = q * ROWS + row;
+        if (a.stats && q == 1)  // nodes that received random mass
+          acc1 += (v.x > 0.f) + (v.y > 0.f) + (v.z > 0.f) + (v.w > 0.f);
         s[Lay::phys(2 * m2, col)] = make_float2(v.x, v.y);
         s[Lay::phys(2 * m2 + 1, col)] = make_float2(v.z, v.w);
       }
@@ -225,11 +227,6 @@ __global__ void __launch_bounds__(kZThreads) zpass_kernel(const ZArgs a) {
       const int row = rem / (L / 2), m2 = rem % (L / 2);
       const int col = q * ROWS + row;
       const float2 v0 = s[Lay::phys(2 * m2, col)], v1 = s[Lay::phys(2 * m2 + 1, col)];
-      if (MODE == Z_INV && a.stats && q == 1) {
-        acc0 += (v0.x > 0.f ? v0.x : 0.f) + (v0.y > 0.f ? v0.y : 0.f) + (v1.x > 0.f ? v1.x : 0.f) +
-                (v1.y > 0.f ? v1.y : 0.f);
-        acc1 += (v0.x > 0.f) + (v0.y > 0.f) + (v1.x > 0.f) + (v1.y > 0.f);
-      }
       reinterpret_cast<float4*>(a.f[q].M + (row0 + row) * L)[m2] = make_float4(v0.x, v0.y, v1.x, v1.y);
     }
   } else {
@@ -251,7 +248,7 @@ __global__ void __launch_bounds__(kZThreads) zpass_kernel(const ZArgs a) {
     }
   }
 
-  const bool want_red = (MODE == Z_DELTA) || (MODE == Z_INV && a.stats);
+  const bool want_red = (MODE == Z_DELTA) || (MODE == Z_FWD && a.stats);
   if (want_red) {
     double r0 = block_sum((double)acc0, red_sh);
     double r1 = block_sum((double)acc1, red_sh);

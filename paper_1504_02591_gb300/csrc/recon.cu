@@ -2,7 +2,8 @@
 //
 // Pipeline per reconstruction (Burden, Percival & Howlett 2015):
 //   deposit  CIC of galaxies and randoms -> rho_g, rho_r; sums of weights (float64)
-//   smooth   Z r2c | Y | X (x exp(-k^2 R^2/2)) | Y | Z c2r + mask statistics      (Sec. 3.1, 3.2)
+//   smooth   Z r2c + count of nodes with random mass | Y | X (x exp(-k^2 R^2/2)) | Y | Z c2r
+//                                                                                  (Sec. 3.1, 3.2)
 //            Z: delta = rho_g,s/(alpha rho_r,s) - 1 in the mask (+ lognormal) and its r2c | Y
 //   iterate  X: delta(k), S_-1 = delta/b, Psi_s = Z[delta/b] | Y | Z: P_0 = (1-c)(Psi_s.r)r | Y
 //            repeat: X: S_n = delta/b + beta i k.P_n, norms, Psi = i k S/k^2 | Y |
@@ -526,7 +527,9 @@ recon_status recon_smooth(recon_handle* h) {
     ZArgs a = zargs(h);
     a.f[0] = h->V[0];
     a.f[1] = h->V[1];
+    a.stats = !uniform;
     RG_TRY(run_z(h, Z_FWD, nc, a));
+    if (!uniform) RG_TRY(finalize(h, h->mk->z_blocks, 2, RED_SUM_RPOS, 0));
   }
   RG_TRY(ypass(h, S_FWD, nc, h->V));
   {
@@ -540,9 +543,7 @@ recon_status recon_smooth(recon_handle* h) {
     ZArgs a = zargs(h);
     a.f[0] = h->V[0];
     a.f[1] = h->V[1];
-    a.stats = !uniform;
     RG_TRY(run_z(h, Z_INV, nc, a));
-    if (!uniform) RG_TRY(finalize(h, h->mk->z_blocks, 2, RED_SUM_RPOS, 0));
   }
   {
     ZArgs a = zargs(h);
@@ -741,7 +742,7 @@ recon_status recon_get_scalars(recon_handle* h, double out[8]) {
   out[0] = r[RED_SUM_WG];
   out[1] = r[RED_SUM_WR];
   out[2] = uniform ? r[RED_SUM_WG] / nr : r[RED_SUM_WG] / r[RED_SUM_WR];
-  out[3] = uniform ? 0.0 : h->p.mask_frac * r[RED_SUM_RPOS] / r[RED_CNT_RPOS];
+  out[3] = uniform ? 0.0 : h->p.mask_frac * r[RED_SUM_WR] / r[RED_CNT_RPOS];
   out[4] = h->p.lognormal ? -r[RED_SUM_LOG] / nr : 0.0;
   out[5] = uniform ? nr : r[RED_CNT_MASK];
   out[6] = r[RED_NORM_D2];

@@ -19,8 +19,8 @@ struct Field {
 enum RedSlot {
   RED_SUM_WG = 0,      // sum of galaxy weights
   RED_SUM_WR = 1,      // sum of random weights
-  RED_SUM_RPOS = 2,    // sum of smoothed random density over nodes where it is > 0
-  RED_CNT_RPOS = 3,    // number of such nodes
+  RED_SUM_RPOS = 2,    // (unused) partner slot of RED_CNT_RPOS in the reduction
+  RED_CNT_RPOS = 3,    // number of nodes that received random mass in the deposit
   RED_SUM_LOG = 4,     // sum over nodes of ln(max(1 + delta, floor)) (lognormal mode)
   RED_CNT_MASK = 5,    // number of nodes inside the survey mask
   RED_NORM_D2 = 6,     // Parseval sum for |dPsi|^2 of the last iteration
@@ -47,7 +47,7 @@ struct ZArgs {
   const float2* tw;       // exp(-2 pi i m / N), m < N
   double* partials;       // per-block reduction partials (4 per block)
   const double* red;      // reduction block (read by Z_DELTA)
-  int stats;              // Z_INV: accumulate positive-part statistics of f[1]
+  int stats;              // Z_FWD: count the nodes of f[1] (unsmoothed randoms) that are > 0
   float coef;             // Z_PROJ: (1 - c) multiplier of the projection
   // Z_DELTA
   Field dout;             // delta on the (z-transformed) half grid

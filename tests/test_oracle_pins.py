@@ -230,10 +230,10 @@ def test_overdensity_zero_when_galaxies_trace_randoms():
     rng = np.random.default_rng(8)
     rr = rng.uniform(0.1, 2.0, (8, 8, 8))
     rr[0, 0, :4] = 0.0
-    d, mask, alpha, thr = O.overdensity_randoms(3.0 * rr, rr, 30.0, 10.0, 0.01)
+    d, mask, alpha, thr = O.overdensity_randoms(3.0 * rr, rr, 30.0, 10.0, 0.01, 500)
     assert alpha == 3.0 and not mask[0, 0, 0] and mask[4, 4, 4]
     assert np.abs(d).max() < 1e-15
-    assert thr == pytest.approx(0.01 * rr[rr > 0].mean())
+    assert thr == pytest.approx(0.01 * 10.0 / 500)
 
 
 def test_shift_decomposition():
