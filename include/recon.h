@@ -165,12 +165,12 @@ enum {
   RECON_K_DEPOSIT = 0,   /* CIC deposit                                  */
   RECON_K_ZFWD = 1,      /* Z pass, r2c (densities, FFT export)          */
   RECON_K_ZINV = 2,      /* Z pass, c2r of the smoothed densities        */
-  RECON_K_ZDELTA = 3,    /* Z pass forming delta + r2c                   */
+  RECON_K_ZDELTA = 3,    /* Z pass: z smoothing, delta, r2c              */
   RECON_K_ZPROJ = 4,     /* Z pass: c2r, radial projection, r2c          */
   RECON_K_ZFINAL = 5,    /* Z pass: c2r of the final Psi                 */
   RECON_K_YFWD = 6,      /* Y pass forward                               */
   RECON_K_YINV = 7,      /* Y pass inverse                               */
-  RECON_K_XSMOOTH = 8,   /* X pass with the Gaussian smoothing           */
+  RECON_K_CONV = 8,      /* x / y Gaussian smoothing convolutions        */
   RECON_K_XDELTA = 9,    /* X pass: delta(k), S_-1 and Z[delta/b]        */
   RECON_K_XITER = 10,    /* X pass: source update, norms and Z[S]        */
   RECON_K_SHIFT = 11,    /* CIC interpolation and shift                  */

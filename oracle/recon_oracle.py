@@ -289,10 +289,14 @@ def shifted_positions(pos, d, L: float, periodic: bool):
 # --------------------------------------------------------------------------------------------
 def reconstruct(params: dict, gal_pos, gal_w=None, ran_pos=None, ran_w=None,
                 start: int = START_PLAIN, tol: float = 0.0, max_iter: int = 6,
-                shift: bool = True):
+                shift: bool = True, mask_flip=None):
     """Run the whole method on a catalogue; returns a dict of every intermediate.
 
     params: n, L, b, f, R, los_mode, observer, periodic, mask_frac, lognormal, uniform (bool).
+    mask_flip: optional flat node indices at which the survey-mask decision is inverted.  The mask
+    is a floating-point comparison of the smoothed random density with a threshold; at nodes whose
+    density lies within rounding of the threshold either decision is valid, and a comparison with
+    a float32 implementation picks the branch that implementation took there.
     """
     n, L = int(params["n"]), float(params["L"])
     gal_pos = np.asarray(gal_pos, dtype=np.float64)
@@ -316,6 +320,13 @@ def reconstruct(params: dict, gal_pos, gal_w=None, ran_pos=None, ran_w=None,
         delta, mask, alpha, thr = overdensity_randoms(rho_g_s, rho_r_s, wg.sum(), wr.sum(),
                                                       params.get("mask_frac", 0.01),
                                                       int(np.count_nonzero(rho_r > 0)))
+        if mask_flip is not None and len(mask_flip):
+            mask = mask.copy()
+            mf = mask.reshape(-1)
+            idx = np.asarray(mask_flip, dtype=np.int64)
+            mf[idx] = ~mf[idx]
+            delta = np.zeros_like(rho_g_s)
+            delta[mask] = rho_g_s[mask] / (alpha * rho_r_s[mask]) - 1.0
         out.update(mask=mask, alpha=alpha, threshold=thr)
     out["rho_g_s"] = rho_g_s
     if params.get("lognormal", False):

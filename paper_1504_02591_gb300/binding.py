@@ -30,7 +30,7 @@ ABI_SYMBOLS = (
     "recon_set_timing", "recon_get_timing", "recon_reset_timing",
 )
 KERNEL_KINDS = ("deposit", "z_fwd", "z_inv", "z_delta", "z_proj", "z_final", "y_fwd", "y_inv",
-                "x_smooth", "x_delta", "x_iter", "shift", "other")
+                "conv", "x_delta", "x_iter", "shift", "other")
 
 
 class ReconParams(C.Structure):

@@ -1,0 +1,98 @@
+// conv.cu: Gaussian smoothing of the densities along x and y as periodic 1-D convolutions.
+//
+// The smoothing kernel of Sec. 3.1, S(k) = exp(-k^2 R^2 / 2), is a product of one factor per axis,
+// so on the periodic mesh it is exactly three 1-D periodic convolutions with the real kernel
+// g[t] = (1/N) sum_m exp(-k_m^2 R^2 / 2) exp(2 pi i m t / N) (computed on the host in float64).
+// Applying it in configuration space keeps the float32 rounding relative to the local density:
+// near the survey edge, where the smoothed random density falls to the mask threshold, a
+// Fourier-space product would carry rounding of the order of the field's global magnitude.
+// The z factor is applied inside the delta-forming Z pass; this file holds the x and y passes.
+#include "conv.h"
+
+namespace rg {
+
+// One tile: every line of the axis (length n) for C adjacent z columns of one y (X pass) or one x
+// (Y pass).  Lines are staged in shared memory; each output is written straight back to global
+// memory (in place: all reads come from the staged copy).
+template <int C>
+__global__ void __launch_bounds__(256) conv_kernel(const ConvArgs a) {
+  extern __shared__ float csm[];
+  const int n = a.n;
+  const int ntap = a.ntap;
+  float* taps = csm;                         // ntap values
+  float* s = csm + ((ntap + 3) & ~3);        // nf * n * C
+  for (int j = threadIdx.x; j < ntap; j += blockDim.x) taps[j] = a.taps[j];
+
+  const int zb = n / C;
+  const int t = blockIdx.x;
+  const int other = t / zb;                  // y (X pass) or x (Y pass)
+  const int z0 = (t % zb) * C;
+  const size_t nn = (size_t)n;
+  size_t base, ls;
+  if (a.axis == 0) {  // lines along x: (x N + y) N + z
+    base = (size_t)other * nn + z0;
+    ls = nn * nn;
+  } else {            // lines along y
+    base = (size_t)other * nn * nn + z0;
+    ls = nn;
+  }
+  float cnt = 0.f;
+  for (int q = 0; q < a.nf; ++q) {
+    const float* src = a.f[q];
+    for (int e = threadIdx.x; e < n * (C / 4); e += blockDim.x) {
+      const int i = e / (C / 4), c4 = e % (C / 4);
+      const float4 v = *reinterpret_cast<const float4*>(src + base + (size_t)i * ls + 4 * c4);
+      if (a.count && q == a.nf - 1) cnt += (v.x > 0.f) + (v.y > 0.f) + (v.z > 0.f) + (v.w > 0.f);
+      *reinterpret_cast<float4*>(s + (size_t)(q * n + i) * C + 4 * c4) = v;
+    }
+  }
+  __syncthreads();
+  for (int q = 0; q < a.nf; ++q) {
+    const float* sq = s + (size_t)q * n * C;
+    float* dst = a.f[q];
+    for (int e = threadIdx.x; e < n * C; e += blockDim.x) {
+      const int i = e / C, c = e % C;
+      int idx = i + a.t0;
+      if (idx < 0) idx += n;
+      float acc = 0.f;
+      for (int j = 0; j < ntap; ++j) {
+        acc = fmaf(taps[j], sq[idx * C + c], acc);
+        if (++idx == n) idx = 0;
+      }
+      dst[base + (size_t)i * ls + c] = acc;
+    }
+  }
+  if (a.count) {
+    __shared__ double sh[8];
+    double v = cnt;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double r = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sh[w];
+      a.partials[2 * blockIdx.x + 0] = 0.0;
+      a.partials[2 * blockIdx.x + 1] = r;
+    }
+  }
+}
+
+int conv_cols(int n) { return n >= 1024 ? 8 : 16; }
+
+int conv_blocks(int n) { return n * (n / conv_cols(n)); }
+
+size_t conv_smem(int n, int nf, int ntap) {
+  return sizeof(float) * (((size_t)ntap + 3) / 4 * 4 + (size_t)nf * n * conv_cols(n));
+}
+
+cudaError_t launch_conv(const ConvArgs& a, cudaStream_t st) {
+  const int C = conv_cols(a.n);
+  const size_t smem = conv_smem(a.n, a.nf, a.ntap);
+  const void* k = (C == 16) ? (const void*)conv_kernel<16> : (const void*)conv_kernel<8>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {const_cast<ConvArgs*>(&a)};
+  return cudaLaunchKernel(k, dim3(conv_blocks(a.n)), dim3(256), args, smem, st);
+}
+
+}  // namespace rg

@@ -4,8 +4,8 @@
 // Y and X (strided lines, one [N x C] tile of C adjacent columns per CTA).  Work that is pointwise
 // in configuration space rides on the Z pass (delta formation, the radial projection (Psi.r)r of
 // Eq. Nusser); work that is pointwise in Fourier space rides on the X pass, between its forward
-// and inverse transforms (Gaussian smoothing of Sec. 3.1, Z[s] = i k s / k^2 of Eq. Zeldovich, the
-// source update of Eq. iterative with its convergence norms).
+// and inverse transforms (Z[s] = i k s / k^2 of Eq. Zeldovich, the source update of Eq. iterative
+// with its convergence norms).
 #pragma once
 #include "fft_core.cuh"
 #include "types.h"
@@ -136,38 +136,56 @@ __global__ void __launch_bounds__(kZThreads) zpass_kernel(const ZArgs a) {
     // load real rows of N floats as L packed complex values
     const int nin = (MODE == Z_DELTA) ? (a.uniform ? 1 : 2) : NC;
     if (MODE == Z_DELTA) {
+      // rows of rho_g (and rho_r) already smoothed along x and y: apply the z factor of the
+      // Gaussian as a periodic convolution, then form delta (Sec. 3.2) node by node
       const double* red = a.red;
       const float inv_alpha = a.uniform ? (float)((double)N * N * N / red[RED_SUM_WG])
                                         : (float)(red[RED_SUM_WR] / red[RED_SUM_WG]);
       const float thr = a.uniform ? 0.f : (float)(a.mask_frac * red[RED_SUM_WR] / red[RED_CNT_RPOS]);
-      for (int e = threadIdx.x; e < ROWS * (L / 2); e += kZThreads) {
-        const int row = e / (L / 2), m2 = e % (L / 2);
-        const float4 g = reinterpret_cast<const float4*>(a.f[0].M + (row0 + row) * L)[m2];
-        float d[4];
+      float* raw = reinterpret_cast<float*>(s + NCOL * Lay::kStride);   // nin * ROWS * N
+      float* taps = raw + 2 * ROWS * N;                                 // ntap
+      for (int j = threadIdx.x; j < a.ntap; j += kZThreads) taps[j] = a.taps[j];
+      for (int e = threadIdx.x; e < nin * ROWS * (N / 4); e += kZThreads) {
+        const int q = e / (ROWS * (N / 4));
+        const int rem = e % (ROWS * (N / 4));
+        const int row = rem / (N / 4), m4 = rem % (N / 4);
+        reinterpret_cast<float4*>(raw + (q * ROWS + row) * N)[m4] =
+            reinterpret_cast<const float4*>(a.f[q].M + (row0 + row) * L)[m4];
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < ROWS * N; e += kZThreads) {
+        const int row = e / N, z = e % N;
+        int idx = z + a.t0;
+        if (idx < 0) idx += N;
+        const float* rg = raw + row * N;
+        const float* rr = raw + (ROWS + row) * N;
+        float g = 0.f, r = 0.f;
         if (nin == 1) {
-          d[0] = g.x * inv_alpha - 1.f; d[1] = g.y * inv_alpha - 1.f;
-          d[2] = g.z * inv_alpha - 1.f; d[3] = g.w * inv_alpha - 1.f;
-        } else {
-          const float4 r = reinterpret_cast<const float4*>(a.f[1].M + (row0 + row) * L)[m2];
-          const float gg[4] = {g.x, g.y, g.z, g.w}, rr[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const bool in = rr[u] > thr;
-            d[u] = in ? gg[u] * inv_alpha / rr[u] - 1.f : 0.f;
-            acc1 += in ? 1.f : 0.f;
+          for (int j = 0; j < a.ntap; ++j) {
+            g = fmaf(taps[j], rg[idx], g);
+            if (++idx == N) idx = 0;
           }
+        } else {
+          for (int j = 0; j < a.ntap; ++j) {
+            g = fmaf(taps[j], rg[idx], g);
+            r = fmaf(taps[j], rr[idx], r);
+            if (++idx == N) idx = 0;
+          }
+        }
+        float d;
+        if (nin == 1) {
+          d = g * inv_alpha - 1.f;
+        } else {
+          const bool in = r > thr;
+          d = in ? g * inv_alpha / r - 1.f : 0.f;
+          acc1 += in ? 1.f : 0.f;
         }
         if (a.lognormal) {
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            d[u] = logf(fmaxf(1.f + d[u], 1e-6f));
-            acc0 += d[u];
-          }
+          d = logf(fmaxf(1.f + d, 1e-6f));
+          acc0 += d;
         }
-        if (a.delta_real)
-          reinterpret_cast<float4*>(a.delta_real + (row0 + row) * N)[m2] = make_float4(d[0], d[1], d[2], d[3]);
-        s[Lay::phys(2 * m2, row)] = make_float2(d[0], d[1]);
-        s[Lay::phys(2 * m2 + 1, row)] = make_float2(d[2], d[3]);
+        if (a.delta_real) a.delta_real[(row0 + row) * N + z] = d;
+        reinterpret_cast<float*>(s + Lay::phys(z >> 1, row))[z & 1] = d;
       }
     } else {
       for (int e = threadIdx.x; e < NC * ROWS * (L / 2); e += kZThreads) {
@@ -262,7 +280,8 @@ __global__ void __launch_bounds__(kZThreads) zpass_kernel(const ZArgs a) {
 template <int N, int NC>
 constexpr size_t zpass_smem(int mode) {
   return sizeof(float2) * (N + 2 * ZRows<N>::v * NC + 2 +
-                           (size_t)ZRows<N>::v * (mode == Z_DELTA ? 1 : NC) * RowLayout<N / 2>::kStride);
+                           (size_t)ZRows<N>::v * (mode == Z_DELTA ? 1 : NC) * RowLayout<N / 2>::kStride) +
+         (mode == Z_DELTA ? sizeof(float) * ((size_t)2 * ZRows<N>::v * N + N) : 0);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -363,7 +382,7 @@ __global__ void __launch_bounds__(kSThreads) spass_kernel(const SArgs a) {
   __syncthreads();
 
   // ---- forward transform along the line
-  if (MODE == S_FWD || MODE == S_SMOOTH || MODE == S_ITER) {
+  if (MODE == S_FWD || MODE == S_ITER) {
 #pragma unroll
     for (int q = 0; q < NC; ++q) Plan<N>::template run<C, kSThreads, false, Lay, 1>(s + q * N * C, tw);
   } else if (MODE == S_DELTA) {
@@ -371,7 +390,7 @@ __global__ void __launch_bounds__(kSThreads) spass_kernel(const SArgs a) {
   }
 
   float d2 = 0.f, s2 = 0.f;
-  if (MODE == S_SMOOTH || MODE == S_DELTA || MODE == S_ITER) {
+  if (MODE == S_DELTA || MODE == S_ITER) {
     const Geometry& g = a.g;
     for (int e = threadIdx.x; e < N * C; e += kSThreads) {
       const int i = e / C, c = e % C;
@@ -382,11 +401,7 @@ __global__ void __launch_bounds__(kSThreads) spass_kernel(const SArgs a) {
       const float kx = g.kf * mx, kyf = g.kf * my, kzf = g.kf * kz;
       const float k2 = kx * kx + kyf * kyf + kzf * kzf;
       const int p = Lay::phys(i, c);
-      if (MODE == S_SMOOTH) {
-        const float w = expf(-a.half_R2 * k2) * g.inv_n3;
-#pragma unroll
-        for (int q = 0; q < NC; ++q) s[q * N * C + p] = cscale(s[q * N * C + p], w);
-      } else {
+      {
         const float kdx = (i == H) ? 0.f : kx;
         const float kdy = (ky == H) ? 0.f : kyf;
         const float kdz = (kz == H) ? 0.f : kzf;
@@ -431,7 +446,7 @@ __global__ void __launch_bounds__(kSThreads) spass_kernel(const SArgs a) {
   }
 
   // ---- inverse transform along the line
-  if (MODE == S_INV || MODE == S_SMOOTH || MODE == S_DELTA || MODE == S_ITER) {
+  if (MODE == S_INV || MODE == S_DELTA || MODE == S_ITER) {
 #pragma unroll
     for (int q = 0; q < NS; ++q) Plan<N>::template run<C, kSThreads, true, Lay, 1>(s + q * N * C, tw);
   }
@@ -490,7 +505,6 @@ struct MeshImpl {
     RG_S(S_FWD, 1, AX_Y) RG_S(S_FWD, 2, AX_Y) RG_S(S_FWD, 3, AX_Y)
     RG_S(S_INV, 1, AX_Y) RG_S(S_INV, 2, AX_Y) RG_S(S_INV, 3, AX_Y)
     RG_S(S_FWD, 1, AX_X) RG_S(S_INV, 1, AX_X)
-    RG_S(S_SMOOTH, 1, AX_X) RG_S(S_SMOOTH, 2, AX_X)
     RG_S(S_DELTA, 1, AX_X) RG_S(S_ITER, 3, AX_X)
 #undef RG_S
     return cudaErrorInvalidValue;

@@ -2,9 +2,9 @@
 //
 // Pipeline per reconstruction (Burden, Percival & Howlett 2015):
 //   deposit  CIC of galaxies and randoms -> rho_g, rho_r; sums of weights (float64)
-//   smooth   Z r2c + count of nodes with random mass | Y | X (x exp(-k^2 R^2/2)) | Y | Z c2r
-//                                                                                  (Sec. 3.1, 3.2)
-//            Z: delta = rho_g,s/(alpha rho_r,s) - 1 in the mask (+ lognormal) and its r2c | Y
+//   smooth   Gaussian exp(-k^2 R^2/2) as three periodic 1-D convolutions (x, y passes, then z
+//            inside the next pass); Z: delta = rho_g,s/(alpha rho_r,s) - 1 in the mask (+ lognormal)
+//            and its r2c | Y                                                        (Sec. 3.1, 3.2)
 //   iterate  X: delta(k), S_-1 = delta/b, Psi_s = Z[delta/b] | Y | Z: P_0 = (1-c)(Psi_s.r)r | Y
 //            repeat: X: S_n = delta/b + beta i k.P_n, norms, Psi = i k S/k^2 | Y |
 //                    Z: P = (Psi.r)r (or the final real Psi) | Y                  (Sec. 5.1)
@@ -17,6 +17,7 @@
 
 #include "../../include/recon.h"
 #include "cic.h"
+#include "conv.h"
 #include "types.h"
 
 namespace rg {
@@ -58,7 +59,7 @@ enum State { ST_CREATED = 0, ST_DEPOSITED = 1, ST_SMOOTHED = 2, ST_ITERATED = 3 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t field_M, field_Q, field, tw, off, red, partials, stage, total;
+  size_t field_M, field_Q, field, tw, off, taps, red, partials, stage, total;
 };
 
 Layout layout_for(int n) {
@@ -69,13 +70,15 @@ Layout layout_for(int n) {
   l.field = l.field_M + l.field_Q;
   l.tw = align256((size_t)n * sizeof(float2));
   l.off = align256((size_t)3 * n * sizeof(float));
+  l.taps = align256((size_t)n * sizeof(float));
   l.red = align256(64 * sizeof(double));
   size_t nb = (size_t)mk->z_blocks;
   if ((size_t)mk->s_blocks > nb) nb = mk->s_blocks;
   if ((size_t)kDepositBlocks > nb) nb = kDepositBlocks;
+  if ((size_t)conv_blocks(n) > nb) nb = conv_blocks(n);
   l.partials = align256(nb * 4 * sizeof(double));
   l.stage = align256((size_t)kStageParticles * kStageBytesPer);
-  l.total = 5 * l.field + l.tw + l.off + l.red + l.partials + l.stage;
+  l.total = 5 * l.field + l.tw + l.off + l.taps + l.red + l.partials + l.stage;
   return l;
 }
 
@@ -113,6 +116,8 @@ struct recon_handle {
   Field V[3]{}, D{}, S{};
   float2* tw = nullptr;
   float* off = nullptr;
+  float* taps = nullptr;   // smoothing kernel g[t0 .. t0 + ntap - 1]
+  int ntap = 1, t0 = 0;
   double* red = nullptr;
   double* partials = nullptr;
   char* stage = nullptr;
@@ -188,7 +193,6 @@ int zkind(int mode) {
 int skind(int mode, int axis) {
   if (axis == AX_Y) return mode == S_FWD ? RECON_K_YFWD : RECON_K_YINV;
   switch (mode) {
-    case S_SMOOTH: return RECON_K_XSMOOTH;
     case S_DELTA: return RECON_K_XDELTA;
     case S_ITER: return RECON_K_XITER;
     default: return RECON_K_OTHER;
@@ -225,7 +229,6 @@ SArgs sargs(recon_handle* h) {
   a.sbuf = h->S;
   a.inv_b = (float)(1.0 / h->p.b);
   a.beta = (float)(h->p.f / h->p.b);
-  a.half_R2 = (float)(0.5 * h->p.smooth_R * h->p.smooth_R);
   a.lognormal = h->p.lognormal;
   return a;
 }
@@ -406,6 +409,8 @@ recon_status recon_create(const recon_params* p, void* stream, void* workspace, 
   b += h->lay.tw;
   h->off = (float*)b;
   b += h->lay.off;
+  h->taps = (float*)b;
+  b += h->lay.taps;
   h->red = (double*)b;
   b += h->lay.red;
   h->partials = (double*)b;
@@ -423,10 +428,36 @@ recon_status recon_create(const recon_params* p, void* stream, void* workspace, 
   const double H = h->L / n;
   for (int a = 0; a < 3; ++a)
     for (int i = 0; i < n; ++i) off[a * n + i] = (float)((double)i * H - p->observer[a]);
+  // Gaussian smoothing as a periodic convolution per axis: g[t] = (1/N) sum_m exp(-k_m^2 R^2/2)
+  // cos(2 pi m t / N); taps beyond the last |g[t]| > 1e-9 g[0] are dropped, and a kernel that has
+  // not decayed by then is used over the whole period.
+  std::vector<double> gk(n);
+  for (int t = 0; t < n; ++t) {
+    double acc = 0.0;
+    for (int m = 0; m < n; ++m) {
+      const int mm = (m <= n / 2) ? m : m - n;
+      const double k = 2.0 * M_PI * mm / h->L;
+      acc += std::exp(-0.5 * k * k * p->smooth_R * p->smooth_R) * std::cos(2.0 * M_PI * (double)m * t / n);
+    }
+    gk[t] = acc / n;
+  }
+  int K = 0;
+  for (int t = 1; t <= n / 2; ++t)
+    if (std::fabs(gk[t]) > 1e-9 * std::fabs(gk[0])) K = t;
+  if (2 * K + 1 >= n) {
+    h->t0 = -n / 2;
+    h->ntap = n;
+  } else {
+    h->t0 = -K;
+    h->ntap = 2 * K + 1;
+  }
+  std::vector<float> taps(h->ntap);
+  for (int j = 0; j < h->ntap; ++j) taps[j] = (float)gk[((h->t0 + j) % n + n) % n];
   recon_status rs = RECON_OK;
   do {
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(h->tw, tw.data(), n * sizeof(float2), cudaMemcpyHostToDevice, h->st)) != cudaSuccess ||
+    if ((e = cudaMemcpyAsync(h->taps, taps.data(), h->ntap * sizeof(float), cudaMemcpyHostToDevice, h->st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(h->tw, tw.data(), n * sizeof(float2), cudaMemcpyHostToDevice, h->st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(h->off, off.data(), 3 * n * sizeof(float), cudaMemcpyHostToDevice, h->st)) != cudaSuccess ||
         (e = cudaMemsetAsync(h->red, 0, h->lay.red, h->st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(h->st)) != cudaSuccess) {
@@ -522,35 +553,35 @@ recon_status recon_smooth(recon_handle* h) {
   if (!h) return RECON_ERR_INVALID_ARG;
   if (h->state != ST_DEPOSITED) return RECON_ERR_STATE;
   const bool uniform = h->p.mean_density_mode == RECON_MEAN_UNIFORM;
-  const int nc = uniform ? 1 : 2;
-  {
-    ZArgs a = zargs(h);
-    a.f[0] = h->V[0];
-    a.f[1] = h->V[1];
-    a.stats = !uniform;
-    RG_TRY(run_z(h, Z_FWD, nc, a));
-    if (!uniform) RG_TRY(finalize(h, h->mk->z_blocks, 2, RED_SUM_RPOS, 0));
-  }
-  RG_TRY(ypass(h, S_FWD, nc, h->V));
-  {
-    SArgs a = sargs(h);
-    a.f[0] = h->V[0];
-    a.f[1] = h->V[1];
-    RG_TRY(run_s(h, S_SMOOTH, nc, AX_X, a));
-  }
-  RG_TRY(ypass(h, S_INV, nc, h->V));
-  {
-    ZArgs a = zargs(h);
-    a.f[0] = h->V[0];
-    a.f[1] = h->V[1];
-    RG_TRY(run_z(h, Z_INV, nc, a));
-  }
+  const int nf = uniform ? 1 : 2;
+  ConvArgs c{};
+  c.f[0] = reinterpret_cast<float*>(h->V[0].M);
+  c.f[1] = reinterpret_cast<float*>(h->V[1].M);
+  c.nf = nf;
+  c.n = h->n;
+  c.taps = h->taps;
+  c.ntap = h->ntap;
+  c.t0 = h->t0;
+  c.partials = h->partials;
+  // x factor of the Gaussian; counts the nodes that received random mass (mask threshold)
+  c.axis = 0;
+  c.count = !uniform;
+  RG_CUDA(timed(h, RECON_K_CONV, 2.0 * nf * rfield(h), [&] { return launch_conv(c, h->st); }));
+  if (!uniform) RG_TRY(finalize(h, conv_blocks(h->n), 2, RED_SUM_RPOS, 0));
+  // y factor
+  c.axis = 1;
+  c.count = 0;
+  RG_CUDA(timed(h, RECON_K_CONV, 2.0 * nf * rfield(h), [&] { return launch_conv(c, h->st); }));
+  // z factor, delta (mask, lognormal) and its r2c along z
   {
     ZArgs a = zargs(h);
     a.f[0] = h->V[0];
     a.f[1] = h->V[1];
     a.dout = h->D;
     a.delta_real = reinterpret_cast<float*>(h->V[2].M);
+    a.taps = h->taps;
+    a.ntap = h->ntap;
+    a.t0 = h->t0;
     RG_TRY(run_z(h, Z_DELTA, 2, a));
     RG_TRY(finalize(h, h->mk->z_blocks, 2, RED_SUM_LOG, 0));
   }

@@ -38,7 +38,7 @@ struct Geometry {
 };
 
 enum ZMode { Z_FWD = 0, Z_INV = 1, Z_DELTA = 2, Z_PROJ = 3, Z_FINAL = 4 };
-enum SMode { S_FWD = 0, S_INV = 1, S_SMOOTH = 2, S_DELTA = 3, S_ITER = 4 };
+enum SMode { S_FWD = 0, S_INV = 1, S_DELTA = 3, S_ITER = 4 };
 enum Axis { AX_X = 0, AX_Y = 1 };
 
 struct ZArgs {
@@ -55,6 +55,9 @@ struct ZArgs {
   float mask_frac;
   int uniform;            // delta from rho_bar = sum w_g / N^3
   int lognormal;
+  const float* taps;      // z factor of the Gaussian smoothing: g[t0 .. t0 + ntap - 1]
+  int ntap;
+  int t0;
 };
 
 struct SArgs {
@@ -67,7 +70,6 @@ struct SArgs {
   Field sbuf;             // stored source S of the previous iteration
   float inv_b;            // 1 / b
   float beta;             // f / b
-  float half_R2;          // R^2 / 2 (S_SMOOTH)
   int d_is_k;             // S_DELTA: dk is already fully transformed
   int lognormal;          // S_DELTA: subtract the lognormal constant at k = 0
 };

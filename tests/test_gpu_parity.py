@@ -79,7 +79,7 @@ def test_periodic_pipeline_vs_oracle(B, periodic_mock, periodic_oracle, start):
     r.smooth()
     sc = r.scalars()
     assert sc["sum_wg"] == len(m.galaxies.pos) and sc["sum_wr"] == len(m.randoms.pos)
-    assert sc["threshold"] == pytest.approx(ref["threshold"], rel=1e-5)
+    assert sc["threshold"] == pytest.approx(ref["threshold"], rel=1e-12)
     delta = r.get_field(B.FIELD_DELTA).cpu().numpy()
     assert rel_l2(delta, ref["delta"]) < 2e-6
     n_it, rel, st = r.iterate(start, 0.0, 6)
@@ -112,6 +112,30 @@ def test_delta_k_export_matches_oracle(B, periodic_mock, periodic_oracle):
 # ------------------------------------------------------------------------------------------------
 # Survey shell with mask (the 512^3 survey shape scaled to 128^3 and 6e4 galaxies)
 # ------------------------------------------------------------------------------------------------
+MASK_BAND = 1e-5   # relative distance to the mask threshold within which either decision is valid
+
+
+def mask_ambiguity(ref):
+    """Flat indices of nodes whose FP64 smoothed random density is within MASK_BAND of the threshold."""
+    rr = ref["rho_r_s"].reshape(-1)
+    return np.nonzero(np.abs(rr - ref["threshold"]) <= MASK_BAND * ref["threshold"])[0]
+
+
+def check_mask_and_rerun(m, ref, gpu_delta, start, tol, max_iter):
+    """The GPU mask (nodes where its delta is nonzero) may differ from the oracle's only at nodes
+    within rounding of the threshold; if it does, the oracle is rerun with those decisions taken
+    the GPU's way (each is a valid branch) so the comparison is against the same branch."""
+    gmask = (gpu_delta != 0).reshape(-1)
+    omask = ref["mask"].reshape(-1)
+    diff = np.nonzero(gmask != omask)[0]
+    amb = set(mask_ambiguity(ref).tolist())
+    assert all(int(i) in amb for i in diff), f"{len(diff)} mask differences, not all at the threshold"
+    if len(diff) == 0:
+        return ref
+    return O.reconstruct(m.params(), m.galaxies.pos, None, m.randoms.pos, None, start=start, tol=tol,
+                         max_iter=max_iter, mask_flip=diff)
+
+
 @pytest.fixture(scope="module")
 def shell_case():
     m = mocks.survey_shell_512(n_gal=60_000, ran_ratio=50, n_mesh=128)
@@ -123,13 +147,16 @@ def shell_case():
 def test_shell_survey_converged_vs_oracle(B, shell_case):
     m, ref = shell_case
     r = B.Recon.from_mock(m)
-    n_it, rel, st = r.run(torch.from_numpy(m.galaxies.pos).cuda(), torch.from_numpy(m.randoms.pos).cuda(),
-                          start=2, tol=1e-6, max_iter=40)
+    r.deposit(torch.from_numpy(m.galaxies.pos).cuda(), None, torch.from_numpy(m.randoms.pos).cuda(), None)
+    r.smooth()
+    sc = r.scalars()
+    assert sc["threshold"] == pytest.approx(ref["threshold"], rel=1e-12)
+    delta = r.get_field(B.FIELD_DELTA).cpu().numpy()
+    ref = check_mask_and_rerun(m, ref, delta, O.START_FFTA, 1e-6, 40)
+    assert rel_l2(delta, ref["delta"]) < 1e-5
+    n_it, rel, st = r.iterate(2, 1e-6, 40)
     assert st == B.OK and rel < 1e-6
     assert abs(n_it - ref["n_iter"]) <= 1
-    sc = r.scalars()
-    # the mask is a float32 decision on the smoothed randoms: nodes may differ only at the threshold
-    assert abs(sc["n_mask"] - ref["mask"].sum()) <= 1e-4 * ref["mask"].sum() + 5
     psi = r.get_psi().cpu().numpy()
     assert rel_l2(psi, ref["psi"]) <= PSI_TOL
     sg = r.shift(torch.from_numpy(m.galaxies.pos).cuda(), True).cpu().numpy()
