@@ -213,7 +213,7 @@ ZArgs zargs(recon_handle* h) {
   a.partials = h->partials;
   a.red = h->red;
   a.coef = 1.f;
-  a.mask_frac = (float)h->p.mask_frac;
+  a.mask_frac = h->p.mask_frac;
   a.uniform = h->p.mean_density_mode == RECON_MEAN_UNIFORM;
   a.lognormal = h->p.lognormal;
   return a;

@@ -52,7 +52,7 @@ struct ZArgs {
   // Z_DELTA
   Field dout;             // delta on the (z-transformed) half grid
   float* delta_real;      // optional real copy of delta
-  float mask_frac;
+  double mask_frac;
   int uniform;            // delta from rho_bar = sum w_g / N^3
   int lognormal;
   const float* taps;      // z factor of the Gaussian smoothing: g[t0 .. t0 + ntap - 1]
