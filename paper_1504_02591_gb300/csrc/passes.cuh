@@ -108,10 +108,14 @@ __global__ void __launch_bounds__(kZThreads) zpass_kernel(const ZArgs a) {
   __shared__ double red_sh[kZThreads / 32];
 
   for (int m = threadIdx.x; m < N; m += kZThreads) tw[m] = a.tw[m];
-  const size_t row0 = (size_t)blockIdx.x * ROWS;
-
   float acc0 = 0.f, acc1 = 0.f;
   constexpr bool kInverse = (MODE == Z_INV || MODE == Z_PROJ || MODE == Z_FINAL);
+  constexpr int kRowBlocks = N * N / ROWS;
+
+  // persistent: each CTA walks row blocks blockIdx.x, blockIdx.x + gridDim.x, ...
+  for (int rb = blockIdx.x; rb < kRowBlocks; rb += gridDim.x) {
+  const size_t row0 = (size_t)rb * ROWS;
+  __syncthreads();   // the previous block's stores have read s
 
   if (kInverse) {
     // load M rows (L complex) and the Nyquist values
@@ -266,6 +270,8 @@ __global__ void __launch_bounds__(kZThreads) zpass_kernel(const ZArgs a) {
     }
   }
 
+  }  // row blocks
+
   const bool want_red = (MODE == Z_DELTA) || (MODE == Z_FWD && a.stats);
   if (want_red) {
     double r0 = block_sum((double)acc0, red_sh);
@@ -359,7 +365,7 @@ __device__ __forceinline__ void tile_store(const float2* s, float2* __restrict__
 }
 
 template <int N, int MODE, int NC, int AXIS>
-__global__ void __launch_bounds__(kSThreads) spass_kernel(const SArgs a) {
+__global__ void __launch_bounds__(kSThreads, 2) spass_kernel(const SArgs a) {
   constexpr int C = SCols<N>::v;
   constexpr int H = N / 2;
   constexpr int NS = (MODE == S_DELTA || MODE == S_ITER) ? 3 : NC;   // smem slots
@@ -381,6 +387,25 @@ __global__ void __launch_bounds__(kSThreads) spass_kernel(const SArgs a) {
   }
   __syncthreads();
 
+  // ---- S_ITER: fetch delta(k) and the previous source for this thread's elements now, so the
+  // loads are in flight during the forward transforms instead of inside the element loop
+  constexpr int PE = (N * C + kSThreads - 1) / kSThreads;
+  float2 dkr[MODE == S_ITER ? PE : 1], spr[MODE == S_ITER ? PE : 1];
+  if (MODE == S_ITER) {
+    const float2* __restrict__ dkp = t.isQ ? a.dk.Q : a.dk.M;
+    const float2* __restrict__ spp = t.isQ ? a.sbuf.Q : a.sbuf.M;
+#pragma unroll
+    for (int k = 0; k < PE; ++k) {
+      const int e = threadIdx.x + k * kSThreads;
+      if ((N * C) % kSThreads == 0 || e < N * C) {
+        const int i = e / C, c = e % C;
+        const size_t gi = t.base + (size_t)i * t.ls + (size_t)c * t.cs;
+        dkr[k] = dkp[gi];
+        spr[k] = spp[gi];
+      }
+    }
+  }
+
   // ---- forward transform along the line
   if (MODE == S_FWD || MODE == S_ITER) {
 #pragma unroll
@@ -392,7 +417,10 @@ __global__ void __launch_bounds__(kSThreads) spass_kernel(const SArgs a) {
   float d2 = 0.f, s2 = 0.f;
   if (MODE == S_DELTA || MODE == S_ITER) {
     const Geometry& g = a.g;
-    for (int e = threadIdx.x; e < N * C; e += kSThreads) {
+#pragma unroll
+    for (int k = 0; k < PE; ++k) {
+      const int e = threadIdx.x + k * kSThreads;
+      if ((N * C) % kSThreads != 0 && e >= N * C) break;
       const int i = e / C, c = e % C;
       const int mx = (i < H) ? i : i - N;
       int ky, kz;
@@ -417,7 +445,7 @@ __global__ void __launch_bounds__(kSThreads) spass_kernel(const SArgs a) {
           }
           S = cscale(dk, a.inv_b);
         } else {
-          const float2 dk = (t.isQ ? a.dk.Q : a.dk.M)[gi];
+          const float2 dk = dkr[MODE == S_ITER ? k : 0];
           const float2 px = s[p], py = s[N * C + p], pz = s[2 * N * C + p];
           // i k . P
           const float dre = kdx * px.x + kdy * py.x + kdz * pz.x;
@@ -427,7 +455,7 @@ __global__ void __launch_bounds__(kSThreads) spass_kernel(const SArgs a) {
         if (k2 == 0.f) S = make_float2(0.f, 0.f);
         const float inv_k2 = (k2 > 0.f) ? 1.f / k2 : 0.f;
         if (MODE == S_ITER) {
-          const float2 sp = Sp[gi];
+          const float2 sp = spr[MODE == S_ITER ? k : 0];
           const float wgt = (kz == 0 || kz == H) ? 1.f : 2.f;
           const float fac = wgt * (kdx * kdx + kdy * kdy + kdz * kdz) * inv_k2 * inv_k2;
           const float ddx = S.x - sp.x, ddy = S.y - sp.y;
@@ -484,13 +512,13 @@ static cudaError_t launch_with_smem(K kern, int blocks, int threads, size_t smem
 
 template <int N>
 struct MeshImpl {
-  static constexpr int kZBlocks = N * N / ZRows<N>::v;
+  static constexpr int kZBlocks = N * N / ZRows<N>::v;   // row blocks (upper bound of the Z grid)
   static constexpr int kSBlocks = N * ((N / 2) / SCols<N>::v) + N / SCols<N>::v;
 
   static cudaError_t zpass(int mode, int nc, const ZArgs& a, cudaStream_t st) {
 #define RG_Z(M_, NC_)                                                                                   \
   if (mode == M_ && nc == NC_)                                                                          \
-    return launch_with_smem(zpass_kernel<N, M_, NC_>, kZBlocks, kZThreads, zpass_smem<N, NC_>(M_), st, &a);
+    return launch_with_smem(zpass_kernel<N, M_, NC_>, zgrid(), kZThreads, zpass_smem<N, NC_>(M_), st, &a);
     RG_Z(Z_FWD, 1) RG_Z(Z_FWD, 2) RG_Z(Z_INV, 1) RG_Z(Z_INV, 2) RG_Z(Z_DELTA, 2) RG_Z(Z_PROJ, 3)
     RG_Z(Z_FINAL, 3)
 #undef RG_Z
@@ -510,8 +538,22 @@ struct MeshImpl {
     return cudaErrorInvalidValue;
   }
 
+  // persistent Z grid: 4 CTAs per SM (register-bound at 256 threads), at most one per row block
+  static int zgrid() {
+    static const int g = [] {
+      int dev = 0, sm = 152;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        sm = 152;
+      }
+      return kZBlocks < 4 * sm ? kZBlocks : 4 * sm;
+    }();
+    return g;
+  }
+
   static const MeshKernels* table() {
-    static const MeshKernels t = {N, kZBlocks, kSBlocks, &zpass, &spass};
+    static const MeshKernels t = {N, kZBlocks, kSBlocks, &zgrid, &zpass, &spass};
     return &t;
   }
 };

@@ -583,7 +583,7 @@ recon_status recon_smooth(recon_handle* h) {
     a.ntap = h->ntap;
     a.t0 = h->t0;
     RG_TRY(run_z(h, Z_DELTA, 2, a));
-    RG_TRY(finalize(h, h->mk->z_blocks, 2, RED_SUM_LOG, 0));
+    RG_TRY(finalize(h, h->mk->z_grid(), 2, RED_SUM_LOG, 0));
   }
   RG_TRY(ypass(h, S_FWD, 1, &h->D));
   h->state = ST_SMOOTHED;

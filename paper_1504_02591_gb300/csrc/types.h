@@ -77,8 +77,9 @@ struct SArgs {
 // Kernels of one mesh size (one table per supported N).
 struct MeshKernels {
   int n;
-  int z_blocks;           // CTAs of a Z pass
+  int z_blocks;           // row blocks of a Z pass (upper bound of its grid)
   int s_blocks;           // CTAs of a strided pass
+  int (*z_grid)();        // CTAs actually launched by a Z pass (persistent)
   cudaError_t (*zpass)(int mode, int nc, const ZArgs& a, cudaStream_t st);
   cudaError_t (*spass)(int mode, int nc, int axis, const SArgs& a, cudaStream_t st);
 };
