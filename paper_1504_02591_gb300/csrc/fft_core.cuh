@@ -136,17 +136,26 @@ struct RowLayout {
 };
 
 // One Stockham stage over NCOL lines of length L with T threads.  The twiddle table holds
-// exp(-2 pi i m / (L * TWS)); index m * TWS gives exp(-2 pi i m / L).
-template <int L, int NCOL, int T, int R, int NS, bool INV, class Lay, int TWS>
+// exp(-2 pi i m / (L * TWS)); index m * TWS gives exp(-2 pi i m / L).  WARP selects a single warp
+// working on its own lines (lane index, __syncwarp) instead of the whole CTA (__syncthreads).
+template <bool WARP>
+__device__ __forceinline__ int group_tid() { return WARP ? (threadIdx.x & 31) : threadIdx.x; }
+template <bool WARP>
+__device__ __forceinline__ void group_sync() {
+  if (WARP) __syncwarp(); else __syncthreads();
+}
+
+template <int L, int NCOL, int T, int R, int NS, bool INV, class Lay, int TWS, bool WARP>
 __device__ __forceinline__ void stockham_stage(float2* __restrict__ s, const float2* __restrict__ tw) {
   constexpr int NBL = L / R;
   constexpr int NB = NBL * NCOL;
   constexpr int PER = (NB + T - 1) / T;
   constexpr int TWSTEP = L / (NS * R);
+  const int tid = group_tid<WARP>();
   float2 v[PER][R];
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
-    const int b = threadIdx.x + p * T;
+    const int b = tid + p * T;
     if ((NB % T == 0) || b < NB) {
       const int col = Lay::kColFast ? (b % NCOL) : (b / NBL);
       const int j = Lay::kColFast ? (b / NCOL) : (b % NBL);
@@ -164,10 +173,10 @@ __device__ __forceinline__ void stockham_stage(float2* __restrict__ s, const flo
       Dft<R, INV>::run(v[p]);
     }
   }
-  __syncthreads();
+  group_sync<WARP>();
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
-    const int b = threadIdx.x + p * T;
+    const int b = tid + p * T;
     if ((NB % T == 0) || b < NB) {
       const int col = Lay::kColFast ? (b % NCOL) : (b / NBL);
       const int j = Lay::kColFast ? (b / NCOL) : (b % NBL);
@@ -177,13 +186,13 @@ __device__ __forceinline__ void stockham_stage(float2* __restrict__ s, const flo
       for (int r = 0; r < R; ++r) s[Lay::phys(base + r * NS, col)] = v[p][r];
     }
   }
-  __syncthreads();
+  group_sync<WARP>();
 }
 
-template <int L, int NCOL, int T, bool INV, class Lay, int TWS, int NS, int R, int... Rest>
+template <int L, int NCOL, int T, bool INV, class Lay, int TWS, bool WARP, int NS, int R, int... Rest>
 __device__ __forceinline__ void stockham_run(float2* s, const float2* tw) {
-  stockham_stage<L, NCOL, T, R, NS, INV, Lay, TWS>(s, tw);
-  if constexpr (sizeof...(Rest) > 0) stockham_run<L, NCOL, T, INV, Lay, TWS, NS * R, Rest...>(s, tw);
+  stockham_stage<L, NCOL, T, R, NS, INV, Lay, TWS, WARP>(s, tw);
+  if constexpr (sizeof...(Rest) > 0) stockham_run<L, NCOL, T, INV, Lay, TWS, WARP, NS * R, Rest...>(s, tw);
 }
 
 // Radix plan per line length.
@@ -192,9 +201,9 @@ struct Plan;
 #define RG_PLAN(LEN, ...)                                                                   \
   template <>                                                                               \
   struct Plan<LEN> {                                                                        \
-    template <int NCOL, int T, bool INV, class Lay, int TWS>                                \
+    template <int NCOL, int T, bool INV, class Lay, int TWS, bool WARP = false>             \
     __device__ __forceinline__ static void run(float2* s, const float2* tw) {               \
-      stockham_run<LEN, NCOL, T, INV, Lay, TWS, 1, __VA_ARGS__>(s, tw);                    \
+      stockham_run<LEN, NCOL, T, INV, Lay, TWS, WARP, 1, __VA_ARGS__>(s, tw);              \
     }                                                                                       \
   };
 RG_PLAN(16, 4, 4)

@@ -16,10 +16,6 @@ constexpr int kZThreads = 256;
 constexpr int kSThreads = 256;
 
 template <int N>
-struct ZRows {  // rows of the real field handled by one CTA of a Z pass
-  static constexpr int v = (N >= 512) ? 4 : (N >= 256 ? 8 : (N >= 128 ? 16 : 32));
-};
-template <int N>
 struct SCols {  // adjacent columns in one strided tile
   static constexpr int v = (N >= 1024) ? 4 : 8;
 };
@@ -41,13 +37,15 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // A real row is packed as N/2 complex z_m = x_2m + i x_2m+1 and transformed with an N/2-point FFT;
 // the split into even/odd spectra with the exp(-2 pi i k / N) twiddles completes the r2c (and the
 // reverse for c2r, which returns N times the inverse transform of the row).
+// Each warp owns one row (all of its components) at a time and synchronises only with itself, so
+// the CTA never waits at a block-wide barrier inside the row loop.
 // ------------------------------------------------------------------------------------------------
 template <int N, int NCOL>
-__device__ __forceinline__ void r2c_split(float2* s, float2* qv, const float2* tw) {
+__device__ __forceinline__ void r2c_split(float2* s, float2* qv, const float2* tw, int lane) {
   constexpr int L = N / 2;
   using Lay = RowLayout<L>;
   // every line: pairs (k, L - k) for k = 1..L/2, and k = 0 (which also gives the Nyquist value)
-  for (int e = threadIdx.x; e < NCOL * (L / 2 + 1); e += kZThreads) {
+  for (int e = lane; e < NCOL * (L / 2 + 1); e += 32) {
     const int col = e / (L / 2 + 1), k = e % (L / 2 + 1);
     if (k == 0) {
       float2 z0 = s[Lay::phys(0, col)];
@@ -70,10 +68,10 @@ __device__ __forceinline__ void r2c_split(float2* s, float2* qv, const float2* t
 }
 
 template <int N, int NCOL>
-__device__ __forceinline__ void c2r_merge(float2* s, const float2* qv, const float2* tw) {
+__device__ __forceinline__ void c2r_merge(float2* s, const float2* qv, const float2* tw, int lane) {
   constexpr int L = N / 2;
   using Lay = RowLayout<L>;
-  for (int e = threadIdx.x; e < NCOL * (L / 2 + 1); e += kZThreads) {
+  for (int e = lane; e < NCOL * (L / 2 + 1); e += 32) {
     const int col = e / (L / 2 + 1), k = e % (L / 2 + 1);
     if (k == 0) {
       const float2 x0 = s[Lay::phys(0, col)], xl = qv[col];
@@ -94,75 +92,75 @@ __device__ __forceinline__ void c2r_merge(float2* s, const float2* qv, const flo
   }
 }
 
+constexpr int kZWarps = kZThreads / 32;
+
+template <int N, int MODE>
+struct ZWarpSmem {  // float2 slots of one warp's private region
+  static constexpr int NF = (MODE == Z_DELTA) ? 1 : 3;
+  static constexpr int kLines = (NF * RowLayout<N / 2>::kStride + 1) & ~1;   // even: keeps raw 16-B aligned
+  static constexpr int kQ = 4;                                  // Nyquist values (padded)
+  static constexpr int kRaw = (MODE == Z_DELTA) ? N : 0;        // 2 N floats of raw rows
+  static constexpr int v = kLines + kQ + kRaw + ((kLines + kQ + kRaw) & 1);
+};
+
 template <int N, int MODE, int NC>
 __global__ void __launch_bounds__(kZThreads) zpass_kernel(const ZArgs a) {
   constexpr int L = N / 2;
-  constexpr int ROWS = ZRows<N>::v;
   constexpr int NF = (MODE == Z_DELTA) ? 1 : NC;   // lines transformed per row
-  constexpr int NCOL = ROWS * NF;
   using Lay = RowLayout<L>;
+  constexpr int WS = ZWarpSmem<N, MODE>::v;
   extern __shared__ float4 zsm[];
-  float2* tw = reinterpret_cast<float2*>(zsm);
-  float2* qv = tw + N;                       // Nyquist values, one per line
-  float2* s = qv + NCOL + (NCOL & 1);        // lines
-  __shared__ double red_sh[kZThreads / 32];
+  float2* tw = reinterpret_cast<float2*>(zsm);                       // N twiddles
+  float* taps = reinterpret_cast<float*>(tw + N);                    // N floats (Z_DELTA)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* s = tw + N + N / 2 + warp * WS;                            // this warp's lines
+  float2* qv = s + ZWarpSmem<N, MODE>::kLines;
+  float* raw = reinterpret_cast<float*>(qv + ZWarpSmem<N, MODE>::kQ);
+  __shared__ double red_sh[kZWarps];
 
   for (int m = threadIdx.x; m < N; m += kZThreads) tw[m] = a.tw[m];
+  if (MODE == Z_DELTA)
+    for (int j = threadIdx.x; j < a.ntap; j += kZThreads) taps[j] = a.taps[j];
+  __syncthreads();
+
   float acc0 = 0.f, acc1 = 0.f;
   constexpr bool kInverse = (MODE == Z_INV || MODE == Z_PROJ || MODE == Z_FINAL);
-  constexpr int kRowBlocks = N * N / ROWS;
+  float inv_alpha = 0.f, thr = 0.f;
+  const int nin = a.uniform ? 1 : 2;
+  if (MODE == Z_DELTA) {
+    const double* red = a.red;
+    inv_alpha = a.uniform ? (float)((double)N * N * N / red[RED_SUM_WG]) : (float)(red[RED_SUM_WR] / red[RED_SUM_WG]);
+    thr = a.uniform ? 0.f : (float)(a.mask_frac * red[RED_SUM_WR] / red[RED_CNT_RPOS]);
+  }
 
-  // persistent: each CTA walks row blocks blockIdx.x, blockIdx.x + gridDim.x, ...
-  for (int rb = blockIdx.x; rb < kRowBlocks; rb += gridDim.x) {
-  const size_t row0 = (size_t)rb * ROWS;
-  __syncthreads();   // the previous block's stores have read s
-
-  if (kInverse) {
-    // load M rows (L complex) and the Nyquist values
-    for (int e = threadIdx.x; e < NC * ROWS * (L / 2); e += kZThreads) {
-      const int q = e / (ROWS * (L / 2));
-      const int rem = e % (ROWS * (L / 2));
-      const int row = rem / (L / 2), m2 = rem % (L / 2);
-      const float4 v = reinterpret_cast<const float4*>(a.f[q].M + (row0 + row) * L)[m2];
-      const int col = q * ROWS + row;
-      s[Lay::phys(2 * m2, col)] = make_float2(v.x, v.y);
-      s[Lay::phys(2 * m2 + 1, col)] = make_float2(v.z, v.w);
-    }
-    for (int e = threadIdx.x; e < NC * ROWS; e += kZThreads) {
-      const int q = e / ROWS, row = e % ROWS;
-      qv[q * ROWS + row] = a.f[q].Q[row0 + row];
-    }
-    __syncthreads();
-    c2r_merge<N, NCOL>(s, qv, tw);
-    __syncthreads();
-    Plan<L>::template run<NCOL, kZThreads, true, Lay, 2>(s, tw);
-  } else {
-    // load real rows of N floats as L packed complex values
-    const int nin = (MODE == Z_DELTA) ? (a.uniform ? 1 : 2) : NC;
-    if (MODE == Z_DELTA) {
-      // rows of rho_g (and rho_r) already smoothed along x and y: apply the z factor of the
-      // Gaussian as a periodic convolution, then form delta (Sec. 3.2) node by node
-      const double* red = a.red;
-      const float inv_alpha = a.uniform ? (float)((double)N * N * N / red[RED_SUM_WG])
-                                        : (float)(red[RED_SUM_WR] / red[RED_SUM_WG]);
-      const float thr = a.uniform ? 0.f : (float)(a.mask_frac * red[RED_SUM_WR] / red[RED_CNT_RPOS]);
-      float* raw = reinterpret_cast<float*>(s + NCOL * Lay::kStride);   // nin * ROWS * N
-      float* taps = raw + 2 * ROWS * N;                                 // ntap
-      for (int j = threadIdx.x; j < a.ntap; j += kZThreads) taps[j] = a.taps[j];
-      for (int e = threadIdx.x; e < nin * ROWS * (N / 4); e += kZThreads) {
-        const int q = e / (ROWS * (N / 4));
-        const int rem = e % (ROWS * (N / 4));
-        const int row = rem / (N / 4), m4 = rem % (N / 4);
-        reinterpret_cast<float4*>(raw + (q * ROWS + row) * N)[m4] =
-            reinterpret_cast<const float4*>(a.f[q].M + (row0 + row) * L)[m4];
+  for (size_t row = (size_t)blockIdx.x * kZWarps + warp; row < (size_t)N * N; row += (size_t)gridDim.x * kZWarps) {
+    if (kInverse) {
+      // half-complex rows (L values) and Nyquist values of every component
+      for (int e = lane; e < NC * (L / 2); e += 32) {
+        const int q = e / (L / 2), m2 = e % (L / 2);
+        const float4 v = reinterpret_cast<const float4*>(a.f[q].M + row * L)[m2];
+        s[Lay::phys(2 * m2, q)] = make_float2(v.x, v.y);
+        s[Lay::phys(2 * m2 + 1, q)] = make_float2(v.z, v.w);
       }
-      __syncthreads();
-      for (int e = threadIdx.x; e < ROWS * N; e += kZThreads) {
-        const int row = e / N, z = e % N;
+      if (lane < NC) qv[lane] = a.f[lane].Q[row];
+      __syncwarp();
+      c2r_merge<N, NF>(s, qv, tw, lane);
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < NF; ++q) Plan<L>::template run<1, 32, true, Lay, 2, true>(s + q * Lay::kStride, tw);
+    } else if (MODE == Z_DELTA) {
+      // rows of rho_g (and rho_r) smoothed along x and y: z factor of the Gaussian as a periodic
+      // convolution, then delta (Sec. 3.2) node by node
+      for (int e = lane; e < nin * (N / 4); e += 32) {
+        const int q = e / (N / 4), m4 = e % (N / 4);
+        reinterpret_cast<float4*>(raw + q * N)[m4] = reinterpret_cast<const float4*>(a.f[q].M + row * L)[m4];
+      }
+      __syncwarp();
+      const float* rg = raw;
+      const float* rr = raw + N;
+      for (int z = lane; z < N; z += 32) {
         int idx = z + a.t0;
         if (idx < 0) idx += N;
-        const float* rg = raw + row * N;
-        const float* rr = raw + (ROWS + row) * N;
         float g = 0.f, r = 0.f;
         if (nin == 1) {
           for (int j = 0; j < a.ntap; ++j) {
@@ -188,41 +186,36 @@ __global__ void __launch_bounds__(kZThreads) zpass_kernel(const ZArgs a) {
           d = logf(fmaxf(1.f + d, 1e-6f));
           acc0 += d;
         }
-        if (a.delta_real) a.delta_real[(row0 + row) * N + z] = d;
-        reinterpret_cast<float*>(s + Lay::phys(z >> 1, row))[z & 1] = d;
+        if (a.delta_real) a.delta_real[row * N + z] = d;
+        reinterpret_cast<float*>(s + Lay::phys(z >> 1, 0))[z & 1] = d;
       }
+      __syncwarp();
     } else {
-      for (int e = threadIdx.x; e < NC * ROWS * (L / 2); e += kZThreads) {
-        const int q = e / (ROWS * (L / 2));
-        const int rem = e % (ROWS * (L / 2));
-        const int row = rem / (L / 2), m2 = rem % (L / 2);
-        const float4 v = reinterpret_cast<const float4*>(a.f[q].M + (row0 + row) * L)[m2];
-        const int col = q * ROWS + row;
-        if (a.stats && q == 1)  // nodes that received random mass
-          acc1 += (v.x > 0.f) + (v.y > 0.f) + (v.z > 0.f) + (v.w > 0.f);
-        s[Lay::phys(2 * m2, col)] = make_float2(v.x, v.y);
-        s[Lay::phys(2 * m2 + 1, col)] = make_float2(v.z, v.w);
+      // real rows of N floats as L packed complex values
+      for (int e = lane; e < NC * (L / 2); e += 32) {
+        const int q = e / (L / 2), m2 = e % (L / 2);
+        const float4 v = reinterpret_cast<const float4*>(a.f[q].M + row * L)[m2];
+        s[Lay::phys(2 * m2, q)] = make_float2(v.x, v.y);
+        s[Lay::phys(2 * m2 + 1, q)] = make_float2(v.z, v.w);
       }
+      __syncwarp();
     }
-    __syncthreads();
-  }
 
-  if (MODE == Z_PROJ || MODE == Z_FINAL) {
-    // s holds Psi_j(x, y, z) for the rows, z = 2m (.x) and 2m + 1 (.y)
     if (MODE == Z_PROJ) {
+      // s holds Psi_j(x, y, z), z = 2m (.x) and 2m + 1 (.y): P = coef (Psi.r) r (Eq. Nusser)
       const Geometry& g = a.g;
-      for (int e = threadIdx.x; e < ROWS * L; e += kZThreads) {
-        const int row = e / L, m = e % L;
-        const size_t rr = row0 + row;
-        const int ix = (int)(rr / N), iy = (int)(rr % N);
-        float2 p0 = s[Lay::phys(m, 0 * ROWS + row)];
-        float2 p1 = s[Lay::phys(m, 1 * ROWS + row)];
-        float2 p2 = s[Lay::phys(m, 2 * ROWS + row)];
+      const int ix = (int)(row / N), iy = (int)(row % N);
+      float dx = 0.f, dy = 0.f;
+      if (g.los_mode != 1) {
+        dx = g.off[ix];
+        dy = g.off[N + iy];
+      }
+      for (int m = lane; m < L; m += 32) {
+        const float2 p0 = s[Lay::phys(m, 0)], p1 = s[Lay::phys(m, 1)], p2 = s[Lay::phys(m, 2)];
         float rx0, ry0, rz0, rx1, ry1, rz1;
         if (g.los_mode == 1) {
           rx0 = rx1 = g.los.x; ry0 = ry1 = g.los.y; rz0 = rz1 = g.los.z;
         } else {
-          const float dx = g.off[ix], dy = g.off[N + iy];
           const float dz0 = g.off[2 * N + 2 * m], dz1 = g.off[2 * N + 2 * m + 1];
           const float q0 = fmaf(dx, dx, fmaf(dy, dy, dz0 * dz0));
           const float q1 = fmaf(dx, dx, fmaf(dy, dy, dz1 * dz1));
@@ -233,47 +226,36 @@ __global__ void __launch_bounds__(kZThreads) zpass_kernel(const ZArgs a) {
         }
         const float u0 = a.coef * fmaf(p0.x, rx0, fmaf(p1.x, ry0, p2.x * rz0));
         const float u1 = a.coef * fmaf(p0.y, rx1, fmaf(p1.y, ry1, p2.y * rz1));
-        s[Lay::phys(m, 0 * ROWS + row)] = make_float2(u0 * rx0, u1 * rx1);
-        s[Lay::phys(m, 1 * ROWS + row)] = make_float2(u0 * ry0, u1 * ry1);
-        s[Lay::phys(m, 2 * ROWS + row)] = make_float2(u0 * rz0, u1 * rz1);
+        s[Lay::phys(m, 0)] = make_float2(u0 * rx0, u1 * rx1);
+        s[Lay::phys(m, 1)] = make_float2(u0 * ry0, u1 * ry1);
+        s[Lay::phys(m, 2)] = make_float2(u0 * rz0, u1 * rz1);
       }
-      __syncthreads();
+      __syncwarp();
     }
+
+    if (MODE == Z_INV || MODE == Z_FINAL) {
+      for (int e = lane; e < NC * (L / 2); e += 32) {
+        const int q = e / (L / 2), m2 = e % (L / 2);
+        const float2 v0 = s[Lay::phys(2 * m2, q)], v1 = s[Lay::phys(2 * m2 + 1, q)];
+        reinterpret_cast<float4*>(a.f[q].M + row * L)[m2] = make_float4(v0.x, v0.y, v1.x, v1.y);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < NF; ++q) Plan<L>::template run<1, 32, false, Lay, 2, true>(s + q * Lay::kStride, tw);
+      r2c_split<N, NF>(s, qv, tw, lane);
+      __syncwarp();
+      for (int e = lane; e < NF * (L / 2); e += 32) {
+        const int q = e / (L / 2), m2 = e % (L / 2);
+        const float2 v0 = s[Lay::phys(2 * m2, q)], v1 = s[Lay::phys(2 * m2 + 1, q)];
+        float2* dst = (MODE == Z_DELTA) ? a.dout.M : a.f[q].M;
+        reinterpret_cast<float4*>(dst + row * L)[m2] = make_float4(v0.x, v0.y, v1.x, v1.y);
+      }
+      if (lane < NF) ((MODE == Z_DELTA) ? a.dout.Q : a.f[lane].Q)[row] = qv[lane];
+    }
+    __syncwarp();   // the stores above read s before the next row overwrites it
   }
 
-  if (MODE == Z_INV || MODE == Z_FINAL) {
-    // store real rows
-    for (int e = threadIdx.x; e < NC * ROWS * (L / 2); e += kZThreads) {
-      const int q = e / (ROWS * (L / 2));
-      const int rem = e % (ROWS * (L / 2));
-      const int row = rem / (L / 2), m2 = rem % (L / 2);
-      const int col = q * ROWS + row;
-      const float2 v0 = s[Lay::phys(2 * m2, col)], v1 = s[Lay::phys(2 * m2 + 1, col)];
-      reinterpret_cast<float4*>(a.f[q].M + (row0 + row) * L)[m2] = make_float4(v0.x, v0.y, v1.x, v1.y);
-    }
-  } else {
-    // forward: FFT, split, store half complex rows + Nyquist
-    Plan<L>::template run<NCOL, kZThreads, false, Lay, 2>(s, tw);
-    r2c_split<N, NCOL>(s, qv, tw);
-    __syncthreads();
-    for (int e = threadIdx.x; e < NCOL * (L / 2); e += kZThreads) {
-      const int col = e / (L / 2), m2 = e % (L / 2);
-      const int q = col / ROWS, row = col % ROWS;
-      const float2 v0 = s[Lay::phys(2 * m2, col)], v1 = s[Lay::phys(2 * m2 + 1, col)];
-      float2* dst = (MODE == Z_DELTA) ? a.dout.M : a.f[q].M;
-      reinterpret_cast<float4*>(dst + (row0 + row) * L)[m2] = make_float4(v0.x, v0.y, v1.x, v1.y);
-    }
-    for (int e = threadIdx.x; e < NCOL; e += kZThreads) {
-      const int q = e / ROWS, row = e % ROWS;
-      float2* dst = (MODE == Z_DELTA) ? a.dout.Q : a.f[q].Q;
-      dst[row0 + row] = qv[e];
-    }
-  }
-
-  }  // row blocks
-
-  const bool want_red = (MODE == Z_DELTA) || (MODE == Z_FWD && a.stats);
-  if (want_red) {
+  if (MODE == Z_DELTA) {
     double r0 = block_sum((double)acc0, red_sh);
     double r1 = block_sum((double)acc1, red_sh);
     if (threadIdx.x == 0) {
@@ -285,9 +267,8 @@ __global__ void __launch_bounds__(kZThreads) zpass_kernel(const ZArgs a) {
 
 template <int N, int NC>
 constexpr size_t zpass_smem(int mode) {
-  return sizeof(float2) * (N + 2 * ZRows<N>::v * NC + 2 +
-                           (size_t)ZRows<N>::v * (mode == Z_DELTA ? 1 : NC) * RowLayout<N / 2>::kStride) +
-         (mode == Z_DELTA ? sizeof(float) * ((size_t)2 * ZRows<N>::v * N + N) : 0);
+  return sizeof(float2) * ((size_t)N + N / 2 +
+                           (size_t)kZWarps * (mode == Z_DELTA ? ZWarpSmem<N, Z_DELTA>::v : ZWarpSmem<N, Z_PROJ>::v));
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -512,15 +493,35 @@ static cudaError_t launch_with_smem(K kern, int blocks, int threads, size_t smem
 
 template <int N>
 struct MeshImpl {
-  static constexpr int kZBlocks = N * N / ZRows<N>::v;   // row blocks (upper bound of the Z grid)
+  static constexpr int kZBlocks = N * N / kZWarps;   // rows / warps per CTA: upper bound of the Z grid
   static constexpr int kSBlocks = N * ((N / 2) / SCols<N>::v) + N / SCols<N>::v;
 
-  static cudaError_t zpass(int mode, int nc, const ZArgs& a, cudaStream_t st) {
-#define RG_Z(M_, NC_)                                                                                   \
-  if (mode == M_ && nc == NC_)                                                                          \
-    return launch_with_smem(zpass_kernel<N, M_, NC_>, zgrid(), kZThreads, zpass_smem<N, NC_>(M_), st, &a);
-    RG_Z(Z_FWD, 1) RG_Z(Z_FWD, 2) RG_Z(Z_INV, 1) RG_Z(Z_INV, 2) RG_Z(Z_DELTA, 2) RG_Z(Z_PROJ, 3)
-    RG_Z(Z_FINAL, 3)
+  // persistent Z launch: exactly as many CTAs as fit on the device at once (occupancy x SMs),
+  // never more than one row per warp
+  template <int M_, int NC_>
+  static cudaError_t zlaunch(const ZArgs& a, cudaStream_t st, int* grid_out) {
+    static int grid = 0;
+    const size_t smem = zpass_smem<N, NC_>(M_);
+    const void* k = (const void*)zpass_kernel<N, M_, NC_>;
+    if (grid == 0) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      int dev = 0, sm = 0, occ = 0;
+      if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+      if ((e = cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kZThreads, smem)) != cudaSuccess) return e;
+      if (occ < 1) return cudaErrorInvalidConfiguration;
+      grid = occ * sm < kZBlocks ? occ * sm : kZBlocks;
+    }
+    if (grid_out) *grid_out = grid;
+    void* args[] = {const_cast<ZArgs*>(&a)};
+    return cudaLaunchKernel(k, dim3(grid), dim3(kZThreads), args, smem, st);
+  }
+
+  static cudaError_t zpass(int mode, int nc, const ZArgs& a, cudaStream_t st, int* grid_out) {
+#define RG_Z(M_, NC_) \
+  if (mode == M_ && nc == NC_) return zlaunch<M_, NC_>(a, st, grid_out);
+    RG_Z(Z_FWD, 1) RG_Z(Z_INV, 1) RG_Z(Z_DELTA, 2) RG_Z(Z_PROJ, 3) RG_Z(Z_FINAL, 3)
 #undef RG_Z
     return cudaErrorInvalidValue;
   }
@@ -538,22 +539,8 @@ struct MeshImpl {
     return cudaErrorInvalidValue;
   }
 
-  // persistent Z grid: 4 CTAs per SM (register-bound at 256 threads), at most one per row block
-  static int zgrid() {
-    static const int g = [] {
-      int dev = 0, sm = 152;
-      if (cudaGetDevice(&dev) != cudaSuccess ||
-          cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-        cudaGetLastError();
-        sm = 152;
-      }
-      return kZBlocks < 4 * sm ? kZBlocks : 4 * sm;
-    }();
-    return g;
-  }
-
   static const MeshKernels* table() {
-    static const MeshKernels t = {N, kZBlocks, kSBlocks, &zgrid, &zpass, &spass};
+    static const MeshKernels t = {N, kZBlocks, kSBlocks, &zpass, &spass};
     return &t;
   }
 };

@@ -252,8 +252,8 @@ double sbytes(const recon_handle* h, int mode, int nc) {
   return 2.0 * nc * cfield(h);
 }
 
-recon_status run_z(recon_handle* h, int mode, int nc, const ZArgs& a) {
-  RG_CUDA(timed(h, zkind(mode), zbytes(h, mode, nc, a), [&] { return h->mk->zpass(mode, nc, a, h->st); }));
+recon_status run_z(recon_handle* h, int mode, int nc, const ZArgs& a, int* grid = nullptr) {
+  RG_CUDA(timed(h, zkind(mode), zbytes(h, mode, nc, a), [&] { return h->mk->zpass(mode, nc, a, h->st, grid); }));
   return RECON_OK;
 }
 
@@ -582,8 +582,9 @@ recon_status recon_smooth(recon_handle* h) {
     a.taps = h->taps;
     a.ntap = h->ntap;
     a.t0 = h->t0;
-    RG_TRY(run_z(h, Z_DELTA, 2, a));
-    RG_TRY(finalize(h, h->mk->z_grid(), 2, RED_SUM_LOG, 0));
+    int zg = 0;
+    RG_TRY(run_z(h, Z_DELTA, 2, a, &zg));
+    RG_TRY(finalize(h, zg, 2, RED_SUM_LOG, 0));
   }
   RG_TRY(ypass(h, S_FWD, 1, &h->D));
   h->state = ST_SMOOTHED;

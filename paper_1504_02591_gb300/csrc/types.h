@@ -47,7 +47,6 @@ struct ZArgs {
   const float2* tw;       // exp(-2 pi i m / N), m < N
   double* partials;       // per-block reduction partials (4 per block)
   const double* red;      // reduction block (read by Z_DELTA)
-  int stats;              // Z_FWD: count the nodes of f[1] (unsmoothed randoms) that are > 0
   float coef;             // Z_PROJ: (1 - c) multiplier of the projection
   // Z_DELTA
   Field dout;             // delta on the (z-transformed) half grid
@@ -77,10 +76,10 @@ struct SArgs {
 // Kernels of one mesh size (one table per supported N).
 struct MeshKernels {
   int n;
-  int z_blocks;           // row blocks of a Z pass (upper bound of its grid)
+  int z_blocks;           // upper bound of a Z pass grid (rows / warps per CTA)
   int s_blocks;           // CTAs of a strided pass
-  int (*z_grid)();        // CTAs actually launched by a Z pass (persistent)
-  cudaError_t (*zpass)(int mode, int nc, const ZArgs& a, cudaStream_t st);
+  // persistent Z pass; *grid_out receives the number of CTAs launched (its reduction partials)
+  cudaError_t (*zpass)(int mode, int nc, const ZArgs& a, cudaStream_t st, int* grid_out);
   cudaError_t (*spass)(int mode, int nc, int axis, const SArgs& a, cudaStream_t st);
 };
 
