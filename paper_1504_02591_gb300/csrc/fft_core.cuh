@@ -145,12 +145,15 @@ __device__ __forceinline__ void group_sync() {
   if (WARP) __syncwarp(); else __syncthreads();
 }
 
-template <int L, int NCOL, int T, int R, int NS, bool INV, class Lay, int TWS, bool WARP>
-__device__ __forceinline__ void stockham_stage(float2* __restrict__ s, const float2* __restrict__ tw) {
+// Stage twiddle tables.  A stage of radix R after NS points have been combined needs
+// w^(r k) = exp(-2 pi i r k / (NS R)) for r = 1..R-1, k = 0..NS-1; they are stored per stage as
+// [r - 1][k], so lanes with consecutive k read consecutive words.  OFF is the stage's offset in the
+// table of the whole plan.
+template <int L, int NCOL, int T, int R, int NS, int OFF, bool INV, class Lay, bool WARP>
+__device__ __forceinline__ void stockham_stage(float2* __restrict__ s, const float2* __restrict__ tab) {
   constexpr int NBL = L / R;
   constexpr int NB = NBL * NCOL;
   constexpr int PER = (NB + T - 1) / T;
-  constexpr int TWSTEP = L / (NS * R);
   const int tid = group_tid<WARP>();
   float2 v[PER][R];
 #pragma unroll
@@ -165,7 +168,7 @@ __device__ __forceinline__ void stockham_stage(float2* __restrict__ s, const flo
         const int k = j % NS;
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          float2 w = tw[(r * k * TWSTEP) * TWS];
+          float2 w = tab[OFF + (r - 1) * NS + k];
           if (INV) w.y = -w.y;
           v[p][r] = cmul(v[p][r], w);
         }
@@ -189,10 +192,33 @@ __device__ __forceinline__ void stockham_stage(float2* __restrict__ s, const flo
   group_sync<WARP>();
 }
 
-template <int L, int NCOL, int T, bool INV, class Lay, int TWS, bool WARP, int NS, int R, int... Rest>
-__device__ __forceinline__ void stockham_run(float2* s, const float2* tw) {
-  stockham_stage<L, NCOL, T, R, NS, INV, Lay, TWS, WARP>(s, tw);
-  if constexpr (sizeof...(Rest) > 0) stockham_run<L, NCOL, T, INV, Lay, TWS, WARP, NS * R, Rest...>(s, tw);
+template <int NS, int R>
+constexpr int stage_tab_size() { return NS > 1 ? (R - 1) * NS : 0; }
+
+template <int L, int NCOL, int T, bool INV, class Lay, bool WARP, int NS, int OFF, int R, int... Rest>
+__device__ __forceinline__ void stockham_run(float2* s, const float2* tab) {
+  stockham_stage<L, NCOL, T, R, NS, OFF, INV, Lay, WARP>(s, tab);
+  if constexpr (sizeof...(Rest) > 0)
+    stockham_run<L, NCOL, T, INV, Lay, WARP, NS * R, OFF + stage_tab_size<NS, R>(), Rest...>(s, tab);
+}
+
+// Fill the stage tables of a plan from the base table tw[m] = exp(-2 pi i m / (L TWS)).
+template <int L, int TWS, int NS, int OFF, int R, int... Rest>
+__device__ __forceinline__ void stockham_fill(float2* tab, const float2* tw, int tid, int nthr) {
+  if (NS > 1) {
+    constexpr int STEP = L / (NS * R);
+    for (int e = tid; e < (R - 1) * NS; e += nthr) {
+      const int r = 1 + e / NS, k = e % NS;
+      tab[OFF + e] = tw[(r * k * STEP) * TWS];
+    }
+  }
+  if constexpr (sizeof...(Rest) > 0) stockham_fill<L, TWS, NS * R, OFF + stage_tab_size<NS, R>(), Rest...>(tab, tw, tid, nthr);
+}
+
+template <int NS, int R, int... Rest>
+constexpr int plan_tab_size() {
+  if constexpr (sizeof...(Rest) > 0) return stage_tab_size<NS, R>() + plan_tab_size<NS * R, Rest...>();
+  else return stage_tab_size<NS, R>();
 }
 
 // Radix plan per line length.
@@ -201,9 +227,14 @@ struct Plan;
 #define RG_PLAN(LEN, ...)                                                                   \
   template <>                                                                               \
   struct Plan<LEN> {                                                                        \
-    template <int NCOL, int T, bool INV, class Lay, int TWS, bool WARP = false>             \
-    __device__ __forceinline__ static void run(float2* s, const float2* tw) {               \
-      stockham_run<LEN, NCOL, T, INV, Lay, TWS, WARP, 1, __VA_ARGS__>(s, tw);              \
+    static constexpr int kTab = plan_tab_size<1, __VA_ARGS__>();                            \
+    template <int NCOL, int T, bool INV, class Lay, bool WARP = false>                      \
+    __device__ __forceinline__ static void run(float2* s, const float2* tab) {              \
+      stockham_run<LEN, NCOL, T, INV, Lay, WARP, 1, 0, __VA_ARGS__>(s, tab);               \
+    }                                                                                       \
+    template <int TWS>                                                                      \
+    __device__ __forceinline__ static void fill(float2* tab, const float2* tw, int tid, int nthr) { \
+      stockham_fill<LEN, TWS, 1, 0, __VA_ARGS__>(tab, tw, tid, nthr);                      \
     }                                                                                       \
   };
 RG_PLAN(16, 4, 4)

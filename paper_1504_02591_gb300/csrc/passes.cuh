@@ -13,7 +13,6 @@
 namespace rg {
 
 constexpr int kZThreads = 256;
-constexpr int kSThreads = 256;
 
 template <int N>
 struct SCols {  // adjacent columns in one strided tile
@@ -109,16 +108,19 @@ __global__ void __launch_bounds__(kZThreads) zpass_kernel(const ZArgs a) {
   constexpr int NF = (MODE == Z_DELTA) ? 1 : NC;   // lines transformed per row
   using Lay = RowLayout<L>;
   constexpr int WS = ZWarpSmem<N, MODE>::v;
+  constexpr int TABZ = (Plan<L>::kTab + 1) & ~1;
   extern __shared__ float4 zsm[];
-  float2* tw = reinterpret_cast<float2*>(zsm);                       // N twiddles
-  float* taps = reinterpret_cast<float*>(tw + N);                    // N floats (Z_DELTA)
+  float2* tw = reinterpret_cast<float2*>(zsm);                       // exp(-2 pi i k / N), k <= L
+  float2* tab = tw + L + 2;                                          // stage twiddles of the L-point FFT
+  float* taps = reinterpret_cast<float*>(tab + TABZ);                // N floats (Z_DELTA)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* s = tw + N + N / 2 + warp * WS;                            // this warp's lines
+  float2* s = tab + TABZ + N / 2 + warp * WS;                        // this warp's lines
   float2* qv = s + ZWarpSmem<N, MODE>::kLines;
   float* raw = reinterpret_cast<float*>(qv + ZWarpSmem<N, MODE>::kQ);
   __shared__ double red_sh[kZWarps];
 
-  for (int m = threadIdx.x; m < N; m += kZThreads) tw[m] = a.tw[m];
+  for (int m = threadIdx.x; m <= L; m += kZThreads) tw[m] = a.tw[m];
+  for (int m = threadIdx.x; m < Plan<L>::kTab; m += kZThreads) tab[m] = a.tab[m];
   if (MODE == Z_DELTA)
     for (int j = threadIdx.x; j < a.ntap; j += kZThreads) taps[j] = a.taps[j];
   __syncthreads();
@@ -147,7 +149,7 @@ __global__ void __launch_bounds__(kZThreads) zpass_kernel(const ZArgs a) {
       c2r_merge<N, NF>(s, qv, tw, lane);
       __syncwarp();
 #pragma unroll
-      for (int q = 0; q < NF; ++q) Plan<L>::template run<1, 32, true, Lay, 2, true>(s + q * Lay::kStride, tw);
+      for (int q = 0; q < NF; ++q) Plan<L>::template run<1, 32, true, Lay, true>(s + q * Lay::kStride, tab);
     } else if (MODE == Z_DELTA) {
       // rows of rho_g (and rho_r) smoothed along x and y: z factor of the Gaussian as a periodic
       // convolution, then delta (Sec. 3.2) node by node
@@ -241,7 +243,7 @@ __global__ void __launch_bounds__(kZThreads) zpass_kernel(const ZArgs a) {
       }
     } else {
 #pragma unroll
-      for (int q = 0; q < NF; ++q) Plan<L>::template run<1, 32, false, Lay, 2, true>(s + q * Lay::kStride, tw);
+      for (int q = 0; q < NF; ++q) Plan<L>::template run<1, 32, false, Lay, true>(s + q * Lay::kStride, tab);
       r2c_split<N, NF>(s, qv, tw, lane);
       __syncwarp();
       for (int e = lane; e < NF * (L / 2); e += 32) {
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(kZThreads) zpass_kernel(const ZArgs a) {
 
 template <int N, int NC>
 constexpr size_t zpass_smem(int mode) {
-  return sizeof(float2) * ((size_t)N + N / 2 +
+  return sizeof(float2) * ((size_t)N / 2 + 2 + ((Plan<N / 2>::kTab + 1) & ~1) + N / 2 +
                            (size_t)kZWarps * (mode == Z_DELTA ? ZWarpSmem<N, Z_DELTA>::v : ZWarpSmem<N, Z_PROJ>::v));
 }
 
@@ -310,75 +312,88 @@ __device__ __forceinline__ Tile tile_of(int t) {
   return r;
 }
 
-template <int N, int C>
+template <int N, int C, int T>
 __device__ __forceinline__ void tile_load(float2* s, const float2* __restrict__ P, const Tile& t) {
   using Lay = ColLayout<C>;
   if (t.cs == 1) {
-    for (int e = threadIdx.x; e < N * (C / 2); e += kSThreads) {
+#pragma unroll 4
+    for (int e = threadIdx.x; e < N * (C / 2); e += T) {
       const int i = e / (C / 2), cp = e % (C / 2);
       const float4 v = *reinterpret_cast<const float4*>(P + t.base + (size_t)i * t.ls + 2 * cp);
       s[Lay::phys(i, 2 * cp)] = make_float2(v.x, v.y);
       s[Lay::phys(i, 2 * cp + 1)] = make_float2(v.z, v.w);
     }
   } else {
-    for (int e = threadIdx.x; e < N * C; e += kSThreads) {
+    for (int e = threadIdx.x; e < N * C; e += T) {
       const int c = e / N, i = e % N;
       s[Lay::phys(i, c)] = P[t.base + (size_t)c * t.cs + (size_t)i * t.ls];
     }
   }
 }
 
-template <int N, int C>
+template <int N, int C, int T>
 __device__ __forceinline__ void tile_store(const float2* s, float2* __restrict__ P, const Tile& t) {
   using Lay = ColLayout<C>;
   if (t.cs == 1) {
-    for (int e = threadIdx.x; e < N * (C / 2); e += kSThreads) {
+    for (int e = threadIdx.x; e < N * (C / 2); e += T) {
       const int i = e / (C / 2), cp = e % (C / 2);
       const float2 v0 = s[Lay::phys(i, 2 * cp)], v1 = s[Lay::phys(i, 2 * cp + 1)];
       *reinterpret_cast<float4*>(P + t.base + (size_t)i * t.ls + 2 * cp) = make_float4(v0.x, v0.y, v1.x, v1.y);
     }
   } else {
-    for (int e = threadIdx.x; e < N * C; e += kSThreads) {
+    for (int e = threadIdx.x; e < N * C; e += T) {
       const int c = e / N, i = e % N;
       P[t.base + (size_t)c * t.cs + (size_t)i * t.ls] = s[Lay::phys(i, c)];
     }
   }
 }
 
+// Threads of a strided CTA: the 3-component k-space passes use 512 so that their two resident CTAs
+// (the 96 KB tile bounds them) still give 32 warps per SM; the plain passes move one component
+// per CTA with 256 threads and fit 4 CTAs per SM.
+template <int MODE>
+struct SThreads {
+  static constexpr int v = (MODE == S_DELTA || MODE == S_ITER) ? 512 : 256;
+  static constexpr int minb = (MODE == S_DELTA || MODE == S_ITER) ? 2 : 4;
+};
+
 template <int N, int MODE, int NC, int AXIS>
-__global__ void __launch_bounds__(kSThreads, 2) spass_kernel(const SArgs a) {
+__global__ void __launch_bounds__(SThreads<MODE>::v, SThreads<MODE>::minb) spass_kernel(const SArgs a) {
+  constexpr int T = SThreads<MODE>::v;
   constexpr int C = SCols<N>::v;
   constexpr int H = N / 2;
   constexpr int NS = (MODE == S_DELTA || MODE == S_ITER) ? 3 : NC;   // smem slots
   using Lay = ColLayout<C>;
+  constexpr int TABS = (Plan<N>::kTab + 1) & ~1;
   extern __shared__ float4 ssm[];
-  float2* tw = reinterpret_cast<float2*>(ssm);
-  float2* s = tw + N;
-  __shared__ double red_sh[kSThreads / 32];
+  float2* tw = reinterpret_cast<float2*>(ssm);   // stage twiddles of the N-point FFT
+  float2* s = tw + TABS;
+  __shared__ double red_sh[T / 32];
+  const int q0 = blockIdx.y;   // plain passes: the component this CTA transforms
 
-  for (int m = threadIdx.x; m < N; m += kSThreads) tw[m] = a.tw[m];
+  for (int m = threadIdx.x; m < Plan<N>::kTab; m += T) tw[m] = a.tab[m];
   const Tile t = tile_of<N, C, AXIS>(blockIdx.x);
 
   // ---- load
   if (MODE == S_DELTA) {
-    tile_load<N, C>(s, t.isQ ? a.dk.Q : a.dk.M, t);
+    tile_load<N, C, T>(s, t.isQ ? a.dk.Q : a.dk.M, t);
   } else {
 #pragma unroll
-    for (int q = 0; q < NC; ++q) tile_load<N, C>(s + q * N * C, t.isQ ? a.f[q].Q : a.f[q].M, t);
+    for (int q = 0; q < NC; ++q) tile_load<N, C, T>(s + q * N * C, t.isQ ? a.f[q0 + q].Q : a.f[q0 + q].M, t);
   }
   __syncthreads();
 
   // ---- S_ITER: fetch delta(k) and the previous source for this thread's elements now, so the
   // loads are in flight during the forward transforms instead of inside the element loop
-  constexpr int PE = (N * C + kSThreads - 1) / kSThreads;
+  constexpr int PE = (N * C + T - 1) / T;
   float2 dkr[MODE == S_ITER ? PE : 1], spr[MODE == S_ITER ? PE : 1];
   if (MODE == S_ITER) {
     const float2* __restrict__ dkp = t.isQ ? a.dk.Q : a.dk.M;
     const float2* __restrict__ spp = t.isQ ? a.sbuf.Q : a.sbuf.M;
 #pragma unroll
     for (int k = 0; k < PE; ++k) {
-      const int e = threadIdx.x + k * kSThreads;
-      if ((N * C) % kSThreads == 0 || e < N * C) {
+      const int e = threadIdx.x + k * T;
+      if ((N * C) % T == 0 || e < N * C) {
         const int i = e / C, c = e % C;
         const size_t gi = t.base + (size_t)i * t.ls + (size_t)c * t.cs;
         dkr[k] = dkp[gi];
@@ -390,9 +405,9 @@ __global__ void __launch_bounds__(kSThreads, 2) spass_kernel(const SArgs a) {
   // ---- forward transform along the line
   if (MODE == S_FWD || MODE == S_ITER) {
 #pragma unroll
-    for (int q = 0; q < NC; ++q) Plan<N>::template run<C, kSThreads, false, Lay, 1>(s + q * N * C, tw);
+    for (int q = 0; q < NC; ++q) Plan<N>::template run<C, T, false, Lay>(s + q * N * C, tw);
   } else if (MODE == S_DELTA) {
-    if (!a.d_is_k) Plan<N>::template run<C, kSThreads, false, Lay, 1>(s, tw);
+    if (!a.d_is_k) Plan<N>::template run<C, T, false, Lay>(s, tw);
   }
 
   float d2 = 0.f, s2 = 0.f;
@@ -400,8 +415,8 @@ __global__ void __launch_bounds__(kSThreads, 2) spass_kernel(const SArgs a) {
     const Geometry& g = a.g;
 #pragma unroll
     for (int k = 0; k < PE; ++k) {
-      const int e = threadIdx.x + k * kSThreads;
-      if ((N * C) % kSThreads != 0 && e >= N * C) break;
+      const int e = threadIdx.x + k * T;
+      if ((N * C) % T != 0 && e >= N * C) break;
       const int i = e / C, c = e % C;
       const int mx = (i < H) ? i : i - N;
       int ky, kz;
@@ -457,12 +472,12 @@ __global__ void __launch_bounds__(kSThreads, 2) spass_kernel(const SArgs a) {
   // ---- inverse transform along the line
   if (MODE == S_INV || MODE == S_DELTA || MODE == S_ITER) {
 #pragma unroll
-    for (int q = 0; q < NS; ++q) Plan<N>::template run<C, kSThreads, true, Lay, 1>(s + q * N * C, tw);
+    for (int q = 0; q < NS; ++q) Plan<N>::template run<C, T, true, Lay>(s + q * N * C, tw);
   }
 
   // ---- store
 #pragma unroll
-  for (int q = 0; q < NS; ++q) tile_store<N, C>(s + q * N * C, t.isQ ? a.f[q].Q : a.f[q].M, t);
+  for (int q = 0; q < NS; ++q) tile_store<N, C, T>(s + q * N * C, t.isQ ? a.f[q0 + q].Q : a.f[q0 + q].M, t);
 
   if (MODE == S_ITER) {
     double r0 = block_sum((double)d2, red_sh);
@@ -476,7 +491,16 @@ __global__ void __launch_bounds__(kSThreads, 2) spass_kernel(const SArgs a) {
 
 template <int N>
 constexpr size_t spass_smem(int nslots) {
-  return sizeof(float2) * ((size_t)N + (size_t)nslots * N * SCols<N>::v);
+  return sizeof(float2) * ((size_t)((Plan<N>::kTab + 1) & ~1) + (size_t)nslots * N * SCols<N>::v);
+}
+
+// Stage twiddle tables of the N-point (strided passes) and N/2-point (Z pass) plans, built once
+// from the float32 table of exp(-2 pi i m / N) that the host computed in float64.
+template <int N>
+__global__ void build_tables_kernel(const float2* __restrict__ tw, float2* tabS, float2* tabZ) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  Plan<N>::template fill<1>(tabS, tw, tid, nthr);
+  Plan<N / 2>::template fill<2>(tabZ, tw, tid, nthr);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -526,21 +550,40 @@ struct MeshImpl {
     return cudaErrorInvalidValue;
   }
 
+  template <int M_, int NC_, int AX_>
+  static cudaError_t slaunch(const SArgs& a, cudaStream_t st, int ncomp) {
+    const size_t smem = spass_smem<N>((M_ == S_DELTA || M_ == S_ITER) ? 3 : NC_);
+    const void* k = (const void*)spass_kernel<N, M_, NC_, AX_>;
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    void* args[] = {const_cast<SArgs*>(&a)};
+    return cudaLaunchKernel(k, dim3(kSBlocks, ncomp), dim3(SThreads<M_>::v), args, smem, st);
+  }
+
   static cudaError_t spass(int mode, int nc, int axis, const SArgs& a, cudaStream_t st) {
-#define RG_S(M_, NC_, AX_)                                                                              \
-  if (mode == M_ && nc == NC_ && axis == AX_)                                                           \
-    return launch_with_smem(spass_kernel<N, M_, NC_, AX_>, kSBlocks, kSThreads,                         \
-                            spass_smem<N>((M_ == S_DELTA || M_ == S_ITER) ? 3 : NC_), st, &a);
-    RG_S(S_FWD, 1, AX_Y) RG_S(S_FWD, 2, AX_Y) RG_S(S_FWD, 3, AX_Y)
-    RG_S(S_INV, 1, AX_Y) RG_S(S_INV, 2, AX_Y) RG_S(S_INV, 3, AX_Y)
-    RG_S(S_FWD, 1, AX_X) RG_S(S_INV, 1, AX_X)
-    RG_S(S_DELTA, 1, AX_X) RG_S(S_ITER, 3, AX_X)
-#undef RG_S
+    if (nc < 1 || nc > 3) return cudaErrorInvalidValue;
+    // plain passes: one component per CTA, components along gridDim.y
+    if (mode == S_FWD && axis == AX_Y) return slaunch<S_FWD, 1, AX_Y>(a, st, nc);
+    if (mode == S_INV && axis == AX_Y) return slaunch<S_INV, 1, AX_Y>(a, st, nc);
+    if (mode == S_FWD && axis == AX_X) return slaunch<S_FWD, 1, AX_X>(a, st, nc);
+    if (mode == S_INV && axis == AX_X) return slaunch<S_INV, 1, AX_X>(a, st, nc);
+    if (mode == S_DELTA && axis == AX_X) return slaunch<S_DELTA, 1, AX_X>(a, st, 1);
+    if (mode == S_ITER && axis == AX_X && nc == 3) return slaunch<S_ITER, 3, AX_X>(a, st, 1);
     return cudaErrorInvalidValue;
   }
 
+  static cudaError_t build_tables(const float2* tw, float2* tabS, float2* tabZ, cudaStream_t st) {
+    build_tables_kernel<N><<<4, 256, 0, st>>>(tw, tabS, tabZ);
+    return cudaGetLastError();
+  }
+
   static const MeshKernels* table() {
-    static const MeshKernels t = {N, kZBlocks, kSBlocks, &zpass, &spass};
+    static const MeshKernels t = {N, kZBlocks, kSBlocks, Plan<N>::kTab, Plan<N / 2>::kTab, &zpass, &spass,
+                                  &build_tables};
     return &t;
   }
 };

@@ -59,7 +59,7 @@ enum State { ST_CREATED = 0, ST_DEPOSITED = 1, ST_SMOOTHED = 2, ST_ITERATED = 3 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t field_M, field_Q, field, tw, off, taps, red, partials, stage, total;
+  size_t field_M, field_Q, field, tw, tabs, tabz, off, taps, red, partials, stage, total;
 };
 
 Layout layout_for(int n) {
@@ -69,6 +69,8 @@ Layout layout_for(int n) {
   l.field_Q = align256((size_t)n * n * sizeof(float2));
   l.field = l.field_M + l.field_Q;
   l.tw = align256((size_t)n * sizeof(float2));
+  l.tabs = align256((size_t)mk->tab_s * sizeof(float2) + 16);
+  l.tabz = align256((size_t)mk->tab_z * sizeof(float2) + 16);
   l.off = align256((size_t)3 * n * sizeof(float));
   l.taps = align256((size_t)n * sizeof(float));
   l.red = align256(64 * sizeof(double));
@@ -78,7 +80,7 @@ Layout layout_for(int n) {
   if ((size_t)conv_blocks(n) > nb) nb = conv_blocks(n);
   l.partials = align256(nb * 4 * sizeof(double));
   l.stage = align256((size_t)kStageParticles * kStageBytesPer);
-  l.total = 5 * l.field + l.tw + l.off + l.taps + l.red + l.partials + l.stage;
+  l.total = 5 * l.field + l.tw + l.tabs + l.tabz + l.off + l.taps + l.red + l.partials + l.stage;
   return l;
 }
 
@@ -115,6 +117,8 @@ struct recon_handle {
   Layout lay{};
   Field V[3]{}, D{}, S{};
   float2* tw = nullptr;
+  float2* tabs = nullptr;   // stage twiddles, N-point plan
+  float2* tabz = nullptr;   // stage twiddles, N/2-point plan
   float* off = nullptr;
   float* taps = nullptr;   // smoothing kernel g[t0 .. t0 + ntap - 1]
   int ntap = 1, t0 = 0;
@@ -210,6 +214,7 @@ ZArgs zargs(recon_handle* h) {
   ZArgs a{};
   a.g = h->geo;
   a.tw = h->tw;
+  a.tab = h->tabz;
   a.partials = h->partials;
   a.red = h->red;
   a.coef = 1.f;
@@ -222,7 +227,7 @@ ZArgs zargs(recon_handle* h) {
 SArgs sargs(recon_handle* h) {
   SArgs a{};
   a.g = h->geo;
-  a.tw = h->tw;
+  a.tab = h->tabs;
   a.partials = h->partials;
   a.red = h->red;
   a.dk = h->D;
@@ -407,6 +412,10 @@ recon_status recon_create(const recon_params* p, void* stream, void* workspace, 
   b += h->lay.field;
   h->tw = (float2*)b;
   b += h->lay.tw;
+  h->tabs = (float2*)b;
+  b += h->lay.tabs;
+  h->tabz = (float2*)b;
+  b += h->lay.tabz;
   h->off = (float*)b;
   b += h->lay.off;
   h->taps = (float*)b;
@@ -460,6 +469,7 @@ recon_status recon_create(const recon_params* p, void* stream, void* workspace, 
         (e = cudaMemcpyAsync(h->tw, tw.data(), n * sizeof(float2), cudaMemcpyHostToDevice, h->st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(h->off, off.data(), 3 * n * sizeof(float), cudaMemcpyHostToDevice, h->st)) != cudaSuccess ||
         (e = cudaMemsetAsync(h->red, 0, h->lay.red, h->st)) != cudaSuccess ||
+        (e = h->mk->build_tables(h->tw, h->tabs, h->tabz, h->st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(h->st)) != cudaSuccess) {
       h->err = cudaGetErrorString(e);
       rs = RECON_ERR_CUDA;

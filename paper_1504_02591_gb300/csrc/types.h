@@ -45,6 +45,7 @@ struct ZArgs {
   Field f[3];             // fields transformed in place
   Geometry g;
   const float2* tw;       // exp(-2 pi i m / N), m < N
+  const float2* tab;      // stage twiddles of the N/2-point plan
   double* partials;       // per-block reduction partials (4 per block)
   const double* red;      // reduction block (read by Z_DELTA)
   float coef;             // Z_PROJ: (1 - c) multiplier of the projection
@@ -62,7 +63,7 @@ struct ZArgs {
 struct SArgs {
   Field f[3];             // fields transformed in place
   Geometry g;
-  const float2* tw;       // exp(-2 pi i m / N), m < N
+  const float2* tab;      // stage twiddles of the N-point plan
   double* partials;       // per-block partials (2 per block, S_ITER)
   const double* red;      // reduction block (S_DELTA reads the lognormal sum)
   Field dk;               // delta: partially transformed (S_DELTA input) / k-space (S_ITER)
@@ -78,9 +79,11 @@ struct MeshKernels {
   int n;
   int z_blocks;           // upper bound of a Z pass grid (rows / warps per CTA)
   int s_blocks;           // CTAs of a strided pass
+  int tab_s, tab_z;       // stage-twiddle table lengths (N-point and N/2-point plans)
   // persistent Z pass; *grid_out receives the number of CTAs launched (its reduction partials)
   cudaError_t (*zpass)(int mode, int nc, const ZArgs& a, cudaStream_t st, int* grid_out);
   cudaError_t (*spass)(int mode, int nc, int axis, const SArgs& a, cudaStream_t st);
+  cudaError_t (*build_tables)(const float2* tw, float2* tabS, float2* tabZ, cudaStream_t st);
 };
 
 const MeshKernels* mesh_kernels(int n);
