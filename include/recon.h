@@ -192,6 +192,30 @@ recon_status recon_get_timing(recon_handle* h, int kind, double* total_ms, int64
 /* Zero the launch counts and timings. */
 recon_status recon_reset_timing(recon_handle* h);
 
+/* CIC deposit for callers that cannot allocate device memory.  (The paper has no counterpart: it
+ * is a service entry point of this library.)  Some callers may not allocate: code that runs while
+ * a CUDA stream is being captured into a graph (cudaMalloc is not allowed there), plugins whose
+ * host application owns every device buffer through its own pool, and real-time pipelines that
+ * must not enter an allocator mid-run.  This call allocates nothing and uses no handle: the
+ * caller passes every input and output, and the only scratch (per-block partial sums of the
+ * weights) is a fixed 32 KB array inside the library's device image, kept by every device that
+ * loads the library until the process exits.
+ *   pos     device (n, 3) positions, dtype RECON_F64 or RECON_F32, in [0, box) up to periodic wrap
+ *   w       device (n) float32 weights or NULL (unit weights)
+ *   n       0 .. 67,108,864 particles per call (the scratch bound); larger n -> INVALID_ARG
+ *   nmesh   mesh side, 2 .. 2048; box > 0 is the side length
+ *   rho     device nmesh^3 float32, overwritten with the CIC density (zeroed first)
+ *   sum_w   device float64, overwritten with the sum of the weights
+ *   stream  cudaStream_t the work is ordered on
+ * The first call on each device looks up the scratch array's device address (once, with that
+ * device current); make that first call before any stream capture begins.  Every call shares the
+ * one scratch array, which keeps the last call's partial sums: calls that overlap on the GPU (on
+ * different streams, or from several host threads without ordering) race on it and must be
+ * serialised by the caller.  Errors: INVALID_ARG for bad arguments or too many particles, CUDA
+ * for a runtime error. */
+recon_status recon_cic_deposit_noalloc(const void* pos, int dtype, const float* w, int64_t n, int nmesh,
+                                       double box, float* rho, double* sum_w, void* stream);
+
 /* Release the handle and, if it allocated them, its device buffers. NULL is accepted. */
 recon_status recon_destroy(recon_handle* h);
 

@@ -27,7 +27,7 @@ ABI_SYMBOLS = (
     "recon_workspace_bytes", "recon_create", "recon_deposit", "recon_smooth", "recon_iterate",
     "recon_get_trace", "recon_shift", "recon_get_psi", "recon_get_field", "recon_get_scalars",
     "recon_fft_r2c", "recon_fft_c2r", "recon_destroy", "recon_status_str", "recon_last_error",
-    "recon_set_timing", "recon_get_timing", "recon_reset_timing",
+    "recon_set_timing", "recon_get_timing", "recon_reset_timing", "recon_cic_deposit_noalloc",
 )
 KERNEL_KINDS = ("deposit", "z_fwd", "z_inv", "z_delta", "z_proj", "z_final", "y_fwd", "y_inv",
                 "conv", "x_delta", "x_iter", "shift", "other")
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
     lib.recon_set_timing.argtypes = [VP, I]
     lib.recon_get_timing.argtypes = [VP, I, P(D), P(C.c_int64), P(D)]
     lib.recon_reset_timing.argtypes = [VP]
+    lib.recon_cic_deposit_noalloc.argtypes = [VP, I, VP, C.c_int64, I, D, VP, VP, VP]
     lib.recon_status_str.argtypes = [I]
     lib.recon_status_str.restype = C.c_char_p
     lib.recon_last_error.argtypes = [VP]

@@ -4,6 +4,9 @@
 // particle at grid coordinate u = x N / L deposits w (1 - t) and w t on the nodes floor(u) and
 // floor(u) + 1 of each axis, t = u - floor(u), with periodic wrap.  The same kernel interpolates
 // Psi back to particles for the shift of Sec. 1 (reversing Eq. Lagrange x = q + Psi).
+#include <mutex>
+
+#include "../../include/recon.h"
 #include "cic.h"
 
 namespace rg {
@@ -182,3 +185,67 @@ cudaError_t launch_add_scalar(float* x, size_t n, float v, cudaStream_t st) {
 }
 
 }  // namespace rg
+
+// ------------------------------------------------------------------------------------------------
+// CIC deposit that allocates nothing (recon_cic_deposit_noalloc).  The only scratch it needs, the
+// per-block partial sums of the weights, lives in a fixed file-scope device array; every device
+// that loads the library holds these 32 KB until the process exits.
+// ------------------------------------------------------------------------------------------------
+namespace rg {
+namespace {
+
+constexpr int kNoAllocMaxBlocks = 4096;                    // partial sums in the static scratch
+constexpr long long kNoAllocPerThread = 64;                // particles per thread at most
+constexpr long long kNoAllocMaxParticles = (long long)kNoAllocMaxBlocks * 256 * kNoAllocPerThread;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array for the current device, looked up once per device.  The
+// host-side name of a __device__ array is only a stand-in: kernels must be given this address.
+cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace rg
+
+extern "C" recon_status recon_cic_deposit_noalloc(const void* pos, int dtype, const float* w, int64_t n,
+                                                  int nmesh, double box, float* rho, double* sum_w,
+                                                  void* stream) {
+  using namespace rg;
+  if (n < 0 || (n > 0 && !pos) || !rho || !sum_w || nmesh < 2 || nmesh > 2048 || !(box > 0))
+    return RECON_ERR_INVALID_ARG;
+  if (dtype != RECON_F64 && dtype != RECON_F32) return RECON_ERR_INVALID_ARG;
+  if (n > kNoAllocMaxParticles) return RECON_ERR_INVALID_ARG;
+  double* scratch = nullptr;
+  if (noalloc_scratch(&scratch) != cudaSuccess) {
+    cudaGetLastError();
+    return RECON_ERR_CUDA;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t cells = (size_t)nmesh * nmesh * nmesh;
+  if (cudaMemsetAsync(rho, 0, cells * sizeof(float), st) != cudaSuccess) return RECON_ERR_CUDA;
+  if (n == 0) return cudaMemsetAsync(sum_w, 0, sizeof(double), st) == cudaSuccess ? RECON_OK : RECON_ERR_CUDA;
+  long long blocks = (n + 255) / 256;
+  if (blocks > kNoAllocMaxBlocks) blocks = kNoAllocMaxBlocks;
+  if (launch_deposit(pos, dtype == RECON_F64 ? 0 : 1, w, n, nmesh, box, rho, scratch, (int)blocks, st) != cudaSuccess)
+    return RECON_ERR_CUDA;
+  if (launch_finalize(scratch, (int)blocks, 1, sum_w, 0, 0, st) != cudaSuccess) return RECON_ERR_CUDA;
+  return RECON_OK;
+}
