@@ -118,21 +118,29 @@ struct Dft<6, INV> {
 };
 
 // ----------------------------------------------------------------------------------------------
-// Shared-memory layouts.  Element i of line col lives at phys(i, col).
-//   ColLayout<C>: lines are columns of an [L][C] tile (strided passes), C lines side by side.
-//   RowLayout<L>: lines are rows, padded by one element every 8 to spread bank accesses.
+// Shared-memory layouts.  Element i of line col lives at phys(i, col).  The swizzles make every
+// Stockham access pattern (contiguous reads j + r L/R, strided first-stage writes 8 j + r) hit
+// distinct banks within each 128-byte wavefront, with no padding.
+//   ColLayout<C>: lines are the C columns of an [L][C] tile (strided passes); rows 8 apart that a
+//                 wavefront touches together are moved to different bank halves by XOR-ing the
+//                 row's low bits with bits 3.. of the row index.
+//   RowLayout<L>: lines are rows (one per component); within each aligned 16-element block,
+//                 bits 0-3 are XOR-ed with bits 3-6 (a permutation of the block).
 // ----------------------------------------------------------------------------------------------
 template <int C>
 struct ColLayout {
   static constexpr bool kColFast = true;
-  __device__ __forceinline__ static int phys(int i, int col) { return i * C + col; }
+  static constexpr int kMask = (C >= 16) ? 0 : (16 / C - 1);
+  __device__ __forceinline__ static int phys(int i, int col) { return (i ^ ((i >> 3) & kMask)) * C + col; }
 };
 
 template <int L>
 struct RowLayout {
   static constexpr bool kColFast = false;
-  static constexpr int kStride = L + L / 8;
-  __device__ __forceinline__ static int phys(int i, int col) { return col * kStride + i + (i >> 3); }
+  static constexpr int kStride = L;
+  __device__ __forceinline__ static int phys(int i, int col) {
+    return col * kStride + (i ^ ((i >> 3) & 15));
+  }
 };
 
 // One Stockham stage over NCOL lines of length L with T threads.  The twiddle table holds

@@ -103,7 +103,7 @@ struct ZWarpSmem {  // float2 slots of one warp's private region
 };
 
 template <int N, int MODE, int NC>
-__global__ void __launch_bounds__(kZThreads) zpass_kernel(const ZArgs a) {
+__global__ void __launch_bounds__(kZThreads, 4) zpass_kernel(const ZArgs a) {
   constexpr int L = N / 2;
   constexpr int NF = (MODE == Z_DELTA) ? 1 : NC;   // lines transformed per row
   using Lay = RowLayout<L>;
