@@ -14,9 +14,10 @@ namespace rg {
 
 constexpr int kZThreads = 256;
 
-template <int N>
-struct SCols {  // adjacent columns in one strided tile
-  static constexpr int v = (N >= 1024) ? 4 : 8;
+template <int N, int MODE = 0>
+struct SCols {  // adjacent columns in one strided tile (the 3-component k-space tiles are narrower)
+  static constexpr bool kK = (MODE == S_DELTA || MODE == S_ITER);
+  static constexpr int v = kK ? 4 : ((N >= 1024) ? 4 : 8);
 };
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -348,19 +349,18 @@ __device__ __forceinline__ void tile_store(const float2* s, float2* __restrict__
   }
 }
 
-// Threads of a strided CTA: the 3-component k-space passes use 512 so that their two resident CTAs
-// (the 96 KB tile bounds them) still give 32 warps per SM; the plain passes move one component
-// per CTA with 256 threads and fit 4 CTAs per SM.
+// Threads of a strided CTA: 256, four CTAs per SM.  The plain passes move one component per CTA;
+// the 3-component k-space passes use 4-column (32-byte) tiles so that three components fit.
 template <int MODE>
 struct SThreads {
-  static constexpr int v = (MODE == S_DELTA || MODE == S_ITER) ? 512 : 256;
-  static constexpr int minb = (MODE == S_DELTA || MODE == S_ITER) ? 2 : 4;
+  static constexpr int v = 256;
+  static constexpr int minb = (MODE == S_DELTA || MODE == S_ITER) ? 3 : 4;
 };
 
 template <int N, int MODE, int NC, int AXIS>
 __global__ void __launch_bounds__(SThreads<MODE>::v, SThreads<MODE>::minb) spass_kernel(const SArgs a) {
   constexpr int T = SThreads<MODE>::v;
-  constexpr int C = SCols<N>::v;
+  constexpr int C = SCols<N, MODE>::v;
   constexpr int H = N / 2;
   constexpr int NS = (MODE == S_DELTA || MODE == S_ITER) ? 3 : NC;   // smem slots
   using Lay = ColLayout<C>;
@@ -489,9 +489,9 @@ __global__ void __launch_bounds__(SThreads<MODE>::v, SThreads<MODE>::minb) spass
   }
 }
 
-template <int N>
+template <int N, int MODE>
 constexpr size_t spass_smem(int nslots) {
-  return sizeof(float2) * ((size_t)((Plan<N>::kTab + 1) & ~1) + (size_t)nslots * N * SCols<N>::v);
+  return sizeof(float2) * ((size_t)((Plan<N>::kTab + 1) & ~1) + (size_t)nslots * N * SCols<N, MODE>::v);
 }
 
 // Stage twiddle tables of the N-point (strided passes) and N/2-point (Z pass) plans, built once
@@ -518,7 +518,9 @@ static cudaError_t launch_with_smem(K kern, int blocks, int threads, size_t smem
 template <int N>
 struct MeshImpl {
   static constexpr int kZBlocks = N * N / kZWarps;   // rows / warps per CTA: upper bound of the Z grid
-  static constexpr int kSBlocks = N * ((N / 2) / SCols<N>::v) + N / SCols<N>::v;
+  template <int M_>
+  static constexpr int sblocks() { return N * ((N / 2) / SCols<N, M_>::v) + N / SCols<N, M_>::v; }
+  static constexpr int kSBlocks = sblocks<S_ITER>();   // grid of the k-space pass (its partials)
 
   // persistent Z launch: exactly as many CTAs as fit on the device at once (occupancy x SMs),
   // never more than one row per warp
@@ -552,7 +554,7 @@ struct MeshImpl {
 
   template <int M_, int NC_, int AX_>
   static cudaError_t slaunch(const SArgs& a, cudaStream_t st, int ncomp) {
-    const size_t smem = spass_smem<N>((M_ == S_DELTA || M_ == S_ITER) ? 3 : NC_);
+    const size_t smem = spass_smem<N, M_>((M_ == S_DELTA || M_ == S_ITER) ? 3 : NC_);
     const void* k = (const void*)spass_kernel<N, M_, NC_, AX_>;
     static bool attr = false;
     if (!attr) {
@@ -561,7 +563,7 @@ struct MeshImpl {
       attr = true;
     }
     void* args[] = {const_cast<SArgs*>(&a)};
-    return cudaLaunchKernel(k, dim3(kSBlocks, ncomp), dim3(SThreads<M_>::v), args, smem, st);
+    return cudaLaunchKernel(k, dim3(sblocks<M_>(), ncomp), dim3(SThreads<M_>::v), args, smem, st);
   }
 
   static cudaError_t spass(int mode, int nc, int axis, const SArgs& a, cudaStream_t st) {
