@@ -168,11 +168,11 @@ enum {
   RECON_K_ZDELTA = 3,    /* Z pass: z smoothing, delta, r2c              */
   RECON_K_ZPROJ = 4,     /* Z pass: c2r, radial projection, r2c          */
   RECON_K_ZFINAL = 5,    /* Z pass: c2r of the final Psi                 */
-  RECON_K_YFWD = 6,      /* Y pass forward                               */
-  RECON_K_YINV = 7,      /* Y pass inverse                               */
+  RECON_K_LINE_FWD = 6,      /* plain x-line FFT pass, forward               */
+  RECON_K_LINE_INV = 7,      /* plain x-line FFT pass, inverse               */
   RECON_K_CONV = 8,      /* x / y Gaussian smoothing convolutions        */
-  RECON_K_XDELTA = 9,    /* X pass: delta(k), S_-1 and Z[delta/b]        */
-  RECON_K_XITER = 10,    /* X pass: source update, norms and Z[S]        */
+  RECON_K_KDELTA = 9,    /* y-line pass: delta(k), S_-1 and Z[delta/b]   */
+  RECON_K_KITER = 10,    /* y-line pass: source update, norms and Z[S]   */
   RECON_K_SHIFT = 11,    /* CIC interpolation and shift                  */
   RECON_K_OTHER = 12,    /* reductions, FFT export passes                */
   RECON_K_COUNT = 13

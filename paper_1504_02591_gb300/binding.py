@@ -29,8 +29,8 @@ ABI_SYMBOLS = (
     "recon_fft_r2c", "recon_fft_c2r", "recon_destroy", "recon_status_str", "recon_last_error",
     "recon_set_timing", "recon_get_timing", "recon_reset_timing", "recon_cic_deposit_noalloc",
 )
-KERNEL_KINDS = ("deposit", "z_fwd", "z_inv", "z_delta", "z_proj", "z_final", "y_fwd", "y_inv",
-                "conv", "x_delta", "x_iter", "shift", "other")
+KERNEL_KINDS = ("deposit", "z_fwd", "z_inv", "z_delta", "z_proj", "z_final", "line_fwd", "line_inv",
+                "conv", "k_delta", "k_iter", "shift", "other")
 
 
 class ReconParams(C.Structure):

@@ -17,7 +17,7 @@ constexpr int kZThreads = 256;
 template <int N, int MODE = 0>
 struct SCols {  // adjacent columns in one strided tile (the 3-component k-space tiles are narrower)
   static constexpr bool kK = (MODE == S_DELTA || MODE == S_ITER);
-  static constexpr int v = kK ? 4 : ((N >= 1024) ? 4 : 8);
+  static constexpr int v = kK ? 4 : ((N >= 1024) ? 8 : 16);
 };
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -278,7 +278,8 @@ constexpr size_t zpass_smem(int mode) {
 // Strided passes (Y and X).  A tile is N lines x C adjacent columns.  Tiles over the main array M:
 //   Y: lines along y at fixed x, columns kz0..kz0+C-1      (offset (x N + y) N/2 + kz)
 //   X: lines along x at fixed ky, columns kz0..kz0+C-1     (offset (x N + ky) N/2 + kz)
-// and over the Nyquist plane Q [kx][ky]:
+// and over the Nyquist plane Q [kx][ky] (the k-space passes, which need all three components of
+// P at once, run along y; the plain passes run along either axis):
 //   Y: lines along y (contiguous), columns are C values of x
 //   X: lines along x (stride N), columns are C adjacent ky
 // ------------------------------------------------------------------------------------------------
@@ -349,17 +350,21 @@ __device__ __forceinline__ void tile_store(const float2* s, float2* __restrict__
   }
 }
 
-// Threads of a strided CTA: 256, four CTAs per SM.  The plain passes move one component per CTA;
-// the 3-component k-space passes use 4-column (32-byte) tiles so that three components fit.
-template <int MODE>
+// Threads of a strided CTA.  The plain passes move one component per CTA in 16-column (128-byte)
+// tiles with 512 threads; the 3-component k-space passes use 4-column (32-byte) tiles with 256
+// threads so that three components fit three CTAs per SM.  The k-space passes run along y, whose
+// lines are 2 KB strided, so narrow tiles still stream well; the 1 MB-strided x lines get the
+// wide tiles.
+template <int N, int MODE>
 struct SThreads {
-  static constexpr int v = 256;
-  static constexpr int minb = (MODE == S_DELTA || MODE == S_ITER) ? 3 : 4;
+  static constexpr bool kK = (MODE == S_DELTA || MODE == S_ITER);
+  static constexpr int v = (!kK && SCols<N, MODE>::v == 16) ? 512 : 256;
+  static constexpr int minb = kK ? 3 : (v == 512 ? 2 : 4);
 };
 
 template <int N, int MODE, int NC, int AXIS>
-__global__ void __launch_bounds__(SThreads<MODE>::v, SThreads<MODE>::minb) spass_kernel(const SArgs a) {
-  constexpr int T = SThreads<MODE>::v;
+__global__ void __launch_bounds__(SThreads<N, MODE>::v, SThreads<N, MODE>::minb) spass_kernel(const SArgs a) {
+  constexpr int T = SThreads<N, MODE>::v;
   constexpr int C = SCols<N, MODE>::v;
   constexpr int H = N / 2;
   constexpr int NS = (MODE == S_DELTA || MODE == S_ITER) ? 3 : NC;   // smem slots
@@ -418,15 +423,22 @@ __global__ void __launch_bounds__(SThreads<MODE>::v, SThreads<MODE>::minb) spass
       const int e = threadIdx.x + k * T;
       if ((N * C) % T != 0 && e >= N * C) break;
       const int i = e / C, c = e % C;
-      const int mx = (i < H) ? i : i - N;
-      int ky, kz;
-      if (!t.isQ) { ky = t.a; kz = t.c0 + c; } else { ky = t.c0 + c; kz = H; }
+      // wavenumber indices of element (i, c): i runs along the pass axis
+      int ix, ky, kz;
+      if (AXIS == AX_X) {
+        ix = i;
+        if (!t.isQ) { ky = t.a; kz = t.c0 + c; } else { ky = t.c0 + c; kz = H; }
+      } else {
+        ky = i;
+        if (!t.isQ) { ix = t.a; kz = t.c0 + c; } else { ix = t.c0 + c; kz = H; }
+      }
+      const int mx = (ix < H) ? ix : ix - N;
       const int my = (ky < H) ? ky : ky - N;
       const float kx = g.kf * mx, kyf = g.kf * my, kzf = g.kf * kz;
       const float k2 = kx * kx + kyf * kyf + kzf * kzf;
       const int p = Lay::phys(i, c);
       {
-        const float kdx = (i == H) ? 0.f : kx;
+        const float kdx = (ix == H) ? 0.f : kx;
         const float kdy = (ky == H) ? 0.f : kyf;
         const float kdz = (kz == H) ? 0.f : kzf;
         const size_t gi = t.base + (size_t)i * t.ls + (size_t)c * t.cs;
@@ -435,7 +447,7 @@ __global__ void __launch_bounds__(SThreads<MODE>::v, SThreads<MODE>::minb) spass
         if (MODE == S_DELTA) {
           float2 dk = s[p];
           if (!a.d_is_k) {
-            if (a.lognormal && i == 0 && ky == 0 && kz == 0)
+            if (a.lognormal && ix == 0 && ky == 0 && kz == 0)
               dk.x -= (float)(a.red[RED_SUM_LOG]);   // subtract N^3 <ln(1+delta)> at k = 0
             (t.isQ ? a.dk.Q : a.dk.M)[gi] = dk;
           }
@@ -563,7 +575,7 @@ struct MeshImpl {
       attr = true;
     }
     void* args[] = {const_cast<SArgs*>(&a)};
-    return cudaLaunchKernel(k, dim3(sblocks<M_>(), ncomp), dim3(SThreads<M_>::v), args, smem, st);
+    return cudaLaunchKernel(k, dim3(sblocks<M_>(), ncomp), dim3(SThreads<N, M_>::v), args, smem, st);
   }
 
   static cudaError_t spass(int mode, int nc, int axis, const SArgs& a, cudaStream_t st) {
@@ -573,8 +585,8 @@ struct MeshImpl {
     if (mode == S_INV && axis == AX_Y) return slaunch<S_INV, 1, AX_Y>(a, st, nc);
     if (mode == S_FWD && axis == AX_X) return slaunch<S_FWD, 1, AX_X>(a, st, nc);
     if (mode == S_INV && axis == AX_X) return slaunch<S_INV, 1, AX_X>(a, st, nc);
-    if (mode == S_DELTA && axis == AX_X) return slaunch<S_DELTA, 1, AX_X>(a, st, 1);
-    if (mode == S_ITER && axis == AX_X && nc == 3) return slaunch<S_ITER, 3, AX_X>(a, st, 1);
+    if (mode == S_DELTA && axis == AX_Y) return slaunch<S_DELTA, 1, AX_Y>(a, st, 1);
+    if (mode == S_ITER && axis == AX_Y && nc == 3) return slaunch<S_ITER, 3, AX_Y>(a, st, 1);
     return cudaErrorInvalidValue;
   }
 

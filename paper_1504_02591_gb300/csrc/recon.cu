@@ -4,10 +4,10 @@
 //   deposit  CIC of galaxies and randoms -> rho_g, rho_r; sums of weights (float64)
 //   smooth   Gaussian exp(-k^2 R^2/2) as three periodic 1-D convolutions (x, y passes, then z
 //            inside the next pass); Z: delta = rho_g,s/(alpha rho_r,s) - 1 in the mask (+ lognormal)
-//            and its r2c | Y                                                        (Sec. 3.1, 3.2)
-//   iterate  X: delta(k), S_-1 = delta/b, Psi_s = Z[delta/b] | Y | Z: P_0 = (1-c)(Psi_s.r)r | Y
-//            repeat: X: S_n = delta/b + beta i k.P_n, norms, Psi = i k S/k^2 | Y |
-//                    Z: P = (Psi.r)r (or the final real Psi) | Y                  (Sec. 5.1)
+//            and its r2c | X                                                        (Sec. 3.1, 3.2)
+//   iterate  Y: delta(k), S_-1 = delta/b, Psi_s = Z[delta/b] | X | Z: P_0 = (1-c)(Psi_s.r)r | X
+//            repeat: Y: S_n = delta/b + beta i k.P_n, norms, Psi = i k S/k^2 | X |
+//                    Z: P = (Psi.r)r (or the final real Psi) | X                  (Sec. 5.1)
 //   shift    CIC interpolation of Psi to the particles, d = -(Psi + f (Psi.r) r) or -Psi (Sec. 1)
 #include <cmath>
 #include <cstdio>
@@ -195,11 +195,10 @@ int zkind(int mode) {
 }
 
 int skind(int mode, int axis) {
-  if (axis == AX_Y) return mode == S_FWD ? RECON_K_YFWD : RECON_K_YINV;
   switch (mode) {
-    case S_DELTA: return RECON_K_XDELTA;
-    case S_ITER: return RECON_K_XITER;
-    default: return RECON_K_OTHER;
+    case S_DELTA: return RECON_K_KDELTA;
+    case S_ITER: return RECON_K_KITER;
+    default: return axis == AX_X ? (mode == S_FWD ? RECON_K_LINE_FWD : RECON_K_LINE_INV) : RECON_K_OTHER;
   }
 }
 
@@ -279,11 +278,12 @@ recon_status finalize(recon_handle* h, int nblocks, int nq, int dst, int accumul
     if (s_ != RECON_OK) return s_;     \
   } while (0)
 
-// plain Y pass over nc of the vector fields
-recon_status ypass(recon_handle* h, int mode, int nc, const Field* f) {
+// plain X pass (one FFT along x per component) over nc fields.  The forward 3-D transform runs
+// Z (r2c) -> X -> Y, the inverse Y -> X -> Z; the Y passes carry the k-space work.
+recon_status xpass(recon_handle* h, int mode, int nc, const Field* f) {
   SArgs a = sargs(h);
   for (int q = 0; q < nc; ++q) a.f[q] = f[q];
-  return run_s(h, mode, nc, AX_Y, a);
+  return run_s(h, mode, nc, AX_X, a);
 }
 
 size_t elem_size(int dtype) { return dtype == RECON_F64 ? 8 : 4; }
@@ -596,7 +596,7 @@ recon_status recon_smooth(recon_handle* h) {
     RG_TRY(run_z(h, Z_DELTA, 2, a, &zg));
     RG_TRY(finalize(h, zg, 2, RED_SUM_LOG, 0));
   }
-  RG_TRY(ypass(h, S_FWD, 1, &h->D));
+  RG_TRY(xpass(h, S_FWD, 1, &h->D));
   h->state = ST_SMOOTHED;
   h->d_is_k = 0;
   h->delta_real_valid = 1;
@@ -617,16 +617,16 @@ recon_status recon_iterate(recon_handle* h, int start, double tol, int max_iter,
     SArgs a = sargs(h);
     for (int q = 0; q < 3; ++q) a.f[q] = h->V[q];
     a.d_is_k = h->d_is_k;
-    RG_TRY(run_s(h, S_DELTA, 1, AX_X, a));
+    RG_TRY(run_s(h, S_DELTA, 1, AX_Y, a));
     h->d_is_k = 1;
   }
-  RG_TRY(ypass(h, S_INV, 3, h->V));
+  RG_TRY(xpass(h, S_INV, 3, h->V));
   ZArgs za = zargs(h);
   for (int q = 0; q < 3; ++q) za.f[q] = h->V[q];
   za.coef = coef0;
   RG_TRY(run_z(h, Z_PROJ, 3, za));
   za.coef = 1.f;
-  RG_TRY(ypass(h, S_FWD, 3, h->V));
+  RG_TRY(xpass(h, S_FWD, 3, h->V));
 
   SArgs ia = sargs(h);
   for (int q = 0; q < 3; ++q) ia.f[q] = h->V[q];
@@ -635,13 +635,13 @@ recon_status recon_iterate(recon_handle* h, int start, double tol, int max_iter,
   int it = 0;
   recon_status result = RECON_OK;
   while (true) {
-    RG_TRY(run_s(h, S_ITER, 3, AX_X, ia));
+    RG_TRY(run_s(h, S_ITER, 3, AX_Y, ia));
     RG_TRY(finalize(h, h->mk->s_blocks, 2, RED_NORM_D2, 0));
     RG_CUDA(cudaMemcpyAsync(host_norm, h->red + RED_NORM_D2, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
     cudaEvent_t ev;
     RG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     RG_CUDA(cudaEventRecord(ev, h->st));
-    RG_TRY(ypass(h, S_INV, 3, h->V));
+    RG_TRY(xpass(h, S_INV, 3, h->V));
     cudaError_t es = cudaEventSynchronize(ev);
     cudaEventDestroy(ev);
     RG_CUDA(es);
@@ -659,7 +659,7 @@ recon_status recon_iterate(recon_handle* h, int start, double tol, int max_iter,
       break;
     }
     RG_TRY(run_z(h, Z_PROJ, 3, za));
-    RG_TRY(ypass(h, S_FWD, 3, h->V));
+    RG_TRY(xpass(h, S_FWD, 3, h->V));
   }
   if (result == RECON_OK) {
     h->state = ST_ITERATED;
@@ -802,10 +802,10 @@ recon_status recon_fft_r2c(recon_handle* h, const float* in_real, float* out_hal
   ZArgs a = zargs(h);
   a.f[0] = h->V[0];
   RG_TRY(run_z(h, Z_FWD, 1, a));
-  RG_TRY(ypass(h, S_FWD, 1, h->V));
+  RG_TRY(xpass(h, S_FWD, 1, h->V));
   SArgs s = sargs(h);
   s.f[0] = h->V[0];
-  RG_TRY(run_s(h, S_FWD, 1, AX_X, s));
+  RG_TRY(run_s(h, S_FWD, 1, AX_Y, s));
   RG_TRY(export_half(h, h->V[0], out_half));
   return RECON_OK;
 }
@@ -819,8 +819,8 @@ recon_status recon_fft_c2r(recon_handle* h, const float* in_half, float* out_rea
   RG_TRY(import_half(h, in_half, h->V[0]));
   SArgs s = sargs(h);
   s.f[0] = h->V[0];
-  RG_TRY(run_s(h, S_INV, 1, AX_X, s));
-  RG_TRY(ypass(h, S_INV, 1, h->V));
+  RG_TRY(run_s(h, S_INV, 1, AX_Y, s));
+  RG_TRY(xpass(h, S_INV, 1, h->V));
   ZArgs a = zargs(h);
   a.f[0] = h->V[0];
   RG_TRY(run_z(h, Z_INV, 1, a));
