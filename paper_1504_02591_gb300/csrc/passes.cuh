@@ -17,7 +17,9 @@ constexpr int kZThreads = 256;
 template <int N, int MODE = 0>
 struct SCols {  // adjacent columns in one strided tile (the 3-component k-space tiles are narrower)
   static constexpr bool kK = (MODE == S_DELTA || MODE == S_ITER);
-  static constexpr int v = kK ? 4 : ((N >= 1024) ? 8 : 16);
+  static constexpr int kWide = ((N / 2) % 16 == 0 && N < 1024) ? 16 : 8;   // must divide N / 2
+  static constexpr int v = kK ? 4 : kWide;
+  static_assert((N / 2) % v == 0 && N % v == 0, "tile columns must divide the half-grid rows");
 };
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
