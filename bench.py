@@ -114,28 +114,59 @@ def dist_info():
     return ws, rank, local
 
 
+CPU_MESH = 256
+CPU_SCALE = (512 / CPU_MESH) ** 3 * 27.0 / (3 * 8)      # volume x log(512^3)/log(256^3)
+CPU_SAMPLE = (f"oracle deposit+smooth+iterations+shift on the {CPU_MESH}^3 version of the workload "
+              f"(75000 galaxies, 3750000 randoms), x{CPU_SCALE:.3f} to 512^3")
+
+
 def cpu_sample(n_iter):
     """The FP64 oracle as it stands on a bounded sample of the workload, scaled to 512^3.
 
-    Sample: the same survey shape on a 128^3 mesh with 1/64 of the tracers, the GPU's iteration
+    Sample: the same survey shape on a 256^3 mesh with 1/8 of the tracers and the GPU's iteration
     count.  Every stage scales with the mesh volume (FFT stages as N^3 log N) or with the tracer
-    count, so the time is multiplied by 64 * log(512^3)/log(128^3) = 64 * 9/7.
+    count, so the time is multiplied by 8 * log(512^3)/log(256^3) = 9.
     """
     from oracle import recon_oracle as O
     from paper_1504_02591_gb300 import mocks
-    m = mocks.survey_shell_512(n_gal=600_000 // 64, ran_ratio=50, n_mesh=128)
+    m = mocks.survey_shell_512(n_gal=600_000 // 8, ran_ratio=50, n_mesh=CPU_MESH)
     t0 = time.perf_counter()
     O.reconstruct(m.params(), m.galaxies.pos, None, m.randoms.pos, None, start=O.START_FFTA,
                   tol=0.0, max_iter=n_iter)
     dt = time.perf_counter() - t0
-    return dt * 1000.0 * 64 * 9 / 7, dt
+    return dt * 1000.0 * CPU_SCALE, dt
+
+
+def kernel_sources_sha1():
+    import glob
+    import hashlib
+    d = os.path.join(ROOT, "paper_1504_02591_gb300", "csrc")
+    files = sorted(glob.glob(os.path.join(d, "*.cu")) + glob.glob(os.path.join(d, "*.cuh")) +
+                   glob.glob(os.path.join(d, "*.h")))
+    h = hashlib.sha1()
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu capture, if the kernels have not changed since."""
+    path = os.path.join(ROOT, "profiles", "traffic_shell512.txt")
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return None
+    if rec.get("sources_sha1") != kernel_sources_sha1():
+        return None
+    return rec.get("kernels", {}).get(kernel)
 
 
 def reference_arm(args):
     ws, rank, _ = dist_info()
     if rank != 0:
         return
-    n_iter = 16
+    n_iter = 13
     for _ in range(args.warmup):
         cpu_sample(n_iter)
     vals, raw = [], []
@@ -144,8 +175,7 @@ def reference_arm(args):
         vals.append(v)
         raw.append(dt)
     value = statistics.mean(vals)
-    sample = (f"oracle deposit+smooth+{n_iter} iterations+shift on the 128^3 version of the workload "
-              f"(9375 galaxies, 468750 randoms), {statistics.mean(raw):.1f} s each, x64*9/7 to 512^3")
+    sample = CPU_SAMPLE + f"; {n_iter} iterations, {statistics.mean(raw):.1f} s per sample"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -261,8 +291,7 @@ def gpu_arm(args):
     if rank == 0 and ws == 1 and not args.no_cpu:
         v, dt = cpu_sample(n_iter)
         cpu = {"value": round(v, 1), "unit": "ms", "cores": 1, "kind": "oracle",
-               "sample": (f"oracle deposit+smooth+{n_iter} iterations+shift on the 128^3 version of the "
-                          f"workload (9375 galaxies, 468750 randoms) took {dt:.2f} s; x64*9/7 to 512^3")}
+               "sample": CPU_SAMPLE + f"; {n_iter} iterations took {dt:.2f} s"}
 
     if rank == 0:
         line = {
@@ -277,7 +306,7 @@ def gpu_arm(args):
             "plain_start": {"ms": round(plain_ms, 4), "n_iter": plain_iter},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                          "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                         "traffic": None, "alg_bytes_per_launch": by / cnt,
+                         "traffic": recorded_traffic(dom), "alg_bytes_per_launch": by / cnt,
                          "ms_per_launch": round(ms_k / cnt, 5)},
             "kernels": kernels,
             "cpu_baseline": cpu,
