@@ -162,7 +162,7 @@ recon_status recon_fft_c2r(recon_handle* h, const float* in_half, float* out_rea
 
 /* Kernel kinds counted and (optionally) timed by the handle. */
 enum {
-  RECON_K_DEPOSIT = 0,   /* CIC deposit                                  */
+  RECON_K_DEPOSIT = 0,   /* CIC deposit from brick-sorted particles      */
   RECON_K_ZFWD = 1,      /* Z pass, r2c (densities, FFT export)          */
   RECON_K_ZINV = 2,      /* Z pass, c2r of the smoothed densities        */
   RECON_K_ZDELTA = 3,    /* Z pass: z smoothing, delta, r2c              */
@@ -173,9 +173,10 @@ enum {
   RECON_K_CONV = 8,      /* x / y Gaussian smoothing convolutions        */
   RECON_K_KDELTA = 9,    /* y-line pass: delta(k), S_-1 and Z[delta/b]   */
   RECON_K_KITER = 10,    /* y-line pass: source update, norms and Z[S]   */
-  RECON_K_SHIFT = 11,    /* CIC interpolation and shift                  */
+  RECON_K_SHIFT = 11,    /* sorted CIC interpolation and shift           */
   RECON_K_OTHER = 12,    /* reductions, FFT export passes                */
-  RECON_K_COUNT = 13
+  RECON_K_SORT = 13,     /* particle pack + brick counting sort          */
+  RECON_K_COUNT = 14
 };
 
 /* Enable (1) or disable (0) CUDA-event timing of every kernel launch on the handle's stream.

@@ -30,7 +30,7 @@ ABI_SYMBOLS = (
     "recon_set_timing", "recon_get_timing", "recon_reset_timing", "recon_cic_deposit_noalloc",
 )
 KERNEL_KINDS = ("deposit", "z_fwd", "z_inv", "z_delta", "z_proj", "z_final", "line_fwd", "line_inv",
-                "conv", "k_delta", "k_iter", "shift", "other")
+                "conv", "k_delta", "k_iter", "shift", "other", "sort")
 
 
 class ReconParams(C.Structure):

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/recon.h"
+#include "bricks.h"
 #include "cic.h"
 #include "conv.h"
 #include "types.h"
@@ -59,7 +60,7 @@ enum State { ST_CREATED = 0, ST_DEPOSITED = 1, ST_SMOOTHED = 2, ST_ITERATED = 3 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t field_M, field_Q, field, tw, tabs, tabz, off, taps, red, partials, stage, total;
+  size_t field_M, field_Q, field, tw, tabs, tabz, off, taps, red, partials, stage, bricks, total;
 };
 
 Layout layout_for(int n) {
@@ -78,9 +79,11 @@ Layout layout_for(int n) {
   if ((size_t)mk->s_blocks > nb) nb = mk->s_blocks;
   if ((size_t)kDepositBlocks > nb) nb = kDepositBlocks;
   if ((size_t)conv_blocks(n) > nb) nb = conv_blocks(n);
+  if ((size_t)brick_grid() > nb) nb = brick_grid();
   l.partials = align256(nb * 4 * sizeof(double));
   l.stage = align256((size_t)kStageParticles * kStageBytesPer);
-  l.total = 5 * l.field + l.tw + l.tabs + l.tabz + l.off + l.taps + l.red + l.partials + l.stage;
+  l.bricks = align256(brick_scratch_bytes(n));
+  l.total = 5 * l.field + l.tw + l.tabs + l.tabz + l.off + l.taps + l.red + l.partials + l.stage + l.bricks;
   return l;
 }
 
@@ -125,6 +128,7 @@ struct recon_handle {
   double* red = nullptr;
   double* partials = nullptr;
   char* stage = nullptr;
+  BrickBuffers bb{};       // brick sort of one particle chunk
   const MeshKernels* mk = nullptr;
   int state = ST_CREATED;
   int d_is_k = 0;
@@ -296,28 +300,32 @@ recon_status check_catalog(const recon_catalog* c) {
   return RECON_OK;
 }
 
-// Deposit one catalogue into rho; the weight sum goes to red[slot].
+// Deposit one catalogue into rho; the weight sum goes to red[slot].  Particles go through in chunks
+// (staged through the host buffer when the catalogue is in host memory): brick sort, then the
+// shared-memory binned deposit.
 recon_status deposit_one(recon_handle* h, const recon_catalog* c, float* rho, int slot) {
   const size_t es = elem_size(c->dtype);
-  if (c->on_device || c->n == 0) {
-    const int blocks = kDepositBlocks;
-    RG_CUDA(timed(h, RECON_K_DEPOSIT, (double)c->n * (3 * es + (c->w ? 4 : 0)) + rfield(h), [&] {
-      return launch_deposit(c->pos, c->dtype, c->w, c->n, h->n, h->L, rho, h->partials, blocks, h->st); }));
-    RG_TRY(finalize(h, blocks, 1, slot, 0));
-    return RECON_OK;
-  }
+  const long long chunk = c->on_device ? kSortChunk : (kStageParticles < kSortChunk ? kStageParticles : kSortChunk);
   char* spos = h->stage;
   float* sw = reinterpret_cast<float*>(h->stage + kStageParticles * 24);
-  for (long long p0 = 0; p0 < c->n; p0 += kStageParticles) {
-    const long long m = (c->n - p0 < kStageParticles) ? c->n - p0 : kStageParticles;
-    RG_CUDA(cudaMemcpyAsync(spos, (const char*)c->pos + (size_t)p0 * 3 * es, (size_t)m * 3 * es,
-                            cudaMemcpyHostToDevice, h->st));
-    if (c->w)
-      RG_CUDA(cudaMemcpyAsync(sw, c->w + p0, (size_t)m * sizeof(float), cudaMemcpyHostToDevice, h->st));
-    const int blocks = kDepositBlocks;
-    RG_CUDA(timed(h, RECON_K_DEPOSIT, (double)m * (3 * es + (c->w ? 4 : 0)) + (p0 == 0 ? rfield(h) : 0.0), [&] {
-      return launch_deposit(spos, c->dtype, c->w ? sw : nullptr, m, h->n, h->L, rho, h->partials, blocks, h->st); }));
-    RG_TRY(finalize(h, blocks, 1, slot, p0 > 0));
+  if (c->n == 0) RG_CUDA(cudaMemsetAsync(h->red + slot, 0, sizeof(double), h->st));
+  for (long long p0 = 0; p0 < c->n; p0 += chunk) {
+    const long long m = (c->n - p0 < chunk) ? c->n - p0 : chunk;
+    const void* pin = (const char*)c->pos + (size_t)p0 * 3 * es;
+    const float* win = c->w ? c->w + p0 : nullptr;
+    if (!c->on_device) {
+      RG_CUDA(cudaMemcpyAsync(spos, pin, (size_t)m * 3 * es, cudaMemcpyHostToDevice, h->st));
+      pin = spos;
+      if (c->w) {
+        RG_CUDA(cudaMemcpyAsync(sw, c->w + p0, (size_t)m * sizeof(float), cudaMemcpyHostToDevice, h->st));
+        win = sw;
+      }
+    }
+    RG_CUDA(timed(h, RECON_K_SORT, (double)m * (6 * es + (c->w ? 4 : 0) + 20),
+                  [&] { return brick_sort(h->bb, pin, c->dtype, win, m, h->st); }));
+    RG_CUDA(timed(h, RECON_K_DEPOSIT, (double)m * 16,
+                  [&] { return brick_deposit(h->bb, rho, h->partials, h->st); }));
+    RG_TRY(finalize(h, brick_grid(), 1, slot, p0 > 0));
   }
   return RECON_OK;
 }
@@ -425,6 +433,8 @@ recon_status recon_create(const recon_params* p, void* stream, void* workspace, 
   h->partials = (double*)b;
   b += h->lay.partials;
   h->stage = b;
+  b += h->lay.stage;
+  h->bb = brick_buffers(b, h->n, h->L);
 
   // twiddles exp(-2 pi i m / N) and node offsets from the observer, computed in float64
   const int n = h->n;
@@ -696,27 +706,36 @@ recon_status recon_shift(recon_handle* h, const recon_catalog* cat, int is_galax
   for (int q = 0; q < 3; ++q) a.obs[q] = h->p.observer[q];
   a.periodic = h->p.periodic;
   const size_t es = elem_size(cat->dtype);
-  if (cat->on_device && out_on_device) {
-    a.shift = shift_out;
-    a.pos_out = pos_out;
-    RG_CUDA(timed(h, RECON_K_SHIFT, (double)cat->n * (3 * es + 12 + (pos_out ? 24 : 0)),
-                  [&] { return launch_shift(cat->pos, cat->dtype, cat->n, a, h->st); }));
-    return RECON_OK;
-  }
+  BrickShiftArgs ba{};
+  for (int q = 0; q < 3; ++q) ba.psi[q] = a.psi[q];
+  ba.off = h->off;
+  ba.H = h->L / h->n;
+  ba.is_galaxy = a.is_galaxy;
+  ba.f = a.f;
+  ba.los_mode = a.los_mode;
+  ba.los = a.los;
+  ba.periodic = a.periodic;
+  ba.L = h->L;
+  ba.dtype = cat->dtype == RECON_F64 ? 0 : 1;
+  const bool staged = !cat->on_device || !out_on_device;
+  const long long chunk = staged ? (kStageParticles < kSortChunk ? kStageParticles : kSortChunk) : kSortChunk;
   char* spos = h->stage;
   float* sshift = reinterpret_cast<float*>(h->stage + kStageParticles * 28);
   double* spout = reinterpret_cast<double*>(h->stage + kStageParticles * 40);
-  for (long long p0 = 0; p0 < cat->n; p0 += kStageParticles) {
-    const long long m = (cat->n - p0 < kStageParticles) ? cat->n - p0 : kStageParticles;
+  for (long long p0 = 0; p0 < cat->n; p0 += chunk) {
+    const long long m = (cat->n - p0 < chunk) ? cat->n - p0 : chunk;
     const void* pin = (const char*)cat->pos + (size_t)p0 * 3 * es;
     if (!cat->on_device) {
       RG_CUDA(cudaMemcpyAsync(spos, pin, (size_t)m * 3 * es, cudaMemcpyHostToDevice, h->st));
       pin = spos;
     }
-    a.shift = out_on_device ? shift_out + 3 * p0 : sshift;
-    a.pos_out = pos_out ? (out_on_device ? pos_out + 3 * p0 : spout) : nullptr;
-    RG_CUDA(timed(h, RECON_K_SHIFT, (double)m * (3 * es + 12 + (pos_out ? 24 : 0)),
-                  [&] { return launch_shift(pin, cat->dtype, m, a, h->st); }));
+    ba.pos = pin;
+    ba.shift = out_on_device ? shift_out + 3 * p0 : sshift;
+    ba.pos_out = pos_out ? (out_on_device ? pos_out + 3 * p0 : spout) : nullptr;
+    RG_CUDA(timed(h, RECON_K_SORT, (double)m * (6 * es + 20),
+                  [&] { return brick_sort(h->bb, pin, cat->dtype, nullptr, m, h->st); }));
+    RG_CUDA(timed(h, RECON_K_SHIFT, (double)m * (16 + 4 + 12 + (pos_out ? 3 * es + 24 : 0)),
+                  [&] { return brick_shift(h->bb, ba, h->st); }));
     if (!out_on_device) {
       RG_CUDA(cudaMemcpyAsync(shift_out + 3 * p0, sshift, (size_t)m * 3 * sizeof(float), cudaMemcpyDeviceToHost, h->st));
       if (pos_out)
