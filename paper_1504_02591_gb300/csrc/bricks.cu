@@ -44,25 +44,31 @@ __device__ __forceinline__ uint32_t brick_key(const uint32_t (&q)[3], int nb) {
   return (bx * (uint32_t)nb + by) * (uint32_t)nb + bz;
 }
 
+// Count particles per brick; each particle keeps its brick and its arrival rank in the brick.
 template <typename PT>
 __global__ void __launch_bounds__(256) count_kernel(const PT* __restrict__ pos, long long np, double scale, int n,
-                                                    int nb, uint32_t* __restrict__ hist) {
+                                                    int nb, uint32_t* __restrict__ hist, uint32_t* __restrict__ key,
+                                                    uint32_t* __restrict__ rank) {
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x) {
     uint32_t q[3];
     pack(pos, p, scale, n, q);
-    atomicAdd(hist + brick_key(q, nb), 1u);
+    const uint32_t k = brick_key(q, nb);
+    key[p] = k;
+    rank[p] = atomicAdd(hist + k, 1u);
   }
 }
 
+// Place every particle at offs[brick] + rank as a packed record.
 template <typename PT>
 __global__ void __launch_bounds__(256) scatter_kernel(const PT* __restrict__ pos, const float* __restrict__ w,
-                                                      long long np, double scale, int n, int nb,
-                                                      uint32_t* __restrict__ cursor, uint4* __restrict__ rec,
+                                                      long long np, double scale, int n,
+                                                      const uint32_t* __restrict__ offs, const uint32_t* __restrict__ key,
+                                                      const uint32_t* __restrict__ rank, uint4* __restrict__ rec,
                                                       uint32_t* __restrict__ perm) {
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x) {
     uint32_t q[3];
     pack(pos, p, scale, n, q);
-    const uint32_t slot = atomicAdd(cursor + brick_key(q, nb), 1u);
+    const uint32_t slot = offs[key[p]] + rank[p];
     rec[slot] = make_uint4(q[0], q[1], q[2], __float_as_uint(w ? w[p] : 1.f));
     perm[slot] = (uint32_t)p;
   }
@@ -135,13 +141,9 @@ __global__ void __launch_bounds__(1024) scan_sums_kernel(uint32_t* __restrict__ 
   if (threadIdx.x == 0) *total = tot;
 }
 
-__global__ void __launch_bounds__(256) scan_add_kernel(uint32_t* __restrict__ out, uint32_t* __restrict__ cursor,
-                                                       const uint32_t* __restrict__ bsum, int m) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-    const uint32_t v = out[i] + bsum[i / 1024];
-    out[i] = v;
-    cursor[i] = v;
-  }
+__global__ void __launch_bounds__(256) scan_add_kernel(uint32_t* __restrict__ out, const uint32_t* __restrict__ bsum,
+                                                       int m) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) out[i] += bsum[i / 1024];
 }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -303,8 +305,8 @@ constexpr int kGrid = 152 * 8;
 
 size_t brick_scratch_bytes(int n) {
   const size_t nb3 = (size_t)(n / kBrick) * (n / kBrick) * (n / kBrick);
-  return a256(nb3 * 4) + a256((nb3 + 1) * 4) + a256(nb3 * 4) + a256(4096 * 4) + a256((size_t)kSortChunk * 16) +
-         a256((size_t)kSortChunk * 4);
+  const size_t ch = (size_t)sort_chunk(n);
+  return a256(nb3 * 4) + a256((nb3 + 1) * 4) + a256(4096 * 4) + a256(ch * 16) + 3 * a256(ch * 4);
 }
 
 BrickBuffers brick_buffers(char* base, int n, double L) {
@@ -312,25 +314,29 @@ BrickBuffers brick_buffers(char* base, int n, double L) {
   b.n = n;
   b.nb = n / kBrick;
   b.scale = (double)n / L;
+  b.chunk = sort_chunk(n);
   const size_t nb3 = (size_t)b.nb * b.nb * b.nb;
+  const size_t ch = (size_t)b.chunk;
   b.hist = reinterpret_cast<uint32_t*>(base);
   base += a256(nb3 * 4);
   b.offs = reinterpret_cast<uint32_t*>(base);
   base += a256((nb3 + 1) * 4);
-  b.cursor = reinterpret_cast<uint32_t*>(base);
-  base += a256(nb3 * 4);
   b.bsum = reinterpret_cast<uint32_t*>(base);
   base += a256(4096 * 4);
   b.rec = reinterpret_cast<uint4*>(base);
-  base += a256((size_t)kSortChunk * 16);
+  base += a256(ch * 16);
   b.perm = reinterpret_cast<uint32_t*>(base);
+  base += a256(ch * 4);
+  b.key = reinterpret_cast<uint32_t*>(base);
+  base += a256(ch * 4);
+  b.rank = reinterpret_cast<uint32_t*>(base);
   return b;
 }
 
 int brick_grid() { return kGrid; }
 
 cudaError_t brick_sort(const BrickBuffers& b, const void* pos, int dtype, const float* w, long long np, cudaStream_t st) {
-  if (np <= 0 || np > kSortChunk) return np == 0 ? cudaSuccess : cudaErrorInvalidValue;
+  if (np <= 0 || np > b.chunk) return np == 0 ? cudaSuccess : cudaErrorInvalidValue;
   const int m = b.nb * b.nb * b.nb;
   const int nblk = (m + 1023) / 1024;
   if (nblk > 4096) return cudaErrorInvalidValue;
@@ -339,16 +345,18 @@ cudaError_t brick_sort(const BrickBuffers& b, const void* pos, int dtype, const 
   long long want = (np + 255) / 256;
   const int blocks = (int)(want < kGrid * 2 ? want : kGrid * 2);
   if (dtype == 0)
-    count_kernel<double><<<blocks, 256, 0, st>>>((const double*)pos, np, b.scale, b.n, b.nb, b.hist);
+    count_kernel<double><<<blocks, 256, 0, st>>>((const double*)pos, np, b.scale, b.n, b.nb, b.hist, b.key, b.rank);
   else
-    count_kernel<float><<<blocks, 256, 0, st>>>((const float*)pos, np, b.scale, b.n, b.nb, b.hist);
+    count_kernel<float><<<blocks, 256, 0, st>>>((const float*)pos, np, b.scale, b.n, b.nb, b.hist, b.key, b.rank);
   scan_blocks_kernel<<<nblk, 256, 0, st>>>(b.hist, b.offs, b.bsum, m);
   scan_sums_kernel<<<1, 1024, 0, st>>>(b.bsum, nblk, b.offs + m);
-  scan_add_kernel<<<(m + 255) / 256 < kGrid ? (m + 255) / 256 : kGrid, 256, 0, st>>>(b.offs, b.cursor, b.bsum, m);
+  scan_add_kernel<<<(m + 255) / 256 < kGrid ? (m + 255) / 256 : kGrid, 256, 0, st>>>(b.offs, b.bsum, m);
   if (dtype == 0)
-    scatter_kernel<double><<<blocks, 256, 0, st>>>((const double*)pos, w, np, b.scale, b.n, b.nb, b.cursor, b.rec, b.perm);
+    scatter_kernel<double><<<blocks, 256, 0, st>>>((const double*)pos, w, np, b.scale, b.n, b.offs, b.key, b.rank,
+                                                    b.rec, b.perm);
   else
-    scatter_kernel<float><<<blocks, 256, 0, st>>>((const float*)pos, w, np, b.scale, b.n, b.nb, b.cursor, b.rec, b.perm);
+    scatter_kernel<float><<<blocks, 256, 0, st>>>((const float*)pos, w, np, b.scale, b.n, b.offs, b.key, b.rank,
+                                                   b.rec, b.perm);
   return cudaGetLastError();
 }
 

@@ -9,19 +9,23 @@ namespace rg {
 constexpr int kBrick = 8;                         // cells per brick edge
 constexpr int kBrickHalo = kBrick + 1;            // CIC touches one node beyond the brick
 constexpr int kBrickNodes = kBrickHalo * kBrickHalo * kBrickHalo;   // 729
-constexpr long long kSortChunk = 1LL << 22;       // particles sorted together
+constexpr long long kSortChunk = 1LL << 25;       // particles sorted together (meshes >= 256)
+constexpr long long kSortChunkSmall = 1LL << 22;  // ... on smaller meshes
+inline long long sort_chunk(int n) { return n >= 256 ? kSortChunk : kSortChunkSmall; }
 constexpr int kFracBits = 21;                     // fixed-point fraction of a cell per axis
 
 struct BrickBuffers {
   int n;                 // mesh side (multiple of 8)
   int nb;                // bricks per axis
   double scale;          // n / L
+  long long chunk;       // particles per sort (sort_chunk(n))
   uint32_t* hist;        // nb^3 counts
   uint32_t* offs;        // nb^3 + 1 exclusive offsets
-  uint32_t* cursor;      // nb^3 scatter cursors
   uint32_t* bsum;        // scan block sums (<= 4096)
   uint4* rec;            // kSortChunk sorted records: packed x, y, z (cell << 21 | frac), weight bits
   uint32_t* perm;        // kSortChunk: sorted slot -> index within the chunk
+  uint32_t* key;         // kSortChunk: brick of each particle (input order)
+  uint32_t* rank;        // kSortChunk: arrival rank of each particle within its brick
 };
 
 size_t brick_scratch_bytes(int n);

@@ -305,7 +305,7 @@ recon_status check_catalog(const recon_catalog* c) {
 // shared-memory binned deposit.
 recon_status deposit_one(recon_handle* h, const recon_catalog* c, float* rho, int slot) {
   const size_t es = elem_size(c->dtype);
-  const long long chunk = c->on_device ? kSortChunk : (kStageParticles < kSortChunk ? kStageParticles : kSortChunk);
+  const long long chunk = c->on_device ? h->bb.chunk : (kStageParticles < h->bb.chunk ? kStageParticles : h->bb.chunk);
   char* spos = h->stage;
   float* sw = reinterpret_cast<float*>(h->stage + kStageParticles * 24);
   if (c->n == 0) RG_CUDA(cudaMemsetAsync(h->red + slot, 0, sizeof(double), h->st));
@@ -718,7 +718,7 @@ recon_status recon_shift(recon_handle* h, const recon_catalog* cat, int is_galax
   ba.L = h->L;
   ba.dtype = cat->dtype == RECON_F64 ? 0 : 1;
   const bool staged = !cat->on_device || !out_on_device;
-  const long long chunk = staged ? (kStageParticles < kSortChunk ? kStageParticles : kSortChunk) : kSortChunk;
+  const long long chunk = staged ? (kStageParticles < h->bb.chunk ? kStageParticles : h->bb.chunk) : h->bb.chunk;
   char* spos = h->stage;
   float* sshift = reinterpret_cast<float*>(h->stage + kStageParticles * 28);
   double* spout = reinterpret_cast<double*>(h->stage + kStageParticles * 40);
