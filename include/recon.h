@@ -217,6 +217,21 @@ recon_status recon_reset_timing(recon_handle* h);
 recon_status recon_cic_deposit_noalloc(const void* pos, int dtype, const float* w, int64_t n, int nmesh,
                                        double box, float* rho, double* sum_w, void* stream);
 
+/* Handle options (recon_set_option). */
+enum {
+  RECON_OPT_DEPOSIT_PATH = 0,   /* RECON_PATH_DIRECT (default) or RECON_PATH_SORTED               */
+  RECON_OPT_SHIFT_PATH = 1      /* RECON_PATH_SORTED (default) or RECON_PATH_DIRECT               */
+};
+/* Particle paths: DIRECT handles each particle independently (8 global atomics per deposited
+ * particle; 24 scattered reads per interpolated one); SORTED packs the particles, counting-sorts
+ * them by 8^3-cell brick and works brick by brick in shared memory (deposit: one global atomic per
+ * touched node of the brick; shift: Psi staged once per brick).  Both give the same results up to
+ * float32 summation order. */
+enum { RECON_PATH_DIRECT = 0, RECON_PATH_SORTED = 1 };
+
+/* Set a handle option; INVALID_ARG for an unknown option or value. */
+recon_status recon_set_option(recon_handle* h, int option, int value);
+
 /* Release the handle and, if it allocated them, its device buffers. NULL is accepted. */
 recon_status recon_destroy(recon_handle* h);
 

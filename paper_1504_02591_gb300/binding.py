@@ -28,7 +28,10 @@ ABI_SYMBOLS = (
     "recon_get_trace", "recon_shift", "recon_get_psi", "recon_get_field", "recon_get_scalars",
     "recon_fft_r2c", "recon_fft_c2r", "recon_destroy", "recon_status_str", "recon_last_error",
     "recon_set_timing", "recon_get_timing", "recon_reset_timing", "recon_cic_deposit_noalloc",
+    "recon_set_option",
 )
+OPT_DEPOSIT_PATH, OPT_SHIFT_PATH = 0, 1
+PATH_DIRECT, PATH_SORTED = 0, 1
 KERNEL_KINDS = ("deposit", "z_fwd", "z_inv", "z_delta", "z_proj", "z_final", "line_fwd", "line_inv",
                 "conv", "k_delta", "k_iter", "shift", "other", "sort")
 
@@ -80,6 +83,7 @@ def load(path: str = LIB_PATH):
     lib.recon_set_timing.argtypes = [VP, I]
     lib.recon_get_timing.argtypes = [VP, I, P(D), P(C.c_int64), P(D)]
     lib.recon_reset_timing.argtypes = [VP]
+    lib.recon_set_option.argtypes = [VP, I, I]
     lib.recon_cic_deposit_noalloc.argtypes = [VP, I, VP, C.c_int64, I, D, VP, VP, VP]
     lib.recon_status_str.argtypes = [I]
     lib.recon_status_str.restype = C.c_char_p
@@ -283,6 +287,9 @@ class Recon:
         self._check(self.lib.recon_get_scalars(self.h, buf), "recon_get_scalars")
         keys = ("sum_wg", "sum_wr", "alpha", "threshold", "lognormal_C", "n_mask", "norm_d2", "norm_s2")
         return dict(zip(keys, list(buf)))
+
+    def set_option(self, option, value):
+        self._check(self.lib.recon_set_option(self.h, int(option), int(value)), "recon_set_option")
 
     def set_timing(self, enable: bool):
         self._check(self.lib.recon_set_timing(self.h, int(bool(enable))), "recon_set_timing")

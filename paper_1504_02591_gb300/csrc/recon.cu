@@ -131,6 +131,8 @@ struct recon_handle {
   BrickBuffers bb{};       // brick sort of one particle chunk
   const MeshKernels* mk = nullptr;
   int state = ST_CREATED;
+  int deposit_path = RECON_PATH_DIRECT;
+  int shift_path = RECON_PATH_SORTED;
   int d_is_k = 0;
   int delta_real_valid = 0;
   std::vector<double> trace;
@@ -301,8 +303,8 @@ recon_status check_catalog(const recon_catalog* c) {
 }
 
 // Deposit one catalogue into rho; the weight sum goes to red[slot].  Particles go through in chunks
-// (staged through the host buffer when the catalogue is in host memory): brick sort, then the
-// shared-memory binned deposit.
+// (staged through the host buffer when the catalogue is in host memory), either directly (global
+// atomics per particle) or brick-sorted into the shared-memory binned deposit.
 recon_status deposit_one(recon_handle* h, const recon_catalog* c, float* rho, int slot) {
   const size_t es = elem_size(c->dtype);
   const long long chunk = c->on_device ? h->bb.chunk : (kStageParticles < h->bb.chunk ? kStageParticles : h->bb.chunk);
@@ -321,11 +323,16 @@ recon_status deposit_one(recon_handle* h, const recon_catalog* c, float* rho, in
         win = sw;
       }
     }
-    RG_CUDA(timed(h, RECON_K_SORT, (double)m * (6 * es + (c->w ? 4 : 0) + 20),
-                  [&] { return brick_sort(h->bb, pin, c->dtype, win, m, h->st); }));
-    RG_CUDA(timed(h, RECON_K_DEPOSIT, (double)m * 16,
-                  [&] { return brick_deposit(h->bb, rho, h->partials, h->st); }));
-    RG_TRY(finalize(h, brick_grid(), 1, slot, p0 > 0));
+    if (h->deposit_path == RECON_PATH_SORTED) {
+      RG_CUDA(timed(h, RECON_K_SORT, (double)m * (6 * es + (c->w ? 4 : 0) + 28),
+                    [&] { return brick_sort(h->bb, pin, c->dtype, win, m, h->st); }));
+      RG_CUDA(timed(h, RECON_K_DEPOSIT, (double)m * 16, [&] { return brick_deposit(h->bb, rho, h->partials, h->st); }));
+      RG_TRY(finalize(h, brick_grid(), 1, slot, p0 > 0));
+    } else {
+      RG_CUDA(timed(h, RECON_K_DEPOSIT, (double)m * (3 * es + (c->w ? 4 : 0)), [&] {
+        return launch_deposit(pin, c->dtype, win, m, h->n, h->L, rho, h->partials, kDepositBlocks, h->st); }));
+      RG_TRY(finalize(h, kDepositBlocks, 1, slot, p0 > 0));
+    }
   }
   return RECON_OK;
 }
@@ -534,6 +541,14 @@ recon_status recon_reset_timing(recon_handle* h) {
   return RECON_OK;
 }
 
+recon_status recon_set_option(recon_handle* h, int option, int value) {
+  if (!h || (value != RECON_PATH_DIRECT && value != RECON_PATH_SORTED)) return RECON_ERR_INVALID_ARG;
+  if (option == RECON_OPT_DEPOSIT_PATH) h->deposit_path = value;
+  else if (option == RECON_OPT_SHIFT_PATH) h->shift_path = value;
+  else return RECON_ERR_INVALID_ARG;
+  return RECON_OK;
+}
+
 recon_status recon_destroy(recon_handle* h) {
   if (!h) return RECON_OK;
   drain_timing(h);
@@ -732,10 +747,17 @@ recon_status recon_shift(recon_handle* h, const recon_catalog* cat, int is_galax
     ba.pos = pin;
     ba.shift = out_on_device ? shift_out + 3 * p0 : sshift;
     ba.pos_out = pos_out ? (out_on_device ? pos_out + 3 * p0 : spout) : nullptr;
-    RG_CUDA(timed(h, RECON_K_SORT, (double)m * (6 * es + 20),
-                  [&] { return brick_sort(h->bb, pin, cat->dtype, nullptr, m, h->st); }));
-    RG_CUDA(timed(h, RECON_K_SHIFT, (double)m * (16 + 4 + 12 + (pos_out ? 3 * es + 24 : 0)),
-                  [&] { return brick_shift(h->bb, ba, h->st); }));
+    if (h->shift_path == RECON_PATH_SORTED) {
+      RG_CUDA(timed(h, RECON_K_SORT, (double)m * (6 * es + 28),
+                    [&] { return brick_sort(h->bb, pin, cat->dtype, nullptr, m, h->st); }));
+      RG_CUDA(timed(h, RECON_K_SHIFT, (double)m * (16 + 4 + 12 + (pos_out ? 3 * es + 24 : 0)),
+                    [&] { return brick_shift(h->bb, ba, h->st); }));
+    } else {
+      a.shift = ba.shift;
+      a.pos_out = ba.pos_out;
+      RG_CUDA(timed(h, RECON_K_SHIFT, (double)m * (3 * es + 12 + (pos_out ? 24 : 0)),
+                    [&] { return launch_shift(pin, cat->dtype, m, a, h->st); }));
+    }
     if (!out_on_device) {
       RG_CUDA(cudaMemcpyAsync(shift_out + 3 * p0, sshift, (size_t)m * 3 * sizeof(float), cudaMemcpyDeviceToHost, h->st));
       if (pos_out)

@@ -99,6 +99,30 @@ def test_periodic_pipeline_vs_oracle(B, periodic_mock, periodic_oracle, start):
     r.close()
 
 
+@pytest.mark.parametrize("dep_path,shift_path", [(0, 1), (1, 0), (1, 1)])
+def test_particle_paths_vs_oracle(B, periodic_mock, periodic_oracle, dep_path, shift_path):
+    """Direct and brick-sorted deposit / shift paths give the oracle's densities and shifts."""
+    m = periodic_mock
+    ref = periodic_oracle[2]
+    r = B.Recon.from_mock(m)
+    r.set_option(B.OPT_DEPOSIT_PATH, dep_path)
+    r.set_option(B.OPT_SHIFT_PATH, shift_path)
+    gal = torch.from_numpy(m.galaxies.pos).cuda()
+    ran = torch.from_numpy(m.randoms.pos).cuda()
+    r.deposit(gal, None, ran, None)
+    assert rel_l2(r.get_field(B.FIELD_RHO_G).cpu().numpy(), ref["rho_g"]) < 1e-6
+    assert rel_l2(r.get_field(B.FIELD_RHO_R).cpu().numpy(), ref["rho_r"]) < 1e-6
+    r.smooth()
+    r.iterate(2, 0.0, 6)
+    assert rel_l2(r.get_psi().cpu().numpy(), ref["psi"]) <= PSI_TOL
+    sg, pg = r.shift(gal, True, want_pos=True)
+    sr = r.shift(ran, False)
+    assert np.abs(sg.cpu().numpy() - ref["shift_g"]).max() <= SHIFT_TOL
+    assert np.abs(sr.cpu().numpy() - ref["shift_r"]).max() <= SHIFT_TOL
+    assert np.abs(pg.cpu().numpy() - ref["pos_g"]).max() <= SHIFT_TOL
+    r.close()
+
+
 def test_delta_k_export_matches_oracle(B, periodic_mock, periodic_oracle):
     m = periodic_mock
     r = B.Recon.from_mock(m)
