@@ -125,7 +125,8 @@ recon_status recon_smooth(recon_handle* h);
  * components, from the Parseval sum of the sources; the first entry is measured against the
  * uncorrected estimate Z[delta/b]).  On return *n_iter is the number of updates and *rel_change
  * the last rel.  Returns NOT_CONVERGED when max_iter was reached with rel >= tol and tol > 0.
- * Blocks the calling thread once per iteration to read the norm. */
+ * By default the loop runs on the device as one CUDA graph (RECON_OPT_GRAPH) and the call blocks
+ * once, at the end; max_iter <= 1024 in that mode (larger values use the host-driven loop). */
 recon_status recon_iterate(recon_handle* h, int start, double tol, int max_iter, int* n_iter,
                            double* rel_change);
 
@@ -220,7 +221,11 @@ recon_status recon_cic_deposit_noalloc(const void* pos, int dtype, const float* 
 /* Handle options (recon_set_option). */
 enum {
   RECON_OPT_DEPOSIT_PATH = 0,   /* RECON_PATH_DIRECT (default) or RECON_PATH_SORTED               */
-  RECON_OPT_SHIFT_PATH = 1      /* RECON_PATH_SORTED (default) or RECON_PATH_DIRECT               */
+  RECON_OPT_SHIFT_PATH = 1,     /* RECON_PATH_SORTED (default) or RECON_PATH_DIRECT               */
+  RECON_OPT_GRAPH = 2           /* 1 (default): recon_iterate runs the whole loop as one CUDA graph
+                                   with a conditional WHILE node and a device-side convergence
+                                   test; 0: the host reads the norms after every update.  Kernel
+                                   timing (recon_set_timing) always uses the host-driven loop.   */
 };
 /* Particle paths: DIRECT handles each particle independently (8 global atomics per deposited
  * particle; 24 scattered reads per interpolated one); SORTED packs the particles, counting-sorts
@@ -229,7 +234,7 @@ enum {
  * float32 summation order. */
 enum { RECON_PATH_DIRECT = 0, RECON_PATH_SORTED = 1 };
 
-/* Set a handle option; INVALID_ARG for an unknown option or value. */
+/* Set a handle option (values 0 or 1); INVALID_ARG for an unknown option or value. */
 recon_status recon_set_option(recon_handle* h, int option, int value);
 
 /* Release the handle and, if it allocated them, its device buffers. NULL is accepted. */

@@ -30,7 +30,7 @@ ABI_SYMBOLS = (
     "recon_set_timing", "recon_get_timing", "recon_reset_timing", "recon_cic_deposit_noalloc",
     "recon_set_option",
 )
-OPT_DEPOSIT_PATH, OPT_SHIFT_PATH = 0, 1
+OPT_DEPOSIT_PATH, OPT_SHIFT_PATH, OPT_GRAPH = 0, 1, 2
 PATH_DIRECT, PATH_SORTED = 0, 1
 KERNEL_KINDS = ("deposit", "z_fwd", "z_inv", "z_delta", "z_proj", "z_final", "line_fwd", "line_inv",
                 "conv", "k_delta", "k_iter", "shift", "other", "sort")

@@ -130,6 +130,8 @@ __global__ void __launch_bounds__(kZThreads, 4) zpass_kernel(const ZArgs a) {
 
   float acc0 = 0.f, acc1 = 0.f;
   constexpr bool kInverse = (MODE == Z_INV || MODE == Z_PROJ || MODE == Z_FINAL);
+  // device-driven iteration: once the loop flag says converged, this pass writes the real Psi
+  const bool fin = (MODE == Z_PROJ) && a.loop_flag && *a.loop_flag == 1;
   float inv_alpha = 0.f, thr = 0.f;
   const int nin = a.uniform ? 1 : 2;
   if (MODE == Z_DELTA) {
@@ -206,7 +208,7 @@ __global__ void __launch_bounds__(kZThreads, 4) zpass_kernel(const ZArgs a) {
       __syncwarp();
     }
 
-    if (MODE == Z_PROJ) {
+    if (MODE == Z_PROJ && !fin) {
       // s holds Psi_j(x, y, z), z = 2m (.x) and 2m + 1 (.y): P = coef (Psi.r) r (Eq. Nusser)
       const Geometry& g = a.g;
       const int ix = (int)(row / N), iy = (int)(row % N);
@@ -238,7 +240,7 @@ __global__ void __launch_bounds__(kZThreads, 4) zpass_kernel(const ZArgs a) {
       __syncwarp();
     }
 
-    if (MODE == Z_INV || MODE == Z_FINAL) {
+    if (MODE == Z_INV || MODE == Z_FINAL || (MODE == Z_PROJ && fin)) {
       for (int e = lane; e < NC * (L / 2); e += 32) {
         const int q = e / (L / 2), m2 = e % (L / 2);
         const float2 v0 = s[Lay::phys(2 * m2, q)], v1 = s[Lay::phys(2 * m2 + 1, q)];
@@ -378,6 +380,7 @@ __global__ void __launch_bounds__(SThreads<N, MODE>::v, SThreads<N, MODE>::minb)
   __shared__ double red_sh[T / 32];
   const int q0 = blockIdx.y;   // plain passes: the component this CTA transforms
 
+  if ((MODE == S_FWD || MODE == S_INV) && a.skip_flag && *a.skip_flag != 0) return;   // uniform
   for (int m = threadIdx.x; m < Plan<N>::kTab; m += T) tw[m] = a.tab[m];
   const Tile t = tile_of<N, C, AXIS>(blockIdx.x);
 

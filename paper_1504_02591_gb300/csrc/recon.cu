@@ -19,6 +19,7 @@
 #include "bricks.h"
 #include "cic.h"
 #include "conv.h"
+#include "loop.h"
 #include "types.h"
 
 namespace rg {
@@ -74,7 +75,7 @@ Layout layout_for(int n) {
   l.tabz = align256((size_t)mk->tab_z * sizeof(float2) + 16);
   l.off = align256((size_t)3 * n * sizeof(float));
   l.taps = align256((size_t)n * sizeof(float));
-  l.red = align256(64 * sizeof(double));
+  l.red = align256(64 * sizeof(double) + sizeof(LoopState));
   size_t nb = (size_t)mk->z_blocks;
   if ((size_t)mk->s_blocks > nb) nb = mk->s_blocks;
   if ((size_t)kDepositBlocks > nb) nb = kDepositBlocks;
@@ -126,6 +127,9 @@ struct recon_handle {
   float* taps = nullptr;   // smoothing kernel g[t0 .. t0 + ntap - 1]
   int ntap = 1, t0 = 0;
   double* red = nullptr;
+  LoopState* loop = nullptr;   // device-driven iteration state (inside the red region)
+  cudaStream_t cap_stream = nullptr;   // private stream for graph capture
+  int use_graph = 1;
   double* partials = nullptr;
   char* stage = nullptr;
   BrickBuffers bb{};       // brick sort of one particle chunk
@@ -436,6 +440,7 @@ recon_status recon_create(const recon_params* p, void* stream, void* workspace, 
   h->taps = (float*)b;
   b += h->lay.taps;
   h->red = (double*)b;
+  h->loop = reinterpret_cast<LoopState*>(h->red + 64);
   b += h->lay.red;
   h->partials = (double*)b;
   b += h->lay.partials;
@@ -542,9 +547,10 @@ recon_status recon_reset_timing(recon_handle* h) {
 }
 
 recon_status recon_set_option(recon_handle* h, int option, int value) {
-  if (!h || (value != RECON_PATH_DIRECT && value != RECON_PATH_SORTED)) return RECON_ERR_INVALID_ARG;
+  if (!h || (value != 0 && value != 1)) return RECON_ERR_INVALID_ARG;
   if (option == RECON_OPT_DEPOSIT_PATH) h->deposit_path = value;
   else if (option == RECON_OPT_SHIFT_PATH) h->shift_path = value;
+  else if (option == RECON_OPT_GRAPH) h->use_graph = value;
   else return RECON_ERR_INVALID_ARG;
   return RECON_OK;
 }
@@ -552,6 +558,7 @@ recon_status recon_set_option(recon_handle* h, int option, int value) {
 recon_status recon_destroy(recon_handle* h) {
   if (!h) return RECON_OK;
   drain_timing(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->own_ws && h->ws) {
     cudaStreamSynchronize(h->st);
     cudaFree(h->ws);
@@ -628,6 +635,126 @@ recon_status recon_smooth(recon_handle* h) {
   return RECON_OK;
 }
 
+namespace {
+
+// Start of the iteration (Sec. 5.2): delta(k), S_-1 = delta/b, Psi_s = Z[delta/b] along y, back to
+// configuration space, P_0 = (1 - c)(Psi_s.r) r, forward along z and x.
+recon_status iterate_start(recon_handle* h, float coef0) {
+  {
+    SArgs a = sargs(h);
+    for (int q = 0; q < 3; ++q) a.f[q] = h->V[q];
+    a.d_is_k = h->d_is_k;
+    RG_TRY(run_s(h, S_DELTA, 1, AX_Y, a));
+  }
+  RG_TRY(xpass(h, S_INV, 3, h->V));
+  ZArgs za = zargs(h);
+  for (int q = 0; q < 3; ++q) za.f[q] = h->V[q];
+  za.coef = coef0;
+  RG_TRY(run_z(h, Z_PROJ, 3, za));
+  RG_TRY(xpass(h, S_FWD, 3, h->V));
+  return RECON_OK;
+}
+
+// One update of Eq. iterative inside the device-driven loop: S_n, norms, Psi_n+1 = Z[S_n] along y;
+// the decide kernel records rel and ends the loop on convergence, after which the Z pass writes
+// the real Psi and the forward x pass is skipped.
+recon_status iterate_body(recon_handle* h, cudaGraphConditionalHandle cond) {
+  SArgs ia = sargs(h);
+  for (int q = 0; q < 3; ++q) ia.f[q] = h->V[q];
+  RG_TRY(run_s(h, S_ITER, 3, AX_Y, ia));
+  RG_TRY(finalize(h, h->mk->s_blocks, 2, RED_NORM_D2, 0));
+  RG_CUDA(timed(h, RECON_K_OTHER, 0.0, [&] { return launch_loop_decide(h->loop, h->red, cond, h->st); }));
+  RG_TRY(xpass(h, S_INV, 3, h->V));
+  ZArgs za = zargs(h);
+  for (int q = 0; q < 3; ++q) za.f[q] = h->V[q];
+  za.loop_flag = &h->loop->flag;
+  RG_TRY(run_z(h, Z_PROJ, 3, za));
+  SArgs fa = sargs(h);
+  for (int q = 0; q < 3; ++q) fa.f[q] = h->V[q];
+  fa.skip_flag = &h->loop->flag;
+  RG_TRY(run_s(h, S_FWD, 3, AX_X, fa));
+  return RECON_OK;
+}
+
+struct GraphGuard {
+  cudaGraph_t gs = nullptr, g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  ~GraphGuard() {
+    if (ex) cudaGraphExecDestroy(ex);
+    if (g) cudaGraphDestroy(g);
+    if (gs) cudaGraphDestroy(gs);
+  }
+};
+
+// The whole iteration as one CUDA graph: the start sequence, then a conditional WHILE node whose
+// body is one update.  One launch, one host synchronisation at the end.
+recon_status iterate_graph(recon_handle* h, float coef0, double tol, int max_iter, int* it_out, double* rel_out,
+                           int* flag_out) {
+  if (!h->cap_stream) RG_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  const cudaStream_t user = h->st;
+  const int timing = h->timing;
+  int64_t before[RECON_K_COUNT];
+  GraphGuard gg;
+  recon_status rs = RECON_OK;
+  int64_t body_launches = 0;
+  h->st = h->cap_stream;
+  h->timing = 0;
+  do {
+    cudaError_t e;
+    if ((e = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
+    rs = [&]() -> recon_status {
+      RG_CUDA(launch_loop_init(h->loop, tol, max_iter, h->st));
+      return iterate_start(h, coef0);
+    }();
+    e = cudaStreamEndCapture(h->st, &gg.gs);
+    if (rs != RECON_OK) break;
+    if (e != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
+    if ((e = cudaGraphCreate(&gg.g, 0)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
+    cudaGraphNode_t child = nullptr, cnode = nullptr;
+    if ((e = cudaGraphAddChildGraphNode(&child, gg.g, nullptr, 0, gg.gs)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
+    cudaGraphConditionalHandle cond;
+    if ((e = cudaGraphConditionalHandleCreate(&cond, gg.g, 1, cudaGraphCondAssignDefault)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    if ((e = cudaGraphAddNode(&cnode, gg.g, &child, nullptr, 1, &np)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    for (int k = 0; k < RECON_K_COUNT; ++k) before[k] = h->launches[k];
+    if ((e = cudaStreamBeginCaptureToGraph(h->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
+    rs = iterate_body(h, cond);
+    cudaGraph_t body_out = nullptr;
+    e = cudaStreamEndCapture(h->st, &body_out);
+    if (rs != RECON_OK) break;
+    if (e != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
+    for (int k = 0; k < RECON_K_COUNT; ++k) body_launches += h->launches[k] - before[k];
+    if ((e = cudaGraphInstantiate(&gg.ex, gg.g, 0)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
+  } while (0);
+  h->st = user;
+  h->timing = timing;
+  if (rs != RECON_OK) return rs;
+  RG_CUDA(cudaGraphLaunch(gg.ex, h->st));
+  int hdr[2];
+  RG_CUDA(cudaMemcpyAsync(hdr, h->loop, sizeof(hdr), cudaMemcpyDeviceToHost, h->st));
+  RG_CUDA(cudaStreamSynchronize(h->st));
+  const int it = hdr[1];
+  h->trace.assign(it < kMaxTrace ? it : kMaxTrace, 0.0);
+  if (!h->trace.empty())
+    RG_CUDA(cudaMemcpy(h->trace.data(), h->loop->trace, h->trace.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  // the captured body ran it times: count its launches accordingly
+  for (int k = 0; k < RECON_K_COUNT; ++k) {
+    const int64_t d = h->launches[k] - before[k];
+    h->launches[k] += d * (it > 0 ? it - 1 : -1);
+  }
+  (void)body_launches;
+  *it_out = it;
+  *rel_out = h->trace.empty() ? 0.0 : h->trace.back();
+  *flag_out = hdr[0];
+  return RECON_OK;
+}
+
+}  // namespace
+
 recon_status recon_iterate(recon_handle* h, int start, double tol, int max_iter, int* n_iter, double* rel_change) {
   if (!h) return RECON_ERR_INVALID_ARG;
   if (h->state < ST_SMOOTHED) return RECON_ERR_STATE;
@@ -637,54 +764,54 @@ recon_status recon_iterate(recon_handle* h, int start, double tol, int max_iter,
   const float coef0 = (float)(1.0 - start_coefficient(start, beta));
   h->trace.clear();
   h->delta_real_valid = 0;
-  // start: delta(k), S_-1 = delta/b, Psi_s = Z[delta/b], P_0 = (1 - c)(Psi_s.r) r
-  {
-    SArgs a = sargs(h);
-    for (int q = 0; q < 3; ++q) a.f[q] = h->V[q];
-    a.d_is_k = h->d_is_k;
-    RG_TRY(run_s(h, S_DELTA, 1, AX_Y, a));
-    h->d_is_k = 1;
-  }
-  RG_TRY(xpass(h, S_INV, 3, h->V));
-  ZArgs za = zargs(h);
-  for (int q = 0; q < 3; ++q) za.f[q] = h->V[q];
-  za.coef = coef0;
-  RG_TRY(run_z(h, Z_PROJ, 3, za));
-  za.coef = 1.f;
-  RG_TRY(xpass(h, S_FWD, 3, h->V));
-
-  SArgs ia = sargs(h);
-  for (int q = 0; q < 3; ++q) ia.f[q] = h->V[q];
-  double host_norm[2] = {0, 0};
   double rel = 0.0;
   int it = 0;
   recon_status result = RECON_OK;
-  while (true) {
-    RG_TRY(run_s(h, S_ITER, 3, AX_Y, ia));
-    RG_TRY(finalize(h, h->mk->s_blocks, 2, RED_NORM_D2, 0));
-    RG_CUDA(cudaMemcpyAsync(host_norm, h->red + RED_NORM_D2, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
-    cudaEvent_t ev;
-    RG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    RG_CUDA(cudaEventRecord(ev, h->st));
-    RG_TRY(xpass(h, S_INV, 3, h->V));
-    cudaError_t es = cudaEventSynchronize(ev);
-    cudaEventDestroy(ev);
-    RG_CUDA(es);
-    ++it;
-    if (!std::isfinite(host_norm[0]) || !std::isfinite(host_norm[1])) {
+  if (h->use_graph && !h->timing && max_iter <= kMaxTrace) {
+    // device-driven loop in one CUDA graph
+    int flag = 0;
+    RG_TRY(iterate_graph(h, coef0, tol, max_iter, &it, &rel, &flag));
+    h->d_is_k = 1;
+    if (flag == 2) {
       h->state = ST_SMOOTHED;
       result = RECON_ERR_NONFINITE;
-      break;
     }
-    rel = host_norm[1] > 0 ? std::sqrt(host_norm[0] / host_norm[1]) : 0.0;
-    h->trace.push_back(rel);
-    const bool done = (it >= 2 && rel < tol) || it >= max_iter;
-    if (done) {
-      RG_TRY(run_z(h, Z_FINAL, 3, za));
-      break;
+  } else {
+    // host-driven loop: the norms come back to the host after every update
+    RG_TRY(iterate_start(h, coef0));
+    h->d_is_k = 1;
+    ZArgs za = zargs(h);
+    for (int q = 0; q < 3; ++q) za.f[q] = h->V[q];
+    SArgs ia = sargs(h);
+    for (int q = 0; q < 3; ++q) ia.f[q] = h->V[q];
+    double host_norm[2] = {0, 0};
+    while (true) {
+      RG_TRY(run_s(h, S_ITER, 3, AX_Y, ia));
+      RG_TRY(finalize(h, h->mk->s_blocks, 2, RED_NORM_D2, 0));
+      RG_CUDA(cudaMemcpyAsync(host_norm, h->red + RED_NORM_D2, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      cudaEvent_t ev;
+      RG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      RG_CUDA(cudaEventRecord(ev, h->st));
+      RG_TRY(xpass(h, S_INV, 3, h->V));
+      cudaError_t es = cudaEventSynchronize(ev);
+      cudaEventDestroy(ev);
+      RG_CUDA(es);
+      ++it;
+      if (!std::isfinite(host_norm[0]) || !std::isfinite(host_norm[1])) {
+        h->state = ST_SMOOTHED;
+        result = RECON_ERR_NONFINITE;
+        break;
+      }
+      rel = host_norm[1] > 0 ? std::sqrt(host_norm[0] / host_norm[1]) : 0.0;
+      h->trace.push_back(rel);
+      const bool done = (it >= 2 && rel < tol) || it >= max_iter;
+      if (done) {
+        RG_TRY(run_z(h, Z_FINAL, 3, za));
+        break;
+      }
+      RG_TRY(run_z(h, Z_PROJ, 3, za));
+      RG_TRY(xpass(h, S_FWD, 3, h->V));
     }
-    RG_TRY(run_z(h, Z_PROJ, 3, za));
-    RG_TRY(xpass(h, S_FWD, 3, h->V));
   }
   if (result == RECON_OK) {
     h->state = ST_ITERATED;

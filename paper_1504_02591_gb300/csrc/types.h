@@ -58,6 +58,7 @@ struct ZArgs {
   const float* taps;      // z factor of the Gaussian smoothing: g[t0 .. t0 + ntap - 1]
   int ntap;
   int t0;
+  const int* loop_flag;   // Z_PROJ in a device-driven loop: 1 = converged, write the real Psi
 };
 
 struct SArgs {
@@ -72,6 +73,18 @@ struct SArgs {
   float beta;             // f / b
   int d_is_k;             // S_DELTA: dk is already fully transformed
   int lognormal;          // S_DELTA: subtract the lognormal constant at k = 0
+  const int* skip_flag;   // plain passes: do nothing when *skip_flag != 0 (device-driven loop)
+};
+
+// State of the device-driven iteration (in the workspace).
+constexpr int kMaxTrace = 1024;
+struct LoopState {
+  int flag;               // 0 running, 1 converged (final pass pending), 2 non-finite norms
+  int it;                 // updates done
+  int max_iter;
+  int pad;
+  double tol;
+  double trace[kMaxTrace];
 };
 
 // Kernels of one mesh size (one table per supported N).

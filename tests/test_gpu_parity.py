@@ -123,6 +123,28 @@ def test_particle_paths_vs_oracle(B, periodic_mock, periodic_oracle, dep_path, s
     r.close()
 
 
+def test_graph_and_host_loops_agree(B, shell_case):
+    """The device-driven loop (one CUDA graph, conditional WHILE node) and the host-driven loop
+    stop at the same update with the same trace and the same Psi."""
+    m, ref = shell_case
+    out = {}
+    for graph in (1, 0):
+        r = B.Recon.from_mock(m)
+        r.set_option(B.OPT_GRAPH, graph)
+        n_it, rel, st = r.run(torch.from_numpy(m.galaxies.pos).cuda(), torch.from_numpy(m.randoms.pos).cuda(),
+                              start=2, tol=1e-6, max_iter=40)
+        out[graph] = (n_it, np.array(r.trace()), r.get_psi().cpu().numpy(), st)
+        r.close()
+    assert out[1][0] == out[0][0] and out[1][3] == out[0][3] == B.OK
+    assert np.allclose(out[1][1], out[0][1], rtol=1e-6, atol=0)
+    assert rel_l2(out[1][2], out[0][2]) < 1e-7
+    # max_iter caps the device loop too
+    r = B.Recon.from_mock(m)
+    n_it, rel, st = r.run(m.galaxies.pos, m.randoms.pos, start=0, tol=1e-12, max_iter=3)
+    assert n_it == 3 and st == B.ERR_NOT_CONVERGED and len(r.trace()) == 3
+    r.close()
+
+
 def test_delta_k_export_matches_oracle(B, periodic_mock, periodic_oracle):
     m = periodic_mock
     r = B.Recon.from_mock(m)
