@@ -109,6 +109,11 @@ recon_status recon_workspace_bytes(const recon_params* p, size_t* bytes);
 recon_status recon_create(const recon_params* p, void* stream, void* workspace,
                           size_t workspace_bytes, recon_handle** out);
 
+/* Replace the parameters of a handle by p (same mesh side N; box, b, f, R, observer, LOS, mask and
+ * density options may all change), keeping its buffers.  Resets the call sequence (deposit next).
+ * INVALID_ARG if p is invalid or its mesh differs. */
+recon_status recon_reconfigure(recon_handle* h, const recon_params* p);
+
 /* CIC mass assignment of galaxies and randoms (Sec. 3: binning; CIC instead of NGP) and the
  * weight sums sum w_g, sum w_r (float64) that give alpha = sum w_g / sum w_r.
  * ran may be NULL (or n = 0) only with RECON_MEAN_UNIFORM. */
@@ -222,10 +227,12 @@ recon_status recon_cic_deposit_noalloc(const void* pos, int dtype, const float* 
 enum {
   RECON_OPT_DEPOSIT_PATH = 0,   /* RECON_PATH_DIRECT (default) or RECON_PATH_SORTED               */
   RECON_OPT_SHIFT_PATH = 1,     /* RECON_PATH_SORTED (default) or RECON_PATH_DIRECT               */
-  RECON_OPT_GRAPH = 2           /* 1 (default): recon_iterate runs the whole loop as one CUDA graph
+  RECON_OPT_GRAPH = 2,          /* 1 (default): recon_iterate runs the whole loop as one CUDA graph
                                    with a conditional WHILE node and a device-side convergence
                                    test; 0: the host reads the norms after every update.  Kernel
                                    timing (recon_set_timing) always uses the host-driven loop.   */
+  RECON_OPT_LINE_TILE = 3       /* FFT tile of the x-line passes: 0 (default) 16 adjacent columns
+                                   (128-byte rows) per tile, 1: 8 columns                         */
 };
 /* Particle paths: DIRECT handles each particle independently (8 global atomics per deposited
  * particle; 24 scattered reads per interpolated one); SORTED packs the particles, counting-sorts
@@ -236,6 +243,36 @@ enum { RECON_PATH_DIRECT = 0, RECON_PATH_SORTED = 1 };
 
 /* Set a handle option (values 0 or 1); INVALID_ARG for an unknown option or value. */
 recon_status recon_set_option(recon_handle* h, int option, int value);
+
+/* One reconstruction of a batch (recon_batch_run). */
+typedef struct recon_batch_item {
+  recon_params params;     /* any supported mesh; items are grouped by mesh side               */
+  recon_catalog gal;       /* galaxies, as for recon_deposit                                     */
+  recon_catalog ran;       /* randoms (ignored with RECON_MEAN_UNIFORM)                          */
+  int start;               /* RECON_START_*                                                      */
+  double tol;              /* as for recon_iterate                                               */
+  int max_iter;
+  float* shift_gal;        /* (n_gal, 3) galaxy shifts, or NULL for none                         */
+  float* shift_ran;        /* (n_ran, 3) random shifts, or NULL for none                         */
+  int out_on_device;       /* shift buffers are device (1) or host (0) memory                    */
+  int n_iter;              /* out: updates done                                                  */
+  double rel;              /* out: last |dPsi|/|Psi|                                             */
+  int status;              /* out: recon_status of this item (OK or NOT_CONVERGED on success)    */
+  float ms;                /* out: device milliseconds of this item on the stream                */
+} recon_batch_item;
+
+/* Reconstruct many mocks of uneven mesh and catalogue sizes (deposit -> smooth -> iterate ->
+ * shift each).  Items are grouped by mesh side; each size class uses one persistent handle
+ * (allocated with cudaMalloc, freed at the end of the class) and its items run back to back on
+ * `stream`, each iteration loop as one CUDA graph.  With autotune = 1, the first item of a size
+ * class not seen before in this process is also used to time the class's schedules (x-line FFT tile
+ * width, deposit path, shift path); the fastest are kept for the rest of the process
+ * (recon_batch_plan).  Returns the first error of any item (per-item statuses in items[i].status),
+ * else OK. */
+recon_status recon_batch_run(recon_batch_item* items, int n_items, void* stream, int autotune);
+
+/* The schedule the batch autotuner chose for mesh side nmesh (STATE if none yet). */
+recon_status recon_batch_plan(int nmesh, int* line_tile, int* deposit_path, int* shift_path);
 
 /* Release the handle and, if it allocated them, its device buffers. NULL is accepted. */
 recon_status recon_destroy(recon_handle* h);

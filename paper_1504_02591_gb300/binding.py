@@ -28,9 +28,9 @@ ABI_SYMBOLS = (
     "recon_get_trace", "recon_shift", "recon_get_psi", "recon_get_field", "recon_get_scalars",
     "recon_fft_r2c", "recon_fft_c2r", "recon_destroy", "recon_status_str", "recon_last_error",
     "recon_set_timing", "recon_get_timing", "recon_reset_timing", "recon_cic_deposit_noalloc",
-    "recon_set_option",
+    "recon_set_option", "recon_reconfigure", "recon_batch_run", "recon_batch_plan",
 )
-OPT_DEPOSIT_PATH, OPT_SHIFT_PATH, OPT_GRAPH = 0, 1, 2
+OPT_DEPOSIT_PATH, OPT_SHIFT_PATH, OPT_GRAPH, OPT_LINE_TILE = 0, 1, 2, 3
 PATH_DIRECT, PATH_SORTED = 0, 1
 KERNEL_KINDS = ("deposit", "z_fwd", "z_inv", "z_delta", "z_proj", "z_final", "line_fwd", "line_inv",
                 "conv", "k_delta", "k_iter", "shift", "other", "sort")
@@ -46,6 +46,13 @@ class ReconParams(C.Structure):
 class ReconCatalog(C.Structure):
     _fields_ = [("pos", C.c_void_p), ("w", C.c_void_p), ("n", C.c_int64), ("dtype", C.c_int),
                 ("on_device", C.c_int)]
+
+
+class ReconBatchItem(C.Structure):
+    _fields_ = [("params", ReconParams), ("gal", ReconCatalog), ("ran", ReconCatalog), ("start", C.c_int),
+                ("tol", C.c_double), ("max_iter", C.c_int), ("shift_gal", C.c_void_p), ("shift_ran", C.c_void_p),
+                ("out_on_device", C.c_int), ("n_iter", C.c_int), ("rel", C.c_double), ("status", C.c_int),
+                ("ms", C.c_float)]
 
 
 class ReconError(RuntimeError):
@@ -84,6 +91,9 @@ def load(path: str = LIB_PATH):
     lib.recon_get_timing.argtypes = [VP, I, P(D), P(C.c_int64), P(D)]
     lib.recon_reset_timing.argtypes = [VP]
     lib.recon_set_option.argtypes = [VP, I, I]
+    lib.recon_reconfigure.argtypes = [VP, P(ReconParams)]
+    lib.recon_batch_run.argtypes = [P(ReconBatchItem), I, VP, I]
+    lib.recon_batch_plan.argtypes = [I, P(I), P(I), P(I)]
     lib.recon_cic_deposit_noalloc.argtypes = [VP, I, VP, C.c_int64, I, D, VP, VP, VP]
     lib.recon_status_str.argtypes = [I]
     lib.recon_status_str.restype = C.c_char_p
@@ -332,3 +342,46 @@ class Recon:
         self.deposit(gal_pos, gal_w, ran_pos, ran_w)
         self.smooth()
         return self.iterate(start, tol, max_iter)
+
+
+def batch_run(mocks, start=START_FFTA, tol=1e-6, max_iter=80, autotune=True, stream=None, **over):
+    """Reconstruct a list of mocks.Mock in one recon_batch_run call.
+
+    Catalogues are moved to the GPU first (one CUDA tensor per catalogue); returns, per mock, a dict
+    with n_iter, rel, status, ms and the galaxy / random shift tensors."""
+    import torch
+    lib = load()
+    items = (ReconBatchItem * len(mocks))()
+    keep, outs = [], []
+    for i, m in enumerate(mocks):
+        p = m.params(**over)
+        items[i].params = make_params(p["n"], p["L"], p["b"], p["f"], p["R"], p["observer"], p["los_mode"],
+                                      p["periodic"], p["mask_frac"], p["lognormal"], p["uniform"])
+        g = torch.from_numpy(m.galaxies.pos).cuda()
+        items[i].gal = _catalog(g, None, keep)
+        sg = torch.empty((len(g), 3), dtype=torch.float32, device="cuda")
+        items[i].shift_gal = sg.data_ptr()
+        sr = None
+        if m.randoms is not None and not p["uniform"]:
+            r = torch.from_numpy(m.randoms.pos).cuda()
+            items[i].ran = _catalog(r, None, keep)
+            sr = torch.empty((len(r), 3), dtype=torch.float32, device="cuda")
+            items[i].shift_ran = sr.data_ptr()
+        keep += [sg, sr]
+        items[i].start, items[i].tol, items[i].max_iter, items[i].out_on_device = int(start), float(tol), int(max_iter), 1
+        outs.append((sg, sr))
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    status = lib.recon_batch_run(items, len(mocks), C.c_void_p(st), int(bool(autotune)))
+    torch.cuda.synchronize()
+    res = []
+    for i in range(len(mocks)):
+        res.append(dict(n_iter=items[i].n_iter, rel=items[i].rel, status=items[i].status, ms=items[i].ms,
+                        shift_gal=outs[i][0], shift_ran=outs[i][1]))
+    return status, res
+
+
+def batch_plan(nmesh):
+    lib = load()
+    a, b, c = C.c_int(), C.c_int(), C.c_int()
+    st = lib.recon_batch_plan(int(nmesh), C.byref(a), C.byref(b), C.byref(c))
+    return None if st != OK else dict(line_tile=a.value, deposit_path=b.value, shift_path=c.value)

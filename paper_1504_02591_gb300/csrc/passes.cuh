@@ -14,10 +14,10 @@ namespace rg {
 
 constexpr int kZThreads = 256;
 
-template <int N, int MODE = 0>
+template <int N, int MODE = 0, int NARROW = 0>
 struct SCols {  // adjacent columns in one strided tile (the 3-component k-space tiles are narrower)
   static constexpr bool kK = (MODE == S_DELTA || MODE == S_ITER);
-  static constexpr int kWide = ((N / 2) % 16 == 0 && N < 1024) ? 16 : 8;   // must divide N / 2
+  static constexpr int kWide = ((N / 2) % 16 == 0 && N < 1024 && !NARROW) ? 16 : 8;   // must divide N / 2
   static constexpr int v = kK ? 4 : kWide;
   static_assert((N / 2) % v == 0 && N % v == 0, "tile columns must divide the half-grid rows");
 };
@@ -359,17 +359,18 @@ __device__ __forceinline__ void tile_store(const float2* s, float2* __restrict__
 // threads so that three components fit three CTAs per SM.  The k-space passes run along y, whose
 // lines are 2 KB strided, so narrow tiles still stream well; the 1 MB-strided x lines get the
 // wide tiles.
-template <int N, int MODE>
+template <int N, int MODE, int NARROW = 0>
 struct SThreads {
   static constexpr bool kK = (MODE == S_DELTA || MODE == S_ITER);
-  static constexpr int v = (!kK && SCols<N, MODE>::v == 16) ? 512 : 256;
+  static constexpr int v = (!kK && SCols<N, MODE, NARROW>::v == 16) ? 512 : 256;
   static constexpr int minb = kK ? 3 : (v == 512 ? 2 : 4);
 };
 
-template <int N, int MODE, int NC, int AXIS>
-__global__ void __launch_bounds__(SThreads<N, MODE>::v, SThreads<N, MODE>::minb) spass_kernel(const SArgs a) {
-  constexpr int T = SThreads<N, MODE>::v;
-  constexpr int C = SCols<N, MODE>::v;
+template <int N, int MODE, int NC, int AXIS, int NARROW = 0>
+__global__ void __launch_bounds__(SThreads<N, MODE, NARROW>::v, SThreads<N, MODE, NARROW>::minb)
+    spass_kernel(const SArgs a) {
+  constexpr int T = SThreads<N, MODE, NARROW>::v;
+  constexpr int C = SCols<N, MODE, NARROW>::v;
   constexpr int H = N / 2;
   constexpr int NS = (MODE == S_DELTA || MODE == S_ITER) ? 3 : NC;   // smem slots
   using Lay = ColLayout<C>;
@@ -506,9 +507,9 @@ __global__ void __launch_bounds__(SThreads<N, MODE>::v, SThreads<N, MODE>::minb)
   }
 }
 
-template <int N, int MODE>
+template <int N, int MODE, int NARROW = 0>
 constexpr size_t spass_smem(int nslots) {
-  return sizeof(float2) * ((size_t)((Plan<N>::kTab + 1) & ~1) + (size_t)nslots * N * SCols<N, MODE>::v);
+  return sizeof(float2) * ((size_t)((Plan<N>::kTab + 1) & ~1) + (size_t)nslots * N * SCols<N, MODE, NARROW>::v);
 }
 
 // Stage twiddle tables of the N-point (strided passes) and N/2-point (Z pass) plans, built once
@@ -535,8 +536,10 @@ static cudaError_t launch_with_smem(K kern, int blocks, int threads, size_t smem
 template <int N>
 struct MeshImpl {
   static constexpr int kZBlocks = N * N / kZWarps;   // rows / warps per CTA: upper bound of the Z grid
-  template <int M_>
-  static constexpr int sblocks() { return N * ((N / 2) / SCols<N, M_>::v) + N / SCols<N, M_>::v; }
+  template <int M_, int NARROW = 0>
+  static constexpr int sblocks() {
+    return N * ((N / 2) / SCols<N, M_, NARROW>::v) + N / SCols<N, M_, NARROW>::v;
+  }
   static constexpr int kSBlocks = sblocks<S_ITER>();   // grid of the k-space pass (its partials)
 
   // persistent Z launch: exactly as many CTAs as fit on the device at once (occupancy x SMs),
@@ -569,10 +572,10 @@ struct MeshImpl {
     return cudaErrorInvalidValue;
   }
 
-  template <int M_, int NC_, int AX_>
+  template <int M_, int NC_, int AX_, int NARROW = 0>
   static cudaError_t slaunch(const SArgs& a, cudaStream_t st, int ncomp) {
-    const size_t smem = spass_smem<N, M_>((M_ == S_DELTA || M_ == S_ITER) ? 3 : NC_);
-    const void* k = (const void*)spass_kernel<N, M_, NC_, AX_>;
+    const size_t smem = spass_smem<N, M_, NARROW>((M_ == S_DELTA || M_ == S_ITER) ? 3 : NC_);
+    const void* k = (const void*)spass_kernel<N, M_, NC_, AX_, NARROW>;
     static bool attr = false;
     if (!attr) {
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -580,7 +583,8 @@ struct MeshImpl {
       attr = true;
     }
     void* args[] = {const_cast<SArgs*>(&a)};
-    return cudaLaunchKernel(k, dim3(sblocks<M_>(), ncomp), dim3(SThreads<N, M_>::v), args, smem, st);
+    return cudaLaunchKernel(k, dim3(sblocks<M_, NARROW>(), ncomp), dim3(SThreads<N, M_, NARROW>::v), args, smem,
+                            st);
   }
 
   static cudaError_t spass(int mode, int nc, int axis, const SArgs& a, cudaStream_t st) {
@@ -588,8 +592,10 @@ struct MeshImpl {
     // plain passes: one component per CTA, components along gridDim.y
     if (mode == S_FWD && axis == AX_Y) return slaunch<S_FWD, 1, AX_Y>(a, st, nc);
     if (mode == S_INV && axis == AX_Y) return slaunch<S_INV, 1, AX_Y>(a, st, nc);
-    if (mode == S_FWD && axis == AX_X) return slaunch<S_FWD, 1, AX_X>(a, st, nc);
-    if (mode == S_INV && axis == AX_X) return slaunch<S_INV, 1, AX_X>(a, st, nc);
+    if (mode == S_FWD && axis == AX_X)
+      return a.narrow ? slaunch<S_FWD, 1, AX_X, 1>(a, st, nc) : slaunch<S_FWD, 1, AX_X>(a, st, nc);
+    if (mode == S_INV && axis == AX_X)
+      return a.narrow ? slaunch<S_INV, 1, AX_X, 1>(a, st, nc) : slaunch<S_INV, 1, AX_X>(a, st, nc);
     if (mode == S_DELTA && axis == AX_Y) return slaunch<S_DELTA, 1, AX_Y>(a, st, 1);
     if (mode == S_ITER && axis == AX_Y && nc == 3) return slaunch<S_ITER, 3, AX_Y>(a, st, 1);
     return cudaErrorInvalidValue;

@@ -137,6 +137,7 @@ struct recon_handle {
   int state = ST_CREATED;
   int deposit_path = RECON_PATH_DIRECT;
   int shift_path = RECON_PATH_SORTED;
+  int narrow_lines = 0;
   int d_is_k = 0;
   int delta_real_valid = 0;
   std::vector<double> trace;
@@ -243,6 +244,7 @@ SArgs sargs(recon_handle* h) {
   a.sbuf = h->S;
   a.inv_b = (float)(1.0 / h->p.b);
   a.beta = (float)(h->p.f / h->p.b);
+  a.narrow = h->narrow_lines;
   a.lognormal = h->p.lognormal;
   return a;
 }
@@ -370,6 +372,69 @@ double start_coefficient(int start, double beta) {
 
 }  // namespace
 
+namespace {
+
+// Per-reconstruction parameters that do not change the mesh: box, bias, growth rate, smoothing
+// length, line of sight, mask and density options.  Uploads the node offsets from the observer and
+// the smoothing taps, and resets the call sequence.
+recon_status configure(recon_handle* h, const recon_params* p) {
+  h->p = *p;
+  h->L = p->box[0];
+  h->bb.scale = (double)h->n / h->L;
+  const int n = h->n;
+  std::vector<float> off(3 * n);
+  const double H = h->L / n;
+  for (int a = 0; a < 3; ++a)
+    for (int i = 0; i < n; ++i) off[a * n + i] = (float)((double)i * H - p->observer[a]);
+  // Gaussian smoothing as a periodic convolution per axis: g[t] = (1/N) sum_m exp(-k_m^2 R^2/2)
+  // cos(2 pi m t / N); taps beyond the last |g[t]| > 1e-9 g[0] are dropped, and a kernel that has
+  // not decayed by then is used over the whole period.
+  std::vector<double> gk(n);
+  for (int t = 0; t < n; ++t) {
+    double acc = 0.0;
+    for (int m = 0; m < n; ++m) {
+      const int mm = (m <= n / 2) ? m : m - n;
+      const double k = 2.0 * M_PI * mm / h->L;
+      acc += std::exp(-0.5 * k * k * p->smooth_R * p->smooth_R) * std::cos(2.0 * M_PI * (double)m * t / n);
+    }
+    gk[t] = acc / n;
+  }
+  int K = 0;
+  for (int t = 1; t <= n / 2; ++t)
+    if (std::fabs(gk[t]) > 1e-9 * std::fabs(gk[0])) K = t;
+  if (2 * K + 1 >= n) {
+    h->t0 = -n / 2;
+    h->ntap = n;
+  } else {
+    h->t0 = -K;
+    h->ntap = 2 * K + 1;
+  }
+  std::vector<float> taps(h->ntap);
+  for (int j = 0; j < h->ntap; ++j) taps[j] = (float)gk[((h->t0 + j) % n + n) % n];
+  RG_CUDA(cudaMemcpyAsync(h->taps, taps.data(), h->ntap * sizeof(float), cudaMemcpyHostToDevice, h->st));
+  RG_CUDA(cudaMemcpyAsync(h->off, off.data(), 3 * n * sizeof(float), cudaMemcpyHostToDevice, h->st));
+  RG_CUDA(cudaStreamSynchronize(h->st));   // the host vectors go out of scope
+  Geometry& g = h->geo;
+  g.n = n;
+  g.kf = (float)(2.0 * M_PI / h->L);
+  g.inv_n3 = (float)(1.0 / ((double)n * n * n));
+  g.los_mode = p->los_mode;
+  if (p->los_mode == RECON_LOS_FIXED) {
+    const double q = std::sqrt(p->observer[0] * p->observer[0] + p->observer[1] * p->observer[1] +
+                               p->observer[2] * p->observer[2]);
+    g.los = make_float3((float)(p->observer[0] / q), (float)(p->observer[1] / q), (float)(p->observer[2] / q));
+  } else {
+    g.los = make_float3(0.f, 0.f, 0.f);
+  }
+  g.off = h->off;
+  h->state = ST_CREATED;
+  h->d_is_k = 0;
+  h->delta_real_valid = 0;
+  return RECON_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* recon_status_str(recon_status s) {
@@ -448,75 +513,34 @@ recon_status recon_create(const recon_params* p, void* stream, void* workspace, 
   b += h->lay.stage;
   h->bb = brick_buffers(b, h->n, h->L);
 
-  // twiddles exp(-2 pi i m / N) and node offsets from the observer, computed in float64
+  // twiddles exp(-2 pi i m / N), computed in float64, and the stage tables built from them
   const int n = h->n;
   std::vector<float2> tw(n);
   for (int m = 0; m < n; ++m) {
     const double ang = -2.0 * M_PI * (double)m / (double)n;
     tw[m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
   }
-  std::vector<float> off(3 * n);
-  const double H = h->L / n;
-  for (int a = 0; a < 3; ++a)
-    for (int i = 0; i < n; ++i) off[a * n + i] = (float)((double)i * H - p->observer[a]);
-  // Gaussian smoothing as a periodic convolution per axis: g[t] = (1/N) sum_m exp(-k_m^2 R^2/2)
-  // cos(2 pi m t / N); taps beyond the last |g[t]| > 1e-9 g[0] are dropped, and a kernel that has
-  // not decayed by then is used over the whole period.
-  std::vector<double> gk(n);
-  for (int t = 0; t < n; ++t) {
-    double acc = 0.0;
-    for (int m = 0; m < n; ++m) {
-      const int mm = (m <= n / 2) ? m : m - n;
-      const double k = 2.0 * M_PI * mm / h->L;
-      acc += std::exp(-0.5 * k * k * p->smooth_R * p->smooth_R) * std::cos(2.0 * M_PI * (double)m * t / n);
-    }
-    gk[t] = acc / n;
-  }
-  int K = 0;
-  for (int t = 1; t <= n / 2; ++t)
-    if (std::fabs(gk[t]) > 1e-9 * std::fabs(gk[0])) K = t;
-  if (2 * K + 1 >= n) {
-    h->t0 = -n / 2;
-    h->ntap = n;
-  } else {
-    h->t0 = -K;
-    h->ntap = 2 * K + 1;
-  }
-  std::vector<float> taps(h->ntap);
-  for (int j = 0; j < h->ntap; ++j) taps[j] = (float)gk[((h->t0 + j) % n + n) % n];
   recon_status rs = RECON_OK;
-  do {
-    cudaError_t e;
-    if ((e = cudaMemcpyAsync(h->taps, taps.data(), h->ntap * sizeof(float), cudaMemcpyHostToDevice, h->st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(h->tw, tw.data(), n * sizeof(float2), cudaMemcpyHostToDevice, h->st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(h->off, off.data(), 3 * n * sizeof(float), cudaMemcpyHostToDevice, h->st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(h->red, 0, h->lay.red, h->st)) != cudaSuccess ||
-        (e = h->mk->build_tables(h->tw, h->tabs, h->tabz, h->st)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(h->st)) != cudaSuccess) {
-      h->err = cudaGetErrorString(e);
-      rs = RECON_ERR_CUDA;
-    }
-  } while (0);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(h->tw, tw.data(), n * sizeof(float2), cudaMemcpyHostToDevice, h->st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(h->red, 0, h->lay.red, h->st)) != cudaSuccess ||
+      (e = h->mk->build_tables(h->tw, h->tabs, h->tabz, h->st)) != cudaSuccess) {
+    h->err = cudaGetErrorString(e);
+    rs = RECON_ERR_CUDA;
+  }
+  if (rs == RECON_OK) rs = configure(h, p);
   if (rs != RECON_OK) {
     if (h->own_ws) cudaFree(h->ws);
     delete h;
     return rs;
   }
-  Geometry& g = h->geo;
-  g.n = n;
-  g.kf = (float)(2.0 * M_PI / h->L);
-  g.inv_n3 = (float)(1.0 / ((double)n * n * n));
-  g.los_mode = p->los_mode;
-  if (p->los_mode == RECON_LOS_FIXED) {
-    const double q = std::sqrt(p->observer[0] * p->observer[0] + p->observer[1] * p->observer[1] +
-                               p->observer[2] * p->observer[2]);
-    g.los = make_float3((float)(p->observer[0] / q), (float)(p->observer[1] / q), (float)(p->observer[2] / q));
-  } else {
-    g.los = make_float3(0.f, 0.f, 0.f);
-  }
-  g.off = h->off;
   *out = h;
   return RECON_OK;
+}
+
+recon_status recon_reconfigure(recon_handle* h, const recon_params* p) {
+  if (!h || !valid_params(p) || p->nmesh[0] != h->n) return RECON_ERR_INVALID_ARG;
+  return configure(h, p);
 }
 
 recon_status recon_set_timing(recon_handle* h, int enable) {
@@ -551,6 +575,7 @@ recon_status recon_set_option(recon_handle* h, int option, int value) {
   if (option == RECON_OPT_DEPOSIT_PATH) h->deposit_path = value;
   else if (option == RECON_OPT_SHIFT_PATH) h->shift_path = value;
   else if (option == RECON_OPT_GRAPH) h->use_graph = value;
+  else if (option == RECON_OPT_LINE_TILE) h->narrow_lines = value;
   else return RECON_ERR_INVALID_ARG;
   return RECON_OK;
 }

@@ -74,6 +74,7 @@ struct SArgs {
   int d_is_k;             // S_DELTA: dk is already fully transformed
   int lognormal;          // S_DELTA: subtract the lognormal constant at k = 0
   const int* skip_flag;   // plain passes: do nothing when *skip_flag != 0 (device-driven loop)
+  int narrow;             // plain x passes: 8-column instead of 16-column tiles
 };
 
 // State of the device-driven iteration (in the workspace).
