@@ -274,6 +274,37 @@ recon_status recon_batch_run(recon_batch_item* items, int n_items, void* stream,
 /* The schedule the batch autotuner chose for mesh side nmesh (STATE if none yet). */
 recon_status recon_batch_plan(int nmesh, int* line_tile, int* deposit_path, int* shift_path);
 
+/* ---- Learned warm start: a small 3-D U-Net (no counterpart in the paper) ----------------------
+ * The network maps, per node of a periodic mesh, 5 input channels — smoothed overdensity delta,
+ * the three components of the line of sight r, and the radial displacement u_0 = Psi_0 . r of the
+ * Eq. approx2 start — to the radial displacement u = Psi . r of the converged solution of Eq. Nusser
+ * (its head adds its output to u_0).  Three levels of widths c1, 2 c1, 4 c1 with two 3x3x3
+ * convolutions + ReLU each, 2x2x2 average pooling, nearest-neighbour upsampling, skip
+ * concatenation, periodic padding.  Tensors are float32 channels-last on the device:
+ * x[(ix n + iy) n + iz][c].  Parameters are one float32 array, layer by layer (enc1a, enc1b, enc2a,
+ * enc2b, bota, botb, dec2a, dec2b, dec1a, dec1b, head), each as weights w[tap][cin][cout]
+ * (tap = (dx+1) 9 + (dy+1) 3 + (dz+1); the head has one tap) then biases b[cout]. */
+typedef struct recon_unet recon_unet;
+
+/* Number of float32 parameters for width c1 (8 or 16). */
+recon_status recon_unet_param_count(int c1, size_t* count);
+/* Network with float32 master weights and AdamW state; activations stored as bfloat16
+ * (bf16_storage = 1) or float32; all sums in float32.  Allocates its own device memory. */
+recon_status recon_unet_create(int c1, int bf16_storage, void* stream, recon_unet** out);
+recon_status recon_unet_set_params(recon_unet* u, const float* host, size_t count);
+recon_status recon_unet_get_params(recon_unet* u, float* host, size_t count);
+/* Gradients of the last recon_unet_backward, same layout as the parameters (host copy). */
+recon_status recon_unet_get_grads(recon_unet* u, float* host, size_t count);
+/* y (device, n^3 float32) = network(x) for x (device, n^3 x 5); n a multiple of 8. */
+recon_status recon_unet_forward(recon_unet* u, const float* x, int n, float* y);
+/* Forward, mean squared error against target (device, n^3) and all parameter gradients; *loss
+ * (host) receives the loss when not NULL. */
+recon_status recon_unet_backward(recon_unet* u, const float* x, const float* target, int n, double* loss);
+/* One AdamW step (beta 0.9 / 0.999, decoupled weight decay wd on the weights, not the biases). */
+recon_status recon_unet_adamw(recon_unet* u, float lr, float wd);
+recon_status recon_unet_destroy(recon_unet* u);
+const char* recon_unet_last_error(recon_unet* u);
+
 /* Release the handle and, if it allocated them, its device buffers. NULL is accepted. */
 recon_status recon_destroy(recon_handle* h);
 

@@ -29,6 +29,9 @@ ABI_SYMBOLS = (
     "recon_fft_r2c", "recon_fft_c2r", "recon_destroy", "recon_status_str", "recon_last_error",
     "recon_set_timing", "recon_get_timing", "recon_reset_timing", "recon_cic_deposit_noalloc",
     "recon_set_option", "recon_reconfigure", "recon_batch_run", "recon_batch_plan",
+    "recon_unet_param_count", "recon_unet_create", "recon_unet_set_params", "recon_unet_get_params",
+    "recon_unet_get_grads", "recon_unet_forward", "recon_unet_backward", "recon_unet_adamw",
+    "recon_unet_destroy", "recon_unet_last_error",
 )
 OPT_DEPOSIT_PATH, OPT_SHIFT_PATH, OPT_GRAPH, OPT_LINE_TILE = 0, 1, 2, 3
 PATH_DIRECT, PATH_SORTED = 0, 1
@@ -94,13 +97,24 @@ def load(path: str = LIB_PATH):
     lib.recon_reconfigure.argtypes = [VP, P(ReconParams)]
     lib.recon_batch_run.argtypes = [P(ReconBatchItem), I, VP, I]
     lib.recon_batch_plan.argtypes = [I, P(I), P(I), P(I)]
+    lib.recon_unet_param_count.argtypes = [I, P(C.c_size_t)]
+    lib.recon_unet_create.argtypes = [I, I, VP, P(VP)]
+    lib.recon_unet_set_params.argtypes = [VP, VP, C.c_size_t]
+    lib.recon_unet_get_params.argtypes = [VP, VP, C.c_size_t]
+    lib.recon_unet_get_grads.argtypes = [VP, VP, C.c_size_t]
+    lib.recon_unet_forward.argtypes = [VP, VP, I, VP]
+    lib.recon_unet_backward.argtypes = [VP, VP, VP, I, P(D)]
+    lib.recon_unet_adamw.argtypes = [VP, C.c_float, C.c_float]
+    lib.recon_unet_destroy.argtypes = [VP]
+    lib.recon_unet_last_error.argtypes = [VP]
+    lib.recon_unet_last_error.restype = C.c_char_p
     lib.recon_cic_deposit_noalloc.argtypes = [VP, I, VP, C.c_int64, I, D, VP, VP, VP]
     lib.recon_status_str.argtypes = [I]
     lib.recon_status_str.restype = C.c_char_p
     lib.recon_last_error.argtypes = [VP]
     lib.recon_last_error.restype = C.c_char_p
     for name in ABI_SYMBOLS:
-        if name not in ("recon_status_str", "recon_last_error"):
+        if name not in ("recon_status_str", "recon_last_error", "recon_unet_last_error"):
             getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -385,3 +399,96 @@ def batch_plan(nmesh):
     a, b, c = C.c_int(), C.c_int(), C.c_int()
     st = lib.recon_batch_plan(int(nmesh), C.byref(a), C.byref(b), C.byref(c))
     return None if st != OK else dict(line_tile=a.value, deposit_path=b.value, shift_path=c.value)
+
+
+class UNet:
+    """The warm-start network (recon_unet_*): parameters live on the device."""
+
+    def __init__(self, c1=16, bf16=True, stream=None):
+        import torch
+        self.lib = load()
+        self.c1 = int(c1)
+        cnt = C.c_size_t(0)
+        st = self.lib.recon_unet_param_count(self.c1, C.byref(cnt))
+        if st != OK:
+            raise ReconError(st, "recon_unet_param_count")
+        self.count = cnt.value
+        h = C.c_void_p()
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        st = self.lib.recon_unet_create(self.c1, int(bool(bf16)), C.c_void_p(s), C.byref(h))
+        if st != OK:
+            raise ReconError(st, "recon_unet_create: " + self.lib.recon_status_str(st).decode())
+        self.h = h
+
+    def _check(self, st, what):
+        if st != OK:
+            raise ReconError(st, f"{what}: {self.lib.recon_status_str(st).decode()} "
+                                 f"({self.lib.recon_unet_last_error(self.h).decode()})")
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        self._check(self.lib.recon_unet_set_params(self.h, flat.ctypes.data, flat.size), "recon_unet_set_params")
+
+    def get_params(self):
+        out = np.empty(self.count, dtype=np.float32)
+        self._check(self.lib.recon_unet_get_params(self.h, out.ctypes.data, out.size), "recon_unet_get_params")
+        return out
+
+    def get_grads(self):
+        out = np.empty(self.count, dtype=np.float32)
+        self._check(self.lib.recon_unet_get_grads(self.h, out.ctypes.data, out.size), "recon_unet_get_grads")
+        return out
+
+    def forward(self, x):
+        import torch
+        n = x.shape[0]
+        x = x.to(device="cuda", dtype=torch.float32).contiguous()
+        y = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+        self._check(self.lib.recon_unet_forward(self.h, C.c_void_p(x.data_ptr()), n, C.c_void_p(y.data_ptr())),
+                    "recon_unet_forward")
+        return y
+
+    def backward(self, x, target):
+        import torch
+        n = x.shape[0]
+        x = x.to(device="cuda", dtype=torch.float32).contiguous()
+        t = target.to(device="cuda", dtype=torch.float32).contiguous()
+        loss = C.c_double(0)
+        self._check(self.lib.recon_unet_backward(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()), n,
+                                                 C.byref(loss)), "recon_unet_backward")
+        return loss.value
+
+    def adamw(self, lr, wd=1e-4):
+        self._check(self.lib.recon_unet_adamw(self.h, float(lr), float(wd)), "recon_unet_adamw")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.recon_unet_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def flat_params(params, specs):
+    """Flatten {name: (w, b)} in the layer order of the ABI (host float32)."""
+    parts = []
+    for name, _, _ in specs:
+        w, b = params[name]
+        parts += [np.asarray(w, dtype=np.float64).ravel(), np.asarray(b, dtype=np.float64).ravel()]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def unflat_params(flat, specs):
+    out, o = {}, 0
+    for name, ci, co in specs:
+        nt = 1 if name == "head" else 27
+        w = flat[o:o + nt * ci * co].reshape(nt, ci, co)
+        o += nt * ci * co
+        b = flat[o:o + co]
+        o += co
+        out[name] = (w, b)
+    return out
