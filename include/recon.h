@@ -135,6 +135,22 @@ recon_status recon_smooth(recon_handle* h);
 recon_status recon_iterate(recon_handle* h, int start, double tol, int max_iter, int* n_iter,
                            double* rel_change);
 
+/* The iteration of recon_iterate started from a supplied radial displacement u0 (device, N^3
+ * float32 [ix][iy][iz]): P_0 = u0 r instead of an analytic start (the learned warm start feeds the
+ * network's output here; u0 = the converged Psi . r reproduces the fixed point).  Same stopping
+ * rule, outputs and trace as recon_iterate.  u0 is borrowed for the call. */
+recon_status recon_iterate_from(recon_handle* h, const float* u0, double tol, int max_iter, int* n_iter,
+                                double* rel_change);
+
+/* Network inputs for the learned start, after recon_smooth: feat (device, N^3 x 5 float32,
+ * channels-last) = (delta, r_x, r_y, r_z, u_0) per node, u_0 = (1 - c)(Z[delta/b] . r) the radial
+ * displacement of the analytic start `start` (RECON_START_*).  Consumes the real delta copy
+ * (RECON_FIELD_DELTA is no longer available); the handle stays ready for recon_iterate(_from). */
+recon_status recon_start_features(recon_handle* h, int start, float* feat);
+
+/* The radial displacement u = Psi . r of the final Psi (device, N^3 float32), after an iterate. */
+recon_status recon_get_radial(recon_handle* h, float* u);
+
 /* The rel values of the last recon_iterate: up to cap entries into rel (host), count into *n. */
 recon_status recon_get_trace(recon_handle* h, double* rel, int cap, int* n);
 

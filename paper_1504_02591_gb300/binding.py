@@ -31,7 +31,8 @@ ABI_SYMBOLS = (
     "recon_set_option", "recon_reconfigure", "recon_batch_run", "recon_batch_plan",
     "recon_unet_param_count", "recon_unet_create", "recon_unet_set_params", "recon_unet_get_params",
     "recon_unet_get_grads", "recon_unet_forward", "recon_unet_backward", "recon_unet_adamw",
-    "recon_unet_destroy", "recon_unet_last_error",
+    "recon_unet_destroy", "recon_unet_last_error", "recon_iterate_from", "recon_start_features",
+    "recon_get_radial",
 )
 OPT_DEPOSIT_PATH, OPT_SHIFT_PATH, OPT_GRAPH, OPT_LINE_TILE = 0, 1, 2, 3
 PATH_DIRECT, PATH_SORTED = 0, 1
@@ -97,6 +98,9 @@ def load(path: str = LIB_PATH):
     lib.recon_reconfigure.argtypes = [VP, P(ReconParams)]
     lib.recon_batch_run.argtypes = [P(ReconBatchItem), I, VP, I]
     lib.recon_batch_plan.argtypes = [I, P(I), P(I), P(I)]
+    lib.recon_iterate_from.argtypes = [VP, VP, D, I, P(I), P(D)]
+    lib.recon_start_features.argtypes = [VP, I, VP]
+    lib.recon_get_radial.argtypes = [VP, VP]
     lib.recon_unet_param_count.argtypes = [I, P(C.c_size_t)]
     lib.recon_unet_create.argtypes = [I, I, VP, P(VP)]
     lib.recon_unet_set_params.argtypes = [VP, VP, C.c_size_t]
@@ -255,6 +259,33 @@ class Recon:
         st = self.lib.recon_iterate(self.h, int(start), float(tol), int(max_iter), C.byref(n), C.byref(rel))
         self._check(st, "recon_iterate", allow=(ERR_NOT_CONVERGED,))
         return n.value, rel.value, st
+
+    def iterate_from(self, u0, tol=0.0, max_iter=6):
+        """Iterate from a supplied radial displacement u0 (CUDA tensor, N^3); (n_iter, rel, status)."""
+        import torch
+        u0 = u0.to(device="cuda", dtype=torch.float32).contiguous()
+        n = C.c_int(0)
+        rel = C.c_double(0)
+        st = self.lib.recon_iterate_from(self.h, C.c_void_p(u0.data_ptr()), float(tol), int(max_iter), C.byref(n),
+                                         C.byref(rel))
+        self._check(st, "recon_iterate_from", allow=(ERR_NOT_CONVERGED,))
+        return n.value, rel.value, st
+
+    def start_features(self, start=START_FFTA):
+        """(N, N, N, 5) CUDA tensor of network inputs (delta, r, u_0), after smooth()."""
+        import torch
+        n = self.n
+        feat = torch.empty((n, n, n, 5), dtype=torch.float32, device="cuda")
+        self._check(self.lib.recon_start_features(self.h, int(start), C.c_void_p(feat.data_ptr())),
+                    "recon_start_features")
+        return feat
+
+    def get_radial(self):
+        import torch
+        n = self.n
+        u = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+        self._check(self.lib.recon_get_radial(self.h, C.c_void_p(u.data_ptr())), "recon_get_radial")
+        return u
 
     def trace(self):
         buf = (C.c_double * 4096)()

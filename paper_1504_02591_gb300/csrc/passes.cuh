@@ -155,6 +155,30 @@ __global__ void __launch_bounds__(kZThreads, 4) zpass_kernel(const ZArgs a) {
       __syncwarp();
 #pragma unroll
       for (int q = 0; q < NF; ++q) Plan<L>::template run<1, 32, true, Lay, true>(s + q * Lay::kStride, tab);
+    } else if (MODE == Z_USTART) {
+      // a supplied radial displacement u: P_j = u r_j on the row, then the forward r2c of P
+      const Geometry& g = a.g;
+      const int ix = (int)(row / N), iy = (int)(row % N);
+      const float dx = g.los_mode == 1 ? 0.f : g.off[ix], dy = g.los_mode == 1 ? 0.f : g.off[N + iy];
+      const float* ur = a.u_in + row * N;
+      for (int m = lane; m < L; m += 32) {
+        const float2 uu = reinterpret_cast<const float2*>(ur)[m];
+        float r[2][3];
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          if (g.los_mode == 1) {
+            r[h2][0] = g.los.x; r[h2][1] = g.los.y; r[h2][2] = g.los.z;
+          } else {
+            const float dz = g.off[2 * N + 2 * m + h2];
+            const float q = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float inv = q > 0.f ? rsqrtf(q) : 0.f;
+            r[h2][0] = dx * inv; r[h2][1] = dy * inv; r[h2][2] = dz * inv;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) s[Lay::phys(m, q)] = make_float2(uu.x * r[0][q], uu.y * r[1][q]);
+      }
+      __syncwarp();
     } else if (MODE == Z_DELTA) {
       // rows of rho_g (and rho_r) smoothed along x and y: z factor of the Gaussian as a periodic
       // convolution, then delta (Sec. 3.2) node by node
@@ -567,7 +591,7 @@ struct MeshImpl {
   static cudaError_t zpass(int mode, int nc, const ZArgs& a, cudaStream_t st, int* grid_out) {
 #define RG_Z(M_, NC_) \
   if (mode == M_ && nc == NC_) return zlaunch<M_, NC_>(a, st, grid_out);
-    RG_Z(Z_FWD, 1) RG_Z(Z_INV, 1) RG_Z(Z_DELTA, 2) RG_Z(Z_PROJ, 3) RG_Z(Z_FINAL, 3)
+    RG_Z(Z_FWD, 1) RG_Z(Z_INV, 1) RG_Z(Z_DELTA, 2) RG_Z(Z_PROJ, 3) RG_Z(Z_FINAL, 3) RG_Z(Z_USTART, 3)
 #undef RG_Z
     return cudaErrorInvalidValue;
   }

@@ -20,6 +20,7 @@
 #include "cic.h"
 #include "conv.h"
 #include "loop.h"
+#include "warm.h"
 #include "types.h"
 
 namespace rg {
@@ -701,6 +702,8 @@ recon_status iterate_body(recon_handle* h, cudaGraphConditionalHandle cond) {
   return RECON_OK;
 }
 
+recon_status iterate_start_from(recon_handle* h, const float* u0);
+
 struct GraphGuard {
   cudaGraph_t gs = nullptr, g = nullptr;
   cudaGraphExec_t ex = nullptr;
@@ -713,8 +716,8 @@ struct GraphGuard {
 
 // The whole iteration as one CUDA graph: the start sequence, then a conditional WHILE node whose
 // body is one update.  One launch, one host synchronisation at the end.
-recon_status iterate_graph(recon_handle* h, float coef0, double tol, int max_iter, int* it_out, double* rel_out,
-                           int* flag_out) {
+recon_status iterate_graph(recon_handle* h, float coef0, const float* u0, double tol, int max_iter, int* it_out,
+                           double* rel_out, int* flag_out) {
   if (!h->cap_stream) RG_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   const cudaStream_t user = h->st;
   const int timing = h->timing;
@@ -729,7 +732,7 @@ recon_status iterate_graph(recon_handle* h, float coef0, double tol, int max_ite
     if ((e = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
     rs = [&]() -> recon_status {
       RG_CUDA(launch_loop_init(h->loop, tol, max_iter, h->st));
-      return iterate_start(h, coef0);
+      return u0 ? iterate_start_from(h, u0) : iterate_start(h, coef0);
     }();
     e = cudaStreamEndCapture(h->st, &gg.gs);
     if (rs != RECON_OK) break;
@@ -780,30 +783,43 @@ recon_status iterate_graph(recon_handle* h, float coef0, double tol, int max_ite
 
 }  // namespace
 
-recon_status recon_iterate(recon_handle* h, int start, double tol, int max_iter, int* n_iter, double* rel_change) {
-  if (!h) return RECON_ERR_INVALID_ARG;
-  if (h->state < ST_SMOOTHED) return RECON_ERR_STATE;
-  if (max_iter < 1 || !(tol >= 0) || start < RECON_START_PLAIN || start > RECON_START_FFTA)
-    return RECON_ERR_INVALID_ARG;
-  const double beta = h->p.f / h->p.b;
-  const float coef0 = (float)(1.0 - start_coefficient(start, beta));
+namespace {
+
+// Start sequence for a supplied radial displacement u0 (device, N^3): delta(k) and S_-1 along y,
+// then P_0 = u0 r transformed along z and x.
+recon_status iterate_start_from(recon_handle* h, const float* u0) {
+  {
+    SArgs a = sargs(h);
+    for (int q = 0; q < 3; ++q) a.f[q] = h->V[q];
+    a.d_is_k = h->d_is_k;
+    RG_TRY(run_s(h, S_DELTA, 1, AX_Y, a));
+  }
+  ZArgs za = zargs(h);
+  for (int q = 0; q < 3; ++q) za.f[q] = h->V[q];
+  za.u_in = u0;
+  RG_TRY(run_z(h, Z_USTART, 3, za));
+  RG_TRY(xpass(h, S_FWD, 3, h->V));
+  return RECON_OK;
+}
+
+// The loop of Sec. 5.1 after a start: device-driven (one CUDA graph) or host-driven.
+recon_status iterate_core(recon_handle* h, float coef0, const float* u0, double tol, int max_iter, int* n_iter,
+                          double* rel_change) {
   h->trace.clear();
   h->delta_real_valid = 0;
   double rel = 0.0;
   int it = 0;
   recon_status result = RECON_OK;
   if (h->use_graph && !h->timing && max_iter <= kMaxTrace) {
-    // device-driven loop in one CUDA graph
     int flag = 0;
-    RG_TRY(iterate_graph(h, coef0, tol, max_iter, &it, &rel, &flag));
+    RG_TRY(iterate_graph(h, coef0, u0, tol, max_iter, &it, &rel, &flag));
     h->d_is_k = 1;
     if (flag == 2) {
       h->state = ST_SMOOTHED;
       result = RECON_ERR_NONFINITE;
     }
   } else {
-    // host-driven loop: the norms come back to the host after every update
-    RG_TRY(iterate_start(h, coef0));
+    RG_TRY(u0 ? iterate_start_from(h, u0) : iterate_start(h, coef0));
     h->d_is_k = 1;
     ZArgs za = zargs(h);
     for (int q = 0; q < 3; ++q) za.f[q] = h->V[q];
@@ -845,6 +861,59 @@ recon_status recon_iterate(recon_handle* h, int start, double tol, int max_iter,
   if (n_iter) *n_iter = it;
   if (rel_change) *rel_change = rel;
   return result;
+}
+
+}  // namespace
+
+recon_status recon_iterate(recon_handle* h, int start, double tol, int max_iter, int* n_iter, double* rel_change) {
+  if (!h) return RECON_ERR_INVALID_ARG;
+  if (h->state < ST_SMOOTHED) return RECON_ERR_STATE;
+  if (max_iter < 1 || !(tol >= 0) || start < RECON_START_PLAIN || start > RECON_START_FFTA)
+    return RECON_ERR_INVALID_ARG;
+  const double beta = h->p.f / h->p.b;
+  const float coef0 = (float)(1.0 - start_coefficient(start, beta));
+  return iterate_core(h, coef0, nullptr, tol, max_iter, n_iter, rel_change);
+}
+
+recon_status recon_iterate_from(recon_handle* h, const float* u0, double tol, int max_iter, int* n_iter,
+                                double* rel_change) {
+  if (!h || !u0) return RECON_ERR_INVALID_ARG;
+  if (h->state < ST_SMOOTHED) return RECON_ERR_STATE;
+  if (max_iter < 1 || !(tol >= 0)) return RECON_ERR_INVALID_ARG;
+  return iterate_core(h, 1.f, u0, tol, max_iter, n_iter, rel_change);
+}
+
+recon_status recon_start_features(recon_handle* h, int start, float* feat) {
+  if (!h || !feat || start < RECON_START_PLAIN || start > RECON_START_FFTA) return RECON_ERR_INVALID_ARG;
+  if (h->state < ST_SMOOTHED || !h->delta_real_valid) return RECON_ERR_STATE;
+  RG_CUDA(timed(h, RECON_K_OTHER, 0.0, [&] {
+    return launch_features(reinterpret_cast<const float*>(h->V[2].M), h->geo, feat, h->st); }));
+  {
+    SArgs a = sargs(h);
+    for (int q = 0; q < 3; ++q) a.f[q] = h->V[q];
+    a.d_is_k = h->d_is_k;
+    RG_TRY(run_s(h, S_DELTA, 1, AX_Y, a));
+    h->d_is_k = 1;
+  }
+  RG_TRY(xpass(h, S_INV, 3, h->V));
+  ZArgs za = zargs(h);
+  for (int q = 0; q < 3; ++q) za.f[q] = h->V[q];
+  RG_TRY(run_z(h, Z_FINAL, 3, za));
+  const float coef = (float)(1.0 - start_coefficient(start, h->p.f / h->p.b));
+  RG_CUDA(timed(h, RECON_K_OTHER, 0.0, [&] {
+    return launch_radial(reinterpret_cast<const float*>(h->V[0].M), reinterpret_cast<const float*>(h->V[1].M),
+                         reinterpret_cast<const float*>(h->V[2].M), h->geo, coef, feat, 5, 4, h->st); }));
+  h->delta_real_valid = 0;
+  return RECON_OK;
+}
+
+recon_status recon_get_radial(recon_handle* h, float* u) {
+  if (!h || !u) return RECON_ERR_INVALID_ARG;
+  if (h->state != ST_ITERATED) return RECON_ERR_STATE;
+  RG_CUDA(timed(h, RECON_K_OTHER, 0.0, [&] {
+    return launch_radial(reinterpret_cast<const float*>(h->V[0].M), reinterpret_cast<const float*>(h->V[1].M),
+                         reinterpret_cast<const float*>(h->V[2].M), h->geo, 1.f, u, 1, 0, h->st); }));
+  return RECON_OK;
 }
 
 recon_status recon_get_trace(recon_handle* h, double* rel, int cap, int* n) {

@@ -37,7 +37,7 @@ struct Geometry {
   const float* off;       // 3 N node offsets from the observer: x_i - o_a, per axis a (radial)
 };
 
-enum ZMode { Z_FWD = 0, Z_INV = 1, Z_DELTA = 2, Z_PROJ = 3, Z_FINAL = 4 };
+enum ZMode { Z_FWD = 0, Z_INV = 1, Z_DELTA = 2, Z_PROJ = 3, Z_FINAL = 4, Z_USTART = 5 };
 enum SMode { S_FWD = 0, S_INV = 1, S_DELTA = 3, S_ITER = 4 };
 enum Axis { AX_X = 0, AX_Y = 1 };
 
@@ -59,6 +59,7 @@ struct ZArgs {
   int ntap;
   int t0;
   const int* loop_flag;   // Z_PROJ in a device-driven loop: 1 = converged, write the real Psi
+  const float* u_in;      // Z_USTART: radial displacement u (real N^3); P = u r is transformed
 };
 
 struct SArgs {
