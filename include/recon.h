@@ -311,13 +311,24 @@ recon_status recon_unet_set_params(recon_unet* u, const float* host, size_t coun
 recon_status recon_unet_get_params(recon_unet* u, float* host, size_t count);
 /* Gradients of the last recon_unet_backward, same layout as the parameters (host copy). */
 recon_status recon_unet_get_grads(recon_unet* u, float* host, size_t count);
-/* y (device, n^3 float32) = network(x) for x (device, n^3 x 5); n a multiple of 8. */
+/* y (device, n^3 float32) = network(x) for x (device, n^3 x 5); n a multiple of 8.  With bfloat16
+ * storage, the convolutions of every level whose side is 64 or a multiple of 128 run on the tensor
+ * cores (tcgen05.mma, float32 accumulation in tensor memory); the others on the CUDA cores.  Both
+ * round every stored activation to bfloat16 at the same points, so they differ only in the order
+ * of the float32 sums.  Returns ERR_CUDA if a tensor-core wait timed out. */
 recon_status recon_unet_forward(recon_unet* u, const float* x, int n, float* y);
 /* Forward, mean squared error against target (device, n^3) and all parameter gradients; *loss
  * (host) receives the loss when not NULL. */
 recon_status recon_unet_backward(recon_unet* u, const float* x, const float* target, int n, double* loss);
 /* One AdamW step (beta 0.9 / 0.999, decoupled weight decay wd on the weights, not the biases). */
 recon_status recon_unet_adamw(recon_unet* u, float lr, float wd);
+/* Options: RECON_UNET_OPT_TENSOR_CORES (1 default, 0 = every convolution on the CUDA cores). */
+enum { RECON_UNET_OPT_TENSOR_CORES = 0 };
+recon_status recon_unet_set_option(recon_unet* u, int option, int value);
+/* Output of convolution layer `layer` (0..9, in the parameter order) from the last forward, as
+ * float32 on the host (count = side^3 x cout of that layer's level).  STATE if that activation was
+ * not stored (the last layer when its 1x1 head was fused into it). */
+recon_status recon_unet_get_layer(recon_unet* u, int layer, float* host, size_t count);
 recon_status recon_unet_destroy(recon_unet* u);
 const char* recon_unet_last_error(recon_unet* u);
 

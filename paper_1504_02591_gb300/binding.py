@@ -31,10 +31,12 @@ ABI_SYMBOLS = (
     "recon_set_option", "recon_reconfigure", "recon_batch_run", "recon_batch_plan",
     "recon_unet_param_count", "recon_unet_create", "recon_unet_set_params", "recon_unet_get_params",
     "recon_unet_get_grads", "recon_unet_forward", "recon_unet_backward", "recon_unet_adamw",
-    "recon_unet_destroy", "recon_unet_last_error", "recon_iterate_from", "recon_start_features",
+    "recon_unet_destroy", "recon_unet_last_error", "recon_unet_set_option", "recon_unet_get_layer",
+    "recon_iterate_from", "recon_start_features",
     "recon_get_radial",
 )
 OPT_DEPOSIT_PATH, OPT_SHIFT_PATH, OPT_GRAPH, OPT_LINE_TILE = 0, 1, 2, 3
+UNET_OPT_TENSOR_CORES = 0
 PATH_DIRECT, PATH_SORTED = 0, 1
 KERNEL_KINDS = ("deposit", "z_fwd", "z_inv", "z_delta", "z_proj", "z_final", "line_fwd", "line_inv",
                 "conv", "k_delta", "k_iter", "shift", "other", "sort")
@@ -110,6 +112,8 @@ def load(path: str = LIB_PATH):
     lib.recon_unet_backward.argtypes = [VP, VP, VP, I, P(D)]
     lib.recon_unet_adamw.argtypes = [VP, C.c_float, C.c_float]
     lib.recon_unet_destroy.argtypes = [VP]
+    lib.recon_unet_set_option.argtypes = [VP, C.c_int, C.c_int]
+    lib.recon_unet_get_layer.argtypes = [VP, C.c_int, VP, C.c_size_t]
     lib.recon_unet_last_error.argtypes = [VP]
     lib.recon_unet_last_error.restype = C.c_char_p
     lib.recon_cic_deposit_noalloc.argtypes = [VP, I, VP, C.c_int64, I, D, VP, VP, VP]
@@ -491,6 +495,16 @@ class UNet:
 
     def adamw(self, lr, wd=1e-4):
         self._check(self.lib.recon_unet_adamw(self.h, float(lr), float(wd)), "recon_unet_adamw")
+
+    def set_option(self, option, value):
+        self._check(self.lib.recon_unet_set_option(self.h, int(option), int(value)), "recon_unet_set_option")
+
+    def get_layer(self, layer, n, cout):
+        """Output of convolution layer `layer` of the last forward, (n, n, n, cout) host float32."""
+        out = np.empty((n, n, n, cout), dtype=np.float32)
+        self._check(self.lib.recon_unet_get_layer(self.h, int(layer), out.ctypes.data, out.size),
+                    "recon_unet_get_layer")
+        return out
 
     def close(self):
         if getattr(self, "h", None):

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/recon.h"
+#include "unet_tc.h"
 
 namespace rg {
 namespace {
@@ -296,6 +297,16 @@ __global__ void to_t_kernel(const float* __restrict__ x, T* __restrict__ y, long
     y[i] = fromf<T>(x[i]);
 }
 
+// network input for the tensor-core path: 5 float32 channels -> 8 bf16 channels (16 bytes a voxel)
+__global__ void to_x8_kernel(const float* __restrict__ x, int cin, long long nv, bf16* __restrict__ y) {
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x) {
+    __align__(16) bf16 o[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) o[c] = __float2bfloat16_rn(c < cin ? x[v * cin + c] : 0.f);
+    *reinterpret_cast<uint4*>(y + v * 8) = *reinterpret_cast<const uint4*>(o);
+  }
+}
+
 // mean squared error: g = 2 (y - t) / m, loss = sum (y - t)^2 / m (float64 accumulation)
 __global__ void mse_kernel(const float* __restrict__ y, const float* __restrict__ t, long long m, float* __restrict__ g,
                            double* __restrict__ loss) {
@@ -362,6 +373,18 @@ struct recon_unet {
   float* y = nullptr;                  // network output (float)
   double* loss = nullptr;
   std::string err;
+  // tensor-core forward
+  int use_tc = 1;
+  int* dev_err = nullptr;              // set by a tensor-core kernel whose wait timed out
+  void* wpack = nullptr;               // packed weight tiles of the layers on the tensor-core path
+  size_t wpack_cap = 0;
+  rg::tc::ConvPlan plan[10];
+  bool plan_ok[10] = {};
+  size_t pack_off[10] = {};
+  int plan_n = 0;
+  unsigned pver = 1, packed_ver = 0;   // parameter version, version the packed tiles were made from
+  int last_n = 0;                      // side of the last forward
+  bool head_fused = false;             // last forward fused the head into layer 9 (d1b not stored)
 };
 
 namespace {
@@ -385,7 +408,7 @@ void make_spec(recon_unet* u) {
 
 // activation layout for one grid of side n (offsets in elements of the stored type)
 struct Acts {
-  size_t x, a1a, a1b, p1, a2a, a2b, p2, a3a, a3b, u3, d2a, d2b, u2, d1a, d1b, total;
+  size_t x, a1a, a1b, p1, a2a, a2b, p2, a3a, a3b, u3, d2a, d2b, u2, d1a, d1b, x8, total;
 };
 Acts act_layout(const recon_unet* u, int n) {
   const size_t V1 = (size_t)n * n * n, V2 = V1 / 8, V3 = V1 / 64;
@@ -399,6 +422,7 @@ Acts act_layout(const recon_unet* u, int n) {
   a.a3a = take(V3 * c3); a.a3b = take(V3 * c3); a.u3 = take(V2 * c3);
   a.d2a = take(V2 * c2); a.d2b = take(V2 * c2); a.u2 = take(V1 * c2);
   a.d1a = take(V1 * c1); a.d1b = take(V1 * c1);
+  a.x8 = take(V1 * 8);
   a.total = o;
   return a;
 }
@@ -517,6 +541,128 @@ recon_status forward_t(recon_unet* u, const float* x, int n, float* out) {
   return RECON_OK;
 }
 
+// Tensor-core plans for the ten 3x3x3 layers at grid side n (levels n, n/2, n/4), and the packed
+// weight tiles; a layer whose level does not fit the tensor-core tiling stays on the CUDA cores.
+recon_status tc_prepare(recon_unet* u, int n) {
+  const int c1 = u->c1, c2 = 2 * c1, c3 = 4 * c1, n2 = n / 2, n4 = n / 4;
+  if (u->plan_n != n) {
+    struct L {
+      int n, c0, up0, c1, cin, cout;
+    };
+    const L ls[10] = {{n, 8, 0, 0, u->cin, c1},      {n, c1, 0, 0, c1, c1},         {n2, c1, 0, 0, c1, c2},
+                      {n2, c2, 0, 0, c2, c2},        {n4, c2, 0, 0, c2, c3},        {n4, c3, 0, 0, c3, c3},
+                      {n2, c3, 1, c2, c3 + c2, c2},  {n2, c2, 0, 0, c2, c2},        {n, c2, 1, c1, c2 + c1, c1},
+                      {n, c1, 0, 0, c1, c1}};
+    size_t off = 0;
+    for (int l = 0; l < 10; ++l) {
+      u->plan_ok[l] = tc::plan_conv(ls[l].n, ls[l].c0, ls[l].up0, ls[l].c1, ls[l].cin, ls[l].cout, &u->plan[l]);
+      u->pack_off[l] = off;
+      if (u->plan_ok[l]) off += (u->plan[l].packed_elems + 127) / 128 * 128;
+    }
+    if (off * sizeof(bf16) > u->wpack_cap) {
+      cudaFree(u->wpack);
+      u->wpack = nullptr;
+      u->wpack_cap = 0;
+      if (cudaMalloc(&u->wpack, off * sizeof(bf16)) != cudaSuccess) {
+        cudaGetLastError();
+        u->plan_n = 0;
+        return RECON_ERR_OOM;
+      }
+      u->wpack_cap = off * sizeof(bf16);
+    }
+    u->plan_n = n;
+    u->packed_ver = 0;
+  }
+  if (u->packed_ver != u->pver) {
+    const bf16* w = static_cast<const bf16*>(u->pt);
+    for (int l = 0; l < 10; ++l)
+      if (u->plan_ok[l])
+        UN_CUDA(tc::pack_weights(u->plan[l], w + u->woff[l], static_cast<bf16*>(u->wpack) + u->pack_off[l], u->st));
+    u->packed_ver = u->pver;
+  }
+  return RECON_OK;
+}
+
+// Inference forward with bf16 storage: the same network and rounding points as forward_t<bf16>,
+// with the convolutions on the tensor cores where the level allows, the upsampling folded into the
+// loads of the decoder convolutions and the 1x1 head folded into the last convolution.
+recon_status forward_tc(recon_unet* u, const float* x, int n, float* out) {
+  recon_status rs = tc_prepare(u, n);
+  if (rs != RECON_OK) return rs;
+  const Acts A = act_layout(u, n);
+  bf16* a = static_cast<bf16*>(u->acts);
+  const bf16* wp = static_cast<const bf16*>(u->wpack);
+  const int c1 = u->c1, c2 = 2 * c1, c3 = 4 * c1, n2 = n / 2, n4 = n / 4;
+  const long long V1 = (long long)n * n * n;
+  auto run = [&](int l, const bf16* s0, const bf16* s1, bf16* y) -> cudaError_t {
+    tc::ConvIO io;
+    io.src0 = s0;
+    io.src1 = s1;
+    io.wpack = wp + u->pack_off[l];
+    io.bias = u->p + u->boff[l];
+    io.out = y;
+    io.err = u->dev_err;
+    return tc::conv_forward(u->plan[l], io, u->st);
+  };
+  auto plain = [&](int l, const bf16* s0, int ca, bf16* y, int nl) -> cudaError_t {
+    return u->plan_ok[l] ? run(l, s0, nullptr, y)
+                         : conv_fwd<bf16>(u, l, s0, ca, nullptr, 0, nl, 1, nullptr, 0, y, nullptr);
+  };
+  if (u->plan_ok[0]) {
+    to_x8_kernel<<<grid_for(V1), 256, 0, u->st>>>(x, u->cin, V1, a + A.x8);
+    UN_CUDA(run(0, a + A.x8, nullptr, a + A.a1a));
+  } else {
+    to_t_kernel<bf16><<<grid_for(V1 * u->cin), 256, 0, u->st>>>(x, a + A.x, V1 * u->cin);
+    UN_CUDA(conv_fwd<bf16>(u, 0, a + A.x, u->cin, nullptr, 0, n, 1, nullptr, 0, a + A.a1a, nullptr));
+  }
+  UN_CUDA(plain(1, a + A.a1a, c1, a + A.a1b, n));
+  pool_kernel<bf16><<<grid_for(V1 / 8 * c1), 256, 0, u->st>>>(a + A.a1b, c1, n, a + A.p1);
+  UN_CUDA(plain(2, a + A.p1, c1, a + A.a2a, n2));
+  UN_CUDA(plain(3, a + A.a2a, c2, a + A.a2b, n2));
+  pool_kernel<bf16><<<grid_for(V1 / 64 * c2), 256, 0, u->st>>>(a + A.a2b, c2, n2, a + A.p2);
+  UN_CUDA(plain(4, a + A.p2, c2, a + A.a3a, n4));
+  UN_CUDA(plain(5, a + A.a3a, c3, a + A.a3b, n4));
+  if (u->plan_ok[6]) {
+    UN_CUDA(run(6, a + A.a3b, a + A.a2b, a + A.d2a));
+  } else {
+    up_kernel<bf16><<<grid_for(V1 / 8 * c3), 256, 0, u->st>>>(a + A.a3b, c3, n2, a + A.u3);
+    UN_CUDA(conv_fwd<bf16>(u, 6, a + A.u3, c3, a + A.a2b, c2, n2, 1, nullptr, 0, a + A.d2a, nullptr));
+  }
+  UN_CUDA(plain(7, a + A.d2a, c2, a + A.d2b, n2));
+  if (u->plan_ok[8]) {
+    UN_CUDA(run(8, a + A.d2b, a + A.a1b, a + A.d1a));
+  } else {
+    up_kernel<bf16><<<grid_for(V1 * c2), 256, 0, u->st>>>(a + A.d2b, c2, n, a + A.u2);
+    UN_CUDA(conv_fwd<bf16>(u, 8, a + A.u2, c2, a + A.a1b, c1, n, 1, nullptr, 0, a + A.d1a, nullptr));
+  }
+  u->head_fused = u->plan_ok[9] && u->plan[9].orient == 0;
+  if (u->head_fused) {
+    tc::ConvIO io;
+    io.src0 = a + A.d1a;
+    io.wpack = wp + u->pack_off[9];
+    io.bias = u->p + u->boff[9];
+    io.head_w = static_cast<const bf16*>(u->pt) + u->woff[10];
+    io.head_b = u->p + u->boff[10];
+    io.res = x + (u->cin - 1);
+    io.res_stride = u->cin;
+    io.yout = out;
+    io.err = u->dev_err;
+    UN_CUDA(tc::conv_forward(u->plan[9], io, u->st));
+  } else {
+    UN_CUDA(plain(9, a + A.d1a, c1, a + A.d1b, n));
+    UN_CUDA(conv_fwd<bf16>(u, 10, a + A.d1b, c1, nullptr, 0, n, 0, x + (u->cin - 1), u->cin, nullptr, out));
+  }
+  int flag = 0;
+  UN_CUDA(cudaMemcpyAsync(&flag, u->dev_err, sizeof(int), cudaMemcpyDeviceToHost, u->st));
+  UN_CUDA(cudaStreamSynchronize(u->st));
+  if (flag) {
+    cudaMemsetAsync(u->dev_err, 0, sizeof(int), u->st);
+    u->err = "tensor-core convolution: a pipeline wait timed out";
+    return RECON_ERR_CUDA;
+  }
+  return RECON_OK;
+}
+
 template <typename T>
 recon_status backward_t(recon_unet* u, const float* x, const float* target, int n, double* loss) {
   recon_status rs = forward_t<T>(u, x, n, u->y);
@@ -591,7 +737,7 @@ recon_status recon_unet_create(int c1, int bf16_storage, void* stream, recon_une
   if (cudaMalloc(&u->p, u->np * 4) != cudaSuccess || cudaMalloc(&u->g, u->np * 4) != cudaSuccess ||
       cudaMalloc(&u->m1, u->np * 4) != cudaSuccess || cudaMalloc(&u->m2, u->np * 4) != cudaSuccess ||
       cudaMalloc(&u->decay, u->np) != cudaSuccess || cudaMalloc(&u->pt, u->np * es) != cudaSuccess ||
-      cudaMalloc(&u->loss, sizeof(double)) != cudaSuccess) {
+      cudaMalloc(&u->loss, sizeof(double)) != cudaSuccess || cudaMalloc(&u->dev_err, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     recon_unet_destroy(u);
     return RECON_ERR_OOM;
@@ -601,7 +747,8 @@ recon_status recon_unet_create(int c1, int bf16_storage, void* stream, recon_une
     for (size_t i = u->woff[l]; i < u->boff[l]; ++i) dec[i] = 1;
   if (cudaMemcpy(u->decay, dec.data(), u->np, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(u->p, 0, u->np * 4) != cudaSuccess || cudaMemset(u->pt, 0, u->np * es) != cudaSuccess ||
-      cudaMemset(u->m1, 0, u->np * 4) != cudaSuccess || cudaMemset(u->m2, 0, u->np * 4) != cudaSuccess) {
+      cudaMemset(u->m1, 0, u->np * 4) != cudaSuccess || cudaMemset(u->m2, 0, u->np * 4) != cudaSuccess ||
+      cudaMemset(u->dev_err, 0, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     recon_unet_destroy(u);
     return RECON_ERR_CUDA;
@@ -620,6 +767,7 @@ recon_status recon_unet_set_params(recon_unet* u, const float* host, size_t coun
   UN_CUDA(cudaMemsetAsync(u->m1, 0, u->np * 4, u->st));
   UN_CUDA(cudaMemsetAsync(u->m2, 0, u->np * 4, u->st));
   u->step = 0;
+  ++u->pver;
   UN_CUDA(cudaStreamSynchronize(u->st));
   return RECON_OK;
 }
@@ -642,6 +790,9 @@ recon_status recon_unet_forward(recon_unet* u, const float* x, int n, float* y) 
   if (!u || !x || !y) return RECON_ERR_INVALID_ARG;
   recon_status rs = ensure(u, n, false);
   if (rs != RECON_OK) return rs;
+  u->last_n = n;
+  u->head_fused = false;
+  if (u->bf16 && u->use_tc) return forward_tc(u, x, n, y);
   return u->bf16 ? forward_t<bf16>(u, x, n, y) : forward_t<float>(u, x, n, y);
 }
 
@@ -649,12 +800,15 @@ recon_status recon_unet_backward(recon_unet* u, const float* x, const float* tar
   if (!u || !x || !target) return RECON_ERR_INVALID_ARG;
   recon_status rs = ensure(u, n, true);
   if (rs != RECON_OK) return rs;
+  u->last_n = n;
+  u->head_fused = false;
   return u->bf16 ? backward_t<bf16>(u, x, target, n, loss) : backward_t<float>(u, x, target, n, loss);
 }
 
 recon_status recon_unet_adamw(recon_unet* u, float lr, float wd) {
   if (!u || !(lr > 0) || !(wd >= 0)) return RECON_ERR_INVALID_ARG;
   u->step += 1;
+  ++u->pver;
   const float c1 = 1.f - powf(0.9f, (float)u->step), c2 = 1.f - powf(0.999f, (float)u->step);
   if (u->bf16)
     adamw_kernel<bf16><<<grid_for((long long)u->np), 256, 0, u->st>>>(u->p, u->g, u->m1, u->m2, u->decay,
@@ -681,7 +835,41 @@ recon_status recon_unet_destroy(recon_unet* u) {
   cudaFree(u->acts);
   cudaFree(u->grads);
   cudaFree(u->y);
+  cudaFree(u->dev_err);
+  cudaFree(u->wpack);
   delete u;
+  return RECON_OK;
+}
+
+recon_status recon_unet_set_option(recon_unet* u, int option, int value) {
+  if (!u) return RECON_ERR_INVALID_ARG;
+  if (option == RECON_UNET_OPT_TENSOR_CORES) {
+    u->use_tc = value ? 1 : 0;
+    return RECON_OK;
+  }
+  return RECON_ERR_INVALID_ARG;
+}
+
+recon_status recon_unet_get_layer(recon_unet* u, int layer, float* host, size_t count) {
+  if (!u || !host || layer < 0 || layer > 9 || !u->last_n || !u->acts) return RECON_ERR_INVALID_ARG;
+  if (layer == 9 && u->head_fused) return RECON_ERR_STATE;
+  static const int level[10] = {0, 0, 1, 1, 2, 2, 1, 1, 0, 0};
+  const long long side = u->last_n >> level[layer];
+  const size_t m = (size_t)(side * side * side) * u->spec[layer].cout;
+  if (count != m) return RECON_ERR_INVALID_ARG;
+  const Acts A = act_layout(u, u->last_n);
+  const size_t offs[10] = {A.a1a, A.a1b, A.a2a, A.a2b, A.a3a, A.a3b, A.d2a, A.d2b, A.d1a, A.d1b};
+  UN_CUDA(cudaStreamSynchronize(u->st));
+  if (u->bf16) {
+    std::vector<unsigned short> raw(m);
+    UN_CUDA(cudaMemcpy(raw.data(), static_cast<const bf16*>(u->acts) + offs[layer], m * 2, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < m; ++i) {
+      const unsigned int bits = (unsigned int)raw[i] << 16;
+      std::memcpy(host + i, &bits, 4);
+    }
+  } else {
+    UN_CUDA(cudaMemcpy(host, static_cast<const float*>(u->acts) + offs[layer], m * 4, cudaMemcpyDeviceToHost));
+  }
   return RECON_OK;
 }
 
