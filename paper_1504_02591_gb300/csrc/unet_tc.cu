@@ -21,7 +21,10 @@ namespace {
 
 typedef __nv_bfloat16 bf16;
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;       // warps 0-2 producers, warp 3 MMA issue, warps 4-7 epilogue
+constexpr int kProducers = 96;
+constexpr int kStages = 2;
+constexpr int kCtlBytes = 1536;     // mbarriers, TMEM slot, abort flag, offset tables, bias, head weights
 constexpr int kMaxSmem = 232448;                      // 227 KB per CTA
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s: far beyond any legitimate wait
 constexpr long long kWaitSpins = 1ll << 26;
@@ -64,17 +67,6 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
   return t;
 }
-// Waits for the completion of the mbarrier phase with the given parity; false after the time limit.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = globaltimer();
-  for (long long it = 0; it < kWaitSpins; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (globaltimer() - t0 > kWaitNs) return false;
-  }
-  return false;
-}
-
 __device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(slot), "r"(ncols)
                : "memory");
@@ -161,21 +153,86 @@ __device__ __forceinline__ void block_origin(const KArgs& a, int blk, int& xb, i
   zb = bz * a.zlen;
 }
 
-template <int ORIENT, int MODE>
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+
+// Bounded wait that also gives up as soon as another role of the CTA has given up.  Waiters off
+// the critical path back off with nanosleep so they do not take issue slots from the MMA thread.
+template <bool BACKOFF>
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err) {
+#pragma unroll 1
+  for (int k = 0; k < 32; ++k)
+    if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+#pragma unroll 1
+  for (long long it = 0; it < kWaitSpins; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 31) == 0) {
+      if (*abort_flag) return false;
+      if (globaltimer() - t0 > kWaitNs) break;
+    }
+    if (BACKOFF) __nanosleep(128);
+  }
+  *abort_flag = 1;
+  atomicExch(err, 1);
+  return false;
+}
+
+// Warp roles: warps 0-2 stage halos and weight tiles (two stages), warp 3 issues the MMAs (one
+// thread), warps 4-7 run the epilogue (warp 4 + q reads TMEM lanes 32q..32q+31).  Two accumulator
+// buffers in tensor memory let the epilogue of one block run under the MMAs of the next.
+// Barriers: full[s] (producers -> MMA), empty[s] (MMA commit -> producers), accf[b] (MMA commit ->
+// epilogue), acce[b] (epilogue -> MMA).
+template <int ORIENT, int MODE, int NT>
 __global__ void __launch_bounds__(kThreads, 1) tc_conv_kernel(const KArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const unsigned stage_bytes = a.halo_bytes + a.wts_bytes;
-  unsigned char* ctl = sm + 2 * stage_bytes;
-  const uint32_t bar[2] = {smem_u32(ctl), smem_u32(ctl) + 8u};
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(ctl + 16);
+  unsigned char* ctl = sm + kStages * stage_bytes;
+  const uint32_t ctl_a = smem_u32(ctl);
+  const uint32_t bar_full = ctl_a, bar_empty = ctl_a + 16u, bar_accf = ctl_a + 32u, bar_acce = ctl_a + 48u;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(ctl + 64);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(ctl + 68);
+  uint32_t* tapoff = reinterpret_cast<uint32_t*>(ctl + 128);   // per MMA: halo offset of its tap (16-B units)
+  uint32_t* tileoff = reinterpret_cast<uint32_t*>(ctl + 256);  // per tile: halo offset of its run (16-B units)
+  float* sbias = reinterpret_cast<float*>(ctl + 384);          // up to 128
+  float* shead = reinterpret_cast<float*>(ctl + 896);          // up to 128
+  const int HX = a.bx + 2, HY = a.by + 2;
+  constexpr int ntiles = NT;   // = a.bx * a.by
+  if (tid < a.nmma) {
+    int dx, dy, dz;
+    if (MODE == 0) {
+      dx = tid / 9 - 1;
+      dy = (tid / 3) % 3 - 1;
+      dz = tid % 3 - 1;
+    } else {
+      const int dxy = tid >> 1;
+      dx = dxy / 3 - 1;
+      dy = dxy % 3 - 1;
+      dz = (tid & 1) ? 1 : -1;
+    }
+    tapoff[tid] = (uint32_t)(((1 + dx) * HY + (1 + dy)) * a.hz + (1 + dz));
+  }
+  if (tid < ntiles) tileoff[tid] = (uint32_t)(((tid / a.by) * HY + tid % a.by) * a.hz);
+  if (tid < 128) {
+    sbias[tid] = tid < a.cout ? a.bias[tid] : 0.f;
+    shead[tid] = (a.yout && tid < a.cout) ? __bfloat162float(a.head_w[tid]) : 0.f;
+  }
   if (warp == 0) {
     tmem_alloc(smem_u32(tslot), (uint32_t)a.tmem_cols);
     tmem_relinquish();
   }
   if (tid == 0) {
-    mbar_init(bar[0], 1);
-    mbar_init(bar[1], 1);
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(bar_full + 8u * s, kProducers);
+      mbar_init(bar_empty + 8u * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(bar_accf + 8u * b, 1);
+      mbar_init(bar_acce + 8u * b, 128);
+    }
+    *abort_flag = 0;
     fence_mbar_init();
   }
   tc_fence_before();
@@ -183,129 +240,133 @@ __global__ void __launch_bounds__(kThreads, 1) tc_conv_kernel(const KArgs a) {
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  const int HX = a.bx + 2, HY = a.by + 2;
-  const int ntiles = a.bx * a.by;
   const int n = a.n, m = n >> 1;
   const int G0 = a.c0 >> 3;
   const uint32_t plane = (uint32_t)(HX * HY * a.hz * 16);
   const int n_mine = (int)blockIdx.x < a.nblocks ? (a.nblocks - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const int n_items = n_mine * a.nchunk;
+  const uint32_t acc_cols = (uint32_t)(ntiles * a.N);
 
-  // stage the halo of one (block, chunk) item and its weight tiles into stage s
-  auto load = [&](int item, int s) {
-    const int blk = (int)blockIdx.x + (item / a.nchunk) * (int)gridDim.x;
-    const int c = item % a.nchunk;
-    int xb, yb, zb;
-    block_origin(a, blk, xb, yb, zb);
-    const uint32_t hdst = smem_u32(sm + (size_t)s * stage_bytes);
-    const int total = a.gpc * HX * HY * a.hz;
-    for (int idx = tid; idx < total; idx += kThreads) {
-      // layout [group][hx][hy][hz], 16 bytes (8 channels) per entry: the entry index is idx
-      const int hzi = idx % a.hz;
-      int t = idx / a.hz;
-      const int hyi = t % HY;
-      t /= HY;
-      const int hxi = t % HX, gl = t / HX;
-      const int g = c * a.gpc + gl;
-      const int x = wrapc(xb - 1 + hxi, n), y = wrapc(yb - 1 + hyi, n), z = wrapc(zb - 1 + hzi, n);
-      const bf16* src;
-      if (g < G0) {
-        if (a.up0)
-          src = a.src0 + ((((long long)(x >> 1) * m + (y >> 1)) * m + (z >> 1)) * a.c0 + g * 8);
-        else
-          src = a.src0 + ((((long long)x * n + y) * n + z) * a.c0 + g * 8);
-      } else {
-        src = a.src1 + ((((long long)x * n + y) * n + z) * a.c1 + (g - G0) * 8);
-      }
-      cp_async16(hdst + (uint32_t)idx * 16u, src);
-    }
-    const uint32_t wdst = hdst + a.halo_bytes;
-    const bf16* wsrc = a.wpack + (size_t)c * a.nmma * a.rows * 16;
-    const int nw = a.nmma * a.rows * 2;
-    for (int e = tid; e < nw; e += kThreads) cp_async16(wdst + (uint32_t)e * 16u, wsrc + (size_t)e * 8);
-    cp_async_commit();
-  };
-
-  int ok = 1;
-  int last_commit[2] = {-1, -1};
-  if (n_items > 0) load(0, 0);
-  for (int i = 0; i < n_items; ++i) {
-    const int s = i & 1;
-    if (i + 1 < n_items) {
-      // stage s^1 was last read by the MMAs of item i-1
-      int bad = 0;
-      if (i >= 1) bad = !mbar_wait(bar[s ^ 1], (uint32_t)(((i - 1) >> 1) & 1));
-      if (__syncthreads_or(bad)) {
-        ok = 0;
-        break;
-      }
-      load(i + 1, s ^ 1);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    fence_proxy_async();
-    __syncthreads();
-    const int blk = (int)blockIdx.x + (i / a.nchunk) * (int)gridDim.x;
-    const int c = i % a.nchunk;
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t hb = smem_u32(sm + (size_t)s * stage_bytes), wb = hb + a.halo_bytes;
-      const uint32_t lbo_act = MODE == 0 ? plane : 16u;
-      for (int mm = 0; mm < a.nmma; ++mm) {
-        int dx, dy, dz;
-        if (MODE == 0) {
-          dx = mm / 9 - 1;
-          dy = (mm / 3) % 3 - 1;
-          dz = mm % 3 - 1;
-        } else {
-          const int dxy = mm >> 1;
-          dx = dxy / 3 - 1;
-          dy = dxy % 3 - 1;
-          dz = (mm & 1) ? 1 : -1;
-        }
-        const uint32_t tap = (uint32_t)((((1 + dx) * HY + (1 + dy)) * a.hz + (1 + dz)) * 16);
-        const uint64_t wdesc = smem_desc(wb + (uint32_t)(mm * a.rows * 32), 128u, 256u);
-        const uint32_t accumulate = (c > 0 || mm > 0) ? 1u : 0u;
-        for (int j = 0; j < ntiles; ++j) {
-          const int tx = j / a.by, ty = j % a.by;
-          const uint32_t toff = (uint32_t)((tx * HY + ty) * a.hz * 16);
-          const uint64_t adesc = smem_desc(hb + tap + toff, lbo_act, 128u);
-          if (ORIENT == 0)
-            mma_bf16(tmem + (uint32_t)(j * a.N), adesc, wdesc, a.idesc, accumulate);
-          else
-            mma_bf16(tmem + (uint32_t)(j * a.N), wdesc, adesc, a.idesc, accumulate);
-        }
-      }
-      mma_commit(bar[s]);
-    }
-    last_commit[s] = i;
-    if (c == a.nchunk - 1) {
-      const int bad = !mbar_wait(bar[s], (uint32_t)((i >> 1) & 1));
-      if (__syncthreads_or(bad)) {
-        ok = 0;
-        break;
-      }
-      tc_fence_after();
+  if (warp < kProducers / 32) {
+    // ---- producers: halo rows (one warp per (group, hx, hy) row, lanes along z) and weight tiles
+    for (int i = 0; i < n_items; ++i) {
+      const int s = i % kStages, u = i / kStages;
+      if (u >= 1 && !wait_bar<true>(bar_empty + 8u * s, (uint32_t)((u - 1) & 1), abort_flag, a.err)) break;
+      const int blk = (int)blockIdx.x + (i / a.nchunk) * (int)gridDim.x;
+      const int c = i % a.nchunk;
       int xb, yb, zb;
       block_origin(a, blk, xb, yb, zb);
-      const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+      const uint32_t hdst = smem_u32(sm + (size_t)s * stage_bytes);
+      const int nrows = a.gpc * HX * HY;
+      for (int row = warp; row < nrows; row += kProducers / 32) {
+        const int hyi = row % HY;
+        const int t = row / HY;
+        const int hxi = t % HX, gl = t / HX;
+        const int g = c * a.gpc + gl;
+        const int x = wrapc(xb - 1 + hxi, n), y = wrapc(yb - 1 + hyi, n);
+        const bf16* base;
+        int zstride, zshift;
+        if (g < G0) {
+          zstride = a.c0;
+          if (a.up0) {
+            base = a.src0 + ((long long)(x >> 1) * m + (y >> 1)) * m * a.c0 + g * 8;
+            zshift = 1;
+          } else {
+            base = a.src0 + ((long long)x * n + y) * n * a.c0 + g * 8;
+            zshift = 0;
+          }
+        } else {
+          zstride = a.c1;
+          zshift = 0;
+          base = a.src1 + ((long long)x * n + y) * n * a.c1 + (g - G0) * 8;
+        }
+        const uint32_t drow = hdst + (uint32_t)(row * a.hz) * 16u;
+        for (int hzi = lane; hzi < a.hz; hzi += 32) {
+          const int z = wrapc(zb - 1 + hzi, n);
+          cp_async16(drow + (uint32_t)hzi * 16u, base + (long long)(z >> zshift) * zstride);
+        }
+      }
+      const uint32_t wdst = hdst + a.halo_bytes;
+      const bf16* wsrc = a.wpack + (size_t)c * a.nmma * a.rows * 16;
+      const int nw = a.nmma * a.rows * 2;
+      for (int e = tid; e < nw; e += kProducers) cp_async16(wdst + (uint32_t)e * 16u, wsrc + (size_t)e * 8);
+      cp_async_commit();
+      cp_async_wait<0>();
+      fence_proxy_async();      // make the copies visible to the tensor cores' (async-proxy) reads
+      mbar_arrive(bar_full + 8u * s);
+    }
+    cp_async_wait<0>();
+  } else if (warp == kProducers / 32) {
+    // ---- one thread issues every MMA of the CTA
+    if (lane == 0) {
+      uint32_t toff[NT];
+#pragma unroll
+      for (int j = 0; j < NT; ++j) toff[j] = tileoff[j];
+      int last = -1;
+      for (int i = 0; i < n_items; ++i) {
+        const int s = i % kStages, u = i / kStages;
+        const int k = i / a.nchunk, c = i % a.nchunk, b = k & 1, ub = k >> 1;
+        if (!wait_bar<false>(bar_full + 8u * s, (uint32_t)(u & 1), abort_flag, a.err)) break;
+        if (c == 0 && ub >= 1 && !wait_bar<false>(bar_acce + 8u * b, (uint32_t)((ub - 1) & 1), abort_flag, a.err))
+          break;
+        tc_fence_after();
+        const uint32_t hb = smem_u32(sm + (size_t)s * stage_bytes), wb = hb + a.halo_bytes;
+        // the start-address field is the low 14 bits of the descriptor (address / 16, below 256 KB),
+        // so operand offsets are added to a base descriptor directly
+        const uint64_t a0 = smem_desc(hb, MODE == 0 ? plane : 16u, 128u);
+        const uint64_t w0 = smem_desc(wb, 128u, 256u);
+        const uint32_t wstep = (uint32_t)(a.rows * 32) >> 4;
+        const uint32_t dbase = tmem + (uint32_t)b * acc_cols;
+        for (int mm = 0; mm < a.nmma; ++mm) {
+          const uint64_t wdesc = w0 + (uint64_t)(mm * wstep);
+          const uint64_t at = a0 + tapoff[mm];
+          const uint32_t accumulate = (c > 0 || mm > 0) ? 1u : 0u;
+#pragma unroll
+          for (int j = 0; j < NT; ++j) {
+            const uint64_t adesc = at + toff[j];
+            if (ORIENT == 0)
+              mma_bf16(dbase + (uint32_t)(j * a.N), adesc, wdesc, a.idesc, accumulate);
+            else
+              mma_bf16(dbase + (uint32_t)(j * a.N), wdesc, adesc, a.idesc, accumulate);
+          }
+        }
+        mma_commit(bar_empty + 8u * s);
+        if (c == a.nchunk - 1) mma_commit(bar_accf + 8u * b);
+        last = i;
+      }
+      // every MMA issued must be complete before the tensor memory is released
+      if (last >= 0)
+        wait_bar<false>(bar_empty + 8u * (last % kStages), (uint32_t)((last / kStages) & 1), abort_flag, a.err);
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue: TMEM -> bias, ReLU, bf16 -> global (or the fused head)
+    const int q = warp & 3;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
+    for (int k = 0; k < n_mine; ++k) {
+      const int b = k & 1, ub = k >> 1;
+      if (!wait_bar<true>(bar_accf + 8u * b, (uint32_t)(ub & 1), abort_flag, a.err)) break;
+      tc_fence_after();
+      const int blk = (int)blockIdx.x + k * (int)gridDim.x;
+      int xb, yb, zb;
+      block_origin(a, blk, xb, yb, zb);
+      const uint32_t cbase = lane_base + (uint32_t)b * acc_cols;
       if (ORIENT == 0) {
-        const int r = 32 * warp + lane;   // voxel along the z run
-        for (int j = 0; j < ntiles; ++j) {
+        const int r = 32 * q + lane;   // voxel along the z run
+#pragma unroll 1
+        for (int j = 0; j < NT; ++j) {
           const int x = xb + j / a.by, y = yb + j % a.by, z = zb + r;
           const long long v = ((long long)x * n + y) * n + z;
+          const float rv = a.yout ? a.res[v * a.res_stride] : 0.f;
           float hsum = 0.f;
           for (int cc = 0; cc < a.N; cc += 16) {
             float acc[16];
-            tmem_ld16(lane_base + (uint32_t)(j * a.N + cc), acc);
+            tmem_ld16(cbase + (uint32_t)(j * a.N + cc), acc);
             __align__(16) bf16 o[16];
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
-              const int co = cc + e;
-              const float val = co < a.cout ? fmaxf(acc[e] + a.bias[co], 0.f) : 0.f;
-              o[e] = __float2bfloat16_rn(val);
-              if (a.yout && co < a.cout) hsum = fmaf(__bfloat162float(o[e]), __bfloat162float(a.head_w[co]), hsum);
+              o[e] = __float2bfloat16_rn(fmaxf(acc[e] + sbias[cc + e], 0.f));
+              hsum = fmaf(__bfloat162float(o[e]), shead[cc + e], hsum);
             }
             if (!a.yout) {
 #pragma unroll
@@ -314,36 +375,29 @@ __global__ void __launch_bounds__(kThreads, 1) tc_conv_kernel(const KArgs a) {
                   *reinterpret_cast<uint4*>(a.out + v * a.cout + cc + 8 * h) = *reinterpret_cast<const uint4*>(o + 8 * h);
             }
           }
-          if (a.yout) a.yout[v] = a.head_b[0] + hsum + a.res[v * a.res_stride];
+          if (a.yout) a.yout[v] = a.head_b[0] + hsum + rv;
         }
-      } else if (32 * warp < a.cout) {
-        const int co = 32 * warp + lane;   // output channel = TMEM lane
+      } else if (32 * q < a.cout) {
+        const int co = 32 * q + lane;   // output channel = TMEM lane
         const bool valid = co < a.cout;
-        const float b = valid ? a.bias[co] : 0.f;
+        const float bco = sbias[co < 128 ? co : 0];
         for (int j = 0; j < ntiles; ++j) {
           const int x = xb + j / a.by, y = yb + j % a.by;
           const long long v0 = ((long long)x * n + y) * n + zb;
           for (int cc = 0; cc < a.N; cc += 16) {
             float acc[16];
-            tmem_ld16(lane_base + (uint32_t)(j * a.N + cc), acc);
+            tmem_ld16(cbase + (uint32_t)(j * a.N + cc), acc);
             if (valid) {
 #pragma unroll
               for (int e = 0; e < 16; ++e)
-                a.out[(v0 + cc + e) * a.cout + co] = __float2bfloat16_rn(fmaxf(acc[e] + b, 0.f));
+                a.out[(v0 + cc + e) * a.cout + co] = __float2bfloat16_rn(fmaxf(acc[e] + bco, 0.f));
             }
           }
         }
       }
       tc_fence_before();
-      __syncthreads();
+      mbar_arrive(bar_acce + 8u * b);
     }
-  }
-  cp_async_wait<0>();
-  if (!ok) {
-    if (tid == 0) atomicExch(a.err, 1);
-    // let every MMA already issued finish (bounded) before the tensor memory is released
-    for (int s = 0; s < 2; ++s)
-      if (last_commit[s] >= 0) mbar_wait(bar[s], (uint32_t)((last_commit[s] >> 1) & 1));
   }
   tc_fence_before();
   __syncthreads();
@@ -383,9 +437,9 @@ __global__ void pack_kernel(const bf16* __restrict__ w, int cin, int cout, int m
   }
 }
 
-template <int O, int M>
+template <int O, int M, int NT>
 cudaError_t launch(const ConvPlan& p, const KArgs& a, cudaStream_t st) {
-  const void* k = (const void*)tc_conv_kernel<O, M>;
+  const void* k = (const void*)tc_conv_kernel<O, M, NT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
   if (e != cudaSuccess) return e;
   int occ = 0, dev = 0, sms = 0;
@@ -399,7 +453,7 @@ cudaError_t launch(const ConvPlan& p, const KArgs& a, cudaStream_t st) {
   if (occ > tm) occ = tm;
   if (occ < 1) occ = 1;
   const int grid = p.nblocks < sms * occ ? p.nblocks : sms * occ;
-  tc_conv_kernel<O, M><<<grid, kThreads, p.smem, st>>>(a);
+  tc_conv_kernel<O, M, NT><<<grid, kThreads, p.smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -446,10 +500,10 @@ bool plan_conv(int n, int c0, int up0, int c1, int cin, int cout, ConvPlan* out)
   for (const auto& c : cand) {
     const int bx = c[0], by = c[1];
     if (n % bx || n % by) continue;
-    const int cols = bx * by * q.N;
+    const int cols = 2 * bx * by * q.N;    // two accumulator buffers
     if (cols > 512) continue;
     const size_t halo = (size_t)q.gpc * (bx + 2) * (by + 2) * q.hz * 16;
-    const size_t smem = 2 * (halo + q.wts_bytes) + 64;
+    const size_t smem = kStages * (halo + q.wts_bytes) + kCtlBytes;
     if (smem > (size_t)kMaxSmem) continue;
     q.bx = bx;
     q.by = by;
@@ -514,8 +568,21 @@ cudaError_t conv_forward(const ConvPlan& p, const ConvIO& io, cudaStream_t st) {
   if (!a.err || !a.wpack || !a.bias || !a.src0 || (p.c1 && !a.src1)) return cudaErrorInvalidValue;
   if (io.yout && (p.orient != 0 || !io.head_w || !io.head_b || !io.res)) return cudaErrorInvalidValue;
   if (!io.yout && !io.out) return cudaErrorInvalidValue;
-  if (p.orient == 0) return p.mode == 0 ? launch<0, 0>(p, a, st) : launch<0, 1>(p, a, st);
-  return p.mode == 0 ? launch<1, 0>(p, a, st) : launch<1, 1>(p, a, st);
+  const int nt = p.bx * p.by;
+#define TC_NT(O_, M_)                                                  \
+  switch (nt) {                                                       \
+    case 16: return launch<O_, M_, 16>(p, a, st);                     \
+    case 8: return launch<O_, M_, 8>(p, a, st);                       \
+    case 4: return launch<O_, M_, 4>(p, a, st);                       \
+    case 2: return launch<O_, M_, 2>(p, a, st);                       \
+    case 1: return launch<O_, M_, 1>(p, a, st);                       \
+    default: return cudaErrorInvalidValue;                            \
+  }
+  if (p.orient == 0) {
+    if (p.mode == 0) TC_NT(0, 0) else TC_NT(0, 1)
+  }
+  if (p.mode == 0) TC_NT(1, 0) else TC_NT(1, 1)
+#undef TC_NT
 }
 
 }  // namespace tc
