@@ -135,21 +135,32 @@ recon_status recon_smooth(recon_handle* h);
 recon_status recon_iterate(recon_handle* h, int start, double tol, int max_iter, int* n_iter,
                            double* rel_change);
 
-/* The iteration of recon_iterate started from a supplied radial displacement u0 (device, N^3
- * float32 [ix][iy][iz]): P_0 = u0 r instead of an analytic start (the learned warm start feeds the
- * network's output here; u0 = the converged Psi . r reproduces the fixed point).  Same stopping
- * rule, outputs and trace as recon_iterate.  u0 is borrowed for the call. */
-recon_status recon_iterate_from(recon_handle* h, const float* u0, double tol, int max_iter, int* n_iter,
+/* Network inputs for the learned start (no counterpart in the paper), after recon_smooth.
+ * feat (device, M^3 x 5 float32, channels-last, M = N >> level, level 0..2) holds per coarse node
+ * the means over its 2^level-node block of (delta, r_x, r_y, r_z, u_s), u_s = (1 - c)(Psi_s . r)
+ * the radial displacement of the analytic start `start` (RECON_START_*; Psi_s = Z[delta/b],
+ * c as in recon_iterate).  Computes delta(k), S_-1 and u_s on the mesh and keeps them for
+ * recon_iterate_from at the same level.  Consumes the real delta copy (RECON_FIELD_DELTA is no
+ * longer available).  UNSUPPORTED if N is not a multiple of 2^level. */
+recon_status recon_start_features(recon_handle* h, int start, int level, float* feat);
+
+/* The iteration of recon_iterate started from a supplied radial displacement (the learned warm
+ * start feeds the network's output here), same stopping rule, outputs and trace:
+ *   level 0: u0 (device, N^3 float32 [ix][iy][iz]) is the displacement on the mesh: P_0 = u0 r;
+ *            u0 = the converged Psi . r reproduces the fixed point.
+ *   level 1, 2: u0 (device, M^3, M = N >> level) is a prediction of the block means of the
+ *            converged Psi . r; P_0 = (u_s + U[u0 - mean(u_s)]) r, where u_s and its block means
+ *            come from the last recon_start_features at this level (STATE otherwise) and U is
+ *            periodic trilinear interpolation with the coarse node J at mesh index
+ *            (J + 1/2) 2^level - 1/2.  u0 = the features' u_s channel gives exactly the analytic
+ *            start.  Consumes that preparation.
+ * u0 is borrowed for the call. */
+recon_status recon_iterate_from(recon_handle* h, const float* u0, int level, double tol, int max_iter, int* n_iter,
                                 double* rel_change);
 
-/* Network inputs for the learned start, after recon_smooth: feat (device, N^3 x 5 float32,
- * channels-last) = (delta, r_x, r_y, r_z, u_0) per node, u_0 = (1 - c)(Z[delta/b] . r) the radial
- * displacement of the analytic start `start` (RECON_START_*).  Consumes the real delta copy
- * (RECON_FIELD_DELTA is no longer available); the handle stays ready for recon_iterate(_from). */
-recon_status recon_start_features(recon_handle* h, int start, float* feat);
-
-/* The radial displacement u = Psi . r of the final Psi (device, N^3 float32), after an iterate. */
-recon_status recon_get_radial(recon_handle* h, float* u);
+/* Block means (level 0..2, as in recon_start_features) of the radial displacement Psi . r of the
+ * final Psi (device, M^3 float32), after an iterate: the training target of the learned start. */
+recon_status recon_get_radial(recon_handle* h, int level, float* u);
 
 /* The rel values of the last recon_iterate: up to cap entries into rel (host), count into *n. */
 recon_status recon_get_trace(recon_handle* h, double* rel, int cap, int* n);

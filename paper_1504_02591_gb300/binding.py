@@ -100,9 +100,9 @@ def load(path: str = LIB_PATH):
     lib.recon_reconfigure.argtypes = [VP, P(ReconParams)]
     lib.recon_batch_run.argtypes = [P(ReconBatchItem), I, VP, I]
     lib.recon_batch_plan.argtypes = [I, P(I), P(I), P(I)]
-    lib.recon_iterate_from.argtypes = [VP, VP, D, I, P(I), P(D)]
-    lib.recon_start_features.argtypes = [VP, I, VP]
-    lib.recon_get_radial.argtypes = [VP, VP]
+    lib.recon_iterate_from.argtypes = [VP, VP, I, D, I, P(I), P(D)]
+    lib.recon_start_features.argtypes = [VP, I, I, VP]
+    lib.recon_get_radial.argtypes = [VP, I, VP]
     lib.recon_unet_param_count.argtypes = [I, P(C.c_size_t)]
     lib.recon_unet_create.argtypes = [I, I, VP, P(VP)]
     lib.recon_unet_set_params.argtypes = [VP, VP, C.c_size_t]
@@ -264,31 +264,32 @@ class Recon:
         self._check(st, "recon_iterate", allow=(ERR_NOT_CONVERGED,))
         return n.value, rel.value, st
 
-    def iterate_from(self, u0, tol=0.0, max_iter=6):
-        """Iterate from a supplied radial displacement u0 (CUDA tensor, N^3); (n_iter, rel, status)."""
+    def iterate_from(self, u0, tol=0.0, max_iter=6, level=0):
+        """Iterate from a supplied radial displacement (CUDA tensor): level 0 on the mesh, level 1/2
+        a prediction of the block means after start_features(level); (n_iter, rel, status)."""
         import torch
         u0 = u0.to(device="cuda", dtype=torch.float32).contiguous()
         n = C.c_int(0)
         rel = C.c_double(0)
-        st = self.lib.recon_iterate_from(self.h, C.c_void_p(u0.data_ptr()), float(tol), int(max_iter), C.byref(n),
-                                         C.byref(rel))
+        st = self.lib.recon_iterate_from(self.h, C.c_void_p(u0.data_ptr()), int(level), float(tol), int(max_iter),
+                                         C.byref(n), C.byref(rel))
         self._check(st, "recon_iterate_from", allow=(ERR_NOT_CONVERGED,))
         return n.value, rel.value, st
 
-    def start_features(self, start=START_FFTA):
-        """(N, N, N, 5) CUDA tensor of network inputs (delta, r, u_0), after smooth()."""
+    def start_features(self, start=START_FFTA, level=0):
+        """(M, M, M, 5) CUDA tensor of network inputs (delta, r, u_s) block means, M = N >> level."""
         import torch
-        n = self.n
-        feat = torch.empty((n, n, n, 5), dtype=torch.float32, device="cuda")
-        self._check(self.lib.recon_start_features(self.h, int(start), C.c_void_p(feat.data_ptr())),
+        m = self.n >> level
+        feat = torch.empty((m, m, m, 5), dtype=torch.float32, device="cuda")
+        self._check(self.lib.recon_start_features(self.h, int(start), int(level), C.c_void_p(feat.data_ptr())),
                     "recon_start_features")
         return feat
 
-    def get_radial(self):
+    def get_radial(self, level=0):
         import torch
-        n = self.n
-        u = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
-        self._check(self.lib.recon_get_radial(self.h, C.c_void_p(u.data_ptr())), "recon_get_radial")
+        m = self.n >> level
+        u = torch.empty((m, m, m), dtype=torch.float32, device="cuda")
+        self._check(self.lib.recon_get_radial(self.h, int(level), C.c_void_p(u.data_ptr())), "recon_get_radial")
         return u
 
     def trace(self):

@@ -101,7 +101,7 @@ struct ZWarpSmem {  // float2 slots of one warp's private region
   static constexpr int NF = (MODE == Z_DELTA) ? 1 : 3;
   static constexpr int kLines = (NF * RowLayout<N / 2>::kStride + 1) & ~1;   // even: keeps raw 16-B aligned
   static constexpr int kQ = 4;                                  // Nyquist values (padded)
-  static constexpr int kRaw = (MODE == Z_DELTA) ? N : 0;        // 2 N floats of raw rows
+  static constexpr int kRaw = (MODE == Z_DELTA) ? N : (MODE == Z_WARM ? N / 4 : 0);   // raw rows / coarse row
   static constexpr int v = kLines + kQ + kRaw + ((kLines + kQ + kRaw) & 1);
 };
 
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kZThreads, 4) zpass_kernel(const ZArgs a) {
   __syncthreads();
 
   float acc0 = 0.f, acc1 = 0.f;
-  constexpr bool kInverse = (MODE == Z_INV || MODE == Z_PROJ || MODE == Z_FINAL);
+  constexpr bool kInverse = (MODE == Z_INV || MODE == Z_PROJ || MODE == Z_FINAL || MODE == Z_RADIAL);
   // device-driven iteration: once the loop flag says converged, this pass writes the real Psi
   const bool fin = (MODE == Z_PROJ) && a.loop_flag && *a.loop_flag == 1;
   float inv_alpha = 0.f, thr = 0.f;
@@ -155,14 +155,54 @@ __global__ void __launch_bounds__(kZThreads, 4) zpass_kernel(const ZArgs a) {
       __syncwarp();
 #pragma unroll
       for (int q = 0; q < NF; ++q) Plan<L>::template run<1, 32, true, Lay, true>(s + q * Lay::kStride, tab);
-    } else if (MODE == Z_USTART) {
-      // a supplied radial displacement u: P_j = u r_j on the row, then the forward r2c of P
+    } else if (MODE == Z_USTART || MODE == Z_WARM) {
+      // a radial displacement u: P_j = u r_j on the row, then the forward r2c of P.  Z_WARM adds to
+      // u the trilinear (periodic) upsampling of a coarse correction: the coarse node J of level l
+      // sits at fine index (J + 1/2) 2^l - 1/2 along each axis.
       const Geometry& g = a.g;
       const int ix = (int)(row / N), iy = (int)(row % N);
       const float dx = g.los_mode == 1 ? 0.f : g.off[ix], dy = g.los_mode == 1 ? 0.f : g.off[N + iy];
       const float* ur = a.u_in + row * N;
+      float* crow = raw;   // Z_WARM: the correction bilinearly interpolated to this (x, y) row
+      int nc = 0, fl = 0;
+      float inv_f = 0.f;
+      if (MODE == Z_WARM) {
+        fl = a.clevel;
+        nc = N >> fl;
+        inv_f = 1.f / (float)(1 << fl);
+        const float tx = ((float)ix + 0.5f) * inv_f - 0.5f, ty = ((float)iy + 0.5f) * inv_f - 0.5f;
+        const float fx = floorf(tx), fy = floorf(ty);
+        const float wx = tx - fx, wy = ty - fy;
+        int x0 = (int)fx, y0 = (int)fy;
+        x0 = x0 < 0 ? x0 + nc : x0;
+        y0 = y0 < 0 ? y0 + nc : y0;
+        const int x1 = x0 + 1 == nc ? 0 : x0 + 1, y1 = y0 + 1 == nc ? 0 : y0 + 1;
+        const size_t r00 = ((size_t)x0 * nc + y0) * nc, r01 = ((size_t)x0 * nc + y1) * nc;
+        const size_t r10 = ((size_t)x1 * nc + y0) * nc, r11 = ((size_t)x1 * nc + y1) * nc;
+        for (int j = lane; j < nc; j += 32) {
+          const float c00 = a.corr[r00 + j] - a.ucoarse[r00 + j], c01 = a.corr[r01 + j] - a.ucoarse[r01 + j];
+          const float c10 = a.corr[r10 + j] - a.ucoarse[r10 + j], c11 = a.corr[r11 + j] - a.ucoarse[r11 + j];
+          crow[j] = (1.f - wx) * ((1.f - wy) * c00 + wy * c01) + wx * ((1.f - wy) * c10 + wy * c11);
+        }
+        __syncwarp();
+      }
       for (int m = lane; m < L; m += 32) {
-        const float2 uu = reinterpret_cast<const float2*>(ur)[m];
+        float2 uu = reinterpret_cast<const float2*>(ur)[m];
+        if (MODE == Z_WARM) {
+          float add[2];
+#pragma unroll
+          for (int h2 = 0; h2 < 2; ++h2) {
+            const float tz = ((float)(2 * m + h2) + 0.5f) * inv_f - 0.5f;
+            const float fz = floorf(tz);
+            const float wz = tz - fz;
+            int z0 = (int)fz;
+            z0 = z0 < 0 ? z0 + nc : z0;
+            const int z1 = z0 + 1 == nc ? 0 : z0 + 1;
+            add[h2] = (1.f - wz) * crow[z0] + wz * crow[z1];
+          }
+          uu.x += add[0];
+          uu.y += add[1];
+        }
         float r[2][3];
 #pragma unroll
         for (int h2 = 0; h2 < 2; ++h2) {
@@ -232,6 +272,33 @@ __global__ void __launch_bounds__(kZThreads, 4) zpass_kernel(const ZArgs a) {
       __syncwarp();
     }
 
+    if (MODE == Z_RADIAL) {
+      // s holds Psi_j(x, y, z): the start's radial displacement coef (Psi.r), as a real row
+      const Geometry& g = a.g;
+      const int ix = (int)(row / N), iy = (int)(row % N);
+      const float dx = g.los_mode == 1 ? 0.f : g.off[ix], dy = g.los_mode == 1 ? 0.f : g.off[N + iy];
+      for (int m = lane; m < L; m += 32) {
+        const float2 p0 = s[Lay::phys(m, 0)], p1 = s[Lay::phys(m, 1)], p2 = s[Lay::phys(m, 2)];
+        float rx0, ry0, rz0, rx1, ry1, rz1;
+        if (g.los_mode == 1) {
+          rx0 = rx1 = g.los.x; ry0 = ry1 = g.los.y; rz0 = rz1 = g.los.z;
+        } else {
+          const float dz0 = g.off[2 * N + 2 * m], dz1 = g.off[2 * N + 2 * m + 1];
+          const float q0 = fmaf(dx, dx, fmaf(dy, dy, dz0 * dz0));
+          const float q1 = fmaf(dx, dx, fmaf(dy, dy, dz1 * dz1));
+          const float i0 = q0 > 0.f ? rsqrtf(q0) : 0.f;
+          const float i1 = q1 > 0.f ? rsqrtf(q1) : 0.f;
+          rx0 = dx * i0; ry0 = dy * i0; rz0 = dz0 * i0;
+          rx1 = dx * i1; ry1 = dy * i1; rz1 = dz1 * i1;
+        }
+        const float u0 = a.coef * fmaf(p0.x, rx0, fmaf(p1.x, ry0, p2.x * rz0));
+        const float u1 = a.coef * fmaf(p0.y, rx1, fmaf(p1.y, ry1, p2.y * rz1));
+        reinterpret_cast<float2*>(a.u_out + row * N)[m] = make_float2(u0, u1);
+      }
+      __syncwarp();
+      continue;
+    }
+
     if (MODE == Z_PROJ && !fin) {
       // s holds Psi_j(x, y, z), z = 2m (.x) and 2m + 1 (.y): P = coef (Psi.r) r (Eq. Nusser)
       const Geometry& g = a.g;
@@ -299,7 +366,9 @@ __global__ void __launch_bounds__(kZThreads, 4) zpass_kernel(const ZArgs a) {
 template <int N, int NC>
 constexpr size_t zpass_smem(int mode) {
   return sizeof(float2) * ((size_t)N / 2 + 2 + ((Plan<N / 2>::kTab + 1) & ~1) + N / 2 +
-                           (size_t)kZWarps * (mode == Z_DELTA ? ZWarpSmem<N, Z_DELTA>::v : ZWarpSmem<N, Z_PROJ>::v));
+                           (size_t)kZWarps * (mode == Z_DELTA  ? ZWarpSmem<N, Z_DELTA>::v
+                                              : mode == Z_WARM ? ZWarpSmem<N, Z_WARM>::v
+                                                               : ZWarpSmem<N, Z_PROJ>::v));
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -592,6 +661,7 @@ struct MeshImpl {
 #define RG_Z(M_, NC_) \
   if (mode == M_ && nc == NC_) return zlaunch<M_, NC_>(a, st, grid_out);
     RG_Z(Z_FWD, 1) RG_Z(Z_INV, 1) RG_Z(Z_DELTA, 2) RG_Z(Z_PROJ, 3) RG_Z(Z_FINAL, 3) RG_Z(Z_USTART, 3)
+    RG_Z(Z_RADIAL, 3) RG_Z(Z_WARM, 3)
 #undef RG_Z
     return cudaErrorInvalidValue;
   }

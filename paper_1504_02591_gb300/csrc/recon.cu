@@ -62,7 +62,7 @@ enum State { ST_CREATED = 0, ST_DEPOSITED = 1, ST_SMOOTHED = 2, ST_ITERATED = 3 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t field_M, field_Q, field, tw, tabs, tabz, off, taps, red, partials, stage, bricks, total;
+  size_t field_M, field_Q, field, tw, tabs, tabz, off, taps, red, partials, stage, bricks, coarse, total;
 };
 
 Layout layout_for(int n) {
@@ -85,7 +85,9 @@ Layout layout_for(int n) {
   l.partials = align256(nb * 4 * sizeof(double));
   l.stage = align256((size_t)kStageParticles * kStageBytesPer);
   l.bricks = align256(brick_scratch_bytes(n));
-  l.total = 5 * l.field + l.tw + l.tabs + l.tabz + l.off + l.taps + l.red + l.partials + l.stage + l.bricks;
+  l.coarse = align256((size_t)(n / 2) * (n / 2) * (n / 2) * sizeof(float));   // warm start, level >= 1
+  l.total = 5 * l.field + l.tw + l.tabs + l.tabz + l.off + l.taps + l.red + l.partials + l.stage + l.bricks +
+            l.coarse;
   return l;
 }
 
@@ -141,6 +143,8 @@ struct recon_handle {
   int narrow_lines = 0;
   int d_is_k = 0;
   int delta_real_valid = 0;
+  float* ucoarse = nullptr;   // block means of the start's radial displacement (warm start, level >= 1)
+  int warm_level = -1;        // level of the pending warm start prepared by recon_start_features
   std::vector<double> trace;
   std::string err;
   Geometry geo{};
@@ -260,6 +264,8 @@ double zbytes(const recon_handle* h, int mode, int nc, const ZArgs& a) {
     return nin * rfield(h) + cfield(h) + (a.delta_real ? rfield(h) : 0.0);
   }
   if (mode == Z_FINAL) return nc * (cfield(h) + rfield(h));
+  if (mode == Z_RADIAL) return nc * cfield(h) + rfield(h);
+  if (mode == Z_USTART || mode == Z_WARM) return rfield(h) + nc * cfield(h);
   return 2.0 * nc * cfield(h);
 }
 
@@ -429,6 +435,7 @@ recon_status configure(recon_handle* h, const recon_params* p) {
   }
   g.off = h->off;
   h->state = ST_CREATED;
+  h->warm_level = -1;
   h->d_is_k = 0;
   h->delta_real_valid = 0;
   return RECON_OK;
@@ -513,6 +520,8 @@ recon_status recon_create(const recon_params* p, void* stream, void* workspace, 
   h->stage = b;
   b += h->lay.stage;
   h->bb = brick_buffers(b, h->n, h->L);
+  b += h->lay.bricks;
+  h->ucoarse = (float*)b;
 
   // twiddles exp(-2 pi i m / N), computed in float64, and the stage tables built from them
   const int n = h->n;
@@ -613,6 +622,7 @@ recon_status recon_deposit(recon_handle* h, const recon_catalog* gal, const reco
   }
   h->state = ST_DEPOSITED;
   h->delta_real_valid = 0;
+  h->warm_level = -1;
   h->d_is_k = 0;
   return RECON_OK;
 }
@@ -702,7 +712,14 @@ recon_status iterate_body(recon_handle* h, cudaGraphConditionalHandle cond) {
   return RECON_OK;
 }
 
-recon_status iterate_start_from(recon_handle* h, const float* u0);
+// How the iteration starts: the analytic start (coefficient 1 - c), a supplied radial displacement
+// on the mesh, or the warm start prepared by recon_start_features plus a coarse correction.
+struct StartSpec {
+  float coef0 = 1.f;
+  const float* u0 = nullptr;
+  int level = 0;
+};
+recon_status run_start(recon_handle* h, const StartSpec& sp);
 
 struct GraphGuard {
   cudaGraph_t gs = nullptr, g = nullptr;
@@ -716,7 +733,7 @@ struct GraphGuard {
 
 // The whole iteration as one CUDA graph: the start sequence, then a conditional WHILE node whose
 // body is one update.  One launch, one host synchronisation at the end.
-recon_status iterate_graph(recon_handle* h, float coef0, const float* u0, double tol, int max_iter, int* it_out,
+recon_status iterate_graph(recon_handle* h, const StartSpec& sp, double tol, int max_iter, int* it_out,
                            double* rel_out, int* flag_out) {
   if (!h->cap_stream) RG_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   const cudaStream_t user = h->st;
@@ -732,7 +749,7 @@ recon_status iterate_graph(recon_handle* h, float coef0, const float* u0, double
     if ((e = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
     rs = [&]() -> recon_status {
       RG_CUDA(launch_loop_init(h->loop, tol, max_iter, h->st));
-      return u0 ? iterate_start_from(h, u0) : iterate_start(h, coef0);
+      return run_start(h, sp);
     }();
     e = cudaStreamEndCapture(h->st, &gg.gs);
     if (rs != RECON_OK) break;
@@ -802,24 +819,45 @@ recon_status iterate_start_from(recon_handle* h, const float* u0) {
   return RECON_OK;
 }
 
+// Warm start: recon_start_features left delta(k), S_-1 and the start's radial displacement u_s
+// (real, in the first vector field); P_0 = (u_s + up(u0 - mean(u_s))) r transformed along z and x.
+recon_status iterate_start_warm(recon_handle* h, const float* u0, int level) {
+  ZArgs za = zargs(h);
+  for (int q = 0; q < 3; ++q) za.f[q] = h->V[q];
+  za.u_in = reinterpret_cast<const float*>(h->V[0].M);
+  za.corr = u0;
+  za.ucoarse = h->ucoarse;
+  za.clevel = level;
+  RG_TRY(run_z(h, Z_WARM, 3, za));
+  RG_TRY(xpass(h, S_FWD, 3, h->V));
+  return RECON_OK;
+}
+
+recon_status run_start(recon_handle* h, const StartSpec& sp) {
+  if (!sp.u0) return iterate_start(h, sp.coef0);
+  if (sp.level == 0) return iterate_start_from(h, sp.u0);
+  return iterate_start_warm(h, sp.u0, sp.level);
+}
+
 // The loop of Sec. 5.1 after a start: device-driven (one CUDA graph) or host-driven.
-recon_status iterate_core(recon_handle* h, float coef0, const float* u0, double tol, int max_iter, int* n_iter,
+recon_status iterate_core(recon_handle* h, const StartSpec& sp, double tol, int max_iter, int* n_iter,
                           double* rel_change) {
   h->trace.clear();
   h->delta_real_valid = 0;
+  h->warm_level = -1;
   double rel = 0.0;
   int it = 0;
   recon_status result = RECON_OK;
   if (h->use_graph && !h->timing && max_iter <= kMaxTrace) {
     int flag = 0;
-    RG_TRY(iterate_graph(h, coef0, u0, tol, max_iter, &it, &rel, &flag));
+    RG_TRY(iterate_graph(h, sp, tol, max_iter, &it, &rel, &flag));
     h->d_is_k = 1;
     if (flag == 2) {
       h->state = ST_SMOOTHED;
       result = RECON_ERR_NONFINITE;
     }
   } else {
-    RG_TRY(u0 ? iterate_start_from(h, u0) : iterate_start(h, coef0));
+    RG_TRY(run_start(h, sp));
     h->d_is_k = 1;
     ZArgs za = zargs(h);
     for (int q = 0; q < 3; ++q) za.f[q] = h->V[q];
@@ -871,23 +909,30 @@ recon_status recon_iterate(recon_handle* h, int start, double tol, int max_iter,
   if (max_iter < 1 || !(tol >= 0) || start < RECON_START_PLAIN || start > RECON_START_FFTA)
     return RECON_ERR_INVALID_ARG;
   const double beta = h->p.f / h->p.b;
-  const float coef0 = (float)(1.0 - start_coefficient(start, beta));
-  return iterate_core(h, coef0, nullptr, tol, max_iter, n_iter, rel_change);
+  StartSpec sp;
+  sp.coef0 = (float)(1.0 - start_coefficient(start, beta));
+  return iterate_core(h, sp, tol, max_iter, n_iter, rel_change);
 }
 
-recon_status recon_iterate_from(recon_handle* h, const float* u0, double tol, int max_iter, int* n_iter,
+recon_status recon_iterate_from(recon_handle* h, const float* u0, int level, double tol, int max_iter, int* n_iter,
                                 double* rel_change) {
-  if (!h || !u0) return RECON_ERR_INVALID_ARG;
+  if (!h || !u0 || level < 0 || level > 2) return RECON_ERR_INVALID_ARG;
   if (h->state < ST_SMOOTHED) return RECON_ERR_STATE;
   if (max_iter < 1 || !(tol >= 0)) return RECON_ERR_INVALID_ARG;
-  return iterate_core(h, 1.f, u0, tol, max_iter, n_iter, rel_change);
+  if (level > 0 && h->warm_level != level) return RECON_ERR_STATE;
+  StartSpec sp;
+  sp.u0 = u0;
+  sp.level = level;
+  return iterate_core(h, sp, tol, max_iter, n_iter, rel_change);
 }
 
-recon_status recon_start_features(recon_handle* h, int start, float* feat) {
-  if (!h || !feat || start < RECON_START_PLAIN || start > RECON_START_FFTA) return RECON_ERR_INVALID_ARG;
+recon_status recon_start_features(recon_handle* h, int start, int level, float* feat) {
+  if (!h || !feat || start < RECON_START_PLAIN || start > RECON_START_FFTA || level < 0 || level > 2)
+    return RECON_ERR_INVALID_ARG;
+  if (h->n % (1 << level) != 0) return RECON_ERR_UNSUPPORTED;
   if (h->state < ST_SMOOTHED || !h->delta_real_valid) return RECON_ERR_STATE;
   RG_CUDA(timed(h, RECON_K_OTHER, 0.0, [&] {
-    return launch_features(reinterpret_cast<const float*>(h->V[2].M), h->geo, feat, h->st); }));
+    return launch_features(reinterpret_cast<const float*>(h->V[2].M), h->geo, level, feat, h->st); }));
   {
     SArgs a = sargs(h);
     for (int q = 0; q < 3; ++q) a.f[q] = h->V[q];
@@ -898,21 +943,24 @@ recon_status recon_start_features(recon_handle* h, int start, float* feat) {
   RG_TRY(xpass(h, S_INV, 3, h->V));
   ZArgs za = zargs(h);
   for (int q = 0; q < 3; ++q) za.f[q] = h->V[q];
-  RG_TRY(run_z(h, Z_FINAL, 3, za));
-  const float coef = (float)(1.0 - start_coefficient(start, h->p.f / h->p.b));
+  za.coef = (float)(1.0 - start_coefficient(start, h->p.f / h->p.b));
+  za.u_out = reinterpret_cast<float*>(h->V[0].M);
+  RG_TRY(run_z(h, Z_RADIAL, 3, za));
   RG_CUDA(timed(h, RECON_K_OTHER, 0.0, [&] {
-    return launch_radial(reinterpret_cast<const float*>(h->V[0].M), reinterpret_cast<const float*>(h->V[1].M),
-                         reinterpret_cast<const float*>(h->V[2].M), h->geo, coef, feat, 5, 4, h->st); }));
+    return launch_radial(reinterpret_cast<const float*>(h->V[0].M), nullptr, nullptr, h->geo, 1.f, level, feat, 5, 4,
+                         level ? h->ucoarse : nullptr, h->st); }));
   h->delta_real_valid = 0;
+  h->warm_level = level;
   return RECON_OK;
 }
 
-recon_status recon_get_radial(recon_handle* h, float* u) {
-  if (!h || !u) return RECON_ERR_INVALID_ARG;
+recon_status recon_get_radial(recon_handle* h, int level, float* u) {
+  if (!h || !u || level < 0 || level > 2) return RECON_ERR_INVALID_ARG;
+  if (h->n % (1 << level) != 0) return RECON_ERR_UNSUPPORTED;
   if (h->state != ST_ITERATED) return RECON_ERR_STATE;
   RG_CUDA(timed(h, RECON_K_OTHER, 0.0, [&] {
     return launch_radial(reinterpret_cast<const float*>(h->V[0].M), reinterpret_cast<const float*>(h->V[1].M),
-                         reinterpret_cast<const float*>(h->V[2].M), h->geo, 1.f, u, 1, 0, h->st); }));
+                         reinterpret_cast<const float*>(h->V[2].M), h->geo, 1.f, level, u, 1, 0, nullptr, h->st); }));
   return RECON_OK;
 }
 
@@ -1058,6 +1106,7 @@ recon_status recon_fft_r2c(recon_handle* h, const float* in_real, float* out_hal
   if (!h || !in_real || !out_half) return RECON_ERR_INVALID_ARG;
   const size_t nr = (size_t)h->n * h->n * h->n;
   h->state = ST_CREATED;
+  h->warm_level = -1;
   h->d_is_k = 0;
   h->delta_real_valid = 0;
   RG_CUDA(cudaMemcpyAsync(h->V[0].M, in_real, nr * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
@@ -1076,6 +1125,7 @@ recon_status recon_fft_c2r(recon_handle* h, const float* in_half, float* out_rea
   if (!h || !in_half || !out_real) return RECON_ERR_INVALID_ARG;
   const size_t nr = (size_t)h->n * h->n * h->n;
   h->state = ST_CREATED;
+  h->warm_level = -1;
   h->d_is_k = 0;
   h->delta_real_valid = 0;
   RG_TRY(import_half(h, in_half, h->V[0]));

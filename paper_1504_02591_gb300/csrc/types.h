@@ -37,7 +37,7 @@ struct Geometry {
   const float* off;       // 3 N node offsets from the observer: x_i - o_a, per axis a (radial)
 };
 
-enum ZMode { Z_FWD = 0, Z_INV = 1, Z_DELTA = 2, Z_PROJ = 3, Z_FINAL = 4, Z_USTART = 5 };
+enum ZMode { Z_FWD = 0, Z_INV = 1, Z_DELTA = 2, Z_PROJ = 3, Z_FINAL = 4, Z_USTART = 5, Z_RADIAL = 6, Z_WARM = 7 };
 enum SMode { S_FWD = 0, S_INV = 1, S_DELTA = 3, S_ITER = 4 };
 enum Axis { AX_X = 0, AX_Y = 1 };
 
@@ -59,7 +59,12 @@ struct ZArgs {
   int ntap;
   int t0;
   const int* loop_flag;   // Z_PROJ in a device-driven loop: 1 = converged, write the real Psi
-  const float* u_in;      // Z_USTART: radial displacement u (real N^3); P = u r is transformed
+  const float* u_in;      // Z_USTART / Z_WARM: radial displacement u (real N^3); P = u r is transformed
+  float* u_out;           // Z_RADIAL: coef (Psi.r), real N^3 (may alias f[0])
+  // Z_WARM: u += trilinear upsampling of (corr - ucoarse), both on the (N >> clevel)^3 grid
+  const float* corr;
+  const float* ucoarse;
+  int clevel;
 };
 
 struct SArgs {

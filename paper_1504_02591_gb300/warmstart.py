@@ -15,16 +15,17 @@ import numpy as np
 from . import binding as B
 
 
-def training_pair(mock, tol=1e-6, max_iter=120, start=B.START_FFTA):
-    """(features, target) for one mock: the network inputs after smoothing, and the converged
-    radial displacement from the plain method (the iteration from the analytic start)."""
+def training_pair(mock, level=0, tol=1e-6, max_iter=120, start=B.START_FFTA):
+    """(features, target, n_iter) for one mock: the network inputs after smoothing and the block means
+    of the converged radial displacement from the plain method (the iteration from the analytic
+    start), both on the mesh coarsened `level` times."""
     r = B.Recon.from_mock(mock)
     try:
         r.deposit(mock.galaxies.pos, None, None if mock.randoms is None else mock.randoms.pos, None)
         r.smooth()
-        feat = r.start_features(start)
+        feat = r.start_features(start, level)
         n_it, rel, st = r.iterate(start, tol, max_iter)
-        u = r.get_radial()
+        u = r.get_radial(level)
     finally:
         r.close()
     return feat, u, n_it
@@ -41,11 +42,12 @@ def train(net, pairs, steps, lr=1e-3, wd=1e-4, warmup=20):
     return losses
 
 
-def warm_iterate(recon, net, tol=1e-6, max_iter=120):
-    """After recon.smooth(): network start, then the iteration to the stopping rule."""
-    feat = recon.start_features(B.START_FFTA)
+def warm_iterate(recon, net, level=0, tol=1e-6, max_iter=120):
+    """After recon.smooth(): network start on the mesh coarsened `level` times, then the iteration
+    to the stopping rule."""
+    feat = recon.start_features(B.START_FFTA, level)
     u0 = net.forward(feat)
-    return recon.iterate_from(u0, tol, max_iter)
+    return recon.iterate_from(u0, tol, max_iter, level)
 
 
 def save(net, path):
