@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--max-iter", type=int, default=80)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-warm", action="store_true")
     return ap.parse_args()
 
 
@@ -190,7 +191,7 @@ def gpu_arm(args):
     import torch
     import torch.distributed as dist
 
-    from paper_1504_02591_gb300 import binding
+    from paper_1504_02591_gb300 import binding, warmstart
 
     ws, rank, local = dist_info()
     torch.cuda.set_device(local)
@@ -255,10 +256,44 @@ def gpu_arm(args):
     r.set_timing(False)
     kt = r.timing()
 
-    # the uncorrected ("plain") start on the same input, for the plain vs corrected comparison
+    # the uncorrected start (c = 0) on the same input
     plain_steps = 2
     plain_ms = timed(plain_steps, lambda: step(binding.START_PLAIN)) / plain_steps
     plain_iter = info["n_iter"]
+
+    # the learned warm start on the same input: the network trained for this workload on other
+    # seeds (train_warmstart.py), run on the mesh coarsened `level` times, then the same iteration
+    # from its prediction to the same stopping rule
+    warm = None
+    wpath = warmstart.default_weights_path()
+    if not args.no_warm and os.path.exists(wpath):
+        net, level = warmstart.load(wpath)
+
+        def step_warm():
+            r.deposit(gal, None, ran, None)
+            r.smooth()
+            feat = r.start_features(binding.START_FFTA, level)
+            info["warm_feat"] = feat
+            y = net.forward(feat)
+            n_it, rel_w, st = r.iterate_from(y, args.tol, args.max_iter, level)
+            r.shift(gal, True, out=sg)
+            r.shift(ran, False, out=sr)
+            info["warm_iter"], info["warm_rel"], info["warm_status"] = n_it, rel_w, st
+
+        for _ in range(2):
+            step_warm()
+        r.reset_timing()
+        l0 = net.launch_count()
+        warm_ms = timed(args.steps, step_warm) / args.steps
+        warm_launches = sum(v[0] for v in r.timing().values()) + net.launch_count() - l0
+        # the network alone, on this workload's features
+        feat = info.pop("warm_feat")
+        net_ms = timed(3, lambda: net.forward(feat)) / 3
+        warm = {"ms": round(warm_ms, 4), "n_iter": info["warm_iter"], "final_rel": info["warm_rel"],
+                "network_ms": round(net_ms, 4), "level": level, "grid": args.mesh >> level, "c1": net.c1,
+                "gpu_launches": int(warm_launches),
+                "weights": os.path.relpath(wpath, os.path.dirname(os.path.abspath(__file__)))}
+        net.close()
 
     # roofline of the dominant kernel (largest share of device time in the timed region)
     peak, peak_kind = peaks()
@@ -309,6 +344,7 @@ def gpu_arm(args):
                        "l2": "inputs larger than L2 (each field 539 MB), no flush",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "plain_start": {"ms": round(plain_ms, 4), "n_iter": plain_iter},
+            "warm_start": warm,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                          "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": recorded_traffic(dom), "alg_bytes_per_launch": by / cnt,

@@ -340,6 +340,8 @@ recon_status recon_unet_set_option(recon_unet* u, int option, int value);
  * float32 on the host (count = side^3 x cout of that layer's level).  STATE if that activation was
  * not stored (the last layer when its 1x1 head was fused into it). */
 recon_status recon_unet_get_layer(recon_unet* u, int layer, float* host, size_t count);
+/* Number of kernels the tensor-core forward path of recon_unet_forward has launched so far. */
+recon_status recon_unet_launch_count(recon_unet* u, long long* count);
 recon_status recon_unet_destroy(recon_unet* u);
 const char* recon_unet_last_error(recon_unet* u);
 

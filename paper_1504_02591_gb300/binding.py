@@ -32,6 +32,7 @@ ABI_SYMBOLS = (
     "recon_unet_param_count", "recon_unet_create", "recon_unet_set_params", "recon_unet_get_params",
     "recon_unet_get_grads", "recon_unet_forward", "recon_unet_backward", "recon_unet_adamw",
     "recon_unet_destroy", "recon_unet_last_error", "recon_unet_set_option", "recon_unet_get_layer",
+    "recon_unet_launch_count",
     "recon_iterate_from", "recon_start_features",
     "recon_get_radial",
 )
@@ -114,6 +115,7 @@ def load(path: str = LIB_PATH):
     lib.recon_unet_destroy.argtypes = [VP]
     lib.recon_unet_set_option.argtypes = [VP, C.c_int, C.c_int]
     lib.recon_unet_get_layer.argtypes = [VP, C.c_int, VP, C.c_size_t]
+    lib.recon_unet_launch_count.argtypes = [VP, C.POINTER(C.c_longlong)]
     lib.recon_unet_last_error.argtypes = [VP]
     lib.recon_unet_last_error.restype = C.c_char_p
     lib.recon_cic_deposit_noalloc.argtypes = [VP, I, VP, C.c_int64, I, D, VP, VP, VP]
@@ -499,6 +501,11 @@ class UNet:
 
     def set_option(self, option, value):
         self._check(self.lib.recon_unet_set_option(self.h, int(option), int(value)), "recon_unet_set_option")
+
+    def launch_count(self):
+        c = C.c_longlong(0)
+        self._check(self.lib.recon_unet_launch_count(self.h, C.byref(c)), "recon_unet_launch_count")
+        return c.value
 
     def get_layer(self, layer, n, cout):
         """Output of convolution layer `layer` of the last forward, (n, n, n, cout) host float32."""

@@ -384,6 +384,7 @@ struct recon_unet {
   int plan_n = 0;
   unsigned pver = 1, packed_ver = 0;   // parameter version, version the packed tiles were made from
   int last_n = 0;                      // side of the last forward
+  long long launches = 0;              // kernels launched by recon_unet_forward (all calls)
   bool head_fused = false;             // last forward fused the head into layer 9 (d1b not stored)
 };
 
@@ -576,8 +577,10 @@ recon_status tc_prepare(recon_unet* u, int n) {
   if (u->packed_ver != u->pver) {
     const bf16* w = static_cast<const bf16*>(u->pt);
     for (int l = 0; l < 10; ++l)
-      if (u->plan_ok[l])
+      if (u->plan_ok[l]) {
+        ++u->launches;
         UN_CUDA(tc::pack_weights(u->plan[l], w + u->woff[l], static_cast<bf16*>(u->wpack) + u->pack_off[l], u->st));
+      }
     u->packed_ver = u->pver;
   }
   return RECON_OK;
@@ -595,6 +598,7 @@ recon_status forward_tc(recon_unet* u, const float* x, int n, float* out) {
   const int c1 = u->c1, c2 = 2 * c1, c3 = 4 * c1, n2 = n / 2, n4 = n / 4;
   const long long V1 = (long long)n * n * n;
   auto run = [&](int l, const bf16* s0, const bf16* s1, bf16* y) -> cudaError_t {
+    ++u->launches;
     tc::ConvIO io;
     io.src0 = s0;
     io.src1 = s1;
@@ -605,9 +609,11 @@ recon_status forward_tc(recon_unet* u, const float* x, int n, float* out) {
     return tc::conv_forward(u->plan[l], io, u->st);
   };
   auto plain = [&](int l, const bf16* s0, int ca, bf16* y, int nl) -> cudaError_t {
-    return u->plan_ok[l] ? run(l, s0, nullptr, y)
-                         : conv_fwd<bf16>(u, l, s0, ca, nullptr, 0, nl, 1, nullptr, 0, y, nullptr);
+    if (u->plan_ok[l]) return run(l, s0, nullptr, y);
+    ++u->launches;
+    return conv_fwd<bf16>(u, l, s0, ca, nullptr, 0, nl, 1, nullptr, 0, y, nullptr);
   };
+  u->launches += 3;   // input conversion and the two poolings
   if (u->plan_ok[0]) {
     to_x8_kernel<<<grid_for(V1), 256, 0, u->st>>>(x, u->cin, V1, a + A.x8);
     UN_CUDA(run(0, a + A.x8, nullptr, a + A.a1a));
@@ -625,6 +631,7 @@ recon_status forward_tc(recon_unet* u, const float* x, int n, float* out) {
   if (u->plan_ok[6]) {
     UN_CUDA(run(6, a + A.a3b, a + A.a2b, a + A.d2a));
   } else {
+    u->launches += 2;
     up_kernel<bf16><<<grid_for(V1 / 8 * c3), 256, 0, u->st>>>(a + A.a3b, c3, n2, a + A.u3);
     UN_CUDA(conv_fwd<bf16>(u, 6, a + A.u3, c3, a + A.a2b, c2, n2, 1, nullptr, 0, a + A.d2a, nullptr));
   }
@@ -632,6 +639,7 @@ recon_status forward_tc(recon_unet* u, const float* x, int n, float* out) {
   if (u->plan_ok[8]) {
     UN_CUDA(run(8, a + A.d2b, a + A.a1b, a + A.d1a));
   } else {
+    u->launches += 2;
     up_kernel<bf16><<<grid_for(V1 * c2), 256, 0, u->st>>>(a + A.d2b, c2, n, a + A.u2);
     UN_CUDA(conv_fwd<bf16>(u, 8, a + A.u2, c2, a + A.a1b, c1, n, 1, nullptr, 0, a + A.d1a, nullptr));
   }
@@ -647,8 +655,10 @@ recon_status forward_tc(recon_unet* u, const float* x, int n, float* out) {
     io.res_stride = u->cin;
     io.yout = out;
     io.err = u->dev_err;
+    ++u->launches;
     UN_CUDA(tc::conv_forward(u->plan[9], io, u->st));
   } else {
+    ++u->launches;
     UN_CUDA(plain(9, a + A.d1a, c1, a + A.d1b, n));
     UN_CUDA(conv_fwd<bf16>(u, 10, a + A.d1b, c1, nullptr, 0, n, 0, x + (u->cin - 1), u->cin, nullptr, out));
   }
@@ -848,6 +858,12 @@ recon_status recon_unet_set_option(recon_unet* u, int option, int value) {
     return RECON_OK;
   }
   return RECON_ERR_INVALID_ARG;
+}
+
+recon_status recon_unet_launch_count(recon_unet* u, long long* count) {
+  if (!u || !count) return RECON_ERR_INVALID_ARG;
+  *count = u->launches;
+  return RECON_OK;
 }
 
 recon_status recon_unet_get_layer(recon_unet* u, int layer, float* host, size_t count) {

@@ -250,13 +250,14 @@ def small_periodic(n_gal: int = 200_000, n_ran: int = 2_000_000, n_mesh: int = 6
 
 
 def survey_shell_512(n_gal: int = 600_000, ran_ratio: int = 50, n_mesh: int = 512,
-                     L: float = 3500.0) -> Mock:
+                     L: float = 3500.0, seed: int = 10) -> Mock:
     """512^3 mesh in a 3500 Mpc/h box, shell 1100-1800 Mpc/h, 25% sky cap, 6e5 galaxies, 50x
     randoms, b = 1.85, f = 0.74, R = 15.  Observer at the centre of the x = 0 face, cap axis +x
-    (a box-corner observer sees at most 1/8 of the sky, so a 25% cap cannot sit at the corner)."""
+    (a box-corner observer sees at most 1/8 of the sky, so a 25% cap cannot sit at the corner).
+    Seeds seed, seed + 1, seed + 2 (field, galaxies, randoms); the benchmark mock is seed 10."""
     return shell_survey(L, n_mesh, n_gal, n_gal * ran_ratio, 1.85, 0.74, 15.0,
                         (0.0, L / 2, L / 2), (1.0, 0.0, 0.0), 1100.0, 1800.0, 0.25,
-                        10, 11, 12, ng=256, name=f"shell-{n_mesh}")
+                        seed, seed + 1, seed + 2, ng=256, name=f"shell-{n_mesh}")
 
 
 def scaled_shell(n_mesh: int, L: float, n_gal: int, ran_ratio: int, b: float, f: float,

@@ -50,16 +50,24 @@ def warm_iterate(recon, net, level=0, tol=1e-6, max_iter=120):
     return recon.iterate_from(u0, tol, max_iter, level)
 
 
-def save(net, path):
-    np.savez(path, params=net.get_params(), c1=net.c1)
+def save(net, path, level, meta=None):
+    """Weights (float32, the ABI's parameter order), width, level; meta (a dict) as JSON beside."""
+    import json
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    np.savez(path, params=net.get_params(), c1=net.c1, level=level)
+    if meta is not None:
+        with open(os.path.splitext(path)[0] + ".json", "w") as f:
+            json.dump(meta, f, indent=1)
 
 
 def load(path, bf16=True):
+    """(network, level) from a file written by save()."""
     d = np.load(path)
     net = B.UNet(c1=int(d["c1"]), bf16=bf16)
     net.set_params(d["params"])
-    return net
+    return net, int(d["level"])
 
 
-def default_weights_path(c1=16):
-    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", f"unet_c{c1}.npz")
+def default_weights_path():
+    """The network trained for the 512^3 survey-shell workload (train_warmstart.py)."""
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "warm_shell512_c8_l2.npz")
