@@ -65,7 +65,7 @@ def workload(mesh):
 
 def workload_name(mesh):
     return (f"survey shell {mesh}^3, L=3500 Mpc/h, 6e5 galaxies + 3e7 randoms (50x), shell 1100-1800 "
-            f"Mpc/h, 25% sky, b=1.85 f=0.74 R=15, RSD-corrected start, tol 1e-6")
+            f"Mpc/h, 25% sky, b=1.85 f=0.74 R=15, converged to 1e-6")
 
 
 class Clocks:
@@ -237,63 +237,62 @@ def gpu_arm(args):
             ms = float(t.item())
         return ms
 
-    for _ in range(max(3, args.warmup)):
-        step()
-    # timed region: the library's default path (iteration as one CUDA graph), no per-kernel events
-    r.reset_timing()
-    clocks = Clocks(local)
-    clocks.start()
-    total_ms = timed(args.steps, step)
-    clk = clocks.stop()
-    launches = sum(v[0] for v in r.timing().values())
-    n_iter, rel = info["n_iter"], info["rel"]
-    ms_per_step = total_ms / args.steps
-    # per-kernel CUDA-event timings over the same number of steps (events around every launch on
-    # the library's stream; the iteration runs host-driven so that each launch can be bracketed)
-    r.reset_timing()
-    r.set_timing(True)
-    timed(args.steps, step)
-    r.set_timing(False)
-    kt = r.timing()
-
-    # the uncorrected start (c = 0) on the same input
-    plain_steps = 2
-    plain_ms = timed(plain_steps, lambda: step(binding.START_PLAIN)) / plain_steps
-    plain_iter = info["n_iter"]
-
-    # the learned warm start on the same input: the network trained for this workload on other
-    # seeds (train_warmstart.py), run on the mesh coarsened `level` times, then the same iteration
-    # from its prediction to the same stopping rule
-    warm = None
+    # the learned warm start: the network trained for this workload on other seeds
+    # (train_warmstart.py), run on the mesh coarsened `level` times, then the same iteration from its
+    # prediction to the same stopping rule.  It is the timed path when its weights are present.
+    net, level = None, 0
     wpath = warmstart.default_weights_path()
     if not args.no_warm and os.path.exists(wpath):
         net, level = warmstart.load(wpath)
 
-        def step_warm():
-            r.deposit(gal, None, ran, None)
-            r.smooth()
-            feat = r.start_features(binding.START_FFTA, level)
-            info["warm_feat"] = feat
-            y = net.forward(feat)
-            n_it, rel_w, st = r.iterate_from(y, args.tol, args.max_iter, level)
-            r.shift(gal, True, out=sg)
-            r.shift(ran, False, out=sr)
-            info["warm_iter"], info["warm_rel"], info["warm_status"] = n_it, rel_w, st
+    def step_warm(gal_in=gal, ran_in=ran, sg_out=sg, sr_out=sr):
+        r.deposit(gal_in, None, ran_in, None)
+        r.smooth()
+        feat = r.start_features(binding.START_FFTA, level)
+        info["warm_feat"] = feat
+        y = net.forward(feat)
+        n_it, rel_w, st = r.iterate_from(y, args.tol, args.max_iter, level)
+        r.shift(gal_in, True, out=sg_out)
+        r.shift(ran_in, False, out=sr_out)
+        info["n_iter"], info["rel"], info["status"] = n_it, rel_w, st
 
-        for _ in range(2):
-            step_warm()
-        r.reset_timing()
-        l0 = net.launch_count()
-        warm_ms = timed(args.steps, step_warm) / args.steps
-        warm_launches = sum(v[0] for v in r.timing().values()) + net.launch_count() - l0
-        # the network alone, on this workload's features
+    main_step = step_warm if net is not None else step
+    for _ in range(max(3, args.warmup)):
+        main_step()
+    # timed region: the library's default path (iteration as one CUDA graph), no per-kernel events
+    r.reset_timing()
+    l0 = net.launch_count() if net is not None else 0
+    clocks = Clocks(local)
+    clocks.start()
+    total_ms = timed(args.steps, main_step)
+    clk = clocks.stop()
+    launches = sum(v[0] for v in r.timing().values()) + ((net.launch_count() - l0) if net is not None else 0)
+    n_iter, rel = info["n_iter"], info["rel"]
+    ms_per_step = total_ms / args.steps
+    warm = None
+    if net is not None:
         feat = info.pop("warm_feat")
         net_ms = timed(3, lambda: net.forward(feat)) / 3
-        warm = {"ms": round(warm_ms, 4), "n_iter": info["warm_iter"], "final_rel": info["warm_rel"],
-                "network_ms": round(net_ms, 4), "level": level, "grid": args.mesh >> level, "c1": net.c1,
-                "gpu_launches": int(warm_launches),
+        warm = {"ms": round(ms_per_step, 4), "n_iter": n_iter, "final_rel": rel, "network_ms": round(net_ms, 4),
+                "level": level, "grid": args.mesh >> level, "c1": net.c1,
                 "weights": os.path.relpath(wpath, os.path.dirname(os.path.abspath(__file__)))}
-        net.close()
+    # the plain iteration from the Eq. approx2 start on the same input
+    for _ in range(2):
+        step()
+    plain_ms = timed(args.steps, step) / args.steps
+    plain = {"ms": round(plain_ms, 4), "n_iter": info["n_iter"], "final_rel": info["rel"], "start": "Eq. approx2"}
+    # per-kernel CUDA-event timings over the same number of steps (events around every launch on
+    # the library's stream; the iteration runs host-driven so that each launch can be bracketed)
+    r.reset_timing()
+    r.set_timing(True)
+    timed(args.steps, main_step)
+    r.set_timing(False)
+    kt = r.timing()
+
+    # the uncorrected start (c = 0) on the same input
+    unc_steps = 2
+    unc_ms = timed(unc_steps, lambda: step(binding.START_PLAIN)) / unc_steps
+    unc_iter = info["n_iter"]
 
     # roofline of the dominant kernel (largest share of device time in the timed region)
     peak, peak_kind = peaks()
@@ -304,6 +303,9 @@ def gpu_arm(args):
     kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / sum(x[1] for x in busy.values()), 4),
                    "GBps": round(v[2] / (v[1] * 1e-3) / 1e9, 1) if v[1] > 0 else None}
                for k, v in busy.items()}
+    if warm:
+        kernels["unet_forward"] = {"launches": args.steps, "ms": round(warm["network_ms"] * args.steps, 3),
+                                   "share": None, "GBps": None}
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     e2e = None
@@ -314,6 +316,9 @@ def gpu_arm(args):
         sr_h = torch.empty((len(ran_h), 3), dtype=torch.float32).pin_memory()
 
         def step_e2e():
+            if net is not None:
+                step_warm(gal_h, ran_h, sg_h, sr_h)
+                return
             r.deposit(gal_h, None, ran_h, None)
             r.smooth()
             r.iterate(binding.START_FFTA, args.tol, args.max_iter)
@@ -341,10 +346,13 @@ def gpu_arm(args):
             "data": "synthetic",
             "config": {"workload": workload_name(args.mesh), "mesh": args.mesh, "box": 3500.0,
                        "n_gal": len(gal), "n_ran": len(ran), "n_iter": n_iter, "final_rel": rel,
+                       "start": "learned warm start (U-Net on the 4x coarsened mesh)" if warm else "Eq. approx2",
                        "l2": "inputs larger than L2 (each field 539 MB), no flush",
                        "parallelism": "replicas" if ws > 1 else "single"},
-            "plain_start": {"ms": round(plain_ms, 4), "n_iter": plain_iter},
+            "path": "learned warm start" if warm else "Eq. approx2 start",
             "warm_start": warm,
+            "plain": plain,
+            "uncorrected_start": {"ms": round(unc_ms, 4), "n_iter": unc_iter},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                          "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": recorded_traffic(dom), "alg_bytes_per_launch": by / cnt,
@@ -356,6 +364,8 @@ def gpu_arm(args):
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
+    if net is not None:
+        net.close()
     r.close()
     if ws > 1:
         dist.destroy_process_group()
