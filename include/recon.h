@@ -258,8 +258,11 @@ enum {
                                    with a conditional WHILE node and a device-side convergence
                                    test; 0: the host reads the norms after every update.  Kernel
                                    timing (recon_set_timing) always uses the host-driven loop.   */
-  RECON_OPT_LINE_TILE = 3       /* FFT tile of the x-line passes: 0 (default) 16 adjacent columns
+  RECON_OPT_LINE_TILE = 3,      /* FFT tile of the x-line passes: 0 (default) 16 adjacent columns
                                    (128-byte rows) per tile, 1: 8 columns                         */
+  RECON_OPT_KSPACE_GENERIC = 4  /* 0 (default): for N = 512 the source update runs in the kernel
+                                   that keeps the last forward and first inverse FFT stage in
+                                   registers; 1: the generic staged kernel (same butterflies)     */
 };
 /* Particle paths: DIRECT handles each particle independently (8 global atomics per deposited
  * particle; 24 scattered reads per interpolated one); SORTED packs the particles, counting-sorts

@@ -605,6 +605,148 @@ constexpr size_t spass_smem(int nslots) {
   return sizeof(float2) * ((size_t)((Plan<N>::kTab + 1) & ~1) + (size_t)nslots * N * SCols<N, MODE, NARROW>::v);
 }
 
+// ------------------------------------------------------------------------------------------------
+// The k-space update along y for N = 512 = 8 x 8 x 8.  With three radix-8 Stockham stages the
+// butterfly j of the last forward stage produces X[j + 64 r] (r = 0..7), and these are exactly the
+// inputs of butterfly j of the first inverse stage.  So each thread loads its 8 points of a column
+// straight from global memory into the first forward stage, keeps the last forward stage's outputs
+// in registers for the source update, starts the inverse transform on them, and stores the last
+// inverse stage straight to global memory: two shared-memory round trips per transform instead of
+// three plus the staging of loads, stores and the update.  The arithmetic of every butterfly is the
+// same as in the generic stages.
+// ------------------------------------------------------------------------------------------------
+template <int N, int C>
+struct KIter8 {
+  static_assert(N == 512, "three radix-8 stages");
+  static constexpr int T = (N / 8) * C;        // one butterfly of one column per thread and stage
+  static constexpr int TAB = (Plan<N>::kTab + 1) & ~1;
+  static constexpr size_t smem = sizeof(float2) * ((size_t)TAB + (size_t)N * C);
+};
+
+// stage 2 (NS = 8): butterfly j reads j + 64 r, twiddles w64^(r (j mod 8)), writes (j / 8) 64 + j mod 8 + 8 r
+template <bool INV, int C>
+__device__ __forceinline__ void r512_mid(float2* __restrict__ s, const float2* __restrict__ tw, int j, int col) {
+  using Lay = ColLayout<C>;
+  float2 v[8];
+  const int k = j & 7;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) v[r] = s[Lay::phys(j + 64 * r, col)];
+#pragma unroll
+  for (int r = 1; r < 8; ++r) {
+    float2 w = tw[(r - 1) * 8 + k];
+    if (INV) w.y = -w.y;
+    v[r] = cmul(v[r], w);
+  }
+  Dft<8, INV>::run(v);
+  __syncthreads();
+  const int base = (j >> 3) * 64 + k;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) s[Lay::phys(base + 8 * r, col)] = v[r];
+  __syncthreads();
+}
+
+// The 512-point transform of one column: v[r] = x[j + 64 r] in, X[j + 64 r] out (registers).
+template <bool INV, int C>
+__device__ __forceinline__ void r512_line(float2 (&v)[8], float2* __restrict__ s, const float2* __restrict__ tw, int j,
+                                          int col) {
+  using Lay = ColLayout<C>;
+  Dft<8, INV>::run(v);                                   // stage 1 (NS = 1): no twiddles
+#pragma unroll
+  for (int r = 0; r < 8; ++r) s[Lay::phys(8 * j + r, col)] = v[r];
+  __syncthreads();
+  r512_mid<INV, C>(s, tw, j, col);
+#pragma unroll
+  for (int r = 0; r < 8; ++r) v[r] = s[Lay::phys(j + 64 * r, col)];
+#pragma unroll
+  for (int r = 1; r < 8; ++r) {                          // stage 3 (NS = 64): twiddles w512^(r j)
+    float2 w = tw[56 + (r - 1) * 64 + j];
+    if (INV) w.y = -w.y;
+    v[r] = cmul(v[r], w);
+  }
+  Dft<8, INV>::run(v);
+  __syncthreads();                                       // s is reused by the next line
+}
+
+template <int N, int C>
+__global__ void __launch_bounds__(KIter8<N, C>::T, 2) kiter8_kernel(const SArgs a) {
+  constexpr int T = KIter8<N, C>::T;
+  constexpr int H = N / 2;
+  extern __shared__ float4 ssm[];
+  float2* tw = reinterpret_cast<float2*>(ssm);
+  float2* s = tw + KIter8<N, C>::TAB;
+  __shared__ double red_sh[T / 32];
+  for (int m = threadIdx.x; m < Plan<N>::kTab; m += T) tw[m] = a.tab[m];
+  const Tile t = tile_of<N, C, AX_Y>(blockIdx.x);
+  const int col = threadIdx.x % C, j = threadIdx.x / C;
+
+  // every global read of the tile up front: the three components, delta(k), S_(n-1)
+  float2 v[3][8], dk[8], sp[8];
+  {
+    const float2* __restrict__ dkp = t.isQ ? a.dk.Q : a.dk.M;
+    const float2* __restrict__ spp = t.isQ ? a.sbuf.Q : a.sbuf.M;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const size_t gi = t.base + (size_t)(j + 64 * r) * t.ls + (size_t)col * t.cs;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) v[q][r] = (t.isQ ? a.f[q].Q : a.f[q].M)[gi];
+      dk[r] = dkp[gi];
+      sp[r] = spp[gi];
+    }
+  }
+  __syncthreads();   // twiddles
+#pragma unroll
+  for (int q = 0; q < 3; ++q) r512_line<false, C>(v[q], s, tw, j, col);
+
+  // S_n = delta/b + beta i k . P_n, the Parseval norms, Psi_n+1 = i kd S_n / k^2 (Eq. iterative)
+  float d2 = 0.f, s2 = 0.f;
+  const Geometry& g = a.g;
+  float2* Sp = t.isQ ? a.sbuf.Q : a.sbuf.M;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int ky = j + 64 * r;
+    int ix, kz;
+    if (!t.isQ) { ix = t.a; kz = t.c0 + col; } else { ix = t.c0 + col; kz = H; }
+    const int mx = (ix < H) ? ix : ix - N;
+    const int my = (ky < H) ? ky : ky - N;
+    const float kx = g.kf * mx, kyf = g.kf * my, kzf = g.kf * kz;
+    const float k2 = kx * kx + kyf * kyf + kzf * kzf;
+    const float kdx = (ix == H) ? 0.f : kx;
+    const float kdy = (ky == H) ? 0.f : kyf;
+    const float kdz = (kz == H) ? 0.f : kzf;
+    const float2 px = v[0][r], py = v[1][r], pz = v[2][r];
+    const float dre = kdx * px.x + kdy * py.x + kdz * pz.x;
+    const float dim = kdx * px.y + kdy * py.y + kdz * pz.y;
+    float2 S = make_float2(fmaf(a.beta, -dim, dk[r].x * a.inv_b), fmaf(a.beta, dre, dk[r].y * a.inv_b));
+    if (k2 == 0.f) S = make_float2(0.f, 0.f);
+    const float inv_k2 = (k2 > 0.f) ? 1.f / k2 : 0.f;
+    const float wgt = (kz == 0 || kz == H) ? 1.f : 2.f;
+    const float fac = wgt * (kdx * kdx + kdy * kdy + kdz * kdz) * inv_k2 * inv_k2;
+    const float ddx = S.x - sp[r].x, ddy = S.y - sp[r].y;
+    d2 = fmaf(fac, ddx * ddx + ddy * ddy, d2);
+    s2 = fmaf(fac, S.x * S.x + S.y * S.y, s2);
+    Sp[t.base + (size_t)ky * t.ls + (size_t)col * t.cs] = S;
+    const float2 iS = cscale(mul_i(S), inv_k2 * g.inv_n3);
+    v[0][r] = cscale(iS, kdx);
+    v[1][r] = cscale(iS, kdy);
+    v[2][r] = cscale(iS, kdz);
+  }
+
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    r512_line<true, C>(v[q], s, tw, j, col);
+    float2* __restrict__ dst = t.isQ ? a.f[q].Q : a.f[q].M;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) dst[t.base + (size_t)(j + 64 * r) * t.ls + (size_t)col * t.cs] = v[q][r];
+  }
+
+  double r0 = block_sum((double)d2, red_sh);
+  double r1 = block_sum((double)s2, red_sh);
+  if (threadIdx.x == 0) {
+    a.partials[2 * blockIdx.x + 0] = r0;
+    a.partials[2 * blockIdx.x + 1] = r1;
+  }
+}
+
 // Stage twiddle tables of the N-point (strided passes) and N/2-point (Z pass) plans, built once
 // from the float32 table of exp(-2 pi i m / N) that the host computed in float64.
 template <int N>
@@ -681,6 +823,22 @@ struct MeshImpl {
                             st);
   }
 
+  static cudaError_t klaunch(const SArgs& a, cudaStream_t st) {
+    if constexpr (N == 512) {
+      constexpr int C = SCols<N, S_ITER>::v;
+      const void* k = (const void*)kiter8_kernel<N, C>;
+      static bool attr = false;
+      if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)KIter8<N, C>::smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+      }
+      void* args[] = {const_cast<SArgs*>(&a)};
+      return cudaLaunchKernel(k, dim3(sblocks<S_ITER>()), dim3(KIter8<N, C>::T), args, KIter8<N, C>::smem, st);
+    }
+    return cudaErrorInvalidValue;
+  }
+
   static cudaError_t spass(int mode, int nc, int axis, const SArgs& a, cudaStream_t st) {
     if (nc < 1 || nc > 3) return cudaErrorInvalidValue;
     // plain passes: one component per CTA, components along gridDim.y
@@ -691,7 +849,12 @@ struct MeshImpl {
     if (mode == S_INV && axis == AX_X)
       return a.narrow ? slaunch<S_INV, 1, AX_X, 1>(a, st, nc) : slaunch<S_INV, 1, AX_X>(a, st, nc);
     if (mode == S_DELTA && axis == AX_Y) return slaunch<S_DELTA, 1, AX_Y>(a, st, 1);
-    if (mode == S_ITER && axis == AX_Y && nc == 3) return slaunch<S_ITER, 3, AX_Y>(a, st, 1);
+    if (mode == S_ITER && axis == AX_Y && nc == 3) {
+      if constexpr (N == 512) {
+        if (!a.generic) return klaunch(a, st);
+      }
+      return slaunch<S_ITER, 3, AX_Y>(a, st, 1);
+    }
     return cudaErrorInvalidValue;
   }
 

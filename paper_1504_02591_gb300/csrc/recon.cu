@@ -141,6 +141,7 @@ struct recon_handle {
   int deposit_path = RECON_PATH_DIRECT;
   int shift_path = RECON_PATH_SORTED;
   int narrow_lines = 0;
+  int kspace_generic = 0;
   int d_is_k = 0;
   int delta_real_valid = 0;
   float* ucoarse = nullptr;   // block means of the start's radial displacement (warm start, level >= 1)
@@ -250,6 +251,7 @@ SArgs sargs(recon_handle* h) {
   a.inv_b = (float)(1.0 / h->p.b);
   a.beta = (float)(h->p.f / h->p.b);
   a.narrow = h->narrow_lines;
+  a.generic = h->kspace_generic;
   a.lognormal = h->p.lognormal;
   return a;
 }
@@ -586,6 +588,7 @@ recon_status recon_set_option(recon_handle* h, int option, int value) {
   else if (option == RECON_OPT_SHIFT_PATH) h->shift_path = value;
   else if (option == RECON_OPT_GRAPH) h->use_graph = value;
   else if (option == RECON_OPT_LINE_TILE) h->narrow_lines = value;
+  else if (option == RECON_OPT_KSPACE_GENERIC) h->kspace_generic = value ? 1 : 0;
   else return RECON_ERR_INVALID_ARG;
   return RECON_OK;
 }

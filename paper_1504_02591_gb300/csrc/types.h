@@ -81,6 +81,7 @@ struct SArgs {
   int lognormal;          // S_DELTA: subtract the lognormal constant at k = 0
   const int* skip_flag;   // plain passes: do nothing when *skip_flag != 0 (device-driven loop)
   int narrow;             // plain x passes: 8-column instead of 16-column tiles
+  int generic;            // k-space update: the generic staged kernel instead of the register-fused one
 };
 
 // State of the device-driven iteration (in the workspace).
