@@ -260,9 +260,10 @@ enum {
                                    timing (recon_set_timing) always uses the host-driven loop.   */
   RECON_OPT_LINE_TILE = 3,      /* FFT tile of the x-line passes: 0 (default) 16 adjacent columns
                                    (128-byte rows) per tile, 1: 8 columns                         */
-  RECON_OPT_KSPACE_GENERIC = 4  /* 0 (default): for N = 512 the source update runs in the kernel
-                                   that keeps the last forward and first inverse FFT stage in
-                                   registers; 1: the generic staged kernel (same butterflies)     */
+  RECON_OPT_KSPACE_GENERIC = 4  /* 0 (default): for N = 512 the source update and the projection
+                                   pass run in kernels that keep the first and last FFT stages
+                                   (and the c2r/r2c pairing) in registers; 1: the generic staged
+                                   kernels (same butterflies)                                     */
 };
 /* Particle paths: DIRECT handles each particle independently (8 global atomics per deposited
  * particle; 24 scattered reads per interpolated one); SORTED packs the particles, counting-sorts

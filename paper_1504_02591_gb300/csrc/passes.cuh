@@ -363,6 +363,205 @@ __global__ void __launch_bounds__(kZThreads, 4) zpass_kernel(const ZArgs a) {
   }
 }
 
+// ------------------------------------------------------------------------------------------------
+// The projection pass for N = 512 (rows of L = 256 complex values, radices 8 x 8 x 4), one warp per
+// row.  Lane l holds the points l + 32 r (r = 0..7) of each component.  The c2r merge pairs point
+// m with L - m, which for l >= 1 sits on lane 32 - l (lane 0 pairs with itself and the Nyquist
+// value), so the merge runs on shuffles straight after the global loads and feeds the first
+// inverse stage in registers.  The last inverse stage (radix 4, butterflies l and l + 32) leaves
+// exactly the points l + 32 r on lane l, so the projection and the first forward stage run in
+// registers too; the r2c split again pairs lanes l and 32 - l, and the results go straight to
+// global memory.  Shared memory carries only the two middle stages of each transform.  The
+// butterflies, twiddles and merge/split formulas are those of the generic pass.
+// ------------------------------------------------------------------------------------------------
+template <int N>
+struct ZProj8 {
+  static_assert(N == 512, "radices 8 x 8 x 4 of the 256-point row transform");
+  static constexpr int L = N / 2;
+  static constexpr int TABZ = (Plan<L>::kTab + 1) & ~1;
+  static constexpr size_t smem = sizeof(float2) * ((size_t)L + 2 + TABZ + (size_t)kZWarps * L);
+};
+
+// the middle stage (NS = 8, radix 8): butterfly l reads l + 32 r, writes (l / 8) 64 + l mod 8 + 8 r
+template <bool INV>
+__device__ __forceinline__ void zrow_mid(float2* __restrict__ s, const float2* __restrict__ tab, int lane) {
+  using Lay = RowLayout<256>;
+  float2 v[8];
+  const int k = lane & 7;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) v[r] = s[Lay::phys(lane + 32 * r, 0)];
+#pragma unroll
+  for (int r = 1; r < 8; ++r) {
+    float2 w = tab[(r - 1) * 8 + k];
+    if (INV) w.y = -w.y;
+    v[r] = cmul(v[r], w);
+  }
+  Dft<8, INV>::run(v);
+  __syncwarp();
+  const int base = (lane >> 3) * 64 + k;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) s[Lay::phys(base + 8 * r, 0)] = v[r];
+  __syncwarp();
+}
+
+// One 256-point transform: in, z[l + 32 r] (registers, r = 0..7); out, Z[j + 64 r] for the two
+// butterflies j = l (A[r]) and j = l + 32 (B[r]), r = 0..3.
+template <bool INV>
+__device__ __forceinline__ void zrow_fft(float2 (&v)[8], float2 (&A)[4], float2 (&B)[4], float2* __restrict__ s,
+                                         const float2* __restrict__ tab, int lane) {
+  using Lay = RowLayout<256>;
+  Dft<8, INV>::run(v);                                   // stage 1 (NS = 1): butterfly l, no twiddles
+#pragma unroll
+  for (int r = 0; r < 8; ++r) s[Lay::phys(8 * lane + r, 0)] = v[r];
+  __syncwarp();
+  zrow_mid<INV>(s, tab, lane);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {                          // stage 3 (NS = 64, radix 4): butterflies l, l + 32
+    const int j = lane + 32 * h;
+    float2 u[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) u[r] = s[Lay::phys(j + 64 * r, 0)];
+#pragma unroll
+    for (int r = 1; r < 4; ++r) {
+      float2 w = tab[56 + (r - 1) * 64 + j];
+      if (INV) w.y = -w.y;
+      u[r] = cmul(u[r], w);
+    }
+    Dft<4, INV>::run(u);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) (h ? B : A)[r] = u[r];
+  }
+  __syncwarp();                                          // s is reused by the next line
+}
+
+template <int N>
+__global__ void __launch_bounds__(kZThreads, 2) zproj8_kernel(const ZArgs a) {
+  constexpr int L = ZProj8<N>::L;
+  using Lay = RowLayout<L>;
+  extern __shared__ float4 zsm[];
+  float2* tw = reinterpret_cast<float2*>(zsm);                        // exp(-2 pi i m / N), m <= L
+  float2* tab = tw + L + 2;                                           // stage twiddles (256-point plan)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* s = tab + ZProj8<N>::TABZ + warp * L;
+  for (int m = threadIdx.x; m <= L; m += kZThreads) tw[m] = a.tw[m];
+  for (int m = threadIdx.x; m < Plan<L>::kTab; m += kZThreads) tab[m] = a.tab[m];
+  __syncthreads();
+  const bool fin = a.loop_flag && *a.loop_flag == 1;   // converged: write the real Psi and stop
+  const int partner = (32 - lane) & 31;
+  const Geometry& g = a.g;
+
+  for (size_t row = (size_t)blockIdx.x * kZWarps + warp; row < (size_t)N * N; row += (size_t)gridDim.x * kZWarps) {
+    float2 A[3][4], B[3][4];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      // load X[l + 32 r] and merge with its mirror X[L - l - 32 r] (c2r): Z = E + i O conj(w^m)
+      float2 x[8];
+      const float2* src = a.f[q].M + row * L;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) x[r] = src[lane + 32 * r];
+      const float2 xl = a.f[q].Q[row];
+      float2 z[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        float2 xm;
+        xm.x = __shfl_sync(0xffffffffu, x[7 - r].x, partner);
+        xm.y = __shfl_sync(0xffffffffu, x[7 - r].y, partner);
+        if (lane == 0) xm = (r == 0) ? xl : x[(8 - r) & 7];
+        const int m = lane + 32 * r;
+        const float2 w = cconj(tw[m]);
+        const float2 xk = x[r];
+        const float2 ev = make_float2(xk.x + xm.x, xk.y - xm.y);
+        const float2 o = cmul(make_float2(xk.x - xm.x, xk.y + xm.y), w);
+        z[r] = cadd(ev, mul_i(o));
+      }
+      zrow_fft<true>(z, A[q], B[q], s, tab, lane);
+    }
+    if (fin) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        float2* dst = a.f[q].M + row * L;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          dst[lane + 64 * r] = A[q][r];
+          dst[lane + 32 + 64 * r] = B[q][r];
+        }
+      }
+      continue;
+    }
+    // P = coef (Psi . r) r at the real points 2m, 2m + 1 of the complex point m (Eq. Nusser)
+    const int ix = (int)(row / N), iy = (int)(row % N);
+    float dx = 0.f, dy = 0.f;
+    if (g.los_mode != 1) {
+      dx = g.off[ix];
+      dy = g.off[N + iy];
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int m = lane + 32 * h + 64 * r;
+        const float2 p0 = h ? B[0][r] : A[0][r], p1 = h ? B[1][r] : A[1][r], p2 = h ? B[2][r] : A[2][r];
+        float rx0, ry0, rz0, rx1, ry1, rz1;
+        if (g.los_mode == 1) {
+          rx0 = rx1 = g.los.x; ry0 = ry1 = g.los.y; rz0 = rz1 = g.los.z;
+        } else {
+          const float dz0 = g.off[2 * N + 2 * m], dz1 = g.off[2 * N + 2 * m + 1];
+          const float q0 = fmaf(dx, dx, fmaf(dy, dy, dz0 * dz0));
+          const float q1 = fmaf(dx, dx, fmaf(dy, dy, dz1 * dz1));
+          const float i0 = q0 > 0.f ? rsqrtf(q0) : 0.f;
+          const float i1 = q1 > 0.f ? rsqrtf(q1) : 0.f;
+          rx0 = dx * i0; ry0 = dy * i0; rz0 = dz0 * i0;
+          rx1 = dx * i1; ry1 = dy * i1; rz1 = dz1 * i1;
+        }
+        const float u0 = a.coef * fmaf(p0.x, rx0, fmaf(p1.x, ry0, p2.x * rz0));
+        const float u1 = a.coef * fmaf(p0.y, rx1, fmaf(p1.y, ry1, p2.y * rz1));
+        const float2 n0 = make_float2(u0 * rx0, u1 * rx1), n1 = make_float2(u0 * ry0, u1 * ry1),
+                     n2 = make_float2(u0 * rz0, u1 * rz1);
+        if (h) { B[0][r] = n0; B[1][r] = n1; B[2][r] = n2; } else { A[0][r] = n0; A[1][r] = n1; A[2][r] = n2; }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      // the points l + 32 r of the real row: A[r/2] (r even), B[(r-1)/2] (r odd)
+      float2 v[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) v[r] = (r & 1) ? B[q][r >> 1] : A[q][r >> 1];
+      float2 Y0[4], Y1[4];
+      zrow_fft<false>(v, Y0, Y1, s, tab, lane);
+      // r2c split: pairs (k, L - k); Y0[r] = Y[l + 64 r] pairs with lane 32 - l's Y1[3 - r] (l >= 1),
+      // Y1[r] = Y[l + 32 + 64 r] with lane 32 - l's Y0[3 - r]; lane 0 pairs with itself
+      float2* dst = a.f[q].M + row * L;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        float2 pa, pb;
+        pa.x = __shfl_sync(0xffffffffu, Y1[3 - r].x, partner);
+        pa.y = __shfl_sync(0xffffffffu, Y1[3 - r].y, partner);
+        pb.x = __shfl_sync(0xffffffffu, Y0[3 - r].x, partner);
+        pb.y = __shfl_sync(0xffffffffu, Y0[3 - r].y, partner);
+        if (lane == 0) {
+          pa = Y0[(4 - r) & 3];
+          pb = Y1[3 - r];
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int k = lane + 32 * h + 64 * r;
+          const float2 zk = h ? Y1[r] : Y0[r], zm = h ? pb : pa;
+          float2 xk;
+          if (k == 0) {
+            xk = make_float2(zk.x + zk.y, 0.f);
+            a.f[q].Q[row] = make_float2(zk.x - zk.y, 0.f);
+          } else {
+            const float2 ev = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+            const float2 o = make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y + zm.y));
+            xk = cadd(ev, cmul(make_float2(o.y, -o.x), tw[k]));
+          }
+          dst[k] = xk;
+        }
+      }
+    }
+  }
+}
+
 template <int N, int NC>
 constexpr size_t zpass_smem(int mode) {
   return sizeof(float2) * ((size_t)N / 2 + 2 + ((Plan<N / 2>::kTab + 1) & ~1) + N / 2 +
@@ -799,7 +998,32 @@ struct MeshImpl {
     return cudaLaunchKernel(k, dim3(grid), dim3(kZThreads), args, smem, st);
   }
 
+  static cudaError_t zfused(const ZArgs& a, cudaStream_t st, int* grid_out) {
+    if constexpr (N == 512) {
+      static int grid = 0;
+      const void* k = (const void*)zproj8_kernel<N>;
+      const size_t smem = ZProj8<N>::smem;
+      if (grid == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sm = 0, occ = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kZThreads, smem)) != cudaSuccess) return e;
+        if (occ < 1) return cudaErrorInvalidConfiguration;
+        grid = occ * sm < kZBlocks ? occ * sm : kZBlocks;
+      }
+      if (grid_out) *grid_out = grid;
+      void* args[] = {const_cast<ZArgs*>(&a)};
+      return cudaLaunchKernel(k, dim3(grid), dim3(kZThreads), args, smem, st);
+    }
+    return cudaErrorInvalidValue;
+  }
+
   static cudaError_t zpass(int mode, int nc, const ZArgs& a, cudaStream_t st, int* grid_out) {
+    if constexpr (N == 512) {
+      if (mode == Z_PROJ && nc == 3 && !a.generic) return zfused(a, st, grid_out);
+    }
 #define RG_Z(M_, NC_) \
   if (mode == M_ && nc == NC_) return zlaunch<M_, NC_>(a, st, grid_out);
     RG_Z(Z_FWD, 1) RG_Z(Z_INV, 1) RG_Z(Z_DELTA, 2) RG_Z(Z_PROJ, 3) RG_Z(Z_FINAL, 3) RG_Z(Z_USTART, 3)

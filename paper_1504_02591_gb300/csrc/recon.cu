@@ -237,6 +237,7 @@ ZArgs zargs(recon_handle* h) {
   a.mask_frac = h->p.mask_frac;
   a.uniform = h->p.mean_density_mode == RECON_MEAN_UNIFORM;
   a.lognormal = h->p.lognormal;
+  a.generic = h->kspace_generic;
   return a;
 }
 

@@ -65,6 +65,7 @@ struct ZArgs {
   const float* corr;
   const float* ucoarse;
   int clevel;
+  int generic;            // Z_PROJ: the generic staged kernel instead of the register-fused one
 };
 
 struct SArgs {
