@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-warm", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="host-driven iteration (every pass a plain launch; for ncu launch lists)")
     return ap.parse_args()
 
 
@@ -202,6 +204,8 @@ def gpu_arm(args):
     gal = torch.from_numpy(m.galaxies.pos).cuda()
     ran = torch.from_numpy(m.randoms.pos).cuda()
     r = binding.Recon.from_mock(m)
+    if args.host_loop:
+        r.set_option(binding.OPT_GRAPH, 0)
     sg = torch.empty((len(gal), 3), dtype=torch.float32, device="cuda")
     sr = torch.empty((len(ran), 3), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -348,7 +352,8 @@ def gpu_arm(args):
                        "n_gal": len(gal), "n_ran": len(ran), "n_iter": n_iter, "final_rel": rel,
                        "start": "learned warm start (U-Net on the 4x coarsened mesh)" if warm else "Eq. approx2",
                        "l2": "inputs larger than L2 (each field 539 MB), no flush",
-                       "parallelism": "replicas" if ws > 1 else "single"},
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "iteration_loop": "host" if args.host_loop else "cuda graph"},
             "path": "learned warm start" if warm else "Eq. approx2 start",
             "warm_start": warm,
             "plain": plain,

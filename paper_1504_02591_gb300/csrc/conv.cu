@@ -77,18 +77,108 @@ __global__ void __launch_bounds__(256) conv_kernel(const ConvArgs a) {
   }
 }
 
+// Register-blocked form for kernels of at most KT taps: the line is staged with its periodic
+// continuation (s[p] = x[(p + t0) mod n], p < n + KT + V), the taps sit in registers (zero past
+// ntap), and each thread slides over V consecutive outputs of one column, so every staged value is
+// read once per V outputs instead of once per output.
+template <int C, int KT, int V>
+__global__ void __launch_bounds__(256) conv_blocked_kernel(const ConvArgs a) {
+  extern __shared__ float csm[];
+  constexpr int T = 256;
+  const int n = a.n;
+  const int len = n + KT + V;                // staged entries per line
+  float tp[KT];
+#pragma unroll
+  for (int j = 0; j < KT; ++j) tp[j] = j < a.ntap ? a.taps[j] : 0.f;
+  const int zb = n / C;
+  const int t = blockIdx.x;
+  const int other = t / zb;
+  const int z0 = (t % zb) * C;
+  const size_t nn = (size_t)n;
+  size_t base, ls;
+  if (a.axis == 0) {
+    base = (size_t)other * nn + z0;
+    ls = nn * nn;
+  } else {
+    base = (size_t)other * nn * nn + z0;
+    ls = nn;
+  }
+  float cnt = 0.f;
+  for (int q = 0; q < a.nf; ++q) {
+    const float* src = a.f[q];
+    float* sq = csm + (size_t)q * len * C;
+    for (int e = threadIdx.x; e < len * (C / 4); e += T) {
+      const int p = e / (C / 4), c4 = e % (C / 4);
+      int i = (p + a.t0) % n;
+      if (i < 0) i += n;
+      const float4 v = *reinterpret_cast<const float4*>(src + base + (size_t)i * ls + 4 * c4);
+      if (a.count && q == a.nf - 1 && p < n) cnt += (v.x > 0.f) + (v.y > 0.f) + (v.z > 0.f) + (v.w > 0.f);
+      *reinterpret_cast<float4*>(sq + (size_t)p * C + 4 * c4) = v;
+    }
+  }
+  __syncthreads();
+  const int c = threadIdx.x % C;
+  for (int q = 0; q < a.nf; ++q) {
+    const float* sq = csm + (size_t)q * len * C;
+    float* dst = a.f[q];
+    for (int i0 = (threadIdx.x / C) * V; i0 < n; i0 += (T / C) * V) {
+      float acc[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[v] = 0.f;
+#pragma unroll
+      for (int j = 0; j < KT + V - 1; ++j) {
+        const float x = sq[(size_t)(i0 + j) * C + c];
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+          if (j - v >= 0 && j - v < KT) acc[v] = fmaf(tp[j - v], x, acc[v]);
+      }
+#pragma unroll
+      for (int v = 0; v < V; ++v) dst[base + (size_t)(i0 + v) * ls + c] = acc[v];
+    }
+  }
+  if (a.count) {
+    __shared__ double sh[8];
+    double v = cnt;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double r = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sh[w];
+      a.partials[2 * blockIdx.x + 0] = 0.0;
+      a.partials[2 * blockIdx.x + 1] = r;
+    }
+  }
+}
+
+constexpr int kConvV = 8;
+
 int conv_cols(int n) { return n >= 1024 ? 8 : 16; }
 
 int conv_blocks(int n) { return n * (n / conv_cols(n)); }
 
+static int conv_kt(int n, int ntap) {
+  if (n % (256 / conv_cols(n) * kConvV) != 0) return 0;   // every thread's blocks of V outputs fit the line
+  return ntap <= 32 ? 32 : (ntap <= 64 ? 64 : 0);
+}
+
 size_t conv_smem(int n, int nf, int ntap) {
+  const int kt = conv_kt(n, ntap);
+  if (kt) return sizeof(float) * (size_t)nf * (n + kt + kConvV) * conv_cols(n);
   return sizeof(float) * (((size_t)ntap + 3) / 4 * 4 + (size_t)nf * n * conv_cols(n));
 }
 
 cudaError_t launch_conv(const ConvArgs& a, cudaStream_t st) {
   const int C = conv_cols(a.n);
   const size_t smem = conv_smem(a.n, a.nf, a.ntap);
-  const void* k = (C == 16) ? (const void*)conv_kernel<16> : (const void*)conv_kernel<8>;
+  const int kt = conv_kt(a.n, a.ntap);
+  const void* k;
+  if (kt == 32)
+    k = (C == 16) ? (const void*)conv_blocked_kernel<16, 32, kConvV> : (const void*)conv_blocked_kernel<8, 32, kConvV>;
+  else if (kt == 64)
+    k = (C == 16) ? (const void*)conv_blocked_kernel<16, 64, kConvV> : (const void*)conv_blocked_kernel<8, 64, kConvV>;
+  else
+    k = (C == 16) ? (const void*)conv_kernel<16> : (const void*)conv_kernel<8>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   void* args[] = {const_cast<ConvArgs*>(&a)};
