@@ -866,6 +866,85 @@ __device__ __forceinline__ void r512_line(float2 (&v)[8], float2* __restrict__ s
   __syncthreads();                                       // s is reused by the next line
 }
 
+// The plain line transform along x for N = 512, one component per CTA (blockIdx.y): the first
+// radix-8 stage reads its inputs straight from global memory and the last writes its outputs
+// straight back, so shared memory carries only the middle stage (the generic pass also stages the
+// loads and stores).  Tiles of C adjacent columns, 64 butterflies per column and stage, NB per
+// thread.
+template <int C>
+struct XLine8 {
+  static constexpr int T = 512;
+  static constexpr int NB = 64 * C / T;        // butterflies per thread and stage
+  static constexpr int TAB = (Plan<512>::kTab + 1) & ~1;
+  static constexpr size_t smem = sizeof(float2) * ((size_t)TAB + (size_t)512 * C);
+};
+
+template <bool INV, int C>
+__global__ void __launch_bounds__(XLine8<C>::T, 2) xline8_kernel(const SArgs a) {
+  constexpr int N = 512, H = N / 2, T = XLine8<C>::T, NB = XLine8<C>::NB;
+  using Lay = ColLayout<C>;
+  extern __shared__ float4 ssm[];
+  float2* tw = reinterpret_cast<float2*>(ssm);
+  float2* s = tw + XLine8<C>::TAB;
+  if (!INV && a.skip_flag && *a.skip_flag != 0) return;   // uniform: device loop already converged
+  for (int m = threadIdx.x; m < Plan<N>::kTab; m += T) tw[m] = a.tab[m];
+  const Tile t = tile_of<N, C, AX_X>(blockIdx.x);
+  float2* __restrict__ P = t.isQ ? a.f[blockIdx.y].Q : a.f[blockIdx.y].M;
+  const int col = threadIdx.x % C, jb = threadIdx.x / C;
+  float2 v[NB][8];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = jb + b * (T / C);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[b][r] = P[t.base + (size_t)(j + 64 * r) * t.ls + (size_t)col * t.cs];
+  }
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {                          // stage 1 (NS = 1)
+    const int j = jb + b * (T / C);
+    Dft<8, INV>::run(v[b]);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) s[Lay::phys(8 * j + r, col)] = v[b][r];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {                          // stage 2 (NS = 8)
+    const int j = jb + b * (T / C), k = j & 7;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[b][r] = s[Lay::phys(j + 64 * r, col)];
+#pragma unroll
+    for (int r = 1; r < 8; ++r) {
+      float2 w = tw[(r - 1) * 8 + k];
+      if (INV) w.y = -w.y;
+      v[b][r] = cmul(v[b][r], w);
+    }
+    Dft<8, INV>::run(v[b]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = jb + b * (T / C), base = (j >> 3) * 64 + (j & 7);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) s[Lay::phys(base + 8 * r, col)] = v[b][r];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {                          // stage 3 (NS = 64), straight to global
+    const int j = jb + b * (T / C);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[b][r] = s[Lay::phys(j + 64 * r, col)];
+#pragma unroll
+    for (int r = 1; r < 8; ++r) {
+      float2 w = tw[56 + (r - 1) * 64 + j];
+      if (INV) w.y = -w.y;
+      v[b][r] = cmul(v[b][r], w);
+    }
+    Dft<8, INV>::run(v[b]);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) P[t.base + (size_t)(j + 64 * r) * t.ls + (size_t)col * t.cs] = v[b][r];
+  }
+  (void)H;
+}
+
 template <int N, int C>
 __global__ void __launch_bounds__(KIter8<N, C>::T, 2) kiter8_kernel(const SArgs a) {
   constexpr int T = KIter8<N, C>::T;
@@ -1063,11 +1142,31 @@ struct MeshImpl {
     return cudaErrorInvalidValue;
   }
 
+  static cudaError_t xlaunch(bool inv, const SArgs& a, cudaStream_t st, int ncomp) {
+    if constexpr (N == 512) {
+      constexpr int C = SCols<N, S_FWD>::v;   // 16 adjacent columns (128-byte rows)
+      const void* k = inv ? (const void*)xline8_kernel<true, C> : (const void*)xline8_kernel<false, C>;
+      static bool attr[2] = {false, false};
+      if (!attr[inv]) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XLine8<C>::smem);
+        if (e != cudaSuccess) return e;
+        attr[inv] = true;
+      }
+      void* args[] = {const_cast<SArgs*>(&a)};
+      return cudaLaunchKernel(k, dim3(sblocks<S_FWD>(), ncomp), dim3(XLine8<C>::T), args, XLine8<C>::smem, st);
+    }
+    return cudaErrorInvalidValue;
+  }
+
   static cudaError_t spass(int mode, int nc, int axis, const SArgs& a, cudaStream_t st) {
     if (nc < 1 || nc > 3) return cudaErrorInvalidValue;
     // plain passes: one component per CTA, components along gridDim.y
     if (mode == S_FWD && axis == AX_Y) return slaunch<S_FWD, 1, AX_Y>(a, st, nc);
     if (mode == S_INV && axis == AX_Y) return slaunch<S_INV, 1, AX_Y>(a, st, nc);
+    if constexpr (N == 512) {
+      if ((mode == S_FWD || mode == S_INV) && axis == AX_X && !a.narrow && !a.generic)
+        return xlaunch(mode == S_INV, a, st, nc);
+    }
     if (mode == S_FWD && axis == AX_X)
       return a.narrow ? slaunch<S_FWD, 1, AX_X, 1>(a, st, nc) : slaunch<S_FWD, 1, AX_X>(a, st, nc);
     if (mode == S_INV && axis == AX_X)
