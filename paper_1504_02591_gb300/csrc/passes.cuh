@@ -819,51 +819,56 @@ struct KIter8 {
   static_assert(N == 512, "three radix-8 stages");
   static constexpr int T = (N / 8) * C;        // one butterfly of one column per thread and stage
   static constexpr int TAB = (Plan<N>::kTab + 1) & ~1;
-  static constexpr size_t smem = sizeof(float2) * ((size_t)TAB + (size_t)N * C);
+  static constexpr size_t smem = sizeof(float2) * ((size_t)TAB + 3 * (size_t)N * C);   // one buffer per component
 };
 
-// stage 2 (NS = 8): butterfly j reads j + 64 r, twiddles w64^(r (j mod 8)), writes (j / 8) 64 + j mod 8 + 8 r
-template <bool INV, int C>
-__device__ __forceinline__ void r512_mid(float2* __restrict__ s, const float2* __restrict__ tw, int j, int col) {
+// The three components' 512-point transforms of one column, stage by stage together (one buffer
+// each, so a stage needs one barrier for all three): v[q][r] = x_q[j + 64 r] in, X_q[j + 64 r] out.
+template <bool INV, int N, int C>
+__device__ __forceinline__ void r512_lines3(float2 (&v)[3][8], float2* __restrict__ s, const float2* __restrict__ tw,
+                                            int j, int col) {
   using Lay = ColLayout<C>;
-  float2 v[8];
+  constexpr int B = N * C;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {                          // stage 1 (NS = 1): no twiddles
+    Dft<8, INV>::run(v[q]);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) s[q * B + Lay::phys(8 * j + r, col)] = v[q][r];
+  }
+  __syncthreads();
   const int k = j & 7;
 #pragma unroll
-  for (int r = 0; r < 8; ++r) v[r] = s[Lay::phys(j + 64 * r, col)];
+  for (int q = 0; q < 3; ++q) {                          // stage 2 (NS = 8)
 #pragma unroll
-  for (int r = 1; r < 8; ++r) {
-    float2 w = tw[(r - 1) * 8 + k];
-    if (INV) w.y = -w.y;
-    v[r] = cmul(v[r], w);
+    for (int r = 0; r < 8; ++r) v[q][r] = s[q * B + Lay::phys(j + 64 * r, col)];
+#pragma unroll
+    for (int r = 1; r < 8; ++r) {
+      float2 w = tw[(r - 1) * 8 + k];
+      if (INV) w.y = -w.y;
+      v[q][r] = cmul(v[q][r], w);
+    }
+    Dft<8, INV>::run(v[q]);
   }
-  Dft<8, INV>::run(v);
   __syncthreads();
   const int base = (j >> 3) * 64 + k;
 #pragma unroll
-  for (int r = 0; r < 8; ++r) s[Lay::phys(base + 8 * r, col)] = v[r];
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int r = 0; r < 8; ++r) s[q * B + Lay::phys(base + 8 * r, col)] = v[q][r];
   __syncthreads();
-}
-
-// The 512-point transform of one column: v[r] = x[j + 64 r] in, X[j + 64 r] out (registers).
-template <bool INV, int C>
-__device__ __forceinline__ void r512_line(float2 (&v)[8], float2* __restrict__ s, const float2* __restrict__ tw, int j,
-                                          int col) {
-  using Lay = ColLayout<C>;
-  Dft<8, INV>::run(v);                                   // stage 1 (NS = 1): no twiddles
 #pragma unroll
-  for (int r = 0; r < 8; ++r) s[Lay::phys(8 * j + r, col)] = v[r];
-  __syncthreads();
-  r512_mid<INV, C>(s, tw, j, col);
+  for (int q = 0; q < 3; ++q) {                          // stage 3 (NS = 64)
 #pragma unroll
-  for (int r = 0; r < 8; ++r) v[r] = s[Lay::phys(j + 64 * r, col)];
+    for (int r = 0; r < 8; ++r) v[q][r] = s[q * B + Lay::phys(j + 64 * r, col)];
 #pragma unroll
-  for (int r = 1; r < 8; ++r) {                          // stage 3 (NS = 64): twiddles w512^(r j)
-    float2 w = tw[56 + (r - 1) * 64 + j];
-    if (INV) w.y = -w.y;
-    v[r] = cmul(v[r], w);
+    for (int r = 1; r < 8; ++r) {
+      float2 w = tw[56 + (r - 1) * 64 + j];
+      if (INV) w.y = -w.y;
+      v[q][r] = cmul(v[q][r], w);
+    }
+    Dft<8, INV>::run(v[q]);
   }
-  Dft<8, INV>::run(v);
-  __syncthreads();                                       // s is reused by the next line
+  __syncthreads();                                       // the buffers are reused
 }
 
 // The plain line transform along x for N = 512, one component per CTA (blockIdx.y): the first
@@ -972,8 +977,7 @@ __global__ void __launch_bounds__(KIter8<N, C>::T, 2) kiter8_kernel(const SArgs 
     }
   }
   __syncthreads();   // twiddles
-#pragma unroll
-  for (int q = 0; q < 3; ++q) r512_line<false, C>(v[q], s, tw, j, col);
+  r512_lines3<false, N, C>(v, s, tw, j, col);
 
   // S_n = delta/b + beta i k . P_n, the Parseval norms, Psi_n+1 = i kd S_n / k^2 (Eq. iterative)
   float d2 = 0.f, s2 = 0.f;
@@ -1009,9 +1013,9 @@ __global__ void __launch_bounds__(KIter8<N, C>::T, 2) kiter8_kernel(const SArgs 
     v[2][r] = cscale(iS, kdz);
   }
 
+  r512_lines3<true, N, C>(v, s, tw, j, col);
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    r512_line<true, C>(v[q], s, tw, j, col);
     float2* __restrict__ dst = t.isQ ? a.f[q].Q : a.f[q].M;
 #pragma unroll
     for (int r = 0; r < 8; ++r) dst[t.base + (size_t)(j + 64 * r) * t.ls + (size_t)col * t.cs] = v[q][r];
