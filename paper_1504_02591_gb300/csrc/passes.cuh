@@ -379,7 +379,8 @@ struct ZProj8 {
   static_assert(N == 512, "radices 8 x 8 x 4 of the 256-point row transform");
   static constexpr int L = N / 2;
   static constexpr int TABZ = (Plan<L>::kTab + 1) & ~1;
-  static constexpr size_t smem = sizeof(float2) * ((size_t)L + 2 + TABZ + (size_t)kZWarps * L);
+  static constexpr int kWarp = L + L / 2;      // FFT buffer + the coarse correction row (Z_WARM)
+  static constexpr size_t smem = sizeof(float2) * ((size_t)L + 2 + TABZ + (size_t)kZWarps * kWarp);
 };
 
 // the middle stage (NS = 8, radix 8): butterfly l reads l + 32 r, writes (l / 8) 64 + l mod 8 + 8 r
@@ -434,91 +435,195 @@ __device__ __forceinline__ void zrow_fft(float2 (&v)[8], float2 (&A)[4], float2 
   __syncwarp();                                          // s is reused by the next line
 }
 
-template <int N>
-__global__ void __launch_bounds__(kZThreads, 2) zproj8_kernel(const ZArgs a) {
+// c2r of one component's row (loaded by zrow_load: X[l + 32 r] and the Nyquist value): merge with
+// the mirror X[L - l - 32 r] (on lane 32 - l; lane 0 with itself and the Nyquist value), inverse
+// transform; out A[r] = x[l + 64 r], B[r] = x[l + 32 + 64 r] (complex points = real pairs 2m, 2m + 1).
+__device__ __forceinline__ void zrow_load(const Field& f, size_t row, int lane, float2 (&x)[8], float2& xl) {
+  const float2* src = f.M + row * 256;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) x[r] = src[lane + 32 * r];
+  xl = f.Q[row];
+}
+
+__device__ __forceinline__ void zrow_c2r(const float2 (&x)[8], float2 xl, int lane, int partner,
+                                         const float2* __restrict__ tw, float2* __restrict__ s,
+                                         const float2* __restrict__ tab, float2 (&A)[4], float2 (&B)[4]) {
+  float2 z[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    float2 xm;
+    xm.x = __shfl_sync(0xffffffffu, x[7 - r].x, partner);
+    xm.y = __shfl_sync(0xffffffffu, x[7 - r].y, partner);
+    if (lane == 0) xm = (r == 0) ? xl : x[(8 - r) & 7];
+    const float2 w = cconj(tw[lane + 32 * r]);
+    const float2 xk = x[r];
+    const float2 ev = make_float2(xk.x + xm.x, xk.y - xm.y);
+    const float2 o = cmul(make_float2(xk.x - xm.x, xk.y + xm.y), w);
+    z[r] = cadd(ev, mul_i(o));
+  }
+  zrow_fft<true>(z, A, B, s, tab, lane);
+}
+
+// r2c of one component's row from the real points v[r] = (x[2m], x[2m + 1]), m = l + 32 r: forward
+// transform, split (pairs k, L - k on lanes l and 32 - l), store the half-complex row and Nyquist value.
+__device__ __forceinline__ void zrow_r2c(float2 (&v)[8], const Field& f, size_t row, int lane, int partner,
+                                         const float2* __restrict__ tw, float2* __restrict__ s,
+                                         const float2* __restrict__ tab) {
+  constexpr int L = 256;
+  float2 Y0[4], Y1[4];
+  zrow_fft<false>(v, Y0, Y1, s, tab, lane);
+  float2* dst = f.M + row * L;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    float2 pa, pb;
+    pa.x = __shfl_sync(0xffffffffu, Y1[3 - r].x, partner);
+    pa.y = __shfl_sync(0xffffffffu, Y1[3 - r].y, partner);
+    pb.x = __shfl_sync(0xffffffffu, Y0[3 - r].x, partner);
+    pb.y = __shfl_sync(0xffffffffu, Y0[3 - r].y, partner);
+    if (lane == 0) {
+      pa = Y0[(4 - r) & 3];
+      pb = Y1[3 - r];
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = lane + 32 * h + 64 * r;
+      const float2 zk = h ? Y1[r] : Y0[r], zm = h ? pb : pa;
+      float2 xk;
+      if (k == 0) {
+        xk = make_float2(zk.x + zk.y, 0.f);
+        f.Q[row] = make_float2(zk.x - zk.y, 0.f);
+      } else {
+        const float2 ev = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+        const float2 o = make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y + zm.y));
+        xk = cadd(ev, cmul(make_float2(o.y, -o.x), tw[k]));
+      }
+      dst[k] = xk;
+    }
+  }
+}
+
+// line of sight at the real points 2m and 2m + 1 of row (dx, dy)
+__device__ __forceinline__ void zrow_rhat(const Geometry& g, float dx, float dy, int m, float (&r0)[3], float (&r1)[3]) {
+  if (g.los_mode == 1) {
+    r0[0] = r1[0] = g.los.x; r0[1] = r1[1] = g.los.y; r0[2] = r1[2] = g.los.z;
+    return;
+  }
+  const int n = g.n;
+  const float dz0 = g.off[2 * n + 2 * m], dz1 = g.off[2 * n + 2 * m + 1];
+  const float q0 = fmaf(dx, dx, fmaf(dy, dy, dz0 * dz0));
+  const float q1 = fmaf(dx, dx, fmaf(dy, dy, dz1 * dz1));
+  const float i0 = q0 > 0.f ? rsqrtf(q0) : 0.f;
+  const float i1 = q1 > 0.f ? rsqrtf(q1) : 0.f;
+  r0[0] = dx * i0; r0[1] = dy * i0; r0[2] = dz0 * i0;
+  r1[0] = dx * i1; r1[1] = dy * i1; r1[2] = dz1 * i1;
+}
+
+// Z_PROJ (c2r x3, P = coef (Psi.r) r, r2c x3; or, once the device loop has converged, c2r x3 and
+// the real Psi), Z_RADIAL (c2r x3, u = coef Psi.r as a real row) and Z_WARM (u from the real row
+// plus the upsampled coarse correction, P = u r, r2c x3), one warp per row.
+template <int N, int MODE>
+__global__ void __launch_bounds__(kZThreads, 2) zfused8_kernel(const ZArgs a) {
   constexpr int L = ZProj8<N>::L;
-  using Lay = RowLayout<L>;
   extern __shared__ float4 zsm[];
   float2* tw = reinterpret_cast<float2*>(zsm);                        // exp(-2 pi i m / N), m <= L
   float2* tab = tw + L + 2;                                           // stage twiddles (256-point plan)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* s = tab + ZProj8<N>::TABZ + warp * L;
+  float2* s = tab + ZProj8<N>::TABZ + warp * ZProj8<N>::kWarp;
+  float* crow = reinterpret_cast<float*>(s + L);                      // Z_WARM: this row's coarse correction
   for (int m = threadIdx.x; m <= L; m += kZThreads) tw[m] = a.tw[m];
   for (int m = threadIdx.x; m < Plan<L>::kTab; m += kZThreads) tab[m] = a.tab[m];
   __syncthreads();
-  const bool fin = a.loop_flag && *a.loop_flag == 1;   // converged: write the real Psi and stop
+  const bool fin = (MODE == Z_PROJ) && a.loop_flag && *a.loop_flag == 1;
   const int partner = (32 - lane) & 31;
   const Geometry& g = a.g;
 
   for (size_t row = (size_t)blockIdx.x * kZWarps + warp; row < (size_t)N * N; row += (size_t)gridDim.x * kZWarps) {
+    const int ix = (int)(row / N), iy = (int)(row % N);
+    const float dx = g.los_mode == 1 ? 0.f : g.off[ix], dy = g.los_mode == 1 ? 0.f : g.off[N + iy];
     float2 A[3][4], B[3][4];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      // load X[l + 32 r] and merge with its mirror X[L - l - 32 r] (c2r): Z = E + i O conj(w^m)
-      float2 x[8];
-      const float2* src = a.f[q].M + row * L;
-#pragma unroll
-      for (int r = 0; r < 8; ++r) x[r] = src[lane + 32 * r];
-      const float2 xl = a.f[q].Q[row];
-      float2 z[8];
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        float2 xm;
-        xm.x = __shfl_sync(0xffffffffu, x[7 - r].x, partner);
-        xm.y = __shfl_sync(0xffffffffu, x[7 - r].y, partner);
-        if (lane == 0) xm = (r == 0) ? xl : x[(8 - r) & 7];
-        const int m = lane + 32 * r;
-        const float2 w = cconj(tw[m]);
-        const float2 xk = x[r];
-        const float2 ev = make_float2(xk.x + xm.x, xk.y - xm.y);
-        const float2 o = cmul(make_float2(xk.x - xm.x, xk.y + xm.y), w);
-        z[r] = cadd(ev, mul_i(o));
+    if (MODE == Z_WARM) {
+      // u = u_s + U[corr - ucoarse] (see the generic pass), then P_j = u r_j in A/B order
+      const int fl = a.clevel, nc = N >> fl;
+      const float inv_f = 1.f / (float)(1 << fl);
+      const float tx = ((float)ix + 0.5f) * inv_f - 0.5f, ty = ((float)iy + 0.5f) * inv_f - 0.5f;
+      const float fx = floorf(tx), fy = floorf(ty);
+      const float wx = tx - fx, wy = ty - fy;
+      int x0 = (int)fx, y0 = (int)fy;
+      x0 = x0 < 0 ? x0 + nc : x0;
+      y0 = y0 < 0 ? y0 + nc : y0;
+      const int x1 = x0 + 1 == nc ? 0 : x0 + 1, y1 = y0 + 1 == nc ? 0 : y0 + 1;
+      const size_t r00 = ((size_t)x0 * nc + y0) * nc, r01 = ((size_t)x0 * nc + y1) * nc;
+      const size_t r10 = ((size_t)x1 * nc + y0) * nc, r11 = ((size_t)x1 * nc + y1) * nc;
+      for (int jz = lane; jz < nc; jz += 32) {
+        const float c00 = a.corr[r00 + jz] - a.ucoarse[r00 + jz], c01 = a.corr[r01 + jz] - a.ucoarse[r01 + jz];
+        const float c10 = a.corr[r10 + jz] - a.ucoarse[r10 + jz], c11 = a.corr[r11 + jz] - a.ucoarse[r11 + jz];
+        crow[jz] = (1.f - wx) * ((1.f - wy) * c00 + wy * c01) + wx * ((1.f - wy) * c10 + wy * c11);
       }
-      zrow_fft<true>(z, A[q], B[q], s, tab, lane);
-    }
-    if (fin) {
+      __syncwarp();
+      const float2* ur = reinterpret_cast<const float2*>(a.u_in + row * N);
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        float2* dst = a.f[q].M + row * L;
+      for (int h = 0; h < 2; ++h)
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          dst[lane + 64 * r] = A[q][r];
-          dst[lane + 32 + 64 * r] = B[q][r];
-        }
-      }
-      continue;
-    }
-    // P = coef (Psi . r) r at the real points 2m, 2m + 1 of the complex point m (Eq. Nusser)
-    const int ix = (int)(row / N), iy = (int)(row % N);
-    float dx = 0.f, dy = 0.f;
-    if (g.los_mode != 1) {
-      dx = g.off[ix];
-      dy = g.off[N + iy];
-    }
+          const int m = lane + 32 * h + 64 * r;
+          float2 uu = ur[m];
+          float add[2];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+          for (int h2 = 0; h2 < 2; ++h2) {
+            const float tz = ((float)(2 * m + h2) + 0.5f) * inv_f - 0.5f;
+            const float fz = floorf(tz);
+            const float wz = tz - fz;
+            int z0 = (int)fz;
+            z0 = z0 < 0 ? z0 + nc : z0;
+            const int z1 = z0 + 1 == nc ? 0 : z0 + 1;
+            add[h2] = (1.f - wz) * crow[z0] + wz * crow[z1];
+          }
+          uu.x += add[0];
+          uu.y += add[1];
+          float r0[3], r1[3];
+          zrow_rhat(g, dx, dy, m, r0, r1);
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int m = lane + 32 * h + 64 * r;
-        const float2 p0 = h ? B[0][r] : A[0][r], p1 = h ? B[1][r] : A[1][r], p2 = h ? B[2][r] : A[2][r];
-        float rx0, ry0, rz0, rx1, ry1, rz1;
-        if (g.los_mode == 1) {
-          rx0 = rx1 = g.los.x; ry0 = ry1 = g.los.y; rz0 = rz1 = g.los.z;
-        } else {
-          const float dz0 = g.off[2 * N + 2 * m], dz1 = g.off[2 * N + 2 * m + 1];
-          const float q0 = fmaf(dx, dx, fmaf(dy, dy, dz0 * dz0));
-          const float q1 = fmaf(dx, dx, fmaf(dy, dy, dz1 * dz1));
-          const float i0 = q0 > 0.f ? rsqrtf(q0) : 0.f;
-          const float i1 = q1 > 0.f ? rsqrtf(q1) : 0.f;
-          rx0 = dx * i0; ry0 = dy * i0; rz0 = dz0 * i0;
-          rx1 = dx * i1; ry1 = dy * i1; rz1 = dz1 * i1;
+          for (int q = 0; q < 3; ++q) (h ? B : A)[q][r] = make_float2(uu.x * r0[q], uu.y * r1[q]);
         }
-        const float u0 = a.coef * fmaf(p0.x, rx0, fmaf(p1.x, ry0, p2.x * rz0));
-        const float u1 = a.coef * fmaf(p0.y, rx1, fmaf(p1.y, ry1, p2.y * rz1));
-        const float2 n0 = make_float2(u0 * rx0, u1 * rx1), n1 = make_float2(u0 * ry0, u1 * ry1),
-                     n2 = make_float2(u0 * rz0, u1 * rz1);
-        if (h) { B[0][r] = n0; B[1][r] = n1; B[2][r] = n2; } else { A[0][r] = n0; A[1][r] = n1; A[2][r] = n2; }
+      __syncwarp();   // crow is rewritten by the next row
+    } else {
+      // all three rows' loads in flight before the first transform
+      float2 x[3][8], xl[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) zrow_load(a.f[q], row, lane, x[q], xl[q]);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) zrow_c2r(x[q], xl[q], lane, partner, tw, s, tab, A[q], B[q]);
+      if (MODE == Z_PROJ && fin) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          float2* dst = a.f[q].M + row * L;
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            dst[lane + 64 * r] = A[q][r];
+            dst[lane + 32 + 64 * r] = B[q][r];
+          }
+        }
+        continue;
       }
+      // u = coef (Psi . r) at the real points 2m, 2m + 1 of the complex point m (Eq. Nusser)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int m = lane + 32 * h + 64 * r;
+          float r0[3], r1[3];
+          zrow_rhat(g, dx, dy, m, r0, r1);
+          const float2 p0 = h ? B[0][r] : A[0][r], p1 = h ? B[1][r] : A[1][r], p2 = h ? B[2][r] : A[2][r];
+          const float u0 = a.coef * fmaf(p0.x, r0[0], fmaf(p1.x, r0[1], p2.x * r0[2]));
+          const float u1 = a.coef * fmaf(p0.y, r1[0], fmaf(p1.y, r1[1], p2.y * r1[2]));
+          if (MODE == Z_RADIAL) {
+            reinterpret_cast<float2*>(a.u_out + row * N)[m] = make_float2(u0, u1);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) (h ? B : A)[q][r] = make_float2(u0 * r0[q], u1 * r1[q]);
+          }
+        }
+      if (MODE == Z_RADIAL) continue;
     }
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -526,38 +631,7 @@ __global__ void __launch_bounds__(kZThreads, 2) zproj8_kernel(const ZArgs a) {
       float2 v[8];
 #pragma unroll
       for (int r = 0; r < 8; ++r) v[r] = (r & 1) ? B[q][r >> 1] : A[q][r >> 1];
-      float2 Y0[4], Y1[4];
-      zrow_fft<false>(v, Y0, Y1, s, tab, lane);
-      // r2c split: pairs (k, L - k); Y0[r] = Y[l + 64 r] pairs with lane 32 - l's Y1[3 - r] (l >= 1),
-      // Y1[r] = Y[l + 32 + 64 r] with lane 32 - l's Y0[3 - r]; lane 0 pairs with itself
-      float2* dst = a.f[q].M + row * L;
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        float2 pa, pb;
-        pa.x = __shfl_sync(0xffffffffu, Y1[3 - r].x, partner);
-        pa.y = __shfl_sync(0xffffffffu, Y1[3 - r].y, partner);
-        pb.x = __shfl_sync(0xffffffffu, Y0[3 - r].x, partner);
-        pb.y = __shfl_sync(0xffffffffu, Y0[3 - r].y, partner);
-        if (lane == 0) {
-          pa = Y0[(4 - r) & 3];
-          pb = Y1[3 - r];
-        }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int k = lane + 32 * h + 64 * r;
-          const float2 zk = h ? Y1[r] : Y0[r], zm = h ? pb : pa;
-          float2 xk;
-          if (k == 0) {
-            xk = make_float2(zk.x + zk.y, 0.f);
-            a.f[q].Q[row] = make_float2(zk.x - zk.y, 0.f);
-          } else {
-            const float2 ev = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-            const float2 o = make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y + zm.y));
-            xk = cadd(ev, cmul(make_float2(o.y, -o.x), tw[k]));
-          }
-          dst[k] = xk;
-        }
-      }
+      zrow_r2c(v, a.f[q], row, lane, partner, tw, s, tab);
     }
   }
 }
@@ -1081,10 +1155,11 @@ struct MeshImpl {
     return cudaLaunchKernel(k, dim3(grid), dim3(kZThreads), args, smem, st);
   }
 
+  template <int M_>
   static cudaError_t zfused(const ZArgs& a, cudaStream_t st, int* grid_out) {
     if constexpr (N == 512) {
       static int grid = 0;
-      const void* k = (const void*)zproj8_kernel<N>;
+      const void* k = (const void*)zfused8_kernel<N, M_>;
       const size_t smem = ZProj8<N>::smem;
       if (grid == 0) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1105,7 +1180,11 @@ struct MeshImpl {
 
   static cudaError_t zpass(int mode, int nc, const ZArgs& a, cudaStream_t st, int* grid_out) {
     if constexpr (N == 512) {
-      if (mode == Z_PROJ && nc == 3 && !a.generic) return zfused(a, st, grid_out);
+      if (nc == 3 && !a.generic) {
+        if (mode == Z_PROJ) return zfused<Z_PROJ>(a, st, grid_out);
+        if (mode == Z_RADIAL) return zfused<Z_RADIAL>(a, st, grid_out);
+        if (mode == Z_WARM && a.clevel >= 1) return zfused<Z_WARM>(a, st, grid_out);
+      }
     }
 #define RG_Z(M_, NC_) \
   if (mode == M_ && nc == NC_) return zlaunch<M_, NC_>(a, st, grid_out);
