@@ -136,13 +136,21 @@ __global__ void __launch_bounds__(256) shift_kernel(const PT* __restrict__ pos, 
 }
 
 // Sum nq interleaved partial columns: red[dst + q] (=|+=) sum_b partials[b * nq + q].
-__global__ void __launch_bounds__(256) finalize_kernel(const double* __restrict__ partials, int nblocks, int nq,
-                                                       double* __restrict__ red, int dst, int accumulate) {
+// One block sums the per-block partials (nq <= 4 quantities, interleaved), all quantities in one
+// sweep with independent loads in flight; the order of the sums is fixed.
+constexpr int kFinalizeThreads = 1024;
+__global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(const double* __restrict__ partials, int nblocks,
+                                                                    int nq, double* __restrict__ red, int dst,
+                                                                    int accumulate) {
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+  for (int b = threadIdx.x; b < nblocks; b += kFinalizeThreads)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (q < nq) s[q] += partials[(size_t)b * nq + q];
   for (int q = 0; q < nq; ++q) {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partials[(size_t)b * nq + q];
-    s = block_sum_d(s);
-    if (threadIdx.x == 0) red[dst + q] = accumulate ? red[dst + q] + s : s;
+    const double t = block_sum_d(s[q]);
+    if (threadIdx.x == 0) red[dst + q] = accumulate ? red[dst + q] + t : t;
   }
 }
 
@@ -175,7 +183,8 @@ cudaError_t launch_shift(const void* pos, int dtype, long long np, const ShiftAr
 
 cudaError_t launch_finalize(const double* partials, int nblocks, int nq, double* red, int dst, int accumulate,
                             cudaStream_t st) {
-  finalize_kernel<<<1, 256, 0, st>>>(partials, nblocks, nq, red, dst, accumulate);
+  if (nq < 1 || nq > 4) return cudaErrorInvalidValue;
+  finalize_kernel<<<1, kFinalizeThreads, 0, st>>>(partials, nblocks, nq, red, dst, accumulate);
   return cudaGetLastError();
 }
 

@@ -892,6 +892,7 @@ template <int N, int C>
 struct KIter8 {
   static_assert(N == 512, "three radix-8 stages");
   static constexpr int T = (N / 8) * C;        // one butterfly of one column per thread and stage
+  static constexpr int kMinBlocks = T <= 256 ? 2 : 1;
   static constexpr int TAB = (Plan<N>::kTab + 1) & ~1;
   static constexpr size_t smem = sizeof(float2) * ((size_t)TAB + 3 * (size_t)N * C);   // one buffer per component
 };
@@ -1025,7 +1026,7 @@ __global__ void __launch_bounds__(XLine8<C>::T, 2) xline8_kernel(const SArgs a) 
 }
 
 template <int N, int C>
-__global__ void __launch_bounds__(KIter8<N, C>::T, 2) kiter8_kernel(const SArgs a) {
+__global__ void __launch_bounds__(KIter8<N, C>::T, KIter8<N, C>::kMinBlocks) kiter8_kernel(const SArgs a) {
   constexpr int T = KIter8<N, C>::T;
   constexpr int H = N / 2;
   extern __shared__ float4 ssm[];
