@@ -636,6 +636,115 @@ __global__ void __launch_bounds__(kZThreads, 2) zfused8_kernel(const ZArgs a) {
   }
 }
 
+// Z_DELTA for N = 512 (at most 32 smoothing taps): each warp stages its row of rho_g (and rho_r)
+// with the periodic continuation the z convolution reads, each lane convolves 16 consecutive nodes
+// with the taps in registers (every staged value read once per 16 outputs; the row is stored with
+// one pad word per 16 so the lanes' windows fall in distinct banks), forms delta (mask, lognormal)
+// exactly as the generic pass, stores the real copy, and runs the r2c of the fused passes.
+template <int N>
+struct ZDelta8 {
+  static_assert(N == 512, "rows of 256 complex points");
+  static constexpr int L = N / 2, KT = 32, V = 16;
+  static constexpr int kExt = N + KT + V;                       // staged entries per row
+  static constexpr int kExtPad = kExt + kExt / 16 + 1;          // with one pad word per 16
+  static constexpr int TABZ = (Plan<L>::kTab + 1) & ~1;
+  static constexpr int kWarp = L + kExtPad;                      // float2: FFT buffer + two staged rows
+  static constexpr size_t smem = sizeof(float2) * ((size_t)L + 2 + TABZ + (size_t)kZWarps * kWarp);
+  __device__ __forceinline__ static int pad(int p) { return p + (p >> 4); }
+};
+
+template <int N>
+__global__ void __launch_bounds__(kZThreads, 2) zdelta8_kernel(const ZArgs a) {
+  using Z = ZDelta8<N>;
+  constexpr int L = Z::L, KT = Z::KT, V = Z::V;
+  using Lay = RowLayout<L>;
+  extern __shared__ float4 zsm[];
+  float2* tw = reinterpret_cast<float2*>(zsm);
+  float2* tab = tw + L + 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* s = tab + Z::TABZ + warp * Z::kWarp;
+  float* xg = reinterpret_cast<float*>(s + L);                   // staged rho_g row, then rho_r row
+  float* xr = xg + Z::kExtPad;
+  __shared__ double red_sh[kZWarps];
+  for (int m = threadIdx.x; m <= L; m += kZThreads) tw[m] = a.tw[m];
+  for (int m = threadIdx.x; m < Plan<L>::kTab; m += kZThreads) tab[m] = a.tab[m];
+  __syncthreads();
+  float tp[KT];
+#pragma unroll
+  for (int jt = 0; jt < KT; ++jt) tp[jt] = jt < a.ntap ? a.taps[jt] : 0.f;
+  const double* red = a.red;
+  const int nin = a.uniform ? 1 : 2;
+  const float inv_alpha = a.uniform ? (float)((double)N * N * N / red[RED_SUM_WG]) : (float)(red[RED_SUM_WR] / red[RED_SUM_WG]);
+  const float thr = a.uniform ? 0.f : (float)(a.mask_frac * red[RED_SUM_WR] / red[RED_CNT_RPOS]);
+  const int partner = (32 - lane) & 31;
+  float acc0 = 0.f, acc1 = 0.f;
+
+  for (size_t row = (size_t)blockIdx.x * kZWarps + warp; row < (size_t)N * N; row += (size_t)gridDim.x * kZWarps) {
+    const float* rg = reinterpret_cast<const float*>(a.f[0].M) + row * N;
+    const float* rr = reinterpret_cast<const float*>(a.f[1].M) + row * N;
+    for (int p = lane; p < Z::kExt; p += 32) {
+      int i = (p + a.t0) % N;
+      if (i < 0) i += N;
+      xg[Z::pad(p)] = rg[i];
+      if (nin == 2) xr[Z::pad(p)] = rr[i];
+    }
+    __syncwarp();
+    const int z0 = V * lane;
+    float ag[V], ar[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) ag[v] = ar[v] = 0.f;
+#pragma unroll
+    for (int w = 0; w < KT + V - 1; ++w) {
+      const float g = xg[Z::pad(z0 + w)];
+      const float r = nin == 2 ? xr[Z::pad(z0 + w)] : 0.f;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int jt = w - v;
+        if (jt >= 0 && jt < KT) {
+          ag[v] = fmaf(tp[jt], g, ag[v]);
+          if (nin == 2) ar[v] = fmaf(tp[jt], r, ar[v]);
+        }
+      }
+    }
+    float d[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      float dv;
+      if (nin == 1) {
+        dv = ag[v] * inv_alpha - 1.f;
+      } else {
+        const bool in = ar[v] > thr;
+        dv = in ? ag[v] * inv_alpha / ar[v] - 1.f : 0.f;
+        acc1 += in ? 1.f : 0.f;
+      }
+      if (a.lognormal) {
+        dv = logf(fmaxf(1.f + dv, 1e-6f));
+        acc0 += dv;
+      }
+      d[v] = dv;
+    }
+    if (a.delta_real) {
+      float4* dr = reinterpret_cast<float4*>(a.delta_real + row * N + z0);
+#pragma unroll
+      for (int v4 = 0; v4 < V / 4; ++v4) dr[v4] = make_float4(d[4 * v4], d[4 * v4 + 1], d[4 * v4 + 2], d[4 * v4 + 3]);
+    }
+#pragma unroll
+    for (int i = 0; i < V / 2; ++i) s[Lay::phys(z0 / 2 + i, 0)] = make_float2(d[2 * i], d[2 * i + 1]);
+    __syncwarp();
+    float2 v8[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v8[r] = s[Lay::phys(lane + 32 * r, 0)];
+    __syncwarp();
+    zrow_r2c(v8, a.dout, row, lane, partner, tw, s, tab);
+  }
+  const double r0 = block_sum((double)acc0, red_sh);
+  const double r1 = block_sum((double)acc1, red_sh);
+  if (threadIdx.x == 0) {
+    a.partials[2 * blockIdx.x + 0] = r0;
+    a.partials[2 * blockIdx.x + 1] = r1;
+  }
+}
+
 template <int N, int NC>
 constexpr size_t zpass_smem(int mode) {
   return sizeof(float2) * ((size_t)N / 2 + 2 + ((Plan<N / 2>::kTab + 1) & ~1) + N / 2 +
@@ -1179,8 +1288,31 @@ struct MeshImpl {
     return cudaErrorInvalidValue;
   }
 
+  static cudaError_t zdelta_fused(const ZArgs& a, cudaStream_t st, int* grid_out) {
+    if constexpr (N == 512) {
+      static int grid = 0;
+      const void* k = (const void*)zdelta8_kernel<N>;
+      const size_t smem = ZDelta8<N>::smem;
+      if (grid == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sm = 0, occ = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kZThreads, smem)) != cudaSuccess) return e;
+        if (occ < 1) return cudaErrorInvalidConfiguration;
+        grid = occ * sm < kZBlocks ? occ * sm : kZBlocks;
+      }
+      if (grid_out) *grid_out = grid;
+      void* args[] = {const_cast<ZArgs*>(&a)};
+      return cudaLaunchKernel(k, dim3(grid), dim3(kZThreads), args, smem, st);
+    }
+    return cudaErrorInvalidValue;
+  }
+
   static cudaError_t zpass(int mode, int nc, const ZArgs& a, cudaStream_t st, int* grid_out) {
     if constexpr (N == 512) {
+      if (mode == Z_DELTA && nc == 2 && !a.generic && a.ntap <= ZDelta8<N>::KT) return zdelta_fused(a, st, grid_out);
       if (nc == 3 && !a.generic) {
         if (mode == Z_PROJ) return zfused<Z_PROJ>(a, st, grid_out);
         if (mode == Z_RADIAL) return zfused<Z_RADIAL>(a, st, grid_out);

@@ -69,3 +69,34 @@ def test_fused_warm_start_passes_512(lib):
     d = float(np.sqrt(((out[0].astype(np.float64) - out[1]) ** 2).sum() / (out[1].astype(np.float64) ** 2).sum()))
     # the two deposits differ in the order of their float32 atomic sums (about 1e-7)
     assert d < 1e-6, d
+
+
+@pytest.mark.parametrize("uniform", [False, True])
+def test_fused_delta_pass_512(lib, uniform):
+    """The z convolution, delta and its r2c at N = 512 (fused pass) against the generic pass: the real
+    delta and delta(k) agree up to the order of the deposit's float32 atomic sums."""
+    from paper_1504_02591_gb300 import binding as B
+    from paper_1504_02591_gb300 import mocks
+    if uniform:
+        m = mocks.periodic_box(3500.0, 512, 100_000, 0, 1.85, 0.74, 15.0, (0.0, 1750.0, 1750.0), 4, 5, 6, ng=128,
+                               uniform=True)
+    else:
+        m = mocks.survey_shell_512(n_gal=100_000, ran_ratio=20)
+    gal = torch.from_numpy(m.galaxies.pos).cuda()
+    ran = None if uniform else torch.from_numpy(m.randoms.pos).cuda()
+    r = B.Recon.from_mock(m, uniform=uniform)
+    out = {}
+    for generic in (1, 0):
+        r.set_option(B.OPT_KSPACE_GENERIC, generic)
+        r.deposit(gal, None, ran, None)
+        r.smooth()
+        d_real = r.get_field(B.FIELD_DELTA).cpu().numpy()
+        r.iterate(B.START_FFTA, 0.0, 1)          # delta(k) is exported once the y transform has run
+        out[generic] = (d_real, r.get_field(B.FIELD_DELTA_K).cpu().numpy())
+    r.close()
+    for i in range(2):
+        dt = np.complex128 if np.iscomplexobj(out[0][i]) else np.float64
+        a, b = out[0][i].astype(dt), out[1][i].astype(dt)
+        d = float(np.sqrt((np.abs(a - b) ** 2).sum() / (np.abs(b) ** 2).sum()))
+        print(f"fused delta pass ({'uniform' if uniform else 'survey'}), {'delta(k)' if i else 'delta'}: rel L2 {d:.2e}")
+        assert d < 1e-5, d
