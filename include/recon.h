@@ -92,7 +92,10 @@ typedef struct recon_catalog {
   const float* w;          /* (n) weights or NULL for unit weights                              */
   int64_t n;               /* number of particles, 0 allowed                                    */
   int dtype;               /* RECON_F64 or RECON_F32 (positions)                                */
-  int on_device;           /* 1: pos and w are device pointers; 0: host pointers                */
+  int on_device;           /* 1: pos and w are device pointers; 0: host pointers (page-locked
+                              host memory is read by the direct deposit kernel in place, other
+                              host memory goes through the handle's staging buffer in chunks;
+                              a call given host memory returns once it has been read)           */
 } recon_catalog;
 
 typedef struct recon_handle recon_handle;

@@ -321,8 +321,30 @@ recon_status check_catalog(const recon_catalog* c) {
 // Deposit one catalogue into rho; the weight sum goes to red[slot].  Particles go through in chunks
 // (staged through the host buffer when the catalogue is in host memory), either directly (global
 // atomics per particle) or brick-sorted into the shared-memory binned deposit.
+// The device-side address of page-locked host memory (null for other host memory).
+const void* mapped_host(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 recon_status deposit_one(recon_handle* h, const recon_catalog* c, float* rho, int slot) {
   const size_t es = elem_size(c->dtype);
+  if (!c->on_device && c->n > 0 && h->deposit_path == RECON_PATH_DIRECT) {
+    // page-locked host catalogue: the direct deposit reads it where it is, in one launch
+    const void* dpos = mapped_host(c->pos);
+    const float* dw = c->w ? static_cast<const float*>(mapped_host(c->w)) : nullptr;
+    if (dpos && (!c->w || dw)) {
+      RG_CUDA(timed(h, RECON_K_DEPOSIT, (double)c->n * (3 * es + (c->w ? 4 : 0)), [&] {
+        return launch_deposit(dpos, c->dtype, dw, c->n, h->n, h->L, rho, h->partials, kDepositBlocks, h->st); }));
+      RG_TRY(finalize(h, kDepositBlocks, 1, slot, 0));
+      return RECON_OK;
+    }
+  }
   const long long chunk = c->on_device ? h->bb.chunk : (kStageParticles < h->bb.chunk ? kStageParticles : h->bb.chunk);
   char* spos = h->stage;
   float* sw = reinterpret_cast<float*>(h->stage + kStageParticles * 24);
@@ -624,6 +646,8 @@ recon_status recon_deposit(recon_handle* h, const recon_catalog* gal, const reco
     RG_CUDA(cudaMemsetAsync(h->V[1].M, 0, bytes, h->st));
     RG_TRY(deposit_one(h, ran, reinterpret_cast<float*>(h->V[1].M), RED_SUM_WR));
   }
+  // host catalogues are borrowed for the call only: they are read before it returns
+  if (!gal->on_device || (ran && ran->n > 0 && !ran->on_device)) RG_CUDA(cudaStreamSynchronize(h->st));
   h->state = ST_DEPOSITED;
   h->delta_real_valid = 0;
   h->warm_level = -1;
