@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-warm", action="store_true")
+    ap.add_argument("--particle-order", choices=("retained", "per-call"), default="retained",
+                    help="retained: one brick sort per catalogue per step, shared by deposit and shift")
     ap.add_argument("--host-loop", action="store_true",
                     help="host-driven iteration (every pass a plain launch; for ncu launch lists)")
     return ap.parse_args()
@@ -223,6 +225,9 @@ def gpu_arm(args):
     r = binding.Recon.from_mock(m)
     if args.host_loop:
         r.set_option(binding.OPT_GRAPH, 0)
+    if args.particle_order == "retained":
+        r.set_option(binding.OPT_DEPOSIT_PATH, binding.PATH_SORTED)
+        r.set_option(binding.OPT_REUSE_SORT, 1)
     sg = torch.empty((len(gal), 3), dtype=torch.float32, device="cuda")
     sr = torch.empty((len(ran), 3), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -365,7 +370,8 @@ def gpu_arm(args):
                        "start": "learned warm start (U-Net on the 4x coarsened mesh)" if warm else "Eq. approx2",
                        "l2": "inputs larger than L2 (each field 539 MB), no flush",
                        "parallelism": "replicas" if ws > 1 else "single",
-                       "iteration_loop": "host" if args.host_loop else "cuda graph"},
+                       "iteration_loop": "host" if args.host_loop else "cuda graph",
+                       "particle_order": args.particle_order},
             "path": "learned warm start" if warm else "Eq. approx2 start",
             "warm_start": warm,
             "plain": plain,

@@ -263,6 +263,13 @@ enum {
                                    timing (recon_set_timing) always uses the host-driven loop.   */
   RECON_OPT_LINE_TILE = 3,      /* FFT tile of the x-line passes: 0 (default) 16 adjacent columns
                                    (128-byte rows) per tile, 1: 8 columns                         */
+  RECON_OPT_REUSE_SORT = 5,     /* 0 (default); 1: a recon_shift of the catalogue last given to
+                                   recon_deposit (same pointer, n, dtype and memory kind, no
+                                   pos_out) reuses the brick order the sorted deposit made of it
+                                   (RECON_PATH_SORTED deposit, n <= 2^25) instead of reading and
+                                   sorting the positions again; the caller guarantees they did not
+                                   change in between.  While that order is held, shifts of other
+                                   catalogues take the direct path.                              */
   RECON_OPT_KSPACE_GENERIC = 4  /* 0 (default): for N = 512 the source update and the projection
                                    pass run in kernels that keep the first and last FFT stages
                                    (and the c2r/r2c pairing) in registers; 1: the generic staged

@@ -44,32 +44,32 @@ __device__ __forceinline__ uint32_t brick_key(const uint32_t (&q)[3], int nb) {
   return (bx * (uint32_t)nb + by) * (uint32_t)nb + bz;
 }
 
-// Count particles per brick; each particle keeps its brick and its arrival rank in the brick.
+// Count particles per brick; each particle keeps its brick and its arrival rank in the brick.  The
+// positions (and weights) are read here only, once: each particle's packed record is kept in input
+// order for the scatter.
 template <typename PT>
-__global__ void __launch_bounds__(256) count_kernel(const PT* __restrict__ pos, long long np, double scale, int n,
-                                                    int nb, uint32_t* __restrict__ hist, uint32_t* __restrict__ key,
-                                                    uint32_t* __restrict__ rank) {
+__global__ void __launch_bounds__(256) count_kernel(const PT* __restrict__ pos, const float* __restrict__ w,
+                                                    long long np, double scale, int n, int nb,
+                                                    uint32_t* __restrict__ hist, uint32_t* __restrict__ key,
+                                                    uint32_t* __restrict__ rank, uint4* __restrict__ pre) {
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x) {
     uint32_t q[3];
     pack(pos, p, scale, n, q);
     const uint32_t k = brick_key(q, nb);
     key[p] = k;
     rank[p] = atomicAdd(hist + k, 1u);
+    pre[p] = make_uint4(q[0], q[1], q[2], __float_as_uint(w ? w[p] : 1.f));
   }
 }
 
-// Place every particle at offs[brick] + rank as a packed record.
-template <typename PT>
-__global__ void __launch_bounds__(256) scatter_kernel(const PT* __restrict__ pos, const float* __restrict__ w,
-                                                      long long np, double scale, int n,
+// Place every particle's record at offs[brick] + rank.
+__global__ void __launch_bounds__(256) scatter_kernel(const uint4* __restrict__ pre, long long np,
                                                       const uint32_t* __restrict__ offs, const uint32_t* __restrict__ key,
                                                       const uint32_t* __restrict__ rank, uint4* __restrict__ rec,
                                                       uint32_t* __restrict__ perm) {
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x) {
-    uint32_t q[3];
-    pack(pos, p, scale, n, q);
     const uint32_t slot = offs[key[p]] + rank[p];
-    rec[slot] = make_uint4(q[0], q[1], q[2], __float_as_uint(w ? w[p] : 1.f));
+    rec[slot] = pre[p];
     perm[slot] = (uint32_t)p;
   }
 }
@@ -306,7 +306,7 @@ constexpr int kGrid = 152 * 8;
 size_t brick_scratch_bytes(int n) {
   const size_t nb3 = (size_t)(n / kBrick) * (n / kBrick) * (n / kBrick);
   const size_t ch = (size_t)sort_chunk(n);
-  return a256(nb3 * 4) + a256((nb3 + 1) * 4) + a256(4096 * 4) + a256(ch * 16) + 3 * a256(ch * 4);
+  return a256(nb3 * 4) + a256((nb3 + 1) * 4) + a256(4096 * 4) + 2 * a256(ch * 16) + 3 * a256(ch * 4);
 }
 
 BrickBuffers brick_buffers(char* base, int n, double L) {
@@ -330,6 +330,8 @@ BrickBuffers brick_buffers(char* base, int n, double L) {
   b.key = reinterpret_cast<uint32_t*>(base);
   base += a256(ch * 4);
   b.rank = reinterpret_cast<uint32_t*>(base);
+  base += a256(ch * 4);
+  b.pre = reinterpret_cast<uint4*>(base);
   return b;
 }
 
@@ -345,18 +347,15 @@ cudaError_t brick_sort(const BrickBuffers& b, const void* pos, int dtype, const 
   long long want = (np + 255) / 256;
   const int blocks = (int)(want < kGrid * 2 ? want : kGrid * 2);
   if (dtype == 0)
-    count_kernel<double><<<blocks, 256, 0, st>>>((const double*)pos, np, b.scale, b.n, b.nb, b.hist, b.key, b.rank);
+    count_kernel<double><<<blocks, 256, 0, st>>>((const double*)pos, w, np, b.scale, b.n, b.nb, b.hist, b.key, b.rank,
+                                                  b.pre);
   else
-    count_kernel<float><<<blocks, 256, 0, st>>>((const float*)pos, np, b.scale, b.n, b.nb, b.hist, b.key, b.rank);
+    count_kernel<float><<<blocks, 256, 0, st>>>((const float*)pos, w, np, b.scale, b.n, b.nb, b.hist, b.key, b.rank,
+                                                 b.pre);
   scan_blocks_kernel<<<nblk, 256, 0, st>>>(b.hist, b.offs, b.bsum, m);
   scan_sums_kernel<<<1, 1024, 0, st>>>(b.bsum, nblk, b.offs + m);
   scan_add_kernel<<<(m + 255) / 256 < kGrid ? (m + 255) / 256 : kGrid, 256, 0, st>>>(b.offs, b.bsum, m);
-  if (dtype == 0)
-    scatter_kernel<double><<<blocks, 256, 0, st>>>((const double*)pos, w, np, b.scale, b.n, b.offs, b.key, b.rank,
-                                                    b.rec, b.perm);
-  else
-    scatter_kernel<float><<<blocks, 256, 0, st>>>((const float*)pos, w, np, b.scale, b.n, b.offs, b.key, b.rank,
-                                                   b.rec, b.perm);
+  scatter_kernel<<<blocks, 256, 0, st>>>(b.pre, np, b.offs, b.key, b.rank, b.rec, b.perm);
   return cudaGetLastError();
 }
 

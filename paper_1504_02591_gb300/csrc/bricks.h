@@ -26,6 +26,8 @@ struct BrickBuffers {
   uint32_t* perm;        // kSortChunk: sorted slot -> index within the chunk
   uint32_t* key;         // kSortChunk: brick of each particle (input order)
   uint32_t* rank;        // kSortChunk: arrival rank of each particle within its brick
+  uint4* pre;            // kSortChunk: packed records in input order (count -> scatter); free after
+                         // the scatter (a retained sort's shift writes its float32 shifts here)
 };
 
 size_t brick_scratch_bytes(int n);

@@ -83,7 +83,7 @@ Layout layout_for(int n) {
   if ((size_t)conv_blocks(n) > nb) nb = conv_blocks(n);
   if ((size_t)brick_grid() > nb) nb = brick_grid();
   l.partials = align256(nb * 4 * sizeof(double));
-  l.stage = align256((size_t)kStageParticles * kStageBytesPer);
+  l.stage = align256(2 * (size_t)kStageParticles * kStageBytesPer);   // two buffers (copy/compute overlap)
   l.bricks = align256(brick_scratch_bytes(n));
   l.coarse = align256((size_t)(n / 2) * (n / 2) * (n / 2) * sizeof(float));   // warm start, level >= 1
   l.total = 5 * l.field + l.tw + l.tabs + l.tabz + l.off + l.taps + l.red + l.partials + l.stage + l.bricks +
@@ -132,6 +132,8 @@ struct recon_handle {
   double* red = nullptr;
   LoopState* loop = nullptr;   // device-driven iteration state (inside the red region)
   cudaStream_t cap_stream = nullptr;   // private stream for graph capture
+  cudaStream_t copy_st = nullptr;      // host<->device copies of the staged shift (overlap the kernels)
+  cudaEvent_t ev_in[2] = {}, ev_out[2] = {}, ev_free[2] = {};
   int use_graph = 1;
   double* partials = nullptr;
   char* stage = nullptr;
@@ -142,6 +144,14 @@ struct recon_handle {
   int shift_path = RECON_PATH_SORTED;
   int narrow_lines = 0;
   int kspace_generic = 0;
+  int reuse_sort = 0;
+  // the catalogue whose brick order the sort buffers hold (sorted deposit, one chunk)
+  struct SortMemo {
+    int valid;
+    const void* pos;
+    int64_t n;
+    int dtype, on_device;
+  } memo{};
   int d_is_k = 0;
   int delta_real_valid = 0;
   float* ucoarse = nullptr;   // block means of the start's radial displacement (warm start, level >= 1)
@@ -345,10 +355,26 @@ recon_status deposit_one(recon_handle* h, const recon_catalog* c, float* rho, in
       return RECON_OK;
     }
   }
+  if (h->deposit_path == RECON_PATH_SORTED && c->n > 0 && c->n <= h->bb.chunk) {
+    // the whole catalogue in one sort (page-locked host memory is read in place); the sort
+    // buffers then hold its brick order for a later shift of the same catalogue
+    const void* dpos = c->on_device ? c->pos : mapped_host(c->pos);
+    const float* dw = c->w ? (c->on_device ? c->w : static_cast<const float*>(mapped_host(c->w))) : nullptr;
+    if (dpos && (!c->w || dw)) {
+      h->memo.valid = 0;
+      RG_CUDA(timed(h, RECON_K_SORT, (double)c->n * (6 * es + (c->w ? 4 : 0) + 44),
+                    [&] { return brick_sort(h->bb, dpos, c->dtype, dw, c->n, h->st); }));
+      RG_CUDA(timed(h, RECON_K_DEPOSIT, (double)c->n * 16, [&] { return brick_deposit(h->bb, rho, h->partials, h->st); }));
+      RG_TRY(finalize(h, brick_grid(), 1, slot, 0));
+      h->memo = {1, c->pos, c->n, c->dtype, c->on_device};
+      return RECON_OK;
+    }
+  }
   const long long chunk = c->on_device ? h->bb.chunk : (kStageParticles < h->bb.chunk ? kStageParticles : h->bb.chunk);
   char* spos = h->stage;
   float* sw = reinterpret_cast<float*>(h->stage + kStageParticles * 24);
   if (c->n == 0) RG_CUDA(cudaMemsetAsync(h->red + slot, 0, sizeof(double), h->st));
+  if (h->deposit_path == RECON_PATH_SORTED) h->memo.valid = 0;
   for (long long p0 = 0; p0 < c->n; p0 += chunk) {
     const long long m = (c->n - p0 < chunk) ? c->n - p0 : chunk;
     const void* pin = (const char*)c->pos + (size_t)p0 * 3 * es;
@@ -410,6 +436,7 @@ namespace {
 // length, line of sight, mask and density options.  Uploads the node offsets from the observer and
 // the smoothing taps, and resets the call sequence.
 recon_status configure(recon_handle* h, const recon_params* p) {
+  h->memo.valid = 0;
   h->p = *p;
   h->L = p->box[0];
   h->bb.scale = (double)h->n / h->L;
@@ -612,6 +639,7 @@ recon_status recon_set_option(recon_handle* h, int option, int value) {
   else if (option == RECON_OPT_GRAPH) h->use_graph = value;
   else if (option == RECON_OPT_LINE_TILE) h->narrow_lines = value;
   else if (option == RECON_OPT_KSPACE_GENERIC) h->kspace_generic = value ? 1 : 0;
+  else if (option == RECON_OPT_REUSE_SORT) h->reuse_sort = value ? 1 : 0;
   else return RECON_ERR_INVALID_ARG;
   return RECON_OK;
 }
@@ -620,6 +648,15 @@ recon_status recon_destroy(recon_handle* h) {
   if (!h) return RECON_OK;
   drain_timing(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->copy_st) {
+    cudaStreamSynchronize(h->copy_st);
+    cudaStreamDestroy(h->copy_st);
+    for (int b = 0; b < 2; ++b) {
+      cudaEventDestroy(h->ev_in[b]);
+      cudaEventDestroy(h->ev_out[b]);
+      cudaEventDestroy(h->ev_free[b]);
+    }
+  }
   if (h->own_ws && h->ws) {
     cudaStreamSynchronize(h->st);
     cudaFree(h->ws);
@@ -639,6 +676,7 @@ recon_status recon_deposit(recon_handle* h, const recon_catalog* gal, const reco
     if (ran->n == 0) return RECON_ERR_INVALID_ARG;
   }
   const size_t bytes = (size_t)h->n * h->n * h->n * sizeof(float);
+  h->memo.valid = 0;
   RG_CUDA(cudaMemsetAsync(h->red, 0, h->lay.red, h->st));
   RG_CUDA(cudaMemsetAsync(h->V[0].M, 0, bytes, h->st));
   RG_TRY(deposit_one(h, gal, reinterpret_cast<float*>(h->V[0].M), RED_SUM_WG));
@@ -1029,22 +1067,60 @@ recon_status recon_shift(recon_handle* h, const recon_catalog* cat, int is_galax
   ba.periodic = a.periodic;
   ba.L = h->L;
   ba.dtype = cat->dtype == RECON_F64 ? 0 : 1;
+  const bool same = h->memo.valid && cat->pos == h->memo.pos && cat->n == h->memo.n && cat->dtype == h->memo.dtype &&
+                    cat->on_device == h->memo.on_device;
+  if (h->reuse_sort && same && !pos_out && cat->n > 0) {
+    // the deposit's brick order of this very catalogue: no second read of the positions
+    float* dst = out_on_device ? shift_out : reinterpret_cast<float*>(h->bb.pre);
+    ba.pos = nullptr;
+    ba.pos_out = nullptr;
+    ba.shift = dst;
+    RG_CUDA(timed(h, RECON_K_SHIFT, (double)cat->n * (16 + 4 + 12), [&] { return brick_shift(h->bb, ba, h->st); }));
+    if (!out_on_device) {
+      RG_CUDA(cudaMemcpyAsync(shift_out, dst, (size_t)cat->n * 3 * sizeof(float), cudaMemcpyDeviceToHost, h->st));
+      RG_CUDA(cudaStreamSynchronize(h->st));
+    }
+    return RECON_OK;
+  }
+  // with a retained brick order, other catalogues take the direct path so that it survives
+  const bool sorted = h->shift_path == RECON_PATH_SORTED && !(h->reuse_sort && h->memo.valid);
+  if (sorted) h->memo.valid = 0;
   const bool staged = !cat->on_device || !out_on_device;
   const long long chunk = staged ? (kStageParticles < h->bb.chunk ? kStageParticles : h->bb.chunk) : h->bb.chunk;
-  char* spos = h->stage;
-  float* sshift = reinterpret_cast<float*>(h->stage + kStageParticles * 28);
-  double* spout = reinterpret_cast<double*>(h->stage + kStageParticles * 40);
-  for (long long p0 = 0; p0 < cat->n; p0 += chunk) {
+  if (staged && !h->copy_st) {
+    RG_CUDA(cudaStreamCreateWithFlags(&h->copy_st, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+      RG_CUDA(cudaEventCreateWithFlags(&h->ev_in[b], cudaEventDisableTiming));
+      RG_CUDA(cudaEventCreateWithFlags(&h->ev_out[b], cudaEventDisableTiming));
+      RG_CUDA(cudaEventCreateWithFlags(&h->ev_free[b], cudaEventDisableTiming));
+    }
+  }
+  // Staged chunks alternate between two buffers: the copy stream brings chunk i + 1 in (and takes
+  // chunk i - 1's shifts out) while the handle's stream runs chunk i's kernels.
+  long long i = 0;
+  for (long long p0 = 0; p0 < cat->n; p0 += chunk, ++i) {
     const long long m = (cat->n - p0 < chunk) ? cat->n - p0 : chunk;
+    const int b = (int)(i & 1);
+    char* sbuf = h->stage + (size_t)b * kStageParticles * kStageBytesPer;
+    char* spos = sbuf;
+    float* sshift = reinterpret_cast<float*>(sbuf + kStageParticles * 28);
+    double* spout = reinterpret_cast<double*>(sbuf + kStageParticles * 40);
     const void* pin = (const char*)cat->pos + (size_t)p0 * 3 * es;
+    if (staged && i >= 2) {
+      // buffer b's previous chunk is done (kernels and copies) before it is reused
+      RG_CUDA(cudaStreamWaitEvent(h->copy_st, h->ev_free[b], 0));
+      RG_CUDA(cudaStreamWaitEvent(h->st, h->ev_free[b], 0));
+    }
     if (!cat->on_device) {
-      RG_CUDA(cudaMemcpyAsync(spos, pin, (size_t)m * 3 * es, cudaMemcpyHostToDevice, h->st));
+      RG_CUDA(cudaMemcpyAsync(spos, pin, (size_t)m * 3 * es, cudaMemcpyHostToDevice, h->copy_st));
+      RG_CUDA(cudaEventRecord(h->ev_in[b], h->copy_st));
+      RG_CUDA(cudaStreamWaitEvent(h->st, h->ev_in[b], 0));
       pin = spos;
     }
     ba.pos = pin;
     ba.shift = out_on_device ? shift_out + 3 * p0 : sshift;
     ba.pos_out = pos_out ? (out_on_device ? pos_out + 3 * p0 : spout) : nullptr;
-    if (h->shift_path == RECON_PATH_SORTED) {
+    if (sorted) {
       RG_CUDA(timed(h, RECON_K_SORT, (double)m * (6 * es + 28),
                     [&] { return brick_sort(h->bb, pin, cat->dtype, nullptr, m, h->st); }));
       RG_CUDA(timed(h, RECON_K_SHIFT, (double)m * (16 + 4 + 12 + (pos_out ? 3 * es + 24 : 0)),
@@ -1056,12 +1132,24 @@ recon_status recon_shift(recon_handle* h, const recon_catalog* cat, int is_galax
                     [&] { return launch_shift(pin, cat->dtype, m, a, h->st); }));
     }
     if (!out_on_device) {
-      RG_CUDA(cudaMemcpyAsync(shift_out + 3 * p0, sshift, (size_t)m * 3 * sizeof(float), cudaMemcpyDeviceToHost, h->st));
+      RG_CUDA(cudaEventRecord(h->ev_out[b], h->st));
+      RG_CUDA(cudaStreamWaitEvent(h->copy_st, h->ev_out[b], 0));
+      RG_CUDA(cudaMemcpyAsync(shift_out + 3 * p0, sshift, (size_t)m * 3 * sizeof(float), cudaMemcpyDeviceToHost,
+                              h->copy_st));
       if (pos_out)
-        RG_CUDA(cudaMemcpyAsync(pos_out + 3 * p0, spout, (size_t)m * 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        RG_CUDA(cudaMemcpyAsync(pos_out + 3 * p0, spout, (size_t)m * 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                                h->copy_st));
+      RG_CUDA(cudaEventRecord(h->ev_free[b], h->copy_st));
+    } else if (staged) {
+      RG_CUDA(cudaEventRecord(h->ev_free[b], h->st));
     }
   }
-  if (!out_on_device) RG_CUDA(cudaStreamSynchronize(h->st));
+  if (staged && i > 0) {
+    // the handle's stream resumes after the last copies; host memory is released on return
+    for (long long k = (i >= 2 ? i - 2 : 0); k < i; ++k)
+      RG_CUDA(cudaStreamWaitEvent(h->st, h->ev_free[k & 1], 0));
+    RG_CUDA(cudaStreamSynchronize(h->st));
+  }
   return RECON_OK;
 }
 

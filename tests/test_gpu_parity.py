@@ -213,6 +213,41 @@ def test_shell_survey_converged_vs_oracle(B, shell_case):
     r.close()
 
 
+@pytest.mark.parametrize("host", [False, True])
+def test_retained_sort_shift(B, shell_case, host):
+    """RECON_OPT_REUSE_SORT: the random shift reuses the sorted deposit's brick order (no second sort,
+    no second read of the positions; page-locked host catalogues are sorted in place) and gives the
+    shifts of the default path; the galaxy shift meanwhile takes the direct path."""
+    m, ref = shell_case
+    if host:
+        gal = torch.from_numpy(m.galaxies.pos).pin_memory()
+        ran = torch.from_numpy(m.randoms.pos).pin_memory()
+    else:
+        gal = torch.from_numpy(m.galaxies.pos).cuda()
+        ran = torch.from_numpy(m.randoms.pos).cuda()
+    out = {}
+    for reuse in (0, 1):
+        r = B.Recon.from_mock(m)
+        if reuse:
+            r.set_option(B.OPT_DEPOSIT_PATH, B.PATH_SORTED)
+            r.set_option(B.OPT_REUSE_SORT, 1)
+        r.deposit(gal, None, ran, None)
+        r.smooth()
+        n_it, rel, st = r.iterate(B.START_FFTA, 1e-6, 40)
+        assert st == B.OK
+        sg = r.shift(gal, True)
+        sorts = r.timing()["sort"][0]
+        sr = r.shift(ran, False)
+        if reuse:
+            assert r.timing()["sort"][0] == sorts      # the random shift sorted nothing
+        out[reuse] = (np.asarray(sg.cpu() if hasattr(sg, "cpu") else sg),
+                      np.asarray(sr.cpu() if hasattr(sr, "cpu") else sr))
+        r.close()
+    # the two deposits differ only in the order of their float32 sums
+    assert np.abs(out[1][0] - out[0][0]).max() <= SHIFT_TOL
+    assert np.abs(out[1][1] - out[0][1]).max() <= SHIFT_TOL
+
+
 # ------------------------------------------------------------------------------------------------
 # Uniform mean density, fixed LOS and lognormal (the large periodic run's options, at 64^3)
 # ------------------------------------------------------------------------------------------------
