@@ -9,7 +9,7 @@ Everything is float64 numpy.  The 3-D FFT is ``numpy.fft.rfftn`` / ``irfftn`` us
 primitive (forward e^{-ik.x} unnormalised, inverse with 1/N^3); the test suite pins it against a
 brute-force DFT.  There is no blocking, fusion or reordering beyond what the paper's equations state.
 
-Conventions (readings of the paper where it is silent or inconsistent; each is listed in the design doc):
+Conventions (readings of the paper where it is silent or inconsistent, stated here once):
 
 * Grid: nodes at x_i = i*H, i = 0..N-1 per axis, H = L/N, periodic.  Arrays are indexed [ix, iy, iz].
 * k_j = 2 pi m_j / L with m_j in {0..N/2-1, -N/2..-1}.  The derivative wavenumber kd_j equals k_j
