@@ -1008,13 +1008,13 @@ struct KIter8 {
 
 // The three components' 512-point transforms of one column, stage by stage together (one buffer
 // each, so a stage needs one barrier for all three): v[q][r] = x_q[j + 64 r] in, X_q[j + 64 r] out.
-template <bool INV, int N, int C>
-__device__ __forceinline__ void r512_lines3(float2 (&v)[3][8], float2* __restrict__ s, const float2* __restrict__ tw,
+template <bool INV, int N, int C, int K = 3>
+__device__ __forceinline__ void r512_lines3(float2 (&v)[K][8], float2* __restrict__ s, const float2* __restrict__ tw,
                                             int j, int col) {
   using Lay = ColLayout<C>;
   constexpr int B = N * C;
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {                          // stage 1 (NS = 1): no twiddles
+  for (int q = 0; q < K; ++q) {                          // stage 1 (NS = 1): no twiddles
     Dft<8, INV>::run(v[q]);
 #pragma unroll
     for (int r = 0; r < 8; ++r) s[q * B + Lay::phys(8 * j + r, col)] = v[q][r];
@@ -1022,7 +1022,7 @@ __device__ __forceinline__ void r512_lines3(float2 (&v)[3][8], float2* __restric
   __syncthreads();
   const int k = j & 7;
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {                          // stage 2 (NS = 8)
+  for (int q = 0; q < K; ++q) {                          // stage 2 (NS = 8)
 #pragma unroll
     for (int r = 0; r < 8; ++r) v[q][r] = s[q * B + Lay::phys(j + 64 * r, col)];
 #pragma unroll
@@ -1036,12 +1036,12 @@ __device__ __forceinline__ void r512_lines3(float2 (&v)[3][8], float2* __restric
   __syncthreads();
   const int base = (j >> 3) * 64 + k;
 #pragma unroll
-  for (int q = 0; q < 3; ++q)
+  for (int q = 0; q < K; ++q)
 #pragma unroll
     for (int r = 0; r < 8; ++r) s[q * B + Lay::phys(base + 8 * r, col)] = v[q][r];
   __syncthreads();
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {                          // stage 3 (NS = 64)
+  for (int q = 0; q < K; ++q) {                          // stage 3 (NS = 64)
 #pragma unroll
     for (int r = 0; r < 8; ++r) v[q][r] = s[q * B + Lay::phys(j + 64 * r, col)];
 #pragma unroll
@@ -1053,6 +1053,65 @@ __device__ __forceinline__ void r512_lines3(float2 (&v)[3][8], float2* __restric
     Dft<8, INV>::run(v[q]);
   }
   __syncthreads();                                       // the buffers are reused
+}
+
+// The start's k-space pass along y for N = 512 (S_DELTA): the y transform of delta (unless delta(k)
+// is already stored), delta(k) and S_-1 = delta/b stored, Z[delta/b] and its three inverse y
+// transforms, with the first and last stages in registers as in the update kernel.
+template <int N, int C>
+__global__ void __launch_bounds__(KIter8<N, C>::T, KIter8<N, C>::kMinBlocks) kdelta8_kernel(const SArgs a) {
+  constexpr int T = KIter8<N, C>::T;
+  constexpr int H = N / 2;
+  extern __shared__ float4 ssm[];
+  float2* tw = reinterpret_cast<float2*>(ssm);
+  float2* s = tw + KIter8<N, C>::TAB;
+  for (int m = threadIdx.x; m < Plan<N>::kTab; m += T) tw[m] = a.tab[m];
+  const Tile t = tile_of<N, C, AX_Y>(blockIdx.x);
+  const int col = threadIdx.x % C, j = threadIdx.x / C;
+  float2* __restrict__ dkp = t.isQ ? a.dk.Q : a.dk.M;
+  float2 d[1][8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) d[0][r] = dkp[t.base + (size_t)(j + 64 * r) * t.ls + (size_t)col * t.cs];
+  __syncthreads();   // twiddles
+  if (!a.d_is_k) r512_lines3<false, N, C, 1>(d, s, tw, j, col);
+
+  const Geometry& g = a.g;
+  float2* Sp = t.isQ ? a.sbuf.Q : a.sbuf.M;
+  float2 v[3][8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int ky = j + 64 * r;
+    int ix, kz;
+    if (!t.isQ) { ix = t.a; kz = t.c0 + col; } else { ix = t.c0 + col; kz = H; }
+    const int mx = (ix < H) ? ix : ix - N;
+    const int my = (ky < H) ? ky : ky - N;
+    const float kx = g.kf * mx, kyf = g.kf * my, kzf = g.kf * kz;
+    const float k2 = kx * kx + kyf * kyf + kzf * kzf;
+    const float kdx = (ix == H) ? 0.f : kx;
+    const float kdy = (ky == H) ? 0.f : kyf;
+    const float kdz = (kz == H) ? 0.f : kzf;
+    const size_t gi = t.base + (size_t)ky * t.ls + (size_t)col * t.cs;
+    float2 dk = d[0][r];
+    if (!a.d_is_k) {
+      if (a.lognormal && ix == 0 && ky == 0 && kz == 0) dk.x -= (float)(a.red[RED_SUM_LOG]);   // N^3 <ln(1+delta)>
+      dkp[gi] = dk;
+    }
+    float2 S = cscale(dk, a.inv_b);
+    if (k2 == 0.f) S = make_float2(0.f, 0.f);
+    const float inv_k2 = (k2 > 0.f) ? 1.f / k2 : 0.f;
+    Sp[gi] = S;
+    const float2 iS = cscale(mul_i(S), inv_k2 * g.inv_n3);
+    v[0][r] = cscale(iS, kdx);
+    v[1][r] = cscale(iS, kdy);
+    v[2][r] = cscale(iS, kdz);
+  }
+  r512_lines3<true, N, C>(v, s, tw, j, col);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    float2* __restrict__ dst = t.isQ ? a.f[q].Q : a.f[q].M;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) dst[t.base + (size_t)(j + 64 * r) * t.ls + (size_t)col * t.cs] = v[q][r];
+  }
 }
 
 // The plain line transform along x for N = 512, one component per CTA (blockIdx.y): the first
@@ -1358,6 +1417,22 @@ struct MeshImpl {
     return cudaErrorInvalidValue;
   }
 
+  static cudaError_t dlaunch(const SArgs& a, cudaStream_t st) {
+    if constexpr (N == 512) {
+      constexpr int C = SCols<N, S_DELTA>::v;
+      const void* k = (const void*)kdelta8_kernel<N, C>;
+      static bool attr = false;
+      if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)KIter8<N, C>::smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+      }
+      void* args[] = {const_cast<SArgs*>(&a)};
+      return cudaLaunchKernel(k, dim3(sblocks<S_DELTA>()), dim3(KIter8<N, C>::T), args, KIter8<N, C>::smem, st);
+    }
+    return cudaErrorInvalidValue;
+  }
+
   static cudaError_t xlaunch(bool inv, const SArgs& a, cudaStream_t st, int ncomp) {
     if constexpr (N == 512) {
       constexpr int C = SCols<N, S_FWD>::v;   // 16 adjacent columns (128-byte rows)
@@ -1387,6 +1462,9 @@ struct MeshImpl {
       return a.narrow ? slaunch<S_FWD, 1, AX_X, 1>(a, st, nc) : slaunch<S_FWD, 1, AX_X>(a, st, nc);
     if (mode == S_INV && axis == AX_X)
       return a.narrow ? slaunch<S_INV, 1, AX_X, 1>(a, st, nc) : slaunch<S_INV, 1, AX_X>(a, st, nc);
+    if constexpr (N == 512) {
+      if (mode == S_DELTA && axis == AX_Y && !a.generic) return dlaunch(a, st);
+    }
     if (mode == S_DELTA && axis == AX_Y) return slaunch<S_DELTA, 1, AX_Y>(a, st, 1);
     if (mode == S_ITER && axis == AX_Y && nc == 3) {
       if constexpr (N == 512) {

@@ -73,8 +73,9 @@ def test_fused_warm_start_passes_512(lib):
 
 @pytest.mark.parametrize("uniform", [False, True])
 def test_fused_delta_pass_512(lib, uniform):
-    """The z convolution, delta and its r2c at N = 512 (fused pass) against the generic pass: the real
-    delta and delta(k) agree up to the order of the deposit's float32 atomic sums."""
+    """The z convolution, delta and its r2c at N = 512, and the start's y pass (delta(k), S_-1 and
+    Z[delta/b]), fused against generic: the real delta, delta(k) and Psi after one update agree up
+    to the order of the deposit's float32 atomic sums."""
     from paper_1504_02591_gb300 import binding as B
     from paper_1504_02591_gb300 import mocks
     if uniform:
@@ -92,11 +93,11 @@ def test_fused_delta_pass_512(lib, uniform):
         r.smooth()
         d_real = r.get_field(B.FIELD_DELTA).cpu().numpy()
         r.iterate(B.START_FFTA, 0.0, 1)          # delta(k) is exported once the y transform has run
-        out[generic] = (d_real, r.get_field(B.FIELD_DELTA_K).cpu().numpy())
+        out[generic] = (d_real, r.get_field(B.FIELD_DELTA_K).cpu().numpy(), r.get_psi().cpu().numpy())
     r.close()
-    for i in range(2):
+    for i in range(3):
         dt = np.complex128 if np.iscomplexobj(out[0][i]) else np.float64
         a, b = out[0][i].astype(dt), out[1][i].astype(dt)
         d = float(np.sqrt((np.abs(a - b) ** 2).sum() / (np.abs(b) ** 2).sum()))
-        print(f"fused delta pass ({'uniform' if uniform else 'survey'}), {'delta(k)' if i else 'delta'}: rel L2 {d:.2e}")
+        print(f"fused delta pass ({'uniform' if uniform else 'survey'}), {('delta', 'delta(k)', 'Psi')[i]}: rel L2 {d:.2e}")
         assert d < 1e-5, d
