@@ -1003,7 +1003,8 @@ struct KIter8 {
   static constexpr int T = (N / 8) * C;        // one butterfly of one column per thread and stage
   static constexpr int kMinBlocks = T <= 256 ? 2 : 1;
   static constexpr int TAB = (Plan<N>::kTab + 1) & ~1;
-  static constexpr size_t smem = sizeof(float2) * ((size_t)TAB + 3 * (size_t)N * C);   // one buffer per component
+  // one buffer per transformed line: the x and z terms share one (see kiter8_kernel)
+  static constexpr size_t smem = sizeof(float2) * ((size_t)TAB + 2 * (size_t)N * C);
 };
 
 // The three components' 512-point transforms of one column, stage by stage together (one buffer
@@ -1056,8 +1057,8 @@ __device__ __forceinline__ void r512_lines3(float2 (&v)[K][8], float2* __restric
 }
 
 // The start's k-space pass along y for N = 512 (S_DELTA): the y transform of delta (unless delta(k)
-// is already stored), delta(k) and S_-1 = delta/b stored, Z[delta/b] and its three inverse y
-// transforms, with the first and last stages in registers as in the update kernel.
+// is already stored), delta(k) and S_-1 = delta/b stored, Z[delta/b] with two inverse y transforms
+// (Psi_x and Psi_z share one, as in the update kernel), the first and last stages in registers.
 template <int N, int C>
 __global__ void __launch_bounds__(KIter8<N, C>::T, KIter8<N, C>::kMinBlocks) kdelta8_kernel(const SArgs a) {
   constexpr int T = KIter8<N, C>::T;
@@ -1077,7 +1078,7 @@ __global__ void __launch_bounds__(KIter8<N, C>::T, KIter8<N, C>::kMinBlocks) kde
 
   const Geometry& g = a.g;
   float2* Sp = t.isQ ? a.sbuf.Q : a.sbuf.M;
-  float2 v[3][8];
+  float2 v[2][8];
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     const int ky = j + 64 * r;
@@ -1087,9 +1088,7 @@ __global__ void __launch_bounds__(KIter8<N, C>::T, KIter8<N, C>::kMinBlocks) kde
     const int my = (ky < H) ? ky : ky - N;
     const float kx = g.kf * mx, kyf = g.kf * my, kzf = g.kf * kz;
     const float k2 = kx * kx + kyf * kyf + kzf * kzf;
-    const float kdx = (ix == H) ? 0.f : kx;
     const float kdy = (ky == H) ? 0.f : kyf;
-    const float kdz = (kz == H) ? 0.f : kzf;
     const size_t gi = t.base + (size_t)ky * t.ls + (size_t)col * t.cs;
     float2 dk = d[0][r];
     if (!a.d_is_k) {
@@ -1101,16 +1100,26 @@ __global__ void __launch_bounds__(KIter8<N, C>::T, KIter8<N, C>::kMinBlocks) kde
     const float inv_k2 = (k2 > 0.f) ? 1.f / k2 : 0.f;
     Sp[gi] = S;
     const float2 iS = cscale(mul_i(S), inv_k2 * g.inv_n3);
-    v[0][r] = cscale(iS, kdx);
+    v[0][r] = iS;
     v[1][r] = cscale(iS, kdy);
-    v[2][r] = cscale(iS, kdz);
   }
-  r512_lines3<true, N, C>(v, s, tw, j, col);
+  r512_lines3<true, N, C, 2>(v, s, tw, j, col);
+  {
+    // Psi_x and Psi_z are kdx and kdz (constant along the line) times one inverse transform
+    int ix, kz;
+    if (!t.isQ) { ix = t.a; kz = t.c0 + col; } else { ix = t.c0 + col; kz = H; }
+    const float kdx = (ix == H) ? 0.f : g.kf * ((ix < H) ? ix : ix - N);
+    const float kdz = (kz == H) ? 0.f : g.kf * kz;
+    float2* __restrict__ dx = t.isQ ? a.f[0].Q : a.f[0].M;
+    float2* __restrict__ dy = t.isQ ? a.f[1].Q : a.f[1].M;
+    float2* __restrict__ dz = t.isQ ? a.f[2].Q : a.f[2].M;
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    float2* __restrict__ dst = t.isQ ? a.f[q].Q : a.f[q].M;
-#pragma unroll
-    for (int r = 0; r < 8; ++r) dst[t.base + (size_t)(j + 64 * r) * t.ls + (size_t)col * t.cs] = v[q][r];
+    for (int r = 0; r < 8; ++r) {
+      const size_t gi = t.base + (size_t)(j + 64 * r) * t.ls + (size_t)col * t.cs;
+      dx[gi] = cscale(v[0][r], kdx);
+      dy[gi] = v[1][r];
+      dz[gi] = cscale(v[0][r], kdz);
+    }
   }
 }
 
@@ -1205,63 +1214,75 @@ __global__ void __launch_bounds__(KIter8<N, C>::T, KIter8<N, C>::kMinBlocks) kit
   const Tile t = tile_of<N, C, AX_Y>(blockIdx.x);
   const int col = threadIdx.x % C, j = threadIdx.x / C;
 
+  // kx and kz are constant along the y line: the x and z terms of k . P are combined before the
+  // transform (FFT_y is linear), and Psi_x, Psi_z are kdx and kdz times one inverse transform
+  const Geometry& g = a.g;
+  int ix, kz;
+  if (!t.isQ) { ix = t.a; kz = t.c0 + col; } else { ix = t.c0 + col; kz = H; }
+  const int mx = (ix < H) ? ix : ix - N;
+  const float kx = g.kf * mx, kzf = g.kf * kz;
+  const float kdx = (ix == H) ? 0.f : kx;
+  const float kdz = (kz == H) ? 0.f : kzf;
+
   // every global read of the tile up front: the three components, delta(k), S_(n-1)
-  float2 v[3][8], dk[8], sp[8];
+  float2 v[2][8], dk[8], sp[8];
   {
     const float2* __restrict__ dkp = t.isQ ? a.dk.Q : a.dk.M;
     const float2* __restrict__ spp = t.isQ ? a.sbuf.Q : a.sbuf.M;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const size_t gi = t.base + (size_t)(j + 64 * r) * t.ls + (size_t)col * t.cs;
-#pragma unroll
-      for (int q = 0; q < 3; ++q) v[q][r] = (t.isQ ? a.f[q].Q : a.f[q].M)[gi];
+      const float2 px = (t.isQ ? a.f[0].Q : a.f[0].M)[gi];
+      const float2 pz = (t.isQ ? a.f[2].Q : a.f[2].M)[gi];
+      v[0][r] = make_float2(fmaf(kdx, px.x, kdz * pz.x), fmaf(kdx, px.y, kdz * pz.y));
+      v[1][r] = (t.isQ ? a.f[1].Q : a.f[1].M)[gi];
       dk[r] = dkp[gi];
       sp[r] = spp[gi];
     }
   }
   __syncthreads();   // twiddles
-  r512_lines3<false, N, C>(v, s, tw, j, col);
+  r512_lines3<false, N, C, 2>(v, s, tw, j, col);
 
   // S_n = delta/b + beta i k . P_n, the Parseval norms, Psi_n+1 = i kd S_n / k^2 (Eq. iterative)
   float d2 = 0.f, s2 = 0.f;
-  const Geometry& g = a.g;
   float2* Sp = t.isQ ? a.sbuf.Q : a.sbuf.M;
+  const float kxz2 = kx * kx + kzf * kzf, kdxz2 = kdx * kdx + kdz * kdz;
+  const float wgt = (kz == 0 || kz == H) ? 1.f : 2.f;
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     const int ky = j + 64 * r;
-    int ix, kz;
-    if (!t.isQ) { ix = t.a; kz = t.c0 + col; } else { ix = t.c0 + col; kz = H; }
-    const int mx = (ix < H) ? ix : ix - N;
     const int my = (ky < H) ? ky : ky - N;
-    const float kx = g.kf * mx, kyf = g.kf * my, kzf = g.kf * kz;
-    const float k2 = kx * kx + kyf * kyf + kzf * kzf;
-    const float kdx = (ix == H) ? 0.f : kx;
+    const float kyf = g.kf * my;
+    const float k2 = kxz2 + kyf * kyf;
     const float kdy = (ky == H) ? 0.f : kyf;
-    const float kdz = (kz == H) ? 0.f : kzf;
-    const float2 px = v[0][r], py = v[1][r], pz = v[2][r];
-    const float dre = kdx * px.x + kdy * py.x + kdz * pz.x;
-    const float dim = kdx * px.y + kdy * py.y + kdz * pz.y;
+    const float2 pa = v[0][r], py = v[1][r];
+    const float dre = fmaf(kdy, py.x, pa.x);
+    const float dim = fmaf(kdy, py.y, pa.y);
     float2 S = make_float2(fmaf(a.beta, -dim, dk[r].x * a.inv_b), fmaf(a.beta, dre, dk[r].y * a.inv_b));
     if (k2 == 0.f) S = make_float2(0.f, 0.f);
     const float inv_k2 = (k2 > 0.f) ? 1.f / k2 : 0.f;
-    const float wgt = (kz == 0 || kz == H) ? 1.f : 2.f;
-    const float fac = wgt * (kdx * kdx + kdy * kdy + kdz * kdz) * inv_k2 * inv_k2;
+    const float fac = wgt * (kdxz2 + kdy * kdy) * inv_k2 * inv_k2;
     const float ddx = S.x - sp[r].x, ddy = S.y - sp[r].y;
     d2 = fmaf(fac, ddx * ddx + ddy * ddy, d2);
     s2 = fmaf(fac, S.x * S.x + S.y * S.y, s2);
     Sp[t.base + (size_t)ky * t.ls + (size_t)col * t.cs] = S;
     const float2 iS = cscale(mul_i(S), inv_k2 * g.inv_n3);
-    v[0][r] = cscale(iS, kdx);
+    v[0][r] = iS;
     v[1][r] = cscale(iS, kdy);
-    v[2][r] = cscale(iS, kdz);
   }
 
-  r512_lines3<true, N, C>(v, s, tw, j, col);
+  r512_lines3<true, N, C, 2>(v, s, tw, j, col);
+  {
+    float2* __restrict__ dx = t.isQ ? a.f[0].Q : a.f[0].M;
+    float2* __restrict__ dy = t.isQ ? a.f[1].Q : a.f[1].M;
+    float2* __restrict__ dz = t.isQ ? a.f[2].Q : a.f[2].M;
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    float2* __restrict__ dst = t.isQ ? a.f[q].Q : a.f[q].M;
-#pragma unroll
-    for (int r = 0; r < 8; ++r) dst[t.base + (size_t)(j + 64 * r) * t.ls + (size_t)col * t.cs] = v[q][r];
+    for (int r = 0; r < 8; ++r) {
+      const size_t gi = t.base + (size_t)(j + 64 * r) * t.ls + (size_t)col * t.cs;
+      dx[gi] = cscale(v[0][r], kdx);
+      dy[gi] = v[1][r];
+      dz[gi] = cscale(v[0][r], kdz);
+    }
   }
 
   double r0 = block_sum((double)d2, red_sh);
