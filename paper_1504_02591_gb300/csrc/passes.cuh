@@ -1058,7 +1058,7 @@ __device__ __forceinline__ void r512_lines3(float2 (&v)[K][8], float2* __restric
 
 // The start's k-space pass along y for N = 512 (S_DELTA): the y transform of delta (unless delta(k)
 // is already stored), delta(k) and S_-1 = delta/b stored, Z[delta/b] with two inverse y transforms
-// (Psi_x and Psi_z share one, as in the update kernel), the first and last stages in registers.
+// (G and Psi_y, as the update kernel leaves them), the first and last stages in registers.
 template <int N, int C>
 __global__ void __launch_bounds__(KIter8<N, C>::T, KIter8<N, C>::kMinBlocks) kdelta8_kernel(const SArgs a) {
   constexpr int T = KIter8<N, C>::T;
@@ -1105,29 +1105,23 @@ __global__ void __launch_bounds__(KIter8<N, C>::T, KIter8<N, C>::kMinBlocks) kde
   }
   r512_lines3<true, N, C, 2>(v, s, tw, j, col);
   {
-    // Psi_x and Psi_z are kdx and kdz (constant along the line) times one inverse transform
-    int ix, kz;
-    if (!t.isQ) { ix = t.a; kz = t.c0 + col; } else { ix = t.c0 + col; kz = H; }
-    const float kdx = (ix == H) ? 0.f : g.kf * ((ix < H) ? ix : ix - N);
-    const float kdz = (kz == H) ? 0.f : g.kf * kz;
-    float2* __restrict__ dx = t.isQ ? a.f[0].Q : a.f[0].M;
+    // G (Psi_x = kdx G, Psi_z = kdz G) in the third field, Psi_y in the second, as the update
+    // kernel leaves them
     float2* __restrict__ dy = t.isQ ? a.f[1].Q : a.f[1].M;
-    float2* __restrict__ dz = t.isQ ? a.f[2].Q : a.f[2].M;
+    float2* __restrict__ dg = t.isQ ? a.f[2].Q : a.f[2].M;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const size_t gi = t.base + (size_t)(j + 64 * r) * t.ls + (size_t)col * t.cs;
-      dx[gi] = cscale(v[0][r], kdx);
       dy[gi] = v[1][r];
-      dz[gi] = cscale(v[0][r], kdz);
+      dg[gi] = v[0][r];
     }
   }
 }
 
-// The plain line transform along x for N = 512, one component per CTA (blockIdx.y): the first
-// radix-8 stage reads its inputs straight from global memory and the last writes its outputs
-// straight back, so shared memory carries only the middle stage (the generic pass also stages the
-// loads and stores).  Tiles of C adjacent columns, 64 butterflies per column and stage, NB per
-// thread.
+// The line transform along x for N = 512: the first radix-8 stage reads its inputs straight from
+// global memory and the last writes its outputs straight back, so shared memory carries only the
+// middle stage (the generic pass also stages the loads and stores).  Tiles of C adjacent columns,
+// 64 butterflies per column and stage, NB per thread.
 template <int C>
 struct XLine8 {
   static constexpr int T = 512;
@@ -1136,25 +1130,14 @@ struct XLine8 {
   static constexpr size_t smem = sizeof(float2) * ((size_t)TAB + (size_t)512 * C);
 };
 
+// The three radix-8 stages of this thread's NB butterflies: v[b][r] = x[j_b + 64 r] in, X[j_b + 64 r]
+// out (j_b = jb + b T / C), shared memory for the middle stage.  Starts by writing s: a caller
+// that ran it before syncs first.
 template <bool INV, int C>
-__global__ void __launch_bounds__(XLine8<C>::T, 2) xline8_kernel(const SArgs a) {
-  constexpr int N = 512, H = N / 2, T = XLine8<C>::T, NB = XLine8<C>::NB;
+__device__ __forceinline__ void xline8_lines(float2 (&v)[XLine8<C>::NB][8], float2* __restrict__ s,
+                                             const float2* __restrict__ tw, int jb, int col) {
+  constexpr int T = XLine8<C>::T, NB = XLine8<C>::NB;
   using Lay = ColLayout<C>;
-  extern __shared__ float4 ssm[];
-  float2* tw = reinterpret_cast<float2*>(ssm);
-  float2* s = tw + XLine8<C>::TAB;
-  if (!INV && a.skip_flag && *a.skip_flag != 0) return;   // uniform: device loop already converged
-  for (int m = threadIdx.x; m < Plan<N>::kTab; m += T) tw[m] = a.tab[m];
-  const Tile t = tile_of<N, C, AX_X>(blockIdx.x);
-  float2* __restrict__ P = t.isQ ? a.f[blockIdx.y].Q : a.f[blockIdx.y].M;
-  const int col = threadIdx.x % C, jb = threadIdx.x / C;
-  float2 v[NB][8];
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    const int j = jb + b * (T / C);
-#pragma unroll
-    for (int r = 0; r < 8; ++r) v[b][r] = P[t.base + (size_t)(j + 64 * r) * t.ls + (size_t)col * t.cs];
-  }
 #pragma unroll
   for (int b = 0; b < NB; ++b) {                          // stage 1 (NS = 1)
     const int j = jb + b * (T / C);
@@ -1185,7 +1168,7 @@ __global__ void __launch_bounds__(XLine8<C>::T, 2) xline8_kernel(const SArgs a) 
   }
   __syncthreads();
 #pragma unroll
-  for (int b = 0; b < NB; ++b) {                          // stage 3 (NS = 64), straight to global
+  for (int b = 0; b < NB; ++b) {                          // stage 3 (NS = 64)
     const int j = jb + b * (T / C);
 #pragma unroll
     for (int r = 0; r < 8; ++r) v[b][r] = s[Lay::phys(j + 64 * r, col)];
@@ -1196,10 +1179,99 @@ __global__ void __launch_bounds__(XLine8<C>::T, 2) xline8_kernel(const SArgs a) 
       v[b][r] = cmul(v[b][r], w);
     }
     Dft<8, INV>::run(v[b]);
-#pragma unroll
-    for (int r = 0; r < 8; ++r) P[t.base + (size_t)(j + 64 * r) * t.ls + (size_t)col * t.cs] = v[b][r];
   }
-  (void)H;
+}
+
+// PAIR = false: one component per CTA (blockIdx.y).  PAIR = true, the vector passes between the
+// register-fused k-space passes and the Z passes, which carry the x and z components of k-space
+// vectors as one field: kx and kz (kdx, kdz: zero at the Nyquist index) are constant along a y
+// line, so the y pass needs only A = kdx P_x + kdz P_z and P_y, and returns G (Psi_x = kdx G,
+// Psi_z = kdz G) and Psi_y.  CTAs with blockIdx.y = 1 transform the y component (second field);
+// CTAs with blockIdx.y = 0 do two transforms of one tile:
+//   inverse: G in the third field -> Psi_x = IFFT_x(kdx G) in the first, Psi_z = kdz IFFT_x(G) in
+//            the third (the second read of G finds the tile in the L2);
+//   forward: P_x in the first, P_z in the third -> A = kdx FFT_x(P_x) + kdz FFT_x(P_z) in the first
+//            (the first product goes through the L2 and is read back by the thread that wrote it).
+template <bool INV, int C, bool PAIR>
+__global__ void __launch_bounds__(XLine8<C>::T, 2) xline8_kernel(const SArgs a) {
+  constexpr int N = 512, H = N / 2, T = XLine8<C>::T, NB = XLine8<C>::NB;
+  extern __shared__ float4 ssm[];
+  float2* tw = reinterpret_cast<float2*>(ssm);
+  float2* s = tw + XLine8<C>::TAB;
+  if (!INV && a.skip_flag && *a.skip_flag != 0) return;   // uniform: device loop already converged
+  for (int m = threadIdx.x; m < Plan<N>::kTab; m += T) tw[m] = a.tab[m];
+  const Tile t = tile_of<N, C, AX_X>(blockIdx.x);
+  const int col = threadIdx.x % C, jb = threadIdx.x / C;
+  // element offsets fit 32 bits (at most N^3 / 2 complex points per field)
+  const uint32_t o0 = (uint32_t)t.base + (uint32_t)(col * t.cs) + (uint32_t)jb * (uint32_t)t.ls;
+  const uint32_t ls = (uint32_t)t.ls;
+  auto at = [&](int b, int r) { return o0 + (uint32_t)(b * (T / C) + 64 * r) * ls; };
+  float2 v[NB][8];
+  if (!PAIR || blockIdx.y == 1) {
+    float2* __restrict__ P = t.isQ ? a.f[blockIdx.y].Q : a.f[blockIdx.y].M;
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int r = 0; r < 8; ++r) v[b][r] = P[at(b, r)];
+    xline8_lines<INV, C>(v, s, tw, jb, col);
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int r = 0; r < 8; ++r) P[at(b, r)] = v[b][r];
+    return;
+  }
+  const float kf = a.g.kf;
+  const float kdz = t.isQ ? 0.f : kf * (float)(t.c0 + col);   // M tiles: kz < N/2; Q tiles: kz = N/2
+  auto kdx = [&](int b, int r) {
+    const int i = jb + b * (T / C) + 64 * r;
+    return i == H ? 0.f : kf * (float)(i < H ? i : i - N);
+  };
+  float2* __restrict__ P0 = t.isQ ? a.f[0].Q : a.f[0].M;
+  float2* __restrict__ P2 = t.isQ ? a.f[2].Q : a.f[2].M;
+  if (INV) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int r = 0; r < 8; ++r) v[b][r] = cscale(P2[at(b, r)], kdx(b, r));
+    xline8_lines<INV, C>(v, s, tw, jb, col);
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int r = 0; r < 8; ++r) P0[at(b, r)] = v[b][r];
+    __syncthreads();   // s is rewritten by the second transform
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int r = 0; r < 8; ++r) v[b][r] = P2[at(b, r)];
+    xline8_lines<INV, C>(v, s, tw, jb, col);
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int r = 0; r < 8; ++r) P2[at(b, r)] = cscale(v[b][r], kdz);
+  } else {
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int r = 0; r < 8; ++r) v[b][r] = P0[at(b, r)];
+    xline8_lines<INV, C>(v, s, tw, jb, col);
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int r = 0; r < 8; ++r) P0[at(b, r)] = cscale(v[b][r], kdx(b, r));
+    __syncthreads();   // s is rewritten by the second transform
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int r = 0; r < 8; ++r) v[b][r] = P2[at(b, r)];
+    xline8_lines<INV, C>(v, s, tw, jb, col);
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const float2 x = P0[at(b, r)];   // this thread's own first product
+        P0[at(b, r)] = make_float2(fmaf(kdz, v[b][r].x, x.x), fmaf(kdz, v[b][r].y, x.y));
+      }
+  }
 }
 
 template <int N, int C>
@@ -1214,8 +1286,10 @@ __global__ void __launch_bounds__(KIter8<N, C>::T, KIter8<N, C>::kMinBlocks) kit
   const Tile t = tile_of<N, C, AX_Y>(blockIdx.x);
   const int col = threadIdx.x % C, j = threadIdx.x / C;
 
-  // kx and kz are constant along the y line: the x and z terms of k . P are combined before the
-  // transform (FFT_y is linear), and Psi_x, Psi_z are kdx and kdz times one inverse transform
+  // kx and kz are constant along the y line, so the x and z terms of k . P arrive combined,
+  // A = kdx P_x + kdz P_z in the first field (the forward x pass forms it; FFT_y is linear), and
+  // Psi_x, Psi_z leave as one field G with Psi_x = kdx G, Psi_z = kdz G in the third (the inverse
+  // x pass separates them); P_y and Psi_y in the second
   const Geometry& g = a.g;
   int ix, kz;
   if (!t.isQ) { ix = t.a; kz = t.c0 + col; } else { ix = t.c0 + col; kz = H; }
@@ -1224,7 +1298,7 @@ __global__ void __launch_bounds__(KIter8<N, C>::T, KIter8<N, C>::kMinBlocks) kit
   const float kdx = (ix == H) ? 0.f : kx;
   const float kdz = (kz == H) ? 0.f : kzf;
 
-  // every global read of the tile up front: the three components, delta(k), S_(n-1)
+  // every global read of the tile up front: A, P_y, delta(k), S_(n-1)
   float2 v[2][8], dk[8], sp[8];
   {
     const float2* __restrict__ dkp = t.isQ ? a.dk.Q : a.dk.M;
@@ -1232,9 +1306,7 @@ __global__ void __launch_bounds__(KIter8<N, C>::T, KIter8<N, C>::kMinBlocks) kit
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const size_t gi = t.base + (size_t)(j + 64 * r) * t.ls + (size_t)col * t.cs;
-      const float2 px = (t.isQ ? a.f[0].Q : a.f[0].M)[gi];
-      const float2 pz = (t.isQ ? a.f[2].Q : a.f[2].M)[gi];
-      v[0][r] = make_float2(fmaf(kdx, px.x, kdz * pz.x), fmaf(kdx, px.y, kdz * pz.y));
+      v[0][r] = (t.isQ ? a.f[0].Q : a.f[0].M)[gi];
       v[1][r] = (t.isQ ? a.f[1].Q : a.f[1].M)[gi];
       dk[r] = dkp[gi];
       sp[r] = spp[gi];
@@ -1273,15 +1345,13 @@ __global__ void __launch_bounds__(KIter8<N, C>::T, KIter8<N, C>::kMinBlocks) kit
 
   r512_lines3<true, N, C, 2>(v, s, tw, j, col);
   {
-    float2* __restrict__ dx = t.isQ ? a.f[0].Q : a.f[0].M;
     float2* __restrict__ dy = t.isQ ? a.f[1].Q : a.f[1].M;
-    float2* __restrict__ dz = t.isQ ? a.f[2].Q : a.f[2].M;
+    float2* __restrict__ dg = t.isQ ? a.f[2].Q : a.f[2].M;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const size_t gi = t.base + (size_t)(j + 64 * r) * t.ls + (size_t)col * t.cs;
-      dx[gi] = cscale(v[0][r], kdx);
       dy[gi] = v[1][r];
-      dz[gi] = cscale(v[0][r], kdz);
+      dg[gi] = v[0][r];
     }
   }
 
@@ -1454,21 +1524,29 @@ struct MeshImpl {
     return cudaErrorInvalidValue;
   }
 
-  static cudaError_t xlaunch(bool inv, const SArgs& a, cudaStream_t st, int ncomp) {
+  // x lines for N = 512: C = 16 (128-byte rows) or 8 columns (line tile option); pair: the vector
+  // passes of the register-fused k-space path (two CTA kinds along gridDim.y, see xline8_kernel)
+  template <int C, bool PAIR>
+  static cudaError_t xlaunch_c(bool inv, const SArgs& a, cudaStream_t st, int ncomp) {
+    const void* k = inv ? (const void*)xline8_kernel<true, C, PAIR> : (const void*)xline8_kernel<false, C, PAIR>;
+    static bool attr[2] = {false, false};
+    if (!attr[inv]) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XLine8<C>::smem);
+      if (e != cudaSuccess) return e;
+      attr[inv] = true;
+    }
+    void* args[] = {const_cast<SArgs*>(&a)};
+    constexpr int tiles = N * ((N / 2) / C) + N / C;
+    return cudaLaunchKernel(k, dim3(tiles, PAIR ? 2 : ncomp), dim3(XLine8<C>::T), args, XLine8<C>::smem, st);
+  }
+  static cudaError_t xlaunch(bool inv, const SArgs& a, cudaStream_t st, int ncomp, bool pair) {
     if constexpr (N == 512) {
-      constexpr int C = SCols<N, S_FWD>::v;   // 16 adjacent columns (128-byte rows)
-      const void* k = inv ? (const void*)xline8_kernel<true, C> : (const void*)xline8_kernel<false, C>;
-      static bool attr[2] = {false, false};
-      if (!attr[inv]) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XLine8<C>::smem);
-        if (e != cudaSuccess) return e;
-        attr[inv] = true;
-      }
-      void* args[] = {const_cast<SArgs*>(&a)};
-      return cudaLaunchKernel(k, dim3(sblocks<S_FWD>(), ncomp), dim3(XLine8<C>::T), args, XLine8<C>::smem, st);
+      if (pair) return a.narrow ? xlaunch_c<8, true>(inv, a, st, ncomp) : xlaunch_c<16, true>(inv, a, st, ncomp);
+      return xlaunch_c<16, false>(inv, a, st, ncomp);
     }
     return cudaErrorInvalidValue;
   }
+
 
   static cudaError_t spass(int mode, int nc, int axis, const SArgs& a, cudaStream_t st) {
     if (nc < 1 || nc > 3) return cudaErrorInvalidValue;
@@ -1476,8 +1554,11 @@ struct MeshImpl {
     if (mode == S_FWD && axis == AX_Y) return slaunch<S_FWD, 1, AX_Y>(a, st, nc);
     if (mode == S_INV && axis == AX_Y) return slaunch<S_INV, 1, AX_Y>(a, st, nc);
     if constexpr (N == 512) {
+      // the vector x passes next to the register-fused k-space passes carry their representation
+      if ((mode == S_FWD || mode == S_INV) && axis == AX_X && !a.generic && nc == 3)
+        return xlaunch(mode == S_INV, a, st, nc, true);
       if ((mode == S_FWD || mode == S_INV) && axis == AX_X && !a.narrow && !a.generic)
-        return xlaunch(mode == S_INV, a, st, nc);
+        return xlaunch(mode == S_INV, a, st, nc, false);
     }
     if (mode == S_FWD && axis == AX_X)
       return a.narrow ? slaunch<S_FWD, 1, AX_X, 1>(a, st, nc) : slaunch<S_FWD, 1, AX_X>(a, st, nc);
@@ -1502,8 +1583,8 @@ struct MeshImpl {
   }
 
   static const MeshKernels* table() {
-    static const MeshKernels t = {N, kZBlocks, kSBlocks, Plan<N>::kTab, Plan<N / 2>::kTab, &zpass, &spass,
-                                  &build_tables};
+    static const MeshKernels t = {N, kZBlocks, kSBlocks, Plan<N>::kTab, Plan<N / 2>::kTab, N == 512 ? 1 : 0,
+                                  &zpass, &spass, &build_tables};
     return &t;
   }
 };

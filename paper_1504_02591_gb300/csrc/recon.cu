@@ -282,9 +282,12 @@ double zbytes(const recon_handle* h, int mode, int nc, const ZArgs& a) {
   return 2.0 * nc * cfield(h);
 }
 
-double sbytes(const recon_handle* h, int mode, int nc) {
-  if (mode == S_DELTA) return (1.0 + 1.0 + 1.0 + 3.0) * cfield(h);   // delta in, delta(k), S, 3 Psi
-  if (mode == S_ITER) return 9.0 * cfield(h);                         // 3 P + delta(k) + S in; 3 Psi + S out
+double sbytes(const recon_handle* h, int mode, int nc, int axis) {
+  // the register-fused path carries the x and z components of k-space vectors as one field
+  const bool fused = h->mk->kspace_fused && !h->kspace_generic;
+  if (mode == S_DELTA) return (fused ? 5.0 : 6.0) * cfield(h);   // delta in, delta(k), S, 2 or 3 Psi
+  if (mode == S_ITER) return (fused ? 7.0 : 9.0) * cfield(h);    // 2 or 3 P + delta(k) + S in; 2 or 3 Psi + S out
+  if (fused && axis == AX_X && nc == 3) return 5.0 * cfield(h);  // paired: 2 in, 3 out or 3 in, 2 out
   return 2.0 * nc * cfield(h);
 }
 
@@ -294,7 +297,7 @@ recon_status run_z(recon_handle* h, int mode, int nc, const ZArgs& a, int* grid 
 }
 
 recon_status run_s(recon_handle* h, int mode, int nc, int axis, const SArgs& a) {
-  RG_CUDA(timed(h, skind(mode, axis), sbytes(h, mode, nc), [&] { return h->mk->spass(mode, nc, axis, a, h->st); }));
+  RG_CUDA(timed(h, skind(mode, axis), sbytes(h, mode, nc, axis), [&] { return h->mk->spass(mode, nc, axis, a, h->st); }));
   return RECON_OK;
 }
 

@@ -102,6 +102,8 @@ struct MeshKernels {
   int z_blocks;           // upper bound of a Z pass grid (rows / warps per CTA)
   int s_blocks;           // CTAs of a strided pass
   int tab_s, tab_z;       // stage-twiddle table lengths (N-point and N/2-point plans)
+  int kspace_fused;       // register-fused k-space passes with paired vector x passes (unless the
+                          // generic option is set): 7 field transfers per y pass, 5 per x pass
   // persistent Z pass; *grid_out receives the number of CTAs launched (its reduction partials)
   cudaError_t (*zpass)(int mode, int nc, const ZArgs& a, cudaStream_t st, int* grid_out);
   cudaError_t (*spass)(int mode, int nc, int axis, const SArgs& a, cudaStream_t st);
