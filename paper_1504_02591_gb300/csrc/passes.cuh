@@ -465,10 +465,13 @@ __device__ __forceinline__ void zrow_c2r(const float2 (&x)[8], float2 xl, int la
 }
 
 // r2c of one component's row from the real points v[r] = (x[2m], x[2m + 1]), m = l + 32 r: forward
-// transform, split (pairs k, L - k on lanes l and 32 - l), store the half-complex row and Nyquist value.
+// transform, split (pairs k, L - k on lanes l and 32 - l), store the half-complex row and Nyquist value
+// (COPY: sf times them, and sc times them into fc).
+template <bool COPY = false>
 __device__ __forceinline__ void zrow_r2c(float2 (&v)[8], const Field& f, size_t row, int lane, int partner,
                                          const float2* __restrict__ tw, float2* __restrict__ s,
-                                         const float2* __restrict__ tab) {
+                                         const float2* __restrict__ tab, float sf = 1.f, const Field* fc = nullptr,
+                                         float sc = 0.f) {
   constexpr int L = 256;
   float2 Y0[4], Y1[4];
   zrow_fft<false>(v, Y0, Y1, s, tab, lane);
@@ -491,36 +494,47 @@ __device__ __forceinline__ void zrow_r2c(float2 (&v)[8], const Field& f, size_t 
       float2 xk;
       if (k == 0) {
         xk = make_float2(zk.x + zk.y, 0.f);
-        f.Q[row] = make_float2(zk.x - zk.y, 0.f);
+        f.Q[row] = make_float2(COPY ? sf * (zk.x - zk.y) : zk.x - zk.y, 0.f);
+        if (COPY) fc->Q[row] = make_float2(sc * (zk.x - zk.y), 0.f);
       } else {
         const float2 ev = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
         const float2 o = make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y + zm.y));
         xk = cadd(ev, cmul(make_float2(o.y, -o.x), tw[k]));
       }
-      dst[k] = xk;
+      dst[k] = COPY ? cscale(xk, sf) : xk;
+      if (COPY) fc->M[row * L + k] = cscale(xk, sc);
     }
   }
 }
 
-// line of sight at the real points 2m and 2m + 1 of row (dx, dy)
-__device__ __forceinline__ void zrow_rhat(const Geometry& g, float dx, float dy, int m, float (&r0)[3], float (&r1)[3]) {
+// The observer offset d = (dx, dy, dz) of a node and w with r = w d the line of sight (radial: w =
+// 1/|d|, zero at the observer; fixed LOS: d = the LOS vector, w = 1), at the real points 2m and
+// 2m + 1 of a row; dx and dy are the row's.
+__device__ __forceinline__ void zrow_dw(const Geometry& g, float dx, float dy, int m, float& dz0, float& dz1,
+                                        float& w0, float& w1) {
   if (g.los_mode == 1) {
-    r0[0] = r1[0] = g.los.x; r0[1] = r1[1] = g.los.y; r0[2] = r1[2] = g.los.z;
+    dz0 = dz1 = g.los.z;
+    w0 = w1 = 1.f;
     return;
   }
   const int n = g.n;
-  const float dz0 = g.off[2 * n + 2 * m], dz1 = g.off[2 * n + 2 * m + 1];
+  dz0 = g.off[2 * n + 2 * m];
+  dz1 = g.off[2 * n + 2 * m + 1];
   const float q0 = fmaf(dx, dx, fmaf(dy, dy, dz0 * dz0));
   const float q1 = fmaf(dx, dx, fmaf(dy, dy, dz1 * dz1));
-  const float i0 = q0 > 0.f ? rsqrtf(q0) : 0.f;
-  const float i1 = q1 > 0.f ? rsqrtf(q1) : 0.f;
-  r0[0] = dx * i0; r0[1] = dy * i0; r0[2] = dz0 * i0;
-  r1[0] = dx * i1; r1[1] = dy * i1; r1[2] = dz1 * i1;
+  w0 = q0 > 0.f ? rsqrtf(q0) : 0.f;
+  w1 = q1 > 0.f ? rsqrtf(q1) : 0.f;
 }
 
-// Z_PROJ (c2r x3, P = coef (Psi.r) r, r2c x3; or, once the device loop has converged, c2r x3 and
-// the real Psi), Z_RADIAL (c2r x3, u = coef Psi.r as a real row) and Z_WARM (u from the real row
-// plus the upsampled coarse correction, P = u r, r2c x3), one warp per row.
+// The z passes of the register-fused path, one warp per row.  With r = w d, the projection
+// P = coef (Psi.r) r needs only C = dx Psi_x + dy Psi_y and Psi_z (dx, dy are constant along a z
+// row, so C is formed before the transform):  u = coef w (C + dz Psi_z) and P_j = d_j psi with
+// psi = w u.  So the pass transforms two rows each way: P_x = dx psi and P_y = dy psi are scaled
+// copies of one transform, P_z = dz psi the other.
+//   Z_PROJ:   c2r x2, P, r2c x2; once the device loop has converged, c2r x3 and the real Psi.
+//   Z_RADIAL: c2r x2, u as a real row.
+//   Z_WARM:   u from the real row plus the upsampled coarse correction, r2c x2.
+//   Z_USTART: u from the real row, r2c x2.
 template <int N, int MODE>
 __global__ void __launch_bounds__(kZThreads, 2) zfused8_kernel(const ZArgs a) {
   constexpr int L = ZProj8<N>::L;
@@ -539,27 +553,51 @@ __global__ void __launch_bounds__(kZThreads, 2) zfused8_kernel(const ZArgs a) {
 
   for (size_t row = (size_t)blockIdx.x * kZWarps + warp; row < (size_t)N * N; row += (size_t)gridDim.x * kZWarps) {
     const int ix = (int)(row / N), iy = (int)(row % N);
-    const float dx = g.los_mode == 1 ? 0.f : g.off[ix], dy = g.los_mode == 1 ? 0.f : g.off[N + iy];
-    float2 A[3][4], B[3][4];
-    if (MODE == Z_WARM) {
-      // u = u_s + U[corr - ucoarse] (see the generic pass), then P_j = u r_j in A/B order
-      const int fl = a.clevel, nc = N >> fl;
-      const float inv_f = 1.f / (float)(1 << fl);
-      const float tx = ((float)ix + 0.5f) * inv_f - 0.5f, ty = ((float)iy + 0.5f) * inv_f - 0.5f;
-      const float fx = floorf(tx), fy = floorf(ty);
-      const float wx = tx - fx, wy = ty - fy;
-      int x0 = (int)fx, y0 = (int)fy;
-      x0 = x0 < 0 ? x0 + nc : x0;
-      y0 = y0 < 0 ? y0 + nc : y0;
-      const int x1 = x0 + 1 == nc ? 0 : x0 + 1, y1 = y0 + 1 == nc ? 0 : y0 + 1;
-      const size_t r00 = ((size_t)x0 * nc + y0) * nc, r01 = ((size_t)x0 * nc + y1) * nc;
-      const size_t r10 = ((size_t)x1 * nc + y0) * nc, r11 = ((size_t)x1 * nc + y1) * nc;
-      for (int jz = lane; jz < nc; jz += 32) {
-        const float c00 = a.corr[r00 + jz] - a.ucoarse[r00 + jz], c01 = a.corr[r01 + jz] - a.ucoarse[r01 + jz];
-        const float c10 = a.corr[r10 + jz] - a.ucoarse[r10 + jz], c11 = a.corr[r11 + jz] - a.ucoarse[r11 + jz];
-        crow[jz] = (1.f - wx) * ((1.f - wy) * c00 + wy * c01) + wx * ((1.f - wy) * c10 + wy * c11);
+    if (MODE == Z_PROJ && fin) {
+      float2 x[3][8], xl[3], A[3][4], B[3][4];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) zrow_load(a.f[q], row, lane, x[q], xl[q]);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) zrow_c2r(x[q], xl[q], lane, partner, tw, s, tab, A[q], B[q]);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        float2* dst = a.f[q].M + row * L;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          dst[lane + 64 * r] = A[q][r];
+          dst[lane + 32 + 64 * r] = B[q][r];
+        }
       }
-      __syncwarp();
+      continue;
+    }
+    const float dx = g.los_mode == 1 ? g.los.x : g.off[ix], dy = g.los_mode == 1 ? g.los.y : g.off[N + iy];
+    // the rows psi and dz psi at the points l + 64 r (A) and l + 32 + 64 r (B)
+    float2 A[2][4], B[2][4];
+    if (MODE == Z_WARM || MODE == Z_USTART) {
+      float inv_f = 1.f, wx = 0.f, wy = 0.f;
+      int nc = 1;
+      if (MODE == Z_WARM) {
+        // u = u_s + U[corr - ucoarse] (see the generic pass)
+        const int fl = a.clevel;
+        nc = N >> fl;
+        inv_f = 1.f / (float)(1 << fl);
+        const float tx = ((float)ix + 0.5f) * inv_f - 0.5f, ty = ((float)iy + 0.5f) * inv_f - 0.5f;
+        const float fx = floorf(tx), fy = floorf(ty);
+        wx = tx - fx;
+        wy = ty - fy;
+        int x0 = (int)fx, y0 = (int)fy;
+        x0 = x0 < 0 ? x0 + nc : x0;
+        y0 = y0 < 0 ? y0 + nc : y0;
+        const int x1 = x0 + 1 == nc ? 0 : x0 + 1, y1 = y0 + 1 == nc ? 0 : y0 + 1;
+        const size_t r00 = ((size_t)x0 * nc + y0) * nc, r01 = ((size_t)x0 * nc + y1) * nc;
+        const size_t r10 = ((size_t)x1 * nc + y0) * nc, r11 = ((size_t)x1 * nc + y1) * nc;
+        for (int jz = lane; jz < nc; jz += 32) {
+          const float c00 = a.corr[r00 + jz] - a.ucoarse[r00 + jz], c01 = a.corr[r01 + jz] - a.ucoarse[r01 + jz];
+          const float c10 = a.corr[r10 + jz] - a.ucoarse[r10 + jz], c11 = a.corr[r11 + jz] - a.ucoarse[r11 + jz];
+          crow[jz] = (1.f - wx) * ((1.f - wy) * c00 + wy * c01) + wx * ((1.f - wy) * c10 + wy * c11);
+        }
+        __syncwarp();
+      }
       const float2* ur = reinterpret_cast<const float2*>(a.u_in + row * N);
 #pragma unroll
       for (int h = 0; h < 2; ++h)
@@ -567,71 +605,69 @@ __global__ void __launch_bounds__(kZThreads, 2) zfused8_kernel(const ZArgs a) {
         for (int r = 0; r < 4; ++r) {
           const int m = lane + 32 * h + 64 * r;
           float2 uu = ur[m];
-          float add[2];
+          if (MODE == Z_WARM) {
+            float add[2];
 #pragma unroll
-          for (int h2 = 0; h2 < 2; ++h2) {
-            const float tz = ((float)(2 * m + h2) + 0.5f) * inv_f - 0.5f;
-            const float fz = floorf(tz);
-            const float wz = tz - fz;
-            int z0 = (int)fz;
-            z0 = z0 < 0 ? z0 + nc : z0;
-            const int z1 = z0 + 1 == nc ? 0 : z0 + 1;
-            add[h2] = (1.f - wz) * crow[z0] + wz * crow[z1];
+            for (int h2 = 0; h2 < 2; ++h2) {
+              const float tz = ((float)(2 * m + h2) + 0.5f) * inv_f - 0.5f;
+              const float fz = floorf(tz);
+              const float wz = tz - fz;
+              int z0 = (int)fz;
+              z0 = z0 < 0 ? z0 + nc : z0;
+              const int z1 = z0 + 1 == nc ? 0 : z0 + 1;
+              add[h2] = (1.f - wz) * crow[z0] + wz * crow[z1];
+            }
+            uu.x += add[0];
+            uu.y += add[1];
           }
-          uu.x += add[0];
-          uu.y += add[1];
-          float r0[3], r1[3];
-          zrow_rhat(g, dx, dy, m, r0, r1);
-#pragma unroll
-          for (int q = 0; q < 3; ++q) (h ? B : A)[q][r] = make_float2(uu.x * r0[q], uu.y * r1[q]);
+          float dz0, dz1, w0, w1;
+          zrow_dw(g, dx, dy, m, dz0, dz1, w0, w1);
+          const float p0 = uu.x * w0, p1 = uu.y * w1;
+          (h ? B : A)[0][r] = make_float2(p0, p1);
+          (h ? B : A)[1][r] = make_float2(dz0 * p0, dz1 * p1);
         }
-      __syncwarp();   // crow is rewritten by the next row
+      if (MODE == Z_WARM) __syncwarp();   // crow is rewritten by the next row
     } else {
-      // all three rows' loads in flight before the first transform
+      // all three rows' loads in flight before the first transform; C = dx Psi_x + dy Psi_y
       float2 x[3][8], xl[3];
 #pragma unroll
       for (int q = 0; q < 3; ++q) zrow_load(a.f[q], row, lane, x[q], xl[q]);
 #pragma unroll
-      for (int q = 0; q < 3; ++q) zrow_c2r(x[q], xl[q], lane, partner, tw, s, tab, A[q], B[q]);
-      if (MODE == Z_PROJ && fin) {
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          float2* dst = a.f[q].M + row * L;
-#pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            dst[lane + 64 * r] = A[q][r];
-            dst[lane + 32 + 64 * r] = B[q][r];
-          }
-        }
-        continue;
-      }
+      for (int r = 0; r < 8; ++r)
+        x[0][r] = make_float2(fmaf(dx, x[0][r].x, dy * x[1][r].x), fmaf(dx, x[0][r].y, dy * x[1][r].y));
+      xl[0] = make_float2(fmaf(dx, xl[0].x, dy * xl[1].x), fmaf(dx, xl[0].y, dy * xl[1].y));
+      zrow_c2r(x[0], xl[0], lane, partner, tw, s, tab, A[0], B[0]);
+      zrow_c2r(x[2], xl[2], lane, partner, tw, s, tab, A[1], B[1]);
       // u = coef (Psi . r) at the real points 2m, 2m + 1 of the complex point m (Eq. Nusser)
 #pragma unroll
       for (int h = 0; h < 2; ++h)
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           const int m = lane + 32 * h + 64 * r;
-          float r0[3], r1[3];
-          zrow_rhat(g, dx, dy, m, r0, r1);
-          const float2 p0 = h ? B[0][r] : A[0][r], p1 = h ? B[1][r] : A[1][r], p2 = h ? B[2][r] : A[2][r];
-          const float u0 = a.coef * fmaf(p0.x, r0[0], fmaf(p1.x, r0[1], p2.x * r0[2]));
-          const float u1 = a.coef * fmaf(p0.y, r1[0], fmaf(p1.y, r1[1], p2.y * r1[2]));
+          float dz0, dz1, w0, w1;
+          zrow_dw(g, dx, dy, m, dz0, dz1, w0, w1);
+          const float2 c = h ? B[0][r] : A[0][r], pz = h ? B[1][r] : A[1][r];
+          const float u0 = a.coef * (w0 * fmaf(dz0, pz.x, c.x));
+          const float u1 = a.coef * (w1 * fmaf(dz1, pz.y, c.y));
           if (MODE == Z_RADIAL) {
             reinterpret_cast<float2*>(a.u_out + row * N)[m] = make_float2(u0, u1);
           } else {
-#pragma unroll
-            for (int q = 0; q < 3; ++q) (h ? B : A)[q][r] = make_float2(u0 * r0[q], u1 * r1[q]);
+            const float p0 = u0 * w0, p1 = u1 * w1;
+            (h ? B : A)[0][r] = make_float2(p0, p1);
+            (h ? B : A)[1][r] = make_float2(dz0 * p0, dz1 * p1);
           }
         }
       if (MODE == Z_RADIAL) continue;
     }
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      // the points l + 32 r of the real row: A[r/2] (r even), B[(r-1)/2] (r odd)
+    {
+      // the points l + 32 r of the real rows: A[r/2] (r even), B[(r-1)/2] (r odd)
       float2 v[8];
 #pragma unroll
-      for (int r = 0; r < 8; ++r) v[r] = (r & 1) ? B[q][r >> 1] : A[q][r >> 1];
-      zrow_r2c(v, a.f[q], row, lane, partner, tw, s, tab);
+      for (int r = 0; r < 8; ++r) v[r] = (r & 1) ? B[0][r >> 1] : A[0][r >> 1];
+      zrow_r2c<true>(v, a.f[0], row, lane, partner, tw, s, tab, dx, &a.f[1], dy);   // dx psi, dy psi
+#pragma unroll
+      for (int r = 0; r < 8; ++r) v[r] = (r & 1) ? B[1][r >> 1] : A[1][r >> 1];
+      zrow_r2c(v, a.f[2], row, lane, partner, tw, s, tab);                      // dz psi
     }
   }
 }
@@ -1467,6 +1503,7 @@ struct MeshImpl {
         if (mode == Z_PROJ) return zfused<Z_PROJ>(a, st, grid_out);
         if (mode == Z_RADIAL) return zfused<Z_RADIAL>(a, st, grid_out);
         if (mode == Z_WARM && a.clevel >= 1) return zfused<Z_WARM>(a, st, grid_out);
+        if (mode == Z_USTART) return zfused<Z_USTART>(a, st, grid_out);
       }
     }
 #define RG_Z(M_, NC_) \
