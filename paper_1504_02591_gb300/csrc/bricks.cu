@@ -19,23 +19,23 @@ constexpr uint32_t kFracMask = kFracOne - 1;
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-__device__ __forceinline__ uint32_t pack_axis(double u, int n) {
-  const double fl = floor(u);
-  long long c = (long long)fl;
-  uint32_t f = (uint32_t)((u - fl) * (double)kFracOne + 0.5);
-  if (f == kFracOne) {
-    f = 0;
-    c += 1;
-  }
-  c %= n;
-  if (c < 0) c += n;
-  return ((uint32_t)c << kFracBits) | f;
+// Node index and 21-bit fraction of a grid coordinate u, from t = u 2^21 (computed as x times
+// scale 2^21: the same rounding as u itself).  T = t rounded to the nearest integer (ties to even);
+// node = floor(T / 2^21) (arithmetic shift, also for negative u), fraction = T mod 2^21, so a
+// fraction that rounds up to a whole cell carries into the node.  Two float64 operations per axis:
+// float64 runs at a small fraction of the float32 rate on this GPU.
+__device__ __forceinline__ uint32_t pack_axis(double t, int n) {
+  const long long T = __double2ll_rn(t);
+  int c = (int)(T >> kFracBits);
+  if (c < 0 || c >= n) c = ((c % n) + n) % n;   // outside [0, L): periodic image
+  return ((uint32_t)c << kFracBits) | (uint32_t)(T & (long long)kFracMask);
 }
 
 template <typename PT>
-__device__ __forceinline__ void pack(const PT* __restrict__ pos, long long p, double scale, int n, uint32_t (&q)[3]) {
+__device__ __forceinline__ void pack(const PT* __restrict__ pos, long long p, double scale21, int n,
+                                     uint32_t (&q)[3]) {
 #pragma unroll
-  for (int a = 0; a < 3; ++a) q[a] = pack_axis((double)pos[3 * p + a] * scale, n);
+  for (int a = 0; a < 3; ++a) q[a] = pack_axis((double)pos[3 * p + a] * scale21, n);
 }
 
 __device__ __forceinline__ uint32_t brick_key(const uint32_t (&q)[3], int nb) {
@@ -52,9 +52,10 @@ __global__ void __launch_bounds__(256) count_kernel(const PT* __restrict__ pos, 
                                                     long long np, double scale, int n, int nb,
                                                     uint32_t* __restrict__ hist, uint32_t* __restrict__ key,
                                                     uint32_t* __restrict__ rank, uint4* __restrict__ pre) {
+  const double scale21 = scale * (double)kFracOne;   // exact: a power of two
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x) {
     uint32_t q[3];
-    pack(pos, p, scale, n, q);
+    pack(pos, p, scale21, n, q);
     const uint32_t k = brick_key(q, nb);
     key[p] = k;
     rank[p] = atomicAdd(hist + k, 1u);
@@ -167,10 +168,11 @@ __global__ void __launch_bounds__(kWarps * 32) deposit_kernel(const uint32_t* __
     for (int j = lane; j < kBrickNodes; j += 32) tile[j] = 0.f;
     __syncwarp();
     const int ox = (b / (nb * nb)) * kBrick, oy = ((b / nb) % nb) * kBrick, oz = (b % nb) * kBrick;
+    float bw = 0.f;   // this lane's weight in the brick (float64 once per brick, not per particle)
     for (uint32_t i = s0 + lane; i < s1; i += 32) {
       const uint4 r = rec[i];
       const float wv = __uint_as_float(r.w);
-      wsum += wv;
+      bw += wv;
       const int lx = (int)(r.x >> kFracBits) - ox, ly = (int)(r.y >> kFracBits) - oy, lz = (int)(r.z >> kFracBits) - oz;
       const float tx = (float)(r.x & kFracMask) * inv, ty = (float)(r.y & kFracMask) * inv,
                   tz = (float)(r.z & kFracMask) * inv;
@@ -186,6 +188,7 @@ __global__ void __launch_bounds__(kWarps * 32) deposit_kernel(const uint32_t* __
       atomicAdd(tile + c + DX + DY, wx1 * wy1 * wz0);
       atomicAdd(tile + c + DX + DY + 1, wx1 * wy1 * wz1);
     }
+    wsum += bw;
     __syncwarp();
     for (int j = lane; j < kBrickNodes; j += 32) {
       const float v = tile[j];
