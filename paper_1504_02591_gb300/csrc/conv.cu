@@ -77,10 +77,10 @@ __global__ void __launch_bounds__(256) conv_kernel(const ConvArgs a) {
   }
 }
 
-// Register-blocked form for kernels of at most KT taps: the line is staged with its periodic
-// continuation (s[p] = x[(p + t0) mod n], p < n + KT + V), the taps sit in registers (zero past
-// ntap), and each thread slides over V consecutive outputs of one column, so every staged value is
-// read once per V outputs instead of once per output.
+// Register-blocked form for kernels of at most KT taps, one field per CTA (blockIdx.y): the line is
+// staged with its periodic continuation (s[p] = x[(p + t0) mod n], p < n + KT + V), the taps sit in
+// registers (zero past ntap), and each thread slides over V consecutive outputs of one column, so
+// every staged value is read once per V outputs instead of once per output.
 template <int C, int KT, int V>
 __global__ void __launch_bounds__(256) conv_blocked_kernel(const ConvArgs a) {
   extern __shared__ float csm[];
@@ -103,23 +103,23 @@ __global__ void __launch_bounds__(256) conv_blocked_kernel(const ConvArgs a) {
     base = (size_t)other * nn * nn + z0;
     ls = nn;
   }
+  const int q = blockIdx.y;
+  const bool count = a.count && q == a.nf - 1;
   float cnt = 0.f;
-  for (int q = 0; q < a.nf; ++q) {
+  {
     const float* src = a.f[q];
-    float* sq = csm + (size_t)q * len * C;
     for (int e = threadIdx.x; e < len * (C / 4); e += T) {
       const int p = e / (C / 4), c4 = e % (C / 4);
       int i = (p + a.t0) % n;
       if (i < 0) i += n;
       const float4 v = *reinterpret_cast<const float4*>(src + base + (size_t)i * ls + 4 * c4);
-      if (a.count && q == a.nf - 1 && p < n) cnt += (v.x > 0.f) + (v.y > 0.f) + (v.z > 0.f) + (v.w > 0.f);
-      *reinterpret_cast<float4*>(sq + (size_t)p * C + 4 * c4) = v;
+      if (count && p < n) cnt += (v.x > 0.f) + (v.y > 0.f) + (v.z > 0.f) + (v.w > 0.f);
+      *reinterpret_cast<float4*>(csm + (size_t)p * C + 4 * c4) = v;
     }
   }
   __syncthreads();
   const int c = threadIdx.x % C;
-  for (int q = 0; q < a.nf; ++q) {
-    const float* sq = csm + (size_t)q * len * C;
+  {
     float* dst = a.f[q];
     for (int i0 = (threadIdx.x / C) * V; i0 < n; i0 += (T / C) * V) {
       float acc[V];
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(256) conv_blocked_kernel(const ConvArgs a) {
       for (int v = 0; v < V; ++v) acc[v] = 0.f;
 #pragma unroll
       for (int j = 0; j < KT + V - 1; ++j) {
-        const float x = sq[(size_t)(i0 + j) * C + c];
+        const float x = csm[(size_t)(i0 + j) * C + c];
 #pragma unroll
         for (int v = 0; v < V; ++v)
           if (j - v >= 0 && j - v < KT) acc[v] = fmaf(tp[j - v], x, acc[v]);
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(256) conv_blocked_kernel(const ConvArgs a) {
       for (int v = 0; v < V; ++v) dst[base + (size_t)(i0 + v) * ls + c] = acc[v];
     }
   }
-  if (a.count) {
+  if (count) {
     __shared__ double sh[8];
     double v = cnt;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -153,7 +153,9 @@ __global__ void __launch_bounds__(256) conv_blocked_kernel(const ConvArgs a) {
 
 constexpr int kConvV = 8;
 
-int conv_cols(int n) { return n >= 1024 ? 8 : 16; }
+// Adjacent z columns per tile: 128-byte rows where the staged line of a field still leaves room for
+// three CTAs per SM.
+int conv_cols(int n) { return n >= 1024 ? 8 : (n >= 256 ? 32 : 16); }
 
 int conv_blocks(int n) { return n * (n / conv_cols(n)); }
 
@@ -164,7 +166,7 @@ static int conv_kt(int n, int ntap) {
 
 size_t conv_smem(int n, int nf, int ntap) {
   const int kt = conv_kt(n, ntap);
-  if (kt) return sizeof(float) * (size_t)nf * (n + kt + kConvV) * conv_cols(n);
+  if (kt) return sizeof(float) * (size_t)(n + kt + kConvV) * conv_cols(n);   // one field per CTA
   return sizeof(float) * (((size_t)ntap + 3) / 4 * 4 + (size_t)nf * n * conv_cols(n));
 }
 
@@ -174,15 +176,17 @@ cudaError_t launch_conv(const ConvArgs& a, cudaStream_t st) {
   const int kt = conv_kt(a.n, a.ntap);
   const void* k;
   if (kt == 32)
-    k = (C == 16) ? (const void*)conv_blocked_kernel<16, 32, kConvV> : (const void*)conv_blocked_kernel<8, 32, kConvV>;
+    k = (C == 32) ? (const void*)conv_blocked_kernel<32, 32, kConvV>
+                  : (C == 16) ? (const void*)conv_blocked_kernel<16, 32, kConvV> : (const void*)conv_blocked_kernel<8, 32, kConvV>;
   else if (kt == 64)
-    k = (C == 16) ? (const void*)conv_blocked_kernel<16, 64, kConvV> : (const void*)conv_blocked_kernel<8, 64, kConvV>;
+    k = (C == 32) ? (const void*)conv_blocked_kernel<32, 64, kConvV>
+                  : (C == 16) ? (const void*)conv_blocked_kernel<16, 64, kConvV> : (const void*)conv_blocked_kernel<8, 64, kConvV>;
   else
-    k = (C == 16) ? (const void*)conv_kernel<16> : (const void*)conv_kernel<8>;
+    k = (C == 32) ? (const void*)conv_kernel<32> : (C == 16) ? (const void*)conv_kernel<16> : (const void*)conv_kernel<8>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   void* args[] = {const_cast<ConvArgs*>(&a)};
-  return cudaLaunchKernel(k, dim3(conv_blocks(a.n)), dim3(256), args, smem, st);
+  return cudaLaunchKernel(k, dim3(conv_blocks(a.n), kt ? a.nf : 1), dim3(256), args, smem, st);
 }
 
 }  // namespace rg
