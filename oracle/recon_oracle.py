@@ -269,12 +269,15 @@ def particle_rhat(pos, observer, los_mode: int):
     return out
 
 
-def shift_vectors(psi, pos, L: float, f: float, observer, los_mode: int, is_galaxy: bool):
-    """Shift d = -[Psi + f (Psi.r) r] for galaxies and d = -Psi for randoms, Psi CIC-interpolated."""
+def shift_vectors(psi, pos, L: float, f: float, observer, los_mode: int, is_galaxy: bool, periodic: bool = False):
+    """Shift d = -[Psi + f (Psi.r) r] for galaxies and d = -Psi for randoms, Psi CIC-interpolated.
+
+    In a periodic box a position stands for its image in [0, L): the line of sight runs from the
+    observer to that image (the interpolation is periodic either way)."""
     p = cic_gather(psi, pos, L)
     if not is_galaxy:
         return -p
-    rh = particle_rhat(pos, observer, los_mode)
+    rh = particle_rhat(np.mod(pos, L) if periodic else pos, observer, los_mode)
     u = (p * rh).sum(1)[:, None]
     return -(p + f * u * rh)
 
@@ -339,7 +342,7 @@ def reconstruct(params: dict, gal_pos, gal_w=None, ran_pos=None, ran_w=None,
     if shift:
         periodic = bool(params.get("periodic", False))
         dg = shift_vectors(psi, gal_pos, L, params["f"], params["observer"],
-                           params.get("los_mode", LOS_RADIAL), True)
+                           params.get("los_mode", LOS_RADIAL), True, periodic)
         out["shift_g"] = dg
         out["pos_g"] = shifted_positions(gal_pos, dg, L, periodic)
         if ran_pos is not None:

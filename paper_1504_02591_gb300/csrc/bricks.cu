@@ -1,7 +1,7 @@
 // bricks.cu: brick-sorted particle pipeline for the CIC deposit and the reconstruction shift.
 //
 // Particles are packed into 16-byte records (per axis: node index << 21 | 21-bit fraction of a cell,
-// rounded to nearest; then the weight) and counting-sorted by their 8^3-cell brick.  The deposit
+// rounded down; then the weight) and counting-sorted by their 8^3-cell brick.  The deposit
 // then gives each brick to one warp, which accumulates the CIC weights (Sec. 3 mass assignment,
 // here cloud-in-cell) of its particles into a 9^3 node tile in shared memory and flushes the tile
 // with one global atomic per non-zero node.  The shift (Sec. 1, reversing Eq. Lagrange) stages the
@@ -20,12 +20,13 @@ constexpr uint32_t kFracMask = kFracOne - 1;
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Node index and 21-bit fraction of a grid coordinate u, from t = u 2^21 (computed as x times
-// scale 2^21: the same rounding as u itself).  T = t rounded to the nearest integer (ties to even);
-// node = floor(T / 2^21) (arithmetic shift, also for negative u), fraction = T mod 2^21, so a
-// fraction that rounds up to a whole cell carries into the node.  Two float64 operations per axis:
-// float64 runs at a small fraction of the float32 rate on this GPU.
+// scale 2^21: the same rounding as u itself).  T = floor(t); node = T >> 21 = floor(u)
+// (arithmetic shift, also for negative u), fraction = T mod 2^21.  Rounding down keeps a point just
+// below the periodic boundary on its own side (its image stays below L, where its line of sight
+// points).  Two float64 operations per axis: float64 runs at a small fraction of the float32 rate
+// on this GPU.
 __device__ __forceinline__ uint32_t pack_axis(double t, int n) {
-  const long long T = __double2ll_rn(t);
+  const long long T = __double2ll_rd(t);
   int c = (int)(T >> kFracBits);
   if (c < 0 || c >= n) c = ((c % n) + n) % n;   // outside [0, L): periodic image
   return ((uint32_t)c << kFracBits) | (uint32_t)(T & (long long)kFracMask);

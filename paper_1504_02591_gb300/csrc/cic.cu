@@ -103,7 +103,10 @@ __global__ void __launch_bounds__(256) shift_kernel(const PT* __restrict__ pos, 
       if (a.los_mode == 1) {
         rx = a.los.x; ry = a.los.y; rz = a.los.z;
       } else {
-        const float dx = (float)(x0 - a.obs[0]), dy = (float)(x1 - a.obs[1]), dz = (float)(x2 - a.obs[2]);
+        // offset of the particle's image in [0, L) from the observer, as the brick-sorted path forms it
+        const int n = a.n;
+        const float dx = fmaf(t[0], a.H, a.off[i0[0]]), dy = fmaf(t[1], a.H, a.off[n + i0[1]]),
+                    dz = fmaf(t[2], a.H, a.off[2 * n + i0[2]]);
         const float q = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const float ir = q > 0.f ? rsqrtf(q) : 0.f;
         rx = dx * ir; ry = dy * ir; rz = dz * ir;
@@ -135,21 +138,47 @@ __global__ void __launch_bounds__(256) shift_kernel(const PT* __restrict__ pos, 
 }
 
 // Sum nq interleaved partial columns: red[dst + q] (=|+=) sum_b partials[b * nq + q].
-// One block sums the per-block partials (nq <= 4 quantities, interleaved), all quantities in one
-// sweep with independent loads in flight; the order of the sums is fixed.
+// Sums the per-block partials (nq <= 4 quantities, interleaved) in a fixed order.  With scratch
+// (kFinalizeBlocks x 4 doubles and a zeroed counter), gridDim.x blocks each sum a contiguous range
+// and the last block to finish adds the block sums in block order and resets the counter: float64
+// adds run at a few per clock on one SM, so one block summing tens of thousands of partials takes
+// tens of microseconds.  Without scratch, one block sums everything.
 constexpr int kFinalizeThreads = 1024;
 __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(const double* __restrict__ partials, int nblocks,
                                                                     int nq, double* __restrict__ red, int dst,
-                                                                    int accumulate) {
+                                                                    int accumulate, double* __restrict__ bsum,
+                                                                    unsigned int* __restrict__ counter) {
+  const int per = (nblocks + gridDim.x - 1) / gridDim.x;
+  const int b0 = blockIdx.x * per, b1 = min(nblocks, b0 + per);
   double s[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll 4
-  for (int b = threadIdx.x; b < nblocks; b += kFinalizeThreads)
+  for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x)
 #pragma unroll
     for (int q = 0; q < 4; ++q)
       if (q < nq) s[q] += partials[(size_t)b * nq + q];
-  for (int q = 0; q < nq; ++q) {
-    const double t = block_sum_d(s[q]);
-    if (threadIdx.x == 0) red[dst + q] = accumulate ? red[dst + q] + t : t;
+  double t[4];
+  for (int q = 0; q < nq; ++q) t[q] = block_sum_d(s[q]);
+  if (gridDim.x == 1) {
+    if (threadIdx.x == 0)
+      for (int q = 0; q < nq; ++q) red[dst + q] = accumulate ? red[dst + q] + t[q] : t[q];
+    return;
+  }
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < nq; ++q) bsum[4 * blockIdx.x + q] = t[q];
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    const volatile double* vb = bsum;
+    for (int q = 0; q < nq; ++q) {
+      double r = 0.0;
+      for (int g = 0; g < (int)gridDim.x; ++g) r += vb[4 * g + q];
+      red[dst + q] = accumulate ? red[dst + q] + r : r;
+    }
+    *counter = 0u;
   }
 }
 
@@ -181,9 +210,14 @@ cudaError_t launch_shift(const void* pos, int dtype, long long np, const ShiftAr
 }
 
 cudaError_t launch_finalize(const double* partials, int nblocks, int nq, double* red, int dst, int accumulate,
-                            cudaStream_t st) {
+                            cudaStream_t st, double* bsum, unsigned int* counter) {
   if (nq < 1 || nq > 4) return cudaErrorInvalidValue;
-  finalize_kernel<<<1, kFinalizeThreads, 0, st>>>(partials, nblocks, nq, red, dst, accumulate);
+  int blocks = 1;
+  if (bsum && counter) {   // about 1024 partials per block, at most kFinalizeBlocks blocks
+    blocks = (nblocks + 1023) / 1024;
+    blocks = blocks < 1 ? 1 : (blocks > kFinalizeBlocks ? kFinalizeBlocks : blocks);
+  }
+  finalize_kernel<<<blocks, kFinalizeThreads, 0, st>>>(partials, nblocks, nq, red, dst, accumulate, bsum, counter);
   return cudaGetLastError();
 }
 

@@ -14,7 +14,8 @@ struct ShiftArgs {
   float f;               // growth rate of the galaxy RSD term
   int los_mode;          // 0 radial, 1 fixed
   float3 los;            // fixed LOS unit vector
-  double obs[3];         // observer position (radial)
+  const float* off;      // 3 N node offsets from the observer, per axis (radial)
+  float H;               // cell size: a particle's offset is off[node] + t H, its image in [0, L)
   int periodic;
   float* shift;          // (n, 3) out
   double* pos_out;       // (n, 3) out or null
@@ -25,8 +26,12 @@ constexpr int kDepositBlocks = 152 * 8;
 cudaError_t launch_deposit(const void* pos, int dtype, const float* w, long long np, int n, double L,
                            float* rho, double* partials, int blocks, cudaStream_t st);
 cudaError_t launch_shift(const void* pos, int dtype, long long np, const ShiftArgs& a, cudaStream_t st);
+// red[dst + q] (=|+=) the sum over b < nblocks of partials[b nq + q], q < nq <= 4, in a fixed order.
+// bsum (kFinalizeBlocks x 4 doubles) and counter (zeroed; left zeroed) let several blocks share the
+// sum; with nulls one block does it.
+constexpr int kFinalizeBlocks = 64;
 cudaError_t launch_finalize(const double* partials, int nblocks, int nq, double* red, int dst, int accumulate,
-                            cudaStream_t st);
+                            cudaStream_t st, double* bsum = nullptr, unsigned int* counter = nullptr);
 cudaError_t launch_add_scalar(float* x, size_t n, float v, cudaStream_t st);
 
 }  // namespace rg

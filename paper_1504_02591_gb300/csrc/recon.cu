@@ -76,7 +76,8 @@ Layout layout_for(int n) {
   l.tabz = align256((size_t)mk->tab_z * sizeof(float2) + 16);
   l.off = align256((size_t)3 * n * sizeof(float));
   l.taps = align256((size_t)n * sizeof(float));
-  l.red = align256(64 * sizeof(double) + sizeof(LoopState));
+  // reduction slots, the loop state, the finalize block sums and counter
+  l.red = align256(64 * sizeof(double) + sizeof(LoopState) + kFinalizeBlocks * 4 * sizeof(double) + 64);
   size_t nb = (size_t)mk->z_blocks;
   if ((size_t)mk->s_blocks > nb) nb = mk->s_blocks;
   if ((size_t)kDepositBlocks > nb) nb = kDepositBlocks;
@@ -136,6 +137,8 @@ struct recon_handle {
   cudaEvent_t ev_in[2] = {}, ev_out[2] = {}, ev_free[2] = {};
   int use_graph = 1;
   double* partials = nullptr;
+  double* fin_bsum = nullptr;          // finalize: per-block sums (inside the red region)
+  unsigned int* fin_counter = nullptr; // finalize: blocks done (zero between launches)
   char* stage = nullptr;
   BrickBuffers bb{};       // brick sort of one particle chunk
   const MeshKernels* mk = nullptr;
@@ -303,7 +306,7 @@ recon_status run_s(recon_handle* h, int mode, int nc, int axis, const SArgs& a) 
 
 recon_status finalize(recon_handle* h, int nblocks, int nq, int dst, int accumulate) {
   RG_CUDA(timed(h, RECON_K_OTHER, 8.0 * nblocks * nq, [&] {
-    return launch_finalize(h->partials, nblocks, nq, h->red, dst, accumulate, h->st); }));
+    return launch_finalize(h->partials, nblocks, nq, h->red, dst, accumulate, h->st, h->fin_bsum, h->fin_counter); }));
   return RECON_OK;
 }
 
@@ -569,6 +572,8 @@ recon_status recon_create(const recon_params* p, void* stream, void* workspace, 
   b += h->lay.taps;
   h->red = (double*)b;
   h->loop = reinterpret_cast<LoopState*>(h->red + 64);
+  h->fin_bsum = reinterpret_cast<double*>(h->loop + 1);
+  h->fin_counter = reinterpret_cast<unsigned int*>(h->fin_bsum + kFinalizeBlocks * 4);
   b += h->lay.red;
   h->partials = (double*)b;
   b += h->lay.partials;
@@ -1056,7 +1061,8 @@ recon_status recon_shift(recon_handle* h, const recon_catalog* cat, int is_galax
   a.f = (float)h->p.f;
   a.los_mode = h->p.los_mode;
   a.los = h->geo.los;
-  for (int q = 0; q < 3; ++q) a.obs[q] = h->p.observer[q];
+  a.off = h->off;
+  a.H = (float)(h->L / h->n);
   a.periodic = h->p.periodic;
   const size_t es = elem_size(cat->dtype);
   BrickShiftArgs ba{};

@@ -228,13 +228,17 @@ def test_retained_sort_shift(B, shell_case, host):
     out = {}
     for reuse in (0, 1):
         r = B.Recon.from_mock(m)
+        # both runs deposit through the brick sort (the same fixed-point positions, so the same mask
+        # decisions); the first sorts again for its shifts, the second reuses the deposit's order
+        r.set_option(B.OPT_DEPOSIT_PATH, B.PATH_SORTED)
         if reuse:
-            r.set_option(B.OPT_DEPOSIT_PATH, B.PATH_SORTED)
             r.set_option(B.OPT_REUSE_SORT, 1)
         r.deposit(gal, None, ran, None)
         r.smooth()
-        n_it, rel, st = r.iterate(B.START_FFTA, 1e-6, 40)
-        assert st == B.OK
+        # a fixed number of updates: both runs stop at the same one (with a tolerance the stopping
+        # update itself may differ, a 1e-6 relative change of Psi)
+        n_it, rel, st = r.iterate(B.START_FFTA, 0.0, 12)
+        assert st == B.OK and n_it == 12
         sg = r.shift(gal, True)
         sorts = r.timing()["sort"][0]
         sr = r.shift(ran, False)
@@ -243,7 +247,8 @@ def test_retained_sort_shift(B, shell_case, host):
         out[reuse] = (np.asarray(sg.cpu() if hasattr(sg, "cpu") else sg),
                       np.asarray(sr.cpu() if hasattr(sr, "cpu") else sr))
         r.close()
-    # the two deposits differ only in the order of their float32 sums
+    # the two deposits differ only in the order of their float32 sums; the galaxy shifts in path
+    # (sorted, then direct)
     assert np.abs(out[1][0] - out[0][0]).max() <= SHIFT_TOL
     assert np.abs(out[1][1] - out[0][1]).max() <= SHIFT_TOL
 
@@ -305,4 +310,46 @@ def test_ragged_particle_counts(B):
     assert abs(rho_r.astype(np.float64).sum() - len(ran)) <= 1e-5 * len(ran)
     want = O.cic_deposit(ran, None, 32, 500.0)
     assert rel_l2(rho_r, want) < 1e-6
+    r.close()
+
+
+def test_particle_edge_positions(B):
+    """Positions on nodes, just below a node (fractions that round up to a whole cell), at 0, -0 and
+    L, negative and beyond the box (periodic images, whose line of sight runs to the image in
+    [0, L)): both deposit and both shift paths against the oracle's CIC on the same positions."""
+    n, L = 32, 500.0
+    h = L / n
+    tiny = h * 2.0 ** -23                      # rounds up to a whole cell at 21 fraction bits
+    special = np.array([0.0, -0.0, 3 * h, 4 * h - tiny, 7.3 * h, L - 1e-9, L, -1e-9, -0.5 * L - 0.3,
+                        L + 3.7, 2 * L - 1e-7, 3.5 * L, (n - 1) * h + 0.5 * h])
+    grid = np.stack(np.meshgrid(special, special, special, indexing="ij"), -1).reshape(-1, 3)
+    rng = np.random.default_rng(11)
+    # the special positions inside a uniform catalogue, so that Psi has a realistic size (the shift
+    # error of the fixed-point line of sight scales with it)
+    gal = np.concatenate([rng.uniform(0, L, (100_000, 3)), grid])
+    ran = rng.uniform(0, L, (200_000, 3))
+    r = B.Recon(n, L, 2.0, 0.7, 20.0, (250.0, 250.0, 250.0), periodic=True)
+    psi = None
+    shifts = {}
+    for path in (0, 1):
+        r.set_option(B.OPT_DEPOSIT_PATH, path)
+        r.set_option(B.OPT_SHIFT_PATH, path)
+        r.deposit(torch.from_numpy(gal).cuda(), None, torch.from_numpy(ran).cuda(), None)
+        rho_g = r.get_field(B.FIELD_RHO_G).cpu().numpy()
+        assert abs(rho_g.astype(np.float64).sum() - len(gal)) <= 1e-5 * len(gal)
+        assert rel_l2(rho_g, O.cic_deposit(gal, None, n, L)) < 1e-6, path
+        edge = rho_g - O.cic_deposit(gal[:100_000], None, n, L)   # the special positions' share
+        assert rel_l2(edge, O.cic_deposit(grid, None, n, L)) < 1e-5, path
+        r.smooth()
+        r.iterate(2, 0.0, 3)
+        psi = r.get_psi().cpu().numpy().astype(np.float64)
+        sg, pg = r.shift(torch.from_numpy(grid).cuda(), True, want_pos=True)
+        sr = r.shift(torch.from_numpy(grid).cuda(), False)
+        dg = O.shift_vectors(psi, grid, L, 0.7, (250.0, 250.0, 250.0), 0, True, periodic=True)
+        dr = O.shift_vectors(psi, grid, L, 0.7, (250.0, 250.0, 250.0), 0, False)
+        assert np.abs(sg.cpu().numpy() - dg).max() <= SHIFT_TOL, path
+        assert np.abs(sr.cpu().numpy() - dr).max() <= SHIFT_TOL, path
+        assert np.abs(pg.cpu().numpy() - O.shifted_positions(grid, dg, L, True)).max() <= SHIFT_TOL, path
+        shifts[path] = sr.cpu().numpy()
+    assert np.abs(shifts[0] - shifts[1]).max() <= SHIFT_TOL
     r.close()

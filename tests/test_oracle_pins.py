@@ -236,6 +236,28 @@ def test_overdensity_zero_when_galaxies_trace_randoms():
     assert thr == pytest.approx(0.01 * 10.0 / 500)
 
 
+def test_shift_periodic_images():
+    """Periodic box: moving a tracer by whole box lengths changes neither its interpolated Psi nor,
+    with the image reading, its line of sight, so the shifts are identical; without it the radial
+    LOS of an out-of-box image differs."""
+    n, L, f = 8, 200.0, 0.74
+    rng = np.random.default_rng(10)
+    psi = rng.standard_normal((3, n, n, n))
+    pos = rng.uniform(0, L, (200, 3))
+    k = rng.integers(-3, 4, (200, 3)).astype(np.float64)
+    k[0] = (1, 0, 0)
+    img = pos + L * k
+    obs = (100.0, 100.0, 100.0)
+    d0 = O.shift_vectors(psi, pos, L, f, obs, O.LOS_RADIAL, True, periodic=True)
+    d1 = O.shift_vectors(psi, img, L, f, obs, O.LOS_RADIAL, True, periodic=True)
+    assert np.abs(d0 - d1).max() < 1e-9
+    d2 = O.shift_vectors(psi, img, L, f, obs, O.LOS_RADIAL, True, periodic=False)
+    assert np.abs(d0 - d2).max() > 1e-3
+    r0 = O.shift_vectors(psi, pos, L, f, obs, O.LOS_RADIAL, False)
+    r1 = O.shift_vectors(psi, img, L, f, obs, O.LOS_RADIAL, False)
+    assert np.abs(r0 - r1).max() < 1e-9
+
+
 def test_shift_decomposition():
     """Galaxy shift: along the LOS -(1+f)(Psi.r); across it -Psi_perp.  Randoms: -Psi."""
     n, L, f = 8, 200.0, 0.74
