@@ -350,7 +350,10 @@ def gpu_arm(args):
         k_e = max(1, min(args.steps, 3))
         e_ms = timed(k_e, step_e2e) / k_e
         npart = len(gal_h) + len(ran_h)
-        e2e = {"value": round(job_value(e_ms, ws), 4), "unit": "ms", "h2d_bytes_per_step": int(2 * npart * 24),
+        # positions read over the link: every tracer by the deposit, then by its shift, except the
+        # randoms in the retained order (their shift reuses the deposit's sorted records)
+        reread = len(gal_h) if args.particle_order == "retained" else npart
+        e2e = {"value": round(job_value(e_ms, ws), 4), "unit": "ms", "h2d_bytes_per_step": int((npart + reread) * 24),
                "d2h_bytes_per_step": int(npart * 12), "ms_per_step": round(e_ms, 4)}
 
     cpu = None

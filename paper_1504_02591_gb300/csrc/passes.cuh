@@ -1043,10 +1043,11 @@ struct KIter8 {
   static constexpr size_t smem = sizeof(float2) * ((size_t)TAB + 2 * (size_t)N * C);
 };
 
-// The three components' 512-point transforms of one column, stage by stage together (one buffer
-// each, so a stage needs one barrier for all three): v[q][r] = x_q[j + 64 r] in, X_q[j + 64 r] out.
-template <bool INV, int N, int C, int K = 3>
-__device__ __forceinline__ void r512_lines3(float2 (&v)[K][8], float2* __restrict__ s, const float2* __restrict__ tw,
+// The 512-point transforms of K lines of one column (K = 2 in the update: A and P_y forward, G and
+// Psi_y inverse; K = 1 for delta), stage by stage together (one buffer each, so a stage needs one
+// barrier for all K): v[q][r] = x_q[j + 64 r] in, X_q[j + 64 r] out.
+template <bool INV, int N, int C, int K>
+__device__ __forceinline__ void r512_lines(float2 (&v)[K][8], float2* __restrict__ s, const float2* __restrict__ tw,
                                             int j, int col) {
   using Lay = ColLayout<C>;
   constexpr int B = N * C;
@@ -1110,7 +1111,7 @@ __global__ void __launch_bounds__(KIter8<N, C>::T, KIter8<N, C>::kMinBlocks) kde
 #pragma unroll
   for (int r = 0; r < 8; ++r) d[0][r] = dkp[t.base + (size_t)(j + 64 * r) * t.ls + (size_t)col * t.cs];
   __syncthreads();   // twiddles
-  if (!a.d_is_k) r512_lines3<false, N, C, 1>(d, s, tw, j, col);
+  if (!a.d_is_k) r512_lines<false, N, C, 1>(d, s, tw, j, col);
 
   const Geometry& g = a.g;
   float2* Sp = t.isQ ? a.sbuf.Q : a.sbuf.M;
@@ -1139,7 +1140,7 @@ __global__ void __launch_bounds__(KIter8<N, C>::T, KIter8<N, C>::kMinBlocks) kde
     v[0][r] = iS;
     v[1][r] = cscale(iS, kdy);
   }
-  r512_lines3<true, N, C, 2>(v, s, tw, j, col);
+  r512_lines<true, N, C, 2>(v, s, tw, j, col);
   {
     // G (Psi_x = kdx G, Psi_z = kdz G) in the third field, Psi_y in the second, as the update
     // kernel leaves them
@@ -1349,7 +1350,7 @@ __global__ void __launch_bounds__(KIter8<N, C>::T, KIter8<N, C>::kMinBlocks) kit
     }
   }
   __syncthreads();   // twiddles
-  r512_lines3<false, N, C, 2>(v, s, tw, j, col);
+  r512_lines<false, N, C, 2>(v, s, tw, j, col);
 
   // S_n = delta/b + beta i k . P_n, the Parseval norms, Psi_n+1 = i kd S_n / k^2 (Eq. iterative)
   float d2 = 0.f, s2 = 0.f;
@@ -1379,7 +1380,7 @@ __global__ void __launch_bounds__(KIter8<N, C>::T, KIter8<N, C>::kMinBlocks) kit
     v[1][r] = cscale(iS, kdy);
   }
 
-  r512_lines3<true, N, C, 2>(v, s, tw, j, col);
+  r512_lines<true, N, C, 2>(v, s, tw, j, col);
   {
     float2* __restrict__ dy = t.isQ ? a.f[1].Q : a.f[1].M;
     float2* __restrict__ dg = t.isQ ? a.f[2].Q : a.f[2].M;
