@@ -11,11 +11,14 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def test_fused_kspace_kernel_matches_generic(lib):
+@pytest.mark.parametrize("los_mode", [0, 1])
+def test_fused_kspace_kernel_matches_generic(lib, los_mode):
+    """The whole update (y pass, paired x passes, z pass with the two-field vector forms) fused
+    against generic, for a radial and a fixed line of sight (the z pass's two forms of d and w)."""
     from paper_1504_02591_gb300 import binding as B
     from paper_1504_02591_gb300 import mocks
     m = mocks.periodic_box(3500.0, 512, 100_000, 0, 1.85, 0.74, 15.0, (0.0, 1750.0, 1750.0), 4, 5, 6, ng=128,
-                           uniform=True)
+                           los_mode=los_mode, uniform=True)
     gal = torch.from_numpy(m.galaxies.pos).cuda()
     r = B.Recon.from_mock(m, uniform=True)
     out = {}
