@@ -17,7 +17,11 @@
  *   - Complex fields on the r2c half grid are float32 pairs [kx][ky][kz], kz = 0..N/2 (N/2+1
  *     values, kz fastest), forward transform e^{-ik.x} unnormalised.
  *   - Positions are (n, 3) row-major (x, y, z per particle), float64 or float32, in [0, L) up to
- *     periodic wrap.  Weights are float32 or NULL (unit weights).
+ *     periodic wrap: a position outside [0, L) stands for its image in [0, L) (the mesh wraps it,
+ *     and a galaxy's radial line of sight runs from the observer to that image).  The grid
+ *     coordinate x N / L is one float64 product; the cell fraction is then kept in fixed point
+ *     (21 bits on the brick-sorted paths, 32 bits on the direct ones, rounded down).  Weights are
+ *     float32 or NULL (unit weights).
  *   - Every call is ordered on the CUDA stream given to recon_create.  Calls that return values to
  *     the host (recon_iterate, recon_get_scalars) synchronise that stream.
  *   - Ownership: the handle owns its device fields (inside the caller's workspace when one is
@@ -169,8 +173,8 @@ recon_status recon_get_radial(recon_handle* h, int level, float* u);
 recon_status recon_get_trace(recon_handle* h, double* rel, int cap, int* n);
 
 /* Reconstruction shift (Sec. 1; Eq. Lagrange x = q + Psi reversed): Psi is CIC-interpolated to each
- * particle; galaxies move by -[Psi + f (Psi . r) r] with r from the particle position, randoms by
- * -Psi.  shift_out: (n, 3) float32, required.  pos_out: (n, 3) float64 shifted positions
+ * particle; galaxies move by -[Psi + f (Psi . r) r] with r from the particle position (its image in
+ * [0, L), see the conventions above), randoms by -Psi.  shift_out: (n, 3) float32, required.  pos_out: (n, 3) float64 shifted positions
  * (wrapped modulo L when periodic) or NULL.  Both are host or device memory as out_on_device
  * says; particle order is the catalogue's. */
 recon_status recon_shift(recon_handle* h, const recon_catalog* cat, int is_galaxy,
