@@ -174,9 +174,9 @@ recon_status recon_get_trace(recon_handle* h, double* rel, int cap, int* n);
 
 /* Reconstruction shift (Sec. 1; Eq. Lagrange x = q + Psi reversed): Psi is CIC-interpolated to each
  * particle; galaxies move by -[Psi + f (Psi . r) r] with r from the particle position (its image in
- * [0, L), see the conventions above), randoms by -Psi.  shift_out: (n, 3) float32, required.  pos_out: (n, 3) float64 shifted positions
- * (wrapped modulo L when periodic) or NULL.  Both are host or device memory as out_on_device
- * says; particle order is the catalogue's. */
+ * [0, L), see the conventions above), randoms by -Psi.  shift_out: (n, 3) float32, required.
+ * pos_out: (n, 3) float64 shifted positions (wrapped modulo L when periodic) or NULL.  Both are host
+ * or device memory as out_on_device says; particle order is the catalogue's. */
 recon_status recon_shift(recon_handle* h, const recon_catalog* cat, int is_galaxy,
                          float* shift_out, double* pos_out, int out_on_device);
 
