@@ -276,3 +276,52 @@ def test_shift_decomposition():
     assert np.abs(perp_g + perp_p).max() < 1e-12
     assert np.abs(dr + p).max() == 0.0
     assert np.allclose(np.linalg.norm(rh, axis=1), 1.0)
+
+
+@pytest.mark.parametrize("m", [(1, 0, 0), (0, 3, 0), (2, -1, 1)])
+def test_divergence_of_a_plane_wave(m):
+    """div of v = a sin(k.x) (constant vector a) is (a.k) cos(k.x), exactly for a mode on the mesh."""
+    n, L = 16, 300.0
+    k, arg = _mode(n, L, m)
+    a = np.array([0.7, -1.1, 0.4])
+    v = a[:, None, None, None] * np.sin(arg)[None]
+    got = O.ifft3(O.divergence(v, L), n)
+    assert np.abs(got - (a @ k) * np.cos(arg)).max() < 1e-12
+
+
+def test_overdensity_uniform_single_mode():
+    """rho = c (1 + e cos(k.x)) has mean c, so delta = e cos(k.x) exactly."""
+    n = 8
+    _, arg = _mode(n, 100.0, (1, 2, 0))
+    c, e = 2.5, 0.3
+    rho = c * (1.0 + e * np.cos(arg))
+    d = O.overdensity_uniform(rho, rho.sum())
+    assert np.abs(d - e * np.cos(arg)).max() < 1e-14
+    d2 = O.overdensity_uniform(rho, 2.0 * rho.sum())           # twice the mean: (1 + e cos)/2 - 1
+    assert np.abs(d2 - (0.5 * (1.0 + e * np.cos(arg)) - 1.0)).max() < 1e-14
+
+
+def test_shifted_positions_wrap_only_when_periodic():
+    L = 100.0
+    pos = np.array([[99.9, 0.05, 50.0]])
+    d = np.array([[0.3, -0.1, 0.0]])
+    assert np.allclose(O.shifted_positions(pos, d, L, True), [[0.2, 99.95, 50.0]], atol=1e-12)
+    assert np.allclose(O.shifted_positions(pos, d, L, False), [[100.2, -0.05, 50.0]], atol=1e-12)
+
+
+def test_reconstruct_galaxies_tracing_randoms_is_still():
+    """Randoms that are the galaxies three times over: alpha = 1/3 and delta = 0 in the mask, so the
+    whole pipeline returns Psi = 0 and zero shifts (an inverted alpha, a field smoothed twice or not
+    at all, or a mask applied to one side only would not)."""
+    rng = np.random.default_rng(12)
+    n, L = 16, 400.0
+    gal = rng.uniform(100.0, 300.0, (3000, 3))
+    ran = np.concatenate([gal, gal, gal])
+    p = dict(n=n, L=L, b=2.0, f=0.7, R=30.0, los_mode=O.LOS_RADIAL, observer=(0.0, 200.0, 200.0),
+             periodic=False, mask_frac=0.01, lognormal=False, uniform=False)
+    out = O.reconstruct(p, gal, None, ran, None, start=O.START_FFTA, tol=0.0, max_iter=3)
+    assert out["alpha"] == pytest.approx(1.0 / 3.0, rel=1e-15)
+    assert out["mask"].any() and not out["mask"].all()
+    assert np.abs(out["delta"]).max() < 1e-12
+    assert np.abs(out["psi"]).max() < 1e-12
+    assert np.abs(out["shift_g"]).max() < 1e-12 and np.abs(out["shift_r"]).max() < 1e-12
