@@ -362,3 +362,19 @@ def test_particle_edge_positions(B):
         shifts[path] = sr.cpu().numpy()
     assert np.abs(shifts[0] - shifts[1]).max() <= SHIFT_TOL
     r.close()
+
+
+def test_smoothing_long_kernel_256(B):
+    """A Gaussian wider than 64 taps on a mesh of at least 256 (the staged, unblocked convolution):
+    delta of a uniform-density periodic box against the oracle's deposit, smoothing and delta."""
+    n, L, R = 256, 500.0, 15.0                       # sigma = 7.7 cells: about 100 taps
+    rng = np.random.default_rng(21)
+    gal = rng.uniform(0, L, (400_000, 3))
+    r = B.Recon(n, L, 2.0, 0.7, R, (250.0, 250.0, 250.0), periodic=True, uniform=True)
+    r.deposit(torch.from_numpy(gal).cuda(), None, None, None)
+    r.smooth()
+    delta = r.get_field(B.FIELD_DELTA).cpu().numpy()
+    r.close()
+    rho = O.smooth(O.cic_deposit(gal, None, n, L), R, L)
+    want = O.overdensity_uniform(rho, float(len(gal)))
+    assert rel_l2(delta, want) < 1e-5
