@@ -104,3 +104,24 @@ def test_fused_delta_pass_512(lib, uniform):
         d = float(np.sqrt((np.abs(a - b) ** 2).sum() / (np.abs(b) ** 2).sum()))
         print(f"fused delta pass ({'uniform' if uniform else 'survey'}), {('delta', 'delta(k)', 'Psi')[i]}: rel L2 {d:.2e}")
         assert d < 1e-5, d
+
+
+def test_narrow_line_tiles_512(lib):
+    """RECON_OPT_LINE_TILE = 1 (8-column x tiles, also for the paired vector x passes) gives the
+    update of the default 16-column tiles: the same butterflies on the same columns."""
+    from paper_1504_02591_gb300 import binding as B
+    from paper_1504_02591_gb300 import mocks
+    m = mocks.periodic_box(3500.0, 512, 100_000, 0, 1.85, 0.74, 15.0, (0.0, 1750.0, 1750.0), 4, 5, 6, ng=128,
+                           uniform=True)
+    gal = torch.from_numpy(m.galaxies.pos).cuda()
+    r = B.Recon.from_mock(m, uniform=True)
+    r.deposit(gal, None, None, None)
+    r.smooth()
+    out = {}
+    for tile in (0, 1):
+        r.set_option(B.OPT_LINE_TILE, tile)
+        r.iterate(B.START_FFTA, 0.0, 4)
+        out[tile] = r.get_psi().cpu().numpy().astype(np.float64)
+    r.close()
+    d = float(np.sqrt(((out[1] - out[0]) ** 2).sum() / (out[0] ** 2).sum()))
+    assert d < 1e-6, d
