@@ -378,3 +378,20 @@ def test_smoothing_long_kernel_256(B):
     rho = O.smooth(O.cic_deposit(gal, None, n, L), R, L)
     want = O.overdensity_uniform(rho, float(len(gal)))
     assert rel_l2(delta, want) < 1e-5
+
+
+def test_empty_shift_catalogue(B):
+    """A shift of no tracers (host or device, either path) returns (0, 3) and leaves the handle able
+    to shift a real catalogue."""
+    m = mocks.small_periodic(n_gal=20_000, n_ran=200_000, n_mesh=32)
+    r = B.Recon.from_mock(m)
+    n_it, rel, st = r.run(m.galaxies.pos, m.randoms.pos, start=0, tol=0.0, max_iter=2)
+    assert n_it == 2
+    for path in (0, 1):
+        r.set_option(B.OPT_SHIFT_PATH, path)
+        assert r.shift(np.zeros((0, 3)), True).shape == (0, 3)
+        s, p = r.shift(torch.zeros((0, 3), dtype=torch.float64, device="cuda"), False, want_pos=True)
+        assert tuple(s.shape) == (0, 3) and tuple(p.shape) == (0, 3)
+    sg = r.shift(m.galaxies.pos, True)
+    assert sg.shape == (len(m.galaxies.pos), 3) and np.isfinite(sg).all()
+    r.close()
