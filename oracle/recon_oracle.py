@@ -21,6 +21,8 @@ Conventions (readings of the paper where it is silent or inconsistent, stated he
   The sign is fixed by the plane-parallel Kaiser limit S = (delta/b)/(1 + beta mu^2).
 * Smoothing kernel exp(-k^2 R^2 / 2) (the printed "-ik^2R^2/2" of Sec. 3.1 read as a real Gaussian).
 * CIC (cloud-in-cell) mass assignment on the nodes, periodic wrap; the paper bins with NGP (Sec. 3).
+* Tracers outside a periodic box: a position stands for its image in [0, L); the mesh wraps it and a
+  galaxy's radial line of sight runs from the observer to that image (the paper is silent).
 """
 from __future__ import annotations
 
