@@ -325,3 +325,66 @@ def test_reconstruct_galaxies_tracing_randoms_is_still():
     assert np.abs(out["delta"]).max() < 1e-12
     assert np.abs(out["psi"]).max() < 1e-12
     assert np.abs(out["shift_g"]).max() < 1e-12 and np.abs(out["shift_r"]).max() < 1e-12
+
+
+def test_rhat_nodes_sit_at_i_times_H():
+    """Sec. 3.1: the line of sight is the unit vector from the observer to the point.  With the
+    observer placed exactly on node (i, j, k) (observer = (i, j, k) H), the node-centred field must
+    vanish on that node and be the axis unit vectors on its six neighbours and (1, 1, 0)/sqrt(2) on a
+    diagonal one; a grid offset by any fraction of a cell (nodes at (i + 1/2) H, say) would give a
+    non-zero vector at the observer's node and tilted vectors at the neighbours."""
+    n, L = 16, 320.0
+    H = L / n
+    i, j, k = 5, 9, 12
+    rh = O.rhat_field(n, L, (i * H, j * H, k * H), O.LOS_RADIAL)
+    assert np.array_equal(rh[:, i, j, k], [0.0, 0.0, 0.0])
+    for axis in range(3):
+        for step in (-1, 1):
+            node = [i, j, k]
+            node[axis] += step
+            want = np.zeros(3)
+            want[axis] = step
+            assert np.abs(rh[:, node[0], node[1], node[2]] - want).max() < 1e-15
+    s = 1.0 / np.sqrt(2.0)
+    assert np.abs(rh[:, i + 1, j + 1, k] - [s, s, 0.0]).max() < 1e-15
+    assert np.abs(rh[:, i, j - 3, k - 4] - [0.0, -0.6, -0.8]).max() < 1e-15   # a 3-4-5 triangle
+    # the field is a unit vector everywhere else
+    r = np.sqrt((rh * rh).sum(0))
+    r[i, j, k] = 1.0
+    assert np.abs(r - 1.0).max() < 1e-14
+
+
+def test_mask_threshold_counts_touched_nodes_by_hand():
+    """Sec. 3.2 survey mask reading: the threshold is mask_frac x sum w_r / (nodes that received
+    random mass).  Hand-built randoms: one on a node (touches 1 node), one at a cell centre
+    (touches 8), one more inside that same cell (the same 8 nodes) and one halfway along an x edge
+    of another cell (touches the edge's 2 end nodes): 1 + 8 + 2 = 11 nodes, total weight 5."""
+    n, L = 16, 160.0            # H = 10
+    ran = np.array([[20.0, 30.0, 40.0],     # node (2, 3, 4): 1 node
+                    [105.0, 105.0, 105.0],  # centre of cell (10, 10, 10): nodes 10..11 ^3, 8 nodes
+                    [102.0, 107.0, 103.5],  # inside the same cell: the same 8 nodes
+                    [55.0, 150.0, 0.0]])    # on the x edge of cell (5, 15, 0): nodes (5|6, 15, 0)
+    wr = np.array([1.0, 1.0, 1.0, 2.0])
+    gal = np.array([[50.0, 50.0, 50.0]])
+    p = dict(n=n, L=L, b=2.0, f=0.7, R=10.0, los_mode=O.LOS_RADIAL, observer=(0.0, 80.0, 80.0),
+             periodic=False, mask_frac=0.01, lognormal=False, uniform=False)
+    out = O.reconstruct(p, gal, None, ran, wr, start=O.START_PLAIN, tol=0.0, max_iter=1, shift=False)
+    assert np.count_nonzero(out["rho_r"] > 0) == 11
+    assert out["threshold"] == pytest.approx(0.01 * 5.0 / 11.0, rel=1e-15)
+    assert out["alpha"] == pytest.approx(1.0 / 5.0, rel=1e-15)
+
+
+def test_lognormal_floor_branch():
+    """Eq. logdelta with 1 + delta floored at 1e-6: delta = -1 and delta = -3 both give
+    ln(1e-6) = -6 ln 10, and C = -<ln(max(1 + delta, 1e-6))>."""
+    e = np.e
+    delta = np.array([-1.0, -3.0, e - 1.0, e * e - 1.0])
+    ln_floor = -6.0 * np.log(10.0)
+    raw = np.array([ln_floor, ln_floor, 1.0, 2.0])
+    out, C = O.lognormal(delta)
+    assert C == pytest.approx(-raw.mean(), rel=1e-14)
+    assert np.abs(out - (raw - raw.mean())).max() < 1e-13
+    # just above the floor the logarithm is not clipped
+    d2 = np.array([-1.0 + 2e-6, 0.0])
+    out2, C2 = O.lognormal(d2)
+    assert out2[0] - out2[1] == pytest.approx(np.log(2e-6), rel=1e-9)
