@@ -42,6 +42,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-warm", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the 1024^3 large periodic run")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT context timing")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-mock batch")
+    ap.add_argument("--no-diag", action="store_true", help="skip the paper's diagnostics")
+    ap.add_argument("--plane-batch", type=int, default=None,
+                    help="y-planes per batch of the x -> z -> x passes (0 off; default: the library's)")
     ap.add_argument("--particle-order", choices=("retained", "per-call"), default="retained",
                     help="retained: one brick sort per catalogue per step, shared by deposit and shift")
     ap.add_argument("--host-loop", action="store_true",
@@ -136,27 +142,71 @@ def job_value(ms_per_step, world_size):
     return ms_per_step / world_size
 
 
-CPU_MESH = 256
-CPU_SCALE = (512 / CPU_MESH) ** 3 * 27.0 / (3 * 8)      # volume x log(512^3)/log(256^3)
-CPU_SAMPLE = (f"oracle deposit+smooth+iterations+shift on the {CPU_MESH}^3 version of the workload "
-              f"(75000 galaxies, 3750000 randoms), x{CPU_SCALE:.3f} to 512^3")
+RAN_SAMPLE = 3_000_000      # randoms deposited and shifted by the CPU sample (timing scales with count)
 
 
-def cpu_sample(n_iter):
-    """The FP64 oracle as it stands on a bounded sample of the workload, scaled to 512^3.
+def oracle_stages(m, n_iter, cores):
+    """The FP64 oracle as it stands, timed stage by stage on the full-size workload (512^3 mesh).
 
-    Sample: the same survey shape on a 256^3 mesh with 1/8 of the tracers and the GPU's iteration
-    count.  Every stage scales with the mesh volume (FFT stages as N^3 log N) or with the tracer
-    count, so the time is multiplied by 8 * log(512^3)/log(256^3) = 9.
-    """
+    Every mesh stage runs at full size: smoothing of both densities, delta with the survey mask,
+    the line-of-sight field, the Eq. approx2 start and one update of Eq. iterative.  The particle
+    stages (CIC deposit and shift) run on all galaxies and on RAN_SAMPLE of the randoms; their time
+    is linear in the particle count and is scaled to all randoms.  A converged reconstruction is
+    then deposit + smoothing + delta + start + n_iter updates + shift.  The library FFT runs on
+    `cores` threads; numpy's elementwise work is single-threaded."""
+    import numpy as np
     from oracle import recon_oracle as O
-    from paper_1504_02591_gb300 import mocks
-    m = mocks.survey_shell_512(n_gal=600_000 // 8, ran_ratio=50, n_mesh=CPU_MESH)
+    O.FFT_WORKERS = cores
+    O.fft3(np.zeros((32, 32, 32)))                     # the FFT's thread pool and plan cache
+    p = m.params()
+    n, L = p["n"], p["L"]
+    gal, ran = m.galaxies.pos, m.randoms.pos
+    rs = min(RAN_SAMPLE, len(ran))
+    scale_r = len(ran) / rs
+    t = {}
+    c0 = time.perf_counter()
     t0 = time.perf_counter()
-    O.reconstruct(m.params(), m.galaxies.pos, None, m.randoms.pos, None, start=O.START_FFTA,
-                  tol=0.0, max_iter=n_iter)
-    dt = time.perf_counter() - t0
-    return dt * 1000.0 * CPU_SCALE, dt
+    rho_g = O.cic_deposit(gal, None, n, L)
+    tg = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    rho_r = O.cic_deposit(ran[:rs], None, n, L)
+    t["deposit"] = tg + (time.perf_counter() - t0) * scale_r
+    t0 = time.perf_counter()
+    rho_g_s = O.smooth(rho_g, p["R"], L)
+    rho_r_s = O.smooth(rho_r, p["R"], L)
+    t["smooth"] = time.perf_counter() - t0
+    rho_r_s *= scale_r                                 # the full random catalogue's density scale
+    t0 = time.perf_counter()
+    delta, _, _, _ = O.overdensity_randoms(rho_g_s, rho_r_s, float(len(gal)), float(len(ran)),
+                                           p["mask_frac"], int(np.count_nonzero(rho_r > 0)))
+    t["delta"] = time.perf_counter() - t0
+    del rho_g, rho_r, rho_g_s, rho_r_s
+    t0 = time.perf_counter()
+    rhat = O.rhat_field(n, L, p["observer"], p["los_mode"])
+    t["rhat"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    psi, _ = O.start_estimate(delta, p["b"], p["f"], L, rhat, O.START_FFTA)
+    t["start"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    psi = O.update(psi, delta, p["b"], p["f"], L, rhat)
+    t["update"] = time.perf_counter() - t0
+    del rhat, delta
+    t0 = time.perf_counter()
+    O.shift_vectors(psi, gal, L, p["f"], p["observer"], p["los_mode"], True)
+    tg = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.shift_vectors(psi, ran[:rs], L, p["f"], p["observer"], p["los_mode"], False)
+    t["shift"] = tg + (time.perf_counter() - t0) * scale_r
+    cpu_s = time.perf_counter() - c0
+    total = sum(v for k, v in t.items() if k != "update") + n_iter * t["update"]
+    return total * 1000.0, {k: round(v, 3) for k, v in t.items()}, cpu_s
+
+
+def cpu_sample_text(n_iter, stages, cores, cpu_s):
+    return (f"FP64 oracle on the full 512^3 workload, stage by stage: mesh stages at full size "
+            f"(smoothing, delta, line of sight, start, one update x {n_iter} updates), deposit and "
+            f"shift of all galaxies and {RAN_SAMPLE} of the randoms scaled to all; FFT on {cores} "
+            f"threads; stage seconds {json.dumps(stages)}; {cpu_s:.1f} s of CPU work")
 
 
 def kernel_sources_sha1():
@@ -185,26 +235,224 @@ def recorded_traffic(kernel):
 
 
 def reference_arm(args):
+    """The oracle as the reference arm: one warm-up per step on a small mesh, the once-per-reconstruction
+    stages timed once at full size, then each timed step one full-size update of Eq. iterative."""
+    import numpy as np
+    from oracle import recon_oracle as O
     ws, rank, _ = dist_info()
     if rank != 0:
         return
-    n_iter = 13
-    for _ in range(args.warmup):
-        cpu_sample(n_iter)
-    vals, raw = [], []
+    cores = os.cpu_count() or 1
+    n_iter = 13                                   # updates of the GPU arm's Eq. approx2 start
+    m = workload(args.mesh)
+    for _ in range(args.warmup):                  # warm the FFT plans and thread pool (64^3 update)
+        d = np.random.default_rng(0).standard_normal((64, 64, 64))
+        rh = O.rhat_field(64, 500.0, (0.0, 250.0, 250.0), O.LOS_RADIAL)
+        O.update(O.start_estimate(d, 2.0, 0.7, 500.0, rh)[0], d, 2.0, 0.7, 500.0, rh)
+    _, stages, _ = oracle_stages(m, 1, cores)
+    p = m.params()
+    n, L = p["n"], p["L"]
+    # one update at full size per timed step, on the same delta and start
+    rho_g_s = O.smooth(O.cic_deposit(m.galaxies.pos, None, n, L), p["R"], L)
+    rho_r = O.cic_deposit(m.randoms.pos[:RAN_SAMPLE], None, n, L)
+    scale_r = len(m.randoms.pos) / RAN_SAMPLE
+    delta, _, _, _ = O.overdensity_randoms(rho_g_s, O.smooth(rho_r, p["R"], L) * scale_r,
+                                           float(len(m.galaxies.pos)), float(len(m.randoms.pos)),
+                                           p["mask_frac"], int(np.count_nonzero(rho_r > 0)))
+    del rho_g_s, rho_r
+    rhat = O.rhat_field(n, L, p["observer"], p["los_mode"])
+    psi, _ = O.start_estimate(delta, p["b"], p["f"], L, rhat, O.START_FFTA)
+    upd = []
     for _ in range(args.steps):
-        v, dt = cpu_sample(n_iter)
-        vals.append(v)
-        raw.append(dt)
-    value = statistics.mean(vals)
-    sample = CPU_SAMPLE + f"; {n_iter} iterations, {statistics.mean(raw):.1f} s per sample"
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+        t0 = time.perf_counter()
+        psi = O.update(psi, delta, p["b"], p["f"], L, rhat)
+        upd.append(time.perf_counter() - t0)
+    stages["update"] = round(statistics.mean(upd), 3)
+    value = (sum(v for k, v in stages.items() if k != "update") + n_iter * stages["update"]) * 1000.0
+    step_ms = statistics.mean(upd) * 1000.0
+    sample = (f"each timed step one full-size (512^3) update of Eq. iterative by the FP64 oracle; the "
+              f"once-per-reconstruction stages timed once at full size (deposit and shift on all galaxies "
+              f"and {RAN_SAMPLE} randoms, scaled to all); value = stages + {n_iter} updates; FFT on "
+              f"{cores} threads; stage seconds {json.dumps(stages)}")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_ms, 1), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(args.mesh), "parallelism": "replicas"},
-            "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"value": round(value, 1), "unit": "ms", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def cufft_context(n, steps=10):
+    """cuFFT (through torch.fft) on the same 512^3 r2c / c2r shapes, timed with CUDA events: context
+    only, never on the library's path.  One update of the iteration applies 3 c2r and 3 r2c."""
+    import torch
+    x = torch.randn((n, n, n), device="cuda", dtype=torch.float32)
+    X = torch.fft.rfftn(x)
+    y = torch.fft.irfftn(X, s=(n, n, n))
+    torch.cuda.synchronize()
+
+    def t(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    r2c = t(lambda: torch.fft.rfftn(x, out=X))
+    c2r = t(lambda: torch.fft.irfftn(X, s=(n, n, n), out=y))
+    del x, X, y
+    torch.cuda.empty_cache()
+    return {"r2c_ms": round(r2c, 4), "c2r_ms": round(c2r, 4), "update_transforms_ms": round(3 * (r2c + c2r), 4),
+            "note": f"cuFFT via torch.fft on {n}^3 float32, out of place, context only (not on the library path)"}
+
+
+def large_periodic(args, timed, peak):
+    """The large periodic run: 1024^3 mesh, 1e8 particles, b = 1, f = 0.74, R = 10, uniform mean
+    density, 6 updates from the Eq. approx2 start, shift of every particle; fixed and radial line of
+    sight, and radial with the lognormal transform.  A step is deposit -> smooth -> 6 updates ->
+    shift; the update's HBM fraction comes from the per-kernel CUDA events of one extra step."""
+    import torch
+    from paper_1504_02591_gb300 import binding, mocks
+    m = mocks.large_periodic_1024(los_mode=0)
+    gal = torch.from_numpy(m.galaxies.pos).cuda()
+    sg = torch.empty((len(gal), 3), dtype=torch.float32, device="cuda")
+    out = {"workload": "periodic 1024^3, L=2500 Mpc/h, 1e8 Zel'dovich particles (464^3 lattice + jitter), "
+                       "uniform mean density, b=1 f=0.74 R=10, 6 updates from the Eq. approx2 start",
+           "n_particles": len(gal)}
+    variants = [("fixed", dict(los_mode=1, observer=(1.0, 0.0, 0.0))), ("radial", {}),
+                ("radial_lognormal", dict(lognormal=True))]
+    k = max(1, min(3, args.steps))
+    for name, over in variants:
+        r = binding.Recon.from_mock(m, **over)
+
+        def step():
+            r.deposit(gal, None, None, None)
+            r.smooth()
+            r.iterate(binding.START_FFTA, 0.0, 6)
+            r.shift(gal, True, out=sg)
+
+        step()
+        ms = timed(k, step) / k
+        res = {"ms": round(ms, 3)}
+        if name == "radial":
+            r.reset_timing()
+            r.set_timing(True)
+            step()
+            r.set_timing(False)
+            kt = r.timing()
+            # one update = one launch of each of its four passes (per-launch means over the step)
+            upd = [kk for kk in ("k_iter", "line_inv", "z_proj", "line_fwd") if kt[kk][0] > 0]
+            upd_ms = sum(kt[kk][1] / kt[kk][0] for kk in upd)
+            upd_bytes = sum(kt[kk][2] / kt[kk][0] for kk in upd)
+            res["update_ms"] = round(upd_ms, 4)
+            res["update_hbm_frac"] = round(upd_bytes / (upd_ms * 1e-3) / 1e9 / peak, 4)
+            res["kernels"] = {kk: {"launches": v[0], "ms": round(v[1], 3),
+                                   "GBps": round(v[2] / (v[1] * 1e-3) / 1e9, 1) if v[1] > 0 else None}
+                              for kk, v in kt.items() if v[0] > 0}
+        out[name] = res
+        r.close()
+    del gal, sg
+    torch.cuda.empty_cache()
+    return out
+
+
+def paper_diagnostics(m, r_main):
+    """Sec. 5.2 (Tables 2-3) on the benchmark survey: the mean radial ratio (Eq. ratio) of the
+    real-space galaxies' displacement Z[delta_real/b] to the n-th iterate, at every galaxy, outliers
+    (above 3 or below -1) cut, for n = 0..7 from the uncorrected and the Eq. approx2 starts, and the
+    iteration after which the mean changes by less than 1% (the paper's criterion); plus the Sec. 4.1
+    Helmholtz split of the converged displacement along x (irrotational / solenoidal ratio).  All on
+    the GPU (recon_radial_ratio, recon_helmholtz_x, recon_ratio_stats)."""
+    import torch
+    from paper_1504_02591_gb300 import binding
+    from oracle import recon_oracle as O
+    gal = torch.from_numpy(m.galaxies.pos).cuda()
+    ran = torch.from_numpy(m.randoms.pos).cuda()
+    p = m.params()
+
+    def psi_of(pos, f, start, n_it):
+        r = binding.Recon.from_mock(m, f=f)
+        r.deposit(pos, None, ran, None)
+        r.smooth()
+        r.iterate(start, 0.0, n_it)
+        out = r.get_psi()
+        r.close()
+        return out
+
+    real = psi_of(torch.from_numpy(m.galaxies_real.pos).cuda(), 0.0, binding.START_PLAIN, 1)
+    psi_s = psi_of(gal, 0.0, binding.START_PLAIN, 1)           # Z[delta/b] of the redshift-space data
+    out = {}
+    r = binding.Recon.from_mock(m)
+    r.deposit(gal, None, ran, None)
+    r.smooth()
+    for name, start in (("uncorrected", binding.START_PLAIN), ("eq_approx2", binding.START_FFTA)):
+        c = O.start_coefficient(start, p["f"] / p["b"])
+        rows = [r.radial_ratio(real, (1.0 - c) * psi_s, gal)[:3]]
+        for n in range(1, 8):
+            r.iterate(start, 0.0, n)
+            rows.append(r.radial_ratio(real, r.get_psi(), gal)[:3])
+        means = [x[0] for x in rows]
+        conv = next(n for n in range(len(means)) if all(abs(means[k + 1] - means[k]) < 0.01 * abs(means[k])
+                                                         for k in range(n, len(means) - 1)))
+        out[name] = {"mean_sigma_cut": [[round(v, 4) for v in x] for x in rows], "converged_at": conv}
+    r.iterate(binding.START_FFTA, 1e-6, 80)
+    psi = r.get_psi()
+    ga, cb = r.helmholtz_x(psi[0])
+    out["helmholtz_x_ratio"] = {ax: [round(v, 4) for v in r.ratio_stats(ga[j], cb[j], -1e300, 1e300)[:2]]
+                                for j, ax in enumerate("xyz")}
+    r.close()
+    out["note"] = ("ratio at every galaxy; Psi_real from the same galaxies before their redshift-space shift; "
+                   "paper (mock, Table 3): uncorrected start 0.80 -> 1.10 -> 0.96 ..., converges after 6; "
+                   "Eq. approx2 start 1.04, after 2 (its solve uses f where this build uses beta = f/b)")
+    del gal, ran, real, psi_s, psi, ga, cb
+    torch.cuda.empty_cache()
+    return out
+
+
+def batch_bench(args):
+    """The batched workload: 64 mocks (N from {256, 384, 512}, 2e5-1e6 galaxies, 30-50x randoms,
+    per-mock b and f, shell surveys and periodic boxes) reconstructed to 1e-6 from the Eq. approx2
+    start in one recon_batch_run call (one CUDA graph).  The first call tunes each size class (not
+    timed); each timed call is the whole batch, from the call to its return."""
+    import torch
+    from paper_1504_02591_gb300 import binding, mocks
+    work = mocks.batch_workload_device(64, 100)
+    sizes = [w["params"]["n"] for w in work]
+    particles = sum(len(w["gal"]) + (len(w["ran"]) if w["ran"] is not None else 0) for w in work)
+    st, res = binding.batch_run(work, start=binding.START_FFTA, tol=args.tol, max_iter=args.max_iter)  # tunes
+    k = max(1, min(2, args.steps))
+    times = []
+    for _ in range(k):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, res = binding.batch_run(work, start=binding.START_FFTA, tol=args.tol, max_iter=args.max_iter)
+        times.append(time.perf_counter() - t0)
+    wall = statistics.mean(times)
+    item_ms = [r["ms"] for r in res]
+    by_n = {}
+    for n, r in zip(sizes, res):
+        d = by_n.setdefault(str(n), {"mocks": 0, "ms": [], "n_iter": []})
+        d["mocks"] += 1
+        d["ms"].append(r["ms"])
+        d["n_iter"].append(r["n_iter"])
+    out = {"workload": "64 mocks, N in {256, 384, 512}, 2e5-1e6 galaxies, randoms 30-50x, b in [1.5, 2.5], "
+                       "f in [0.6, 0.8], shell surveys and periodic boxes, converged to 1e-6",
+           "status": int(st), "ok": sum(1 for r in res if r["status"] == binding.OK),
+           "particles": int(particles), "wall_s": round(wall, 4), "mocks_per_s": round(len(work) / wall, 3),
+           "ms_per_mock": round(1000.0 * wall / len(work), 3),
+           "item_ms_sum": round(sum(item_ms), 2),
+           "classes": {n: {"mocks": d["mocks"], "mean_ms": round(statistics.mean(d["ms"]), 3),
+                           "mean_updates": round(statistics.mean(d["n_iter"]), 2)} for n, d in sorted(by_n.items())},
+           "plans": {str(n): binding.batch_plan(n) for n in (256, 384, 512)},
+           "launch": "one CUDA graph per call (a chain per size class, conditional WHILE loops)"}
+    del work, res
+    torch.cuda.empty_cache()
+    return out
 
 
 def gpu_arm(args):
@@ -228,6 +476,8 @@ def gpu_arm(args):
     if args.particle_order == "retained":
         r.set_option(binding.OPT_DEPOSIT_PATH, binding.PATH_SORTED)
         r.set_option(binding.OPT_REUSE_SORT, 1)
+    if args.plane_batch is not None:
+        r.set_option(binding.OPT_PLANE_BATCH, args.plane_batch)
     sg = torch.empty((len(gal), 3), dtype=torch.float32, device="cuda")
     sr = torch.empty((len(ran), 3), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -302,6 +552,7 @@ def gpu_arm(args):
         step()
     plain_ms = timed(args.steps, step) / args.steps
     plain = {"ms": round(plain_ms, 4), "n_iter": info["n_iter"], "final_rel": info["rel"], "start": "Eq. approx2"}
+    info_plain_iter = info["n_iter"]
     # per-kernel CUDA-event timings over the same number of steps (events around every launch on
     # the library's stream; the iteration runs host-driven so that each launch can be bracketed)
     r.reset_timing()
@@ -356,11 +607,17 @@ def gpu_arm(args):
         e2e = {"value": round(job_value(e_ms, ws), 4), "unit": "ms", "h2d_bytes_per_step": int((npart + reread) * 24),
                "d2h_bytes_per_step": int(npart * 12), "ms_per_step": round(e_ms, 4)}
 
+    diag = paper_diagnostics(m, r) if not args.no_diag else None
+    cufft = cufft_context(args.mesh) if not args.no_cufft else None
+    batch = batch_bench(args) if not args.no_batch else None
+    large = large_periodic(args, timed, peak) if not args.no_large else None
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        v, dt = cpu_sample(n_iter)
-        cpu = {"value": round(v, 1), "unit": "ms", "cores": 1, "kind": "oracle",
-               "sample": CPU_SAMPLE + f"; {n_iter} iterations took {dt:.2f} s"}
+        cores = os.cpu_count() or 1
+        v, stages, cpu_s = oracle_stages(m, info_plain_iter, cores)
+        cpu = {"value": round(v, 1), "unit": "ms", "cores": cores, "kind": "oracle",
+               "sample": cpu_sample_text(info_plain_iter, stages, cores, cpu_s)}
 
     if rank == 0:
         line = {
@@ -384,6 +641,10 @@ def gpu_arm(args):
                          "traffic": recorded_traffic(dom), "alg_bytes_per_launch": by / cnt,
                          "ms_per_launch": round(ms_k / cnt, 5)},
             "kernels": kernels,
+            "paper_diagnostics": diag,
+            "large_periodic_1024": large,
+            "batch": batch,
+            "cufft_context": cufft,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(launches),

@@ -112,7 +112,8 @@ recon_status recon_workspace_bytes(const recon_params* p, size_t* bytes);
  *   stream     cudaStream_t to order all work on (NULL = legacy default stream)
  *   workspace  device memory of at least recon_workspace_bytes bytes, 256-byte aligned, owned by
  *              the caller and kept alive until recon_destroy; NULL makes the handle allocate it
- *              itself with cudaMalloc (and free it in recon_destroy). */
+ *              itself with cudaMalloc (and free it in recon_destroy).  A workspace that is not
+ *              256-byte aligned gives INVALID_ARG, one smaller than recon_workspace_bytes OOM. */
 recon_status recon_create(const recon_params* p, void* stream, void* workspace,
                           size_t workspace_bytes, recon_handle** out);
 
@@ -138,7 +139,9 @@ recon_status recon_smooth(recon_handle* h);
  * uncorrected estimate Z[delta/b]).  On return *n_iter is the number of updates and *rel_change
  * the last rel.  Returns NOT_CONVERGED when max_iter was reached with rel >= tol and tol > 0.
  * By default the loop runs on the device as one CUDA graph (RECON_OPT_GRAPH) and the call blocks
- * once, at the end; max_iter <= 1024 in that mode (larger values use the host-driven loop). */
+ * once, at the end; max_iter <= 1024 in that mode (larger values use the host-driven loop).  The
+ * handle keeps the instantiated graph and relaunches it on the next call with the same start, tol,
+ * max_iter, options and parameters (recon_reconfigure or a changed value rebuilds it). */
 recon_status recon_iterate(recon_handle* h, int start, double tol, int max_iter, int* n_iter,
                            double* rel_change);
 
@@ -200,6 +203,32 @@ recon_status recon_fft_r2c(recon_handle* h, const float* in_real, float* out_hal
  * the inverse DFT. Invalidates the reconstruction state like recon_fft_r2c. */
 recon_status recon_fft_c2r(recon_handle* h, const float* in_half, float* out_real);
 
+/* ---- Diagnostics of the paper (computed on the GPU) -------------------------------------------
+ * Statistics of a ratio, as in Tables 1-3: out[0] mean and out[1] standard deviation (population)
+ * of the ratios inside [lo, hi] (the paper cuts ratios above 3 or below -1: lo = -1, hi = 3; a zero
+ * denominator is always cut), out[2] the fraction of points cut, out[3] the number kept.  Sums in
+ * float64; each ratio is formed in float64 from float32 inputs.  Synchronise the handle's stream. */
+
+/* Eq. ratio (Sec. 4.3, 5.2): (Psi_num . r) / (Psi_den . r) at every particle of cat (device memory),
+ * both displacement fields (device, 3 N^3 float32 [comp][ix][iy][iz], e.g. from recon_get_psi)
+ * CIC-interpolated to the particle and projected on the particle's line of sight (radial from the
+ * handle's observer, or its fixed direction).  With Psi_num the displacement of the real-space
+ * tracers and Psi_den an iterate, this is the paper's convergence statistic. */
+recon_status recon_radial_ratio(recon_handle* h, const float* psi_num, const float* psi_den, const recon_catalog* cat,
+                                double lo, double hi, double out[4]);
+
+/* The same statistics of num[i] / den[i] over n device float32 values (e.g. the Helmholtz
+ * components below, node by node). */
+recon_status recon_ratio_stats(recon_handle* h, const float* num, const float* den, int64_t n, double lo, double hi,
+                               double out[4]);
+
+/* Sec. 4.1 (Eq. Helmholtz, Eq. irrotational, Eq. solenoidal): the plane-parallel split of
+ * (Psi . x) x, Psi_x = psi_x (device, N^3 float32), into grad A (Fourier components
+ * (k_j k_x / k^2) Psi_x(k), derivative wavenumbers zero at the Nyquist index) and curl B =
+ * (Psi_x) x - grad A; grad_a and curl_b are device (3, N^3) float32 outputs.  Uses the handle's
+ * FFT passes and fields, so it invalidates the reconstruction state like recon_fft_r2c. */
+recon_status recon_helmholtz_x(recon_handle* h, const float* psi_x, float* grad_a, float* curl_b);
+
 /* Kernel kinds counted and (optionally) timed by the handle. */
 enum {
   RECON_K_DEPOSIT = 0,   /* CIC deposit from brick-sorted particles      */
@@ -234,13 +263,12 @@ recon_status recon_get_timing(recon_handle* h, int kind, double* total_ms, int64
 recon_status recon_reset_timing(recon_handle* h);
 
 /* CIC deposit for callers that cannot allocate device memory.  (The paper has no counterpart: it
- * is a service entry point of this library.)  Some callers may not allocate: code that runs while
- * a CUDA stream is being captured into a graph (cudaMalloc is not allowed there), plugins whose
- * host application owns every device buffer through its own pool, and real-time pipelines that
- * must not enter an allocator mid-run.  This call allocates nothing and uses no handle: the
- * caller passes every input and output, and the only scratch (per-block partial sums of the
- * weights) is a fixed 32 KB array inside the library's device image, kept by every device that
- * loads the library until the process exits.
+ * is a service entry point of this library.)  Some callers may not allocate: plugins whose host
+ * application owns every device buffer through its own pool, and real-time pipelines that must
+ * not enter an allocator (or its synchronisation) once they run.  This call allocates nothing
+ * and uses no handle: the caller passes every input and output, and the only scratch (per-block
+ * partial sums of the weights) is a fixed 32 KB array inside the library's device image, kept by
+ * every device that loads the library until the process exits.
  *   pos     device (n, 3) positions, dtype RECON_F64 or RECON_F32, in [0, box) up to periodic wrap
  *   w       device (n) float32 weights or NULL (unit weights)
  *   n       0 .. 67,108,864 particles per call (the scratch bound); larger n -> INVALID_ARG
@@ -249,7 +277,9 @@ recon_status recon_reset_timing(recon_handle* h);
  *   sum_w   device float64, overwritten with the sum of the weights
  *   stream  cudaStream_t the work is ordered on
  * The first call on each device looks up the scratch array's device address (once, with that
- * device current); make that first call before any stream capture begins.  Every call shares the
+ * device current) and keeps it for the process; make that first call before any stream capture
+ * begins.  After cudaDeviceReset the kept address is stale: do not call this entry point on a
+ * device that was reset since its first call.  Every call shares the
  * one scratch array, which keeps the last call's partial sums: calls that overlap on the GPU (on
  * different streams, or from several host threads without ordering) race on it and must be
  * serialised by the caller.  Errors: INVALID_ARG for bad arguments or too many particles, CUDA
@@ -274,10 +304,15 @@ enum {
                                    sorting the positions again; the caller guarantees they did not
                                    change in between.  While that order is held, shifts of other
                                    catalogues take the direct path.                              */
-  RECON_OPT_KSPACE_GENERIC = 4  /* 0 (default): for N = 512 the source update and the projection
+  RECON_OPT_KSPACE_GENERIC = 4, /* 0 (default): for N = 512 the source update and the projection
                                    pass run in kernels that keep the first and last FFT stages
                                    (and the c2r/r2c pairing) in registers; 1: the generic staged
                                    kernels (same butterflies)                                     */
+  RECON_OPT_PLANE_BATCH = 6     /* register-fused path (N = 512): 0 (off) or 16, 32, 64 y-planes per
+                                   batch; each update then runs its inverse x, projection and forward
+                                   x passes batch by batch, so a batch's fields stay in the L2 between
+                                   the three passes (same arithmetic, fewer HBM round trips).  A
+                                   multiple of the x-line tile width (16, or 8 with RECON_OPT_LINE_TILE) */
 };
 /* Particle paths: DIRECT handles each particle independently (8 global atomics per deposited
  * particle; 24 scattered reads per interpolated one); SORTED packs the particles, counting-sorts
@@ -286,7 +321,8 @@ enum {
  * float32 summation order. */
 enum { RECON_PATH_DIRECT = 0, RECON_PATH_SORTED = 1 };
 
-/* Set a handle option (values 0 or 1); INVALID_ARG for an unknown option or value. */
+/* Set a handle option (values 0 or 1, RECON_OPT_PLANE_BATCH 0/16/32/64); INVALID_ARG for an unknown
+ * option or value. */
 recon_status recon_set_option(recon_handle* h, int option, int value);
 
 /* One reconstruction of a batch (recon_batch_run). */
@@ -296,24 +332,31 @@ typedef struct recon_batch_item {
   recon_catalog ran;       /* randoms (ignored with RECON_MEAN_UNIFORM)                          */
   int start;               /* RECON_START_*                                                      */
   double tol;              /* as for recon_iterate                                               */
-  int max_iter;
+  int max_iter;            /* 1 .. 1024                                                          */
   float* shift_gal;        /* (n_gal, 3) galaxy shifts, or NULL for none                         */
   float* shift_ran;        /* (n_ran, 3) random shifts, or NULL for none                         */
   int out_on_device;       /* shift buffers are device (1) or host (0) memory                    */
   int n_iter;              /* out: updates done                                                  */
   double rel;              /* out: last |dPsi|/|Psi|                                             */
   int status;              /* out: recon_status of this item (OK or NOT_CONVERGED on success)    */
-  float ms;                /* out: device milliseconds of this item on the stream                */
+  float ms;                /* out: device milliseconds from the start to the end of this item's
+                              work (in the one-graph mode, between two device timer stamps; work
+                              of another size class may overlap it)                              */
 } recon_batch_item;
 
 /* Reconstruct many mocks of uneven mesh and catalogue sizes (deposit -> smooth -> iterate ->
- * shift each).  Items are grouped by mesh side; each size class uses one persistent handle
- * (allocated with cudaMalloc, freed at the end of the class) and its items run back to back on
- * `stream`, each iteration loop as one CUDA graph.  With autotune = 1, the first item of a size
- * class not seen before in this process is also used to time the class's schedules (x-line FFT tile
- * width, deposit path, shift path); the fastest are kept for the rest of the process
- * (recon_batch_plan).  Returns the first error of any item (per-item statuses in items[i].status),
- * else OK. */
+ * shift each; the benchmark spec's batched form, no counterpart in the paper).  Items are grouped by mesh
+ * side; each size class uses one handle (allocated with cudaMalloc, freed before returning).
+ * When every catalogue and shift buffer is device memory, the whole batch runs as ONE CUDA graph
+ * launched on `stream`: per size class a chain of its items (each deposit, smoothing, start, the
+ * iteration as a conditional WHILE node with the device-side stopping test, and shifts), the
+ * classes' chains independent of each other, so one item per class is in flight at a time; the
+ * host waits once, at the end.  Otherwise the items run one after another through the handle API.
+ * With autotune = 1, a size class not seen before in this process is first tuned on its first
+ * item, before the batch runs and outside every item's time: the deposit path, the x-line FFT tile
+ * width, at N = 512 the k-space kernel family (register-fused or generic), and the shift path; the
+ * fastest are kept for the process (recon_batch_plan).  Returns the first error of any item
+ * (per-item statuses in items[i].status), else OK. */
 recon_status recon_batch_run(recon_batch_item* items, int n_items, void* stream, int autotune);
 
 /* The schedule the batch autotuner chose for mesh side nmesh (STATE if none yet). */

@@ -225,6 +225,21 @@ def start_coefficient(start: int, beta: float) -> float:
     raise ValueError("unknown start")
 
 
+def start_estimate(delta, b: float, f: float, L: float, rhat, start: int = START_PLAIN):
+    """Starting estimate of Sec. 5.2: Psi_0 = Z[delta/b] - c (Z[delta/b].r) r, and Z[delta/b]."""
+    psi_s = zeldovich(delta / b, L)
+    c = start_coefficient(start, f / b)
+    return psi_s - c * radial_projection(psi_s, rhat), psi_s
+
+
+def update(psi, delta, b: float, f: float, L: float, rhat):
+    """One step of Eq. iterative (Sec. 5.1): the estimate of the real-space delta/b,
+    S = delta/b + beta div((Psi.r) r), and the new displacement Z[S] (Psi_FFT = -grad grad^-2 S)."""
+    n = delta.shape[0]
+    S_k = fft3(delta / b) + (f / b) * divergence(radial_projection(psi, rhat), L)
+    return np.stack([ifft3(c_k, n) for c_k in zeldovich_k(S_k, n, L)])
+
+
 def iterate(delta, b: float, f: float, L: float, rhat, start: int = START_PLAIN,
             tol: float = 0.0, max_iter: int = 6, return_all: bool = False):
     """Iterative solution of Eq. Nusser (Sec. 5.1, Eq. iterative), Psi in configuration space.
@@ -237,18 +252,11 @@ def iterate(delta, b: float, f: float, L: float, rhat, start: int = START_PLAIN,
     Z[delta/b] for every start.  Stops when rel[n] < tol with n >= 1, or after max_iter updates.
     Returns (Psi_final (3,n,n,n), rel list, n_updates[, list of all Psi_n]).
     """
-    n = delta.shape[0]
-    beta = f / b
-    src0 = delta / b
-    psi_s = zeldovich(src0, L)
-    c = start_coefficient(start, beta)
-    psi = psi_s - c * radial_projection(psi_s, rhat)
-    prev_for_rel = psi_s
+    psi, prev_for_rel = start_estimate(delta, b, f, L, rhat, start)
     rels, history = [], [psi]
     it = 0
     while it < max_iter:
-        S_k = fft3(src0) + beta * divergence(radial_projection(psi, rhat), L)
-        psi_new = np.stack([ifft3(c_k, n) for c_k in zeldovich_k(S_k, n, L)])
+        psi_new = update(psi, delta, b, f, L, rhat)
         num = np.sqrt(((psi_new - prev_for_rel) ** 2).sum())
         den = np.sqrt((psi_new ** 2).sum())
         rels.append(num / den if den > 0 else 0.0)
@@ -294,6 +302,56 @@ def shift_vectors(psi, pos, L: float, f: float, observer, los_mode: int, is_gala
 def shifted_positions(pos, d, L: float, periodic: bool):
     x = np.asarray(pos, dtype=np.float64) + d
     return np.mod(x, L) if periodic else x
+
+
+# --------------------------------------------------------------------------------------------
+# Diagnostics of the paper (Sec. 4.1 Helmholtz split, Sec. 4.3 / 5.2 radial ratio)
+# --------------------------------------------------------------------------------------------
+RATIO_LO, RATIO_HI = -1.0, 3.0   # Tables 1-3: ratios above 3 or below -1 are outliers
+
+
+def ratio_stats(num, den, lo: float = RATIO_LO, hi: float = RATIO_HI):
+    """Mean and standard deviation of the ratio num/den over all points, outliers removed (Table 1-3
+    rule: a ratio above hi or below lo; a zero denominator counts as an outlier).  Returns
+    (mean, std, outlier fraction, number kept); std is the population value of the kept ratios."""
+    num = np.asarray(num, dtype=np.float64).ravel()
+    den = np.asarray(den, dtype=np.float64).ravel()
+    ok = den != 0
+    r = num[ok] / den[ok]
+    keep = (r >= lo) & (r <= hi)
+    kept = r[keep]
+    n_keep = kept.size
+    mean = kept.mean() if n_keep else 0.0
+    std = kept.std() if n_keep else 0.0
+    return mean, std, 1.0 - n_keep / num.size, n_keep
+
+
+def radial_ratio(psi_real, psi_est, pos, L: float, observer, los_mode: int, periodic: bool = False,
+                 lo: float = RATIO_LO, hi: float = RATIO_HI):
+    """Eq. ratio at particle positions: (Psi_real . r) / (Psi_est . r), both fields CIC-interpolated
+    to each particle and projected on the particle's line of sight; statistics as ratio_stats."""
+    rh = particle_rhat(np.mod(pos, L) if periodic else pos, observer, los_mode)
+    a = (cic_gather(psi_real, pos, L) * rh).sum(1)
+    b = (cic_gather(psi_est, pos, L) * rh).sum(1)
+    return ratio_stats(a, b, lo, hi)
+
+
+def helmholtz_x(psi, L: float):
+    """Sec. 4.1, plane-parallel split of (Psi.x) x with Psi_x = Psi.x (Eq. Helmholtz): in Fourier
+    space the irrotational part grad A has components (k_j k_x / k^2) Psi_x(k) (Eq. irrotational)
+    and the solenoidal part curl B = (Psi.x) x - grad A (Eq. solenoidal: ((k_y^2 + k_z^2) / k^2,
+    -k_y k_x / k^2, -k_z k_x / k^2) Psi_x(k)).  Derivative wavenumbers as in the rest of the oracle
+    (zero at the Nyquist index); k = 0 carries no irrotational part.  Returns (grad_A, curl_B),
+    each (3, n, n, n)."""
+    n = psi.shape[-1]
+    _, kd, k2 = kgrid(n, L)
+    inv = np.zeros_like(k2)
+    np.divide(1.0, k2, out=inv, where=k2 > 0)
+    Px = fft3(psi[0])
+    grad_a = np.stack([ifft3(kd[j] * kd[0] * inv * Px, n) for j in range(3)])
+    curl_b = -grad_a
+    curl_b[0] += psi[0]
+    return grad_a, curl_b
 
 
 # --------------------------------------------------------------------------------------------

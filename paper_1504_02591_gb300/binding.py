@@ -34,9 +34,10 @@ ABI_SYMBOLS = (
     "recon_unet_destroy", "recon_unet_last_error", "recon_unet_set_option", "recon_unet_get_layer",
     "recon_unet_launch_count",
     "recon_iterate_from", "recon_start_features",
-    "recon_get_radial",
+    "recon_get_radial", "recon_radial_ratio", "recon_ratio_stats", "recon_helmholtz_x",
 )
 OPT_DEPOSIT_PATH, OPT_SHIFT_PATH, OPT_GRAPH, OPT_LINE_TILE, OPT_KSPACE_GENERIC, OPT_REUSE_SORT = 0, 1, 2, 3, 4, 5
+OPT_PLANE_BATCH = 6
 UNET_OPT_TENSOR_CORES = 0
 PATH_DIRECT, PATH_SORTED = 0, 1
 KERNEL_KINDS = ("deposit", "z_fwd", "z_inv", "z_delta", "z_proj", "z_final", "line_fwd", "line_inv",
@@ -118,6 +119,9 @@ def load(path: str = LIB_PATH):
     lib.recon_unet_launch_count.argtypes = [VP, C.POINTER(C.c_longlong)]
     lib.recon_unet_last_error.argtypes = [VP]
     lib.recon_unet_last_error.restype = C.c_char_p
+    lib.recon_radial_ratio.argtypes = [VP, VP, VP, P(ReconCatalog), D, D, P(D)]
+    lib.recon_ratio_stats.argtypes = [VP, VP, VP, C.c_int64, D, D, P(D)]
+    lib.recon_helmholtz_x.argtypes = [VP, VP, VP, VP]
     lib.recon_cic_deposit_noalloc.argtypes = [VP, I, VP, C.c_int64, I, D, VP, VP, VP]
     lib.recon_status_str.argtypes = [I]
     lib.recon_status_str.restype = C.c_char_p
@@ -322,6 +326,37 @@ class Recon:
         self._check(st, "recon_shift")
         return (sh, po) if want_pos else sh
 
+    # -- the paper's diagnostics -----------------------------------------------------------------
+    def radial_ratio(self, psi_num, psi_den, pos, lo=-1.0, hi=3.0):
+        """Eq. ratio at the particles pos (CUDA (n, 3)): (mean, std, outlier fraction, kept)."""
+        keep = []
+        cat = _catalog(pos, None, keep)
+        a = psi_num.contiguous()
+        b = psi_den.contiguous()
+        out = (C.c_double * 4)()
+        self._check(self.lib.recon_radial_ratio(self.h, C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()),
+                                                C.byref(cat), float(lo), float(hi), out), "recon_radial_ratio")
+        return out[0], out[1], out[2], int(out[3])
+
+    def ratio_stats(self, num, den, lo=-1.0, hi=3.0):
+        """Ratio statistics of two CUDA float32 arrays: (mean, std, outlier fraction, kept)."""
+        a = num.contiguous()
+        b = den.contiguous()
+        out = (C.c_double * 4)()
+        self._check(self.lib.recon_ratio_stats(self.h, C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()),
+                                               a.numel(), float(lo), float(hi), out), "recon_ratio_stats")
+        return out[0], out[1], out[2], int(out[3])
+
+    def helmholtz_x(self, psi_x):
+        """Sec. 4.1 split of (Psi.x) x: (grad_A, curl_B), each a (3, N, N, N) CUDA tensor."""
+        import torch
+        x = psi_x.to(device="cuda", dtype=torch.float32).contiguous()
+        ga = torch.empty((3, self.n, self.n, self.n), dtype=torch.float32, device="cuda")
+        cb = torch.empty_like(ga)
+        self._check(self.lib.recon_helmholtz_x(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(ga.data_ptr()),
+                                               C.c_void_p(cb.data_ptr())), "recon_helmholtz_x")
+        return ga, cb
+
     # -- accessors -------------------------------------------------------------------------------
     def get_psi(self):
         import torch
@@ -397,29 +432,35 @@ class Recon:
 
 
 def batch_run(mocks, start=START_FFTA, tol=1e-6, max_iter=80, autotune=True, stream=None, **over):
-    """Reconstruct a list of mocks.Mock in one recon_batch_run call.
+    """Reconstruct a list of mocks in one recon_batch_run call.
 
-    Catalogues are moved to the GPU first (one CUDA tensor per catalogue); returns, per mock, a dict
-    with n_iter, rel, status, ms and the galaxy / random shift tensors."""
+    Each entry is a mocks.Mock (numpy catalogues, moved to the GPU first) or a dict with "params"
+    (as Mock.params()), "gal" and "ran" (CUDA float64 (n, 3) tensors, "ran" None for uniform mean
+    density).  Returns the batch status and, per mock, a dict with n_iter, rel, status, ms and the
+    galaxy / random shift tensors."""
     import torch
     lib = load()
     items = (ReconBatchItem * len(mocks))()
     keep, outs = [], []
     for i, m in enumerate(mocks):
-        p = m.params(**over)
+        if isinstance(m, dict):
+            p = dict(m["params"], **over)
+            g, r = m["gal"], m["ran"]
+        else:
+            p = m.params(**over)
+            g = torch.from_numpy(m.galaxies.pos).cuda()
+            r = torch.from_numpy(m.randoms.pos).cuda() if m.randoms is not None and not p["uniform"] else None
         items[i].params = make_params(p["n"], p["L"], p["b"], p["f"], p["R"], p["observer"], p["los_mode"],
                                       p["periodic"], p["mask_frac"], p["lognormal"], p["uniform"])
-        g = torch.from_numpy(m.galaxies.pos).cuda()
         items[i].gal = _catalog(g, None, keep)
         sg = torch.empty((len(g), 3), dtype=torch.float32, device="cuda")
         items[i].shift_gal = sg.data_ptr()
         sr = None
-        if m.randoms is not None and not p["uniform"]:
-            r = torch.from_numpy(m.randoms.pos).cuda()
+        if r is not None and not p["uniform"]:
             items[i].ran = _catalog(r, None, keep)
             sr = torch.empty((len(r), 3), dtype=torch.float32, device="cuda")
             items[i].shift_ran = sr.data_ptr()
-        keep += [sg, sr]
+        keep += [g, r, sg, sr]
         items[i].start, items[i].tol, items[i].max_iter, items[i].out_on_device = int(start), float(tol), int(max_iter), 1
         outs.append((sg, sr))
     st = (stream or torch.cuda.current_stream()).cuda_stream

@@ -226,6 +226,95 @@ cudaError_t launch_add_scalar(float* x, size_t n, float v, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// One ratio into the running statistics (float64; the decision at the cut is taken in float64 on
+// the float32 inputs).
+__device__ __forceinline__ void ratio_acc(float num, float den, double lo, double hi, double (&acc)[4]) {
+  acc[3] += 1.0;
+  if (den != 0.f) {
+    const double r = (double)num / (double)den;
+    if (r >= lo && r <= hi) {
+      acc[0] += 1.0;
+      acc[1] += r;
+      acc[2] += r * r;
+    }
+  }
+}
+
+__device__ __forceinline__ void ratio_flush(double (&acc)[4], double* partials) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double s = block_sum_d(acc[q]);
+    if (threadIdx.x == 0) partials[4 * blockIdx.x + q] = s;
+  }
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(256) radial_ratio_kernel(const PT* __restrict__ pos, long long np, RatioArgs a) {
+  const size_t nn = (size_t)a.n;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np;
+       p += (long long)gridDim.x * blockDim.x) {
+    int i0[3], i1[3];
+    float t[3];
+    cic_setup(pos, p, a.n, a.scale, i0, i1, t);
+    const size_t r00 = ((size_t)i0[0] * nn + i0[1]) * nn, r01 = ((size_t)i0[0] * nn + i1[1]) * nn;
+    const size_t r10 = ((size_t)i1[0] * nn + i0[1]) * nn, r11 = ((size_t)i1[0] * nn + i1[1]) * nn;
+    const float wx0 = 1.f - t[0], wx1 = t[0], wy0 = 1.f - t[1], wy1 = t[1], wz0 = 1.f - t[2], wz1 = t[2];
+    const size_t idx[8] = {r00 + i0[2], r00 + i1[2], r01 + i0[2], r01 + i1[2],
+                           r10 + i0[2], r10 + i1[2], r11 + i0[2], r11 + i1[2]};
+    const float cw[8] = {wx0 * wy0 * wz0, wx0 * wy0 * wz1, wx0 * wy1 * wz0, wx0 * wy1 * wz1,
+                         wx1 * wy0 * wz0, wx1 * wy0 * wz1, wx1 * wy1 * wz0, wx1 * wy1 * wz1};
+    float rv[3];
+    if (a.los_mode == 1) {
+      rv[0] = a.los.x; rv[1] = a.los.y; rv[2] = a.los.z;
+    } else {
+      const int n = a.n;
+      const float dx = fmaf(t[0], a.H, a.off[i0[0]]), dy = fmaf(t[1], a.H, a.off[n + i0[1]]),
+                  dz = fmaf(t[2], a.H, a.off[2 * n + i0[2]]);
+      const float q = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      const float ir = q > 0.f ? rsqrtf(q) : 0.f;
+      rv[0] = dx * ir; rv[1] = dy * ir; rv[2] = dz * ir;
+    }
+    float un = 0.f, ud = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float gn = 0.f, gd = 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        gn = fmaf(cw[k], __ldg(a.num[c] + idx[k]), gn);
+        gd = fmaf(cw[k], __ldg(a.den[c] + idx[k]), gd);
+      }
+      un = fmaf(gn, rv[c], un);
+      ud = fmaf(gd, rv[c], ud);
+    }
+    ratio_acc(un, ud, a.lo, a.hi, acc);
+  }
+  ratio_flush(acc, a.partials);
+}
+
+__global__ void __launch_bounds__(256) ratio_kernel(const float* __restrict__ num, const float* __restrict__ den,
+                                                    size_t n, double lo, double hi, double* __restrict__ partials) {
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    ratio_acc(num[i], den[i], lo, hi, acc);
+  ratio_flush(acc, partials);
+}
+
+cudaError_t launch_radial_ratio(const void* pos, int dtype, long long np, const RatioArgs& a, int blocks,
+                                cudaStream_t st) {
+  if (dtype == 0)
+    radial_ratio_kernel<double><<<blocks, 256, 0, st>>>((const double*)pos, np, a);
+  else
+    radial_ratio_kernel<float><<<blocks, 256, 0, st>>>((const float*)pos, np, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ratio(const float* num, const float* den, size_t n, double lo, double hi, double* partials,
+                         int blocks, cudaStream_t st) {
+  ratio_kernel<<<blocks, 256, 0, st>>>(num, den, n, lo, hi, partials);
+  return cudaGetLastError();
+}
+
 }  // namespace rg
 
 // ------------------------------------------------------------------------------------------------

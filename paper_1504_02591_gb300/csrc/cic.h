@@ -34,4 +34,27 @@ cudaError_t launch_finalize(const double* partials, int nblocks, int nq, double*
                             cudaStream_t st, double* bsum = nullptr, unsigned int* counter = nullptr);
 cudaError_t launch_add_scalar(float* x, size_t n, float v, cudaStream_t st);
 
+// Ratio statistics of the paper's diagnostics (Eq. ratio; Tables 1-3): per block, the number of
+// ratios num/den inside [lo, hi] (a zero denominator is outside), their sum and sum of squares in
+// float64, and the number of points: partials[4 b + 0..3].
+struct RatioArgs {
+  const float* num[3];   // radial form: the two vector fields (Psi_real, Psi_est), N^3 each
+  const float* den[3];
+  int n;
+  double scale;          // N / L
+  int los_mode;
+  float3 los;
+  const float* off;      // 3 N node offsets from the observer
+  float H;
+  double lo, hi;
+  double* partials;
+};
+// (Psi_num . r)/(Psi_den . r) at each particle, both fields CIC-interpolated, r the particle's line
+// of sight (its image in [0, L), as in the shift).
+cudaError_t launch_radial_ratio(const void* pos, int dtype, long long np, const RatioArgs& a, int blocks,
+                                cudaStream_t st);
+// num[i] / den[i] over n values.
+cudaError_t launch_ratio(const float* num, const float* den, size_t n, double lo, double hi, double* partials,
+                         int blocks, cudaStream_t st);
+
 }  // namespace rg

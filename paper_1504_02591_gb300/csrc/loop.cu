@@ -40,4 +40,27 @@ cudaError_t launch_loop_decide(LoopState* s, const double* red, cudaGraphConditi
   return cudaGetLastError();
 }
 
+__global__ void stamp_kernel(unsigned long long* t) {
+  unsigned long long v;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+  *t = v;
+}
+
+__global__ void loop_record_kernel(const LoopState* s, BatchSlot* out) {
+  const int it = s->it;
+  out->flag = s->flag;
+  out->it = it;
+  out->rel = (it > 0 && it <= kMaxTrace) ? s->trace[it - 1] : 0.0;
+}
+
+cudaError_t launch_stamp(unsigned long long* t, cudaStream_t st) {
+  stamp_kernel<<<1, 1, 0, st>>>(t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loop_record(const LoopState* s, BatchSlot* out, cudaStream_t st) {
+  loop_record_kernel<<<1, 1, 0, st>>>(s, out);
+  return cudaGetLastError();
+}
+
 }  // namespace rg

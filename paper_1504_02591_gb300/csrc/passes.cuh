@@ -245,16 +245,19 @@ __global__ void __launch_bounds__(kZThreads, 4) zpass_kernel(const ZArgs a) {
             if (++idx == N) idx = 0;
           }
         }
-        float d;
+        // q = 1 + delta as the density ratio itself: the logarithm takes q, not 1 + (q - 1), which
+        // in float32 would lose the digits of a low-density node to cancellation
+        float q;
         if (nin == 1) {
-          d = g * inv_alpha - 1.f;
+          q = g * inv_alpha;
         } else {
           const bool in = r > thr;
-          d = in ? g * inv_alpha / r - 1.f : 0.f;
+          q = in ? g * inv_alpha / r : 1.f;
           acc1 += in ? 1.f : 0.f;
         }
+        float d = q - 1.f;
         if (a.lognormal) {
-          d = logf(fmaxf(1.f + d, 1e-6f));
+          d = logf(fmaxf(q, 1e-6f));
           acc0 += d;
         }
         if (a.delta_real) a.delta_real[row * N + z] = d;
@@ -550,8 +553,11 @@ __global__ void __launch_bounds__(kZThreads, 2) zfused8_kernel(const ZArgs a) {
   const bool fin = (MODE == Z_PROJ) && a.loop_flag && *a.loop_flag == 1;
   const int partner = (32 - lane) & 31;
   const Geometry& g = a.g;
+  // rows (ix, iy) of every y-plane, or of the planes [ybeg, ybeg + ycount)
+  const size_t nrows = a.ycount ? (size_t)N * a.ycount : (size_t)N * N;
 
-  for (size_t row = (size_t)blockIdx.x * kZWarps + warp; row < (size_t)N * N; row += (size_t)gridDim.x * kZWarps) {
+  for (size_t lr = (size_t)blockIdx.x * kZWarps + warp; lr < nrows; lr += (size_t)gridDim.x * kZWarps) {
+    const size_t row = a.ycount ? (lr / a.ycount) * N + a.ybeg + lr % a.ycount : lr;
     const int ix = (int)(row / N), iy = (int)(row % N);
     if (MODE == Z_PROJ && fin) {
       float2 x[3][8], xl[3], A[3][4], B[3][4];
@@ -745,16 +751,17 @@ __global__ void __launch_bounds__(kZThreads, 2) zdelta8_kernel(const ZArgs a) {
     float d[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      float dv;
+      float q;   // 1 + delta, kept as the ratio for the logarithm (see the generic pass)
       if (nin == 1) {
-        dv = ag[v] * inv_alpha - 1.f;
+        q = ag[v] * inv_alpha;
       } else {
         const bool in = ar[v] > thr;
-        dv = in ? ag[v] * inv_alpha / ar[v] - 1.f : 0.f;
+        q = in ? ag[v] * inv_alpha / ar[v] : 1.f;
         acc1 += in ? 1.f : 0.f;
       }
+      float dv = q - 1.f;
       if (a.lognormal) {
-        dv = logf(fmaxf(1.f + dv, 1e-6f));
+        dv = logf(fmaxf(q, 1e-6f));
         acc0 += dv;
       }
       d[v] = dv;
@@ -1237,7 +1244,14 @@ __global__ void __launch_bounds__(XLine8<C>::T, 2) xline8_kernel(const SArgs a) 
   float2* s = tw + XLine8<C>::TAB;
   if (!INV && a.skip_flag && *a.skip_flag != 0) return;   // uniform: device loop already converged
   for (int m = threadIdx.x; m < Plan<N>::kTab; m += T) tw[m] = a.tab[m];
-  const Tile t = tile_of<N, C, AX_X>(blockIdx.x);
+  // tiles of every y-plane, or of the planes [ybeg, ybeg + ycount): their M tiles (ky, kz block)
+  // and the Nyquist tiles that hold their ky columns
+  int ti = blockIdx.x;
+  if (a.ycount) {
+    const int mt = a.ycount * (H / C);
+    ti = ti < mt ? a.ybeg * (H / C) + ti : N * (H / C) + a.ybeg / C + (ti - mt);
+  }
+  const Tile t = tile_of<N, C, AX_X>(ti);
   const int col = threadIdx.x % C, jb = threadIdx.x / C;
   // element offsets fit 32 bits (at most N^3 / 2 complex points per field)
   const uint32_t o0 = (uint32_t)t.base + (uint32_t)(col * t.cs) + (uint32_t)jb * (uint32_t)t.ls;
@@ -1468,9 +1482,12 @@ struct MeshImpl {
         if (occ < 1) return cudaErrorInvalidConfiguration;
         grid = occ * sm < kZBlocks ? occ * sm : kZBlocks;
       }
-      if (grid_out) *grid_out = grid;
+      if (a.ycount && (a.ybeg < 0 || a.ycount < 0 || a.ybeg + a.ycount > N)) return cudaErrorInvalidValue;
+      const int rows_blocks = a.ycount ? (N * a.ycount + kZWarps - 1) / kZWarps : kZBlocks;
+      const int g = grid < rows_blocks ? grid : rows_blocks;
+      if (grid_out) *grid_out = g;
       void* args[] = {const_cast<ZArgs*>(&a)};
-      return cudaLaunchKernel(k, dim3(grid), dim3(kZThreads), args, smem, st);
+      return cudaLaunchKernel(k, dim3(g), dim3(kZThreads), args, smem, st);
     }
     return cudaErrorInvalidValue;
   }
@@ -1573,8 +1590,9 @@ struct MeshImpl {
       if (e != cudaSuccess) return e;
       attr[inv] = true;
     }
+    if (a.ycount && (a.ycount % C || a.ybeg % C || a.ybeg < 0 || a.ybeg + a.ycount > N)) return cudaErrorInvalidValue;
     void* args[] = {const_cast<SArgs*>(&a)};
-    constexpr int tiles = N * ((N / 2) / C) + N / C;
+    const int tiles = a.ycount ? a.ycount * ((N / 2) / C) + a.ycount / C : N * ((N / 2) / C) + N / C;
     return cudaLaunchKernel(k, dim3(tiles, PAIR ? 2 : ncomp), dim3(XLine8<C>::T), args, XLine8<C>::smem, st);
   }
   static cudaError_t xlaunch(bool inv, const SArgs& a, cudaStream_t st, int ncomp, bool pair) {

@@ -16,9 +16,11 @@
 #include <vector>
 
 #include "../../include/recon.h"
+#include "batch_graph.h"
 #include "bricks.h"
 #include "cic.h"
 #include "conv.h"
+#include "diag.h"
 #include "loop.h"
 #include "warm.h"
 #include "types.h"
@@ -130,6 +132,9 @@ struct recon_handle {
   float* off = nullptr;
   float* taps = nullptr;   // smoothing kernel g[t0 .. t0 + ntap - 1]
   int ntap = 1, t0 = 0;
+  // the tables the passes read: the handle's own (taps, off) or a batch's per-mock copies
+  const float* cur_taps = nullptr;
+  const float* cur_off = nullptr;
   double* red = nullptr;
   LoopState* loop = nullptr;   // device-driven iteration state (inside the red region)
   cudaStream_t cap_stream = nullptr;   // private stream for graph capture
@@ -147,6 +152,7 @@ struct recon_handle {
   int shift_path = RECON_PATH_SORTED;
   int narrow_lines = 0;
   int kspace_generic = 0;
+  int plane_batch = 0;   // register-fused path: y-planes per batch of the x -> z -> x passes (0: off)
   int reuse_sort = 0;
   // the catalogue whose brick order the sort buffers hold (sorted deposit, one chunk)
   struct SortMemo {
@@ -169,6 +175,30 @@ struct recon_handle {
   double bytes[RECON_K_COUNT] = {};
   struct Pending { int kind; cudaEvent_t a, b; };
   std::vector<Pending> pending;
+  // the instantiated iteration graph of the last device-driven recon_iterate(_from), relaunched
+  // while every value it captured is unchanged (see GraphKey)
+  struct GraphKey {
+    uint32_t coef0_bits;
+    const float* u0;
+    int level, max_iter, d_is_k, generic, narrow, planes;
+    uint64_t tol_bits;
+    uint64_t epoch;
+    bool operator==(const GraphKey& o) const {
+      return coef0_bits == o.coef0_bits && u0 == o.u0 && level == o.level && max_iter == o.max_iter &&
+             d_is_k == o.d_is_k && generic == o.generic && narrow == o.narrow && planes == o.planes &&
+             tol_bits == o.tol_bits &&
+             epoch == o.epoch;
+    }
+  };
+  struct GraphCache {
+    bool valid = false;
+    GraphKey key{};
+    cudaGraph_t start = nullptr, whole = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t start_launches[RECON_K_COUNT] = {}, body_launches[RECON_K_COUNT] = {};
+    double start_bytes[RECON_K_COUNT] = {}, body_bytes[RECON_K_COUNT] = {};
+  } gcache;
+  uint64_t epoch = 0;   // incremented whenever the per-reconstruction parameters change
 };
 
 #define RG_CUDA(call)                                            \
@@ -295,14 +325,18 @@ double sbytes(const recon_handle* h, int mode, int nc, int axis) {
 }
 
 recon_status run_z(recon_handle* h, int mode, int nc, const ZArgs& a, int* grid = nullptr) {
-  RG_CUDA(timed(h, zkind(mode), zbytes(h, mode, nc, a), [&] { return h->mk->zpass(mode, nc, a, h->st, grid); }));
+  const double part = a.ycount ? (double)a.ycount / h->n : 1.0;   // a batch of y-planes
+  RG_CUDA(timed(h, zkind(mode), part * zbytes(h, mode, nc, a), [&] { return h->mk->zpass(mode, nc, a, h->st, grid); }));
   return RECON_OK;
 }
 
 recon_status run_s(recon_handle* h, int mode, int nc, int axis, const SArgs& a) {
-  RG_CUDA(timed(h, skind(mode, axis), sbytes(h, mode, nc, axis), [&] { return h->mk->spass(mode, nc, axis, a, h->st); }));
+  const double part = a.ycount ? (double)a.ycount / h->n : 1.0;
+  RG_CUDA(timed(h, skind(mode, axis), part * sbytes(h, mode, nc, axis), [&] { return h->mk->spass(mode, nc, axis, a, h->st); }));
   return RECON_OK;
 }
+
+
 
 recon_status finalize(recon_handle* h, int nblocks, int nq, int dst, int accumulate) {
   RG_CUDA(timed(h, RECON_K_OTHER, 8.0 * nblocks * nq, [&] {
@@ -315,6 +349,32 @@ recon_status finalize(recon_handle* h, int nblocks, int nq, int dst, int accumul
     recon_status s_ = (x);             \
     if (s_ != RECON_OK) return s_;     \
   } while (0)
+
+// Whether the x -> z -> x passes of an update run in batches of y-planes (register-fused path):
+// the x passes transform lines at fixed (y, kz) and the z pass rows at fixed (x, y), so each batch
+// of planes can go through all three before the next, and its fields stay in the L2 in between.
+int plane_batch(const recon_handle* h) {
+  return (h->plane_batch && h->mk->kspace_fused && !h->kspace_generic) ? h->plane_batch : 0;
+}
+
+// Inverse x, the projection pass and forward x over all y-planes, batch by batch.  za and the x
+// arguments carry the device loop's flags when the passes run inside the iteration graph.
+recon_status xzx_batched(recon_handle* h, int B, const ZArgs& za0, const int* skip_flag) {
+  for (int y0 = 0; y0 < h->n; y0 += B) {
+    SArgs xa = sargs(h);
+    for (int q = 0; q < 3; ++q) xa.f[q] = h->V[q];
+    xa.ybeg = y0;
+    xa.ycount = B;
+    RG_TRY(run_s(h, S_INV, 3, AX_X, xa));
+    ZArgs za = za0;
+    za.ybeg = y0;
+    za.ycount = B;
+    RG_TRY(run_z(h, Z_PROJ, 3, za));
+    xa.skip_flag = skip_flag;
+    RG_TRY(run_s(h, S_FWD, 3, AX_X, xa));
+  }
+  return RECON_OK;
+}
 
 // plain X pass (one FFT along x per component) over nc fields.  The forward 3-D transform runs
 // Z (r2c) -> X -> Y, the inverse Y -> X -> Z; the Y passes carry the k-space work.
@@ -436,30 +496,25 @@ double start_coefficient(int start, double beta) {
 
 }  // namespace
 
-namespace {
+namespace rg {
 
-// Per-reconstruction parameters that do not change the mesh: box, bias, growth rate, smoothing
-// length, line of sight, mask and density options.  Uploads the node offsets from the observer and
-// the smoothing taps, and resets the call sequence.
-recon_status configure(recon_handle* h, const recon_params* p) {
-  h->memo.valid = 0;
-  h->p = *p;
-  h->L = p->box[0];
-  h->bb.scale = (double)h->n / h->L;
-  const int n = h->n;
-  std::vector<float> off(3 * n);
-  const double H = h->L / n;
+// Host tables of one parameter set: node offsets from the observer (3 N floats; x then y then z)
+// and the Gaussian smoothing kernel as a periodic convolution per axis,
+// g[t] = (1/N) sum_m exp(-k_m^2 R^2/2) cos(2 pi m t / N); taps beyond the last |g[t]| > 1e-9 g[0]
+// are dropped, and a kernel that has not decayed by then is used over the whole period.
+void config_tables(int n, const recon_params* p, std::vector<float>& taps, int* t0, int* ntap,
+                   std::vector<float>& off) {
+  const double L = p->box[0];
+  off.assign(3 * n, 0.f);
+  const double H = L / n;
   for (int a = 0; a < 3; ++a)
     for (int i = 0; i < n; ++i) off[a * n + i] = (float)((double)i * H - p->observer[a]);
-  // Gaussian smoothing as a periodic convolution per axis: g[t] = (1/N) sum_m exp(-k_m^2 R^2/2)
-  // cos(2 pi m t / N); taps beyond the last |g[t]| > 1e-9 g[0] are dropped, and a kernel that has
-  // not decayed by then is used over the whole period.
   std::vector<double> gk(n);
   for (int t = 0; t < n; ++t) {
     double acc = 0.0;
     for (int m = 0; m < n; ++m) {
       const int mm = (m <= n / 2) ? m : m - n;
-      const double k = 2.0 * M_PI * mm / h->L;
+      const double k = 2.0 * M_PI * mm / L;
       acc += std::exp(-0.5 * k * k * p->smooth_R * p->smooth_R) * std::cos(2.0 * M_PI * (double)m * t / n);
     }
     gk[t] = acc / n;
@@ -468,17 +523,33 @@ recon_status configure(recon_handle* h, const recon_params* p) {
   for (int t = 1; t <= n / 2; ++t)
     if (std::fabs(gk[t]) > 1e-9 * std::fabs(gk[0])) K = t;
   if (2 * K + 1 >= n) {
-    h->t0 = -n / 2;
-    h->ntap = n;
+    *t0 = -n / 2;
+    *ntap = n;
   } else {
-    h->t0 = -K;
-    h->ntap = 2 * K + 1;
+    *t0 = -K;
+    *ntap = 2 * K + 1;
   }
-  std::vector<float> taps(h->ntap);
-  for (int j = 0; j < h->ntap; ++j) taps[j] = (float)gk[((h->t0 + j) % n + n) % n];
-  RG_CUDA(cudaMemcpyAsync(h->taps, taps.data(), h->ntap * sizeof(float), cudaMemcpyHostToDevice, h->st));
-  RG_CUDA(cudaMemcpyAsync(h->off, off.data(), 3 * n * sizeof(float), cudaMemcpyHostToDevice, h->st));
-  RG_CUDA(cudaStreamSynchronize(h->st));   // the host vectors go out of scope
+  taps.assign(*ntap, 0.f);
+  for (int j = 0; j < *ntap; ++j) taps[j] = (float)gk[((*t0 + j) % n + n) % n];
+}
+
+}  // namespace rg
+
+namespace {
+
+// Point the handle at a parameter set whose tables already sit in device memory (taps_dev holds
+// ntap floats, off_dev 3 N floats), without touching the device; resets the call sequence.
+void apply_config(recon_handle* h, const recon_params* p, const float* taps_dev, int t0, int ntap,
+                  const float* off_dev) {
+  h->memo.valid = 0;
+  h->p = *p;
+  h->L = p->box[0];
+  h->bb.scale = (double)h->n / h->L;
+  h->t0 = t0;
+  h->ntap = ntap;
+  h->cur_taps = taps_dev;
+  h->cur_off = off_dev;
+  const int n = h->n;
   Geometry& g = h->geo;
   g.n = n;
   g.kf = (float)(2.0 * M_PI / h->L);
@@ -491,11 +562,25 @@ recon_status configure(recon_handle* h, const recon_params* p) {
   } else {
     g.los = make_float3(0.f, 0.f, 0.f);
   }
-  g.off = h->off;
+  g.off = off_dev;
+  ++h->epoch;   // kernel arguments captured in a cached iteration graph are now stale
   h->state = ST_CREATED;
   h->warm_level = -1;
   h->d_is_k = 0;
   h->delta_real_valid = 0;
+}
+
+// Per-reconstruction parameters that do not change the mesh: box, bias, growth rate, smoothing
+// length, line of sight, mask and density options.  Uploads the node offsets from the observer and
+// the smoothing taps into the handle's own tables, and resets the call sequence.
+recon_status configure(recon_handle* h, const recon_params* p) {
+  std::vector<float> taps, off;
+  int t0 = 0, ntap = 1;
+  config_tables(h->n, p, taps, &t0, &ntap, off);
+  RG_CUDA(cudaMemcpyAsync(h->taps, taps.data(), ntap * sizeof(float), cudaMemcpyHostToDevice, h->st));
+  RG_CUDA(cudaMemcpyAsync(h->off, off.data(), 3 * h->n * sizeof(float), cudaMemcpyHostToDevice, h->st));
+  RG_CUDA(cudaStreamSynchronize(h->st));   // the host vectors go out of scope
+  apply_config(h, p, h->taps, t0, ntap, h->off);
   return RECON_OK;
 }
 
@@ -541,7 +626,7 @@ recon_status recon_create(const recon_params* p, void* stream, void* workspace, 
   if (workspace) {
     if (workspace_bytes < h->lay.total || ((uintptr_t)workspace & 255)) {
       delete h;
-      return workspace_bytes < 0 ? RECON_ERR_INVALID_ARG : RECON_ERR_OOM;
+      return ((uintptr_t)workspace & 255) ? RECON_ERR_INVALID_ARG : RECON_ERR_OOM;
     }
     h->ws = (char*)workspace;
     h->ws_bytes = workspace_bytes;
@@ -640,8 +725,12 @@ recon_status recon_reset_timing(recon_handle* h) {
   return RECON_OK;
 }
 
+recon_status set_plane_batch(recon_handle* h, int value);
+
 recon_status recon_set_option(recon_handle* h, int option, int value) {
-  if (!h || (value != 0 && value != 1)) return RECON_ERR_INVALID_ARG;
+  if (!h) return RECON_ERR_INVALID_ARG;
+  if (option == RECON_OPT_PLANE_BATCH) return set_plane_batch(h, value);
+  if (value != 0 && value != 1) return RECON_ERR_INVALID_ARG;
   if (option == RECON_OPT_DEPOSIT_PATH) h->deposit_path = value;
   else if (option == RECON_OPT_SHIFT_PATH) h->shift_path = value;
   else if (option == RECON_OPT_GRAPH) h->use_graph = value;
@@ -652,9 +741,20 @@ recon_status recon_set_option(recon_handle* h, int option, int value) {
   return RECON_OK;
 }
 
+recon_status set_plane_batch(recon_handle* h, int value) {
+  if (value != 0 && value != 16 && value != 32 && value != 64) return RECON_ERR_INVALID_ARG;
+  h->plane_batch = value;
+  return RECON_OK;
+}
+
+namespace {
+void drop_graph(recon_handle* h);   // releases the cached iteration graph (defined with it below)
+}  // namespace
+
 recon_status recon_destroy(recon_handle* h) {
   if (!h) return RECON_OK;
   drain_timing(h);
+  drop_graph(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->copy_st) {
     cudaStreamSynchronize(h->copy_st);
@@ -711,7 +811,7 @@ recon_status recon_smooth(recon_handle* h) {
   c.f[1] = reinterpret_cast<float*>(h->V[1].M);
   c.nf = nf;
   c.n = h->n;
-  c.taps = h->taps;
+  c.taps = h->cur_taps;
   c.ntap = h->ntap;
   c.t0 = h->t0;
   c.partials = h->partials;
@@ -731,7 +831,7 @@ recon_status recon_smooth(recon_handle* h) {
     a.f[1] = h->V[1];
     a.dout = h->D;
     a.delta_real = reinterpret_cast<float*>(h->V[2].M);
-    a.taps = h->taps;
+    a.taps = h->cur_taps;
     a.ntap = h->ntap;
     a.t0 = h->t0;
     int zg = 0;
@@ -756,10 +856,11 @@ recon_status iterate_start(recon_handle* h, float coef0) {
     a.d_is_k = h->d_is_k;
     RG_TRY(run_s(h, S_DELTA, 1, AX_Y, a));
   }
-  RG_TRY(xpass(h, S_INV, 3, h->V));
   ZArgs za = zargs(h);
   for (int q = 0; q < 3; ++q) za.f[q] = h->V[q];
   za.coef = coef0;
+  if (const int B = plane_batch(h)) return xzx_batched(h, B, za, nullptr);
+  RG_TRY(xpass(h, S_INV, 3, h->V));
   RG_TRY(run_z(h, Z_PROJ, 3, za));
   RG_TRY(xpass(h, S_FWD, 3, h->V));
   return RECON_OK;
@@ -774,10 +875,11 @@ recon_status iterate_body(recon_handle* h, cudaGraphConditionalHandle cond) {
   RG_TRY(run_s(h, S_ITER, 3, AX_Y, ia));
   RG_TRY(finalize(h, h->mk->s_blocks, 2, RED_NORM_D2, 0));
   RG_CUDA(timed(h, RECON_K_OTHER, 0.0, [&] { return launch_loop_decide(h->loop, h->red, cond, h->st); }));
-  RG_TRY(xpass(h, S_INV, 3, h->V));
   ZArgs za = zargs(h);
   for (int q = 0; q < 3; ++q) za.f[q] = h->V[q];
   za.loop_flag = &h->loop->flag;
+  if (const int B = plane_batch(h)) return xzx_batched(h, B, za, &h->loop->flag);
+  RG_TRY(xpass(h, S_INV, 3, h->V));
   RG_TRY(run_z(h, Z_PROJ, 3, za));
   SArgs fa = sargs(h);
   for (int q = 0; q < 3; ++q) fa.f[q] = h->V[q];
@@ -795,29 +897,32 @@ struct StartSpec {
 };
 recon_status run_start(recon_handle* h, const StartSpec& sp);
 
-struct GraphGuard {
-  cudaGraph_t gs = nullptr, g = nullptr;
-  cudaGraphExec_t ex = nullptr;
-  ~GraphGuard() {
-    if (ex) cudaGraphExecDestroy(ex);
-    if (g) cudaGraphDestroy(g);
-    if (gs) cudaGraphDestroy(gs);
-  }
-};
+void drop_graph(recon_handle* h) {
+  auto& c = h->gcache;
+  if (c.exec) cudaGraphExecDestroy(c.exec);
+  if (c.whole) cudaGraphDestroy(c.whole);
+  if (c.start) cudaGraphDestroy(c.start);
+  c = recon_handle::GraphCache{};
+}
 
 // The whole iteration as one CUDA graph: the start sequence, then a conditional WHILE node whose
-// body is one update.  One launch, one host synchronisation at the end.
-recon_status iterate_graph(recon_handle* h, const StartSpec& sp, double tol, int max_iter, int* it_out,
-                           double* rel_out, int* flag_out) {
+// body is one update.  One launch, one host synchronisation at the end.  The instantiated graph is
+// kept on the handle and relaunched by later calls whose captured values (start coefficient or
+// supplied displacement, level, tol, max_iter, options, parameters) are the same; anything else
+// rebuilds it.
+recon_status build_graph(recon_handle* h, const StartSpec& sp, double tol, int max_iter) {
+  drop_graph(h);
+  auto& c = h->gcache;
   if (!h->cap_stream) RG_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   const cudaStream_t user = h->st;
-  const int timing = h->timing;
-  int64_t before[RECON_K_COUNT];
-  GraphGuard gg;
+  int64_t l0[RECON_K_COUNT], l1[RECON_K_COUNT];
+  double b0[RECON_K_COUNT], b1[RECON_K_COUNT];
+  for (int k = 0; k < RECON_K_COUNT; ++k) {
+    l0[k] = h->launches[k];
+    b0[k] = h->bytes[k];
+  }
   recon_status rs = RECON_OK;
-  int64_t body_launches = 0;
   h->st = h->cap_stream;
-  h->timing = 0;
   do {
     cudaError_t e;
     if ((e = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
@@ -825,34 +930,68 @@ recon_status iterate_graph(recon_handle* h, const StartSpec& sp, double tol, int
       RG_CUDA(launch_loop_init(h->loop, tol, max_iter, h->st));
       return run_start(h, sp);
     }();
-    e = cudaStreamEndCapture(h->st, &gg.gs);
+    e = cudaStreamEndCapture(h->st, &c.start);
     if (rs != RECON_OK) break;
     if (e != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
-    if ((e = cudaGraphCreate(&gg.g, 0)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
+    for (int k = 0; k < RECON_K_COUNT; ++k) {
+      l1[k] = h->launches[k];
+      b1[k] = h->bytes[k];
+    }
+    if ((e = cudaGraphCreate(&c.whole, 0)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
     cudaGraphNode_t child = nullptr, cnode = nullptr;
-    if ((e = cudaGraphAddChildGraphNode(&child, gg.g, nullptr, 0, gg.gs)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
+    if ((e = cudaGraphAddChildGraphNode(&child, c.whole, nullptr, 0, c.start)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
     cudaGraphConditionalHandle cond;
-    if ((e = cudaGraphConditionalHandleCreate(&cond, gg.g, 1, cudaGraphCondAssignDefault)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
+    if ((e = cudaGraphConditionalHandleCreate(&cond, c.whole, 1, cudaGraphCondAssignDefault)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
     cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
     np.conditional.handle = cond;
     np.conditional.type = cudaGraphCondTypeWhile;
     np.conditional.size = 1;
-    if ((e = cudaGraphAddNode(&cnode, gg.g, &child, nullptr, 1, &np)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
+    if ((e = cudaGraphAddNode(&cnode, c.whole, &child, nullptr, 1, &np)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
     cudaGraph_t body = np.conditional.phGraph_out[0];
-    for (int k = 0; k < RECON_K_COUNT; ++k) before[k] = h->launches[k];
     if ((e = cudaStreamBeginCaptureToGraph(h->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
     rs = iterate_body(h, cond);
     cudaGraph_t body_out = nullptr;
     e = cudaStreamEndCapture(h->st, &body_out);
     if (rs != RECON_OK) break;
     if (e != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
-    for (int k = 0; k < RECON_K_COUNT; ++k) body_launches += h->launches[k] - before[k];
-    if ((e = cudaGraphInstantiate(&gg.ex, gg.g, 0)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
+    if ((e = cudaGraphInstantiate(&c.exec, c.whole, 0)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
   } while (0);
   h->st = user;
-  h->timing = timing;
-  if (rs != RECON_OK) return rs;
-  RG_CUDA(cudaGraphLaunch(gg.ex, h->st));
+  // capture recorded the launches once; they are counted per execution instead
+  for (int k = 0; k < RECON_K_COUNT; ++k) {
+    c.start_launches[k] = l1[k] - l0[k];
+    c.start_bytes[k] = b1[k] - b0[k];
+    c.body_launches[k] = h->launches[k] - l1[k];
+    c.body_bytes[k] = h->bytes[k] - b1[k];
+    h->launches[k] = l0[k];
+    h->bytes[k] = b0[k];
+  }
+  if (rs != RECON_OK) {
+    drop_graph(h);
+    return rs;
+  }
+  c.valid = true;
+  return RECON_OK;
+}
+
+recon_status iterate_graph(recon_handle* h, const StartSpec& sp, double tol, int max_iter, int* it_out,
+                           double* rel_out, int* flag_out) {
+  recon_handle::GraphKey key{};
+  std::memcpy(&key.coef0_bits, &sp.coef0, sizeof(float));
+  std::memcpy(&key.tol_bits, &tol, sizeof(double));
+  key.u0 = sp.u0;
+  key.level = sp.level;
+  key.max_iter = max_iter;
+  key.d_is_k = h->d_is_k;
+  key.generic = h->kspace_generic;
+  key.narrow = h->narrow_lines;
+  key.planes = h->plane_batch;
+  key.epoch = h->epoch;
+  if (!(h->gcache.valid && h->gcache.key == key)) {
+    RG_TRY(build_graph(h, sp, tol, max_iter));
+    h->gcache.key = key;
+  }
+  RG_CUDA(cudaGraphLaunch(h->gcache.exec, h->st));
   int hdr[2];
   RG_CUDA(cudaMemcpyAsync(hdr, h->loop, sizeof(hdr), cudaMemcpyDeviceToHost, h->st));
   RG_CUDA(cudaStreamSynchronize(h->st));
@@ -860,12 +999,11 @@ recon_status iterate_graph(recon_handle* h, const StartSpec& sp, double tol, int
   h->trace.assign(it < kMaxTrace ? it : kMaxTrace, 0.0);
   if (!h->trace.empty())
     RG_CUDA(cudaMemcpy(h->trace.data(), h->loop->trace, h->trace.size() * sizeof(double), cudaMemcpyDeviceToHost));
-  // the captured body ran it times: count its launches accordingly
+  // the start ran once and the body it times (its last pass skipped the forward x transforms)
   for (int k = 0; k < RECON_K_COUNT; ++k) {
-    const int64_t d = h->launches[k] - before[k];
-    h->launches[k] += d * (it > 0 ? it - 1 : -1);
+    h->launches[k] += h->gcache.start_launches[k] + h->gcache.body_launches[k] * it;
+    h->bytes[k] += h->gcache.start_bytes[k] + h->gcache.body_bytes[k] * it;
   }
-  (void)body_launches;
   *it_out = it;
   *rel_out = h->trace.empty() ? 0.0 : h->trace.back();
   *flag_out = hdr[0];
@@ -945,7 +1083,8 @@ recon_status iterate_core(recon_handle* h, const StartSpec& sp, double tol, int 
       cudaEvent_t ev;
       RG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
       RG_CUDA(cudaEventRecord(ev, h->st));
-      RG_TRY(xpass(h, S_INV, 3, h->V));
+      const int B = plane_batch(h);
+      if (!B) RG_TRY(xpass(h, S_INV, 3, h->V));
       cudaError_t es = cudaEventSynchronize(ev);
       cudaEventDestroy(ev);
       RG_CUDA(es);
@@ -959,8 +1098,13 @@ recon_status iterate_core(recon_handle* h, const StartSpec& sp, double tol, int 
       h->trace.push_back(rel);
       const bool done = (it >= 2 && rel < tol) || it >= max_iter;
       if (done) {
+        if (B) RG_TRY(xpass(h, S_INV, 3, h->V));
         RG_TRY(run_z(h, Z_FINAL, 3, za));
         break;
+      }
+      if (B) {
+        RG_TRY(xzx_batched(h, B, za, nullptr));
+        continue;
       }
       RG_TRY(run_z(h, Z_PROJ, 3, za));
       RG_TRY(xpass(h, S_FWD, 3, h->V));
@@ -1061,13 +1205,13 @@ recon_status recon_shift(recon_handle* h, const recon_catalog* cat, int is_galax
   a.f = (float)h->p.f;
   a.los_mode = h->p.los_mode;
   a.los = h->geo.los;
-  a.off = h->off;
+  a.off = h->cur_off;
   a.H = (float)(h->L / h->n);
   a.periodic = h->p.periodic;
   const size_t es = elem_size(cat->dtype);
   BrickShiftArgs ba{};
   for (int q = 0; q < 3; ++q) ba.psi[q] = a.psi[q];
-  ba.off = h->off;
+  ba.off = h->cur_off;
   ba.H = h->L / h->n;
   ba.is_galaxy = a.is_galaxy;
   ba.f = a.f;
@@ -1265,4 +1409,192 @@ recon_status recon_fft_c2r(recon_handle* h, const float* in_half, float* out_rea
   return RECON_OK;
 }
 
+// ---- the paper's diagnostics (Sec. 4.1, Eq. Helmholtz; Sec. 4.3 and 5.2, Eq. ratio) ----------
+namespace {
+
+recon_status ratio_result(recon_handle* h, int blocks, double out[4]) {
+  RG_TRY(finalize(h, blocks, 4, RED_DIAG, 0));
+  double r[4];
+  RG_CUDA(cudaMemcpyAsync(r, h->red + RED_DIAG, sizeof(r), cudaMemcpyDeviceToHost, h->st));
+  RG_CUDA(cudaStreamSynchronize(h->st));
+  const double k = r[0];
+  const double mean = k > 0 ? r[1] / k : 0.0;
+  const double var = k > 0 ? r[2] / k - mean * mean : 0.0;
+  out[0] = mean;
+  out[1] = var > 0 ? std::sqrt(var) : 0.0;
+  out[2] = r[3] > 0 ? 1.0 - k / r[3] : 0.0;
+  out[3] = k;
+  return RECON_OK;
+}
+
+}  // namespace
+
+recon_status recon_ratio_stats(recon_handle* h, const float* num, const float* den, int64_t n, double lo, double hi,
+                               double out[4]) {
+  if (!h || !out || n < 0 || (n > 0 && (!num || !den)) || !(lo <= hi)) return RECON_ERR_INVALID_ARG;
+  const int blocks = kDepositBlocks;
+  RG_CUDA(timed(h, RECON_K_OTHER, 8.0 * n, [&] {
+    return launch_ratio(num, den, (size_t)n, lo, hi, h->partials, blocks, h->st); }));
+  return ratio_result(h, blocks, out);
+}
+
+recon_status recon_radial_ratio(recon_handle* h, const float* psi_num, const float* psi_den, const recon_catalog* cat,
+                                double lo, double hi, double out[4]) {
+  if (!h || !psi_num || !psi_den || !out || !(lo <= hi)) return RECON_ERR_INVALID_ARG;
+  RG_TRY(check_catalog(cat));
+  if (cat->n > 0 && !cat->on_device) return RECON_ERR_INVALID_ARG;
+  const size_t nr = (size_t)h->n * h->n * h->n;
+  RatioArgs a{};
+  for (int q = 0; q < 3; ++q) {
+    a.num[q] = psi_num + q * nr;
+    a.den[q] = psi_den + q * nr;
+  }
+  a.n = h->n;
+  a.scale = (double)h->n / h->L;
+  a.los_mode = h->p.los_mode;
+  a.los = h->geo.los;
+  a.off = h->cur_off;
+  a.H = (float)(h->L / h->n);
+  a.lo = lo;
+  a.hi = hi;
+  a.partials = h->partials;
+  const int blocks = kDepositBlocks;
+  RG_CUDA(timed(h, RECON_K_OTHER, (double)cat->n * 3 * elem_size(cat->dtype), [&] {
+    return cat->n > 0 ? launch_radial_ratio(cat->pos, cat->dtype, cat->n, a, blocks, h->st)
+                      : cudaMemsetAsync(h->partials, 0, (size_t)blocks * 4 * sizeof(double), h->st); }));
+  return ratio_result(h, blocks, out);
+}
+
+recon_status recon_helmholtz_x(recon_handle* h, const float* psi_x, float* grad_a, float* curl_b) {
+  if (!h || !psi_x || !grad_a || !curl_b) return RECON_ERR_INVALID_ARG;
+  const size_t nr = (size_t)h->n * h->n * h->n;
+  h->state = ST_CREATED;
+  h->warm_level = -1;
+  h->d_is_k = 0;
+  h->delta_real_valid = 0;
+  // Psi_x(k) in the first field (forward z, x, y passes)
+  RG_CUDA(cudaMemcpyAsync(h->V[0].M, psi_x, nr * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
+  {
+    ZArgs a = zargs(h);
+    a.f[0] = h->V[0];
+    RG_TRY(run_z(h, Z_FWD, 1, a));
+    RG_TRY(xpass(h, S_FWD, 1, h->V));
+    SArgs s = sargs(h);
+    s.f[0] = h->V[0];
+    RG_TRY(run_s(h, S_FWD, 1, AX_Y, s));
+  }
+  for (int j = 0; j < 3; ++j) {
+    RG_CUDA(timed(h, RECON_K_OTHER, 2.0 * cfield(h), [&] { return launch_helmholtz_k(h->V[0], h->V[1], j, h->geo, h->st); }));
+    SArgs s = sargs(h);
+    s.f[0] = h->V[1];
+    RG_TRY(run_s(h, S_INV, 1, AX_Y, s));
+    RG_TRY(xpass(h, S_INV, 1, h->V + 1));
+    ZArgs a = zargs(h);
+    a.f[0] = h->V[1];
+    RG_TRY(run_z(h, Z_INV, 1, a));
+    RG_CUDA(cudaMemcpyAsync(grad_a + j * nr, h->V[1].M, nr * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
+    RG_CUDA(timed(h, RECON_K_OTHER, 12.0 * nr, [&] {
+      return launch_solenoidal(psi_x, grad_a + j * nr, curl_b + j * nr, nr, j, h->st); }));
+  }
+  return RECON_OK;
+}
+
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// Batches as one CUDA graph (recon_batch_run): each mock appends its whole reconstruction to the
+// batch's graph, with the handle of its size class.  The graph orders a class's mocks one after
+// another on the class's buffers; the host waits once, for the whole batch.
+// ------------------------------------------------------------------------------------------------
+namespace rg {
+
+#define RG_GTRY(call)                                              \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) {                                       \
+      h->err = std::string(#call) + ": " + cudaGetErrorString(e_); \
+      return RECON_ERR_CUDA;                                       \
+    }                                                              \
+  } while (0)
+
+recon_status batch_append(recon_handle* h, cudaGraph_t top, cudaGraphNode_t* last, const BatchJob& job) {
+  recon_batch_item& it = *job.item;
+  if (it.tol < 0 || it.max_iter < 1 || it.max_iter > kMaxTrace || it.start < RECON_START_PLAIN ||
+      it.start > RECON_START_FFTA)
+    return RECON_ERR_INVALID_ARG;
+  if (!it.gal.on_device || (it.ran.n > 0 && !it.ran.on_device) ||
+      ((it.shift_gal || it.shift_ran) && !it.out_on_device))
+    return RECON_ERR_UNSUPPORTED;   // host memory cannot be read or written inside the graph
+  if (!h->cap_stream) RG_GTRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  const cudaStream_t user = h->st;
+  h->st = h->cap_stream;
+  const bool uniform = it.params.mean_density_mode == RECON_MEAN_UNIFORM;
+  cudaGraph_t pre = nullptr, post = nullptr;
+  recon_status rs = RECON_OK;
+  do {
+    // deposit, smoothing, loop state and the start
+    if (cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed) != cudaSuccess) { rs = RECON_ERR_CUDA; break; }
+    rs = [&]() -> recon_status {
+      RG_GTRY(launch_stamp(&job.slot->t0, h->st));
+      apply_config(h, &it.params, job.taps_dev, job.t0, job.ntap, job.off_dev);
+      RG_TRY(recon_deposit(h, &it.gal, uniform ? nullptr : &it.ran));
+      RG_TRY(recon_smooth(h));
+      h->trace.clear();
+      h->delta_real_valid = 0;
+      RG_GTRY(launch_loop_init(h->loop, it.tol, it.max_iter, h->st));
+      StartSpec sp;
+      sp.coef0 = (float)(1.0 - start_coefficient(it.start, it.params.f / it.params.b));
+      return run_start(h, sp);
+    }();
+    cudaError_t e = cudaStreamEndCapture(h->st, &pre);
+    if (rs != RECON_OK) break;
+    if (e != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
+    cudaGraphNode_t npre = nullptr, ncond = nullptr, npost = nullptr;
+    if ((e = cudaGraphAddChildGraphNode(&npre, top, *last ? last : nullptr, *last ? 1 : 0, pre)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
+    // the updates of Eq. iterative as a conditional WHILE node (device-side stopping test)
+    cudaGraphConditionalHandle cond;
+    if ((e = cudaGraphConditionalHandleCreate(&cond, top, 1, cudaGraphCondAssignDefault)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    if ((e = cudaGraphAddNode(&ncond, top, &npre, nullptr, 1, &np)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
+    if ((e = cudaStreamBeginCaptureToGraph(h->st, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeRelaxed)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
+    rs = iterate_body(h, cond);
+    cudaGraph_t body_out = nullptr;
+    e = cudaStreamEndCapture(h->st, &body_out);
+    if (rs != RECON_OK) break;
+    if (e != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
+    h->d_is_k = 1;
+    h->state = ST_ITERATED;
+    // the loop's outcome, the shifts, the end stamp
+    if (cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed) != cudaSuccess) { rs = RECON_ERR_CUDA; break; }
+    rs = [&]() -> recon_status {
+      RG_GTRY(launch_loop_record(h->loop, job.slot, h->st));
+      if (it.shift_gal && it.gal.n > 0) RG_TRY(recon_shift(h, &it.gal, 1, it.shift_gal, nullptr, 1));
+      if (!uniform && it.shift_ran && it.ran.n > 0) RG_TRY(recon_shift(h, &it.ran, 0, it.shift_ran, nullptr, 1));
+      RG_GTRY(launch_stamp(&job.slot->t1, h->st));
+      return RECON_OK;
+    }();
+    e = cudaStreamEndCapture(h->st, &post);
+    if (rs != RECON_OK) break;
+    if (e != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
+    if ((e = cudaGraphAddChildGraphNode(&npost, top, &ncond, 1, post)) != cudaSuccess) { h->err = cudaGetErrorString(e); rs = RECON_ERR_CUDA; break; }
+    *last = npost;
+  } while (0);
+  if (pre) cudaGraphDestroy(pre);     // child nodes hold their own copies
+  if (post) cudaGraphDestroy(post);
+  h->st = user;
+  return rs;
+}
+
+void batch_restore(recon_handle* h) {
+  h->cur_taps = h->taps;
+  h->cur_off = h->off;
+  h->geo.off = h->off;
+  ++h->epoch;
+  h->state = ST_CREATED;
+}
+
+}  // namespace rg

@@ -25,7 +25,8 @@ enum RedSlot {
   RED_CNT_MASK = 5,    // number of nodes inside the survey mask
   RED_NORM_D2 = 6,     // Parseval sum for |dPsi|^2 of the last iteration
   RED_NORM_S2 = 7,     // Parseval sum for |Psi|^2 of the last iteration
-  RED_COUNT = 8
+  RED_DIAG = 8,        // 4 slots: ratio statistics (kept count, sum, sum of squares, points)
+  RED_COUNT = 12
 };
 
 struct Geometry {
@@ -66,6 +67,8 @@ struct ZArgs {
   const float* ucoarse;
   int clevel;
   int generic;            // Z_PROJ: the generic staged kernel instead of the register-fused one
+  int ybeg, ycount;       // register-fused passes: only the rows of y-planes [ybeg, ybeg + ycount)
+                          // (ycount 0: every row)
 };
 
 struct SArgs {
@@ -83,6 +86,8 @@ struct SArgs {
   const int* skip_flag;   // plain passes: do nothing when *skip_flag != 0 (device-driven loop)
   int narrow;             // plain x passes: 8-column instead of 16-column tiles
   int generic;            // k-space update: the generic staged kernel instead of the register-fused one
+  int ybeg, ycount;       // paired x passes: only the lines of y-planes [ybeg, ybeg + ycount)
+                          // (ycount 0: every line; both multiples of the tile width)
 };
 
 // State of the device-driven iteration (in the workspace).
@@ -94,6 +99,15 @@ struct LoopState {
   int pad;
   double tol;
   double trace[kMaxTrace];
+};
+
+// Result of one mock of a batch graph, written on the device: the loop's outcome and globaltimer
+// stamps (ns) at the start and end of the mock's work.
+struct BatchSlot {
+  int flag;               // LoopState::flag at the end of the mock's iteration
+  int it;                 // updates done
+  double rel;             // last |dPsi| / |Psi|
+  unsigned long long t0, t1;
 };
 
 // Kernels of one mesh size (one table per supported N).

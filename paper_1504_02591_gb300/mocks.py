@@ -132,6 +132,7 @@ class Mock:
     galaxies: Catalog | None = None
     randoms: Catalog | None = None
     window: dict = field(default_factory=dict)
+    galaxies_real: Catalog | None = None  # the same galaxies before the redshift-space shift
 
     def params(self, **over):
         p = dict(n=self.n_mesh, L=self.L, b=self.b, f=self.f, R=self.R, observer=self.observer,
@@ -170,7 +171,7 @@ def periodic_box(L: float, n_mesh: int, n_gal: int, n_ran: int, b: float, f: flo
     x = q[sel] + v[sel].astype(np.float64)
     s = np.mod(_rsd(x, v[sel].astype(np.float64), f, observer, los_mode), L)
     mock = Mock(name, L, n_mesh, b, f, R, tuple(observer), los_mode, True, uniform,
-                galaxies=Catalog(s))
+                galaxies=Catalog(s), galaxies_real=Catalog(np.mod(x, L)))
     if n_ran > 0:
         rr = np.random.default_rng(seed_ran)
         mock.randoms = Catalog(rr.uniform(0.0, L, (n_ran, 3)))
@@ -207,7 +208,7 @@ def shell_survey(L: float, n_mesh: int, n_gal: int, n_ran: int, b: float, f: flo
                 hi[a] = min(hi[a], obs[a] - r_min * cos_min + margin)
     del sin_max
     rng = np.random.default_rng(seed_gal)
-    got, chunks = 0, []
+    got, chunks, real = 0, [], []
     vol_box = np.prod(hi - lo)
     vol_win = sky_frac * 4.0 / 3.0 * np.pi * (r_max ** 3 - r_min ** 3)
     per = int(n_gal * 2.0 * vol_box / vol_win) + 1000
@@ -218,9 +219,10 @@ def shell_survey(L: float, n_mesh: int, n_gal: int, n_ran: int, b: float, f: flo
         keep = rng.uniform(size=per) * 4.0 < p_keep          # thinning; 4 bounds 1+(b-1)delta
         q, v = q[keep], v[keep].astype(np.float64)
         s = _rsd(q + v, v, f, obs, 0)
-        s = s[_in_window(s, obs, ax, r_min, r_max, cos_min)]
-        chunks.append(s)
-        got += len(s)
+        inw = _in_window(s, obs, ax, r_min, r_max, cos_min)
+        chunks.append(s[inw])
+        real.append((q + v)[inw])
+        got += int(inw.sum())
     gal = np.concatenate(chunks)[:n_gal]
     rr = np.random.default_rng(seed_ran)
     u = rr.uniform(size=(n_ran, 3))
@@ -235,7 +237,8 @@ def shell_survey(L: float, n_mesh: int, n_gal: int, n_ran: int, b: float, f: flo
     ran = obs + r[:, None] * dirs
     mock = Mock(name, L, n_mesh, b, f, R, tuple(obs), 0, False, False,
                 galaxies=Catalog(gal), randoms=Catalog(ran),
-                window=dict(axis=tuple(ax), r_min=r_min, r_max=r_max, sky_frac=sky_frac))
+                window=dict(axis=tuple(ax), r_min=r_min, r_max=r_max, sky_frac=sky_frac),
+                galaxies_real=Catalog(np.concatenate(real)[:n_gal]))
     return mock
 
 
@@ -267,3 +270,199 @@ def scaled_shell(n_mesh: int, L: float, n_gal: int, ran_ratio: int, b: float, f:
     return shell_survey(L, n_mesh, n_gal, n_gal * ran_ratio, b, f, 15.0, (0.0, L / 2, L / 2),
                         (1.0, 0.0, 0.0), 1100.0 * s, 1800.0 * s, 0.25, seed, seed + 1, seed + 2,
                         ng=min(256, n_mesh), name=f"shell-{n_mesh}-{seed}")
+
+
+def lattice_box(L: float, n_mesh: int, side: int, n_total: int, b: float, f: float, R: float,
+                observer, los_mode: int, seed: int, device: str = "cuda", name: str = "lattice") -> Mock:
+    """Periodic box of Zel'dovich-displaced particles, generated with torch on `device`.
+
+    A Gaussian field with the spectrum above is drawn on the side^3 lattice itself (nodes
+    q = i L / side), so each node is displaced by the field's first-order displacement D(q) without
+    interpolation; the n_total - side^3 further particles are randomly chosen nodes jittered
+    uniformly within half a lattice cell, displaced like their node.  Redshift-space positions
+    s = x + f (D.r) r are wrapped into [0, L).  Uniform mean density (no randoms); with b = 1 every
+    particle is kept.  Returns float64 positions on the host."""
+    import torch
+    gen = torch.Generator(device=device).manual_seed(seed)
+    white = torch.randn((side, side, side), generator=gen, device=device, dtype=torch.float32)
+    W = torch.fft.rfftn(white)
+    del white
+    kf = 2 * np.pi / L
+    m = torch.fft.fftfreq(side, d=1.0 / side, device=device, dtype=torch.float64)
+    mz = torch.arange(side // 2 + 1, device=device, dtype=torch.float64)
+    kx, ky, kz = (kf * m)[:, None, None], (kf * m)[None, :, None], (kf * mz)[None, None, :]
+    kk = torch.sqrt(kx * kx + ky * ky + kz * kz)
+    pos_k = kk > 0
+    pk = torch.where(pos_k, PK_AMPLITUDE * torch.where(pos_k, kk, 1.0) ** PK_SLOPE
+                     * torch.exp(-(kk / PK_CUTOFF) ** 2), torch.zeros_like(kk))
+    amp = torch.sqrt(pk / (L / side) ** 3) / torch.where(pos_k, kk * kk, 1.0)
+    amp[0, 0, 0] = 0.0
+    D = W * amp.to(torch.float32)
+    del W, pk, amp
+    disp = torch.empty((side ** 3, 3), device=device, dtype=torch.float64)
+    for a, ka in enumerate((kx, ky, kz)):
+        disp[:, a] = torch.fft.irfftn(1j * ka.to(torch.float32) * D, s=(side,) * 3).reshape(-1).double()
+    del D
+    g = torch.arange(side, device=device, dtype=torch.float64) * (L / side)
+    q = torch.stack(torch.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    extra = max(0, n_total - side ** 3)
+    if extra:
+        pick = torch.randint(0, side ** 3, (extra,), generator=gen, device=device)
+        jit = (torch.rand((extra, 3), generator=gen, device=device, dtype=torch.float64) - 0.5) * (L / side)
+        q = torch.cat([q, q[pick] + jit])
+        disp = torch.cat([disp, disp[pick]])
+    x = q + disp
+    del q
+    obs = torch.tensor(observer, device=device, dtype=torch.float64)
+    if los_mode == 1:
+        rh = (obs / torch.linalg.norm(obs)).expand_as(x)
+    else:
+        d = x - obs
+        rh = d / torch.linalg.norm(d, dim=1, keepdim=True).clamp_min(1e-30)
+        del d
+    s = torch.remainder(x + f * (disp * rh).sum(1, keepdim=True) * rh, L)
+    del x, disp, rh
+    pos = s[:n_total].cpu().numpy()
+    return Mock(name, L, n_mesh, b, f, R, tuple(observer), los_mode, True, True, galaxies=Catalog(pos))
+
+
+def large_periodic_1024(los_mode: int = 0, n_mesh: int = 1024, side: int = 464,
+                        n_total: int = 100_000_000, device: str = "cuda") -> Mock:
+    """The large periodic run: 2500 Mpc/h box, 1024^3 mesh, 1e8 particles (a 464^3 lattice plus
+    102,656 jittered copies of lattice nodes), b = 1, f = 0.74, R = 10, uniform mean density.
+    Radial line of sight from (-1000, 1250, 1250), or (los_mode = 1) the fixed direction +x."""
+    obs = (1.0, 0.0, 0.0) if los_mode == 1 else (-1000.0, 1250.0, 1250.0)
+    return lattice_box(2500.0, n_mesh, side, n_total, 1.0, 0.74, 10.0, obs, los_mode, 20, device=device,
+                       name=f"periodic-{n_mesh}-{'fixed' if los_mode else 'radial'}")
+
+
+# ---------------------------------------------------------------------------------------------
+# Batches of mocks generated on the GPU (the batched workload: dozens of catalogues of up to 5e7
+# tracers each, too many to draw with numpy in a benchmark's time).  Same recipe as above, with
+# torch's seeded generators: Gaussian field on a generator grid, trilinear displacement and
+# overdensity at uniform Lagrangian points, biased thinning, redshift-space shift along the radial
+# line of sight, shell-cap window or periodic wrap; randoms uniform in the window.
+# ---------------------------------------------------------------------------------------------
+def _field_device(ng, L, gen, device):
+    import torch
+    white = torch.randn((ng, ng, ng), generator=gen, device=device, dtype=torch.float32)
+    W = torch.fft.rfftn(white)
+    kf = 2 * np.pi / L
+    m = torch.fft.fftfreq(ng, d=1.0 / ng, device=device, dtype=torch.float64)
+    mz = torch.arange(ng // 2 + 1, device=device, dtype=torch.float64)
+    kx, ky, kz = (kf * m)[:, None, None], (kf * m)[None, :, None], (kf * mz)[None, None, :]
+    kk = torch.sqrt(kx * kx + ky * ky + kz * kz)
+    pos_k = kk > 0
+    ksafe = torch.where(pos_k, kk, torch.ones_like(kk))
+    pk = torch.where(pos_k, PK_AMPLITUDE * ksafe ** PK_SLOPE * torch.exp(-(kk / PK_CUTOFF) ** 2), torch.zeros_like(kk))
+    D = W * torch.sqrt(pk / (L / ng) ** 3).to(torch.float32)
+    fields = [torch.fft.irfftn(D, s=(ng,) * 3)]
+    inv_k2 = torch.where(pos_k, 1.0 / (ksafe * ksafe), torch.zeros_like(kk)).to(torch.float32)
+    for ka in (kx, ky, kz):
+        fields.append(torch.fft.irfftn(1j * ka.to(torch.float32) * D * inv_k2, s=(ng,) * 3))
+    return torch.stack(fields)                 # (4, ng, ng, ng): delta, D_x, D_y, D_z
+
+
+def _trilinear_device(F, pts, L):
+    """F (c, ng, ng, ng) at points (n, 3), periodic; returns (n, c)."""
+    import torch
+    ng = F.shape[-1]
+    u = pts * (ng / L)
+    f0 = torch.floor(u)
+    t = (u - f0).to(torch.float32)
+    i0 = f0.long() % ng
+    i1 = (i0 + 1) % ng
+    flat = F.reshape(F.shape[0], -1)
+    out = torch.zeros((pts.shape[0], F.shape[0]), device=pts.device, dtype=torch.float32)
+    for cx in (0, 1):
+        ix = i1[:, 0] if cx else i0[:, 0]
+        wx = t[:, 0] if cx else 1 - t[:, 0]
+        for cy in (0, 1):
+            iy = i1[:, 1] if cy else i0[:, 1]
+            wy = t[:, 1] if cy else 1 - t[:, 1]
+            for cz in (0, 1):
+                iz = i1[:, 2] if cz else i0[:, 2]
+                wz = t[:, 2] if cz else 1 - t[:, 2]
+                out += (wx * wy * wz)[:, None] * flat[:, (ix * ng + iy) * ng + iz].T
+    return out
+
+
+def _rsd_device(x, v, f, obs):
+    import torch
+    d = x - obs
+    rh = d / torch.linalg.norm(d, dim=1, keepdim=True).clamp_min(1e-30)
+    return x + f * (v * rh).sum(1, keepdim=True) * rh
+
+
+def batch_mock_device(n_mesh: int, n_gal: int, ran_ratio: int, b: float, f: float, shell: bool, seed: int,
+                      device: str = "cuda") -> dict:
+    """One mock of the batched workload on the GPU.  Box L = 6.84 N Mpc/h (the 512^3 survey's cell
+    size), R = 15 Mpc/h.  Shell: observer at the centre of the x = 0 face, comoving 1100-1800 Mpc/h
+    scaled by L/3500, 25% sky cap about +x, randoms ran_ratio x n_gal uniform in the window, mean
+    density from the randoms.  Periodic: observer 1.5 L along -x of the box centre, uniform mean
+    density (no randoms).  Returns params and float64 device positions."""
+    import torch
+    L = 6.84 * n_mesh
+    gen = torch.Generator(device=device).manual_seed(seed)
+    ng = min(n_mesh, 256)
+    F = _field_device(ng, L, gen, device)
+    if shell:
+        sc = L / 3500.0
+        r_min, r_max, cos_min = 1100.0 * sc, 1800.0 * sc, 0.5
+        obs = torch.tensor([0.0, L / 2, L / 2], device=device, dtype=torch.float64)
+        lo = torch.tensor([r_min * cos_min - 80.0, L / 2 - r_max - 80.0, L / 2 - r_max - 80.0],
+                          device=device, dtype=torch.float64).clamp(0.0, L)
+        hi = torch.tensor([r_max + 80.0, L / 2 + r_max + 80.0, L / 2 + r_max + 80.0],
+                          device=device, dtype=torch.float64).clamp(0.0, L)
+        vol_win = 0.25 * 4.0 / 3.0 * np.pi * (r_max ** 3 - r_min ** 3)
+        per = int(n_gal * 2.0 * float(torch.prod(hi - lo)) / vol_win) + 1000
+    else:
+        obs = torch.tensor([L / 2 - 1.5 * L, L / 2, L / 2], device=device, dtype=torch.float64)
+        lo = torch.zeros(3, device=device, dtype=torch.float64)
+        hi = torch.full((3,), L, device=device, dtype=torch.float64)
+        per = 2 * n_gal
+    got, parts = 0, []
+    while got < n_gal:
+        q = lo + torch.rand((per, 3), generator=gen, device=device, dtype=torch.float64) * (hi - lo)
+        s_ = _trilinear_device(F, q, L)
+        keep = torch.rand(per, generator=gen, device=device) * 4.0 < torch.clamp(1.0 + (b - 1.0) * s_[:, 0], min=0.0)
+        q, v = q[keep], s_[keep, 1:].double()
+        s = _rsd_device(q + v, v, f, obs)
+        if shell:
+            d = s - obs
+            r = torch.linalg.norm(d, dim=1)
+            s = s[(r >= r_min) & (r <= r_max) & (d[:, 0] >= cos_min * r)]
+        else:
+            s = torch.remainder(s, L)
+        parts.append(s)
+        got += len(s)
+    gal = torch.cat(parts)[:n_gal].contiguous()
+    ran = None
+    if shell:
+        n_ran = n_gal * ran_ratio
+        u = torch.rand((n_ran, 3), generator=gen, device=device, dtype=torch.float64)
+        r = torch.pow(u[:, 0] * (r_max ** 3 - r_min ** 3) + r_min ** 3, 1.0 / 3.0)
+        ct = cos_min + u[:, 1] * (1.0 - cos_min)
+        st = torch.sqrt(torch.clamp(1 - ct * ct, min=0.0))
+        ph = 2 * np.pi * u[:, 2]
+        ran = obs + r[:, None] * torch.stack([ct, st * torch.cos(ph), st * torch.sin(ph)], 1)
+        ran = ran.contiguous()
+    params = dict(n=n_mesh, L=L, b=b, f=f, R=15.0, observer=tuple(float(v) for v in obs.cpu()), los_mode=0,
+                  periodic=not shell, uniform=not shell, mask_frac=0.01, lognormal=False)
+    return dict(params=params, gal=gal, ran=ran)
+
+
+def batch_workload_device(count: int = 64, seed: int = 100, device: str = "cuda") -> list:
+    """The batched workload: `count` mocks with N drawn from {256, 384, 512}, galaxies uniform in
+    [2e5, 1e6], randoms 30-50 x galaxies, b in [1.5, 2.5], f in [0.6, 0.8]; even-numbered mocks are
+    shell surveys and odd ones periodic boxes.  Mock i uses seed + i."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.choice([256, 384, 512]))
+        ng = int(rng.integers(200_000, 1_000_001))
+        ratio = int(rng.integers(30, 51))
+        b = float(rng.uniform(1.5, 2.5))
+        f = float(rng.uniform(0.6, 0.8))
+        out.append(batch_mock_device(n, ng, ratio, b, f, i % 2 == 0, seed + i, device))
+    return out

@@ -75,3 +75,24 @@ def test_batch_rejects_bad_item(lib, batch_mocks):
     assert st == B.ERR_INVALID_ARG
     assert items[0].status == B.OK and items[0].n_iter == 3
     assert items[1].status == B.ERR_INVALID_ARG
+
+
+def test_batch_384_item_vs_oracle(lib):
+    """A 384^3 survey shell (one of the batched workload's mesh sides) reconstructed inside a batch
+    graph next to a 256^3 periodic box: its shifts equal the FP64 oracle's for the same 3 updates."""
+    from paper_1504_02591_gb300 import binding as B
+    m = mocks.scaled_shell(384, 6.84 * 384, 200_000, 30, 2.1, 0.65, 140)
+    other = mocks.batch_mock_device(256, 200_000, 30, 1.7, 0.7, False, 7)
+    status, res = B.batch_run([other, m], start=B.START_FFTA, tol=0.0, max_iter=3)
+    assert status == B.OK and res[1]["n_iter"] == 3 and res[0]["n_iter"] == 3
+    ref = O.reconstruct(m.params(), m.galaxies.pos, None, m.randoms.pos, None, start=O.START_FFTA, tol=0.0,
+                        max_iter=3, shift=False)
+    p = m.params()
+    rng = np.random.default_rng(5)
+    ir = rng.choice(len(m.randoms.pos), 200_000, replace=False)
+    dg = O.shift_vectors(ref["psi"], m.galaxies.pos, p["L"], p["f"], p["observer"], p["los_mode"], True)
+    dr = O.shift_vectors(ref["psi"], m.randoms.pos[ir], p["L"], p["f"], p["observer"], p["los_mode"], False)
+    e_g = float(np.abs(res[1]["shift_gal"].cpu().numpy() - dg).max())
+    e_r = float(np.abs(res[1]["shift_ran"].cpu().numpy()[ir] - dr).max())
+    print(f"batch 384^3 item: shifts {e_g:.2e} / {e_r:.2e} Mpc/h, {res[1]['ms']:.2f} ms")
+    assert e_g <= 1e-4 and e_r <= 1e-4

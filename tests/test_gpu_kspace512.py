@@ -125,3 +125,32 @@ def test_narrow_line_tiles_512(lib):
     r.close()
     d = float(np.sqrt(((out[1] - out[0]) ** 2).sum() / (out[0] ** 2).sum()))
     assert d < 1e-6, d
+
+
+@pytest.mark.parametrize("graph", [1, 0])
+def test_plane_batched_passes_match_unbatched(lib, graph):
+    """RECON_OPT_PLANE_BATCH runs the same kernels on the same elements, only grouped by y-planes
+    (x inverse, projection and x forward per batch), so Psi and the trace are bitwise those of the
+    unbatched passes, in the device-driven graph loop and in the host-driven loop, for every batch
+    size; with a tolerance the stopping update is the same too."""
+    from paper_1504_02591_gb300 import binding as B
+    from paper_1504_02591_gb300 import mocks
+    m = mocks.periodic_box(3500.0, 512, 100_000, 0, 1.85, 0.74, 15.0, (0.0, 1750.0, 1750.0), 4, 5, 6, ng=128,
+                           uniform=True)
+    gal = torch.from_numpy(m.galaxies.pos).cuda()
+    r = B.Recon.from_mock(m, uniform=True)
+    r.set_option(B.OPT_GRAPH, graph)
+    r.deposit(gal, None, None, None)
+    r.smooth()
+    out = {}
+    for planes in (0, 16, 32, 64):
+        r.set_option(B.OPT_PLANE_BATCH, planes)
+        n, rel, st = r.iterate(B.START_FFTA, 0.0, 4)
+        out[planes] = (r.get_psi().cpu().numpy(), np.array(r.trace()))
+        n_c, rel_c, st_c = r.iterate(B.START_FFTA, 1e-6, 40)
+        out[planes] += (n_c, r.get_psi().cpu().numpy())
+    r.close()
+    for planes in (16, 32, 64):
+        assert np.array_equal(out[planes][0], out[0][0]), planes
+        assert np.array_equal(out[planes][1], out[0][1]), planes
+        assert out[planes][2] == out[0][2] and np.array_equal(out[planes][3], out[0][3]), planes

@@ -1,0 +1,140 @@
+"""Mesh sides beyond the 512^3 benchmark mesh, against the FP64 oracle.
+
+* 384^3 (radix 3 x 2^7, one of the batch's mesh sides): a survey shell with randoms and mask, the
+  whole pipeline for 3 updates from the Eq. approx2 start against the oracle's.
+* 1024^3, the large periodic run (2500 Mpc/h, 1e8 Zel'dovich particles, uniform mean density,
+  b = 1, f = 0.74, R = 10, 6 updates), radial line of sight with the lognormal transform of Sec. 6
+  and the fixed (distant-observer) line of sight.  The oracle cannot iterate a 1024^3 mesh in a
+  test's time, so it checks what holds at any size: the (lognormal) overdensity on every node from
+  its own deposit and smoothing; the last update of Eq. iterative, Psi_6 = Z[delta/b + beta
+  div((Psi_5.r)r)], computed by the oracle's operators in float64 from the GPU's delta and Psi_5;
+  and the shifts of sampled particles, gathered by the oracle from the GPU's Psi_6.
+Tolerances: rel L2 of Psi <= 1e-5, shifts <= 1e-4 Mpc/h.
+"""
+import numpy as np
+import pytest
+
+from oracle import recon_oracle as O
+from paper_1504_02591_gb300 import mocks
+from parity_helpers import host_mem_available_gb, rel_l2, reconstruct_same_branch
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PSI_TOL = 1e-5
+SHIFT_TOL = 1e-4
+
+
+def test_384_survey_shell_vs_oracle(lib):
+    from paper_1504_02591_gb300 import binding as B
+    n = 384
+    m = mocks.scaled_shell(n, 6.84 * n, 200_000, 30, 2.1, 0.65, 140)
+    r = B.Recon.from_mock(m)
+    gal = torch.from_numpy(m.galaxies.pos).cuda()
+    ran = torch.from_numpy(m.randoms.pos).cuda()
+    r.deposit(gal, None, ran, None)
+    r.smooth()
+    delta = r.get_field(B.FIELD_DELTA).cpu().numpy()
+    n_it, rel, st = r.iterate(B.START_FFTA, 0.0, 3)
+    trace = np.array(r.trace())
+    psi = r.get_psi().cpu().numpy()
+    sg = r.shift(gal, True).cpu().numpy()
+    rng = np.random.default_rng(384)
+    ir = rng.choice(len(m.randoms.pos), 200_000, replace=False)
+    sr = r.shift(ran[torch.from_numpy(ir).cuda()], False).cpu().numpy()
+    r.close()
+    kw = dict(start=O.START_FFTA, tol=0.0, max_iter=3, shift=False)
+    ref = O.reconstruct(m.params(), m.galaxies.pos, None, m.randoms.pos, None, **kw)
+    ref = reconstruct_same_branch(m, ref, delta, **kw)
+    e_d, e_p = rel_l2(delta, ref["delta"]), rel_l2(psi, ref["psi"])
+    p = m.params()
+    dg = O.shift_vectors(ref["psi"], m.galaxies.pos, p["L"], p["f"], p["observer"], p["los_mode"], True)
+    dr = O.shift_vectors(ref["psi"], m.randoms.pos[ir], p["L"], p["f"], p["observer"], p["los_mode"], False)
+    e_g, e_r = float(np.abs(sg - dg).max()), float(np.abs(sr - dr).max())
+    print(f"384^3 shell: delta {e_d:.2e}, Psi {e_p:.2e}, shifts {e_g:.2e} / {e_r:.2e} Mpc/h")
+    assert n_it == 3
+    assert e_d < 1e-5 and e_p <= PSI_TOL
+    assert e_g <= SHIFT_TOL and e_r <= SHIFT_TOL
+    assert np.allclose(trace, ref["rel"], rtol=1e-3, atol=0)
+
+
+@pytest.fixture(scope="module")
+def large1024():
+    if host_mem_available_gb() < 160:
+        pytest.skip(f"the 1024^3 float64 oracle checks need ~150 GB of host memory "
+                    f"({host_mem_available_gb():.0f} GB available)")
+    return mocks.large_periodic_1024(los_mode=0)
+
+
+def _last_update(delta, psi5, p, L, n):
+    """One update of Eq. iterative in float64 by the oracle's operators (float32 inputs)."""
+    rhat = O.rhat_field(n, L, p["observer"], p["los_mode"])
+    u = np.zeros((n, n, n))
+    for j in range(3):
+        u += psi5[j].astype(np.float64) * rhat[j]
+    beta = p["f"] / p["b"]
+    _, kd, _ = O.kgrid(n, L)
+    div = None
+    for j in range(3):     # div((Psi.r) r) in Fourier space, one component at a time
+        t = 1j * kd[j] * O.fft3(u * rhat[j])
+        div = t if div is None else div + t
+        del t
+    del rhat, u
+    S_k = O.fft3(delta.astype(np.float64) / p["b"]) + beta * div
+    del div
+    return S_k
+
+
+@pytest.mark.parametrize("los", ["radial-lognormal", "fixed"])
+def test_1024_large_periodic_vs_oracle(lib, large1024, los):
+    from paper_1504_02591_gb300 import binding as B
+    m = large1024
+    n, L = m.n_mesh, m.L
+    over = dict(lognormal=True) if los == "radial-lognormal" else dict(los_mode=O.LOS_FIXED,
+                                                                       observer=(1.0, 0.0, 0.0))
+    p = m.params(**over)
+    r = B.Recon.from_mock(m, **over)
+    gal = torch.from_numpy(m.galaxies.pos).cuda()
+    r.deposit(gal, None, None, None)
+    r.smooth()
+    delta = r.get_field(B.FIELD_DELTA).cpu().numpy()
+    r.iterate(B.START_FFTA, 0.0, 5)
+    psi5 = r.get_psi().cpu().numpy()
+    n_it, rel, st = r.iterate(B.START_FFTA, 0.0, 6)
+    assert n_it == 6
+    psi6_dev = r.get_psi()
+    rng = np.random.default_rng(1024)
+    idx = rng.choice(len(m.galaxies.pos), 20_000, replace=False)
+    sg = r.shift(gal, True)[torch.from_numpy(idx).cuda()].cpu().numpy()
+    r.close()
+    del gal
+    torch.cuda.empty_cache()
+
+    if los == "radial-lognormal":
+        # the lognormal overdensity on every node: the oracle's deposit, smoothing and Eq. logdelta
+        rho_s = O.smooth(O.cic_deposit(m.galaxies.pos, None, n, L), p["R"], L)
+        d_ref, C = O.lognormal(O.overdensity_uniform(rho_s, float(len(m.galaxies.pos))))
+        del rho_s
+        e_d = rel_l2(delta, d_ref)
+        del d_ref
+        print(f"1024^3 {los}: delta rel L2 {e_d:.2e}")
+        assert e_d < 1e-5
+
+    S_k = _last_update(delta, psi5, p, L, n)
+    del psi5
+    num = den = 0.0
+    for j, ck in enumerate(O.zeldovich_k(S_k, n, L)):
+        want = O.ifft3(ck, n)
+        got = psi6_dev[j].cpu().numpy().astype(np.float64)
+        num += ((got - want) ** 2).sum()
+        den += (want ** 2).sum()
+        del want, got
+    del S_k
+    e_fix = float(np.sqrt(num / den))
+    psi6 = psi6_dev.cpu().numpy().astype(np.float64)
+    del psi6_dev
+    dg = O.shift_vectors(psi6, m.galaxies.pos[idx], L, p["f"], p["observer"], p["los_mode"], True, True)
+    e_s = float(np.abs(sg - dg).max())
+    print(f"1024^3 {los}: last update rel L2 {e_fix:.2e}, sampled shifts {e_s:.2e} Mpc/h")
+    assert e_fix <= PSI_TOL
+    assert e_s <= SHIFT_TOL

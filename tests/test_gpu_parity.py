@@ -4,6 +4,8 @@ Tolerances (stated by the method's precision policy): relative L2 error of Psi <
 particle-shift error <= 1e-4 Mpc/h against the FP64 oracle.  Intermediate fields are checked at the
 float32 rounding level they are computed at.
 """
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -59,13 +61,13 @@ def periodic_mock():
 def periodic_oracle(periodic_mock):
     m = periodic_mock
     out = {}
-    for start in (O.START_PLAIN, O.START_FFTA):
+    for start in (O.START_PLAIN, O.START_APPROX1, O.START_FFTA):
         out[start] = O.reconstruct(m.params(), m.galaxies.pos, None, m.randoms.pos, None,
                                    start=start, tol=0.0, max_iter=6)
     return out
 
 
-@pytest.mark.parametrize("start", [0, 2])
+@pytest.mark.parametrize("start", [0, 1, 2])
 def test_periodic_pipeline_vs_oracle(B, periodic_mock, periodic_oracle, start):
     m = periodic_mock
     ref = periodic_oracle[start]
@@ -395,3 +397,35 @@ def test_empty_shift_catalogue(B):
     sg = r.shift(m.galaxies.pos, True)
     assert sg.shape == (len(m.galaxies.pos), 3) and np.isfinite(sg).all()
     r.close()
+
+
+def test_cached_iteration_graph(B, periodic_mock, periodic_oracle):
+    """recon_iterate keeps its instantiated graph: a repeated call relaunches it with the same result,
+    and a changed start, tol or max_iter, or new parameters (recon_reconfigure), rebuilds it."""
+    m = periodic_mock
+    gal = torch.from_numpy(m.galaxies.pos).cuda()
+    ran = torch.from_numpy(m.randoms.pos).cuda()
+    r = B.Recon.from_mock(m)
+    r.deposit(gal, None, ran, None)
+    r.smooth()
+    out = []
+    for start, it in ((2, 6), (2, 6), (0, 6), (2, 4), (2, 6)):
+        n_it, rel, st = r.iterate(start, 0.0, it)
+        assert n_it == it
+        out.append(r.get_psi().cpu().numpy())
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[4])
+    assert rel_l2(out[0], periodic_oracle[2]["psi"]) <= PSI_TOL
+    assert rel_l2(out[2], periodic_oracle[0]["psi"]) <= PSI_TOL
+    # new parameters through recon_reconfigure: the graph is rebuilt with the new b and f
+    p = m.params()
+    p2 = dict(p, b=2.5, f=0.6)
+    prm = B.make_params(p2["n"], p2["L"], p2["b"], p2["f"], p2["R"], p2["observer"], p2["los_mode"], p2["periodic"],
+                        p2["mask_frac"], p2["lognormal"], p2["uniform"])
+    assert r.lib.recon_reconfigure(r.h, C.byref(prm)) == B.OK
+    r.deposit(gal, None, ran, None)
+    r.smooth()
+    r.iterate(2, 0.0, 6)
+    psi2 = r.get_psi().cpu().numpy()
+    r.close()
+    ref2 = O.reconstruct(p2, m.galaxies.pos, None, m.randoms.pos, None, start=O.START_FFTA, tol=0.0, max_iter=6)
+    assert rel_l2(psi2, ref2["psi"]) <= PSI_TOL

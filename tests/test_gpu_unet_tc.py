@@ -75,3 +75,70 @@ def test_tensor_core_forward_after_training_step(lib):
     x4 = x[..., 4].cpu().numpy()
     assert _rel(y_tc - x4, y_ref - x4) < 1e-2
     net.close()
+
+
+def _bf16(x):
+    """Round float32 values to the nearest bfloat16 (ties to even), returned as float32."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32)
+    r = (b + np.uint32(0x7FFF) + ((b >> np.uint32(16)) & np.uint32(1))) & np.uint32(0xFFFF0000)
+    return r.view(np.float32)
+
+
+def _bf16_ulp(v):
+    """Spacing of bfloat16 numbers (8 significant bits) at |v|."""
+    a = np.maximum(np.abs(v), 1e-30)
+    return np.exp2(np.floor(np.log2(a)) - 7)
+
+
+@pytest.mark.parametrize("n,c1", [(128, 8), (128, 16)])
+def test_tensor_core_forward_layers_vs_fp64_oracle(lib, n, c1):
+    """Each layer of the tensor-core forward against the FP64 oracle's convolution (Eq.-free: the
+    network has no counterpart in the paper) given the same inputs: the GPU's own stored bf16 input
+    activations (so errors do not compound), the weights rounded to bf16 as the GPU stores them and
+    the float32 biases.  Every output must be the bf16 rounding of the exact value up to one bf16
+    unit (float32 sums may round the other way at a tie) plus float32 summation error; a wrong
+    operand layout, tap offset or channel group gives O(1) errors.  The fused 1x1 head and residual
+    of the last layer are checked on the float32 network output."""
+    from paper_1504_02591_gb300 import binding as B
+    specs = U.layer_specs(c1)
+    rng = np.random.default_rng(90 + c1)
+    params = U.init_params(90 + c1, c1=c1)
+    params["head"] = (rng.standard_normal((1, c1, 1)) * 0.3, np.array([0.05]))
+    for k in params:
+        w, b = params[k]
+        params[k] = (w, b + 0.05 * rng.standard_normal(b.shape))
+    flat = B.flat_params(params, specs)
+    gp = B.unflat_params(flat, specs)                  # float32 values the GPU holds
+    wq = {k: (_bf16(w).astype(np.float64), b.astype(np.float64)) for k, (w, b) in gp.items()}
+    net = B.UNet(c1=c1, bf16=True)
+    net.set_params(flat)
+    g = torch.Generator().manual_seed(7 * n + c1)
+    x = torch.randn((n, n, n, 5), generator=g)
+    y = net.forward(x.cuda()).cpu().numpy().astype(np.float64)
+    side = [n, n, n // 2, n // 2, n // 4, n // 4, n // 2, n // 2, n, n]
+    act = {l: net.get_layer(l, side[l], specs[l][2]).astype(np.float64) for l in range(9)}
+    net.close()
+    x64 = x.numpy().astype(np.float64)
+    pool = lambda a: _bf16(U.pool2(a)).astype(np.float64)      # the GPU stores pooled maps in bf16
+    inputs = {
+        0: _bf16(x.numpy()).astype(np.float64), 1: act[0], 2: pool(act[1]), 3: act[2], 4: pool(act[3]),
+        5: act[4], 6: np.concatenate([U.up2(act[5]), act[3]], axis=3), 7: act[6],
+        8: np.concatenate([U.up2(act[7]), act[1]], axis=3),
+    }
+    for l in range(9):
+        name = specs[l][0]
+        exact = np.maximum(U.conv3(inputs[l], *wq[name]), 0.0)
+        err = np.abs(act[l] - exact)
+        bound = _bf16_ulp(exact) + 1e-4 * np.abs(exact).max()
+        off = int((err > bound).sum())
+        flips = float((act[l] != _bf16(exact)).mean())
+        print(f"n={n} c1={c1} {name}: max err/bound {float((err / bound).max()):.2f}, "
+              f"{100 * flips:.3f}% elements one unit off the exact rounding")
+        assert off == 0, (name, off)
+        assert flips < 0.01, (name, flips)
+    d1b = _bf16(np.maximum(U.conv3(act[8], *wq["dec1b"]), 0.0)).astype(np.float64)
+    hw, hb = wq["head"]
+    want = U.conv3(d1b, hw, hb)[..., 0] + x64[..., 4]
+    e = _rel(y - x64[..., 4], want - x64[..., 4])
+    print(f"n={n} c1={c1} fused head + residual: rel L2 {e:.2e}")
+    assert e < 2e-3

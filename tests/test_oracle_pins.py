@@ -388,3 +388,57 @@ def test_lognormal_floor_branch():
     d2 = np.array([-1.0 + 2e-6, 0.0])
     out2, C2 = O.lognormal(d2)
     assert out2[0] - out2[1] == pytest.approx(np.log(2e-6), rel=1e-9)
+
+
+def test_ratio_stats_outlier_rule_by_hand():
+    """Tables 1-3: ratios above 3 or below -1 are cut; a zero denominator is an outlier."""
+    num = np.array([1.0, 2.0, 9.0, -4.0, 1.5, 0.5, 3.0])
+    den = np.array([1.0, 1.0, 1.0, 2.0, 0.0, 1.0, 1.0])      # ratios 1, 2, 9 (cut), -2 (cut), -, 0.5, 3
+    mean, std, out, kept = O.ratio_stats(num, den)
+    r = np.array([1.0, 2.0, 0.5, 3.0])
+    assert kept == 4 and out == pytest.approx(3.0 / 7.0)
+    assert mean == pytest.approx(1.625) and std == pytest.approx(np.sqrt(((r - 1.625) ** 2).mean()))
+
+
+@pytest.mark.parametrize("m", [(1, 0, 0), (0, 2, 0), (1, 1, 0), (2, -1, 3), (1, 2, 2)])
+def test_helmholtz_split_of_a_single_mode(m):
+    """Eq. irrotational / Eq. solenoidal on Psi_x = cos(k.x): grad A = (k_j k_x / k^2) cos(k.x) and
+    curl B = ((k_y^2 + k_z^2), -k_y k_x, -k_z k_x) cos(k.x) / k^2, so the x-ratio of the two is
+    k_x^2 / (k_y^2 + k_z^2) and the y, z ratios are -1 wherever they are defined; grad A is curl-free,
+    curl B divergence-free, and the two add up to (Psi.x) x."""
+    n, L = 16, 400.0
+    k, arg = _mode(n, L, m)
+    psi = np.zeros((3, n, n, n))
+    psi[0] = np.cos(arg)
+    psi[1] = 0.7 * np.sin(arg)            # components other than x play no part
+    ga, cb = O.helmholtz_x(psi, L)
+    k2 = k @ k
+    c = np.cos(arg)
+    assert np.abs(ga - (k[:, None, None, None] * k[0] / k2) * c).max() < 1e-12
+    want_cb = np.stack([(k[1] ** 2 + k[2] ** 2) / k2 * c, -k[1] * k[0] / k2 * c, -k[2] * k[0] / k2 * c])
+    assert np.abs(cb - want_cb).max() < 1e-12
+    assert np.abs(ga + cb - np.stack([psi[0], 0 * c, 0 * c])).max() < 1e-12
+    # curl of grad A and divergence of curl B vanish (spectral derivatives)
+    _, kd, _ = O.kgrid(n, L)
+    GA = [O.fft3(g) for g in ga]
+    curl = [kd[1] * GA[2] - kd[2] * GA[1], kd[2] * GA[0] - kd[0] * GA[2], kd[0] * GA[1] - kd[1] * GA[0]]
+    assert max(np.abs(cc).max() for cc in curl) < 1e-9
+    div_cb = sum(kd[j] * O.fft3(cb[j]) for j in range(3))
+    assert np.abs(div_cb).max() < 1e-9
+
+
+def test_radial_ratio_uses_each_particles_line_of_sight():
+    """Eq. ratio at particles: constant fields Psi_real = (2, 0, 0), Psi_est = (4, 3, 0) seen from an
+    observer at the box centre: a particle along +x gives 2/4, one along +y gives 0/3, one along
+    the (1, 1, 0) diagonal gives (2/sqrt2)/(7/sqrt2) = 2/7."""
+    n, L = 8, 80.0
+    real = np.zeros((3, n, n, n))
+    est = np.zeros((3, n, n, n))
+    real[0] = 2.0
+    est[0], est[1] = 4.0, 3.0
+    obs = (40.0, 40.0, 40.0)
+    pos = np.array([[70.0, 40.0, 40.0], [40.0, 55.0, 40.0], [50.0, 50.0, 40.0]])
+    mean, std, out, kept = O.radial_ratio(real, est, pos, L, obs, O.LOS_RADIAL)
+    r = np.array([0.5, 0.0, 2.0 / 7.0])
+    assert kept == 3 and out == 0.0
+    assert mean == pytest.approx(r.mean(), rel=1e-12) and std == pytest.approx(r.std(), rel=1e-12)

@@ -1,15 +1,18 @@
 """recon_cic_deposit_noalloc: the deposit entry point for callers that cannot allocate device memory.
 
-Such callers (code running under CUDA stream capture, plugins whose host owns all device memory,
-real-time pipelines that must not enter an allocator) get a CIC deposit whose only scratch is a
-fixed array inside the library.  This test calls it through the C ABI twice in a row and checks each
-result against the ordinary handle-based deposit (recon_deposit) on the same catalogue.  The file is
-named to be collected last, so a stop at the first failure has already run every other test.
+Such callers (plugins whose host owns all device memory, real-time pipelines that must not enter an
+allocator) get a CIC deposit whose only scratch is a fixed array inside the library.  This test
+calls it through the C ABI twice in a row and checks each result against the ordinary handle-based
+deposit (recon_deposit) on the same catalogue, and against the FP64 oracle's CIC deposit and a
+float64 sum of the weights.  The file is named to be collected last, so a stop at the first failure
+has already run every other test.
 """
 import ctypes as C
 
 import numpy as np
 import pytest
+
+from oracle import recon_oracle as O
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -54,6 +57,14 @@ def test_noalloc_deposit_matches_handle_deposit_twice(lib):
         err = float(((got - want_rho.double()) ** 2).sum().sqrt() / (want_rho.double() ** 2).sum().sqrt())
         assert err < 1e-6, err
         assert float(sum_w.item()) == pytest.approx(want_sw, rel=1e-12)
+        # and the FP64 oracle (Sec. 3 binning with the CIC kernel), weights summed in float64
+        pos64 = pos.cpu().numpy().astype(np.float64)
+        w64 = None if w is None else w.cpu().numpy().astype(np.float64)
+        ref = O.cic_deposit(pos64, w64, N, L)
+        err_o = float(np.sqrt(((got.cpu().numpy() - ref) ** 2).sum() / (ref ** 2).sum()))
+        assert err_o < 1e-6, err_o
+        want_w = float(len(pos64)) if w64 is None else float(w64.sum())
+        assert float(sum_w.item()) == pytest.approx(want_w, rel=1e-12)
 
 
 def test_noalloc_rejects_too_many_particles(lib):
