@@ -111,6 +111,37 @@ def cic_deposit(pos, w, n: int, L: float):
     return rho.reshape(n, n, n)
 
 
+def ngp_deposit(pos, w, n: int, L: float):
+    """Nearest-grid-point binning (Sec. 3: the paper's scheme): each particle's weight goes to the
+    node nearest to it, node i at x_i = i L / N, i.e. i = floor(x N / L + 1/2) modulo N."""
+    pos = np.asarray(pos, dtype=np.float64)
+    w = np.ones(len(pos)) if w is None else np.asarray(w, dtype=np.float64)
+    i = np.floor(pos * (n / L) + 0.5).astype(np.int64) % n
+    idx = (i[:, 0] * n + i[:, 1]) * n + i[:, 2]
+    return np.bincount(idx, weights=w, minlength=n ** 3).reshape(n, n, n)
+
+
+def radial_nbar(pos, observer, r_edges, sky_area: float):
+    """Mean number density of a catalogue in radial shells about the observer (the n(z) of Sec. 3.2
+    in comoving distance): counts per shell / (sky_area (r_hi^3 - r_lo^3) / 3), sky_area in sr."""
+    r = np.sqrt(((np.asarray(pos, dtype=np.float64) - np.asarray(observer, dtype=np.float64)) ** 2).sum(1))
+    counts, _ = np.histogram(r, bins=np.asarray(r_edges, dtype=np.float64))
+    e = np.asarray(r_edges, dtype=np.float64)
+    return counts / (sky_area * (e[1:] ** 3 - e[:-1] ** 3) / 3.0)
+
+
+def fkp_weights(pos, observer, r_edges, nbar, P0: float = 20000.0):
+    """FKP weights w = 1 / (1 + nbar(r) P0) (Sec. 3.2, P0 = 20000 (Mpc/h)^3), nbar of the shell that
+    holds the particle's distance from the observer; particles outside the shells get nbar = 0."""
+    r = np.sqrt(((np.asarray(pos, dtype=np.float64) - np.asarray(observer, dtype=np.float64)) ** 2).sum(1))
+    e = np.asarray(r_edges, dtype=np.float64)
+    b = np.searchsorted(e, r, side="right") - 1
+    inside = (b >= 0) & (b < len(e) - 1)
+    nb = np.zeros(len(r))
+    nb[inside] = np.asarray(nbar, dtype=np.float64)[b[inside]]
+    return 1.0 / (1.0 + nb * P0)
+
+
 def cic_gather(field, pos, L: float):
     """Interpolate a real field (n,n,n) or (3,n,n,n) to particles with the CIC (trilinear) kernel."""
     field = np.asarray(field, dtype=np.float64)
@@ -305,6 +336,111 @@ def shifted_positions(pos, d, L: float, periodic: bool):
 
 
 # --------------------------------------------------------------------------------------------
+# Finite-difference configuration-space method (Sec. 2.1, Eq. mainpot)
+# --------------------------------------------------------------------------------------------
+def _shift(a, d):
+    """a at the node offset by d = (dx, dy, dz), zero beyond the mesh: out[i] = a[i + d] (the
+    finite-difference problem's boundary condition phi = 0 outside the box)."""
+    out = np.zeros_like(a)
+    src = tuple(slice(max(0, k), a.shape[j] + min(0, k)) for j, k in enumerate(d))
+    dst = tuple(slice(max(0, -k), a.shape[j] + min(0, -k)) for j, k in enumerate(d))
+    out[dst] = a[src]
+    return out
+
+
+def fd_operator(phi, L: float, beta: float, observer, los_mode: int):
+    """A phi = grad^2 phi + beta div((grad phi . r) r) on the mesh, phi = 0 outside it, with the
+    stencils of Sec. 2.1: the 7-point Laplacian (set A) and, for the line-of-sight term,
+      -2 phi_0 / g^2 + sum_B (x_i^2 / (g^2 r^2) +- x_i / (g r^2)) phi_(+-i)
+                     + sum_C (-1)^p x_i x_j / (2 g^2 r^2) phi_(+-i, +-j)
+    with x the node's offset from the observer, r = |x|, g the mesh spacing, p = 0 when the two
+    offsets have the same sign and 1 otherwise (the paper writes f where this build uses beta).  For
+    a fixed line of sight u the term is sum_ij u_i u_j d_i d_j phi with the same second-difference
+    stencils (x_i / r -> u_i, no 1/r term).  At the observer's node the term is 0."""
+    n = phi.shape[0]
+    g = L / n
+    out = -6.0 * phi
+    for a in range(3):
+        for sgn in (1, -1):
+            d = [0, 0, 0]
+            d[a] = sgn
+            out = out + _shift(phi, d)
+    out = out / (g * g)
+    if beta == 0.0:
+        return out
+    if los_mode == LOS_FIXED:
+        u = np.asarray(observer, dtype=np.float64)
+        u = u / np.linalg.norm(u)
+        xs = [np.full(phi.shape, u[a]) for a in range(3)]
+        inv_r2 = np.ones(phi.shape)
+        first = 0.0
+    else:
+        o = np.asarray(observer, dtype=np.float64)
+        x = np.arange(n) * g
+        xs = list(np.meshgrid(x - o[0], x - o[1], x - o[2], indexing="ij"))
+        r2 = xs[0] ** 2 + xs[1] ** 2 + xs[2] ** 2
+        inv_r2 = np.zeros_like(r2)
+        np.divide(1.0, r2, out=inv_r2, where=r2 > 0)
+        first = 1.0
+    rsd = -2.0 * phi * (inv_r2 > 0) / (g * g)
+    for a in range(3):
+        for sgn in (1, -1):
+            d = [0, 0, 0]
+            d[a] = sgn
+            coef = xs[a] ** 2 * inv_r2 / (g * g) + sgn * first * xs[a] * inv_r2 / g
+            rsd = rsd + coef * _shift(phi, d)
+    for a in range(3):
+        for b in range(a + 1, 3):
+            for sa in (1, -1):
+                for sb in (1, -1):
+                    d = [0, 0, 0]
+                    d[a], d[b] = sa, sb
+                    rsd = rsd + (sa * sb) * xs[a] * xs[b] * inv_r2 / (2.0 * g * g) * _shift(phi, d)
+    return out + beta * rsd
+
+
+def fd_laplacian_eigen(n: int, L: float):
+    """Eigenvalues of the periodic 7-point Laplacian on the rfftn grid: sum_i (2 cos(k_i g) - 2) / g^2."""
+    g = L / n
+    (kx, ky, kz), _, _ = kgrid(n, L)
+    return sum((2.0 * np.cos(k * g) - 2.0) / (g * g) for k in (kx, ky, kz))
+
+
+def fd_solve(delta, b: float, f: float, L: float, observer, los_mode: int, tol: float = 1e-10,
+             max_iter: int = 500):
+    """The configuration-space method of Sec. 2.1: solve A phi = delta/b (A as fd_operator, the
+    paper's A phi = delta_g / b with Psi = -grad phi, phi = 0 outside the box) with GMRES,
+    preconditioned by the inverse of the periodic 7-point Laplacian (applied with FFTs); then
+    Psi = -grad phi by central differences (phi = 0 beyond the box).  Returns (Psi, phi,
+    iterations, relative residual)."""
+    from scipy.sparse.linalg import LinearOperator, gmres
+    n = delta.shape[0]
+    beta = f / b
+    rhs = delta / b
+    lam = fd_laplacian_eigen(n, L)
+    inv_lam = np.zeros_like(lam)
+    np.divide(1.0, lam, out=inv_lam, where=lam != 0)
+    inv_lam[0, 0, 0] = -L * L / (3.0 * np.pi ** 2)   # the constant mode: the lowest Dirichlet eigenvalue
+    shape = delta.shape
+    A = LinearOperator((n ** 3, n ** 3), dtype=np.float64,
+                       matvec=lambda v: fd_operator(v.reshape(shape), L, beta, observer, los_mode).ravel())
+    M = LinearOperator((n ** 3, n ** 3), dtype=np.float64,
+                       matvec=lambda v: ifft3(fft3(v.reshape(shape)) * inv_lam, n).ravel())
+    count = [0]
+
+    def cb(_):
+        count[0] += 1
+    sol, info = gmres(A, rhs.ravel(), M=M, rtol=tol, atol=0.0, restart=50, maxiter=max_iter,
+                      callback=cb, callback_type="pr_norm")
+    phi = sol.reshape(shape)
+    res = np.linalg.norm(fd_operator(phi, L, beta, observer, los_mode) - rhs) / np.linalg.norm(rhs)
+    g = L / n
+    psi = np.stack([-(_shift(phi, [1 if a == j else 0 for a in range(3)]) -
+                      _shift(phi, [-1 if a == j else 0 for a in range(3)])) / (2.0 * g) for j in range(3)])
+    return psi, phi, count[0], res
+
+
+# --------------------------------------------------------------------------------------------
 # Diagnostics of the paper (Sec. 4.1 Helmholtz split, Sec. 4.3 / 5.2 radial ratio)
 # --------------------------------------------------------------------------------------------
 RATIO_LO, RATIO_HI = -1.0, 3.0   # Tables 1-3: ratios above 3 or below -1 are outliers
@@ -362,7 +498,8 @@ def reconstruct(params: dict, gal_pos, gal_w=None, ran_pos=None, ran_w=None,
                 shift: bool = True, mask_flip=None):
     """Run the whole method on a catalogue; returns a dict of every intermediate.
 
-    params: n, L, b, f, R, los_mode, observer, periodic, mask_frac, lognormal, uniform (bool).
+    params: n, L, b, f, R, los_mode, observer, periodic, mask_frac, lognormal, uniform (bool), and
+    optionally ngp (bool: the paper's nearest-grid-point binning instead of CIC, Sec. 3).
     mask_flip: optional flat node indices at which the survey-mask decision is inverted.  The mask
     is a floating-point comparison of the smoothed random density with a threshold; at nodes whose
     density lies within rounding of the threshold either decision is valid, and a comparison with
@@ -372,7 +509,8 @@ def reconstruct(params: dict, gal_pos, gal_w=None, ran_pos=None, ran_w=None,
     gal_pos = np.asarray(gal_pos, dtype=np.float64)
     wg = np.ones(len(gal_pos)) if gal_w is None else np.asarray(gal_w, dtype=np.float64)
     out = {}
-    rho_g = cic_deposit(gal_pos, wg, n, L)
+    deposit = ngp_deposit if params.get("ngp", False) else cic_deposit
+    rho_g = deposit(gal_pos, wg, n, L)
     out["rho_g"] = rho_g
     out["sum_wg"] = wg.sum()
     rho_g_s = smooth(rho_g, params["R"], L)
@@ -382,7 +520,7 @@ def reconstruct(params: dict, gal_pos, gal_w=None, ran_pos=None, ran_w=None,
     else:
         ran_pos = np.asarray(ran_pos, dtype=np.float64)
         wr = np.ones(len(ran_pos)) if ran_w is None else np.asarray(ran_w, dtype=np.float64)
-        rho_r = cic_deposit(ran_pos, wr, n, L)
+        rho_r = deposit(ran_pos, wr, n, L)
         out["rho_r"] = rho_r
         out["sum_wr"] = wr.sum()
         rho_r_s = smooth(rho_r, params["R"], L)

@@ -442,3 +442,106 @@ def test_radial_ratio_uses_each_particles_line_of_sight():
     r = np.array([0.5, 0.0, 2.0 / 7.0])
     assert kept == 3 and out == 0.0
     assert mean == pytest.approx(r.mean(), rel=1e-12) and std == pytest.approx(r.std(), rel=1e-12)
+
+
+def test_ngp_deposit_by_hand():
+    """Sec. 3 NGP: a particle goes to its nearest node; halfway between nodes it goes up; periodic."""
+    n, L = 8, 80.0                                  # H = 10
+    pos = np.array([[14.9, 25.0, 0.0], [15.0, 24.9, 79.0], [79.9, 0.1, 44.0]])
+    rho = O.ngp_deposit(pos, np.array([1.0, 2.0, 4.0]), n, L)
+    assert rho[1, 3, 0] == 1.0            # (1.49, 2.5, 0) -> (1, 3, 0)
+    assert rho[2, 2, 0] == 2.0            # (1.5, 2.49, 7.9) -> (2, 2, 8 = 0)
+    assert rho[0, 0, 4] == 4.0            # (7.99, 0.01, 4.4) -> (8 = 0, 0, 4)
+    assert rho.sum() == 7.0 and np.count_nonzero(rho) == 3
+
+
+def test_radial_nbar_and_fkp_weights():
+    """n(r) of a uniform shell catalogue is its number over the shell's volume; FKP weights
+    1/(1 + n P0) (Sec. 3.2) by hand, with n = 0 outside the shells."""
+    obs = np.array([100.0, 100.0, 100.0])
+    # 3 particles at r = 10, 2 at r = 25, one at r = 40 (outside the shells [0, 20) and [20, 30))
+    dirs = np.array([[1, 0, 0], [0, 1, 0], [0, 0, -1], [0.6, 0.8, 0], [0, -0.6, 0.8], [1, 0, 0]], dtype=float)
+    rr = np.array([10.0, 10.0, 10.0, 25.0, 25.0, 40.0])
+    pos = obs + dirs * rr[:, None]
+    edges = [0.0, 20.0, 30.0]
+    sky = 2.0
+    nbar = O.radial_nbar(pos, obs, edges, sky)
+    want = np.array([3.0 / (sky * 20.0 ** 3 / 3.0), 2.0 / (sky * (30.0 ** 3 - 20.0 ** 3) / 3.0)])
+    assert np.allclose(nbar, want, rtol=1e-14)
+    w = O.fkp_weights(pos, obs, edges, nbar, P0=20000.0)
+    assert np.allclose(w, [1 / (1 + want[0] * 2e4)] * 3 + [1 / (1 + want[1] * 2e4)] * 2 + [1.0], rtol=1e-14)
+
+
+def _dst_mode(n, m):
+    """Discrete sine mode sin(pi m_a (i_a + 1) / (n + 1)) per axis: zero just outside the mesh."""
+    i = np.arange(n) + 1.0
+    s = [np.sin(np.pi * mm * i / (n + 1)) for mm in m]
+    return s[0][:, None, None] * s[1][None, :, None] * s[2][None, None, :]
+
+
+def test_fd_operator_eigenmodes():
+    """Sec. 2.1 stencils with phi = 0 outside the mesh: a discrete sine mode is an eigenvector of
+    the 7-point Laplacian with eigenvalue sum_a (2 cos(pi m_a / (n + 1)) - 2) / g^2, and for a fixed
+    line of sight along x the line-of-sight term adds beta (2 cos(pi m_x / (n + 1)) - 2) / g^2."""
+    n, L = 12, 300.0
+    g = L / n
+    m = (2, 3, 5)
+    phi = _dst_mode(n, m)
+    lam = [(2.0 * np.cos(np.pi * mm / (n + 1)) - 2.0) / g ** 2 for mm in m]
+    assert np.abs(O.fd_operator(phi, L, 0.0, (1, 0, 0), O.LOS_FIXED) - sum(lam) * phi).max() < 1e-12
+    beta = 0.4
+    got = O.fd_operator(phi, L, beta, (1, 0, 0), O.LOS_FIXED)
+    assert np.abs(got - (sum(lam) + beta * lam[0]) * phi).max() < 1e-12
+
+
+def test_fd_fixed_los_stencil_is_symmetric_and_radial_is_second_order():
+    """The fixed-LOS stencil (central second differences) is symmetric; the radial one, with its
+    (2/r) d/dr term, approximates div((grad phi . r) r) of a smooth blob to second order in g."""
+    rng = np.random.default_rng(4)
+    n, L = 10, 200.0
+    a, b = rng.standard_normal((2, n, n, n))
+    u = (0.3, -0.5, 0.81)
+    Aa, Ab = (O.fd_operator(v, L, 0.7, u, O.LOS_FIXED) for v in (a, b))
+    assert (b * Aa).sum() == pytest.approx((a * Ab).sum(), rel=1e-12)
+    obs = np.array([-150.0, 80.0, 120.0])
+    errs = []
+    for n in (32, 64):
+        L = 200.0
+        g = L / n
+        x = np.arange(n) * g
+        X = np.stack(np.meshgrid(x, x, x, indexing="ij"))
+        c, s2 = np.array([100.0, 100.0, 100.0]), 18.0 ** 2
+        dX = X - c[:, None, None, None]
+        phi = np.exp(-(dX ** 2).sum(0) / (2 * s2))
+        grad = -dX / s2 * phi
+        hess = [[(dX[i] * dX[j] / s2 ** 2 - (i == j) / s2) * phi for j in range(3)] for i in range(3)]
+        d = X - obs[:, None, None, None]
+        r = np.sqrt((d ** 2).sum(0))
+        rh = d / r
+        exact = sum(rh[i] * rh[j] * hess[i][j] for i in range(3) for j in range(3)) + \
+            (2.0 / r) * sum(rh[i] * grad[i] for i in range(3))
+        fd = O.fd_operator(phi, L, 1.0, obs, O.LOS_RADIAL) - O.fd_operator(phi, L, 0.0, obs, O.LOS_RADIAL)
+        errs.append(np.abs(fd - exact).max() / np.abs(exact).max())
+    assert errs[1] < 1e-2 and errs[0] / errs[1] == pytest.approx(4.0, rel=0.15)
+
+
+def test_fd_solve_matches_sine_transform_solution():
+    """f = 0 and a fixed line of sight along x: the operator is diagonal in the discrete sine basis,
+    so the exact solution is a sine transform; the GMRES solve (with its FFT preconditioner for the
+    periodic Laplacian) must reproduce it, and Psi = -grad phi by central differences."""
+    from scipy.fft import dstn, idstn
+    n, L, b = 24, 480.0, 2.0
+    g = L / n
+    rng = np.random.default_rng(9)
+    delta = O.smooth(rng.standard_normal((n, n, n)), 40.0, L)
+    m = np.arange(1, n + 1)
+    lam1 = (2.0 * np.cos(np.pi * m / (n + 1)) - 2.0) / g ** 2
+    lap = lam1[:, None, None] + lam1[None, :, None] + lam1[None, None, :]
+    for f in (0.0, 0.8):
+        eig = lap + (f / b) * lam1[:, None, None]
+        want = idstn(dstn(delta / b, type=1) / eig, type=1)
+        psi, phi, it, res = O.fd_solve(delta, b, f, L, (1.0, 0.0, 0.0), O.LOS_FIXED, tol=1e-12)
+        assert np.abs(phi - want).max() < 1e-9 * np.abs(want).max()
+        ppad = np.pad(want, 1)
+        gx = -(ppad[2:, 1:-1, 1:-1] - ppad[:-2, 1:-1, 1:-1]) / (2 * g)
+        assert np.abs(psi[0] - gx).max() < 1e-9 * np.abs(gx).max()
