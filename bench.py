@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT context timing")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-mock batch")
     ap.add_argument("--no-diag", action="store_true", help="skip the paper's diagnostics")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="only run the whole FP64 oracle on the result table's workloads (host cores)")
+    ap.add_argument("--cpu-full-1024", action="store_true", help="with --cpu-full: also the 1024^3 run (~150 GB)")
     ap.add_argument("--plane-batch", type=int, default=None,
                     help="y-planes per batch of the x -> z -> x passes (0 off; default: the library's)")
     ap.add_argument("--particle-order", choices=("retained", "per-call"), default="retained",
@@ -200,6 +203,50 @@ def oracle_stages(m, n_iter, cores):
     cpu_s = time.perf_counter() - c0
     total = sum(v for k, v in t.items() if k != "update") + n_iter * t["update"]
     return total * 1000.0, {k: round(v, 3) for k, v in t.items()}, cpu_s
+
+
+def cpu_full(args):
+    """The FP64 oracle as it stands, run whole (no sampling) on the workloads of the results table:
+    the 64^3 periodic box (6 updates, uncorrected and Eq. approx2 starts), the 512^3 survey shell to
+    1e-6, and the 1024^3 periodic box (6 updates) when the host has the memory; all host cores and
+    one core.  Prints one JSON line per run."""
+    import numpy as np
+    from oracle import recon_oracle as O
+    from paper_1504_02591_gb300 import mocks
+    cores = os.cpu_count() or 1
+
+    def run(name, m, kw, threads, ran=True):
+        O.FFT_WORKERS = threads
+        O.fft3(np.zeros((32, 32, 32)))
+        t0 = time.perf_counter()
+        out = O.reconstruct(m.params(), m.galaxies.pos, None, m.randoms.pos if ran else None, None, **kw)
+        dt = time.perf_counter() - t0
+        print(json.dumps({"cpu_full": name, "cores": threads, "seconds": round(dt, 2), "n_iter": out["n_iter"],
+                          "last_rel": out["rel"][-1] if out["rel"] else None}), flush=True)
+
+    m1 = mocks.small_periodic()
+    for threads in (cores, 1):
+        for start in (O.START_PLAIN, O.START_FFTA):
+            run(f"64^3 periodic, 6 updates, start {start}", m1, dict(start=start, tol=0.0, max_iter=6), threads)
+    m2 = mocks.survey_shell_512()
+    for threads in (cores, 1):
+        run("512^3 survey shell to 1e-6, Eq. approx2 start", m2, dict(start=O.START_FFTA, tol=1e-6, max_iter=80),
+            threads)
+    del m2
+    mem_gb = 0.0
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                mem_gb = int(line.split()[1]) / 2 ** 20
+    except OSError:
+        pass
+    if not args.cpu_full_1024:
+        return
+    if mem_gb >= 180:
+        m5 = mocks.large_periodic_1024(los_mode=0, device="cpu")
+        run("1024^3 periodic radial, 6 updates", m5, dict(start=O.START_FFTA, tol=0.0, max_iter=6), cores, ran=False)
+    else:
+        print(json.dumps({"cpu_full": "1024^3 periodic", "skipped": f"{mem_gb:.0f} GB host memory available"}))
 
 
 def cpu_sample_text(n_iter, stages, cores, cpu_s):
@@ -660,6 +707,9 @@ def gpu_arm(args):
 
 def main():
     args = parse()
+    if args.cpu_full:
+        cpu_full(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
     else:

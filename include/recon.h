@@ -203,6 +203,34 @@ recon_status recon_fft_r2c(recon_handle* h, const float* in_real, float* out_hal
  * the inverse DFT. Invalidates the reconstruction state like recon_fft_r2c. */
 recon_status recon_fft_c2r(recon_handle* h, const float* in_half, float* out_real);
 
+/* ---- The finite-difference method of Sec. 2.1 (the paper's comparison method) ----------------
+ * Solves Eq. mainpot in configuration space after recon_smooth: A phi = delta / b with A the
+ * 7-point Laplacian plus beta times the line-of-sight stencil of Sec. 2.1 (sets A, B and C; beta =
+ * f / b; a fixed line of sight takes the second differences only), phi = 0 outside the box, then
+ * Psi = -grad phi by central differences.  The linear system is solved with BiCGStab (float32
+ * vectors, float64 inner products), right-preconditioned by the exact inverse of the periodic
+ * 7-point Laplacian (the library's FFT passes on the handle's first field), until the recursive
+ * residual falls below tol x |b|.  psi_out: device (3, N^3) float32.  *n_iter: iterations;
+ * *rel_resid: the true residual |A phi - b| / |b| at the end.  Allocates its 9 Krylov vectors
+ * (9 N^3 float32) with cudaMalloc for the call.  The smoothed delta stays valid, so recon_iterate
+ * may follow.  NOT_CONVERGED when max_iter is reached; STATE before recon_smooth. */
+recon_status recon_fd_solve(recon_handle* h, double tol, int max_iter, int* n_iter, double* rel_resid,
+                            float* psi_out);
+
+/* ---- The paper's front end (Sec. 3.2): FKP weights from the radial number density ------------
+ * Mean number density nbar (host, nbins float64) of the catalogue cat (device memory) in nbins
+ * equal shells of comoving distance [rmin, rmax) about the handle's observer: counts / (sky_area
+ * (r_hi^3 - r_lo^3) / 3), sky_area the survey's solid angle in steradians (the n(z) of the paper in
+ * distance).  Distances in float64.  Synchronises the handle's stream. */
+recon_status recon_radial_nbar(recon_handle* h, const recon_catalog* cat, int nbins, double rmin, double rmax,
+                               double sky_area, double* nbar);
+
+/* FKP weights w = 1 / (1 + nbar(r) P0) (Sec. 3.2; the paper takes P0 = 20000 (Mpc/h)^3) for every
+ * particle of cat (device), nbar (host, nbins) of the shell holding its distance, 0 outside
+ * [rmin, rmax); w_out: device (n) float32, usable as the catalogue's weights in recon_deposit. */
+recon_status recon_fkp_weights(recon_handle* h, const recon_catalog* cat, int nbins, double rmin, double rmax,
+                               const double* nbar, double P0, float* w_out);
+
 /* ---- Diagnostics of the paper (computed on the GPU) -------------------------------------------
  * Statistics of a ratio, as in Tables 1-3: out[0] mean and out[1] standard deviation (population)
  * of the ratios inside [lo, hi] (the paper cuts ratios above 3 or below -1: lo = -1, hi = 3; a zero
@@ -308,6 +336,10 @@ enum {
                                    pass run in kernels that keep the first and last FFT stages
                                    (and the c2r/r2c pairing) in registers; 1: the generic staged
                                    kernels (same butterflies)                                     */
+  RECON_OPT_ASSIGN = 7,         /* mass assignment of recon_deposit: 0 (default) cloud-in-cell, 1 the
+                                   paper's nearest grid point (Sec. 3: node floor(x N / L + 1/2)),
+                                   always on the direct (unsorted) deposit kernel.  The shift still
+                                   interpolates Psi with CIC.                                     */
   RECON_OPT_PLANE_BATCH = 6     /* register-fused path (N = 512): 0 (off) or 16, 32, 64 y-planes per
                                    batch; each update then runs its inverse x, projection and forward
                                    x passes batch by batch, so a batch's fields stay in the L2 between

@@ -35,9 +35,11 @@ ABI_SYMBOLS = (
     "recon_unet_launch_count",
     "recon_iterate_from", "recon_start_features",
     "recon_get_radial", "recon_radial_ratio", "recon_ratio_stats", "recon_helmholtz_x",
+    "recon_radial_nbar", "recon_fkp_weights", "recon_fd_solve",
 )
 OPT_DEPOSIT_PATH, OPT_SHIFT_PATH, OPT_GRAPH, OPT_LINE_TILE, OPT_KSPACE_GENERIC, OPT_REUSE_SORT = 0, 1, 2, 3, 4, 5
-OPT_PLANE_BATCH = 6
+OPT_PLANE_BATCH, OPT_ASSIGN = 6, 7
+ASSIGN_CIC, ASSIGN_NGP = 0, 1
 UNET_OPT_TENSOR_CORES = 0
 PATH_DIRECT, PATH_SORTED = 0, 1
 KERNEL_KINDS = ("deposit", "z_fwd", "z_inv", "z_delta", "z_proj", "z_final", "line_fwd", "line_inv",
@@ -119,6 +121,9 @@ def load(path: str = LIB_PATH):
     lib.recon_unet_launch_count.argtypes = [VP, C.POINTER(C.c_longlong)]
     lib.recon_unet_last_error.argtypes = [VP]
     lib.recon_unet_last_error.restype = C.c_char_p
+    lib.recon_fd_solve.argtypes = [VP, D, I, P(I), P(D), VP]
+    lib.recon_radial_nbar.argtypes = [VP, P(ReconCatalog), I, D, D, D, P(D)]
+    lib.recon_fkp_weights.argtypes = [VP, P(ReconCatalog), I, D, D, P(D), D, VP]
     lib.recon_radial_ratio.argtypes = [VP, VP, VP, P(ReconCatalog), D, D, P(D)]
     lib.recon_ratio_stats.argtypes = [VP, VP, VP, C.c_int64, D, D, P(D)]
     lib.recon_helmholtz_x.argtypes = [VP, VP, VP, VP]
@@ -325,6 +330,41 @@ class Recon:
                                   C.c_void_p(pp) if pp else None, int(on_dev))
         self._check(st, "recon_shift")
         return (sh, po) if want_pos else sh
+
+    # -- the finite-difference method (Sec. 2.1) ------------------------------------------------
+    def fd_solve(self, tol=1e-6, max_iter=200):
+        """Eq. mainpot by finite differences after smooth(): (Psi (3, N, N, N) CUDA, iterations,
+        true relative residual, status)."""
+        import torch
+        psi = torch.empty((3, self.n, self.n, self.n), dtype=torch.float32, device="cuda")
+        it = C.c_int(0)
+        res = C.c_double(0)
+        st = self.lib.recon_fd_solve(self.h, float(tol), int(max_iter), C.byref(it), C.byref(res),
+                                     C.c_void_p(psi.data_ptr()))
+        self._check(st, "recon_fd_solve", allow=(ERR_NOT_CONVERGED,))
+        return psi, it.value, res.value, st
+
+    # -- the paper's front end: n(r) and FKP weights ---------------------------------------------
+    def radial_nbar(self, pos, nbins, rmin, rmax, sky_area):
+        """n(r) (numpy, nbins) of the particles pos (CUDA (n, 3)) about the handle's observer."""
+        keep = []
+        cat = _catalog(pos, None, keep)
+        out = (C.c_double * int(nbins))()
+        self._check(self.lib.recon_radial_nbar(self.h, C.byref(cat), int(nbins), float(rmin), float(rmax),
+                                               float(sky_area), out), "recon_radial_nbar")
+        return np.array(out[:], dtype=np.float64)
+
+    def fkp_weights(self, pos, nbar, rmin, rmax, P0=20000.0):
+        """FKP weights (CUDA float32 (n,)) of the particles pos for the shells' nbar."""
+        import torch
+        keep = []
+        cat = _catalog(pos, None, keep)
+        nb = np.ascontiguousarray(nbar, dtype=np.float64)
+        w = torch.empty(cat.n, dtype=torch.float32, device="cuda")
+        self._check(self.lib.recon_fkp_weights(self.h, C.byref(cat), len(nb), float(rmin), float(rmax),
+                                               nb.ctypes.data_as(C.POINTER(C.c_double)), float(P0),
+                                               C.c_void_p(w.data_ptr())), "recon_fkp_weights")
+        return w
 
     # -- the paper's diagnostics -----------------------------------------------------------------
     def radial_ratio(self, psi_num, psi_den, pos, lo=-1.0, hi=3.0):

@@ -73,6 +73,63 @@ __global__ void __launch_bounds__(256) deposit_kernel(const PT* __restrict__ pos
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+// Nearest-grid-point binning (Sec. 3, the paper's scheme): node floor(u + 1/2) per axis, from the
+// same 32.32 fixed-point coordinate as the CIC kernel (u 2^32 + 2^31 rounded down).
+template <typename PT>
+__global__ void __launch_bounds__(256) ngp_deposit_kernel(const PT* __restrict__ pos, const float* __restrict__ w,
+                                                          long long np, int n, double scale,
+                                                          float* __restrict__ rho, double* __restrict__ partials) {
+  double wsum = 0.0;
+  const size_t nn = (size_t)n;
+  const double scale32 = scale * 4294967296.0;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np;
+       p += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const long long T = __double2ll_rd(fma((double)pos[3 * p + a], scale32, 2147483648.0));
+      int k = (int)(T >> 32);
+      if (k < 0 || k >= n) k = ((k % n) + n) % n;
+      c[a] = k;
+    }
+    const float wp = w ? w[p] : 1.f;
+    wsum += wp;
+    atomicAdd(rho + ((size_t)c[0] * nn + c[1]) * nn + c[2], wp);
+  }
+  const double s = block_sum_d(wsum);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// Radial number density (Sec. 3.2 n(z), in comoving distance from the observer): counts of the
+// particles in nbins equal shells of [rmin, rmax), float64 distances.
+template <typename PT>
+__global__ void __launch_bounds__(256) radial_hist_kernel(const PT* __restrict__ pos, long long np, double3 obs,
+                                                          double rmin, double inv_dr, int nbins,
+                                                          unsigned long long* __restrict__ counts) {
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np;
+       p += (long long)gridDim.x * blockDim.x) {
+    const double dx = (double)pos[3 * p] - obs.x, dy = (double)pos[3 * p + 1] - obs.y, dz = (double)pos[3 * p + 2] - obs.z;
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    const double b = floor((r - rmin) * inv_dr);
+    if (b >= 0.0 && b < (double)nbins) atomicAdd(counts + (int)b, 1ull);
+  }
+}
+
+// FKP weights w = 1 / (1 + nbar(r) P0) (Sec. 3.2), nbar of the particle's shell, 0 outside.
+template <typename PT>
+__global__ void __launch_bounds__(256) fkp_kernel(const PT* __restrict__ pos, long long np, double3 obs, double rmin,
+                                                  double inv_dr, int nbins, const double* __restrict__ nbar,
+                                                  double P0, float* __restrict__ w) {
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np;
+       p += (long long)gridDim.x * blockDim.x) {
+    const double dx = (double)pos[3 * p] - obs.x, dy = (double)pos[3 * p + 1] - obs.y, dz = (double)pos[3 * p + 2] - obs.z;
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    const double b = floor((r - rmin) * inv_dr);
+    const double nb = (b >= 0.0 && b < (double)nbins) ? nbar[(int)b] : 0.0;
+    w[p] = (float)(1.0 / (1.0 + nb * P0));
+  }
+}
+
 template <typename PT>
 __global__ void __launch_bounds__(256) shift_kernel(const PT* __restrict__ pos, long long np, ShiftArgs a) {
   const size_t nn = (size_t)a.n;
@@ -188,9 +245,16 @@ __global__ void add_scalar_kernel(float* __restrict__ x, size_t n, float v) {
 }
 
 cudaError_t launch_deposit(const void* pos, int dtype, const float* w, long long np, int n, double L,
-                           float* rho, double* partials, int blocks, cudaStream_t st) {
+                           float* rho, double* partials, int blocks, cudaStream_t st, int ngp) {
   if (np <= 0) return cudaSuccess;
   const double scale = (double)n / L;
+  if (ngp) {
+    if (dtype == 0)
+      ngp_deposit_kernel<double><<<blocks, 256, 0, st>>>((const double*)pos, w, np, n, scale, rho, partials);
+    else
+      ngp_deposit_kernel<float><<<blocks, 256, 0, st>>>((const float*)pos, w, np, n, scale, rho, partials);
+    return cudaGetLastError();
+  }
   if (dtype == 0)
     deposit_kernel<double><<<blocks, 256, 0, st>>>((const double*)pos, w, np, n, scale, rho, partials);
   else
@@ -306,6 +370,30 @@ cudaError_t launch_radial_ratio(const void* pos, int dtype, long long np, const 
     radial_ratio_kernel<double><<<blocks, 256, 0, st>>>((const double*)pos, np, a);
   else
     radial_ratio_kernel<float><<<blocks, 256, 0, st>>>((const float*)pos, np, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_radial_hist(const void* pos, int dtype, long long np, double3 obs, double rmin, double rmax,
+                               int nbins, unsigned long long* counts, cudaStream_t st) {
+  if (np <= 0) return cudaSuccess;
+  const double inv_dr = nbins / (rmax - rmin);
+  const int blocks = (int)((np + 255) / 256 < 152 * 16 ? (np + 255) / 256 : 152 * 16);
+  if (dtype == 0)
+    radial_hist_kernel<double><<<blocks, 256, 0, st>>>((const double*)pos, np, obs, rmin, inv_dr, nbins, counts);
+  else
+    radial_hist_kernel<float><<<blocks, 256, 0, st>>>((const float*)pos, np, obs, rmin, inv_dr, nbins, counts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fkp(const void* pos, int dtype, long long np, double3 obs, double rmin, double rmax, int nbins,
+                       const double* nbar, double P0, float* w, cudaStream_t st) {
+  if (np <= 0) return cudaSuccess;
+  const double inv_dr = nbins / (rmax - rmin);
+  const int blocks = (int)((np + 255) / 256 < 152 * 16 ? (np + 255) / 256 : 152 * 16);
+  if (dtype == 0)
+    fkp_kernel<double><<<blocks, 256, 0, st>>>((const double*)pos, np, obs, rmin, inv_dr, nbins, nbar, P0, w);
+  else
+    fkp_kernel<float><<<blocks, 256, 0, st>>>((const float*)pos, np, obs, rmin, inv_dr, nbins, nbar, P0, w);
   return cudaGetLastError();
 }
 

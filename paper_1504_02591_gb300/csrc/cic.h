@@ -23,8 +23,15 @@ struct ShiftArgs {
 
 constexpr int kDepositBlocks = 152 * 8;
 
+// CIC (or, with ngp, nearest-grid-point) deposit; the weight sum of each block into partials.
 cudaError_t launch_deposit(const void* pos, int dtype, const float* w, long long np, int n, double L,
-                           float* rho, double* partials, int blocks, cudaStream_t st);
+                           float* rho, double* partials, int blocks, cudaStream_t st, int ngp = 0);
+// Counts of particles in nbins equal radial shells [rmin, rmax) about obs (counts zeroed by the caller).
+cudaError_t launch_radial_hist(const void* pos, int dtype, long long np, double3 obs, double rmin, double rmax,
+                               int nbins, unsigned long long* counts, cudaStream_t st);
+// FKP weights 1 / (1 + nbar P0) with nbar (device, nbins) of each particle's shell, 0 outside.
+cudaError_t launch_fkp(const void* pos, int dtype, long long np, double3 obs, double rmin, double rmax, int nbins,
+                       const double* nbar, double P0, float* w, cudaStream_t st);
 cudaError_t launch_shift(const void* pos, int dtype, long long np, const ShiftArgs& a, cudaStream_t st);
 // red[dst + q] (=|+=) the sum over b < nblocks of partials[b nq + q], q < nq <= 4, in a fixed order.
 // bsum (kFinalizeBlocks x 4 doubles) and counter (zeroed; left zeroed) let several blocks share the

@@ -105,8 +105,13 @@ struct ZWarpSmem {  // float2 slots of one warp's private region
   static constexpr int v = kLines + kQ + kRaw + ((kLines + kQ + kRaw) & 1);
 };
 
+// 1024-point lines hold twice the butterflies per thread: two CTAs per SM (128 registers) there;
+// the radix-3 and 64-point rows of N = 384 and 128 spill at 64 registers, so three CTAs (85)
+template <int N>
+constexpr int kZMinBlocks = N >= 1024 ? 2 : ((N == 384 || N == 128) ? 3 : 4);
+
 template <int N, int MODE, int NC>
-__global__ void __launch_bounds__(kZThreads, 4) zpass_kernel(const ZArgs a) {
+__global__ void __launch_bounds__(kZThreads, kZMinBlocks<N>) zpass_kernel(const ZArgs a) {
   constexpr int L = N / 2;
   constexpr int NF = (MODE == Z_DELTA) ? 1 : NC;   // lines transformed per row
   using Lay = RowLayout<L>;
@@ -880,8 +885,10 @@ __device__ __forceinline__ void tile_store(const float2* s, float2* __restrict__
 template <int N, int MODE, int NARROW = 0>
 struct SThreads {
   static constexpr bool kK = (MODE == S_DELTA || MODE == S_ITER);
-  static constexpr int v = (!kK && SCols<N, MODE, NARROW>::v == 16) ? 512 : 256;
-  static constexpr int minb = kK ? 3 : (v == 512 ? 2 : 4);
+  // 1024-point lines: 128 registers a thread (their butterflies and prefetched values spill at 64),
+  // and the k-space passes on 512 threads so that each prefetches 8 values of delta(k) and S
+  static constexpr int v = (N >= 1024 && kK) ? 512 : ((!kK && SCols<N, MODE, NARROW>::v == 16) ? 512 : 256);
+  static constexpr int minb = N >= 1024 ? (kK ? 1 : 2) : (kK ? 3 : (v == 512 ? 2 : 4));
 };
 
 template <int N, int MODE, int NC, int AXIS, int NARROW = 0>

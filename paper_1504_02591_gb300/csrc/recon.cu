@@ -21,6 +21,7 @@
 #include "cic.h"
 #include "conv.h"
 #include "diag.h"
+#include "fd.h"
 #include "loop.h"
 #include "warm.h"
 #include "types.h"
@@ -153,6 +154,7 @@ struct recon_handle {
   int narrow_lines = 0;
   int kspace_generic = 0;
   int plane_batch = 0;   // register-fused path: y-planes per batch of the x -> z -> x passes (0: off)
+  int assign = 0;        // mass assignment of the deposit: 0 CIC, 1 NGP (the paper's binning)
   int reuse_sort = 0;
   // the catalogue whose brick order the sort buffers hold (sorted deposit, one chunk)
   struct SortMemo {
@@ -410,18 +412,21 @@ const void* mapped_host(const void* p) {
 
 recon_status deposit_one(recon_handle* h, const recon_catalog* c, float* rho, int slot) {
   const size_t es = elem_size(c->dtype);
-  if (!c->on_device && c->n > 0 && h->deposit_path == RECON_PATH_DIRECT) {
+  // nearest-grid-point binning has no brick-sorted form: it always takes the direct kernel
+  const int path = h->assign ? RECON_PATH_DIRECT : h->deposit_path;
+  if (!c->on_device && c->n > 0 && path == RECON_PATH_DIRECT) {
     // page-locked host catalogue: the direct deposit reads it where it is, in one launch
     const void* dpos = mapped_host(c->pos);
     const float* dw = c->w ? static_cast<const float*>(mapped_host(c->w)) : nullptr;
     if (dpos && (!c->w || dw)) {
       RG_CUDA(timed(h, RECON_K_DEPOSIT, (double)c->n * (3 * es + (c->w ? 4 : 0)), [&] {
-        return launch_deposit(dpos, c->dtype, dw, c->n, h->n, h->L, rho, h->partials, kDepositBlocks, h->st); }));
+        return launch_deposit(dpos, c->dtype, dw, c->n, h->n, h->L, rho, h->partials, kDepositBlocks, h->st,
+                              h->assign); }));
       RG_TRY(finalize(h, kDepositBlocks, 1, slot, 0));
       return RECON_OK;
     }
   }
-  if (h->deposit_path == RECON_PATH_SORTED && c->n > 0 && c->n <= h->bb.chunk) {
+  if (path == RECON_PATH_SORTED && c->n > 0 && c->n <= h->bb.chunk) {
     // the whole catalogue in one sort (page-locked host memory is read in place); the sort
     // buffers then hold its brick order for a later shift of the same catalogue
     const void* dpos = c->on_device ? c->pos : mapped_host(c->pos);
@@ -440,7 +445,7 @@ recon_status deposit_one(recon_handle* h, const recon_catalog* c, float* rho, in
   char* spos = h->stage;
   float* sw = reinterpret_cast<float*>(h->stage + kStageParticles * 24);
   if (c->n == 0) RG_CUDA(cudaMemsetAsync(h->red + slot, 0, sizeof(double), h->st));
-  if (h->deposit_path == RECON_PATH_SORTED) h->memo.valid = 0;
+  if (path == RECON_PATH_SORTED) h->memo.valid = 0;
   for (long long p0 = 0; p0 < c->n; p0 += chunk) {
     const long long m = (c->n - p0 < chunk) ? c->n - p0 : chunk;
     const void* pin = (const char*)c->pos + (size_t)p0 * 3 * es;
@@ -453,14 +458,15 @@ recon_status deposit_one(recon_handle* h, const recon_catalog* c, float* rho, in
         win = sw;
       }
     }
-    if (h->deposit_path == RECON_PATH_SORTED) {
+    if (path == RECON_PATH_SORTED) {
       RG_CUDA(timed(h, RECON_K_SORT, (double)m * (6 * es + (c->w ? 4 : 0) + 28),
                     [&] { return brick_sort(h->bb, pin, c->dtype, win, m, h->st); }));
       RG_CUDA(timed(h, RECON_K_DEPOSIT, (double)m * 16, [&] { return brick_deposit(h->bb, rho, h->partials, h->st); }));
       RG_TRY(finalize(h, brick_grid(), 1, slot, p0 > 0));
     } else {
       RG_CUDA(timed(h, RECON_K_DEPOSIT, (double)m * (3 * es + (c->w ? 4 : 0)), [&] {
-        return launch_deposit(pin, c->dtype, win, m, h->n, h->L, rho, h->partials, kDepositBlocks, h->st); }));
+        return launch_deposit(pin, c->dtype, win, m, h->n, h->L, rho, h->partials, kDepositBlocks, h->st,
+                              h->assign); }));
       RG_TRY(finalize(h, kDepositBlocks, 1, slot, p0 > 0));
     }
   }
@@ -737,6 +743,7 @@ recon_status recon_set_option(recon_handle* h, int option, int value) {
   else if (option == RECON_OPT_LINE_TILE) h->narrow_lines = value;
   else if (option == RECON_OPT_KSPACE_GENERIC) h->kspace_generic = value ? 1 : 0;
   else if (option == RECON_OPT_REUSE_SORT) h->reuse_sort = value ? 1 : 0;
+  else if (option == RECON_OPT_ASSIGN) h->assign = value;
   else return RECON_ERR_INVALID_ARG;
   return RECON_OK;
 }
@@ -1406,6 +1413,172 @@ recon_status recon_fft_c2r(recon_handle* h, const float* in_half, float* out_rea
   a.f[0] = h->V[0];
   RG_TRY(run_z(h, Z_INV, 1, a));
   RG_CUDA(cudaMemcpyAsync(out_real, h->V[0].M, nr * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
+  return RECON_OK;
+}
+
+// ---- the finite-difference method of Sec. 2.1 (the paper's comparison method) ----------------
+namespace {
+
+// x . y in float64 over n values (one synchronisation).
+recon_status fd_dot(recon_handle* h, const float* x, const float* y, size_t n, double* out) {
+  const int blocks = kDepositBlocks;
+  RG_CUDA(timed(h, RECON_K_OTHER, 8.0 * n, [&] { return launch_dot(x, y, n, h->partials, blocks, h->st); }));
+  RG_TRY(finalize(h, blocks, 1, RED_DIAG, 0));
+  RG_CUDA(cudaMemcpyAsync(out, h->red + RED_DIAG, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  RG_CUDA(cudaStreamSynchronize(h->st));
+  return RECON_OK;
+}
+
+// out = M^-1 in: the inverse of the periodic 7-point Laplacian through the library's FFT passes on
+// the handle's first field.
+recon_status fd_precond(recon_handle* h, const float* in, float* out) {
+  const size_t nr = (size_t)h->n * h->n * h->n;
+  RG_CUDA(cudaMemcpyAsync(h->V[0].M, in, nr * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
+  ZArgs a = zargs(h);
+  a.f[0] = h->V[0];
+  RG_TRY(run_z(h, Z_FWD, 1, a));
+  RG_TRY(xpass(h, S_FWD, 1, h->V));
+  SArgs s = sargs(h);
+  s.f[0] = h->V[0];
+  RG_TRY(run_s(h, S_FWD, 1, AX_Y, s));
+  RG_CUDA(timed(h, RECON_K_OTHER, 2.0 * cfield(h), [&] { return launch_fd_precond_k(h->V[0], h->n, h->L, h->st); }));
+  RG_TRY(run_s(h, S_INV, 1, AX_Y, s));
+  RG_TRY(xpass(h, S_INV, 1, h->V));
+  RG_TRY(run_z(h, Z_INV, 1, a));
+  RG_CUDA(cudaMemcpyAsync(out, h->V[0].M, nr * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
+  return RECON_OK;
+}
+
+struct DeviceBuffer {
+  void* p = nullptr;
+  ~DeviceBuffer() {
+    if (p) cudaFree(p);
+  }
+};
+
+}  // namespace
+
+recon_status recon_fd_solve(recon_handle* h, double tol, int max_iter, int* n_iter, double* rel_resid, float* psi_out) {
+  if (!h || !psi_out || !(tol > 0) || max_iter < 1) return RECON_ERR_INVALID_ARG;
+  if (h->state < ST_SMOOTHED || !h->delta_real_valid) return RECON_ERR_STATE;
+  const size_t nr = (size_t)h->n * h->n * h->n;
+  DeviceBuffer buf;
+  if (cudaMalloc(&buf.p, 9 * nr * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return RECON_ERR_OOM;
+  }
+  float* v0 = static_cast<float*>(buf.p);
+  float *x = v0, *r = v0 + nr, *rh = v0 + 2 * nr, *p = v0 + 3 * nr, *v = v0 + 4 * nr, *ph = v0 + 5 * nr,
+        *sv = v0 + 6 * nr, *sh = v0 + 7 * nr, *t = v0 + 8 * nr;
+  FDArgs fa{};
+  fa.n = h->n;
+  fa.g = h->L / h->n;
+  fa.beta = h->p.f / h->p.b;
+  fa.los_mode = h->p.los_mode;
+  fa.los = make_double3(h->geo.los.x, h->geo.los.y, h->geo.los.z);
+  fa.off = h->cur_off;
+  // right-hand side delta / b (the lognormal constant added back, as recon_get_field does)
+  RG_CUDA(cudaMemcpyAsync(rh, h->V[2].M, nr * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
+  if (h->p.lognormal) {
+    double sl = 0;
+    RG_CUDA(cudaMemcpyAsync(&sl, h->red + RED_SUM_LOG, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    RG_CUDA(cudaStreamSynchronize(h->st));
+    RG_CUDA(launch_add_scalar(rh, nr, (float)(-sl / (double)nr), h->st));
+  }
+  RG_CUDA(cudaMemsetAsync(x, 0, nr * sizeof(float), h->st));
+  RG_CUDA(launch_fd_sub(r, x, rh, -1.0 / h->p.b, nr, h->st));     // r = 0 + delta / b
+  RG_CUDA(cudaMemcpyAsync(rh, r, nr * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
+  double bnorm2 = 0;
+  RG_TRY(fd_dot(h, r, r, nr, &bnorm2));
+  const double bnorm = std::sqrt(bnorm2);
+  double rho_old = 1.0, alpha = 1.0, omega = 1.0, res = bnorm > 0 ? 1.0 : 0.0;
+  int it = 0;
+  // BiCGStab, right-preconditioned (A M^-1 y = b, x = M^-1 y)
+  while (res > tol && it < max_iter) {
+    ++it;
+    double rho = 0;
+    RG_TRY(fd_dot(h, rh, r, nr, &rho));
+    if (it == 1) {
+      RG_CUDA(cudaMemcpyAsync(p, r, nr * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
+    } else {
+      RG_CUDA(launch_fd_dir(p, r, v, (rho / rho_old) * (alpha / omega), omega, nr, h->st));
+    }
+    RG_TRY(fd_precond(h, p, ph));
+    RG_CUDA(timed(h, RECON_K_OTHER, 8.0 * nr, [&] { return launch_fd_apply(ph, v, fa, h->st); }));
+    double rv = 0;
+    RG_TRY(fd_dot(h, rh, v, nr, &rv));
+    alpha = rho / rv;
+    RG_CUDA(launch_fd_sub(sv, r, v, alpha, nr, h->st));
+    double s2 = 0;
+    RG_TRY(fd_dot(h, sv, sv, nr, &s2));
+    if (std::sqrt(s2) / bnorm <= tol) {
+      RG_CUDA(launch_fd_acc(x, ph, ph, alpha, 0.0, nr, h->st));
+      res = std::sqrt(s2) / bnorm;
+      break;
+    }
+    RG_TRY(fd_precond(h, sv, sh));
+    RG_CUDA(timed(h, RECON_K_OTHER, 8.0 * nr, [&] { return launch_fd_apply(sh, t, fa, h->st); }));
+    double ts = 0, tt = 0;
+    RG_TRY(fd_dot(h, t, sv, nr, &ts));
+    RG_TRY(fd_dot(h, t, t, nr, &tt));
+    omega = tt > 0 ? ts / tt : 0.0;
+    RG_CUDA(launch_fd_acc(x, ph, sh, alpha, omega, nr, h->st));
+    RG_CUDA(launch_fd_sub(r, sv, t, omega, nr, h->st));
+    double r2 = 0;
+    RG_TRY(fd_dot(h, r, r, nr, &r2));
+    res = std::sqrt(r2) / bnorm;
+    if (!std::isfinite(res)) return RECON_ERR_NONFINITE;
+    rho_old = rho;
+    if (omega == 0.0) break;
+  }
+  // the true residual |A x - b| / |b| and Psi = -grad phi
+  RG_CUDA(launch_fd_apply(x, t, fa, h->st));
+  RG_CUDA(launch_fd_sub(t, t, rh, 1.0, nr, h->st));
+  double tr2 = 0;
+  RG_TRY(fd_dot(h, t, t, nr, &tr2));
+  RG_CUDA(timed(h, RECON_K_OTHER, 16.0 * nr, [&] { return launch_fd_gradient(x, psi_out, fa, h->st); }));
+  RG_CUDA(cudaStreamSynchronize(h->st));
+  if (n_iter) *n_iter = it;
+  const double true_res = bnorm > 0 ? std::sqrt(tr2) / bnorm : 0.0;
+  if (rel_resid) *rel_resid = true_res;
+  h->delta_real_valid = 1;   // the real delta (third field) is untouched; only the first field was used
+  return res > tol ? RECON_ERR_NOT_CONVERGED : RECON_OK;
+}
+
+// ---- the paper's front end (Sec. 3.2): radial number density and FKP weights ------------------
+recon_status recon_radial_nbar(recon_handle* h, const recon_catalog* cat, int nbins, double rmin, double rmax,
+                               double sky_area, double* nbar) {
+  if (!h || !nbar || nbins < 1 || nbins > 4096 || !(rmax > rmin) || !(rmin >= 0) || !(sky_area > 0))
+    return RECON_ERR_INVALID_ARG;
+  RG_TRY(check_catalog(cat));
+  if (cat->n > 0 && !cat->on_device) return RECON_ERR_INVALID_ARG;
+  unsigned long long* counts = reinterpret_cast<unsigned long long*>(h->partials);
+  RG_CUDA(cudaMemsetAsync(counts, 0, (size_t)nbins * sizeof(unsigned long long), h->st));
+  const double3 obs = make_double3(h->p.observer[0], h->p.observer[1], h->p.observer[2]);
+  RG_CUDA(timed(h, RECON_K_OTHER, (double)cat->n * 3 * elem_size(cat->dtype), [&] {
+    return launch_radial_hist(cat->pos, cat->dtype, cat->n, obs, rmin, rmax, nbins, counts, h->st); }));
+  std::vector<unsigned long long> c(nbins);
+  RG_CUDA(cudaMemcpyAsync(c.data(), counts, nbins * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->st));
+  RG_CUDA(cudaStreamSynchronize(h->st));
+  const double dr = (rmax - rmin) / nbins;
+  for (int b = 0; b < nbins; ++b) {
+    const double lo = rmin + b * dr, hi = rmin + (b + 1) * dr;
+    nbar[b] = (double)c[b] / (sky_area * (hi * hi * hi - lo * lo * lo) / 3.0);
+  }
+  return RECON_OK;
+}
+
+recon_status recon_fkp_weights(recon_handle* h, const recon_catalog* cat, int nbins, double rmin, double rmax,
+                               const double* nbar, double P0, float* w_out) {
+  if (!h || !nbar || nbins < 1 || nbins > 4096 || !(rmax > rmin) || !(P0 >= 0)) return RECON_ERR_INVALID_ARG;
+  RG_TRY(check_catalog(cat));
+  if (cat->n > 0 && (!cat->on_device || !w_out)) return RECON_ERR_INVALID_ARG;
+  double* dnb = h->partials;
+  RG_CUDA(cudaMemcpyAsync(dnb, nbar, nbins * sizeof(double), cudaMemcpyHostToDevice, h->st));
+  const double3 obs = make_double3(h->p.observer[0], h->p.observer[1], h->p.observer[2]);
+  RG_CUDA(timed(h, RECON_K_OTHER, (double)cat->n * (3 * elem_size(cat->dtype) + 4), [&] {
+    return launch_fkp(cat->pos, cat->dtype, cat->n, obs, rmin, rmax, nbins, dnb, P0, w_out, h->st); }));
+  RG_CUDA(cudaStreamSynchronize(h->st));   // nbar is read from the caller's host memory
   return RECON_OK;
 }
 

@@ -1,15 +1,16 @@
 // unet_tc.cu: periodic 3x3x3 convolution forward on the fifth-generation tensor cores (tcgen05).
 //
-// One CTA of 128 threads owns bx x by voxel tiles (runs of zlen voxels along z) and loops over its
-// share of the grid's blocks (persistent grid).  For every chunk of input channel groups, all
-// threads stage the tiles' halo and the chunk's weight tiles in shared memory with 16-byte cp.async
-// copies (two stages, so the next chunk loads while the tensor cores work on the current one); one
-// thread then issues the chunk's MMAs, each reading its activation operand straight out of the halo
-// through a shared-memory descriptor at the tap's offset, and commits them to the stage's mbarrier.
-// Accumulators live in tensor memory (one column block per tile); after the last chunk of a block
-// the four warps read them back with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31), add the bias,
-// apply ReLU, round to bf16 and store channels-last (or, for the last layer, apply the 1x1 head and
-// the residual and store float32).  Every wait on an mbarrier gives up after a bounded time, sets the
+// One CTA of 256 threads owns bx x by voxel tiles (runs of zlen voxels along z) and loops over its
+// share of the grid's blocks (persistent grid).  Warps 0-2 are producers: for every chunk of input
+// channel groups they stage the tiles' halo and the chunk's weight tiles in shared memory with
+// 16-byte cp.async copies (two stages, so the next chunk loads while the tensor cores work on the
+// current one).  One elected thread of warp 3 issues the chunk's MMAs, each reading its activation
+// operand straight out of the halo through a shared-memory descriptor at the tap's offset, and
+// commits them to the stage's mbarrier.  Accumulators live in tensor memory (one column block per
+// tile, two buffers); after the last chunk of a block the four epilogue warps 4-7 read them back
+// with tcgen05.ld (epilogue warp w owns TMEM lanes 32w..32w+31), add the bias, apply ReLU, round to
+// bf16 and store channels-last (or, for the last layer, apply the 1x1 head and the residual and
+// store float32).  Every wait on an mbarrier gives up after a bounded time, sets the
 // caller's error flag, drains what is in flight and frees the tensor memory before returning.
 #include "unet_tc.h"
 
