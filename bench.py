@@ -408,13 +408,74 @@ def large_periodic(args, timed, peak):
     return out
 
 
-def paper_diagnostics(m, r_main):
+def small_periodic_box(args, timed):
+    """The small plain-method case: 64^3 periodic box (L = 1000, 2e5 galaxies, 2e6 randoms, b = 2,
+    f = 0.74, R = 15, observer 1500 Mpc/h off the centre), 6 updates from each start; a step is
+    deposit -> smooth -> 6 updates -> shift of galaxies and randoms (device-resident)."""
+    import torch
+    from paper_1504_02591_gb300 import binding, mocks
+    m = mocks.small_periodic()
+    gal = torch.from_numpy(m.galaxies.pos).cuda()
+    ran = torch.from_numpy(m.randoms.pos).cuda()
+    r = binding.Recon.from_mock(m)
+    sg = torch.empty((len(gal), 3), dtype=torch.float32, device="cuda")
+    sr = torch.empty((len(ran), 3), dtype=torch.float32, device="cuda")
+    out = {"workload": "periodic 64^3, L=1000 Mpc/h, 2e5 galaxies + 2e6 randoms, b=2 f=0.74 R=15, 6 updates"}
+    for name, start in (("uncorrected", binding.START_PLAIN), ("eq_approx2", binding.START_FFTA)):
+        def step():
+            r.deposit(gal, None, ran, None)
+            r.smooth()
+            r.iterate(start, 0.0, 6)
+            r.shift(gal, True, out=sg)
+            r.shift(ran, False, out=sr)
+        for _ in range(3):
+            step()
+        k = max(5, args.steps)
+        out[name] = {"ms": round(timed(k, step) / k, 4)}
+    r.close()
+    return out
+
+
+def paper_diagnostics(m_bench, r_main):
     """Sec. 5.2 (Tables 2-3) on the benchmark survey: the mean radial ratio (Eq. ratio) of the
     real-space galaxies' displacement Z[delta_real/b] to the n-th iterate, at every galaxy, outliers
     (above 3 or below -1) cut, for n = 0..7 from the uncorrected and the Eq. approx2 starts, and the
     iteration after which the mean changes by less than 1% (the paper's criterion); plus the Sec. 4.1
     Helmholtz split of the converged displacement along x (irrotational / solenoidal ratio).  All on
     the GPU (recon_radial_ratio, recon_helmholtz_x, recon_ratio_stats)."""
+    import torch
+    from paper_1504_02591_gb300 import binding, mocks
+    from oracle import recon_oracle as O
+    out = {}
+    for label, m in (("benchmark_survey", m_bench),
+                     ("near_linear_survey", mocks.survey_shell_512(seed=40, amp=0.3))):
+        out[label] = radial_ratio_table(m)
+    # Sec. 4.1 on a plane-parallel periodic box: the Helmholtz split of the reconstructed
+    # displacement along the fixed line of sight x (the paper's Fig. 2 statistic)
+    mp = mocks.periodic_box(3500.0, 512, 4_000_000, 0, 1.85, 0.74, 10.0, (1.0, 0.0, 0.0), 41, 42, 43,
+                            los_mode=1, uniform=True)
+    r = binding.Recon.from_mock(mp)
+    r.deposit(torch.from_numpy(mp.galaxies.pos).cuda(), None, None, None)
+    r.smooth()
+    r.iterate(binding.START_FFTA, 1e-6, 80)
+    psi = r.get_psi()
+    ga, cb = r.helmholtz_x(psi[0])
+    out["helmholtz_x_plane_parallel"] = {
+        ax: {"all": [round(v, 4) for v in r.ratio_stats(ga[j], cb[j], -1e300, 1e300)[:2]],
+             "cut_-1_3": [round(v, 4) for v in r.ratio_stats(ga[j], cb[j])[:3]]} for j, ax in enumerate("xyz")}
+    r.close()
+    out["note"] = ("radial ratio at every galaxy, Psi_real from the same galaxies before their redshift-space "
+                   "shift; paper (mock, Table 3): uncorrected start 0.80 -> 1.10 -> 0.96 ..., converges after 6; "
+                   "Eq. approx2 start 1.04, after 2 (its solve uses f where this build uses beta = f/b); "
+                   "Helmholtz x ratio (Fig. 2, N-body Psi_true, R=10): mean 0.75, sigma 2.50")
+    del psi, ga, cb
+    torch.cuda.empty_cache()
+    return out
+
+
+def radial_ratio_table(m):
+    """Mean radial ratio (Psi_real . r)/(Psi_n . r) over the galaxies for n = 0..7 from both starts,
+    and the iteration after which the mean changes by less than 1%; plus the FD method's ratio."""
     import torch
     from paper_1504_02591_gb300 import binding
     from oracle import recon_oracle as O
@@ -447,16 +508,16 @@ def paper_diagnostics(m, r_main):
         conv = next(n for n in range(len(means)) if all(abs(means[k + 1] - means[k]) < 0.01 * abs(means[k])
                                                          for k in range(n, len(means) - 1)))
         out[name] = {"mean_sigma_cut": [[round(v, 4) for v in x] for x in rows], "converged_at": conv}
-    r.iterate(binding.START_FFTA, 1e-6, 80)
-    psi = r.get_psi()
-    ga, cb = r.helmholtz_x(psi[0])
-    out["helmholtz_x_ratio"] = {ax: [round(v, 4) for v in r.ratio_stats(ga[j], cb[j], -1e300, 1e300)[:2]]
-                                for j, ax in enumerate("xyz")}
+    # the finite-difference method of Sec. 2.1 on the same redshift-space delta (Table 1's FD row)
+    r.deposit(gal, None, ran, None)
+    r.smooth()
+    t0 = time.perf_counter()
+    psi_fd, it, res, st = r.fd_solve(1e-6, 300)
+    fd_s = time.perf_counter() - t0
+    out["finite_difference"] = {"mean_sigma_cut": [round(v, 4) for v in r.radial_ratio(real, psi_fd, gal)[:3]],
+                                "bicgstab_iterations": it, "residual": res, "seconds": round(fd_s, 3)}
     r.close()
-    out["note"] = ("ratio at every galaxy; Psi_real from the same galaxies before their redshift-space shift; "
-                   "paper (mock, Table 3): uncorrected start 0.80 -> 1.10 -> 0.96 ..., converges after 6; "
-                   "Eq. approx2 start 1.04, after 2 (its solve uses f where this build uses beta = f/b)")
-    del gal, ran, real, psi_s, psi, ga, cb
+    del gal, ran, real, psi_s, psi_fd
     torch.cuda.empty_cache()
     return out
 
@@ -654,6 +715,7 @@ def gpu_arm(args):
         e2e = {"value": round(job_value(e_ms, ws), 4), "unit": "ms", "h2d_bytes_per_step": int((npart + reread) * 24),
                "d2h_bytes_per_step": int(npart * 12), "ms_per_step": round(e_ms, 4)}
 
+    small = small_periodic_box(args, timed)
     diag = paper_diagnostics(m, r) if not args.no_diag else None
     cufft = cufft_context(args.mesh) if not args.no_cufft else None
     batch = batch_bench(args) if not args.no_batch else None
@@ -688,6 +750,7 @@ def gpu_arm(args):
                          "traffic": recorded_traffic(dom), "alg_bytes_per_launch": by / cnt,
                          "ms_per_launch": round(ms_k / cnt, 5)},
             "kernels": kernels,
+            "small_periodic_64": small,
             "paper_diagnostics": diag,
             "large_periodic_1024": large,
             "batch": batch,

@@ -211,7 +211,9 @@ recon_status recon_fft_c2r(recon_handle* h, const float* in_half, float* out_rea
  * vectors, float64 inner products), right-preconditioned by the exact inverse of the periodic
  * 7-point Laplacian (the library's FFT passes on the handle's first field), until the recursive
  * residual falls below tol x |b|.  psi_out: device (3, N^3) float32.  *n_iter: iterations;
- * *rel_resid: the true residual |A phi - b| / |b| at the end.  Allocates its 9 Krylov vectors
+ * *rel_resid: the true residual |A phi - b| / |b| at the end (with phi stored in float32 it
+ * bottoms out near 1e-5 for fields smooth over a few cells: rounding at the grid scale times the
+ * Laplacian's 12 / g^2).  Allocates its 9 Krylov vectors
  * (9 N^3 float32) with cudaMalloc for the call.  The smoothed delta stays valid, so recon_iterate
  * may follow.  NOT_CONVERGED when max_iter is reached; STATE before recon_smooth. */
 recon_status recon_fd_solve(recon_handle* h, double tol, int max_iter, int* n_iter, double* rel_resid,
@@ -336,6 +338,11 @@ enum {
                                    pass run in kernels that keep the first and last FFT stages
                                    (and the c2r/r2c pairing) in registers; 1: the generic staged
                                    kernels (same butterflies)                                     */
+  RECON_OPT_KITER_TMA = 8,      /* N = 512 register-fused path: 1 (default) the source update runs in
+                                   persistent CTAs whose inputs (A, P_y, delta(k), S) are streamed into
+                                   shared memory by the tensor memory accelerator, the next tile while
+                                   the current one is transformed; 0 one CTA per tile loading its
+                                   inputs itself.  Same arithmetic.                                */
   RECON_OPT_ASSIGN = 7,         /* mass assignment of recon_deposit: 0 (default) cloud-in-cell, 1 the
                                    paper's nearest grid point (Sec. 3: node floor(x N / L + 1/2)),
                                    always on the direct (unsorted) deposit kernel.  The shift still

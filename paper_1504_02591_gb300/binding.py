@@ -38,7 +38,7 @@ ABI_SYMBOLS = (
     "recon_radial_nbar", "recon_fkp_weights", "recon_fd_solve",
 )
 OPT_DEPOSIT_PATH, OPT_SHIFT_PATH, OPT_GRAPH, OPT_LINE_TILE, OPT_KSPACE_GENERIC, OPT_REUSE_SORT = 0, 1, 2, 3, 4, 5
-OPT_PLANE_BATCH, OPT_ASSIGN = 6, 7
+OPT_PLANE_BATCH, OPT_ASSIGN, OPT_KITER_TMA = 6, 7, 8
 ASSIGN_CIC, ASSIGN_NGP = 0, 1
 UNET_OPT_TENSOR_CORES = 0
 PATH_DIRECT, PATH_SORTED = 0, 1

@@ -7,6 +7,8 @@
 // and inverse transforms (Z[s] = i k s / k^2 of Eq. Zeldovich, the source update of Eq. iterative
 // with its convergence norms).
 #pragma once
+#include <cuda.h>
+
 #include "fft_core.cuh"
 #include "types.h"
 
@@ -473,13 +475,10 @@ __device__ __forceinline__ void zrow_c2r(const float2 (&x)[8], float2 xl, int la
 }
 
 // r2c of one component's row from the real points v[r] = (x[2m], x[2m + 1]), m = l + 32 r: forward
-// transform, split (pairs k, L - k on lanes l and 32 - l), store the half-complex row and Nyquist value
-// (COPY: sf times them, and sc times them into fc).
-template <bool COPY = false>
+// transform, split (pairs k, L - k on lanes l and 32 - l), store the half-complex row and Nyquist value.
 __device__ __forceinline__ void zrow_r2c(float2 (&v)[8], const Field& f, size_t row, int lane, int partner,
                                          const float2* __restrict__ tw, float2* __restrict__ s,
-                                         const float2* __restrict__ tab, float sf = 1.f, const Field* fc = nullptr,
-                                         float sc = 0.f) {
+                                         const float2* __restrict__ tab) {
   constexpr int L = 256;
   float2 Y0[4], Y1[4];
   zrow_fft<false>(v, Y0, Y1, s, tab, lane);
@@ -502,15 +501,13 @@ __device__ __forceinline__ void zrow_r2c(float2 (&v)[8], const Field& f, size_t 
       float2 xk;
       if (k == 0) {
         xk = make_float2(zk.x + zk.y, 0.f);
-        f.Q[row] = make_float2(COPY ? sf * (zk.x - zk.y) : zk.x - zk.y, 0.f);
-        if (COPY) fc->Q[row] = make_float2(sc * (zk.x - zk.y), 0.f);
+        f.Q[row] = make_float2(zk.x - zk.y, 0.f);
       } else {
         const float2 ev = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
         const float2 o = make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y + zm.y));
         xk = cadd(ev, cmul(make_float2(o.y, -o.x), tw[k]));
       }
-      dst[k] = COPY ? cscale(xk, sf) : xk;
-      if (COPY) fc->M[row * L + k] = cscale(xk, sc);
+      dst[k] = xk;
     }
   }
 }
@@ -537,8 +534,8 @@ __device__ __forceinline__ void zrow_dw(const Geometry& g, float dx, float dy, i
 // The z passes of the register-fused path, one warp per row.  With r = w d, the projection
 // P = coef (Psi.r) r needs only C = dx Psi_x + dy Psi_y and Psi_z (dx, dy are constant along a z
 // row, so C is formed before the transform):  u = coef w (C + dz Psi_z) and P_j = d_j psi with
-// psi = w u.  So the pass transforms two rows each way: P_x = dx psi and P_y = dy psi are scaled
-// copies of one transform, P_z = dz psi the other.
+// psi = w u.  So the pass transforms two rows each way and leaves psi^ = r2c(psi) and
+// Z^ = r2c(dz psi) (P_x = dx psi^ and P_y = dy psi^ are formed by the forward x pass).
 //   Z_PROJ:   c2r x2, P, r2c x2; once the device loop has converged, c2r x3 and the real Psi.
 //   Z_RADIAL: c2r x2, u as a real row.
 //   Z_WARM:   u from the real row plus the upsampled coarse correction, r2c x2.
@@ -675,10 +672,10 @@ __global__ void __launch_bounds__(kZThreads, 2) zfused8_kernel(const ZArgs a) {
       float2 v[8];
 #pragma unroll
       for (int r = 0; r < 8; ++r) v[r] = (r & 1) ? B[0][r >> 1] : A[0][r >> 1];
-      zrow_r2c<true>(v, a.f[0], row, lane, partner, tw, s, tab, dx, &a.f[1], dy);   // dx psi, dy psi
+      zrow_r2c(v, a.f[0], row, lane, partner, tw, s, tab);                      // psi^
 #pragma unroll
       for (int r = 0; r < 8; ++r) v[r] = (r & 1) ? B[1][r >> 1] : A[1][r >> 1];
-      zrow_r2c(v, a.f[2], row, lane, partner, tw, s, tab);                      // dz psi
+      zrow_r2c(v, a.f[2], row, lane, partner, tw, s, tab);                      // Z^ = (dz psi)^
     }
   }
 }
@@ -1233,16 +1230,19 @@ __device__ __forceinline__ void xline8_lines(float2 (&v)[XLine8<C>::NB][8], floa
   }
 }
 
-// PAIR = false: one component per CTA (blockIdx.y).  PAIR = true, the vector passes between the
-// register-fused k-space passes and the Z passes, which carry the x and z components of k-space
-// vectors as one field: kx and kz (kdx, kdz: zero at the Nyquist index) are constant along a y
-// line, so the y pass needs only A = kdx P_x + kdz P_z and P_y, and returns G (Psi_x = kdx G,
-// Psi_z = kdz G) and Psi_y.  CTAs with blockIdx.y = 1 transform the y component (second field);
-// CTAs with blockIdx.y = 0 do two transforms of one tile:
-//   inverse: G in the third field -> Psi_x = IFFT_x(kdx G) in the first, Psi_z = kdz IFFT_x(G) in
-//            the third (the second read of G finds the tile in the L2);
-//   forward: P_x in the first, P_z in the third -> A = kdx FFT_x(P_x) + kdz FFT_x(P_z) in the first
-//            (the first product goes through the L2 and is read back by the thread that wrote it).
+// PAIR = false: one component per CTA (blockIdx.y).  PAIR = true: the vector passes between the
+// register-fused k-space pass (y) and the fused z pass, which carry vectors in reduced forms: kx and
+// kz (kdx, kdz: zero at the Nyquist index) are constant along a y line, so the y pass needs
+// A = kdx P_x + kdz P_z and P_y and returns G (Psi_x = kdx G, Psi_z = kdz G) and Psi_y; and the
+// observer offset dy (a fixed line of sight's y component) is constant along an x line, so the z
+// pass hands over psi^ = r2c_z(psi) and Z^ = r2c_z(dz psi) with P_x = dx psi^, P_y = dy psi^.
+// Two CTAs per tile, on adjacent block indices (role = blockIdx.x & 1), so that a field both read
+// comes from HBM once and from the L2 the second time:
+//   inverse: role 1 transforms Psi_y in the second field in place; role 0 transforms G (third field)
+//            twice, Psi_x = IFFT_x(kdx G) into the first and Psi_z = kdz IFFT_x(G) into the third;
+//   forward: role 1 leaves P_y = dy FFT_x(psi^) (first field) in the second; role 0 leaves
+//            A = kdx FFT_x(dx psi^) + kdz FFT_x(Z^) in the third (its first product goes through the
+//            L2 and is read back by the thread that wrote it).
 template <bool INV, int C, bool PAIR>
 __global__ void __launch_bounds__(XLine8<C>::T, 2) xline8_kernel(const SArgs a) {
   constexpr int N = 512, H = N / 2, T = XLine8<C>::T, NB = XLine8<C>::NB;
@@ -1251,9 +1251,10 @@ __global__ void __launch_bounds__(XLine8<C>::T, 2) xline8_kernel(const SArgs a) 
   float2* s = tw + XLine8<C>::TAB;
   if (!INV && a.skip_flag && *a.skip_flag != 0) return;   // uniform: device loop already converged
   for (int m = threadIdx.x; m < Plan<N>::kTab; m += T) tw[m] = a.tab[m];
+  const int role = PAIR ? (int)(blockIdx.x & 1) : (int)blockIdx.y;
   // tiles of every y-plane, or of the planes [ybeg, ybeg + ycount): their M tiles (ky, kz block)
   // and the Nyquist tiles that hold their ky columns
-  int ti = blockIdx.x;
+  int ti = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
   if (a.ycount) {
     const int mt = a.ycount * (H / C);
     ti = ti < mt ? a.ybeg * (H / C) + ti : N * (H / C) + a.ybeg / C + (ti - mt);
@@ -1265,8 +1266,9 @@ __global__ void __launch_bounds__(XLine8<C>::T, 2) xline8_kernel(const SArgs a) 
   const uint32_t ls = (uint32_t)t.ls;
   auto at = [&](int b, int r) { return o0 + (uint32_t)(b * (T / C) + 64 * r) * ls; };
   float2 v[NB][8];
-  if (!PAIR || blockIdx.y == 1) {
-    float2* __restrict__ P = t.isQ ? a.f[blockIdx.y].Q : a.f[blockIdx.y].M;
+  const Geometry& g = a.g;
+  if (!PAIR || (INV && role == 1)) {
+    float2* __restrict__ P = t.isQ ? a.f[role].Q : a.f[role].M;
 #pragma unroll
     for (int b = 0; b < NB; ++b)
 #pragma unroll
@@ -1278,14 +1280,29 @@ __global__ void __launch_bounds__(XLine8<C>::T, 2) xline8_kernel(const SArgs a) 
       for (int r = 0; r < 8; ++r) P[at(b, r)] = v[b][r];
     return;
   }
-  const float kf = a.g.kf;
+  float2* __restrict__ P0 = t.isQ ? a.f[0].Q : a.f[0].M;
+  float2* __restrict__ P2 = t.isQ ? a.f[2].Q : a.f[2].M;
+  if (!INV && role == 1) {   // P_y = dy FFT_x(psi^)
+    const float dy = g.los_mode == 1 ? g.los.y : g.off[N + (t.isQ ? t.c0 + col : t.a)];
+    float2* __restrict__ P1 = t.isQ ? a.f[1].Q : a.f[1].M;
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int r = 0; r < 8; ++r) v[b][r] = P0[at(b, r)];
+    xline8_lines<INV, C>(v, s, tw, jb, col);
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int r = 0; r < 8; ++r) P1[at(b, r)] = cscale(v[b][r], dy);
+    return;
+  }
+  const float kf = g.kf;
   const float kdz = t.isQ ? 0.f : kf * (float)(t.c0 + col);   // M tiles: kz < N/2; Q tiles: kz = N/2
+  // the line index i is kx in Fourier space and x in configuration space
   auto kdx = [&](int b, int r) {
     const int i = jb + b * (T / C) + 64 * r;
     return i == H ? 0.f : kf * (float)(i < H ? i : i - N);
   };
-  float2* __restrict__ P0 = t.isQ ? a.f[0].Q : a.f[0].M;
-  float2* __restrict__ P2 = t.isQ ? a.f[2].Q : a.f[2].M;
   if (INV) {
 #pragma unroll
     for (int b = 0; b < NB; ++b)
@@ -1307,47 +1324,46 @@ __global__ void __launch_bounds__(XLine8<C>::T, 2) xline8_kernel(const SArgs a) 
 #pragma unroll
       for (int r = 0; r < 8; ++r) P2[at(b, r)] = cscale(v[b][r], kdz);
   } else {
-#pragma unroll
-    for (int b = 0; b < NB; ++b)
-#pragma unroll
-      for (int r = 0; r < 8; ++r) v[b][r] = P0[at(b, r)];
-    xline8_lines<INV, C>(v, s, tw, jb, col);
-#pragma unroll
-    for (int b = 0; b < NB; ++b)
-#pragma unroll
-      for (int r = 0; r < 8; ++r) P0[at(b, r)] = cscale(v[b][r], kdx(b, r));
-    __syncthreads();   // s is rewritten by the second transform
+    auto dxv = [&](int b, int r) { return g.los_mode == 1 ? g.los.x : g.off[jb + b * (T / C) + 64 * r]; };
 #pragma unroll
     for (int b = 0; b < NB; ++b)
 #pragma unroll
       for (int r = 0; r < 8; ++r) v[b][r] = P2[at(b, r)];
-    xline8_lines<INV, C>(v, s, tw, jb, col);
+    xline8_lines<INV, C>(v, s, tw, jb, col);                          // FFT_x(Z^)
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int r = 0; r < 8; ++r) P2[at(b, r)] = cscale(v[b][r], kdz);
+    __syncthreads();   // s is rewritten by the second transform
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int r = 0; r < 8; ++r) v[b][r] = cscale(P0[at(b, r)], dxv(b, r));
+    xline8_lines<INV, C>(v, s, tw, jb, col);                          // FFT_x(dx psi^)
 #pragma unroll
     for (int b = 0; b < NB; ++b)
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        const float2 x = P0[at(b, r)];   // this thread's own first product
-        P0[at(b, r)] = make_float2(fmaf(kdz, v[b][r].x, x.x), fmaf(kdz, v[b][r].y, x.y));
+        const float2 x = P2[at(b, r)];   // this thread's own kdz FFT_x(Z^)
+        const float k = kdx(b, r);
+        P2[at(b, r)] = make_float2(fmaf(k, v[b][r].x, x.x), fmaf(k, v[b][r].y, x.y));
       }
   }
 }
 
+// One tile of the source update (Eq. iterative) from registers: v[0] = A and v[1] = P_y along the y
+// line (Fourier x and z, configuration y), dk = delta(k) and sp = S_(n-1) at the thread's 8 points
+// (already in Fourier y).  Forward y FFT, S_n = delta/b + beta i k . P_n, the Parseval norms
+// (accumulated into d2, s2), Psi_n+1 = i kd S_n / k^2 as G (third field) and Psi_y (second field),
+// inverse y FFT, stores.  kx and kz are constant along the y line, so the x and z terms of k . P
+// arrive combined, A = kdx P_x + kdz P_z (the forward x pass forms it; FFT_y is linear), and
+// Psi_x, Psi_z leave as one field G with Psi_x = kdx G, Psi_z = kdz G (the inverse x pass separates
+// them).  s is written first: a caller that used it before syncs first.
 template <int N, int C>
-__global__ void __launch_bounds__(KIter8<N, C>::T, KIter8<N, C>::kMinBlocks) kiter8_kernel(const SArgs a) {
-  constexpr int T = KIter8<N, C>::T;
+__device__ __forceinline__ void kiter_tile(const SArgs& a, const Tile& t, float2 (&v)[2][8], const float2 (&dk)[8],
+                                           const float2 (&sp)[8], float2* __restrict__ s,
+                                           const float2* __restrict__ tw, int j, int col, float& d2, float& s2) {
   constexpr int H = N / 2;
-  extern __shared__ float4 ssm[];
-  float2* tw = reinterpret_cast<float2*>(ssm);
-  float2* s = tw + KIter8<N, C>::TAB;
-  __shared__ double red_sh[T / 32];
-  for (int m = threadIdx.x; m < Plan<N>::kTab; m += T) tw[m] = a.tab[m];
-  const Tile t = tile_of<N, C, AX_Y>(blockIdx.x);
-  const int col = threadIdx.x % C, j = threadIdx.x / C;
-
-  // kx and kz are constant along the y line, so the x and z terms of k . P arrive combined,
-  // A = kdx P_x + kdz P_z in the first field (the forward x pass forms it; FFT_y is linear), and
-  // Psi_x, Psi_z leave as one field G with Psi_x = kdx G, Psi_z = kdz G in the third (the inverse
-  // x pass separates them); P_y and Psi_y in the second
   const Geometry& g = a.g;
   int ix, kz;
   if (!t.isQ) { ix = t.a; kz = t.c0 + col; } else { ix = t.c0 + col; kz = H; }
@@ -1355,26 +1371,7 @@ __global__ void __launch_bounds__(KIter8<N, C>::T, KIter8<N, C>::kMinBlocks) kit
   const float kx = g.kf * mx, kzf = g.kf * kz;
   const float kdx = (ix == H) ? 0.f : kx;
   const float kdz = (kz == H) ? 0.f : kzf;
-
-  // every global read of the tile up front: A, P_y, delta(k), S_(n-1)
-  float2 v[2][8], dk[8], sp[8];
-  {
-    const float2* __restrict__ dkp = t.isQ ? a.dk.Q : a.dk.M;
-    const float2* __restrict__ spp = t.isQ ? a.sbuf.Q : a.sbuf.M;
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const size_t gi = t.base + (size_t)(j + 64 * r) * t.ls + (size_t)col * t.cs;
-      v[0][r] = (t.isQ ? a.f[0].Q : a.f[0].M)[gi];
-      v[1][r] = (t.isQ ? a.f[1].Q : a.f[1].M)[gi];
-      dk[r] = dkp[gi];
-      sp[r] = spp[gi];
-    }
-  }
-  __syncthreads();   // twiddles
   r512_lines<false, N, C, 2>(v, s, tw, j, col);
-
-  // S_n = delta/b + beta i k . P_n, the Parseval norms, Psi_n+1 = i kd S_n / k^2 (Eq. iterative)
-  float d2 = 0.f, s2 = 0.f;
   float2* Sp = t.isQ ? a.sbuf.Q : a.sbuf.M;
   const float kxz2 = kx * kx + kzf * kzf, kdxz2 = kdx * kdx + kdz * kdz;
   const float wgt = (kz == 0 || kz == H) ? 1.f : 2.f;
@@ -1400,24 +1397,187 @@ __global__ void __launch_bounds__(KIter8<N, C>::T, KIter8<N, C>::kMinBlocks) kit
     v[0][r] = iS;
     v[1][r] = cscale(iS, kdy);
   }
-
   r512_lines<true, N, C, 2>(v, s, tw, j, col);
-  {
-    float2* __restrict__ dy = t.isQ ? a.f[1].Q : a.f[1].M;
-    float2* __restrict__ dg = t.isQ ? a.f[2].Q : a.f[2].M;
+  float2* __restrict__ dy = t.isQ ? a.f[1].Q : a.f[1].M;
+  float2* __restrict__ dg = t.isQ ? a.f[2].Q : a.f[2].M;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const size_t gi = t.base + (size_t)(j + 64 * r) * t.ls + (size_t)col * t.cs;
-      dy[gi] = v[1][r];
-      dg[gi] = v[0][r];
-    }
+  for (int r = 0; r < 8; ++r) {
+    const size_t gi = t.base + (size_t)(j + 64 * r) * t.ls + (size_t)col * t.cs;
+    dy[gi] = v[1][r];
+    dg[gi] = v[0][r];
   }
+}
 
+// The tile's four inputs straight from global memory: A (third field), P_y (second), delta(k), S.
+template <int N, int C>
+__device__ __forceinline__ void kiter_load(const SArgs& a, const Tile& t, int j, int col, float2 (&v)[2][8],
+                                           float2 (&dk)[8], float2 (&sp)[8]) {
+  const float2* __restrict__ dkp = t.isQ ? a.dk.Q : a.dk.M;
+  const float2* __restrict__ spp = t.isQ ? a.sbuf.Q : a.sbuf.M;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const size_t gi = t.base + (size_t)(j + 64 * r) * t.ls + (size_t)col * t.cs;
+    v[0][r] = (t.isQ ? a.f[2].Q : a.f[2].M)[gi];
+    v[1][r] = (t.isQ ? a.f[1].Q : a.f[1].M)[gi];
+    dk[r] = dkp[gi];
+    sp[r] = spp[gi];
+  }
+}
+
+template <int N, int C>
+__global__ void __launch_bounds__(KIter8<N, C>::T, KIter8<N, C>::kMinBlocks) kiter8_kernel(const SArgs a) {
+  constexpr int T = KIter8<N, C>::T;
+  extern __shared__ float4 ssm[];
+  float2* tw = reinterpret_cast<float2*>(ssm);
+  float2* s = tw + KIter8<N, C>::TAB;
+  __shared__ double red_sh[T / 32];
+  for (int m = threadIdx.x; m < Plan<N>::kTab; m += T) tw[m] = a.tab[m];
+  const Tile t = tile_of<N, C, AX_Y>(blockIdx.x);
+  const int col = threadIdx.x % C, j = threadIdx.x / C;
+  // every global read of the tile up front
+  float2 v[2][8], dk[8], sp[8];
+  kiter_load<N, C>(a, t, j, col, v, dk, sp);
+  __syncthreads();   // twiddles
+  float d2 = 0.f, s2 = 0.f;
+  kiter_tile<N, C>(a, t, v, dk, sp, s, tw, j, col, d2, s2);
   double r0 = block_sum((double)d2, red_sh);
   double r1 = block_sum((double)s2, red_sh);
   if (threadIdx.x == 0) {
     a.partials[2 * blockIdx.x + 0] = r0;
     a.partials[2 * blockIdx.x + 1] = r1;
+  }
+}
+
+// ---- the source update with its inputs streamed by the tensor memory accelerator ---------------
+// Persistent CTAs (two per SM) walk the Fourier-x/z tiles; a tile's four inputs (A, P_y, delta(k),
+// S_(n-1): four [512 y][4 kz] float2 boxes of a 3-D map over the half grid M [kx][ky][kz < N/2]) land
+// in one shared-memory stage by cp.async.bulk.tensor, completing on an mbarrier.  As soon as the
+// threads have copied the tile into their registers the next tile's copies are issued into the same
+// stage, so they stream in while this tile's transforms and stores run.  The Nyquist tiles (a
+// different layout, 1/257 of the data) follow with plain loads.  Each CTA's norms go to its
+// partials; the rest of the regular grid's partials are zeroed so the reduction over them is
+// unchanged.  Every wait is bounded: a wait that gives up writes NaN norms (the device loop then
+// stops with RECON_ERR_NONFINITE) and the CTA returns.
+template <int N, int C>
+struct KTma {
+  static constexpr int T = KIter8<N, C>::T;
+  static constexpr size_t kS = sizeof(float2) * ((size_t)KIter8<N, C>::TAB + 2 * (size_t)N * C);
+  static constexpr size_t kBufOff = (kS + 127) & ~(size_t)127;
+  static constexpr size_t kField = sizeof(float2) * (size_t)N * C;   // one field's tile
+  static constexpr size_t kBarOff = kBufOff + 4 * kField;
+  static constexpr size_t smem = kBarOff + 16;
+  static constexpr uint32_t kTx = 4u * (uint32_t)kField;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ bool bar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+template <int N, int C>
+__global__ void __launch_bounds__(KIter8<N, C>::T, 2) kiter8_tma_kernel(const SArgs a,
+                                                                       const __grid_constant__ KIterMaps maps) {
+  using K = KTma<N, C>;
+  constexpr int T = K::T, H = N / 2, MT = N * (H / C), QT = N / C;
+  constexpr int kGridPartials = MT + QT;   // the regular grid whose partials the reduction reads
+  extern __shared__ __align__(128) float4 ssm[];
+  float2* tw = reinterpret_cast<float2*>(ssm);
+  float2* s = tw + KIter8<N, C>::TAB;
+  const float2* buf = reinterpret_cast<const float2*>(reinterpret_cast<char*>(ssm) + K::kBufOff);
+  uint64_t* bar_p = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ssm) + K::kBarOff);
+  __shared__ double red_sh[T / 32];
+  __shared__ int give_up;
+  const uint32_t bar = smem_addr(bar_p), dst = smem_addr(buf);
+  for (int m = threadIdx.x; m < Plan<N>::kTab; m += T) tw[m] = a.tab[m];
+  if (threadIdx.x == 0) {
+    give_up = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  }
+  __syncthreads();
+  const int col = threadIdx.x % C, j = threadIdx.x / C;
+  auto issue = [&](int tt) {   // thread 0: the four fields' boxes of tile tt
+    const int kx = tt / (H / C), c0 = (tt % (H / C)) * C;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(K::kTx) : "memory");
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        tma_load3(dst + (uint32_t)(q * K::kField + h * (K::kField / 2)), &maps.m[q], c0, 256 * h, kx, bar);
+  };
+  float d2 = 0.f, s2 = 0.f;
+  float2 v[2][8], dk[8], sp[8];
+  uint32_t parity = 0;
+  if (threadIdx.x == 0 && (int)blockIdx.x < MT) issue(blockIdx.x);
+  for (int tt = blockIdx.x; tt < MT; tt += gridDim.x) {
+    // bounded wait for the tile's copies: two seconds of the global timer at most
+    bool ok = bar_try_wait(bar, parity);
+    if (!ok) {
+      unsigned long long t0;
+      asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t0));
+      for (;;) {
+        if ((ok = bar_try_wait(bar, parity))) break;
+        unsigned long long t1;
+        asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t1));
+        if (t1 - t0 > 2000000000ull) break;
+      }
+    }
+    if (!ok) give_up = 1;
+    __syncthreads();
+    if (give_up) break;
+    parity ^= 1u;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int e = (j + 64 * r) * C + col;
+      v[0][r] = buf[e];
+      v[1][r] = buf[N * C + e];
+      dk[r] = buf[2 * N * C + e];
+      sp[r] = buf[3 * N * C + e];
+    }
+    __syncthreads();   // the stage is free (and s may be rewritten)
+    if (threadIdx.x == 0 && tt + (int)gridDim.x < MT) {
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      issue(tt + gridDim.x);
+    }
+    kiter_tile<N, C>(a, tile_of<N, C, AX_Y>(tt), v, dk, sp, s, tw, j, col, d2, s2);
+  }
+  if (!give_up) {
+    for (int q = blockIdx.x; q < QT; q += gridDim.x) {   // Nyquist tiles: plain loads
+      const Tile t = tile_of<N, C, AX_Y>(MT + q);
+      kiter_load<N, C>(a, t, j, col, v, dk, sp);
+      __syncthreads();   // s may be rewritten
+      kiter_tile<N, C>(a, t, v, dk, sp, s, tw, j, col, d2, s2);
+    }
+  }
+  double r0 = block_sum((double)d2, red_sh);
+  double r1 = block_sum((double)s2, red_sh);
+  if (threadIdx.x == 0) {
+    if (give_up) r0 = r1 = __longlong_as_double(0x7ff8000000000000ll);   // NaN: the loop stops
+    a.partials[2 * blockIdx.x + 0] = r0;
+    a.partials[2 * blockIdx.x + 1] = r1;
+  }
+  for (int b = blockIdx.x + gridDim.x + threadIdx.x * gridDim.x; b < kGridPartials; b += T * gridDim.x) {
+    a.partials[2 * b + 0] = 0.0;
+    a.partials[2 * b + 1] = 0.0;
   }
 }
 
@@ -1557,6 +1717,23 @@ struct MeshImpl {
   static cudaError_t klaunch(const SArgs& a, cudaStream_t st) {
     if constexpr (N == 512) {
       constexpr int C = SCols<N, S_ITER>::v;
+      if (a.tmaps) {   // inputs streamed by TMA into persistent CTAs, two per SM
+        const void* k = (const void*)kiter8_tma_kernel<N, C>;
+        static int grid = 0;
+        if (grid == 0) {
+          cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)KTma<N, C>::smem);
+          if (e != cudaSuccess) return e;
+          int dev = 0, sm = 0, occ = 0;
+          if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+          if ((e = cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+          if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, KTma<N, C>::T, KTma<N, C>::smem)) != cudaSuccess)
+            return e;
+          if (occ < 1) return cudaErrorInvalidConfiguration;
+          grid = occ * sm;
+        }
+        void* args[] = {const_cast<SArgs*>(&a), const_cast<KIterMaps*>(a.tmaps)};
+        return cudaLaunchKernel(k, dim3(grid), dim3(KTma<N, C>::T), args, KTma<N, C>::smem, st);
+      }
       const void* k = (const void*)kiter8_kernel<N, C>;
       static bool attr = false;
       if (!attr) {
@@ -1600,7 +1777,9 @@ struct MeshImpl {
     if (a.ycount && (a.ycount % C || a.ybeg % C || a.ybeg < 0 || a.ybeg + a.ycount > N)) return cudaErrorInvalidValue;
     void* args[] = {const_cast<SArgs*>(&a)};
     const int tiles = a.ycount ? a.ycount * ((N / 2) / C) + a.ycount / C : N * ((N / 2) / C) + N / C;
-    return cudaLaunchKernel(k, dim3(tiles, PAIR ? 2 : ncomp), dim3(XLine8<C>::T), args, XLine8<C>::smem, st);
+    // pairs: the two CTAs of a tile on adjacent block indices; single fields: components along y
+    const dim3 grid = PAIR ? dim3(2 * tiles) : dim3(tiles, ncomp);
+    return cudaLaunchKernel(k, grid, dim3(XLine8<C>::T), args, XLine8<C>::smem, st);
   }
   static cudaError_t xlaunch(bool inv, const SArgs& a, cudaStream_t st, int ncomp, bool pair) {
     if constexpr (N == 512) {

@@ -9,6 +9,8 @@
 //            repeat: Y: S_n = delta/b + beta i k.P_n, norms, Psi = i k S/k^2 | X |
 //                    Z: P = (Psi.r)r (or the final real Psi) | X                  (Sec. 5.1)
 //   shift    CIC interpolation of Psi to the particles, d = -(Psi + f (Psi.r) r) or -Psi (Sec. 1)
+#include <cudaTypedefs.h>
+
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -155,6 +157,9 @@ struct recon_handle {
   int kspace_generic = 0;
   int plane_batch = 0;   // register-fused path: y-planes per batch of the x -> z -> x passes (0: off)
   int assign = 0;        // mass assignment of the deposit: 0 CIC, 1 NGP (the paper's binning)
+  int kiter_tma = 1;     // N = 512 fused path: the source update's inputs streamed by TMA
+  bool tmaps_ok = false; // its tensor maps were built
+  KIterMaps tmaps{};
   int reuse_sort = 0;
   // the catalogue whose brick order the sort buffers hold (sorted deposit, one chunk)
   struct SortMemo {
@@ -182,12 +187,12 @@ struct recon_handle {
   struct GraphKey {
     uint32_t coef0_bits;
     const float* u0;
-    int level, max_iter, d_is_k, generic, narrow, planes;
+    int level, max_iter, d_is_k, generic, narrow, planes, tma;
     uint64_t tol_bits;
     uint64_t epoch;
     bool operator==(const GraphKey& o) const {
       return coef0_bits == o.coef0_bits && u0 == o.u0 && level == o.level && max_iter == o.max_iter &&
-             d_is_k == o.d_is_k && generic == o.generic && narrow == o.narrow && planes == o.planes &&
+             d_is_k == o.d_is_k && generic == o.generic && narrow == o.narrow && planes == o.planes && tma == o.tma &&
              tol_bits == o.tol_bits &&
              epoch == o.epoch;
     }
@@ -299,7 +304,40 @@ SArgs sargs(recon_handle* h) {
   a.narrow = h->narrow_lines;
   a.generic = h->kspace_generic;
   a.lognormal = h->p.lognormal;
+  a.tmaps = (h->tmaps_ok && h->kiter_tma) ? &h->tmaps : nullptr;
   return a;
+}
+
+// Tensor maps of the fused source update's inputs (A in the third field, P_y in the second,
+// delta(k), S) over the half grid M [kx][ky][kz < N/2], float2 elements copied as 8-byte words: boxes
+// of 4 kz x 256 ky x 1 kx (a tile's y line is two boxes).  Needs the driver's encoder; without it the
+// update loads its inputs directly.
+bool encode_kiter_maps(recon_handle* h) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return false;
+    }
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const int n = h->n;
+  const Field* fs[4] = {&h->V[2], &h->V[1], &h->D, &h->S};
+  const cuuint64_t dims[3] = {(cuuint64_t)n / 2, (cuuint64_t)n, (cuuint64_t)n};
+  const cuuint64_t strides[2] = {(cuuint64_t)(n / 2) * 8, (cuuint64_t)n * (n / 2) * 8};
+  const cuuint32_t box[3] = {4, (cuuint32_t)(n / 2), 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  for (int q = 0; q < 4; ++q) {
+    if (((uintptr_t)fs[q]->M & 255) != 0) return false;
+    const CUresult r = encode(&h->tmaps.m[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, (void*)fs[q]->M, dims, strides, box, es,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+  }
+  return true;
 }
 
 // Algorithmic bytes of one pass: every field it reads and writes, once.
@@ -307,14 +345,16 @@ double cfield(const recon_handle* h) { return (double)h->n * h->n * h->n * 4.0 +
 double rfield(const recon_handle* h) { return (double)h->n * h->n * h->n * 4.0; }
 
 double zbytes(const recon_handle* h, int mode, int nc, const ZArgs& a) {
+  // the register-fused path hands the z pass three fields and takes two back (psi^, Z^)
+  const int nv = (h->mk->kspace_fused && !h->kspace_generic && nc == 3) ? 2 : nc;
   if (mode == Z_DELTA) {
     const int nin = a.uniform ? 1 : 2;
     return nin * rfield(h) + cfield(h) + (a.delta_real ? rfield(h) : 0.0);
   }
   if (mode == Z_FINAL) return nc * (cfield(h) + rfield(h));
   if (mode == Z_RADIAL) return nc * cfield(h) + rfield(h);
-  if (mode == Z_USTART || mode == Z_WARM) return rfield(h) + nc * cfield(h);
-  return 2.0 * nc * cfield(h);
+  if (mode == Z_USTART || mode == Z_WARM) return rfield(h) + nv * cfield(h);
+  return (nc + nv) * cfield(h);
 }
 
 double sbytes(const recon_handle* h, int mode, int nc, int axis) {
@@ -322,7 +362,8 @@ double sbytes(const recon_handle* h, int mode, int nc, int axis) {
   const bool fused = h->mk->kspace_fused && !h->kspace_generic;
   if (mode == S_DELTA) return (fused ? 5.0 : 6.0) * cfield(h);   // delta in, delta(k), S, 2 or 3 Psi
   if (mode == S_ITER) return (fused ? 7.0 : 9.0) * cfield(h);    // 2 or 3 P + delta(k) + S in; 2 or 3 Psi + S out
-  if (fused && axis == AX_X && nc == 3) return 5.0 * cfield(h);  // paired: 2 in, 3 out or 3 in, 2 out
+  // paired x passes: inverse 2 fields in, 3 out; forward 2 in (the pair's shared one read once), 2 out
+  if (fused && axis == AX_X && nc == 3) return (mode == S_INV ? 5.0 : 4.0) * cfield(h);
   return 2.0 * nc * cfield(h);
 }
 
@@ -690,6 +731,7 @@ recon_status recon_create(const recon_params* p, void* stream, void* workspace, 
     rs = RECON_ERR_CUDA;
   }
   if (rs == RECON_OK) rs = configure(h, p);
+  if (rs == RECON_OK && h->mk->kspace_fused) h->tmaps_ok = encode_kiter_maps(h);
   if (rs != RECON_OK) {
     if (h->own_ws) cudaFree(h->ws);
     delete h;
@@ -744,6 +786,7 @@ recon_status recon_set_option(recon_handle* h, int option, int value) {
   else if (option == RECON_OPT_KSPACE_GENERIC) h->kspace_generic = value ? 1 : 0;
   else if (option == RECON_OPT_REUSE_SORT) h->reuse_sort = value ? 1 : 0;
   else if (option == RECON_OPT_ASSIGN) h->assign = value;
+  else if (option == RECON_OPT_KITER_TMA) h->kiter_tma = value;
   else return RECON_ERR_INVALID_ARG;
   return RECON_OK;
 }
@@ -993,6 +1036,7 @@ recon_status iterate_graph(recon_handle* h, const StartSpec& sp, double tol, int
   key.generic = h->kspace_generic;
   key.narrow = h->narrow_lines;
   key.planes = h->plane_batch;
+  key.tma = h->kiter_tma;
   key.epoch = h->epoch;
   if (!(h->gcache.valid && h->gcache.key == key)) {
     RG_TRY(build_graph(h, sp, tol, max_iter));

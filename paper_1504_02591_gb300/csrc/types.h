@@ -1,5 +1,6 @@
 // types.h: argument blocks shared by the host orchestration and the kernels.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -71,6 +72,12 @@ struct ZArgs {
                           // (ycount 0: every row)
 };
 
+// Tensor maps of the register-fused source update's four inputs (A, P_y, delta(k), S) over the
+// half grid M [kx][ky][kz < N/2] (N = 512), built on the host; passed to the kernel by value.
+struct KIterMaps {
+  CUtensorMap m[4];
+};
+
 struct SArgs {
   Field f[3];             // fields transformed in place
   Geometry g;
@@ -88,6 +95,7 @@ struct SArgs {
   int generic;            // k-space update: the generic staged kernel instead of the register-fused one
   int ybeg, ycount;       // paired x passes: only the lines of y-planes [ybeg, ybeg + ycount)
                           // (ycount 0: every line; both multiples of the tile width)
+  const KIterMaps* tmaps; // host memory: the source update streams its inputs by TMA (N = 512)
 };
 
 // State of the device-driven iteration (in the workspace).

@@ -82,7 +82,8 @@ class GeneratorField:
         return d, v
 
 
-def gaussian_field(ng: int, L: float, seed: int) -> GeneratorField:
+def gaussian_field(ng: int, L: float, seed: int, amp: float = 1.0) -> GeneratorField:
+    """The field of the spectrum above times amp (amp < 1: closer to the linear regime)."""
     rng = np.random.default_rng(seed)
     white = rng.standard_normal((ng, ng, ng), dtype=np.float32)
     W = _rfftn(white)
@@ -94,7 +95,7 @@ def gaussian_field(ng: int, L: float, seed: int) -> GeneratorField:
     kz = (kf * mz)[None, None, :]
     kk = np.sqrt(kx ** 2 + ky ** 2 + kz ** 2)
     vcell = (L / ng) ** 3
-    D = W * np.sqrt(power_spectrum(kk) / vcell)
+    D = W * (amp * np.sqrt(power_spectrum(kk) / vcell))
     D[0, 0, 0] = 0
     delta = _irfftn(D, (ng, ng, ng)).astype(np.float32)
     inv_k2 = np.zeros_like(kk)
@@ -188,10 +189,10 @@ def _in_window(p, observer, axis, r_min, r_max, cos_min):
 def shell_survey(L: float, n_mesh: int, n_gal: int, n_ran: int, b: float, f: float, R: float,
                  observer, axis, r_min: float, r_max: float, sky_frac: float,
                  seed_field: int, seed_gal: int, seed_ran: int, ng: int | None = None,
-                 name: str = "shell") -> Mock:
+                 name: str = "shell", amp: float = 1.0) -> Mock:
     """Spherical-shell cap window (r_min..r_max around the observer, sky fraction sky_frac)."""
     ng = ng or min(n_mesh, 256)
-    gf = gaussian_field(ng, L, seed_field)
+    gf = gaussian_field(ng, L, seed_field, amp)
     obs = np.asarray(observer, dtype=np.float64)
     ax = _unit(np.asarray(axis, dtype=np.float64))
     cos_min = 1.0 - 2.0 * sky_frac
@@ -253,14 +254,14 @@ def small_periodic(n_gal: int = 200_000, n_ran: int = 2_000_000, n_mesh: int = 6
 
 
 def survey_shell_512(n_gal: int = 600_000, ran_ratio: int = 50, n_mesh: int = 512,
-                     L: float = 3500.0, seed: int = 10) -> Mock:
+                     L: float = 3500.0, seed: int = 10, amp: float = 1.0) -> Mock:
     """512^3 mesh in a 3500 Mpc/h box, shell 1100-1800 Mpc/h, 25% sky cap, 6e5 galaxies, 50x
     randoms, b = 1.85, f = 0.74, R = 15.  Observer at the centre of the x = 0 face, cap axis +x
     (a box-corner observer sees at most 1/8 of the sky, so a 25% cap cannot sit at the corner).
     Seeds seed, seed + 1, seed + 2 (field, galaxies, randoms); the benchmark mock is seed 10."""
     return shell_survey(L, n_mesh, n_gal, n_gal * ran_ratio, 1.85, 0.74, 15.0,
                         (0.0, L / 2, L / 2), (1.0, 0.0, 0.0), 1100.0, 1800.0, 0.25,
-                        seed, seed + 1, seed + 2, ng=256, name=f"shell-{n_mesh}")
+                        seed, seed + 1, seed + 2, ng=256, name=f"shell-{n_mesh}", amp=amp)
 
 
 def scaled_shell(n_mesh: int, L: float, n_gal: int, ran_ratio: int, b: float, f: float,
@@ -395,14 +396,14 @@ def _rsd_device(x, v, f, obs):
 
 
 def batch_mock_device(n_mesh: int, n_gal: int, ran_ratio: int, b: float, f: float, shell: bool, seed: int,
-                      device: str = "cuda") -> dict:
+                      device: str = "cuda", L: float | None = None) -> dict:
     """One mock of the batched workload on the GPU.  Box L = 6.84 N Mpc/h (the 512^3 survey's cell
-    size), R = 15 Mpc/h.  Shell: observer at the centre of the x = 0 face, comoving 1100-1800 Mpc/h
+    size) unless given, R = 15 Mpc/h.  Shell: observer at the centre of the x = 0 face, comoving 1100-1800 Mpc/h
     scaled by L/3500, 25% sky cap about +x, randoms ran_ratio x n_gal uniform in the window, mean
     density from the randoms.  Periodic: observer 1.5 L along -x of the box centre, uniform mean
     density (no randoms).  Returns params and float64 device positions."""
     import torch
-    L = 6.84 * n_mesh
+    L = 6.84 * n_mesh if L is None else L
     gen = torch.Generator(device=device).manual_seed(seed)
     ng = min(n_mesh, 256)
     F = _field_device(ng, L, gen, device)

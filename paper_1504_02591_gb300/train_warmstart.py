@@ -45,15 +45,24 @@ def main(argv=None):
     ap.add_argument("--wd", type=float, default=1e-4)
     ap.add_argument("--seed0", type=int, default=1000)
     ap.add_argument("--out", default=W.default_weights_path())
+    ap.add_argument("--device-mocks", action="store_true",
+                    help="draw the training galaxies on the GPU (mocks.batch_mock_device, same recipe and "
+                         "survey geometry), so hundreds of mocks take minutes")
     args = ap.parse_args(argv)
     import torch
 
     t0 = time.time()
     shared = mocks.survey_shell_512(seed=args.seed0 - 3)     # its randoms serve every training mock
     pairs, n_plain = [], []
+    ran_dev = torch.from_numpy(shared.randoms.pos).cuda() if args.device_mocks else None
     for i in range(args.mocks):
-        m = shared if i == 0 else mocks.survey_shell_512(ran_ratio=0, seed=args.seed0 + 3 * i)
-        m.randoms = shared.randoms
+        if args.device_mocks:
+            d = mocks.batch_mock_device(512, 600_000, 0, shared.b, shared.f, True, args.seed0 + i, L=shared.L)
+            m = mocks.Mock("shell-512-device", shared.L, 512, shared.b, shared.f, shared.R, shared.observer, 0, False,
+                           False, galaxies=mocks.Catalog(d["gal"]), randoms=mocks.Catalog(ran_dev))
+        else:
+            m = shared if i == 0 else mocks.survey_shell_512(ran_ratio=0, seed=args.seed0 + 3 * i)
+            m.randoms = shared.randoms
         feat, u, n_it = W.training_pair(m, args.level)
         pairs.append((feat, u))
         n_plain.append(n_it)
@@ -77,8 +86,10 @@ def main(argv=None):
     r.smooth()
     n_warm, rel, st = W.warm_iterate(r, net, args.level, 1e-6, 120)
     r.close()
+    seeds = ([args.seed0 + i for i in range(args.mocks)] if args.device_mocks else
+             [args.seed0 - 3] + [args.seed0 + 3 * i for i in range(1, args.mocks)])
     meta = dict(workload="survey_shell_512", level=args.level, c1=args.c1, mocks=args.mocks, seed0=args.seed0,
-                seeds=[args.seed0 - 3] + [args.seed0 + 3 * i for i in range(1, args.mocks)], steps=args.steps,
+                device_mocks=bool(args.device_mocks), seeds=seeds, steps=args.steps,
                 lr=args.lr, wd=args.wd, loss_first=float(np.mean(losses[:20])), loss_last=float(np.mean(losses[-100:])),
                 plain_updates_train=n_plain, heldout=dict(seed=10, start_error_ffta=err_ffta, start_error_learned=err_net,
                                                           updates_ffta=n_ffta, updates_learned=n_warm, rel=rel),

@@ -34,5 +34,7 @@ def test_fd_solve_vs_oracle(lib, los):
     e = rel_l2(psi.cpu().numpy(), want)
     print(f"FD {los}: GPU {it} iterations, true residual {res:.1e}; oracle {it_o} GMRES iterations "
           f"(residual {res_o:.1e}); Psi rel L2 {e:.2e}")
-    assert st == B.OK and res < 1e-6
+    # the true residual of a float32 phi bottoms out near 1e-5: grid-scale rounding of phi, times the
+    # Laplacian's 12 / g^2, against |A phi| of a field smooth over a few cells
+    assert st == B.OK and res < 1e-4
     assert e <= 1e-5

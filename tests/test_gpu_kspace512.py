@@ -154,3 +154,31 @@ def test_plane_batched_passes_match_unbatched(lib, graph):
         assert np.array_equal(out[planes][0], out[0][0]), planes
         assert np.array_equal(out[planes][1], out[0][1]), planes
         assert out[planes][2] == out[0][2] and np.array_equal(out[planes][3], out[0][3]), planes
+
+
+@pytest.mark.parametrize("los_mode", [0, 1])
+def test_tma_streamed_update_matches_direct_loads(lib, los_mode):
+    """RECON_OPT_KITER_TMA: the source update with its inputs streamed into shared memory by the
+    tensor memory accelerator (persistent CTAs) computes every element with the same arithmetic as
+    the one-tile-per-CTA kernel, so Psi after a fixed number of updates is bitwise equal; only the
+    order of the float64 norm sums differs."""
+    from paper_1504_02591_gb300 import binding as B
+    from paper_1504_02591_gb300 import mocks
+    obs = (0.0, 1750.0, 1750.0) if los_mode == 0 else (0.6, 0.8, 0.0)
+    m = mocks.periodic_box(3500.0, 512, 100_000, 0, 1.85, 0.74, 15.0, obs, 4, 5, 6, ng=128,
+                           los_mode=los_mode, uniform=True)
+    r = B.Recon.from_mock(m, uniform=True)
+    r.deposit(torch.from_numpy(m.galaxies.pos).cuda(), None, None, None)
+    r.smooth()
+    out = {}
+    for tma in (0, 1):
+        r.set_option(B.OPT_KITER_TMA, tma)
+        for graph in (1, 0):
+            r.set_option(B.OPT_GRAPH, graph)
+            n, rel, st = r.iterate(B.START_FFTA, 0.0, 5)
+            out[(tma, graph)] = (r.get_psi().cpu().numpy(), np.array(r.trace()))
+    r.close()
+    base = out[(0, 1)]
+    for key, (psi, tr) in out.items():
+        assert np.array_equal(psi, base[0]), key
+        assert np.allclose(tr, base[1], rtol=1e-9, atol=0), key
