@@ -338,11 +338,14 @@ enum {
                                    pass run in kernels that keep the first and last FFT stages
                                    (and the c2r/r2c pairing) in registers; 1: the generic staged
                                    kernels (same butterflies)                                     */
-  RECON_OPT_KITER_TMA = 8,      /* N = 512 register-fused path: 1 (default) the source update runs in
-                                   persistent CTAs whose inputs (A, P_y, delta(k), S) are streamed into
-                                   shared memory by the tensor memory accelerator, the next tile while
-                                   the current one is transformed; 0 one CTA per tile loading its
-                                   inputs itself.  Same arithmetic.                                */
+  RECON_OPT_KITER_TMA = 8,      /* N = 512 register-fused path: 0 (default) one CTA per tile loading its
+                                   inputs itself; 1 persistent CTAs whose inputs (A, P_y, delta(k), S)
+                                   are streamed into shared memory by the tensor memory accelerator,
+                                   the next tile while the current one is transformed.  Same
+                                   arithmetic per element (Psi bitwise equal); the norm sums are
+                                   accumulated per thread over several tiles, so the trace differs in
+                                   float32 rounding.  Slower on GB300 (1.42 against 1.03 ms per
+                                   launch), kept as an option.                                    */
   RECON_OPT_ASSIGN = 7,         /* mass assignment of recon_deposit: 0 (default) cloud-in-cell, 1 the
                                    paper's nearest grid point (Sec. 3: node floor(x N / L + 1/2)),
                                    always on the direct (unsorted) deposit kernel.  The shift still

@@ -157,7 +157,7 @@ struct recon_handle {
   int kspace_generic = 0;
   int plane_batch = 0;   // register-fused path: y-planes per batch of the x -> z -> x passes (0: off)
   int assign = 0;        // mass assignment of the deposit: 0 CIC, 1 NGP (the paper's binning)
-  int kiter_tma = 1;     // N = 512 fused path: the source update's inputs streamed by TMA
+  int kiter_tma = 0;     // N = 512 fused path: 1 streams the source update's inputs by TMA
   bool tmaps_ok = false; // its tensor maps were built
   KIterMaps tmaps{};
   int reuse_sort = 0;

@@ -160,8 +160,8 @@ def test_plane_batched_passes_match_unbatched(lib, graph):
 def test_tma_streamed_update_matches_direct_loads(lib, los_mode):
     """RECON_OPT_KITER_TMA: the source update with its inputs streamed into shared memory by the
     tensor memory accelerator (persistent CTAs) computes every element with the same arithmetic as
-    the one-tile-per-CTA kernel, so Psi after a fixed number of updates is bitwise equal; only the
-    order of the float64 norm sums differs."""
+    the one-tile-per-CTA kernel, so Psi after a fixed number of updates is bitwise equal; its threads
+    accumulate the norm sums in float32 over several tiles, so the trace agrees to float32 rounding."""
     from paper_1504_02591_gb300 import binding as B
     from paper_1504_02591_gb300 import mocks
     obs = (0.0, 1750.0, 1750.0) if los_mode == 0 else (0.6, 0.8, 0.0)
@@ -181,4 +181,4 @@ def test_tma_streamed_update_matches_direct_loads(lib, los_mode):
     base = out[(0, 1)]
     for key, (psi, tr) in out.items():
         assert np.array_equal(psi, base[0]), key
-        assert np.allclose(tr, base[1], rtol=1e-9, atol=0), key
+        assert np.allclose(tr, base[1], rtol=1e-5, atol=0), key
