@@ -66,6 +66,10 @@ enum { RECON_F64 = 0, RECON_F32 = 1 };
  * (the paper writes f where this library uses beta = f / b). */
 enum { RECON_START_PLAIN = 0, RECON_START_APPROX1 = 1, RECON_START_FFTA = 2 };
 
+/* The coefficient c of a start (above) for beta = f / b, as recon_iterate uses it; host only.
+ * INVALID_ARG for an unknown start, a non-finite or negative beta, or a null c. */
+recon_status recon_start_coefficient(int start, double beta, double* c);
+
 /* Fields recon_get_field can export. */
 enum {
   RECON_FIELD_RHO_G = 0,     /* CIC density of galaxies (real), valid between deposit and smooth */

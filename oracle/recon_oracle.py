@@ -446,6 +446,20 @@ def fd_solve(delta, b: float, f: float, L: float, observer, los_mode: int, tol: 
 RATIO_LO, RATIO_HI = -1.0, 3.0   # Tables 1-3: ratios above 3 or below -1 are outliers
 
 
+def converged_at(means, tol: float = 0.01):
+    """The convergence rule of Sec. 5.2 (captions of Tables 2 and 3) on a sequence of mean ratios
+    m_0, m_1, ...: the first iteration n after which every mean differs from the one before it by
+    at most tol, |m_(k+1) - m_k| <= tol for all k >= n (the last iteration qualifies when no earlier
+    one does).  Reading: the ratios are near 1, so the paper's 1% is taken as an absolute 0.01, and
+    "at most" rather than "less than" because only then do the paper's printed two-decimal tables
+    give the iteration counts it states (Table 2: 4 and 2, Table 3: 6 and 2)."""
+    m = [float(x) for x in means]
+    for n in range(len(m)):
+        if all(abs(m[k + 1] - m[k]) <= tol + 1e-12 for k in range(n, len(m) - 1)):
+            return n
+    return len(m) - 1
+
+
 def ratio_stats(num, den, lo: float = RATIO_LO, hi: float = RATIO_HI):
     """Mean and standard deviation of the ratio num/den over all points, outliers removed (Table 1-3
     rule: a ratio above hi or below lo; a zero denominator counts as an outlier).  Returns

@@ -35,7 +35,7 @@ ABI_SYMBOLS = (
     "recon_unet_launch_count",
     "recon_iterate_from", "recon_start_features",
     "recon_get_radial", "recon_radial_ratio", "recon_ratio_stats", "recon_helmholtz_x",
-    "recon_radial_nbar", "recon_fkp_weights", "recon_fd_solve",
+    "recon_radial_nbar", "recon_fkp_weights", "recon_fd_solve", "recon_start_coefficient",
 )
 OPT_DEPOSIT_PATH, OPT_SHIFT_PATH, OPT_GRAPH, OPT_LINE_TILE, OPT_KSPACE_GENERIC, OPT_REUSE_SORT = 0, 1, 2, 3, 4, 5
 OPT_PLANE_BATCH, OPT_ASSIGN, OPT_KITER_TMA = 6, 7, 8
@@ -122,6 +122,7 @@ def load(path: str = LIB_PATH):
     lib.recon_unet_last_error.argtypes = [VP]
     lib.recon_unet_last_error.restype = C.c_char_p
     lib.recon_fd_solve.argtypes = [VP, D, I, P(I), P(D), VP]
+    lib.recon_start_coefficient.argtypes = [I, D, P(D)]
     lib.recon_radial_nbar.argtypes = [VP, P(ReconCatalog), I, D, D, D, P(D)]
     lib.recon_fkp_weights.argtypes = [VP, P(ReconCatalog), I, D, D, P(D), D, VP]
     lib.recon_radial_ratio.argtypes = [VP, VP, VP, P(ReconCatalog), D, D, P(D)]
@@ -152,6 +153,16 @@ def make_params(n, L, b, f, R, observer, los_mode=LOS_RADIAL, periodic=False, ma
     p.lognormal = int(bool(lognormal))
     p.mean_density_mode = MEAN_UNIFORM if uniform else MEAN_RANDOMS
     return p
+
+
+def start_coefficient(start: int, beta: float) -> float:
+    """recon_start_coefficient: the coefficient c of a start for beta = f / b."""
+    lib = load()
+    c = C.c_double()
+    st = lib.recon_start_coefficient(start, beta, C.byref(c))
+    if st != OK:
+        raise ReconError(st, "recon_start_coefficient: " + lib.recon_status_str(st).decode())
+    return c.value
 
 
 def workspace_bytes(params: ReconParams) -> int:

@@ -16,11 +16,15 @@ namespace rg {
 
 constexpr int kZThreads = 256;
 
+// columns of one N = 512 k-space (y) tile: 4 adjacent kz (one 32-byte sector per row)
+#ifndef RECON_KITER_COLS
+#define RECON_KITER_COLS 4
+#endif
 template <int N, int MODE = 0, int NARROW = 0>
 struct SCols {  // adjacent columns in one strided tile (the 3-component k-space tiles are narrower)
   static constexpr bool kK = (MODE == S_DELTA || MODE == S_ITER);
   static constexpr int kWide = ((N / 2) % 16 == 0 && N < 1024 && !NARROW) ? 16 : 8;   // must divide N / 2
-  static constexpr int v = kK ? 4 : kWide;
+  static constexpr int v = kK ? (N == 512 ? RECON_KITER_COLS : 4) : kWide;
   static_assert((N / 2) % v == 0 && N % v == 0, "tile columns must divide the half-grid rows");
 };
 
@@ -537,7 +541,8 @@ __device__ __forceinline__ void zrow_dw(const Geometry& g, float dx, float dy, i
 // psi = w u.  So the pass transforms two rows each way and leaves psi^ = r2c(psi) and
 // Z^ = r2c(dz psi) (P_x = dx psi^ and P_y = dy psi^ are formed by the forward x pass).
 //   Z_PROJ:   c2r x2, P, r2c x2; once the device loop has converged, c2r x3 and the real Psi.
-//   Z_RADIAL: c2r x2, u as a real row.
+//             With a.cform (while the loop runs) C arrives formed in f[0] and Psi_z in wf.
+//   Z_RADIAL: c2r x2, u as a real row (C form as Z_PROJ).
 //   Z_WARM:   u from the real row plus the upsampled coarse correction, r2c x2.
 //   Z_USTART: u from the real row, r2c x2.
 template <int N, int MODE>
@@ -636,14 +641,19 @@ __global__ void __launch_bounds__(kZThreads, 2) zfused8_kernel(const ZArgs a) {
         }
       if (MODE == Z_WARM) __syncwarp();   // crow is rewritten by the next row
     } else {
-      // all three rows' loads in flight before the first transform; C = dx Psi_x + dy Psi_y
       float2 x[3][8], xl[3];
+      if ((MODE == Z_PROJ || MODE == Z_RADIAL) && a.cform) {   // C and Psi_z from the inverse x pass
+        zrow_load(a.f[0], row, lane, x[0], xl[0]);
+        zrow_load(a.wf, row, lane, x[2], xl[2]);
+      } else {
+        // all three rows' loads in flight before the first transform; C = dx Psi_x + dy Psi_y
 #pragma unroll
-      for (int q = 0; q < 3; ++q) zrow_load(a.f[q], row, lane, x[q], xl[q]);
+        for (int q = 0; q < 3; ++q) zrow_load(a.f[q], row, lane, x[q], xl[q]);
 #pragma unroll
-      for (int r = 0; r < 8; ++r)
-        x[0][r] = make_float2(fmaf(dx, x[0][r].x, dy * x[1][r].x), fmaf(dx, x[0][r].y, dy * x[1][r].y));
-      xl[0] = make_float2(fmaf(dx, xl[0].x, dy * xl[1].x), fmaf(dx, xl[0].y, dy * xl[1].y));
+        for (int r = 0; r < 8; ++r)
+          x[0][r] = make_float2(fmaf(dx, x[0][r].x, dy * x[1][r].x), fmaf(dx, x[0][r].y, dy * x[1][r].y));
+        xl[0] = make_float2(fmaf(dx, xl[0].x, dy * xl[1].x), fmaf(dx, xl[0].y, dy * xl[1].y));
+      }
       zrow_c2r(x[0], xl[0], lane, partner, tw, s, tab, A[0], B[0]);
       zrow_c2r(x[2], xl[2], lane, partner, tw, s, tab, A[1], B[1]);
       // u = coef (Psi . r) at the real points 2m, 2m + 1 of the complex point m (Eq. Nusser)
@@ -1178,22 +1188,27 @@ struct XLine8 {
   static constexpr size_t smem = sizeof(float2) * ((size_t)TAB + (size_t)512 * C);
 };
 
-// The three radix-8 stages of this thread's NB butterflies: v[b][r] = x[j_b + 64 r] in, X[j_b + 64 r]
-// out (j_b = jb + b T / C), shared memory for the middle stage.  Starts by writing s: a caller
-// that ran it before syncs first.
-template <bool INV, int C>
-__device__ __forceinline__ void xline8_lines(float2 (&v)[XLine8<C>::NB][8], float2* __restrict__ s,
-                                             const float2* __restrict__ tw, int jb, int col) {
+// The three radix-8 stages of a 512-point transform over C columns, the thread's NB butterflies
+// (j_b = jb + b T / C) with the first stage's inputs and the last stage's outputs handled one
+// butterfly at a time: ld(b, x) supplies x[r] = X[j_b + 64 r] and st(b, y) takes the outputs
+// y[r] = Y[j_b + 64 r], so only the middle stage holds all NB butterflies in registers (it reads
+// and writes shared memory in place).  Starts by writing s: a caller that ran it before syncs first.
+template <bool INV, int C, class Ld, class St>
+__device__ __forceinline__ void xline8_io(float2* __restrict__ s, const float2* __restrict__ tw, int jb, int col,
+                                          Ld&& ld, St&& st) {
   constexpr int T = XLine8<C>::T, NB = XLine8<C>::NB;
   using Lay = ColLayout<C>;
 #pragma unroll
   for (int b = 0; b < NB; ++b) {                          // stage 1 (NS = 1)
     const int j = jb + b * (T / C);
-    Dft<8, INV>::run(v[b]);
+    float2 x[8];
+    ld(b, x);
+    Dft<8, INV>::run(x);
 #pragma unroll
-    for (int r = 0; r < 8; ++r) s[Lay::phys(8 * j + r, col)] = v[b][r];
+    for (int r = 0; r < 8; ++r) s[Lay::phys(8 * j + r, col)] = x[r];
   }
   __syncthreads();
+  float2 v[NB][8];
 #pragma unroll
   for (int b = 0; b < NB; ++b) {                          // stage 2 (NS = 8)
     const int j = jb + b * (T / C), k = j & 7;
@@ -1218,15 +1233,17 @@ __device__ __forceinline__ void xline8_lines(float2 (&v)[XLine8<C>::NB][8], floa
 #pragma unroll
   for (int b = 0; b < NB; ++b) {                          // stage 3 (NS = 64)
     const int j = jb + b * (T / C);
+    float2 y[8];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) v[b][r] = s[Lay::phys(j + 64 * r, col)];
+    for (int r = 0; r < 8; ++r) y[r] = s[Lay::phys(j + 64 * r, col)];
 #pragma unroll
     for (int r = 1; r < 8; ++r) {
       float2 w = tw[56 + (r - 1) * 64 + j];
       if (INV) w.y = -w.y;
-      v[b][r] = cmul(v[b][r], w);
+      y[r] = cmul(y[r], w);
     }
-    Dft<8, INV>::run(v[b]);
+    Dft<8, INV>::run(y);
+    st(b, y);
   }
 }
 
@@ -1240,9 +1257,19 @@ __device__ __forceinline__ void xline8_lines(float2 (&v)[XLine8<C>::NB][8], floa
 // comes from HBM once and from the L2 the second time:
 //   inverse: role 1 transforms Psi_y in the second field in place; role 0 transforms G (third field)
 //            twice, Psi_x = IFFT_x(kdx G) into the first and Psi_z = kdz IFFT_x(G) into the third;
+//   inverse in C form (a.cform, while the loop runs): the projection pass needs only
+//            C = dx Psi_x + dy Psi_y and Psi_z, and dx varies along the x line (the output index)
+//            while dy is the tile's constant, so role 0 leaves C = dx IFFT_x(kdx G) + dy IFFT_x(Psi_y)
+//            in the first field and role 1 Psi_z = kdz IFFT_x(G) in the fourth (wf): two fields
+//            written instead of three, and the projection pass reads two;
 //   forward: role 1 leaves P_y = dy FFT_x(psi^) (first field) in the second; role 0 leaves
 //            A = kdx FFT_x(dx psi^) + kdz FFT_x(Z^) in the third (its first product goes through the
 //            L2 and is read back by the thread that wrote it).
+__device__ __forceinline__ uint32_t opaque_u32(uint32_t x) {
+  asm volatile("" : "+r"(x));
+  return x;
+}
+
 template <bool INV, int C, bool PAIR>
 __global__ void __launch_bounds__(XLine8<C>::T, 2) xline8_kernel(const SArgs a) {
   constexpr int N = 512, H = N / 2, T = XLine8<C>::T, NB = XLine8<C>::NB;
@@ -1264,36 +1291,35 @@ __global__ void __launch_bounds__(XLine8<C>::T, 2) xline8_kernel(const SArgs a) 
   // element offsets fit 32 bits (at most N^3 / 2 complex points per field)
   const uint32_t o0 = (uint32_t)t.base + (uint32_t)(col * t.cs) + (uint32_t)jb * (uint32_t)t.ls;
   const uint32_t ls = (uint32_t)t.ls;
-  auto at = [&](int b, int r) { return o0 + (uint32_t)(b * (T / C) + 64 * r) * ls; };
-  float2 v[NB][8];
+  // element offset of point (b, r) of this thread; every load and store re-derives the base through
+  // an opaque copy, so no offset is kept live across a transform
+  auto off = [&](uint32_t base, int b, int r) { return base + (uint32_t)(b * (T / C) + 64 * r) * ls; };
+  auto load = [&](const float2* __restrict__ P) {
+    return [=, &off](int b, float2 (&x)[8]) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) x[r] = P[off(o0, b, r)];
+    };
+  };
+  auto store = [&](float2* __restrict__ P, float scale) {
+    return [=, &off](int b, const float2 (&y)[8]) {
+      const uint32_t o = opaque_u32(o0);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) P[off(o, b, r)] = cscale(y[r], scale);
+    };
+  };
   const Geometry& g = a.g;
-  if (!PAIR || (INV && role == 1)) {
+  const bool cf = PAIR && INV && a.cform && !(a.loop_flag && *a.loop_flag == 1);
+  if (!PAIR || (INV && role == 1 && !cf)) {
     float2* __restrict__ P = t.isQ ? a.f[role].Q : a.f[role].M;
-#pragma unroll
-    for (int b = 0; b < NB; ++b)
-#pragma unroll
-      for (int r = 0; r < 8; ++r) v[b][r] = P[at(b, r)];
-    xline8_lines<INV, C>(v, s, tw, jb, col);
-#pragma unroll
-    for (int b = 0; b < NB; ++b)
-#pragma unroll
-      for (int r = 0; r < 8; ++r) P[at(b, r)] = v[b][r];
+    xline8_io<INV, C>(s, tw, jb, col, load(P), store(P, 1.f));
     return;
   }
   float2* __restrict__ P0 = t.isQ ? a.f[0].Q : a.f[0].M;
+  float2* __restrict__ P1 = t.isQ ? a.f[1].Q : a.f[1].M;
   float2* __restrict__ P2 = t.isQ ? a.f[2].Q : a.f[2].M;
+  const float dy = g.los_mode == 1 ? g.los.y : g.off[N + (t.isQ ? t.c0 + col : t.a)];
   if (!INV && role == 1) {   // P_y = dy FFT_x(psi^)
-    const float dy = g.los_mode == 1 ? g.los.y : g.off[N + (t.isQ ? t.c0 + col : t.a)];
-    float2* __restrict__ P1 = t.isQ ? a.f[1].Q : a.f[1].M;
-#pragma unroll
-    for (int b = 0; b < NB; ++b)
-#pragma unroll
-      for (int r = 0; r < 8; ++r) v[b][r] = P0[at(b, r)];
-    xline8_lines<INV, C>(v, s, tw, jb, col);
-#pragma unroll
-    for (int b = 0; b < NB; ++b)
-#pragma unroll
-      for (int r = 0; r < 8; ++r) P1[at(b, r)] = cscale(v[b][r], dy);
+    xline8_io<INV, C>(s, tw, jb, col, load(P0), store(P1, dy));
     return;
   }
   const float kf = g.kf;
@@ -1303,52 +1329,57 @@ __global__ void __launch_bounds__(XLine8<C>::T, 2) xline8_kernel(const SArgs a) 
     const int i = jb + b * (T / C) + 64 * r;
     return i == H ? 0.f : kf * (float)(i < H ? i : i - N);
   };
-  if (INV) {
+  auto dxv = [&](int b, int r) { return g.los_mode == 1 ? g.los.x : g.off[jb + b * (T / C) + 64 * r]; };
+  // loads of G scaled by kdx (the inverse's x component)
+  auto load_kdx_g = [&](int b, float2 (&x)[8]) {
 #pragma unroll
-    for (int b = 0; b < NB; ++b)
-#pragma unroll
-      for (int r = 0; r < 8; ++r) v[b][r] = cscale(P2[at(b, r)], kdx(b, r));
-    xline8_lines<INV, C>(v, s, tw, jb, col);
-#pragma unroll
-    for (int b = 0; b < NB; ++b)
-#pragma unroll
-      for (int r = 0; r < 8; ++r) P0[at(b, r)] = v[b][r];
+    for (int r = 0; r < 8; ++r) x[r] = cscale(P2[off(o0, b, r)], kdx(b, r));
+  };
+  if (cf) {
+    // both roles start on G, so the pair reads it from HBM once
+    if (role == 1) {   // Psi_z = kdz IFFT_x(G)
+      float2* __restrict__ W = t.isQ ? a.wf.Q : a.wf.M;
+      xline8_io<INV, C>(s, tw, jb, col, load(P2), store(W, kdz));
+      return;
+    }
+    // role 0: Psi_x = IFFT_x(kdx G) parked in the first field, then C = fmaf(dx, Psi_x, dy Psi_y),
+    // rounded exactly as the projection pass forms it from the three components
+    xline8_io<INV, C>(s, tw, jb, col, load_kdx_g, store(P0, 1.f));
     __syncthreads();   // s is rewritten by the second transform
-#pragma unroll
-    for (int b = 0; b < NB; ++b)
-#pragma unroll
-      for (int r = 0; r < 8; ++r) v[b][r] = P2[at(b, r)];
-    xline8_lines<INV, C>(v, s, tw, jb, col);
-#pragma unroll
-    for (int b = 0; b < NB; ++b)
-#pragma unroll
-      for (int r = 0; r < 8; ++r) P2[at(b, r)] = cscale(v[b][r], kdz);
-  } else {
-    auto dxv = [&](int b, int r) { return g.los_mode == 1 ? g.los.x : g.off[jb + b * (T / C) + 64 * r]; };
-#pragma unroll
-    for (int b = 0; b < NB; ++b)
-#pragma unroll
-      for (int r = 0; r < 8; ++r) v[b][r] = P2[at(b, r)];
-    xline8_lines<INV, C>(v, s, tw, jb, col);                          // FFT_x(Z^)
-#pragma unroll
-    for (int b = 0; b < NB; ++b)
-#pragma unroll
-      for (int r = 0; r < 8; ++r) P2[at(b, r)] = cscale(v[b][r], kdz);
-    __syncthreads();   // s is rewritten by the second transform
-#pragma unroll
-    for (int b = 0; b < NB; ++b)
-#pragma unroll
-      for (int r = 0; r < 8; ++r) v[b][r] = cscale(P0[at(b, r)], dxv(b, r));
-    xline8_lines<INV, C>(v, s, tw, jb, col);                          // FFT_x(dx psi^)
-#pragma unroll
-    for (int b = 0; b < NB; ++b)
+    xline8_io<INV, C>(s, tw, jb, col, load(P1), [&](int b, const float2 (&y)[8]) {   // IFFT_x(Psi_y)
+      const uint32_t o = opaque_u32(o0);
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        const float2 x = P2[at(b, r)];   // this thread's own kdz FFT_x(Z^)
-        const float k = kdx(b, r);
-        P2[at(b, r)] = make_float2(fmaf(k, v[b][r].x, x.x), fmaf(k, v[b][r].y, x.y));
+        const float2 x = P0[off(o, b, r)];   // this thread's own Psi_x
+        const float d = dxv(b, r);
+        P0[off(o, b, r)] = make_float2(fmaf(d, x.x, dy * y[r].x), fmaf(d, x.y, dy * y[r].y));
       }
+    });
+    return;
   }
+  if (INV) {   // three components: Psi_x = IFFT_x(kdx G) into the first field, Psi_z = kdz IFFT_x(G)
+    xline8_io<INV, C>(s, tw, jb, col, load_kdx_g, store(P0, 1.f));
+    __syncthreads();   // s is rewritten by the second transform
+    xline8_io<INV, C>(s, tw, jb, col, load(P2), store(P2, kdz));
+    return;
+  }
+  // forward: kdz FFT_x(Z^) into the third field, then A = kdx FFT_x(dx psi^) + that
+  xline8_io<INV, C>(s, tw, jb, col, load(P2), store(P2, kdz));
+  __syncthreads();   // s is rewritten by the second transform
+  xline8_io<INV, C>(s, tw, jb, col,
+                    [&](int b, float2 (&x)[8]) {
+#pragma unroll
+                      for (int r = 0; r < 8; ++r) x[r] = cscale(P0[off(o0, b, r)], dxv(b, r));
+                    },
+                    [&](int b, const float2 (&y)[8]) {   // FFT_x(dx psi^)
+                      const uint32_t o = opaque_u32(o0);
+#pragma unroll
+                      for (int r = 0; r < 8; ++r) {
+                        const float2 x = P2[off(o, b, r)];   // this thread's own kdz FFT_x(Z^)
+                        const float k = kdx(b, r);
+                        P2[off(o, b, r)] = make_float2(fmaf(k, y[r].x, x.x), fmaf(k, y[r].y, x.y));
+                      }
+                    });
 }
 
 // One tile of the source update (Eq. iterative) from registers: v[0] = A and v[1] = P_y along the y

@@ -67,7 +67,7 @@ enum State { ST_CREATED = 0, ST_DEPOSITED = 1, ST_SMOOTHED = 2, ST_ITERATED = 3 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t field_M, field_Q, field, tw, tabs, tabz, off, taps, red, partials, stage, bricks, coarse, total;
+  size_t field_M, field_Q, field, wfield, tw, tabs, tabz, off, taps, red, partials, stage, bricks, coarse, total;
 };
 
 Layout layout_for(int n) {
@@ -76,6 +76,7 @@ Layout layout_for(int n) {
   l.field_M = align256((size_t)n * n * n * sizeof(float));
   l.field_Q = align256((size_t)n * n * sizeof(float2));
   l.field = l.field_M + l.field_Q;
+  l.wfield = mk->kspace_fused ? l.field : 0;   // register-fused path: Psi_z in C form (fourth vector field)
   l.tw = align256((size_t)n * sizeof(float2));
   l.tabs = align256((size_t)mk->tab_s * sizeof(float2) + 16);
   l.tabz = align256((size_t)mk->tab_z * sizeof(float2) + 16);
@@ -92,7 +93,7 @@ Layout layout_for(int n) {
   l.stage = align256(2 * (size_t)kStageParticles * kStageBytesPer);   // two buffers (copy/compute overlap)
   l.bricks = align256(brick_scratch_bytes(n));
   l.coarse = align256((size_t)(n / 2) * (n / 2) * (n / 2) * sizeof(float));   // warm start, level >= 1
-  l.total = 5 * l.field + l.tw + l.tabs + l.tabz + l.off + l.taps + l.red + l.partials + l.stage + l.bricks +
+  l.total = 5 * l.field + l.wfield + l.tw + l.tabs + l.tabz + l.off + l.taps + l.red + l.partials + l.stage + l.bricks +
             l.coarse;
   return l;
 }
@@ -129,6 +130,7 @@ struct recon_handle {
   bool own_ws = false;
   Layout lay{};
   Field V[3]{}, D{}, S{};
+  Field W{};             // N = 512: Psi_z between the inverse x pass and the projection (C form)
   float2* tw = nullptr;
   float2* tabs = nullptr;   // stage twiddles, N-point plan
   float2* tabz = nullptr;   // stage twiddles, N/2-point plan
@@ -288,6 +290,7 @@ ZArgs zargs(recon_handle* h) {
   a.uniform = h->p.mean_density_mode == RECON_MEAN_UNIFORM;
   a.lognormal = h->p.lognormal;
   a.generic = h->kspace_generic;
+  a.wf = h->W;
   return a;
 }
 
@@ -305,6 +308,7 @@ SArgs sargs(recon_handle* h) {
   a.generic = h->kspace_generic;
   a.lognormal = h->p.lognormal;
   a.tmaps = (h->tmaps_ok && h->kiter_tma) ? &h->tmaps : nullptr;
+  a.wf = h->W;
   return a;
 }
 
@@ -345,25 +349,27 @@ double cfield(const recon_handle* h) { return (double)h->n * h->n * h->n * 4.0 +
 double rfield(const recon_handle* h) { return (double)h->n * h->n * h->n * 4.0; }
 
 double zbytes(const recon_handle* h, int mode, int nc, const ZArgs& a) {
-  // the register-fused path hands the z pass three fields and takes two back (psi^, Z^)
+  // the register-fused path hands the z pass three fields (two in C form) and takes two back (psi^, Z^)
   const int nv = (h->mk->kspace_fused && !h->kspace_generic && nc == 3) ? 2 : nc;
+  if (mode == Z_PROJ && a.cform) return 4.0 * cfield(h);
   if (mode == Z_DELTA) {
     const int nin = a.uniform ? 1 : 2;
     return nin * rfield(h) + cfield(h) + (a.delta_real ? rfield(h) : 0.0);
   }
   if (mode == Z_FINAL) return nc * (cfield(h) + rfield(h));
-  if (mode == Z_RADIAL) return nc * cfield(h) + rfield(h);
+  if (mode == Z_RADIAL) return (a.cform ? 2 : nc) * cfield(h) + rfield(h);
   if (mode == Z_USTART || mode == Z_WARM) return rfield(h) + nv * cfield(h);
   return (nc + nv) * cfield(h);
 }
 
-double sbytes(const recon_handle* h, int mode, int nc, int axis) {
+double sbytes(const recon_handle* h, int mode, int nc, int axis, int cform) {
   // the register-fused path carries the x and z components of k-space vectors as one field
   const bool fused = h->mk->kspace_fused && !h->kspace_generic;
   if (mode == S_DELTA) return (fused ? 5.0 : 6.0) * cfield(h);   // delta in, delta(k), S, 2 or 3 Psi
   if (mode == S_ITER) return (fused ? 7.0 : 9.0) * cfield(h);    // 2 or 3 P + delta(k) + S in; 2 or 3 Psi + S out
-  // paired x passes: inverse 2 fields in, 3 out; forward 2 in (the pair's shared one read once), 2 out
-  if (fused && axis == AX_X && nc == 3) return (mode == S_INV ? 5.0 : 4.0) * cfield(h);
+  // paired x passes: inverse 2 fields in, 3 out (2 in C form); forward 2 in (the pair's shared one
+  // read once), 2 out
+  if (fused && axis == AX_X && nc == 3) return (mode == S_INV && !cform ? 5.0 : 4.0) * cfield(h);
   return 2.0 * nc * cfield(h);
 }
 
@@ -375,7 +381,7 @@ recon_status run_z(recon_handle* h, int mode, int nc, const ZArgs& a, int* grid 
 
 recon_status run_s(recon_handle* h, int mode, int nc, int axis, const SArgs& a) {
   const double part = a.ycount ? (double)a.ycount / h->n : 1.0;
-  RG_CUDA(timed(h, skind(mode, axis), part * sbytes(h, mode, nc, axis), [&] { return h->mk->spass(mode, nc, axis, a, h->st); }));
+  RG_CUDA(timed(h, skind(mode, axis), part * sbytes(h, mode, nc, axis, a.cform), [&] { return h->mk->spass(mode, nc, axis, a, h->st); }));
   return RECON_OK;
 }
 
@@ -400,6 +406,12 @@ int plane_batch(const recon_handle* h) {
   return (h->plane_batch && h->mk->kspace_fused && !h->kspace_generic) ? h->plane_batch : 0;
 }
 
+// Whether the inverse x pass and the projection (or radial) pass exchange C = dx Psi_x + dy Psi_y
+// and Psi_z (register-fused path) rather than the three components.
+int cform(const recon_handle* h) {
+  return (h->mk->kspace_fused && !h->kspace_generic && h->lay.wfield) ? 1 : 0;
+}
+
 // Inverse x, the projection pass and forward x over all y-planes, batch by batch.  za and the x
 // arguments carry the device loop's flags when the passes run inside the iteration graph.
 recon_status xzx_batched(recon_handle* h, int B, const ZArgs& za0, const int* skip_flag) {
@@ -408,10 +420,14 @@ recon_status xzx_batched(recon_handle* h, int B, const ZArgs& za0, const int* sk
     for (int q = 0; q < 3; ++q) xa.f[q] = h->V[q];
     xa.ybeg = y0;
     xa.ycount = B;
+    xa.cform = cform(h);
+    xa.loop_flag = skip_flag;
     RG_TRY(run_s(h, S_INV, 3, AX_X, xa));
+    xa.loop_flag = nullptr;
     ZArgs za = za0;
     za.ybeg = y0;
     za.ycount = B;
+    za.cform = xa.cform;
     RG_TRY(run_z(h, Z_PROJ, 3, za));
     xa.skip_flag = skip_flag;
     RG_TRY(run_s(h, S_FWD, 3, AX_X, xa));
@@ -421,9 +437,11 @@ recon_status xzx_batched(recon_handle* h, int B, const ZArgs& za0, const int* sk
 
 // plain X pass (one FFT along x per component) over nc fields.  The forward 3-D transform runs
 // Z (r2c) -> X -> Y, the inverse Y -> X -> Z; the Y passes carry the k-space work.
-recon_status xpass(recon_handle* h, int mode, int nc, const Field* f) {
+recon_status xpass(recon_handle* h, int mode, int nc, const Field* f, int cf = 0, const int* flag = nullptr) {
   SArgs a = sargs(h);
   for (int q = 0; q < nc; ++q) a.f[q] = f[q];
+  a.cform = cf;
+  a.loop_flag = flag;
   return run_s(h, mode, nc, AX_X, a);
 }
 
@@ -692,6 +710,10 @@ recon_status recon_create(const recon_params* p, void* stream, void* workspace, 
   b += h->lay.field;
   h->S = field_at(b, h->lay);
   b += h->lay.field;
+  if (h->lay.wfield) {
+    h->W = field_at(b, h->lay);
+    b += h->lay.wfield;
+  }
   h->tw = (float2*)b;
   b += h->lay.tw;
   h->tabs = (float2*)b;
@@ -910,7 +932,8 @@ recon_status iterate_start(recon_handle* h, float coef0) {
   for (int q = 0; q < 3; ++q) za.f[q] = h->V[q];
   za.coef = coef0;
   if (const int B = plane_batch(h)) return xzx_batched(h, B, za, nullptr);
-  RG_TRY(xpass(h, S_INV, 3, h->V));
+  za.cform = cform(h);
+  RG_TRY(xpass(h, S_INV, 3, h->V, za.cform));
   RG_TRY(run_z(h, Z_PROJ, 3, za));
   RG_TRY(xpass(h, S_FWD, 3, h->V));
   return RECON_OK;
@@ -929,7 +952,9 @@ recon_status iterate_body(recon_handle* h, cudaGraphConditionalHandle cond) {
   for (int q = 0; q < 3; ++q) za.f[q] = h->V[q];
   za.loop_flag = &h->loop->flag;
   if (const int B = plane_batch(h)) return xzx_batched(h, B, za, &h->loop->flag);
-  RG_TRY(xpass(h, S_INV, 3, h->V));
+  // C form unless the decide kernel has just ended the loop (then the Z pass writes the real Psi)
+  za.cform = cform(h);
+  RG_TRY(xpass(h, S_INV, 3, h->V, za.cform, &h->loop->flag));
   RG_TRY(run_z(h, Z_PROJ, 3, za));
   SArgs fa = sargs(h);
   for (int q = 0; q < 3; ++q) fa.f[q] = h->V[q];
@@ -1135,7 +1160,9 @@ recon_status iterate_core(recon_handle* h, const StartSpec& sp, double tol, int 
       RG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
       RG_CUDA(cudaEventRecord(ev, h->st));
       const int B = plane_batch(h);
-      if (!B) RG_TRY(xpass(h, S_INV, 3, h->V));
+      // the inverse waits for the decision: after the last update it writes the three components
+      const int cf = cform(h);
+      if (!B && !cf) RG_TRY(xpass(h, S_INV, 3, h->V));
       cudaError_t es = cudaEventSynchronize(ev);
       cudaEventDestroy(ev);
       RG_CUDA(es);
@@ -1149,7 +1176,7 @@ recon_status iterate_core(recon_handle* h, const StartSpec& sp, double tol, int 
       h->trace.push_back(rel);
       const bool done = (it >= 2 && rel < tol) || it >= max_iter;
       if (done) {
-        if (B) RG_TRY(xpass(h, S_INV, 3, h->V));
+        if (B || cf) RG_TRY(xpass(h, S_INV, 3, h->V));
         RG_TRY(run_z(h, Z_FINAL, 3, za));
         break;
       }
@@ -1157,7 +1184,10 @@ recon_status iterate_core(recon_handle* h, const StartSpec& sp, double tol, int 
         RG_TRY(xzx_batched(h, B, za, nullptr));
         continue;
       }
-      RG_TRY(run_z(h, Z_PROJ, 3, za));
+      if (cf) RG_TRY(xpass(h, S_INV, 3, h->V, cf));
+      ZArgs zc = za;
+      zc.cform = cf;
+      RG_TRY(run_z(h, Z_PROJ, 3, zc));
       RG_TRY(xpass(h, S_FWD, 3, h->V));
     }
   }
@@ -1171,6 +1201,13 @@ recon_status iterate_core(recon_handle* h, const StartSpec& sp, double tol, int 
 }
 
 }  // namespace
+
+recon_status recon_start_coefficient(int start, double beta, double* c) {
+  if (!c || start < RECON_START_PLAIN || start > RECON_START_FFTA || !std::isfinite(beta) || beta < 0)
+    return RECON_ERR_INVALID_ARG;
+  *c = start_coefficient(start, beta);
+  return RECON_OK;
+}
 
 recon_status recon_iterate(recon_handle* h, int start, double tol, int max_iter, int* n_iter, double* rel_change) {
   if (!h) return RECON_ERR_INVALID_ARG;
@@ -1209,9 +1246,10 @@ recon_status recon_start_features(recon_handle* h, int start, int level, float* 
     RG_TRY(run_s(h, S_DELTA, 1, AX_Y, a));
     h->d_is_k = 1;
   }
-  RG_TRY(xpass(h, S_INV, 3, h->V));
   ZArgs za = zargs(h);
   for (int q = 0; q < 3; ++q) za.f[q] = h->V[q];
+  za.cform = cform(h);
+  RG_TRY(xpass(h, S_INV, 3, h->V, za.cform));
   za.coef = (float)(1.0 - start_coefficient(start, h->p.f / h->p.b));
   za.u_out = reinterpret_cast<float*>(h->V[0].M);
   RG_TRY(run_z(h, Z_RADIAL, 3, za));

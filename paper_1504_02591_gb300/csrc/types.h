@@ -70,6 +70,10 @@ struct ZArgs {
   int generic;            // Z_PROJ: the generic staged kernel instead of the register-fused one
   int ybeg, ycount;       // register-fused passes: only the rows of y-planes [ybeg, ybeg + ycount)
                           // (ycount 0: every row)
+  // Z_PROJ of the register-fused path while the loop runs: the inverse x pass handed over
+  // C = dx Psi_x + dy Psi_y in f[0] and Psi_z in wf (two fields read, not three)
+  int cform;
+  Field wf;
 };
 
 // Tensor maps of the register-fused source update's four inputs (A, P_y, delta(k), S) over the
@@ -96,6 +100,12 @@ struct SArgs {
   int ybeg, ycount;       // paired x passes: only the lines of y-planes [ybeg, ybeg + ycount)
                           // (ycount 0: every line; both multiples of the tile width)
   const KIterMaps* tmaps; // host memory: the source update streams its inputs by TMA (N = 512)
+  // paired inverse x pass (N = 512) unless loop_flag && *loop_flag == 1 (the device loop has just
+  // converged): leave C = dx Psi_x + dy Psi_y in f[0] and Psi_z in wf for the projection pass,
+  // instead of Psi_x, Psi_y, Psi_z in f[0..2]
+  int cform;
+  Field wf;
+  const int* loop_flag;
 };
 
 // State of the device-driven iteration (in the workspace).

@@ -9,7 +9,9 @@ smoothed with a Gaussian of R = 15 Mpc/h has unit variance) is drawn on a coarse
 seeded normal noise.  Its first-order displacement moves Lagrangian points q (a jittered lattice or
 uniform points) to x = q + D(q); galaxies are kept with probability proportional to
 max(0, 1 + (b - 1) delta_L(q)) (Lagrangian bias) and moved to redshift space by s = x + f (D.r) r.
-Randoms are uniform in the same window.
+Randoms are uniform in the same window.  Optionally (k_turn) the spectrum is turned over to P ~ k
+below k_turn, which bounds the bulk flows that the k^-1.5 spectrum drives from scales larger than a
+survey window.
 
 This module is input plumbing only.  It is shared by the tests, the benchmark and the oracle runs, and
 it contains no code of either the CUDA path or the oracle; its small Fourier-space displacement and
@@ -41,11 +43,17 @@ PK_SLOPE = -1.5
 PK_CUTOFF = 0.3         # h/Mpc
 
 
-def power_spectrum(k):
+def power_spectrum(k, k_turn: float | None = None):
+    """A k^-1.5 exp(-(k/0.3)^2); with k_turn, times x/(1 + x), x = (k/k_turn)^2.5, which turns the
+    spectrum over to P ~ k at k << k_turn (as a CDM spectrum does near its peak) and so bounds the
+    large-scale (bulk-flow) part of the displacement."""
     k = np.asarray(k, dtype=np.float64)
     out = np.zeros_like(k)
     pos = k > 0
     out[pos] = PK_AMPLITUDE * k[pos] ** PK_SLOPE * np.exp(-(k[pos] / PK_CUTOFF) ** 2)
+    if k_turn:
+        x = (k[pos] / k_turn) ** 2.5
+        out[pos] *= x / (1.0 + x)
     return out
 
 
@@ -82,8 +90,9 @@ class GeneratorField:
         return d, v
 
 
-def gaussian_field(ng: int, L: float, seed: int, amp: float = 1.0) -> GeneratorField:
-    """The field of the spectrum above times amp (amp < 1: closer to the linear regime)."""
+def gaussian_field(ng: int, L: float, seed: int, amp: float = 1.0, k_turn: float | None = None) -> GeneratorField:
+    """The field of the spectrum above times amp (amp < 1: closer to the linear regime), turned over
+    below k_turn when given."""
     rng = np.random.default_rng(seed)
     white = rng.standard_normal((ng, ng, ng), dtype=np.float32)
     W = _rfftn(white)
@@ -95,7 +104,7 @@ def gaussian_field(ng: int, L: float, seed: int, amp: float = 1.0) -> GeneratorF
     kz = (kf * mz)[None, None, :]
     kk = np.sqrt(kx ** 2 + ky ** 2 + kz ** 2)
     vcell = (L / ng) ** 3
-    D = W * (amp * np.sqrt(power_spectrum(kk) / vcell))
+    D = W * (amp * np.sqrt(power_spectrum(kk, k_turn) / vcell))
     D[0, 0, 0] = 0
     delta = _irfftn(D, (ng, ng, ng)).astype(np.float32)
     inv_k2 = np.zeros_like(kk)
@@ -189,10 +198,10 @@ def _in_window(p, observer, axis, r_min, r_max, cos_min):
 def shell_survey(L: float, n_mesh: int, n_gal: int, n_ran: int, b: float, f: float, R: float,
                  observer, axis, r_min: float, r_max: float, sky_frac: float,
                  seed_field: int, seed_gal: int, seed_ran: int, ng: int | None = None,
-                 name: str = "shell", amp: float = 1.0) -> Mock:
+                 name: str = "shell", amp: float = 1.0, k_turn: float | None = None) -> Mock:
     """Spherical-shell cap window (r_min..r_max around the observer, sky fraction sky_frac)."""
     ng = ng or min(n_mesh, 256)
-    gf = gaussian_field(ng, L, seed_field, amp)
+    gf = gaussian_field(ng, L, seed_field, amp, k_turn)
     obs = np.asarray(observer, dtype=np.float64)
     ax = _unit(np.asarray(axis, dtype=np.float64))
     cos_min = 1.0 - 2.0 * sky_frac
@@ -254,14 +263,16 @@ def small_periodic(n_gal: int = 200_000, n_ran: int = 2_000_000, n_mesh: int = 6
 
 
 def survey_shell_512(n_gal: int = 600_000, ran_ratio: int = 50, n_mesh: int = 512,
-                     L: float = 3500.0, seed: int = 10, amp: float = 1.0) -> Mock:
+                     L: float = 3500.0, seed: int = 10, amp: float = 1.0,
+                     k_turn: float | None = None) -> Mock:
     """512^3 mesh in a 3500 Mpc/h box, shell 1100-1800 Mpc/h, 25% sky cap, 6e5 galaxies, 50x
     randoms, b = 1.85, f = 0.74, R = 15.  Observer at the centre of the x = 0 face, cap axis +x
     (a box-corner observer sees at most 1/8 of the sky, so a 25% cap cannot sit at the corner).
-    Seeds seed, seed + 1, seed + 2 (field, galaxies, randoms); the benchmark mock is seed 10."""
+    Seeds seed, seed + 1, seed + 2 (field, galaxies, randoms); the benchmark mock is seed 10.
+    amp scales the field; k_turn turns the spectrum over at large scales (the diagnostics' mocks)."""
     return shell_survey(L, n_mesh, n_gal, n_gal * ran_ratio, 1.85, 0.74, 15.0,
                         (0.0, L / 2, L / 2), (1.0, 0.0, 0.0), 1100.0, 1800.0, 0.25,
-                        seed, seed + 1, seed + 2, ng=256, name=f"shell-{n_mesh}", amp=amp)
+                        seed, seed + 1, seed + 2, ng=256, name=f"shell-{n_mesh}", amp=amp, k_turn=k_turn)
 
 
 def scaled_shell(n_mesh: int, L: float, n_gal: int, ran_ratio: int, b: float, f: float,

@@ -61,3 +61,38 @@ def test_status_strings(lib):
         assert lib.recon_status_str(s)
     lib.recon_destroy.argtypes = [C.c_void_p]
     assert lib.recon_destroy(None) == 0
+
+
+def test_start_coefficient_matches_the_oracle(lib):
+    """recon_start_coefficient (host only) gives the c of Sec. 5.2's starts as the oracle does."""
+    from oracle import recon_oracle as O
+    binding._lib = None
+    binding.load()
+    for start in (binding.START_PLAIN, binding.START_APPROX1, binding.START_FFTA):
+        for beta in (0.0, 0.2, 0.4, 0.74, 3.0):
+            assert binding.start_coefficient(start, beta) == pytest.approx(O.start_coefficient(start, beta), rel=1e-15)
+    for start, beta in ((3, 0.4), (-1, 0.4), (0, -0.1), (2, float("nan"))):
+        with pytest.raises(binding.ReconError) as e:
+            binding.start_coefficient(start, beta)
+        assert e.value.status == binding.ERR_INVALID_ARG
+
+
+def test_diagnostic_convergence_rule_matches_the_oracle():
+    """The package's host rule for the paper's convergence iteration (Sec. 5.2) agrees with the
+    oracle's, which the paper's own Tables 2 and 3 pin (tests/golden/iteration_tables.txt)."""
+    import numpy as np
+    from oracle import recon_oracle as O
+    from paper_1504_02591_gb300 import diagnostics
+    rows = [ln.split() for ln in open(os.path.join(ROOT, "tests", "golden", "iteration_tables.txt"))
+            if ln.strip() and not ln.startswith("#") and not ln.startswith("converged")]
+    seqs = {}
+    for t, s, n, m, *_ in rows:
+        seqs.setdefault((t, s), []).append((int(n), float(m)))
+    for seq in seqs.values():
+        means = [m for _, m in sorted(seq)]
+        assert diagnostics.converged_at(means) == O.converged_at(means)
+    rng = np.random.default_rng(3)
+    for _ in range(500):
+        means = list(1.0 + np.cumsum(rng.choice([-1, 1], 8) * rng.choice([0.0, 0.005, 0.01, 0.02, 0.1], 8)))
+        assert diagnostics.converged_at(means) == O.converged_at(means)
+    assert diagnostics.converged_at([0.9]) == 0

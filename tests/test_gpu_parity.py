@@ -344,7 +344,10 @@ def test_particle_edge_positions(B):
         r.deposit(torch.from_numpy(both).cuda(), None, torch.from_numpy(ran).cuda(), None)
         rho_g = r.get_field(B.FIELD_RHO_G).cpu().numpy()
         assert abs(rho_g.astype(np.float64).sum() - len(both)) <= 1e-5 * len(both)
-        assert rel_l2(rho_g, O.cic_deposit(both, None, n, L)) < 1e-6, path
+        # float32 sums in a run-dependent order: a node that collects m weights (a few hundred on
+        # the corner node here) carries rounding of about sqrt(m) 2^-24 relative, so 1e-6 is within
+        # reach of the rounding alone; 4e-6 is the bound
+        assert rel_l2(rho_g, O.cic_deposit(both, None, n, L)) < 4e-6, path
         edge = rho_g - O.cic_deposit(gal, None, n, L)   # the special positions' share
         assert rel_l2(edge, O.cic_deposit(grid, None, n, L)) < 1e-5, path
         # shift: Psi of the uniform catalogues alone (the special positions would pile ~200 tracers
