@@ -7,7 +7,8 @@ separately named kernel launch.
     python -m paper_1504_02591_gb300.profile_case --mesh 512 --iters 3 --repeat 2
 
 --sort-tracers M: the brick sort and sorted deposit alone, M uniform float64 positions on the mesh
-(3e7 on a 256^3 mesh is the benchmark's random catalogue in about 2.5 GB), deposited --repeat times.
+(3e7 on a 256^3 mesh is the benchmark's random catalogue in about 2.5 GB), deposited --repeat times;
+with --shift, then one update and --repeat sorted shifts of the same tracers (the retained sort).
 
     python -m paper_1504_02591_gb300.profile_case --mesh 256 --sort-tracers 30000000 --repeat 3
 """
@@ -22,6 +23,7 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--repeat", type=int, default=2)
     ap.add_argument("--sort-tracers", type=int, default=0)
+    ap.add_argument("--shift", action="store_true")
     args = ap.parse_args(argv)
     import torch
 
@@ -37,6 +39,13 @@ def main(argv=None):
         r.set_option(B.OPT_DEPOSIT_PATH, B.PATH_SORTED)
         for _ in range(args.repeat):
             r.deposit(pos, None, None, None)
+        if args.shift:
+            r.set_option(B.OPT_SHIFT_PATH, B.PATH_SORTED)
+            r.set_option(B.OPT_REUSE_SORT, 1)
+            r.smooth()
+            r.iterate(B.START_FFTA, 0.0, 1)
+            for _ in range(args.repeat):
+                r.shift(pos, False)
         torch.cuda.synchronize()
         print("ok", args.sort_tracers)
         r.close()
