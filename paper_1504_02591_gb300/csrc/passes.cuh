@@ -162,12 +162,35 @@ __global__ void __launch_bounds__(kZThreads, kZMinBlocks<N>) zpass_kernel(const 
       }
       if (lane < NC) qv[lane] = a.f[lane].Q[row];
       __syncwarp();
-      c2r_merge<N, NF>(s, qv, tw, lane);
-      __syncwarp();
+      if ((MODE == Z_PROJ || MODE == Z_RADIAL) && NC == 3 && !fin) {
+        // the projection needs only C = dx Psi_x + dy Psi_y and Psi_z (dx and dy are constant along
+        // the row), so two rows are transformed each way: C into line 0, Psi_z into line 1
+        const Geometry& g = a.g;
+        const float dx = g.los_mode == 1 ? g.los.x : g.off[row / N];
+        const float dy = g.los_mode == 1 ? g.los.y : g.off[N + row % N];
+        for (int m = lane; m < L; m += 32) {
+          const float2 p0 = s[Lay::phys(m, 0)], p1 = s[Lay::phys(m, 1)], p2 = s[Lay::phys(m, 2)];
+          s[Lay::phys(m, 0)] = make_float2(fmaf(dx, p0.x, dy * p1.x), fmaf(dx, p0.y, dy * p1.y));
+          s[Lay::phys(m, 1)] = p2;
+        }
+        if (lane == 0) {
+          const float2 q0 = qv[0], q1 = qv[1];
+          qv[0] = make_float2(fmaf(dx, q0.x, dy * q1.x), fmaf(dx, q0.y, dy * q1.y));
+          qv[1] = qv[2];
+        }
+        __syncwarp();
+        c2r_merge<N, 2>(s, qv, tw, lane);
+        __syncwarp();
 #pragma unroll
-      for (int q = 0; q < NF; ++q) Plan<L>::template run<1, 32, true, Lay, true>(s + q * Lay::kStride, tab);
+        for (int q = 0; q < 2; ++q) Plan<L>::template run<1, 32, true, Lay, true>(s + q * Lay::kStride, tab);
+      } else {
+        c2r_merge<N, NF>(s, qv, tw, lane);
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < NF; ++q) Plan<L>::template run<1, 32, true, Lay, true>(s + q * Lay::kStride, tab);
+      }
     } else if (MODE == Z_USTART || MODE == Z_WARM) {
-      // a radial displacement u: P_j = u r_j on the row, then the forward r2c of P.  Z_WARM adds to
+      // a radial displacement u: P = u r on the row, then its forward r2c.  Z_WARM adds to
       // u the trilinear (periodic) upsampling of a coarse correction: the coarse node J of level l
       // sits at fine index (J + 1/2) 2^l - 1/2 along each axis.
       const Geometry& g = a.g;
@@ -214,20 +237,23 @@ __global__ void __launch_bounds__(kZThreads, kZMinBlocks<N>) zpass_kernel(const 
           uu.x += add[0];
           uu.y += add[1];
         }
-        float r[2][3];
-#pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) {
-          if (g.los_mode == 1) {
-            r[h2][0] = g.los.x; r[h2][1] = g.los.y; r[h2][2] = g.los.z;
-          } else {
-            const float dz = g.off[2 * N + 2 * m + h2];
-            const float q = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float inv = q > 0.f ? rsqrtf(q) : 0.f;
-            r[h2][0] = dx * inv; r[h2][1] = dy * inv; r[h2][2] = dz * inv;
-          }
+        // P = u r = d psi with psi = w u (radial: w = 1/|d|; fixed LOS: d = the LOS, w = 1): line 0
+        // takes psi, line 1 dz psi (the forward pass below writes dx psi^, dy psi^ and (dz psi)^)
+        float dz0, dz1, w0, w1;
+        if (g.los_mode == 1) {
+          dz0 = dz1 = g.los.z;
+          w0 = w1 = 1.f;
+        } else {
+          dz0 = g.off[2 * N + 2 * m];
+          dz1 = g.off[2 * N + 2 * m + 1];
+          const float q0 = fmaf(dx, dx, fmaf(dy, dy, dz0 * dz0));
+          const float q1 = fmaf(dx, dx, fmaf(dy, dy, dz1 * dz1));
+          w0 = q0 > 0.f ? rsqrtf(q0) : 0.f;
+          w1 = q1 > 0.f ? rsqrtf(q1) : 0.f;
         }
-#pragma unroll
-        for (int q = 0; q < 3; ++q) s[Lay::phys(m, q)] = make_float2(uu.x * r[0][q], uu.y * r[1][q]);
+        const float p0 = uu.x * w0, p1 = uu.y * w1;
+        s[Lay::phys(m, 0)] = make_float2(p0, p1);
+        s[Lay::phys(m, 1)] = make_float2(dz0 * p0, dz1 * p1);
       }
       __syncwarp();
     } else if (MODE == Z_DELTA) {
@@ -287,33 +313,61 @@ __global__ void __launch_bounds__(kZThreads, kZMinBlocks<N>) zpass_kernel(const 
     }
 
     if (MODE == Z_RADIAL) {
-      // s holds Psi_j(x, y, z): the start's radial displacement coef (Psi.r), as a real row
+      // s holds C and Psi_z (as in the projection): the start's radial displacement
+      // u = coef w (C + dz Psi_z) = coef (Psi.r), as a real row
       const Geometry& g = a.g;
       const int ix = (int)(row / N), iy = (int)(row % N);
       const float dx = g.los_mode == 1 ? 0.f : g.off[ix], dy = g.los_mode == 1 ? 0.f : g.off[N + iy];
       for (int m = lane; m < L; m += 32) {
-        const float2 p0 = s[Lay::phys(m, 0)], p1 = s[Lay::phys(m, 1)], p2 = s[Lay::phys(m, 2)];
-        float rx0, ry0, rz0, rx1, ry1, rz1;
+        const float2 c = s[Lay::phys(m, 0)], pz = s[Lay::phys(m, 1)];
+        float dz0, dz1, w0, w1;
         if (g.los_mode == 1) {
-          rx0 = rx1 = g.los.x; ry0 = ry1 = g.los.y; rz0 = rz1 = g.los.z;
+          dz0 = dz1 = g.los.z;
+          w0 = w1 = 1.f;
         } else {
-          const float dz0 = g.off[2 * N + 2 * m], dz1 = g.off[2 * N + 2 * m + 1];
+          dz0 = g.off[2 * N + 2 * m];
+          dz1 = g.off[2 * N + 2 * m + 1];
           const float q0 = fmaf(dx, dx, fmaf(dy, dy, dz0 * dz0));
           const float q1 = fmaf(dx, dx, fmaf(dy, dy, dz1 * dz1));
-          const float i0 = q0 > 0.f ? rsqrtf(q0) : 0.f;
-          const float i1 = q1 > 0.f ? rsqrtf(q1) : 0.f;
-          rx0 = dx * i0; ry0 = dy * i0; rz0 = dz0 * i0;
-          rx1 = dx * i1; ry1 = dy * i1; rz1 = dz1 * i1;
+          w0 = q0 > 0.f ? rsqrtf(q0) : 0.f;
+          w1 = q1 > 0.f ? rsqrtf(q1) : 0.f;
         }
-        const float u0 = a.coef * fmaf(p0.x, rx0, fmaf(p1.x, ry0, p2.x * rz0));
-        const float u1 = a.coef * fmaf(p0.y, rx1, fmaf(p1.y, ry1, p2.y * rz1));
+        const float u0 = a.coef * (w0 * fmaf(dz0, pz.x, c.x));
+        const float u1 = a.coef * (w1 * fmaf(dz1, pz.y, c.y));
         reinterpret_cast<float2*>(a.u_out + row * N)[m] = make_float2(u0, u1);
       }
       __syncwarp();
       continue;
     }
 
-    if (MODE == Z_PROJ && !fin) {
+    if (MODE == Z_PROJ && NC == 3 && !fin) {
+      // s holds C and Psi_z at z = 2m (.x) and 2m + 1 (.y); with r = w d (radial: w = 1/|d|; fixed
+      // LOS: d = the LOS, w = 1), u = coef w (C + dz Psi_z) = coef (Psi.r) and P = u r = d psi with
+      // psi = w u (Eq. Nusser): line 0 takes psi, line 1 dz psi
+      const Geometry& g = a.g;
+      const float dx = g.los_mode == 1 ? g.los.x : g.off[row / N];
+      const float dy = g.los_mode == 1 ? g.los.y : g.off[N + row % N];
+      for (int m = lane; m < L; m += 32) {
+        const float2 c = s[Lay::phys(m, 0)], pz = s[Lay::phys(m, 1)];
+        float dz0, dz1, w0, w1;
+        if (g.los_mode == 1) {
+          dz0 = dz1 = g.los.z;
+          w0 = w1 = 1.f;
+        } else {
+          dz0 = g.off[2 * N + 2 * m];
+          dz1 = g.off[2 * N + 2 * m + 1];
+          const float q0 = fmaf(dx, dx, fmaf(dy, dy, dz0 * dz0));
+          const float q1 = fmaf(dx, dx, fmaf(dy, dy, dz1 * dz1));
+          w0 = q0 > 0.f ? rsqrtf(q0) : 0.f;
+          w1 = q1 > 0.f ? rsqrtf(q1) : 0.f;
+        }
+        const float p0 = a.coef * (w0 * fmaf(dz0, pz.x, c.x)) * w0;
+        const float p1 = a.coef * (w1 * fmaf(dz1, pz.y, c.y)) * w1;
+        s[Lay::phys(m, 0)] = make_float2(p0, p1);
+        s[Lay::phys(m, 1)] = make_float2(dz0 * p0, dz1 * p1);
+      }
+      __syncwarp();
+    } else if (MODE == Z_PROJ && !fin) {
       // s holds Psi_j(x, y, z), z = 2m (.x) and 2m + 1 (.y): P = coef (Psi.r) r (Eq. Nusser)
       const Geometry& g = a.g;
       const int ix = (int)(row / N), iy = (int)(row % N);
@@ -350,6 +404,27 @@ __global__ void __launch_bounds__(kZThreads, kZMinBlocks<N>) zpass_kernel(const 
         const int q = e / (L / 2), m2 = e % (L / 2);
         const float2 v0 = s[Lay::phys(2 * m2, q)], v1 = s[Lay::phys(2 * m2 + 1, q)];
         reinterpret_cast<float4*>(a.f[q].M + row * L)[m2] = make_float4(v0.x, v0.y, v1.x, v1.y);
+      }
+    } else if ((MODE == Z_PROJ || MODE == Z_USTART || MODE == Z_WARM) && NC == 3) {
+      // psi^ and (dz psi)^; P_x = dx psi^ and P_y = dy psi^ are scaled copies
+#pragma unroll
+      for (int q = 0; q < 2; ++q) Plan<L>::template run<1, 32, false, Lay, true>(s + q * Lay::kStride, tab);
+      r2c_split<N, 2>(s, qv, tw, lane);
+      __syncwarp();
+      const Geometry& g = a.g;
+      const float dx = g.los_mode == 1 ? g.los.x : g.off[row / N];
+      const float dy = g.los_mode == 1 ? g.los.y : g.off[N + row % N];
+      for (int m2 = lane; m2 < L / 2; m2 += 32) {
+        const float2 v0 = s[Lay::phys(2 * m2, 0)], v1 = s[Lay::phys(2 * m2 + 1, 0)];
+        const float2 z0 = s[Lay::phys(2 * m2, 1)], z1 = s[Lay::phys(2 * m2 + 1, 1)];
+        reinterpret_cast<float4*>(a.f[0].M + row * L)[m2] = make_float4(dx * v0.x, dx * v0.y, dx * v1.x, dx * v1.y);
+        reinterpret_cast<float4*>(a.f[1].M + row * L)[m2] = make_float4(dy * v0.x, dy * v0.y, dy * v1.x, dy * v1.y);
+        reinterpret_cast<float4*>(a.f[2].M + row * L)[m2] = make_float4(z0.x, z0.y, z1.x, z1.y);
+      }
+      if (lane == 0) {
+        a.f[0].Q[row] = cscale(qv[0], dx);
+        a.f[1].Q[row] = cscale(qv[0], dy);
+        a.f[2].Q[row] = qv[1];
       }
     } else {
 #pragma unroll
@@ -884,6 +959,43 @@ __device__ __forceinline__ void tile_store(const float2* s, float2* __restrict__
   }
 }
 
+// Stores of the k-space passes along y: the tile of G = iS/k^2 (one slot) goes out twice, scaled by
+// kdx into Psi_x and by kdz into Psi_z (kx and kz are constant along a y line; M tiles: kx = t.a,
+// kz = column; Nyquist tiles: kx = column, kz = N/2, whose derivative wavenumber is zero).
+template <int N, int C, int T>
+__device__ __forceinline__ void tile_store_xz(const float2* s, float2* __restrict__ Px, float2* __restrict__ Pz,
+                                              const Tile& t, float kf) {
+  using Lay = ColLayout<C>;
+  constexpr int H = N / 2;
+  auto kd = [&](int c, float& kdx, float& kdz) {
+    const int ix = t.isQ ? t.c0 + c : t.a, kz = t.isQ ? H : t.c0 + c;
+    kdx = (ix == H) ? 0.f : kf * (float)(ix < H ? ix : ix - N);
+    kdz = (kz == H) ? 0.f : kf * (float)kz;
+  };
+  if (t.cs == 1) {
+    for (int e = threadIdx.x; e < N * (C / 2); e += T) {
+      const int i = e / (C / 2), cp = e % (C / 2);
+      const float2 v0 = s[Lay::phys(i, 2 * cp)], v1 = s[Lay::phys(i, 2 * cp + 1)];
+      float ax0, az0, ax1, az1;
+      kd(2 * cp, ax0, az0);
+      kd(2 * cp + 1, ax1, az1);
+      const size_t gi = t.base + (size_t)i * t.ls + 2 * cp;
+      *reinterpret_cast<float4*>(Px + gi) = make_float4(ax0 * v0.x, ax0 * v0.y, ax1 * v1.x, ax1 * v1.y);
+      *reinterpret_cast<float4*>(Pz + gi) = make_float4(az0 * v0.x, az0 * v0.y, az1 * v1.x, az1 * v1.y);
+    }
+  } else {
+    for (int e = threadIdx.x; e < N * C; e += T) {
+      const int c = e / N, i = e % N;
+      float ax, az;
+      kd(c, ax, az);
+      const float2 v = s[Lay::phys(i, c)];
+      const size_t gi = t.base + (size_t)c * t.cs + (size_t)i * t.ls;
+      Px[gi] = cscale(v, ax);
+      Pz[gi] = cscale(v, az);
+    }
+  }
+}
+
 // Threads of a strided CTA.  The plain passes move one component per CTA in 16-column (128-byte)
 // tiles with 512 threads; the 3-component k-space passes use 4-column (32-byte) tiles with 256
 // threads so that three components fit three CTAs per SM.  The k-space passes run along y, whose
@@ -912,6 +1024,10 @@ __global__ void __launch_bounds__(SThreads<N, MODE, NARROW>::v, SThreads<N, MODE
   float2* s = tw + TABS;
   __shared__ double red_sh[T / 32];
   const int q0 = blockIdx.y;   // plain passes: the component this CTA transforms
+  // k-space passes along y: kx and kz are constant along the line, so the x and z components of
+  // k . P travel as A = kdx P_x + kdz P_z (one forward transform for two) and Psi_x, Psi_z leave as
+  // kdx G and kdz G of one inverse transform of G = iS/k^2
+  constexpr bool RED = (MODE == S_ITER || MODE == S_DELTA) && AXIS == AX_Y;
 
   if ((MODE == S_FWD || MODE == S_INV) && a.skip_flag && *a.skip_flag != 0) return;   // uniform
   for (int m = threadIdx.x; m < Plan<N>::kTab; m += T) tw[m] = a.tab[m];
@@ -925,6 +1041,20 @@ __global__ void __launch_bounds__(SThreads<N, MODE, NARROW>::v, SThreads<N, MODE
     for (int q = 0; q < NC; ++q) tile_load<N, C, T>(s + q * N * C, t.isQ ? a.f[q0 + q].Q : a.f[q0 + q].M, t);
   }
   __syncthreads();
+
+  if (MODE == S_ITER && RED) {
+    const float kf = a.g.kf;
+    for (int e = threadIdx.x; e < N * C; e += T) {
+      const int i = e / C, c = e % C;
+      const int ix = t.isQ ? t.c0 + c : t.a, kz = t.isQ ? H : t.c0 + c;
+      const float kdx = (ix == H) ? 0.f : kf * (float)(ix < H ? ix : ix - N);
+      const float kdz = (kz == H) ? 0.f : kf * (float)kz;
+      const int p = Lay::phys(i, c);
+      const float2 px = s[p], pz = s[2 * N * C + p];
+      s[p] = make_float2(fmaf(kdx, px.x, kdz * pz.x), fmaf(kdx, px.y, kdz * pz.y));
+    }
+    __syncthreads();
+  }
 
   // ---- S_ITER: fetch delta(k) and the previous source for this thread's elements now, so the
   // loads are in flight during the forward transforms instead of inside the element loop
@@ -948,7 +1078,7 @@ __global__ void __launch_bounds__(SThreads<N, MODE, NARROW>::v, SThreads<N, MODE
   // ---- forward transform along the line
   if (MODE == S_FWD || MODE == S_ITER) {
 #pragma unroll
-    for (int q = 0; q < NC; ++q) Plan<N>::template run<C, T, false, Lay>(s + q * N * C, tw);
+    for (int q = 0; q < ((MODE == S_ITER && RED) ? 2 : NC); ++q) Plan<N>::template run<C, T, false, Lay>(s + q * N * C, tw);
   } else if (MODE == S_DELTA) {
     if (!a.d_is_k) Plan<N>::template run<C, T, false, Lay>(s, tw);
   }
@@ -992,10 +1122,17 @@ __global__ void __launch_bounds__(SThreads<N, MODE, NARROW>::v, SThreads<N, MODE
           S = cscale(dk, a.inv_b);
         } else {
           const float2 dk = dkr[MODE == S_ITER ? k : 0];
-          const float2 px = s[p], py = s[N * C + p], pz = s[2 * N * C + p];
           // i k . P
-          const float dre = kdx * px.x + kdy * py.x + kdz * pz.x;
-          const float dim = kdx * px.y + kdy * py.y + kdz * pz.y;
+          float dre, dim;
+          if (RED) {   // slot 0 holds A = kdx P_x + kdz P_z
+            const float2 pa = s[p], py = s[N * C + p];
+            dre = fmaf(kdy, py.x, pa.x);
+            dim = fmaf(kdy, py.y, pa.y);
+          } else {
+            const float2 px = s[p], py = s[N * C + p], pz = s[2 * N * C + p];
+            dre = kdx * px.x + kdy * py.x + kdz * pz.x;
+            dim = kdx * px.y + kdy * py.y + kdz * pz.y;
+          }
           S = make_float2(fmaf(a.beta, -dim, dk.x * a.inv_b), fmaf(a.beta, dre, dk.y * a.inv_b));
         }
         if (k2 == 0.f) S = make_float2(0.f, 0.f);
@@ -1011,9 +1148,14 @@ __global__ void __launch_bounds__(SThreads<N, MODE, NARROW>::v, SThreads<N, MODE
         Sp[gi] = S;
         // Psi_j = i kd_j S / k^2, with the 1/N^3 of the inverse transform folded in
         const float2 iS = cscale(mul_i(S), inv_k2 * g.inv_n3);
-        s[p] = cscale(iS, kdx);
-        s[N * C + p] = cscale(iS, kdy);
-        s[2 * N * C + p] = cscale(iS, kdz);
+        if (RED) {
+          s[p] = iS;                           // G
+          s[N * C + p] = cscale(iS, kdy);      // Psi_y
+        } else {
+          s[p] = cscale(iS, kdx);
+          s[N * C + p] = cscale(iS, kdy);
+          s[2 * N * C + p] = cscale(iS, kdz);
+        }
       }
     }
     __syncthreads();
@@ -1022,12 +1164,17 @@ __global__ void __launch_bounds__(SThreads<N, MODE, NARROW>::v, SThreads<N, MODE
   // ---- inverse transform along the line
   if (MODE == S_INV || MODE == S_DELTA || MODE == S_ITER) {
 #pragma unroll
-    for (int q = 0; q < NS; ++q) Plan<N>::template run<C, T, true, Lay>(s + q * N * C, tw);
+    for (int q = 0; q < (RED ? 2 : NS); ++q) Plan<N>::template run<C, T, true, Lay>(s + q * N * C, tw);
   }
 
   // ---- store
+  if (RED) {
+    tile_store_xz<N, C, T>(s, t.isQ ? a.f[0].Q : a.f[0].M, t.isQ ? a.f[2].Q : a.f[2].M, t, a.g.kf);
+    tile_store<N, C, T>(s + N * C, t.isQ ? a.f[1].Q : a.f[1].M, t);
+  } else {
 #pragma unroll
-  for (int q = 0; q < NS; ++q) tile_store<N, C, T>(s + q * N * C, t.isQ ? a.f[q0 + q].Q : a.f[q0 + q].M, t);
+    for (int q = 0; q < NS; ++q) tile_store<N, C, T>(s + q * N * C, t.isQ ? a.f[q0 + q].Q : a.f[q0 + q].M, t);
+  }
 
   if (MODE == S_ITER) {
     double r0 = block_sum((double)d2, red_sh);
