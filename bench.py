@@ -525,8 +525,9 @@ def radial_ratio_table(m):
 def batch_bench(args):
     """The batched workload: 64 mocks (N from {256, 384, 512}, 2e5-1e6 galaxies, 30-50x randoms,
     per-mock b and f, shell surveys and periodic boxes) reconstructed to 1e-6 from the Eq. approx2
-    start in one recon_batch_run call (one CUDA graph).  The first call tunes each size class (not
-    timed); each timed call is the whole batch, from the call to its return."""
+    start in one recon_batch_run call (a CUDA graph per mock, launched back to back).  The first
+    call tunes each size class (not timed); each timed call is the whole batch, from the call to
+    its return."""
     import torch
     from paper_1504_02591_gb300 import binding, mocks
     work = mocks.batch_workload_device(64, 100)
@@ -557,7 +558,8 @@ def batch_bench(args):
            "classes": {n: {"mocks": d["mocks"], "mean_ms": round(statistics.mean(d["ms"]), 3),
                            "mean_updates": round(statistics.mean(d["n_iter"]), 2)} for n, d in sorted(by_n.items())},
            "plans": {str(n): binding.batch_plan(n) for n in (256, 384, 512)},
-           "launch": "one CUDA graph per call (a chain per size class, conditional WHILE loops)"}
+           "launch": "one CUDA graph per mock (conditional WHILE loop), launched back to back, smallest mesh "
+                     "first; the host builds each graph while the device runs the ones before it"}
     del work, res
     torch.cuda.empty_cache()
     return out

@@ -354,6 +354,11 @@ enum {
                                    paper's nearest grid point (Sec. 3: node floor(x N / L + 1/2)),
                                    always on the direct (unsorted) deposit kernel.  The shift still
                                    interpolates Psi with CIC.                                     */
+  RECON_OPT_FFT_RADIX = 9,      /* radix order of every FFT plan of the handle's mesh: 0 (default)
+                                   largest radix first; 1 smallest first, for N = 256 (4 8 8, its
+                                   z half-length plan 4 4 8) and N = 384 (6 8 8; 3 8 8), other
+                                   meshes UNSUPPORTED.  Same transforms up to float32 rounding;
+                                   the batch autotuner times both.                               */
   RECON_OPT_PLANE_BATCH = 6     /* register-fused path (N = 512): 0 (off) or 16, 32, 64 y-planes per
                                    batch; each update then runs its inverse x, projection and forward
                                    x passes batch by batch, so a batch's fields stay in the L2 between
@@ -368,7 +373,8 @@ enum {
 enum { RECON_PATH_DIRECT = 0, RECON_PATH_SORTED = 1 };
 
 /* Set a handle option (values 0 or 1, RECON_OPT_PLANE_BATCH 0/16/32/64); INVALID_ARG for an unknown
- * option or value. */
+ * option or value; UNSUPPORTED for RECON_OPT_FFT_RADIX 1 on a mesh with one radix order; CUDA if
+ * rebuilding the stage tables for another radix order fails. */
 recon_status recon_set_option(recon_handle* h, int option, int value);
 
 /* One reconstruction of a batch (recon_batch_run). */
@@ -391,22 +397,28 @@ typedef struct recon_batch_item {
 } recon_batch_item;
 
 /* Reconstruct many mocks of uneven mesh and catalogue sizes (deposit -> smooth -> iterate ->
- * shift each; the benchmark spec's batched form, no counterpart in the paper).  Items are grouped by mesh
- * side; each size class uses one handle (allocated with cudaMalloc, freed before returning).
- * When every catalogue and shift buffer is device memory, the whole batch runs as ONE CUDA graph
- * launched on `stream`: per size class a chain of its items (each deposit, smoothing, start, the
- * iteration as a conditional WHILE node with the device-side stopping test, and shifts), the
- * classes' chains independent of each other, so one item per class is in flight at a time; the
- * host waits once, at the end.  Otherwise the items run one after another through the handle API.
- * With autotune = 1, a size class not seen before in this process is first tuned on its first
- * item, before the batch runs and outside every item's time: the deposit path, the x-line FFT tile
- * width, at N = 512 the k-space kernel family (register-fused or generic), and the shift path; the
- * fastest are kept for the process (recon_batch_plan).  Returns the first error of any item
- * (per-item statuses in items[i].status), else OK. */
-recon_status recon_batch_run(recon_batch_item* items, int n_items, void* stream, int autotune);
+ * shift each; a batched form of the method with no counterpart in the paper).  Items are grouped by
+ * mesh side; each size class uses one handle (allocated with cudaMalloc, freed before returning).
+ * When every catalogue and shift buffer is device memory, each item is one CUDA graph (deposit,
+ * smoothing, start, the iteration as a conditional WHILE node with the device-side stopping test,
+ * shifts), and the graphs are launched on `stream` back to back, smallest mesh first: the host
+ * builds each item's graph while the device runs the items before it, and waits once, at the end.
+ * Otherwise the items run one after another through the handle API.  flags is a bitwise OR of
+ * RECON_BATCH_*.  With RECON_BATCH_TUNE, a size class not seen before in this process is first
+ * tuned on its first item, before the batch runs and outside every item's time: the deposit path,
+ * the x-line FFT tile width, at N = 512 the k-space kernel family (register-fused or generic), at
+ * N = 256 and 384 the FFT radix order, and the shift path; the fastest are kept for the process
+ * (recon_batch_plan).  With RECON_BATCH_ONE_GRAPH the whole batch is one CUDA graph, built before
+ * it is launched, with one chain of items per size class and the chains side by side (one item
+ * per class in flight).  Other bits: INVALID_ARG.  Returns the first error of any item (per-item
+ * statuses in items[i].status), else OK. */
+enum { RECON_BATCH_TUNE = 1, RECON_BATCH_ONE_GRAPH = 2 };
+recon_status recon_batch_run(recon_batch_item* items, int n_items, void* stream, int flags);
 
-/* The schedule the batch autotuner chose for mesh side nmesh (STATE if none yet). */
-recon_status recon_batch_plan(int nmesh, int* line_tile, int* deposit_path, int* shift_path);
+/* The schedule the batch autotuner chose for mesh side nmesh (STATE if none yet): the values of
+ * RECON_OPT_LINE_TILE, RECON_OPT_DEPOSIT_PATH, RECON_OPT_SHIFT_PATH and RECON_OPT_FFT_RADIX it
+ * runs the class with; any output pointer may be NULL. */
+recon_status recon_batch_plan(int nmesh, int* line_tile, int* deposit_path, int* shift_path, int* fft_radix);
 
 /* ---- Learned warm start: a small 3-D U-Net (no counterpart in the paper) ----------------------
  * The network maps, per node of a periodic mesh, 5 input channels — smoothed overdensity delta,

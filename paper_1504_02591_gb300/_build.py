@@ -19,7 +19,7 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "librecon_gb300.so")
 
-SOURCES = ["recon.cu", "cic.cu", "conv.cu", "bricks.cu", "loop.cu", "batch.cu", "diag.cu", "fd.cu", "unet.cu", "unet_tc.cu", "warm.cu", "inst_a.cu", "inst_b.cu", "inst_c.cu", "inst_d.cu", "inst_e.cu"]
+SOURCES = ["recon.cu", "cic.cu", "conv.cu", "bricks.cu", "loop.cu", "batch.cu", "diag.cu", "fd.cu", "unet.cu", "unet_tc.cu", "warm.cu", "inst_a.cu", "inst_b.cu", "inst_c.cu", "inst_d.cu", "inst_e.cu", "inst_f.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC,-O2",
          "-I" + os.path.join(ROOT, "include")] + ARCH

@@ -38,10 +38,11 @@ ABI_SYMBOLS = (
     "recon_radial_nbar", "recon_fkp_weights", "recon_fd_solve", "recon_start_coefficient",
 )
 OPT_DEPOSIT_PATH, OPT_SHIFT_PATH, OPT_GRAPH, OPT_LINE_TILE, OPT_KSPACE_GENERIC, OPT_REUSE_SORT = 0, 1, 2, 3, 4, 5
-OPT_PLANE_BATCH, OPT_ASSIGN, OPT_KITER_TMA = 6, 7, 8
+OPT_PLANE_BATCH, OPT_ASSIGN, OPT_KITER_TMA, OPT_FFT_RADIX = 6, 7, 8, 9
 ASSIGN_CIC, ASSIGN_NGP = 0, 1
 UNET_OPT_TENSOR_CORES = 0
 PATH_DIRECT, PATH_SORTED = 0, 1
+BATCH_TUNE, BATCH_ONE_GRAPH = 1, 2
 KERNEL_KINDS = ("deposit", "z_fwd", "z_inv", "z_delta", "z_proj", "z_final", "line_fwd", "line_inv",
                 "conv", "k_delta", "k_iter", "shift", "other", "sort")
 
@@ -103,7 +104,7 @@ def load(path: str = LIB_PATH):
     lib.recon_set_option.argtypes = [VP, I, I]
     lib.recon_reconfigure.argtypes = [VP, P(ReconParams)]
     lib.recon_batch_run.argtypes = [P(ReconBatchItem), I, VP, I]
-    lib.recon_batch_plan.argtypes = [I, P(I), P(I), P(I)]
+    lib.recon_batch_plan.argtypes = [I, P(I), P(I), P(I), P(I)]
     lib.recon_iterate_from.argtypes = [VP, VP, I, D, I, P(I), P(D)]
     lib.recon_start_features.argtypes = [VP, I, I, VP]
     lib.recon_get_radial.argtypes = [VP, I, VP]
@@ -482,8 +483,10 @@ class Recon:
         return self.iterate(start, tol, max_iter)
 
 
-def batch_run(mocks, start=START_FFTA, tol=1e-6, max_iter=80, autotune=True, stream=None, **over):
-    """Reconstruct a list of mocks in one recon_batch_run call.
+def batch_run(mocks, start=START_FFTA, tol=1e-6, max_iter=80, autotune=True, stream=None, one_graph=False,
+              **over):
+    """Reconstruct a list of mocks in one recon_batch_run call (one_graph: the whole batch as one
+    CUDA graph with the size classes side by side, RECON_BATCH_ONE_GRAPH).
 
     Each entry is a mocks.Mock (numpy catalogues, moved to the GPU first) or a dict with "params"
     (as Mock.params()), "gal" and "ran" (CUDA float64 (n, 3) tensors, "ran" None for uniform mean
@@ -515,7 +518,8 @@ def batch_run(mocks, start=START_FFTA, tol=1e-6, max_iter=80, autotune=True, str
         items[i].start, items[i].tol, items[i].max_iter, items[i].out_on_device = int(start), float(tol), int(max_iter), 1
         outs.append((sg, sr))
     st = (stream or torch.cuda.current_stream()).cuda_stream
-    status = lib.recon_batch_run(items, len(mocks), C.c_void_p(st), int(bool(autotune)))
+    flags = (BATCH_TUNE if autotune else 0) | (BATCH_ONE_GRAPH if one_graph else 0)
+    status = lib.recon_batch_run(items, len(mocks), C.c_void_p(st), flags)
     torch.cuda.synchronize()
     res = []
     for i in range(len(mocks)):
@@ -526,9 +530,10 @@ def batch_run(mocks, start=START_FFTA, tol=1e-6, max_iter=80, autotune=True, str
 
 def batch_plan(nmesh):
     lib = load()
-    a, b, c = C.c_int(), C.c_int(), C.c_int()
-    st = lib.recon_batch_plan(int(nmesh), C.byref(a), C.byref(b), C.byref(c))
-    return None if st != OK else dict(line_tile=a.value, deposit_path=b.value, shift_path=c.value)
+    a, b, c, d = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    st = lib.recon_batch_plan(int(nmesh), C.byref(a), C.byref(b), C.byref(c), C.byref(d))
+    return None if st != OK else dict(line_tile=a.value, deposit_path=b.value, shift_path=c.value,
+                                      fft_radix=d.value)
 
 
 class UNet:

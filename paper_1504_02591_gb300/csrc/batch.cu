@@ -2,18 +2,20 @@
 //
 // Mocks are grouped by mesh side.  Each size class gets one persistent handle (its buffers and
 // twiddle tables are reused; each mock's smoothing and line-of-sight tables are uploaded once, for
-// the whole batch).  When every catalogue and output is in device memory, the whole batch is one
-// CUDA graph: per class, a chain of mocks, each its deposit, smoothing, start, the iteration as a
-// conditional WHILE node with the device-side stopping test, and its shifts; the classes' chains
-// are independent branches, so at most one mock per class is in flight.  The host waits once, for
-// the whole batch; per-mock results and globaltimer stamps are written on the device.  Otherwise
-// the mocks run one after another through the handle API.
+// the whole batch).  When every catalogue and output is in device memory, each mock is one CUDA
+// graph (its deposit, smoothing, start, the iteration as a conditional WHILE node with the
+// device-side stopping test, and its shifts), and the graphs go onto the stream back to back,
+// smallest mesh first: the host builds and instantiates mock i + 1's graph while the device runs
+// the mocks before it, and waits once, for the whole batch.  Per-mock results and globaltimer stamps
+// are written on the device.  With RECON_BATCH_ONE_GRAPH the whole batch is instead one graph built
+// before anything runs, with one chain per size class, the chains side by side.  With any catalogue
+// or output in host memory the mocks run one after another through the handle API.
 //
 // Before the first mock of a size class not seen before in this process, the autotuner times the
 // class's candidate schedules on that mock (outside the items' times) and keeps the fastest for the
 // process: the deposit path (direct atomics or brick-sorted), the x-line FFT tile width (16 or 8
-// columns), for N = 512 the k-space kernel family (register-fused or generic staged) and the shift
-// path.
+// columns), for N = 512 the k-space kernel family (register-fused or generic staged), for N = 256
+// and 384 the FFT radix order (largest or smallest radix first) and the shift path.
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -29,6 +31,7 @@ struct Plan {
   int deposit_path = RECON_PATH_DIRECT;
   int shift_path = RECON_PATH_SORTED;
   int kspace_generic = 0;
+  int fft_radix = 0;
 };
 
 std::mutex g_plan_mu;
@@ -60,6 +63,7 @@ void apply_plan(recon_handle* h, const Plan& p) {
   recon_set_option(h, RECON_OPT_DEPOSIT_PATH, p.deposit_path);
   recon_set_option(h, RECON_OPT_SHIFT_PATH, p.shift_path);
   recon_set_option(h, RECON_OPT_KSPACE_GENERIC, p.kspace_generic);
+  recon_set_option(h, RECON_OPT_FFT_RADIX, p.fft_radix);
 }
 
 // Time the candidate schedules of one size class on one mock (each timed run after a warm run).
@@ -88,25 +92,32 @@ recon_status tune(recon_handle* h, recon_batch_item& it, cudaStream_t st, Plan* 
   // iteration schedules, each on the same delta(k) for a fixed number of updates
   best = 1e30f;
   const int fams = it.params.nmesh[0] == 512 ? 2 : 1;   // the register-fused family exists at N = 512
+  // the alternative radix order exists where the option accepts it
+  const int orders = recon_set_option(h, RECON_OPT_FFT_RADIX, 1) == RECON_OK ? 2 : 1;
   int n_it = 0;
   double rel = 0.0;
-  for (int fam = 0; fam < fams; ++fam) {
-    for (int tile : {0, 1}) {
-      recon_set_option(h, RECON_OPT_KSPACE_GENERIC, fam);
-      recon_set_option(h, RECON_OPT_LINE_TILE, tile);
-      recon_status si = recon_iterate(h, it.start, 0.0, 4, &n_it, &rel);   // warm (and graph build)
-      if (si != RECON_OK) return si;
-      t.start();
-      si = recon_iterate(h, it.start, 0.0, 4, &n_it, &rel);
-      const float ms = t.stop();
-      if (si != RECON_OK) return si;
-      if (ms < best) {
-        best = ms;
-        plan->line_tile = tile;
-        plan->kspace_generic = fam;
+  for (int order = 0; order < orders; ++order) {
+    if ((s = recon_set_option(h, RECON_OPT_FFT_RADIX, order)) != RECON_OK) return s;
+    for (int fam = 0; fam < fams; ++fam) {
+      for (int tile : {0, 1}) {
+        recon_set_option(h, RECON_OPT_KSPACE_GENERIC, fam);
+        recon_set_option(h, RECON_OPT_LINE_TILE, tile);
+        recon_status si = recon_iterate(h, it.start, 0.0, 4, &n_it, &rel);   // warm (and graph build)
+        if (si != RECON_OK) return si;
+        t.start();
+        si = recon_iterate(h, it.start, 0.0, 4, &n_it, &rel);
+        const float ms = t.stop();
+        if (si != RECON_OK) return si;
+        if (ms < best) {
+          best = ms;
+          plan->line_tile = tile;
+          plan->kspace_generic = fam;
+          plan->fft_radix = order;
+        }
       }
     }
   }
+  if ((s = recon_set_option(h, RECON_OPT_FFT_RADIX, plan->fft_radix)) != RECON_OK) return s;
   recon_set_option(h, RECON_OPT_KSPACE_GENERIC, plan->kspace_generic);
   recon_set_option(h, RECON_OPT_LINE_TILE, plan->line_tile);
   // shift path, on the randoms (or the galaxies when there are none)
@@ -167,8 +178,10 @@ struct SizeClass {
 
 }  // namespace
 
-extern "C" recon_status recon_batch_run(recon_batch_item* items, int n_items, void* stream, int autotune) {
+extern "C" recon_status recon_batch_run(recon_batch_item* items, int n_items, void* stream, int flags) {
   if (n_items < 0 || (n_items > 0 && !items)) return RECON_ERR_INVALID_ARG;
+  if (flags & ~(RECON_BATCH_TUNE | RECON_BATCH_ONE_GRAPH)) return RECON_ERR_INVALID_ARG;
+  const bool autotune = flags & RECON_BATCH_TUNE, one_graph = flags & RECON_BATCH_ONE_GRAPH;
   cudaStream_t st = (cudaStream_t)stream;
   for (int i = 0; i < n_items; ++i) {
     items[i].status = RECON_ERR_STATE;
@@ -245,6 +258,7 @@ extern "C" recon_status recon_batch_run(recon_batch_item* items, int n_items, vo
     rg::BatchSlot* slots = nullptr;
     cudaGraph_t top = nullptr;
     cudaGraphExec_t exec = nullptr;
+    std::vector<cudaGraphExec_t> execs;   // one per mock, launched back to back
     recon_status s = RECON_OK;
     do {
       if (cudaMalloc(&dtab, std::max<size_t>(host.size(), 1) * sizeof(float)) != cudaSuccess ||
@@ -254,7 +268,11 @@ extern "C" recon_status recon_batch_run(recon_batch_item* items, int n_items, vo
       }
       if (cudaMemcpyAsync(dtab, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess ||
           cudaMemsetAsync(slots, 0, n_items * sizeof(rg::BatchSlot), st) != cudaSuccess ||
-          cudaStreamSynchronize(st) != cudaSuccess || cudaGraphCreate(&top, 0) != cudaSuccess) {
+          cudaStreamSynchronize(st) != cudaSuccess) {
+        s = RECON_ERR_CUDA;
+        break;
+      }
+      if (one_graph && cudaGraphCreate(&top, 0) != cudaSuccess) {
         s = RECON_ERR_CUDA;
         break;
       }
@@ -263,16 +281,45 @@ extern "C" recon_status recon_batch_run(recon_batch_item* items, int n_items, vo
         cudaGraphNode_t last = nullptr;
         for (int k : c.idx) {
           rg::BatchJob job{&items[k], dtab + tabs[k].taps, tabs[k].t0, tabs[k].ntap, dtab + tabs[k].off, slots + k};
-          const recon_status sj = rg::batch_append(c.h, top, &last, job);
+          if (one_graph) {
+            const recon_status sj = rg::batch_append(c.h, top, &last, job);
+            if (sj != RECON_OK) {
+              items[k].status = sj;
+              fail(sj);
+            }
+            continue;
+          }
+          // this mock's own graph, on the stream behind the mocks already launched
+          cudaGraph_t g = nullptr;
+          cudaGraphExec_t ex = nullptr;
+          cudaGraphNode_t none = nullptr;
+          if (cudaGraphCreate(&g, 0) != cudaSuccess) {
+            s = RECON_ERR_CUDA;
+            break;
+          }
+          const recon_status sj = rg::batch_append(c.h, g, &none, job);
           if (sj != RECON_OK) {
             items[k].status = sj;
             fail(sj);
+          } else if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess || cudaGraphLaunch(ex, st) != cudaSuccess) {
+            s = RECON_ERR_CUDA;
           }
+          cudaGraphDestroy(g);
+          if (ex) execs.push_back(ex);
+          if (s != RECON_OK) break;
         }
         rg::batch_restore(c.h);
+        if (s != RECON_OK) break;
       }
-      if (cudaGraphInstantiate(&exec, top, 0) != cudaSuccess || cudaGraphLaunch(exec, st) != cudaSuccess ||
-          cudaStreamSynchronize(st) != cudaSuccess) {
+      if (s != RECON_OK) {
+        cudaStreamSynchronize(st);   // the mocks already launched finish before their buffers go
+        break;
+      }
+      if (one_graph && (cudaGraphInstantiate(&exec, top, 0) != cudaSuccess || cudaGraphLaunch(exec, st) != cudaSuccess)) {
+        s = RECON_ERR_CUDA;
+        break;
+      }
+      if (cudaStreamSynchronize(st) != cudaSuccess) {
         s = RECON_ERR_CUDA;
         break;
       }
@@ -296,6 +343,7 @@ extern "C" recon_status recon_batch_run(recon_batch_item* items, int n_items, vo
         }
       }
     } while (0);
+    for (cudaGraphExec_t ex : execs) cudaGraphExecDestroy(ex);
     if (exec) cudaGraphExecDestroy(exec);
     if (top) cudaGraphDestroy(top);
     if (slots) cudaFree(slots);
@@ -320,12 +368,14 @@ extern "C" recon_status recon_batch_run(recon_batch_item* items, int n_items, vo
   return first_error;
 }
 
-extern "C" recon_status recon_batch_plan(int nmesh, int* line_tile, int* deposit_path, int* shift_path) {
+extern "C" recon_status recon_batch_plan(int nmesh, int* line_tile, int* deposit_path, int* shift_path,
+                                         int* fft_radix) {
   std::lock_guard<std::mutex> lock(g_plan_mu);
   auto f = g_plans.find(nmesh);
   if (f == g_plans.end()) return RECON_ERR_STATE;
   if (line_tile) *line_tile = f->second.line_tile;
   if (deposit_path) *deposit_path = f->second.deposit_path;
   if (shift_path) *shift_path = f->second.shift_path;
+  if (fft_radix) *fft_radix = f->second.fft_radix;
   return RECON_OK;
 }

@@ -11,7 +11,21 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+// Radix order of the plans of the mesh sides that have two (see the plan table at the end): 0 the
+// default, largest radix first; 1 the alternative, smallest radix first.  A translation unit
+// compiles one order, and its kernels live in that order's inline namespace, so the kernels of
+// both orders link into one library under distinct names.
+#ifndef RG_RADIX_ORDER
+#define RG_RADIX_ORDER 0
+#endif
+#if RG_RADIX_ORDER == 0
+#define RG_KNS order0
+#else
+#define RG_KNS order1
+#endif
+
 namespace rg {
+inline namespace RG_KNS {
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -251,12 +265,20 @@ RG_PLAN(32, 8, 4)
 RG_PLAN(48, 8, 6)
 RG_PLAN(64, 8, 8)
 RG_PLAN(96, 8, 4, 3)
+#if RG_RADIX_ORDER == 0
 RG_PLAN(128, 8, 4, 4)
 RG_PLAN(192, 8, 8, 3)
 RG_PLAN(256, 8, 8, 4)
 RG_PLAN(384, 8, 8, 6)
+#else   // the 256 and 384 meshes (and their half-length z plans) smallest radix first
+RG_PLAN(128, 4, 4, 8)
+RG_PLAN(192, 3, 8, 8)
+RG_PLAN(256, 4, 8, 8)
+RG_PLAN(384, 6, 8, 8)
+#endif
 RG_PLAN(512, 8, 8, 8)
 RG_PLAN(1024, 8, 8, 4, 4)
 #undef RG_PLAN
 
+}  // namespace RG_KNS
 }  // namespace rg

@@ -13,6 +13,7 @@
 #include "types.h"
 
 namespace rg {
+inline namespace RG_KNS {   // the radix order's namespace (fft_core.cuh)
 
 constexpr int kZThreads = 256;
 
@@ -2009,4 +2010,5 @@ struct MeshImpl {
   }
 };
 
+}  // namespace RG_KNS
 }  // namespace rg

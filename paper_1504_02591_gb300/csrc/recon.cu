@@ -38,6 +38,17 @@ const MeshKernels* mesh_kernels_256();
 const MeshKernels* mesh_kernels_384();
 const MeshKernels* mesh_kernels_512();
 const MeshKernels* mesh_kernels_1024();
+const MeshKernels* mesh_kernels_256_order1();
+const MeshKernels* mesh_kernels_384_order1();
+
+// The kernels of mesh side n in radix order `order` (1: the alternative order, where one is built).
+const MeshKernels* mesh_kernels_order(int n, int order) {
+  if (order == 0) return mesh_kernels(n);
+  if (order != 1) return nullptr;
+  if (n == 256) return mesh_kernels_256_order1();
+  if (n == 384) return mesh_kernels_384_order1();
+  return nullptr;
+}
 
 const MeshKernels* mesh_kernels(int n) {
   switch (n) {
@@ -78,8 +89,12 @@ Layout layout_for(int n) {
   l.field = l.field_M + l.field_Q;
   l.wfield = mk->kspace_fused ? l.field : 0;   // register-fused path: Psi_z in C form (fourth vector field)
   l.tw = align256((size_t)n * sizeof(float2));
-  l.tabs = align256((size_t)mk->tab_s * sizeof(float2) + 16);
-  l.tabz = align256((size_t)mk->tab_z * sizeof(float2) + 16);
+  // stage tables: room for either radix order (recon_set_option can switch)
+  const MeshKernels* alt = mesh_kernels_order(n, 1);
+  const int tab_s = alt && alt->tab_s > mk->tab_s ? alt->tab_s : mk->tab_s;
+  const int tab_z = alt && alt->tab_z > mk->tab_z ? alt->tab_z : mk->tab_z;
+  l.tabs = align256((size_t)tab_s * sizeof(float2) + 16);
+  l.tabz = align256((size_t)tab_z * sizeof(float2) + 16);
   l.off = align256((size_t)3 * n * sizeof(float));
   l.taps = align256((size_t)n * sizeof(float));
   // reduction slots, the loop state, the finalize block sums and counter
@@ -160,6 +175,7 @@ struct recon_handle {
   int plane_batch = 0;   // register-fused path: y-planes per batch of the x -> z -> x passes (0: off)
   int assign = 0;        // mass assignment of the deposit: 0 CIC, 1 NGP (the paper's binning)
   int kiter_tma = 0;     // N = 512 fused path: 1 streams the source update's inputs by TMA
+  int radix_order = 0;   // FFT plans: 0 default, 1 the alternative order (mk is that order's table)
   bool tmaps_ok = false; // its tensor maps were built
   KIterMaps tmaps{};
   int reuse_sort = 0;
@@ -189,12 +205,13 @@ struct recon_handle {
   struct GraphKey {
     uint32_t coef0_bits;
     const float* u0;
-    int level, max_iter, d_is_k, generic, narrow, planes, tma;
+    int level, max_iter, d_is_k, generic, narrow, planes, tma, radix;
     uint64_t tol_bits;
     uint64_t epoch;
     bool operator==(const GraphKey& o) const {
       return coef0_bits == o.coef0_bits && u0 == o.u0 && level == o.level && max_iter == o.max_iter &&
              d_is_k == o.d_is_k && generic == o.generic && narrow == o.narrow && planes == o.planes && tma == o.tma &&
+             radix == o.radix &&
              tol_bits == o.tol_bits &&
              epoch == o.epoch;
     }
@@ -796,11 +813,13 @@ recon_status recon_reset_timing(recon_handle* h) {
 }
 
 recon_status set_plane_batch(recon_handle* h, int value);
+recon_status set_radix_order(recon_handle* h, int value);
 
 recon_status recon_set_option(recon_handle* h, int option, int value) {
   if (!h) return RECON_ERR_INVALID_ARG;
   if (option == RECON_OPT_PLANE_BATCH) return set_plane_batch(h, value);
   if (value != 0 && value != 1) return RECON_ERR_INVALID_ARG;
+  if (option == RECON_OPT_FFT_RADIX) return set_radix_order(h, value);
   if (option == RECON_OPT_DEPOSIT_PATH) h->deposit_path = value;
   else if (option == RECON_OPT_SHIFT_PATH) h->shift_path = value;
   else if (option == RECON_OPT_GRAPH) h->use_graph = value;
@@ -810,6 +829,18 @@ recon_status recon_set_option(recon_handle* h, int option, int value) {
   else if (option == RECON_OPT_ASSIGN) h->assign = value;
   else if (option == RECON_OPT_KITER_TMA) h->kiter_tma = value;
   else return RECON_ERR_INVALID_ARG;
+  return RECON_OK;
+}
+
+// Switch the FFT plans to another radix order: that order's kernels, and its stage tables rebuilt
+// (in place: the layout has room for either order) on the handle's stream.
+recon_status set_radix_order(recon_handle* h, int value) {
+  const MeshKernels* mk = mesh_kernels_order(h->n, value);
+  if (!mk) return RECON_ERR_UNSUPPORTED;
+  if (value == h->radix_order) return RECON_OK;
+  RG_CUDA(mk->build_tables(h->tw, h->tabs, h->tabz, h->st));
+  h->mk = mk;
+  h->radix_order = value;
   return RECON_OK;
 }
 
@@ -1062,6 +1093,7 @@ recon_status iterate_graph(recon_handle* h, const StartSpec& sp, double tol, int
   key.narrow = h->narrow_lines;
   key.planes = h->plane_batch;
   key.tma = h->kiter_tma;
+  key.radix = h->radix_order;
   key.epoch = h->epoch;
   if (!(h->gcache.valid && h->gcache.key == key)) {
     RG_TRY(build_graph(h, sp, tol, max_iter));

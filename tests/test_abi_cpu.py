@@ -28,6 +28,32 @@ def test_header_and_binding_agree():
     assert declared_symbols() == sorted(binding.ABI_SYMBOLS)
 
 
+def declared_constants():
+    src = open(os.path.join(ROOT, "include", "recon.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return {k: int(v) for k, v in re.findall(r"\bRECON_([A-Z0-9_]+)\s*=\s*(-?\d+)", src)}
+
+
+def test_header_constants_and_binding_agree():
+    consts = declared_constants()
+    assert len(consts) > 40
+    kinds = [k.replace("_", "") for k in binding.KERNEL_KINDS]
+    for name, value in consts.items():
+        if name == "K_COUNT":
+            assert value == len(binding.KERNEL_KINDS)
+        elif name.startswith("K_"):
+            assert kinds.index(name[2:].replace("_", "").lower()) == value, name
+        else:
+            assert getattr(binding, name) == value, name
+
+
+def test_batch_flags_are_validated(lib):
+    lib.recon_batch_run.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int]
+    for bad in (4, 8, -1):   # rejected before any device work
+        assert lib.recon_batch_run(None, 0, None, bad) == binding.ERR_INVALID_ARG
+    assert lib.recon_batch_run(None, -1, None, 0) == binding.ERR_INVALID_ARG
+
+
 def test_library_exports_every_declared_symbol(lib):
     for name in declared_symbols():
         assert hasattr(lib, name), name

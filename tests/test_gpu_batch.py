@@ -45,6 +45,20 @@ def test_batch_matches_single_runs(lib, batch_mocks):
         assert np.abs(r["shift_ran"].cpu().numpy() - sr).max() <= 1e-4
 
 
+def test_batch_one_graph_matches(lib, batch_mocks):
+    """RECON_BATCH_ONE_GRAPH (the whole batch as one graph, size classes side by side) gives the same
+    reconstructions as the per-mock graphs launched back to back (up to the float32 order of the
+    deposit atomics)."""
+    from paper_1504_02591_gb300 import binding as B
+    s0, r0 = B.batch_run(batch_mocks, start=B.START_FFTA, tol=1e-6, max_iter=60)
+    s1, r1 = B.batch_run(batch_mocks, start=B.START_FFTA, tol=1e-6, max_iter=60, one_graph=True)
+    assert s0 == B.OK and s1 == B.OK
+    for a, b in zip(r0, r1):
+        assert b["status"] == a["status"] and abs(a["n_iter"] - b["n_iter"]) <= 1 and b["ms"] > 0
+        assert np.abs(a["shift_gal"].cpu().numpy() - b["shift_gal"].cpu().numpy()).max() <= 1e-4
+        assert np.abs(a["shift_ran"].cpu().numpy() - b["shift_ran"].cpu().numpy()).max() <= 1e-4
+
+
 def test_batch_item_vs_oracle(lib, batch_mocks):
     from paper_1504_02591_gb300 import binding as B
     m = batch_mocks[0]

@@ -25,11 +25,20 @@ PSI_TOL = 1e-5
 SHIFT_TOL = 1e-4
 
 
-def test_384_survey_shell_vs_oracle(lib):
-    from paper_1504_02591_gb300 import binding as B
+@pytest.fixture(scope="module")
+def shell384():
     n = 384
-    m = mocks.scaled_shell(n, 6.84 * n, 200_000, 30, 2.1, 0.65, 140)
+    return mocks.scaled_shell(n, 6.84 * n, 200_000, 30, 2.1, 0.65, 140), {}
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_384_survey_shell_vs_oracle(lib, shell384, order):
+    """Both radix orders of the 384^3 plans (8 8 6 and 6 8 8, RECON_OPT_FFT_RADIX) against the
+    oracle."""
+    from paper_1504_02591_gb300 import binding as B
+    m, cache = shell384
     r = B.Recon.from_mock(m)
+    r.set_option(B.OPT_FFT_RADIX, order)
     gal = torch.from_numpy(m.galaxies.pos).cuda()
     ran = torch.from_numpy(m.randoms.pos).cuda()
     r.deposit(gal, None, ran, None)
@@ -44,18 +53,56 @@ def test_384_survey_shell_vs_oracle(lib):
     sr = r.shift(ran[torch.from_numpy(ir).cuda()], False).cpu().numpy()
     r.close()
     kw = dict(start=O.START_FFTA, tol=0.0, max_iter=3, shift=False)
-    ref = O.reconstruct(m.params(), m.galaxies.pos, None, m.randoms.pos, None, **kw)
-    ref = reconstruct_same_branch(m, ref, delta, **kw)
+    if "ref" not in cache:
+        cache["ref"] = O.reconstruct(m.params(), m.galaxies.pos, None, m.randoms.pos, None, **kw)
+    ref = reconstruct_same_branch(m, cache["ref"], delta, **kw)
     e_d, e_p = rel_l2(delta, ref["delta"]), rel_l2(psi, ref["psi"])
     p = m.params()
     dg = O.shift_vectors(ref["psi"], m.galaxies.pos, p["L"], p["f"], p["observer"], p["los_mode"], True)
     dr = O.shift_vectors(ref["psi"], m.randoms.pos[ir], p["L"], p["f"], p["observer"], p["los_mode"], False)
     e_g, e_r = float(np.abs(sg - dg).max()), float(np.abs(sr - dr).max())
-    print(f"384^3 shell: delta {e_d:.2e}, Psi {e_p:.2e}, shifts {e_g:.2e} / {e_r:.2e} Mpc/h")
+    print(f"384^3 shell, radix order {order}: delta {e_d:.2e}, Psi {e_p:.2e}, shifts {e_g:.2e} / {e_r:.2e} Mpc/h")
     assert n_it == 3
     assert e_d < 1e-5 and e_p <= PSI_TOL
     assert e_g <= SHIFT_TOL and e_r <= SHIFT_TOL
     assert np.allclose(trace, ref["rel"], rtol=1e-3, atol=0)
+
+
+def test_256_radix_orders_vs_oracle(lib):
+    """The 256^3 plans in both radix orders (8 8 4 and 4 8 8, z plans 8 4 4 and 4 4 8) on a
+    periodic box with randoms, 4 updates from the plain start, against the oracle; switching the
+    order on a live handle rebuilds the stage tables."""
+    from paper_1504_02591_gb300 import binding as B
+    m = mocks.periodic_box(1500.0, 256, 300_000, 3_000_000, 1.9, 0.72, 12.0, (-800.0, 750.0, 750.0), 11, 12, 13)
+    gal = torch.from_numpy(m.galaxies.pos).cuda()
+    ran = torch.from_numpy(m.randoms.pos).cuda()
+    r = B.Recon.from_mock(m)
+    out = {}
+    for order in (1, 0, 1):
+        r.set_option(B.OPT_FFT_RADIX, order)
+        r.deposit(gal, None, ran, None)
+        r.smooth()
+        delta = r.get_field(B.FIELD_DELTA).cpu().numpy()
+        r.iterate(B.START_PLAIN, 0.0, 4)
+        out.setdefault(order, []).append((delta, r.get_psi().cpu().numpy(), r.shift(gal, True).cpu().numpy()))
+    r.close()
+    kw = dict(start=O.START_PLAIN, tol=0.0, max_iter=4)
+    ref = O.reconstruct(m.params(), m.galaxies.pos, None, m.randoms.pos, None, shift=False, **kw)
+    p = m.params()
+    for order, runs in out.items():
+        for delta, psi, sg in runs:
+            rb = reconstruct_same_branch(m, ref, delta, shift=False, **kw)
+            dg = O.shift_vectors(rb["psi"], m.galaxies.pos, p["L"], p["f"], p["observer"], p["los_mode"], True)
+            e_p, e_g = rel_l2(psi, rb["psi"]), float(np.abs(sg - dg).max())
+            print(f"256^3 box, radix order {order}: Psi {e_p:.2e}, shifts {e_g:.2e} Mpc/h")
+            assert e_p <= PSI_TOL and e_g <= SHIFT_TOL
+    with pytest.raises(B.ReconError) as e:
+        r2 = B.Recon(64, 1000.0, 2.0, 0.7, 15.0, (0.0, 0.0, 0.0))   # one radix order only
+        try:
+            r2.set_option(B.OPT_FFT_RADIX, 1)
+        finally:
+            r2.close()
+    assert e.value.status == B.ERR_UNSUPPORTED
 
 
 @pytest.fixture(scope="module")
