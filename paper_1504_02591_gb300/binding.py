@@ -484,14 +484,16 @@ class Recon:
 
 
 def batch_run(mocks, start=START_FFTA, tol=1e-6, max_iter=80, autotune=True, stream=None, one_graph=False,
-              **over):
+              out=None, **over):
     """Reconstruct a list of mocks in one recon_batch_run call (one_graph: the whole batch as one
     CUDA graph with the size classes side by side, RECON_BATCH_ONE_GRAPH).
 
     Each entry is a mocks.Mock (numpy catalogues, moved to the GPU first) or a dict with "params"
     (as Mock.params()), "gal" and "ran" (CUDA float64 (n, 3) tensors, "ran" None for uniform mean
-    density).  Returns the batch status and, per mock, a dict with n_iter, rel, status, ms and the
-    galaxy / random shift tensors."""
+    density).  out, if given, holds per mock the (galaxy, random) shift tensors to write into
+    (float32 CUDA (n, 3), contiguous; None for a mock without randoms), e.g. those of an earlier
+    call; otherwise they are allocated.  Returns the batch status and, per mock, a dict with n_iter,
+    rel, status, ms and the galaxy / random shift tensors."""
     import torch
     lib = load()
     items = (ReconBatchItem * len(mocks))()
@@ -507,13 +509,24 @@ def batch_run(mocks, start=START_FFTA, tol=1e-6, max_iter=80, autotune=True, str
         items[i].params = make_params(p["n"], p["L"], p["b"], p["f"], p["R"], p["observer"], p["los_mode"],
                                       p["periodic"], p["mask_frac"], p["lognormal"], p["uniform"])
         items[i].gal = _catalog(g, None, keep)
-        sg = torch.empty((len(g), 3), dtype=torch.float32, device="cuda")
+        has_ran = r is not None and not p["uniform"]
+        if out is not None:
+            sg, sr = out[i]
+            for t, src in ((sg, g), (sr, r if has_ran else None)):
+                if src is None:
+                    continue
+                if (t is None or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous()
+                        or tuple(t.shape) != (len(src), 3)):
+                    raise ValueError(f"batch_run: out[{i}] must hold float32 CUDA (n, 3) tensors")
+        else:
+            sg = torch.empty((len(g), 3), dtype=torch.float32, device="cuda")
+            sr = torch.empty((len(r), 3), dtype=torch.float32, device="cuda") if has_ran else None
         items[i].shift_gal = sg.data_ptr()
-        sr = None
-        if r is not None and not p["uniform"]:
+        if has_ran:
             items[i].ran = _catalog(r, None, keep)
-            sr = torch.empty((len(r), 3), dtype=torch.float32, device="cuda")
             items[i].shift_ran = sr.data_ptr()
+        else:
+            sr = None
         keep += [g, r, sg, sr]
         items[i].start, items[i].tol, items[i].max_iter, items[i].out_on_device = int(start), float(tol), int(max_iter), 1
         outs.append((sg, sr))

@@ -57,6 +57,15 @@ def test_batch_one_graph_matches(lib, batch_mocks):
         assert b["status"] == a["status"] and abs(a["n_iter"] - b["n_iter"]) <= 1 and b["ms"] > 0
         assert np.abs(a["shift_gal"].cpu().numpy() - b["shift_gal"].cpu().numpy()).max() <= 1e-4
         assert np.abs(a["shift_ran"].cpu().numpy() - b["shift_ran"].cpu().numpy()).max() <= 1e-4
+    # the shifts written into the caller's buffers of an earlier call
+    bufs = [(torch.full_like(a["shift_gal"], float("nan")), torch.full_like(a["shift_ran"], float("nan")))
+            for a in r0]
+    s2, r2 = B.batch_run(batch_mocks, start=B.START_FFTA, tol=1e-6, max_iter=60, out=bufs)
+    assert s2 == B.OK
+    for (bg, br), a, c in zip(bufs, r1, r2):
+        assert c["shift_gal"] is bg and c["shift_ran"] is br
+        assert np.abs(a["shift_gal"].cpu().numpy() - bg.cpu().numpy()).max() <= 1e-4
+        assert np.abs(a["shift_ran"].cpu().numpy() - br.cpu().numpy()).max() <= 1e-4
 
 
 def test_batch_item_vs_oracle(lib, batch_mocks):
