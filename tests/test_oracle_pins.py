@@ -582,3 +582,34 @@ def test_convergence_rule_reproduces_the_papers_tables():
     strict = next(n for n in range(len(plain2))
                   if all(abs(plain2[k + 1] - plain2[k]) < 0.01 * abs(plain2[k]) for k in range(n, len(plain2) - 1)))
     assert strict == 5
+
+
+def test_nyquist_mode_takes_the_mean_of_its_two_aliases():
+    """On the mesh, a mode with the Nyquist index along x, m = (N/2, 1, 0), is the same field as its
+    alias (-N/2, 1, 0), and Eq. Zeldovich gives the two opposite x components.  The real answer is
+    their mean (the reading of the Nyquist index: derivative wavenumber 0 along x there, k^2 the
+    full |k|^2): Psi_x = 0, Psi_y = -(A/b) (k_y/k^2) sin(k.x) with k^2 = k_N^2 + k_y^2."""
+    n, L, A, b = 16, 400.0, 0.9, 2.1
+    k, arg = _mode(n, L, (n // 2, 1, 0))
+    delta = A * np.cos(arg)
+    psi = O.zeldovich(delta / b, L)
+    k_alias = k * np.array([-1.0, 1.0, 1.0])
+    arg_alias = _mode(n, L, (-n // 2, 1, 0))[1]
+    assert np.abs(np.cos(arg_alias) - np.cos(arg)).max() < 1e-12      # the same field on the nodes
+    want = -(A / b) * 0.5 * (k[:, None, None, None] * np.sin(arg)[None]
+                             + k_alias[:, None, None, None] * np.sin(arg_alias)[None]) / (k @ k)
+    assert np.abs(psi[0]).max() < 1e-13
+    assert np.abs(psi - want).max() <= 1e-12 * np.abs(want).max()
+    assert np.abs(want[1]).max() > 0.1 * A / b / np.sqrt(k @ k)      # the y component is not trivial
+
+
+def test_divergence_of_a_nyquist_mode():
+    """div of v = a sin(k.x) with the Nyquist index along x: the field equals its (-N/2, 1, 0) alias,
+    whose divergences (a.k) cos(k.x) differ in the x term, so the answer is their mean,
+    a_y k_y cos(k.x)."""
+    n, L = 16, 300.0
+    k, arg = _mode(n, L, (n // 2, 1, 0))
+    a = np.array([0.7, -1.1, 0.4])
+    v = a[:, None, None, None] * np.sin(arg)[None]
+    got = O.ifft3(O.divergence(v, L), n)
+    assert np.abs(got - a[1] * k[1] * np.cos(arg)).max() < 1e-12
