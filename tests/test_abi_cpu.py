@@ -122,3 +122,19 @@ def test_diagnostic_convergence_rule_matches_the_oracle():
         means = list(1.0 + np.cumsum(rng.choice([-1, 1], 8) * rng.choice([0.0, 0.005, 0.01, 0.02, 0.1], 8)))
         assert diagnostics.converged_at(means) == O.converged_at(means)
     assert diagnostics.converged_at([0.9]) == 0
+
+
+def test_no_cpu_fallback(tmp_path):
+    """The product path has no CPU fallback: a missing library and a missing GPU both fail loudly."""
+    saved = binding._lib
+    try:
+        binding._lib = None
+        with pytest.raises(RuntimeError, match="no CPU fallback"):
+            binding.load(str(tmp_path / "librecon_gb300.so"))
+    finally:
+        binding._lib = saved
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(RuntimeError, match="only on the GPU"):
+        binding.Recon(64, 1000.0, 2.0, 0.7, 10.0, (0.0, 0.0, 0.0))
