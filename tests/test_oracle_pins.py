@@ -613,3 +613,31 @@ def test_divergence_of_a_nyquist_mode():
     v = a[:, None, None, None] * np.sin(arg)[None]
     got = O.ifft3(O.divergence(v, L), n)
     assert np.abs(got - a[1] * k[1] * np.cos(arg)).max() < 1e-12
+
+
+def test_updates_are_curl_free():
+    """Every update of Eq. iterative is Psi = Z[S] = i k S / k^2, a gradient: k x Psi(k) = 0 (with the
+    derivative wavenumbers, Nyquist index zero), also for a radial line of sight where (Psi.r)r itself
+    has a curl; and its divergence is -S."""
+    n, L, b, f = 12, 300.0, 1.7, 0.8
+    rng = np.random.default_rng(21)
+    delta = rng.standard_normal((n, n, n))
+    rh = O.rhat_field(n, L, (-150.0, 120.0, 170.0), O.LOS_RADIAL)
+    psi0, _ = O.start_estimate(delta, b, f, L, rh, O.START_FFTA)
+    psi1 = O.update(psi0, delta, b, f, L, rh)
+    _, kd, _ = O.kgrid(n, L)
+    P = [O.fft3(psi1[j]) for j in range(3)]
+    scale = max(np.abs(p).max() for p in P)
+    for a, c in ((1, 2), (2, 0), (0, 1)):
+        assert np.abs(kd[a] * P[c] - kd[c] * P[a]).max() <= 1e-12 * scale * np.abs(kd[0]).max()
+    proj = O.radial_projection(psi0, rh)
+    Q = [O.fft3(proj[j]) for j in range(3)]
+    curl_proj = max(np.abs(kd[a] * Q[c] - kd[c] * Q[a]).max() for a, c in ((1, 2), (2, 0), (0, 1)))
+    assert curl_proj > 1e-3 * max(np.abs(q).max() for q in Q) * np.abs(kd[0]).max()
+    S_k = O.fft3(delta / b) + (f / b) * O.divergence(proj, L)
+    S_k[0, 0, 0] = 0.0
+    div = sum(1j * kd[j] * P[j] for j in range(3))
+    k, _, k2 = O.kgrid(n, L)
+    keep = (k2 > 0) & (kd[0] == k[0]) & (kd[1] == k[1]) & (kd[2] == k[2])   # no Nyquist index
+    assert keep.sum() > 0.5 * keep.size
+    assert np.abs(div + S_k)[keep].max() <= 1e-12 * np.abs(S_k).max()
