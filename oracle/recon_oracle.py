@@ -1,8 +1,8 @@
 """FP64 CPU oracle for iterative Fourier-space reconstruction (Burden, Percival & Howlett 2015).
 
 TEST INFRASTRUCTURE ONLY.  This module is the slow, obviously-correct reference that the CUDA path
-is checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
-``bench.py`` may import it.  The product path (``paper_1504_02591_gb300``) never imports, calls or
+is checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU legs of ``bench.py``
+(``cpu_baseline``, ``--cpu-full`` and the ``--impl reference`` arm) may import it.  The product path (``paper_1504_02591_gb300``) never imports, calls or
 links it, and it shares no code with the CUDA kernels.
 
 Everything is float64 numpy.  The 3-D FFT is ``scipy.fft.rfftn`` / ``irfftn`` used as a library
