@@ -1,5 +1,5 @@
 // batch_graph.h: internal interface between the batch scheduler (batch.cu) and the handle
-// (recon.cu) for running many mocks as one CUDA graph.
+// (recon.cu) for running many mocks as CUDA graphs.
 #pragma once
 #include <vector>
 

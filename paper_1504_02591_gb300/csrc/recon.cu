@@ -1789,9 +1789,9 @@ recon_status recon_helmholtz_x(recon_handle* h, const float* psi_x, float* grad_
 }  // extern "C"
 
 // ------------------------------------------------------------------------------------------------
-// Batches as one CUDA graph (recon_batch_run): each mock appends its whole reconstruction to the
-// batch's graph, with the handle of its size class.  The graph orders a class's mocks one after
-// another on the class's buffers; the host waits once, for the whole batch.
+// Batches as CUDA graphs (recon_batch_run): each mock appends its whole reconstruction to a graph
+// (its own, or the one graph of the whole batch), with the handle of its size class.  A class's
+// mocks run one after another on the class's buffers; the host waits once, for the whole batch.
 // ------------------------------------------------------------------------------------------------
 namespace rg {
 
