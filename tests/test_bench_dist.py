@@ -50,3 +50,19 @@ def test_single_process_is_unchanged():
     import bench
     assert bench.max_over_ranks(12.5, "cpu") == 12.5
     assert bench.job_value(12.5, 1) == 12.5
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    """Under torchrun the oracle's reference arm runs on rank 0 alone; another rank returns at once,
+    prints nothing and does no work (its workload is never built)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+    monkeypatch.setattr(bench, "workload", lambda mesh: pytest.fail("rank 1 built the workload"))
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1",
+                                      "--warmup", "1"])
+    args = bench.parse()
+    assert bench.reference_arm(args) is None
+    assert capsys.readouterr().out == ""
